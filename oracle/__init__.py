@@ -1,0 +1,183 @@
+"""Python access to the WIPES oracle (``wipes_oracle.c``): a brute-force binary64 CPU reference.
+
+TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the benchmark's CPU-baseline leg use
+it; the product package never imports it.  It shares no code with the CUDA path: inputs come from
+``synth`` (seeded generators) and results are compared against the library's outputs.
+
+Every function takes numpy arrays in the record layouts documented in ``synth`` and returns
+numpy arrays.  ``truncated=True`` applies the same per-pixel cutoff decision as the kernels
+(binary32 footprint rule); ``truncated=False`` evaluates every primitive at every pixel.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wipes_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# opts vector layout shared by the 3D calls: cutoff, alpha_min, alpha_max, T_min, dilation, bg(3)
+DEFAULT_OPTS_3D = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0], dtype=np.float32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no fused multiply-add contraction)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                   "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_double
+        lib.wo_footprints.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P, P, P]
+        lib.wo_tile_lists.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P, P, i64]
+        lib.wo_tile_lists.restype = i64
+        lib.wo_render2d.argtypes = [P, i64, i32, i32, f32, i32, P, i64, P]
+        lib.wo_grad2d.argtypes = [P, i64, i32, i32, f32, i32, P, P]
+        lib.wo_render3d.argtypes = [P, i64, P, i32, i32, P, i32, P, i64, P, P, P, P]
+        lib.wo_grad3d.argtypes = [P, i64, P, i32, i32, P, i32, P, P]
+        lib.wo_project3d.argtypes = [P, i64, P, i32, i32, P, P]
+        lib.wo_deform6d.argtypes = [P, i64, f64, P]
+        lib.wo_deform6d_grad.argtypes = [P, i64, f64, P, P]
+        lib.wo_cutoff_coverage.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P]
+        _lib = lib
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def footprints(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
+    """binary32 footprint rule: (rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth, rect[N,4] = u0,v0,u1,v1, valid[N])."""
+    params = _f32(params)
+    n = params.shape[0]
+    rec = np.zeros((n, 8), np.float32)
+    rect = np.zeros((n, 4), np.int32)
+    valid = np.zeros(n, np.int32)
+    camv = _f32(cam) if cam is not None else None
+    _load().wo_footprints(dims, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(rec), _ptr(rect), _ptr(valid))
+    return rec, rect, valid
+
+
+def tile_lists(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
+    """Sorted (tile, primitive) pairs: by tile, then camera depth (3D), then primitive index."""
+    params = _f32(params)
+    n = params.shape[0]
+    camv = _f32(cam) if cam is not None else None
+    lib = _load()
+    total = lib.wo_tile_lists(dims, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, None, None, 0)
+    tiles = np.zeros(max(total, 1), np.uint32)
+    prims = np.zeros(max(total, 1), np.uint32)
+    lib.wo_tile_lists(dims, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(tiles), _ptr(prims), total)
+    return tiles[:total], prims[:total]
+
+
+def _pix(pixels):
+    if pixels is None:
+        return None, 0
+    p = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+    return p, p.shape[0]
+
+
+def render2d(params, H, W, cutoff=3.0, truncated=True, pixels=None):
+    """Summed wavelet field, [H,W,3] (or [npix,3] at the given (u, v) pixels)."""
+    params = _f32(params)
+    pix, npix = _pix(pixels)
+    out = np.zeros((npix if pix is not None else H * W, 3), np.float64)
+    _load().wo_render2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(pix), npix, _ptr(out))
+    return out if pix is not None else out.reshape(H, W, 3)
+
+
+def grad2d(params, H, W, dldimg, cutoff=3.0, truncated=True):
+    """dL/dparams [N,16] for L = sum(dldimg * C)."""
+    params = _f32(params)
+    g = _f32(dldimg)
+    out = np.zeros((params.shape[0], 16), np.float64)
+    _load().wo_grad2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(g), _ptr(out))
+    return out
+
+
+def render3d(params, cam, H, W, opts=None, truncated=True, pixels=None):
+    """Front-to-back blend.  Returns (C, T_final, n_contrib, ambiguous)."""
+    params = _f32(params)
+    camv = _f32(cam)
+    o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
+    pix, npix = _pix(pixels)
+    m = npix if pix is not None else H * W
+    out = np.zeros((m, 3), np.float64)
+    T = np.zeros(m, np.float64)
+    nc = np.zeros(m, np.int32)
+    amb = np.zeros(m, np.uint8)
+    _load().wo_render3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(pix), npix,
+                        _ptr(out), _ptr(T), _ptr(nc), _ptr(amb))
+    if pix is None:
+        return out.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), amb.reshape(H, W).astype(bool)
+    return out, T, nc, amb.astype(bool)
+
+
+def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True):
+    """dL/dparams [N,20] for L = sum(dldimg * C)."""
+    params = _f32(params)
+    camv = _f32(cam)
+    o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
+    g = _f32(dldimg)
+    out = np.zeros((params.shape[0], 20), np.float64)
+    _load().wo_grad3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(g), _ptr(out))
+    return out
+
+
+def project3d(params, cam, H, W, opts=None):
+    """[N,16]: valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), 0, 0."""
+    params = _f32(params)
+    camv = _f32(cam)
+    o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
+    out = np.zeros((params.shape[0], 16), np.float64)
+    _load().wo_project3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), _ptr(out))
+    return out
+
+
+def deform6d(params6, t):
+    """Deformed 3D records [N,20] (binary64) at time t."""
+    p = _f32(params6)
+    out = np.zeros((p.shape[0], 20), np.float64)
+    _load().wo_deform6d(_ptr(p), p.shape[0], float(t), _ptr(out))
+    return out
+
+
+def deform6d_grad(params6, t, g3):
+    """dL/d(record6) [N,32] from dL/d(deformed record) [N,20]."""
+    p = _f32(params6)
+    g = np.ascontiguousarray(g3, dtype=np.float64)
+    out = np.zeros((p.shape[0], 32), np.float64)
+    _load().wo_deform6d_grad(_ptr(p), p.shape[0], float(t), _ptr(g), _ptr(out))
+    return out
+
+
+def cutoff_coverage(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
+    """(pairs inside the cutoff, of those outside the covered pixel range, pixels in the ranges)."""
+    params = _f32(params)
+    camv = _f32(cam) if cam is not None else None
+    counts = np.zeros(3, np.int64)
+    _load().wo_cutoff_coverage(dims, _ptr(params), params.shape[0], _ptr(camv), H, W, cutoff, dilation, _ptr(counts))
+    return int(counts[0]), int(counts[1]), int(counts[2])

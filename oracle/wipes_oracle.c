@@ -1,0 +1,880 @@
+/*
+ * WIPES oracle: a plain, slow, brute-force CPU reference of the wavelet rasterizer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the benchmark's CPU-baseline
+ * leg load this file.  The product library never links, includes or calls it, and it shares no
+ * code with the CUDA path.
+ *
+ * What it computes (paper: "WIPES: Wavelet-based Visual Primitives", ICCV 2025):
+ *   - the wavelet primitive  W(x) = 1/2 [cos(f.(x-mu)) + 1] G(x; mu, Sigma)     (Sec. 4.1, Eq. 5),
+ *     with G the Gaussian of Sec. 3.1 (Eq. 1) and Sigma = R S S^T R^T;
+ *   - the 2D image field  C(x) = sum_i c_i W'_i(x)   (Eq. 4 with G' replaced by W', Sec. 4.3);
+ *   - the 3D splat: EWA projection Sigma' = [J W Sigma W^T J^T]_{2x2} (Sec. 3.1), the frequency
+ *     carried by the same ray-space map (Sec. 4.1), and front-to-back alpha blending of W'
+ *     (Eq. 3 with G' replaced by W', Sec. 4.1);
+ *   - the analytic gradient of a scalar loss L = sum_x g(x).C(x) with respect to every
+ *     primitive parameter (the paper states that explicit gradients exist, Sec. 1).
+ * Values are computed in IEEE binary64, by a double loop over every pixel and every primitive.
+ *
+ * Readings of the paper (where it is silent or inconsistent):
+ *   - frequency f is given in cycles per pixel (2D) or cycles per world unit (3D), so the cosine
+ *     argument is 2 pi f.d; an extra phase phi is added inside the cosine (phi = 0 is the paper);
+ *   - 2D primitives carry no separate opacity (alpha folded into the colour, as in GaussianImage);
+ *   - pixel (u, v) is sampled at (u + 0.5, v + 0.5);
+ *   - the projected frequency is the phase gradient on the fronto-parallel plane through the
+ *     primitive's centre: f' = (fc_x tz / fx, fc_y tz / fy), fc = W f (camera frame);
+ *   - 3D: dilation 0.3 px^2, alpha clamped at alpha_max, skipped below alpha_min, blending stops
+ *     before a primitive that would take the transmittance below T_min; depth order by camera z.
+ *
+ * Decisions that floating point turns into integers (is a pixel inside a primitive's 3-sigma
+ * footprint, which tiles a primitive covers, the depth order) are taken in binary32 by the
+ * "footprint rule" below, so that they are the same decisions the kernels take.  This file is
+ * compiled with -ffp-contract=off: every binary32 expression is a sequence of single IEEE
+ * operations in source order, and a fused multiply-add occurs only where fmaf is written.
+ * The alpha and transmittance thresholds depend on exp and cos and cannot be reproduced bit for
+ * bit; pixels where one of them is within a small margin of its threshold are reported as
+ * ambiguous.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TILE 16
+#define EXT_MARGIN 1.0009765625f /* 1 + 2^-10: footprint half-extent safety factor */
+
+static const double PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------------------------------ */
+/* binary32 footprint rule                                                                     */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+    float mx, my;          /* centre in pixels */
+    float l11, l21, l22;   /* lower Cholesky factor of the inverse covariance */
+    float ex, ey;          /* half extents of the cutoff ellipse, with margin */
+    float depth;           /* camera z (3D), 0 (2D) */
+    int u0, v0, u1, v1;    /* covered pixel range (inclusive); empty if u0 > u1 */
+    int valid;
+} fp32_footprint;
+
+static int finite4(float a, float b, float c, float d) { return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d); }
+
+static void footprint_pixrect(fp32_footprint* k, int W, int H) {
+    float xlo = (k->mx - k->ex) - 0.5f;
+    float xhi = (k->mx + k->ex) - 0.5f;
+    float ylo = (k->my - k->ey) - 0.5f;
+    float yhi = (k->my + k->ey) - 0.5f;
+    xlo = fminf(fmaxf(xlo, -1.0f), (float)W);
+    xhi = fminf(fmaxf(xhi, -1.0f), (float)W);
+    ylo = fminf(fmaxf(ylo, -1.0f), (float)H);
+    yhi = fminf(fmaxf(yhi, -1.0f), (float)H);
+    int u0 = (int)ceilf(xlo), u1 = (int)floorf(xhi);
+    int v0 = (int)ceilf(ylo), v1 = (int)floorf(yhi);
+    if (u0 < 0) u0 = 0;
+    if (v0 < 0) v0 = 0;
+    if (u1 > W - 1) u1 = W - 1;
+    if (v1 > H - 1) v1 = H - 1;
+    k->u0 = u0; k->u1 = u1; k->v0 = v0; k->v1 = v1;
+    if (u0 > u1 || v0 > v1) { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
+}
+
+/* 2D record: mu(2) s(2) theta f(2) phi c(3) */
+static void footprint2d(const float* p, float cutoff, int W, int H, fp32_footprint* k) {
+    float sx = p[2], sy = p[3];
+    float c = (float)cos((double)p[4]);
+    float s = (float)sin((double)p[4]);
+    float sx2 = sx * sx, sy2 = sy * sy;
+    float ix = 1.0f / sx2, iy = 1.0f / sy2;
+    float cc = c * c, ss = s * s, cs = c * s;
+    float A = cc * ix + ss * iy;
+    float B = cs * (ix - iy);
+    float l11 = sqrtf(A);
+    float l21 = B / l11;
+    float l22 = 1.0f / ((sx * sy) * l11);
+    float vxx = cc * sx2 + ss * sy2;
+    float vyy = ss * sx2 + cc * sy2;
+    k->mx = p[0];
+    k->my = p[1];
+    k->l11 = l11; k->l21 = l21; k->l22 = l22;
+    k->ex = (cutoff * sqrtf(vxx)) * EXT_MARGIN;
+    k->ey = (cutoff * sqrtf(vyy)) * EXT_MARGIN;
+    k->depth = 0.0f;
+    k->valid = finite4(k->mx, k->my, l11, l21) && finite4(l22, k->ex, k->ey, 1.0f) && sx > 0.0f && sy > 0.0f &&
+               l11 > 0.0f && l22 > 0.0f;
+    if (k->valid) footprint_pixrect(k, W, H);
+    else { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
+}
+
+/* 3D record: mu(3) s(3) q(4: w,x,y,z) f(3) phi opacity c(3); camera: V[12] fx fy cx cy near */
+static void footprint3d(const float* p, const float* cam, float cutoff, float dil, int W, int H, fp32_footprint* k) {
+    const float* V = cam;
+    float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15], near_z = cam[16];
+    float tx = ((V[0] * p[0] + V[1] * p[1]) + V[2] * p[2]) + V[3];
+    float ty = ((V[4] * p[0] + V[5] * p[1]) + V[6] * p[2]) + V[7];
+    float tz = ((V[8] * p[0] + V[9] * p[1]) + V[10] * p[2]) + V[11];
+    k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0;
+    k->valid = 0;
+    if (!(tz > near_z) || !isfinite(tz) || !isfinite(tx) || !isfinite(ty)) return;
+    float qw = p[6], qx = p[7], qy = p[8], qz = p[9];
+    float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
+    float r = sqrtf(n2);
+    qw = qw / r; qx = qx / r; qy = qy / r; qz = qz / r;
+    float xx = qx * qx, yy = qy * qy, zz = qz * qz;
+    float xy = qx * qy, xz = qx * qz, yz = qy * qz;
+    float wx = qw * qx, wy = qw * qy, wz = qw * qz;
+    float R[9];
+    R[0] = 1.0f - 2.0f * (yy + zz); R[1] = 2.0f * (xy - wz);        R[2] = 2.0f * (xz + wy);
+    R[3] = 2.0f * (xy + wz);        R[4] = 1.0f - 2.0f * (xx + zz); R[5] = 2.0f * (yz - wx);
+    R[6] = 2.0f * (xz - wy);        R[7] = 2.0f * (yz + wx);        R[8] = 1.0f - 2.0f * (xx + yy);
+    float M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i * 3 + j] = R[i * 3 + j] * p[3 + j];
+    float Q[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            Q[i * 3 + j] = (V[i * 4 + 0] * M[0 * 3 + j] + V[i * 4 + 1] * M[1 * 3 + j]) + V[i * 4 + 2] * M[2 * 3 + j];
+    float limx = 1.3f * ((0.5f * (float)W) / fx);
+    float limy = 1.3f * ((0.5f * (float)H) / fy);
+    float txz = fminf(limx, fmaxf(-limx, tx / tz));
+    float tyz = fminf(limy, fmaxf(-limy, ty / tz));
+    float j00 = fx / tz, j02 = -((fx * txz) / tz);
+    float j11 = fy / tz, j12 = -((fy * tyz) / tz);
+    float P0[3], P1[3];
+    for (int j = 0; j < 3; ++j) {
+        P0[j] = j00 * Q[0 * 3 + j] + j02 * Q[2 * 3 + j];
+        P1[j] = j11 * Q[1 * 3 + j] + j12 * Q[2 * 3 + j];
+    }
+    float n0 = (P0[0] * P0[0] + P0[1] * P0[1]) + P0[2] * P0[2];
+    float n1 = (P1[0] * P1[0] + P1[1] * P1[1]) + P1[2] * P1[2];
+    float s01 = (P0[0] * P1[0] + P0[1] * P1[1]) + P0[2] * P1[2];
+    float c0 = P0[1] * P1[2] - P0[2] * P1[1];
+    float c1 = P0[2] * P1[0] - P0[0] * P1[2];
+    float c2 = P0[0] * P1[1] - P0[1] * P1[0];
+    float S00 = n0 + dil, S11 = n1 + dil;
+    float D = (((c0 * c0 + c1 * c1) + c2 * c2) + dil * (n0 + n1)) + dil * dil;
+    float l22 = 1.0f / sqrtf(S11);
+    float l11 = sqrtf(S11 / D);
+    float l21 = -(s01 / sqrtf(S11 * D));
+    k->mx = ((fx * tx) / tz) + cx;
+    k->my = ((fy * ty) / tz) + cy;
+    k->l11 = l11; k->l21 = l21; k->l22 = l22;
+    k->ex = (cutoff * sqrtf(S00)) * EXT_MARGIN;
+    k->ey = (cutoff * sqrtf(S11)) * EXT_MARGIN;
+    k->depth = tz;
+    k->valid = finite4(k->mx, k->my, l11, l21) && finite4(l22, k->ex, k->ey, D) && D > 0.0f && S11 > 0.0f &&
+               l11 > 0.0f && l22 > 0.0f;
+    if (k->valid) footprint_pixrect(k, W, H);
+    else { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
+}
+
+/* binary32 squared Mahalanobis distance of pixel (u, v) from the footprint centre */
+static float q32(const fp32_footprint* k, int u, int v) {
+    float dx = ((float)u + 0.5f) - k->mx;
+    float dy = ((float)v + 0.5f) - k->my;
+    float a = fmaf(k->l11, dx, k->l21 * dy);
+    float b = k->l22 * dy;
+    return fmaf(a, a, b * b);
+}
+
+static uint32_t f32_bits(float x) { uint32_t b; memcpy(&b, &x, 4); return b; }
+
+/* Exported view of the footprint rule: rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth; rect[N,4] = u0,v0,u1,v1;
+ * valid[N].  dims = 2 or 3; cam and dil are ignored in 2D. */
+int wo_footprints(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
+                  float* rec, int32_t* rect, int32_t* valid) {
+    for (int64_t i = 0; i < N; ++i) {
+        fp32_footprint k;
+        if (dims == 2) footprint2d(params + i * 16, cutoff, W, H, &k);
+        else footprint3d(params + i * 20, cam, cutoff, dil, W, H, &k);
+        if (rec) {
+            float* r = rec + i * 8;
+            r[0] = k.mx; r[1] = k.my; r[2] = k.l11; r[3] = k.l21; r[4] = k.l22; r[5] = k.ex; r[6] = k.ey; r[7] = k.depth;
+        }
+        if (rect) { rect[i * 4 + 0] = k.u0; rect[i * 4 + 1] = k.v0; rect[i * 4 + 2] = k.u1; rect[i * 4 + 3] = k.v1; }
+        if (valid) valid[i] = k.valid;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* tile lists: every (tile, primitive) pair whose tile meets the primitive's covered pixel     */
+/* range, ordered by tile, then depth (3D), then primitive index                               */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct { uint32_t tile, depth, prim; } tile_entry;
+
+static int cmp_entry(const void* a, const void* b) {
+    const tile_entry* x = (const tile_entry*)a;
+    const tile_entry* y = (const tile_entry*)b;
+    if (x->tile != y->tile) return x->tile < y->tile ? -1 : 1;
+    if (x->depth != y->depth) return x->depth < y->depth ? -1 : 1;
+    if (x->prim != y->prim) return x->prim < y->prim ? -1 : 1;
+    return 0;
+}
+
+static fp32_footprint* all_footprints(int dims, const float* params, int64_t N, const float* cam, int H, int W,
+                                      float cutoff, float dil) {
+    fp32_footprint* k = (fp32_footprint*)malloc(sizeof(fp32_footprint) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) {
+        if (dims == 2) footprint2d(params + i * 16, cutoff, W, H, &k[i]);
+        else footprint3d(params + i * 20, cam, cutoff, dil, W, H, &k[i]);
+    }
+    return k;
+}
+
+/* Returns the number of entries (also when it exceeds cap; then only cap are written). */
+int64_t wo_tile_lists(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
+                      uint32_t* tile_out, uint32_t* prim_out, int64_t cap) {
+    fp32_footprint* k = all_footprints(dims, params, N, cam, H, W, cutoff, dil);
+    int tiles_x = (W + TILE - 1) / TILE;
+    int64_t total = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!k[i].valid || k[i].u0 > k[i].u1) continue;
+        total += (int64_t)(k[i].u1 / TILE - k[i].u0 / TILE + 1) * (k[i].v1 / TILE - k[i].v0 / TILE + 1);
+    }
+    tile_entry* e = (tile_entry*)malloc(sizeof(tile_entry) * (size_t)(total > 0 ? total : 1));
+    int64_t n = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!k[i].valid || k[i].u0 > k[i].u1) continue;
+        for (int ty = k[i].v0 / TILE; ty <= k[i].v1 / TILE; ++ty)
+            for (int tx = k[i].u0 / TILE; tx <= k[i].u1 / TILE; ++tx) {
+                e[n].tile = (uint32_t)(ty * tiles_x + tx);
+                e[n].depth = dims == 3 ? f32_bits(k[i].depth) : 0u;
+                e[n].prim = (uint32_t)i;
+                ++n;
+            }
+    }
+    qsort(e, (size_t)n, sizeof(tile_entry), cmp_entry);
+    for (int64_t j = 0; j < n && j < cap; ++j) {
+        tile_out[j] = e[j].tile;
+        prim_out[j] = e[j].prim;
+    }
+    free(e);
+    free(k);
+    return total;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* small dense helpers (binary64)                                                              */
+/* ------------------------------------------------------------------------------------------ */
+
+static void mat2_inv(const double a[4], double out[4]) {
+    double det = a[0] * a[3] - a[1] * a[2];
+    out[0] = a[3] / det;
+    out[1] = -a[1] / det;
+    out[2] = -a[2] / det;
+    out[3] = a[0] / det;
+}
+
+/* C = A (m x k) * B (k x n) */
+static void matmul(const double* A, const double* B, double* C, int m, int k, int n) {
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int t = 0; t < k; ++t) s += A[i * k + t] * B[t * n + j];
+            C[i * n + j] = s;
+        }
+}
+
+static void transpose(const double* A, double* At, int m, int n) {
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) At[j * m + i] = A[i * n + j];
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* the projected (image-plane) wavelet of one primitive, binary64                              */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+    int valid;
+    double mu[2];    /* mu' (pixels) */
+    double K[4];     /* inverse of Sigma' (row-major 2x2) */
+    double f[2];     /* f' (cycles per pixel) */
+    double phi;      /* phase (radians) */
+    double o;        /* opacity (3D) */
+    double c[3];     /* colour */
+    /* 3D chain-rule intermediates */
+    double t[3], R[9], M[9], V[9], Sc[9], J[6], fc[3], qn[4], qnorm, s[3];
+    int unclamped_x, unclamped_y;
+} proj;
+
+static void project2d(const float* p, proj* w) {
+    double sx = p[2], sy = p[3], th = p[4];
+    double c = cos(th), s = sin(th);
+    /* Sigma = R diag(sx^2, sy^2) R^T  (Sec. 3.1, Sigma = R S S^T R^T) */
+    double Sig[4] = {c * c * sx * sx + s * s * sy * sy, c * s * (sx * sx - sy * sy),
+                     c * s * (sx * sx - sy * sy), s * s * sx * sx + c * c * sy * sy};
+    memset(w, 0, sizeof(*w));
+    w->valid = sx > 0 && sy > 0 && isfinite(sx) && isfinite(sy);
+    mat2_inv(Sig, w->K);
+    w->mu[0] = p[0]; w->mu[1] = p[1];
+    w->f[0] = p[5]; w->f[1] = p[6];
+    w->phi = p[7];
+    w->o = 1.0;
+    w->c[0] = p[8]; w->c[1] = p[9]; w->c[2] = p[10];
+    w->s[0] = sx; w->s[1] = sy;
+}
+
+static void quat_to_rot(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void project3d(const float* p, const float* cam, int H, int W, double dil, int valid32, proj* w) {
+    memset(w, 0, sizeof(*w));
+    w->valid = valid32;
+    double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) w->V[i * 3 + j] = cam[i * 4 + j];
+    for (int i = 0; i < 3; ++i)
+        w->t[i] = w->V[i * 3 + 0] * p[0] + w->V[i * 3 + 1] * p[1] + w->V[i * 3 + 2] * p[2] + (double)cam[i * 4 + 3];
+    double tx = w->t[0], ty = w->t[1], tz = w->t[2];
+    double qr[4] = {p[6], p[7], p[8], p[9]};
+    w->qnorm = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+    for (int i = 0; i < 4; ++i) w->qn[i] = qr[i] / w->qnorm;
+    quat_to_rot(w->qn, w->R);
+    for (int j = 0; j < 3; ++j) w->s[j] = p[3 + j];
+    /* Sigma = R S S^T R^T, camera frame Sc = V Sigma V^T */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) w->M[i * 3 + j] = w->R[i * 3 + j] * w->s[j];
+    double Mt[9], Sig[9], Vt[9], tmp[9];
+    transpose(w->M, Mt, 3, 3);
+    matmul(w->M, Mt, Sig, 3, 3, 3);
+    transpose(w->V, Vt, 3, 3);
+    matmul(w->V, Sig, tmp, 3, 3, 3);
+    matmul(tmp, Vt, w->Sc, 3, 3, 3);
+    /* local affine Jacobian of the perspective map, with the usual clamp of the view angle */
+    double limx = 1.3 * (0.5 * W / fx), limy = 1.3 * (0.5 * H / fy);
+    double txz = tx / tz, tyz = ty / tz;
+    w->unclamped_x = txz > -limx && txz < limx;
+    w->unclamped_y = tyz > -limy && tyz < limy;
+    if (txz < -limx) txz = -limx;
+    if (txz > limx) txz = limx;
+    if (tyz < -limy) tyz = -limy;
+    if (tyz > limy) tyz = limy;
+    double J[6] = {fx / tz, 0.0, -fx * txz / tz, 0.0, fy / tz, -fy * tyz / tz};
+    memcpy(w->J, J, sizeof(J));
+    double Jt[6], JS[6], S2[4];
+    transpose(J, Jt, 2, 3);
+    matmul(J, w->Sc, JS, 2, 3, 3);
+    matmul(JS, Jt, S2, 2, 3, 2);
+    S2[0] += dil;
+    S2[3] += dil;
+    mat2_inv(S2, w->K);
+    w->mu[0] = fx * tx / tz + cx;
+    w->mu[1] = fy * ty / tz + cy;
+    for (int i = 0; i < 3; ++i) w->fc[i] = w->V[i * 3 + 0] * p[10] + w->V[i * 3 + 1] * p[11] + w->V[i * 3 + 2] * p[12];
+    w->f[0] = w->fc[0] * tz / fx;
+    w->f[1] = w->fc[1] * tz / fy;
+    w->phi = p[13];
+    w->o = p[14];
+    w->c[0] = p[15]; w->c[1] = p[16]; w->c[2] = p[17];
+}
+
+/* W'(x) and its pieces at pixel (u, v) */
+typedef struct { double d[2], Kd[2], q, G, ca, sa, M, W; } wval;
+
+static void eval_wavelet(const proj* w, int u, int v, wval* e) {
+    e->d[0] = (u + 0.5) - w->mu[0];
+    e->d[1] = (v + 0.5) - w->mu[1];
+    e->Kd[0] = w->K[0] * e->d[0] + w->K[1] * e->d[1];
+    e->Kd[1] = w->K[2] * e->d[0] + w->K[3] * e->d[1];
+    e->q = e->d[0] * e->Kd[0] + e->d[1] * e->Kd[1];
+    e->G = exp(-0.5 * e->q);
+    double arg = 2.0 * PI * (w->f[0] * e->d[0] + w->f[1] * e->d[1]) + w->phi;
+    e->ca = cos(arg);
+    e->sa = sin(arg);
+    e->M = 0.5 * (1.0 + e->ca);
+    e->W = e->M * e->G;
+}
+
+/* per-primitive image-plane gradient accumulator: dL/d(mu', K (full 2x2), f', phi, o, c) */
+typedef struct { double mu[2], K[4], f[2], phi, o, c[3]; } pgrad;
+
+/* add gW * dW'/d(mu', K, f', phi) */
+static void accum_wavelet_grad(const proj* w, const wval* e, double gW, pgrad* g) {
+    /* dW/dmu = W K d + pi G sin(arg) f ;  dW/df = -pi G sin(arg) d ;  dW/dphi = -G sin(arg) / 2 ;
+       dW/dK_ab = -W d_a d_b / 2 */
+    for (int a = 0; a < 2; ++a) {
+        g->mu[a] += gW * (e->W * e->Kd[a] + PI * e->G * e->sa * w->f[a]);
+        g->f[a] += gW * (-PI * e->G * e->sa * e->d[a]);
+    }
+    g->phi += gW * (-0.5 * e->G * e->sa);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) g->K[a * 2 + b] += gW * (-0.5 * e->W * e->d[a] * e->d[b]);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 2D: summed field                                                                            */
+/* ------------------------------------------------------------------------------------------ */
+
+static int pixel_of(const int32_t* pix, int64_t j, int W, int* u, int* v) {
+    if (pix) { *u = pix[2 * j]; *v = pix[2 * j + 1]; }
+    else { *u = (int)(j % W); *v = (int)(j / W); }
+    return 0;
+}
+
+/* out[npix,3] (or [H*W,3] when pix is NULL).  truncated: include a primitive at a pixel only if the
+ * binary32 footprint rule puts the pixel inside its cutoff ellipse; otherwise every primitive counts. */
+int wo_render2d(const float* params, int64_t N, int H, int W, float cutoff, int truncated, const int32_t* pix,
+                int64_t npix, double* out) {
+    fp32_footprint* k = all_footprints(2, params, N, NULL, H, W, cutoff, 0.0f);
+    proj* w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, &w[i]);
+    float k2 = cutoff * cutoff;
+    int64_t np = pix ? npix : (int64_t)H * W;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < np; ++j) {
+        int u, v;
+        pixel_of(pix, j, W, &u, &v);
+        double C[3] = {0, 0, 0};
+        for (int64_t i = 0; i < N; ++i) {
+            if (truncated) {
+                if (!k[i].valid || !(q32(&k[i], u, v) <= k2)) continue;
+            } else if (!w[i].valid) continue;
+            wval e;
+            eval_wavelet(&w[i], u, v, &e);
+            for (int ch = 0; ch < 3; ++ch) C[ch] += w[i].c[ch] * e.W;
+        }
+        for (int ch = 0; ch < 3; ++ch) out[j * 3 + ch] = C[ch];
+    }
+    free(w);
+    free(k);
+    return 0;
+}
+
+/* chain the image-plane gradient of a 2D primitive to its record: mu(2) s(2) theta f(2) phi c(3) */
+static void chain2d(const float* p, const pgrad* g, double* out) {
+    double sx = p[2], sy = p[3], th = p[4];
+    double c = cos(th), s = sin(th);
+    double R[4] = {c, -s, s, c}, Rt[4] = {c, s, -s, c};
+    double dR[4] = {-s, -c, c, -s}, dRt[4] = {-s, c, -c, -s};
+    double Dinv[4] = {1.0 / (sx * sx), 0, 0, 1.0 / (sy * sy)};
+    double t1[4], t2[4], dK[4];
+    /* K = R D^-1 R^T:  dK/dtheta = R' D^-1 R^T + R D^-1 R'^T */
+    matmul(dR, Dinv, t1, 2, 2, 2);
+    matmul(t1, Rt, t2, 2, 2, 2);
+    matmul(R, Dinv, t1, 2, 2, 2);
+    matmul(t1, dRt, dK, 2, 2, 2);
+    double gth = 0.0;
+    for (int a = 0; a < 4; ++a) gth += g->K[a] * (t2[a] + dK[a]);
+    double gs[2];
+    for (int j = 0; j < 2; ++j) {
+        double sj = j == 0 ? sx : sy;
+        double Dj[4] = {0, 0, 0, 0};
+        Dj[j * 3] = -2.0 / (sj * sj * sj);
+        matmul(R, Dj, t1, 2, 2, 2);
+        matmul(t1, Rt, t2, 2, 2, 2);
+        gs[j] = 0.0;
+        for (int a = 0; a < 4; ++a) gs[j] += g->K[a] * t2[a];
+    }
+    memset(out, 0, sizeof(double) * 16);
+    out[0] = g->mu[0]; out[1] = g->mu[1];
+    out[2] = gs[0]; out[3] = gs[1];
+    out[4] = gth;
+    out[5] = g->f[0]; out[6] = g->f[1];
+    out[7] = g->phi;
+    out[8] = g->c[0]; out[9] = g->c[1]; out[10] = g->c[2];
+}
+
+/* grad[N,16] of L = sum_pixels dldimg . C */
+int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int truncated, const float* dldimg,
+              double* grad) {
+    fp32_footprint* k = all_footprints(2, params, N, NULL, H, W, cutoff, 0.0f);
+    proj* w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, &w[i]);
+    pgrad* acc = (pgrad*)calloc((size_t)(N > 0 ? N : 1), sizeof(pgrad));
+    float k2 = cutoff * cutoff;
+    /* primitive-major so that each accumulator has one writer */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+        if (!w[i].valid) continue;
+        if (truncated && !k[i].valid) continue;
+        pgrad g;
+        memset(&g, 0, sizeof(g));
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                if (truncated && !(q32(&k[i], u, v) <= k2)) continue;
+                const float* gp = dldimg + ((int64_t)v * W + u) * 3;
+                wval e;
+                eval_wavelet(&w[i], u, v, &e);
+                double gW = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    g.c[ch] += gp[ch] * e.W;
+                    gW += gp[ch] * w[i].c[ch];
+                }
+                accum_wavelet_grad(&w[i], &e, gW, &g);
+            }
+        acc[i] = g;
+    }
+    for (int64_t i = 0; i < N; ++i) chain2d(params + i * 16, &acc[i], grad + i * 16);
+    free(acc);
+    free(w);
+    free(k);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 3D: projection and front-to-back alpha blending                                             */
+/* ------------------------------------------------------------------------------------------ */
+
+/* opts[8] = cutoff, alpha_min, alpha_max, T_min, dilation, bg_r, bg_g, bg_b */
+typedef struct { float cutoff, amin, amax, Tmin, dil; double bg[3]; } blend_opts;
+
+static blend_opts read_opts(const float* o) {
+    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}};
+    return b;
+}
+
+typedef struct { uint32_t depth, prim; } order_entry;
+
+static int cmp_order(const void* a, const void* b) {
+    const order_entry* x = (const order_entry*)a;
+    const order_entry* y = (const order_entry*)b;
+    if (x->depth != y->depth) return x->depth < y->depth ? -1 : 1;
+    return x->prim < y->prim ? -1 : (x->prim > y->prim);
+}
+
+typedef struct {
+    fp32_footprint* k;
+    proj* w;
+    uint32_t* order; /* valid primitives, front to back */
+    int64_t nvalid;
+} scene3;
+
+static void scene3_build(const float* params, int64_t N, const float* cam, int H, int W, const blend_opts* o, scene3* s) {
+    s->k = all_footprints(3, params, N, cam, H, W, o->cutoff, o->dil);
+    s->w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
+    order_entry* e = (order_entry*)malloc(sizeof(order_entry) * (size_t)(N > 0 ? N : 1));
+    int64_t n = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        project3d(params + i * 20, cam, H, W, o->dil, s->k[i].valid, &s->w[i]);
+        if (s->k[i].valid) { e[n].depth = f32_bits(s->k[i].depth); e[n].prim = (uint32_t)i; ++n; }
+    }
+    qsort(e, (size_t)n, sizeof(order_entry), cmp_order);
+    s->order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t j = 0; j < n; ++j) s->order[j] = e[j].prim;
+    s->nvalid = n;
+    free(e);
+}
+
+static void scene3_free(scene3* s) { free(s->k); free(s->w); free(s->order); }
+
+#define AMB_ALPHA 2e-6
+#define AMB_T_REL 2e-4
+
+typedef struct { uint32_t prim; double alpha, T, Wv; int clamped; wval e; } contrib;
+
+/* Blend one pixel front to back.  Writes the contributors (when list != NULL), returns their count.
+ * *amb is set when a threshold decision is within its ambiguity margin. */
+static int64_t blend_pixel(const scene3* s, int u, int v, const blend_opts* o, int truncated, double C[3],
+                           double* Tout, int* amb, contrib* list) {
+    double T = 1.0;
+    float k2 = o->cutoff * o->cutoff;
+    int64_t n = 0;
+    C[0] = C[1] = C[2] = 0.0;
+    *amb = 0;
+    for (int64_t j = 0; j < s->nvalid; ++j) {
+        uint32_t i = s->order[j];
+        if (truncated && !(q32(&s->k[i], u, v) <= k2)) continue;
+        wval e;
+        eval_wavelet(&s->w[i], u, v, &e);
+        double raw = s->w[i].o * e.W;
+        if (fabs(raw - (double)o->amin) < AMB_ALPHA || fabs(raw - (double)o->amax) < AMB_ALPHA) *amb = 1;
+        int clamped = raw > (double)o->amax;
+        double alpha = clamped ? (double)o->amax : raw;
+        if (alpha < (double)o->amin) continue;
+        double testT = T * (1.0 - alpha);
+        if (o->Tmin > 0.0f && fabs(testT - (double)o->Tmin) < AMB_T_REL * (double)o->Tmin) *amb = 1;
+        if (testT < (double)o->Tmin) break;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += s->w[i].c[ch] * alpha * T;
+        if (list) {
+            list[n].prim = i; list[n].alpha = alpha; list[n].T = T; list[n].Wv = e.W;
+            list[n].clamped = clamped; list[n].e = e;
+        }
+        ++n;
+        T = testT;
+    }
+    for (int ch = 0; ch < 3; ++ch) C[ch] += T * o->bg[ch];
+    *Tout = T;
+    return n;
+}
+
+/* out[npix,3], Tout[npix], ncontrib[npix], ambiguous[npix] (any may be NULL except out) */
+int wo_render3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, int truncated,
+                const int32_t* pix, int64_t npix, double* out, double* Tout, int32_t* ncontrib, uint8_t* ambiguous) {
+    blend_opts o = read_opts(opts);
+    scene3 s;
+    scene3_build(params, N, cam, H, W, &o, &s);
+    int64_t np = pix ? npix : (int64_t)H * W;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < np; ++j) {
+        int u, v, amb;
+        pixel_of(pix, j, W, &u, &v);
+        double C[3], T;
+        int64_t n = blend_pixel(&s, u, v, &o, truncated, C, &T, &amb, NULL);
+        for (int ch = 0; ch < 3; ++ch) out[j * 3 + ch] = C[ch];
+        if (Tout) Tout[j] = T;
+        if (ncontrib) ncontrib[j] = (int32_t)n;
+        if (ambiguous) ambiguous[j] = (uint8_t)amb;
+    }
+    scene3_free(&s);
+    return 0;
+}
+
+/* d(entry of R(q))/d(q) for a unit quaternion q = (w, x, y, z); dR[e*4 + m] = dR_e / dq_m */
+static void quat_rot_jac(const double q[4], double dR[36]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double J[36] = {
+        /* R00 */ 0, 0, -4 * y, -4 * z,
+        /* R01 */ -2 * z, 2 * y, 2 * x, -2 * w,
+        /* R02 */ 2 * y, 2 * z, 2 * w, 2 * x,
+        /* R10 */ 2 * z, 2 * y, 2 * x, 2 * w,
+        /* R11 */ 0, -4 * x, 0, -4 * z,
+        /* R12 */ -2 * x, -2 * w, 2 * z, 2 * y,
+        /* R20 */ -2 * y, 2 * z, -2 * w, 2 * x,
+        /* R21 */ 2 * x, 2 * w, 2 * z, 2 * y,
+        /* R22 */ 0, -4 * x, -4 * y, 0};
+    memcpy(dR, J, sizeof(J));
+}
+
+/* chain the image-plane gradient of a 3D primitive to its record:
+ * mu(3) s(3) q(4) f(3) phi opacity c(3) */
+static void chain3d(const proj* w, const float* cam, const pgrad* g, double* out) {
+    double fx = cam[12], fy = cam[13];
+    double tx = w->t[0], ty = w->t[1], tz = w->t[2];
+    memset(out, 0, sizeof(double) * 20);
+    /* K = Sigma'^-1:  dL/dSigma' = -K (dL/dK) K */
+    double t1[4], gS2[4];
+    matmul(w->K, g->K, t1, 2, 2, 2);
+    matmul(t1, w->K, gS2, 2, 2, 2);
+    for (int a = 0; a < 4; ++a) gS2[a] = -gS2[a];
+    /* Sigma' = J Sc J^T + dil I:  dL/dJ = (G + G^T) J Sc,  dL/dSc = J^T G J */
+    double Gs[4] = {gS2[0] + gS2[0], gS2[1] + gS2[2], gS2[2] + gS2[1], gS2[3] + gS2[3]};
+    double JSc[6], gJ[6], Jt[6], tmp[6], gSc[9];
+    matmul(w->J, w->Sc, JSc, 2, 3, 3);
+    matmul(Gs, JSc, gJ, 2, 2, 3);
+    transpose(w->J, Jt, 2, 3);
+    matmul(Jt, gS2, tmp, 3, 2, 2);
+    matmul(tmp, w->J, gSc, 3, 2, 3);
+    /* Sc = V Sigma V^T:  dL/dSigma = V^T gSc V */
+    double Vt[9], t9[9], gSig[9];
+    transpose(w->V, Vt, 3, 3);
+    matmul(Vt, gSc, t9, 3, 3, 3);
+    matmul(t9, w->V, gSig, 3, 3, 3);
+    /* Sigma = M M^T:  dL/dM = (gSig + gSig^T) M */
+    double gSym[9], gM[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) gSym[i * 3 + j] = gSig[i * 3 + j] + gSig[j * 3 + i];
+    matmul(gSym, w->M, gM, 3, 3, 3);
+    /* M = R S */
+    double gR[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            gR[i * 3 + j] = gM[i * 3 + j] * w->s[j];
+            out[3 + j] += gM[i * 3 + j] * w->R[i * 3 + j];
+        }
+    /* R(qn), qn = q / |q| */
+    double dR[36], gqn[4] = {0, 0, 0, 0};
+    quat_rot_jac(w->qn, dR);
+    for (int e = 0; e < 9; ++e)
+        for (int m = 0; m < 4; ++m) gqn[m] += gR[e] * dR[e * 4 + m];
+    double dot = 0.0;
+    for (int m = 0; m < 4; ++m) dot += w->qn[m] * gqn[m];
+    for (int m = 0; m < 4; ++m) out[6 + m] = (gqn[m] - w->qn[m] * dot) / w->qnorm;
+    /* camera-frame centre t: through mu', f' and J */
+    double gt[3] = {0, 0, 0};
+    gt[0] += g->mu[0] * fx / tz;
+    gt[2] += -g->mu[0] * fx * tx / (tz * tz);
+    gt[1] += g->mu[1] * fy / tz;
+    gt[2] += -g->mu[1] * fy * ty / (tz * tz);
+    double gfc[3] = {g->f[0] * tz / fx, g->f[1] * tz / fy, 0.0};
+    gt[2] += g->f[0] * w->fc[0] / fx + g->f[1] * w->fc[1] / fy;
+    /* J = [[fx/tz, 0, -fx txz/tz], [0, fy/tz, -fy tyz/tz]], txz = clamp(tx/tz) */
+    double txz = -w->J[2] * tz / fx, tyz = -w->J[5] * tz / fy;
+    gt[2] += gJ[0] * (-fx / (tz * tz));
+    gt[2] += gJ[4] * (-fy / (tz * tz));
+    gt[2] += gJ[2] * (fx * txz / (tz * tz));
+    gt[2] += gJ[5] * (fy * tyz / (tz * tz));
+    if (w->unclamped_x) {
+        /* d txz/dtx = 1/tz, d txz/dtz = -tx/tz^2 */
+        gt[0] += gJ[2] * (-fx / tz) * (1.0 / tz);
+        gt[2] += gJ[2] * (-fx / tz) * (-tx / (tz * tz));
+    }
+    if (w->unclamped_y) {
+        gt[1] += gJ[5] * (-fy / tz) * (1.0 / tz);
+        gt[2] += gJ[5] * (-fy / tz) * (-ty / (tz * tz));
+    }
+    /* t = V mu + t0,  fc = V f */
+    for (int j = 0; j < 3; ++j) {
+        out[j] = Vt[j * 3 + 0] * gt[0] + Vt[j * 3 + 1] * gt[1] + Vt[j * 3 + 2] * gt[2];
+        out[10 + j] = Vt[j * 3 + 0] * gfc[0] + Vt[j * 3 + 1] * gfc[1] + Vt[j * 3 + 2] * gfc[2];
+    }
+    out[13] = g->phi;
+    out[14] = g->o;
+    out[15] = g->c[0]; out[16] = g->c[1]; out[17] = g->c[2];
+}
+
+/* grad[N,20] of L = sum_pixels dldimg . C.  Pixels with a zero upstream gradient are skipped. */
+int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, int truncated,
+              const float* dldimg, double* grad) {
+    blend_opts o = read_opts(opts);
+    scene3 s;
+    scene3_build(params, N, cam, H, W, &o, &s);
+    int nthreads = 1;
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    nthreads = omp_get_max_threads();
+#endif
+    pgrad* acc = (pgrad*)calloc((size_t)nthreads * (size_t)(N > 0 ? N : 1), sizeof(pgrad));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        extern int omp_get_thread_num(void);
+        tid = omp_get_thread_num();
+#endif
+        pgrad* my = acc + (size_t)tid * (size_t)(N > 0 ? N : 1);
+        contrib* list = (contrib*)malloc(sizeof(contrib) * (size_t)(s.nvalid > 0 ? s.nvalid : 1));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < (int64_t)H * W; ++j) {
+            int u = (int)(j % W), v = (int)(j / W);
+            const float* gp = dldimg + j * 3;
+            if (gp[0] == 0.0f && gp[1] == 0.0f && gp[2] == 0.0f) continue;
+            double C[3], T;
+            int amb;
+            int64_t n = blend_pixel(&s, u, v, &o, truncated, C, &T, &amb, list);
+            /* S = sum over later contributors of c alpha T, plus the background term */
+            double S[3] = {T * o.bg[0], T * o.bg[1], T * o.bg[2]};
+            for (int64_t m = n - 1; m >= 0; --m) {
+                contrib* cb = &list[m];
+                proj* w = &s.w[cb->prim];
+                pgrad* g = &my[cb->prim];
+                double galpha = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    g->c[ch] += gp[ch] * cb->alpha * cb->T;
+                    galpha += gp[ch] * (w->c[ch] * cb->T - S[ch] / (1.0 - cb->alpha));
+                }
+                for (int ch = 0; ch < 3; ++ch) S[ch] += w->c[ch] * cb->alpha * cb->T;
+                if (!cb->clamped) {
+                    g->o += galpha * cb->Wv;
+                    accum_wavelet_grad(w, &cb->e, galpha * w->o, g);
+                }
+            }
+        }
+        free(list);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        pgrad g;
+        memset(&g, 0, sizeof(g));
+        for (int t = 0; t < nthreads; ++t) {
+            pgrad* a = &acc[(size_t)t * (size_t)N + (size_t)i];
+            for (int m = 0; m < 2; ++m) { g.mu[m] += a->mu[m]; g.f[m] += a->f[m]; }
+            for (int m = 0; m < 4; ++m) g.K[m] += a->K[m];
+            for (int m = 0; m < 3; ++m) g.c[m] += a->c[m];
+            g.phi += a->phi;
+            g.o += a->o;
+        }
+        if (s.w[i].valid) chain3d(&s.w[i], cam, &g, grad + i * 20);
+        else memset(grad + i * 20, 0, sizeof(double) * 20);
+    }
+    free(acc);
+    scene3_free(&s);
+    return 0;
+}
+
+/* Binary64 projection of each primitive, out[N,16]:
+ * valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), 0, 0 */
+int wo_project3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, double* out) {
+    blend_opts o = read_opts(opts);
+    for (int64_t i = 0; i < N; ++i) {
+        fp32_footprint k;
+        footprint3d(params + i * 20, cam, o.cutoff, o.dil, W, H, &k);
+        proj w;
+        project3d(params + i * 20, cam, H, W, o.dil, k.valid, &w);
+        double S2[4];
+        mat2_inv(w.K, S2);
+        double* r = out + i * 16;
+        memset(r, 0, sizeof(double) * 16);
+        r[0] = w.valid; r[1] = w.t[2]; r[2] = w.mu[0]; r[3] = w.mu[1];
+        r[4] = S2[0]; r[5] = S2[1]; r[6] = S2[3];
+        r[7] = w.f[0]; r[8] = w.f[1]; r[9] = w.phi; r[10] = w.o;
+        r[11] = w.c[0]; r[12] = w.c[1]; r[13] = w.c[2];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 6D: per-primitive linear time model                                                         */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Reading of the 6D deformation (Sec. 4.3 gives it only as an MLP of unstated architecture):
+ * mu(t) = mu0 + v t, f(t) = f0 + df t, phi(t) = phi0 + dphi t, log s(t) = log s0 + dlog_s t.
+ * in[N,32] -> out[N,20] */
+int wo_deform6d(const float* params6, int64_t N, double t, double* out3) {
+    for (int64_t i = 0; i < N; ++i) {
+        const float* p = params6 + i * 32;
+        double* o = out3 + i * 20;
+        for (int j = 0; j < 20; ++j) o[j] = p[j];
+        for (int j = 0; j < 3; ++j) {
+            o[j] = (double)p[j] + (double)p[20 + j] * t;
+            o[3 + j] = (double)p[3 + j] * exp((double)p[27 + j] * t);
+            o[10 + j] = (double)p[10 + j] + (double)p[23 + j] * t;
+        }
+        o[13] = (double)p[13] + (double)p[26] * t;
+    }
+    return 0;
+}
+
+/* chain dL/d(deformed record)[N,20] to dL/d(record6)[N,32] */
+int wo_deform6d_grad(const float* params6, int64_t N, double t, const double* g3, double* g6) {
+    for (int64_t i = 0; i < N; ++i) {
+        const float* p = params6 + i * 32;
+        const double* g = g3 + i * 20;
+        double* o = g6 + i * 32;
+        memset(o, 0, sizeof(double) * 32);
+        for (int j = 0; j < 20; ++j) o[j] = g[j];
+        for (int j = 0; j < 3; ++j) {
+            double e = exp((double)p[27 + j] * t);
+            o[20 + j] = g[j] * t;
+            o[3 + j] = g[3 + j] * e;
+            o[27 + j] = g[3 + j] * (double)p[3 + j] * e * t;
+            o[23 + j] = g[10 + j] * t;
+        }
+        o[26] = g[13] * t;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* footprint check: every (pixel, primitive) pair that passes the binary32 cutoff test must     */
+/* lie inside the primitive's covered pixel range (so tile lists lose no contribution)          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* counts[0] = pairs inside the cutoff ellipse, counts[1] = of those, pairs outside the pixel range,
+ * counts[2] = pixels inside the pixel ranges (pairs the tile lists make a kernel visit at most) */
+int wo_cutoff_coverage(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff,
+                       float dil, int64_t* counts) {
+    fp32_footprint* k = all_footprints(dims, params, N, cam, H, W, cutoff, dil);
+    float k2 = cutoff * cutoff;
+    int64_t inside = 0, outside = 0, rect_px = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : inside, outside, rect_px)
+    for (int64_t i = 0; i < N; ++i) {
+        if (!k[i].valid) continue;
+        if (k[i].u0 <= k[i].u1) rect_px += (int64_t)(k[i].u1 - k[i].u0 + 1) * (k[i].v1 - k[i].v0 + 1);
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                if (!(q32(&k[i], u, v) <= k2)) continue;
+                ++inside;
+                if (u < k[i].u0 || u > k[i].u1 || v < k[i].v0 || v > k[i].v1) ++outside;
+            }
+    }
+    counts[0] = inside;
+    counts[1] = outside;
+    counts[2] = rect_px;
+    free(k);
+    return 0;
+}

@@ -1,0 +1,24 @@
+"""Test configuration: the ``gpu`` marker selects tests that need a CUDA device and the built library.
+
+Run the CPU suite with ``pytest -m "not gpu"`` and the device parity suite with ``pytest -m gpu``.
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device and the compiled library")
+
+
+@pytest.fixture(scope="session")
+def oracle_lib():
+    import oracle
+
+    oracle.build()
+    return oracle

@@ -1,0 +1,453 @@
+"""Pins of the binary64 oracle against facts the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage it rests on.  Together they are chosen so that a plausible slip in the
+oracle (a dropped factor 1/2 or 2 pi, a sign of the phase or offset, Sigma in place of its inverse,
+a transposed rotation, a wrong Jacobian column, front-to-back order reversed) fails one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.stats
+
+import oracle
+import synth
+
+
+def rec2d(mu, s, theta, f, phi, c):
+    p = np.zeros((1, 16), np.float32)
+    p[0, :11] = [mu[0], mu[1], s[0], s[1], theta, f[0], f[1], phi, c[0], c[1], c[2]]
+    return p
+
+
+def rec3d(mu, s, q, f, phi, o, c):
+    p = np.zeros((1, 20), np.float32)
+    p[0, :18] = [*mu, *s, *q, *f, phi, o, *c]
+    return p
+
+
+def cam_identity(H, W, fx=300.0, fy=None, near=0.2):
+    cam = np.zeros(17, np.float32)
+    cam[:12] = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], np.float32).ravel()
+    cam[12] = fx
+    cam[13] = fx if fy is None else fy
+    cam[14] = W / 2
+    cam[15] = H / 2
+    cam[16] = near
+    return cam
+
+
+OPTS_EXACT = np.array([3.0, 0.0, 1.0, 0.0, 0.3, 0.0, 0.0, 0.0], np.float32)
+
+
+# ---------------------------------------------------------------------------------------------
+# 2D wavelet field (Sec. 4.1 Eq. 5, Sec. 4.3 with the summed field of Eq. 4)
+# ---------------------------------------------------------------------------------------------
+
+def test_zero_frequency_reduces_to_gaussian_splat():
+    """Sec. 4.1: with f = 0 the wavelet is the Gaussian primitive.  The expected image is a sum of
+    scipy multivariate-normal densities scaled by 2 pi sqrt(det Sigma), Sigma = R S S^T R^T."""
+    H, W = 40, 56
+    p = synth.scene2d(12, H, W, 3, (1.5, 6.0))
+    p[:, 5:8] = 0.0
+    img = oracle.render2d(p, H, W, truncated=False)
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    pts = np.stack([xx.ravel(), yy.ravel()], 1)
+    ref = np.zeros((H, W, 3))
+    for i in range(len(p)):
+        c, s = math.cos(p[i, 4]), math.sin(p[i, 4])
+        R = np.array([[c, -s], [s, c]])
+        S = np.diag(p[i, 2:4].astype(np.float64))
+        Sig = R @ S @ S.T @ R.T
+        dens = scipy.stats.multivariate_normal(mean=p[i, :2].astype(np.float64), cov=Sig).pdf(pts)
+        G = dens * 2 * math.pi * math.sqrt(np.linalg.det(Sig))
+        ref += G.reshape(H, W)[..., None] * p[i, 8:11].astype(np.float64)
+    np.testing.assert_allclose(img, ref, rtol=1e-10, atol=1e-13)
+
+
+@pytest.mark.parametrize("phi", [0.0, 1.0, math.pi / 2, 2.5, math.pi, 4.0])
+@pytest.mark.parametrize("truncated", [False, True])
+def test_single_primitive_value_at_centre(phi, truncated):
+    """Eq. 5 at x = mu: G = 1 and the modulation is (1 + cos phi) / 2."""
+    p = rec2d((10.5, 7.5), (3.0, 1.7), 0.4, (0.13, -0.21), phi, (0.2, 0.5, 0.9))
+    out = oracle.render2d(p, 16, 24, truncated=truncated, pixels=[[10, 7]])
+    expected = p[0, 8:11].astype(np.float64) * 0.5 * (1 + math.cos(float(p[0, 7])))
+    np.testing.assert_allclose(out[0], expected, rtol=0, atol=1e-15)
+
+
+def test_phase_sign_and_offset_direction():
+    """Eq. 5 with d = x - mu and the phase added to 2 pi f.d: with f = (1/4, 0) cycles/px and
+    phi = pi/2 the cosine is -1 one pixel to the right of the centre and +1 one pixel to the left;
+    one pixel below it is cos(pi/2) = 0."""
+    s = 2.0
+    p = rec2d((8.5, 8.5), (s, s), 0.0, (0.25, 0.0), math.pi / 2, (1, 1, 1))
+    out = oracle.render2d(p, 17, 17, truncated=False, pixels=[[9, 8], [7, 8], [8, 9]])
+    G1 = math.exp(-0.5 / s ** 2)
+    np.testing.assert_allclose(out[:, 0], [0.0, G1, 0.5 * G1], atol=1e-7)
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_pixel_sum_matches_fourier_closed_form(trial):
+    """Sec. 4.2: the modulation shifts the Gaussian spectrum to +-f.  Summing W over the pixel grid
+    (midpoint rule, spectrally exact for sigma >= 3 px) gives the integral
+    pi sqrt(det Sigma) (1 + cos(phi) exp(-2 pi^2 f^T Sigma f))."""
+    rng = np.random.default_rng(100 + trial)
+    H = W = 160
+    s = rng.uniform(3.0, 7.0, 2)
+    th = rng.uniform(0, math.pi)
+    fm, fd = rng.uniform(0, 0.45), rng.uniform(0, 2 * math.pi)
+    phi = rng.uniform(0, 2 * math.pi)
+    p = rec2d((80.0 + rng.uniform(-1, 1), 80.0 + rng.uniform(-1, 1)), s, th, (fm * math.cos(fd), fm * math.sin(fd)),
+              phi, (1, 0, 0))
+    img = oracle.render2d(p, H, W, truncated=False)
+    q = p[0].astype(np.float64)
+    c, sn = math.cos(q[4]), math.sin(q[4])
+    R = np.array([[c, -sn], [sn, c]])
+    Sig = R @ np.diag(q[2:4] ** 2) @ R.T
+    f = q[5:7]
+    closed = math.pi * math.sqrt(np.linalg.det(Sig)) * (1 + math.cos(q[7]) * math.exp(-2 * math.pi ** 2 * f @ Sig @ f))
+    assert abs(img[..., 0].sum() - closed) <= 1e-9 * closed
+
+
+def test_translation_by_whole_pixels_shifts_the_image():
+    """Eq. 5 depends on x - mu only: moving every centre by (3, 2) pixels moves the image."""
+    H, W = 48, 64
+    p = synth.scene2d(20, H, W, 21, (1.0, 3.0))
+    p[:, 0] = np.clip(p[:, 0], 14, W - 20).astype(np.float32)
+    p[:, 1] = np.clip(p[:, 1], 14, H - 20).astype(np.float32)
+    p[:, :2] = np.round(p[:, :2] * 4096.0) / 4096.0  # so that the shifted centres stay exact in float32
+    a = oracle.render2d(p, H, W, truncated=False)
+    q = p.copy()
+    q[:, 0] += 3.0
+    q[:, 1] += 2.0
+    b = oracle.render2d(q, H, W, truncated=False)
+    np.testing.assert_allclose(b[2:, 3:], a[:-2, :-3], rtol=1e-9, atol=1e-12)
+
+
+def test_truncation_bound():
+    """Dropping the terms outside the 3-sigma ellipse changes a pixel by at most
+    sum_i |c_i| (1/2)(1 + 1) e^{-9/2} over the primitives cut at that pixel."""
+    H, W = 64, 64
+    p = synth.scene2d(60, H, W, 5, (1.0, 8.0))
+    full = oracle.render2d(p, H, W, truncated=False)
+    cut = oracle.render2d(p, H, W, truncated=True)
+    bound = np.abs(p[:, 8:11]).sum(0) * math.exp(-4.5)
+    assert np.all(np.abs(full - cut) <= bound + 1e-12)
+    assert np.abs(full - cut).max() > 0
+
+
+def _central_fd(render, p, rows, cols, rel=2.0 ** -16, floor=None):
+    """Central differences of L(p) with float32-representable steps."""
+    out = np.zeros((len(rows), len(cols)))
+    for a, i in enumerate(rows):
+        for b, j in enumerate(cols):
+            base = float(p[i, j])
+            scale = max(abs(base), floor[j] if floor is not None else 1.0)
+            h = 2.0 ** math.floor(math.log2(scale)) * rel
+            pp, pm = p.copy(), p.copy()
+            pp[i, j] = np.float32(base + h)
+            pm[i, j] = np.float32(base - h)
+            step = float(pp[i, j]) - float(pm[i, j])
+            out[a, b] = (render(pp) - render(pm)) / step
+    return out
+
+
+def test_grad2d_matches_central_differences():
+    """The analytic gradient (Sec. 1 states explicit gradients) equals central differences of
+    the binary64 forward, every parameter of every primitive, no truncation."""
+    H, W = 24, 28
+    p = synth.scene2d(5, H, W, 11, (1.5, 5.0))
+    g = synth.upstream_grad(H, W, 12)
+    an = oracle.grad2d(p, H, W, g, truncated=False)
+    cols = list(range(11))
+    fd = _central_fd(lambda pp: float((oracle.render2d(pp, H, W, truncated=False) * g).sum()), p, range(len(p)), cols)
+    ref = an[:, cols]
+    err = np.abs(ref - fd)
+    tol = 2e-6 * np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max(axis=0, keepdims=True))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-300)).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# 3D projection (Sec. 3.1 EWA, Sec. 4.1 frequency), blending (Eq. 3 with W')
+# ---------------------------------------------------------------------------------------------
+
+def test_on_axis_projection_closed_form():
+    """Sec. 3.1: on the optical axis with R = I, Sigma' = diag(fx^2 sx^2, fy^2 sy^2) / tz^2 + 0.3 I
+    and mu' is the principal point."""
+    H, W = 64, 80
+    cam = cam_identity(H, W, fx=300.0, fy=250.0)
+    p = rec3d((0, 0, 5.0), (0.1, 0.2, 0.3), (1, 0, 0, 0), (0, 0, 0), 0.0, 0.5, (1, 1, 1))
+    r = oracle.project3d(p, cam, H, W)[0]
+    assert r[0] == 1 and r[1] == pytest.approx(5.0)
+    np.testing.assert_allclose(r[2:4], [W / 2, H / 2], atol=1e-12)
+    np.testing.assert_allclose(r[4:7], [300.0 ** 2 * 0.01 / 25 + 0.3, 0.0, 250.0 ** 2 * 0.04 / 25 + 0.3],
+                               rtol=1e-6, atol=1e-12)
+
+
+def test_off_axis_isotropic_projection_closed_form():
+    """Sec. 3.1 with the perspective Jacobian J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]]:
+    an isotropic 3D Gaussian of std sigma projects to sigma^2 J J^T + 0.3 I."""
+    H, W = 200, 240
+    cam = cam_identity(H, W, fx=300.0, fy=280.0)
+    tx, ty, tz, sig = 0.7, -0.4, 4.0, 0.05
+    p = rec3d((tx, ty, tz), (sig, sig, sig), (0.3, -0.2, 0.8, 0.1), (0, 0, 0), 0.0, 0.5, (1, 1, 1))
+    r = oracle.project3d(p, cam, H, W)[0]
+    fx, fy = 300.0, 280.0
+    # the float32 record rounds tx, ty, tz, sigma
+    tx, ty, tz, sig = (float(np.float32(v)) for v in (tx, ty, tz, sig))
+    s2 = sig * sig / tz ** 2
+    expect = [s2 * fx * fx * (1 + tx * tx / tz ** 2) + 0.3, s2 * fx * fy * tx * ty / tz ** 2,
+              s2 * fy * fy * (1 + ty * ty / tz ** 2) + 0.3]
+    np.testing.assert_allclose(r[4:7], expect, rtol=1e-6)
+    np.testing.assert_allclose(r[2:4], [fx * tx / tz + W / 2, fy * ty / tz + H / 2], rtol=1e-6)
+
+
+def test_look_at_camera_projects_centre():
+    """Pinhole projection with the OpenCV look-at camera: a camera at (0, -5, 0) looking at the
+    origin with up +z sees world (x, 0, z) at pixel (fx x / 5 + cx, -fy z / 5 + cy)."""
+    H, W = 100, 120
+    cam = synth.camera(synth.look_at((0.0, -5.0, 0.0)), H, W, 50.0)
+    p = np.concatenate([rec3d((0.3, 0.0, -0.2), (0.01,) * 3, (1, 0, 0, 0), (0, 0, 0), 0, 0.5, (1, 1, 1)),
+                        rec3d((-0.5, 0.0, 0.4), (0.01,) * 3, (1, 0, 0, 0), (0, 0, 0), 0, 0.5, (1, 1, 1))])
+    r = oracle.project3d(p, cam, H, W)
+    fx = float(cam[12])
+    np.testing.assert_allclose(r[0, 2:4], [fx * 0.3 / 5 + W / 2, -fx * -0.2 / 5 + H / 2], rtol=1e-6)
+    np.testing.assert_allclose(r[1, 2:4], [fx * -0.5 / 5 + W / 2, -fx * 0.4 / 5 + H / 2], rtol=1e-6)
+    np.testing.assert_allclose(r[:, 1], [5.0, 5.0], rtol=1e-6)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_projected_frequency_of_a_facing_disc(axis):
+    """Sec. 4.1 (reading: f' is the phase gradient on the fronto-parallel plane through the centre).
+    A flat disc facing the camera at depth tz with f along camera x (or y) shows, along the image
+    row (column) through its centre, alpha = o (1 + cos(2 pi f tz / fx du + phi)) / 2 exp(-du^2 / 2 s'^2)
+    with s'^2 = (fx sigma / tz)^2 + 0.3."""
+    H, W = 65, 65
+    fx = 200.0
+    cam = cam_identity(H, W, fx=fx)
+    cam[14] = cam[15] = 32.5  # principal point on a pixel centre
+    tz, sig, f0, phi, o = 3.0, 0.05, 3.0, 0.7, 0.6
+    f = [0.0, 0.0, 0.0]
+    f[axis] = f0
+    p = rec3d((0, 0, tz), (sig, sig, 1e-5), (1, 0, 0, 0), f, phi, o, (1, 1, 1))
+    C, T, nc, amb = oracle.render3d(p, cam, H, W, OPTS_EXACT, truncated=False)
+    du = np.arange(W) + 0.5 - 32.5
+    line = C[32, :, 0] if axis == 0 else C[:, 32, 0]
+    tzf, sigf, f0f, phif, of = (float(np.float32(v)) for v in (tz, sig, f0, phi, o))
+    s2 = (fx * sigf / tzf) ** 2 + 0.3
+    expect = of * 0.5 * (1 + np.cos(2 * math.pi * f0f * tzf / fx * du + phif)) * np.exp(-0.5 * du ** 2 / s2)
+    np.testing.assert_allclose(line, expect, rtol=1e-5, atol=1e-9)
+
+
+def test_frequency_along_view_axis_is_dropped():
+    """Sec. 4.1: the projected frequency keeps (f_x, f_y) only; a frequency along the viewing axis
+    leaves the splat a plain Gaussian modulated by the constant (1 + cos phi) / 2."""
+    H, W = 33, 33
+    cam = cam_identity(H, W, fx=150.0)
+    a = rec3d((0, 0, 2.0), (0.04, 0.06, 0.03), (0.9, 0.1, -0.2, 0.3), (0, 0, 0), 0.9, 0.5, (1, 1, 1))
+    b = a.copy()
+    b[0, 12] = 25.0
+    Ca = oracle.render3d(a, cam, H, W, OPTS_EXACT, truncated=False)[0]
+    Cb = oracle.render3d(b, cam, H, W, OPTS_EXACT, truncated=False)[0]
+    np.testing.assert_allclose(Ca, Cb, rtol=1e-12, atol=1e-15)
+
+
+def test_front_to_back_two_layers():
+    """Eq. 3 with W': two primitives on the optical axis, the nearer one first:
+    C = c1 a1 + c2 a2 (1 - a1) + (1 - a1)(1 - a2) bg with a = o (1 + cos phi) / 2 at the centre."""
+    H, W = 33, 33
+    cam = cam_identity(H, W, fx=100.0)
+    cam[14] = cam[15] = 16.5
+    near = rec3d((0, 0, 2.0), (0.05, 0.05, 0.05), (1, 0, 0, 0), (0, 0, 0), 0.8, 0.7, (1.0, 0.2, 0.1))
+    far = rec3d((0, 0, 3.0), (0.2, 0.2, 0.2), (1, 0, 0, 0), (0, 0, 0), 2.0, 0.9, (0.1, 0.3, 1.0))
+    opts = np.array([3.0, 1 / 255, 0.99, 1e-4, 0.3, 0.25, 0.5, 0.75], np.float32)
+    for p in (np.concatenate([near, far]), np.concatenate([far, near])):
+        C, T, nc, amb = oracle.render3d(p, cam, H, W, opts, pixels=[[16, 16]])
+        a1 = float(np.float32(0.7)) * 0.5 * (1 + math.cos(float(np.float32(0.8))))
+        a2 = float(np.float32(0.9)) * 0.5 * (1 + math.cos(float(np.float32(2.0))))
+        c1, c2 = near[0, 15:18].astype(np.float64), far[0, 15:18].astype(np.float64)
+        bg = opts[5:8].astype(np.float64)
+        expect = c1 * a1 + c2 * a2 * (1 - a1) + (1 - a1) * (1 - a2) * bg
+        np.testing.assert_allclose(C[0], expect, rtol=1e-12)
+        assert T[0] == pytest.approx((1 - a1) * (1 - a2), rel=1e-12)
+        assert nc[0] == 2
+
+
+def test_transmittance_floor_stops_blending():
+    """Blending stops before a primitive that would take T below T_min: with alpha = 0.95 per
+    layer T goes 0.05, 2.5e-3, 1.25e-4, and the fourth layer (6.25e-6 < 1e-4) is not added."""
+    H, W = 17, 17
+    cam = cam_identity(H, W, fx=100.0)
+    cam[14] = cam[15] = 8.5
+    layers = [rec3d((0, 0, 2.0 + k), (0.1, 0.1, 0.1), (1, 0, 0, 0), (0, 0, 0), 0.0, 0.95, (1, 1, 1)) for k in range(6)]
+    p = np.concatenate(layers)
+    C, T, nc, amb = oracle.render3d(p, cam, H, W, pixels=[[8, 8]])
+    a = float(np.float32(0.95))
+    assert nc[0] == 3
+    assert T[0] == pytest.approx((1 - a) ** 3, rel=1e-12)
+    assert C[0, 0] == pytest.approx(a + a * (1 - a) + a * (1 - a) ** 2, rel=1e-12)
+
+
+def test_alpha_floor_and_ceiling():
+    """alpha below 1/255 is skipped; o W' above alpha_max is clamped to 0.99."""
+    H, W = 17, 17
+    cam = cam_identity(H, W, fx=100.0)
+    cam[14] = cam[15] = 8.5
+    faint = rec3d((0, 0, 2.0), (0.1,) * 3, (1, 0, 0, 0), (0, 0, 0), 0.0, 0.003, (1, 1, 1))
+    solid = rec3d((0, 0, 3.0), (0.1,) * 3, (1, 0, 0, 0), (0, 0, 0), 0.0, 1.0, (0.5, 0.5, 0.5))
+    C, T, nc, amb = oracle.render3d(np.concatenate([faint, solid]), cam, H, W, pixels=[[8, 8]])
+    assert nc[0] == 1
+    amax = float(np.float32(0.99))
+    assert C[0, 0] == pytest.approx(0.5 * amax, rel=1e-12)
+    assert T[0] == pytest.approx(1 - amax, rel=1e-12)
+
+
+def test_blend_first_order_is_summed_field():
+    """With every alpha small the front-to-back blend equals the summed field of c alpha up to
+    second order: |C - sum c a| <= max|c| (sum a)^2 / 2."""
+    H, W = 40, 40
+    p = synth.scene3d(80, 31)
+    p[:, 14] = 0.01
+    cam = synth.sphere_cameras(1, H, W, 32)[0]
+    C = oracle.render3d(p, cam, H, W, OPTS_EXACT, truncated=False)[0]
+    # the same scene with every opacity scaled to 1e-8: pure first order
+    q = p.copy()
+    q[:, 14] = 1e-8
+    lin = oracle.render3d(q, cam, H, W, OPTS_EXACT, truncated=False)[0] * (0.01 / 1e-8)
+    asum = lin.max(axis=2)  # colours are <= 1, so sum a >= the largest channel of sum c a
+    # bound with the exact alpha sum per pixel from a white copy
+    w = q.copy()
+    w[:, 15:18] = 1.0
+    asum = oracle.render3d(w, cam, H, W, OPTS_EXACT, truncated=False)[0][..., 0] * (0.01 / 1e-8)
+    assert np.all(np.abs(C - lin) <= 0.5 * asum[..., None] ** 2 + 1e-12)
+    assert np.abs(C - lin).max() > 0
+
+
+def test_grad3d_matches_central_differences():
+    """Analytic gradient through blending, projection (J, Sigma', mu', f') and the quaternion
+    against central differences of the binary64 forward (no thresholds)."""
+    H, W = 28, 32
+    p = synth.scene3d(6, 41, scale_range=(0.03, 0.08), max_freq=6.0, extent=0.3)
+    p[:, 14] = np.linspace(0.3, 0.8, 6)
+    cam = synth.camera(synth.look_at((0.4, -2.2, 0.9)), H, W, 50.0)
+    g = synth.upstream_grad(H, W, 42)
+    an = oracle.grad3d(p, cam, H, W, g, OPTS_EXACT, truncated=False)
+    cols = list(range(18))
+    floor = [0.3] * 3 + [0.03] * 3 + [0.5] * 4 + [1.0] * 3 + [1.0] + [0.3] + [0.3] * 3
+
+    def L(pp):
+        return float((oracle.render3d(pp, cam, H, W, OPTS_EXACT, truncated=False)[0] * g).sum())
+
+    fd = _central_fd(L, p, range(len(p)), cols, floor=floor)
+    ref = an[:, cols]
+    err = np.abs(ref - fd)
+    tol = 1e-5 * np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max(axis=0, keepdims=True))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-300)).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# binary32 footprint rule and tile lists (the 3DGS-style pipeline the paper follows, Sec. 4.1)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,scale", [(2, (1.0, 16.0)), (2, (0.5, 32.0)), (3, None)])
+def test_cutoff_ellipse_inside_covered_range(dims, scale):
+    """Tile culling loses nothing: every pixel that passes the binary32 3-sigma test lies inside the
+    primitive's covered pixel range, including very elongated primitives (scale ratio up to 64)."""
+    if dims == 2:
+        H, W = 128, 160
+        p = synth.scene2d(1500, H, W, 7, scale)
+        inside, outside, rect = oracle.cutoff_coverage(2, p, H, W)
+    else:
+        H, W = 96, 112
+        p = synth.scene3d(2500, 8)
+        cam = synth.sphere_cameras(1, H, W, 9)[0]
+        inside, outside, rect = oracle.cutoff_coverage(3, p, H, W, cam)
+    assert inside > 0 and outside == 0 and rect >= inside
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_footprint_matches_binary64_projection(dims):
+    """The binary32 Cholesky factor L of the inverse covariance reproduces the binary64 Sigma'^-1:
+    L L^T = Sigma'^-1 to single-precision accuracy, and the centre matches mu'."""
+    if dims == 2:
+        H, W = 64, 64
+        p = synth.scene2d(300, H, W, 13, (0.5, 32.0))
+        rec, rect, valid = oracle.footprints(2, p, H, W)
+        for i in range(len(p)):
+            c, s = math.cos(p[i, 4]), math.sin(p[i, 4])
+            R = np.array([[c, -s], [s, c]])
+            K = np.linalg.inv(R @ np.diag(p[i, 2:4].astype(np.float64) ** 2) @ R.T)
+            L = np.array([[rec[i, 2], 0.0], [rec[i, 3], rec[i, 4]]], np.float64)
+            np.testing.assert_allclose(L @ L.T, K, rtol=2e-5, atol=2e-5 * np.abs(K).max())
+            np.testing.assert_allclose(rec[i, :2], p[i, :2])
+    else:
+        H, W = 120, 100
+        p = synth.scene3d(400, 14)
+        cam = synth.sphere_cameras(1, H, W, 15)[0]
+        rec, rect, valid = oracle.footprints(3, p, H, W, cam)
+        pr = oracle.project3d(p, cam, H, W)
+        assert np.array_equal(valid.astype(bool), pr[:, 0].astype(bool))
+        for i in np.nonzero(valid)[0]:
+            S = np.array([[pr[i, 4], pr[i, 5]], [pr[i, 5], pr[i, 6]]])
+            K = np.linalg.inv(S)
+            L = np.array([[rec[i, 2], 0.0], [rec[i, 3], rec[i, 4]]], np.float64)
+            np.testing.assert_allclose(L @ L.T, K, rtol=1e-4, atol=1e-4 * np.abs(K).max())
+            np.testing.assert_allclose(rec[i, :2], pr[i, 2:4], rtol=1e-5)
+            assert rec[i, 7] == pytest.approx(pr[i, 1], rel=1e-6)
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_tile_lists_enumerate_covered_tiles_in_order(dims):
+    """The sorted lists hold exactly the tiles each covered pixel range touches, ordered by tile,
+    then camera depth (3D), then primitive index."""
+    H, W = 72, 88
+    if dims == 2:
+        p = synth.scene2d(120, H, W, 17, (1.0, 12.0))
+        cam = None
+    else:
+        p = synth.scene3d(600, 18)
+        cam = synth.sphere_cameras(1, H, W, 19)[0]
+    rec, rect, valid = oracle.footprints(dims, p, H, W, cam)
+    tiles, prims = oracle.tile_lists(dims, p, H, W, cam)
+    tx = (W + 15) // 16
+    expect = []
+    for i in range(len(p)):
+        u0, v0, u1, v1 = rect[i]
+        if not valid[i] or u0 > u1:
+            continue
+        depth = rec[i, 7].view(np.uint32) if dims == 3 else 0
+        for ty in range(v0 // 16, v1 // 16 + 1):
+            for tx_ in range(u0 // 16, u1 // 16 + 1):
+                expect.append((ty * tx + tx_, int(depth), i))
+    expect.sort()
+    assert len(expect) == len(tiles)
+    assert [e[0] for e in expect] == tiles.tolist()
+    assert [e[2] for e in expect] == prims.tolist()
+
+
+# ---------------------------------------------------------------------------------------------
+# 6D: linear time model (reading of the deformation of Sec. 4.3)
+# ---------------------------------------------------------------------------------------------
+
+def test_deform6d_identity_at_time_zero_and_rates():
+    p = synth.scene6d(50, 3)
+    d0 = oracle.deform6d(p, 0.0)
+    np.testing.assert_array_equal(d0, p[:, :20].astype(np.float64))
+    d1 = oracle.deform6d(p, 0.5)
+    q = p.astype(np.float64)
+    np.testing.assert_allclose(d1[:, 0:3], q[:, 0:3] + 0.5 * q[:, 20:23])
+    np.testing.assert_allclose(d1[:, 3:6], q[:, 3:6] * np.exp(0.5 * q[:, 27:30]))
+    np.testing.assert_allclose(d1[:, 13], q[:, 13] + 0.5 * q[:, 26])
+
+
+def test_deform6d_grad_matches_central_differences():
+    p = synth.scene6d(4, 5)
+    t = 0.37
+    g3 = np.random.default_rng(6).standard_normal((4, 20))
+    an = oracle.deform6d_grad(p, t, g3)
+
+    def L(pp):
+        return float((oracle.deform6d(pp, t) * g3).sum())
+
+    fd = _central_fd(L, p, range(4), range(30), floor=[1.0] * 20 + [0.05] * 10)
+    np.testing.assert_allclose(an[:, :30], fd, rtol=1e-6, atol=1e-8)
