@@ -1,0 +1,583 @@
+// C ABI of the wavelet rasterizer: contexts, workspaces (states) and the orchestration of the
+// forward and backward passes.  Every numeric step runs in the kernels of footprint.cu,
+// binning.cu, raster2d.cu, raster3d.cu and loss.cu.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <vector>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+using namespace wipes;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+wipes_status fail(wipes_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define WIPES_CUDA(call)                                                                                  \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? WIPES_ERR_OOM : WIPES_ERR_CUDA,                \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+    } while (0)
+
+#define WIPES_TRY(expr)                   \
+    do {                                  \
+        wipes_status s_ = (expr);         \
+        if (s_ != WIPES_OK) return s_;    \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+wipes_status ensure(DevBuf& b, size_t bytes) {
+    if (bytes <= b.cap) return WIPES_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(WIPES_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    b.cap = want;
+    return WIPES_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+int ceil_log2(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+std::atomic<int64_t> g_launches{0};
+
+}  // namespace
+
+void wipes::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct wipes_ctx {
+    int device = 0;
+    unsigned long long* h_total = nullptr;  // pinned readback of the instance count
+    float* d_loss_partials = nullptr;
+    unsigned long long* d_counters = nullptr;  // pair counters
+    // stage timing
+    bool timing = false;
+    struct Bracket {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Bracket> pending;
+    std::vector<cudaEvent_t> free_events;
+    double stage_ms[WIPES_STAGE_COUNT] = {};
+    int64_t stage_n[WIPES_STAGE_COUNT] = {};
+
+    cudaEvent_t take_event() {
+        if (!free_events.empty()) {
+            cudaEvent_t e = free_events.back();
+            free_events.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+namespace {
+
+// Brackets one stage with CUDA events on `s` when timing is enabled on the context.
+struct StageTimer {
+    wipes_ctx* ctx;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(wipes_ctx* c, int st, cudaStream_t stream) : ctx(c), stage(st), s(stream) {
+        if (ctx && ctx->timing) {
+            a = ctx->take_event();
+            cudaEventRecord(a, s);
+        }
+    }
+    void stop() {
+        if (!a) return;
+        cudaEvent_t b = ctx->take_event();
+        cudaEventRecord(b, s);
+        ctx->pending.push_back({stage, a, b});
+        a = nullptr;
+    }
+    ~StageTimer() { stop(); }
+};
+
+}  // namespace
+
+struct wipes_state {
+    wipes_ctx* ctx = nullptr;
+    int dims = 0;
+    int64_t N = 0;
+    int H = 0, W = 0, tiles_x = 0, tiles_y = 0;
+    wipes_opts opts{};
+    wipes_camera cam{};
+    int64_t n_inst = 0;
+    int sorted = 0;  // which ping-pong buffer holds the sorted lists
+    DevBuf rec, rect, counts, offsets, dkeys[2], dvals[2], block_sums, total, keys[2], vals[2], hist, ranges;
+    DevBuf T_final, last, partial, grad_img;
+
+    DevBuf* all[19] = {&rec, &rect, &counts, &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &block_sums,
+                       &total, &keys[0], &keys[1], &vals[0], &vals[1], &hist, &ranges, &T_final, &last, &partial};
+    size_t reserved() const {
+        size_t s = grad_img.cap;
+        for (DevBuf* b : all) s += b->cap;
+        return s;
+    }
+};
+
+namespace {
+
+wipes_status check_image(int H, int W) {
+    if (H < 1 || W < 1 || H > 16384 || W > 16384)
+        return fail(WIPES_ERR_INVALID, "image size must be within 1..16384 (got H=" + std::to_string(H) +
+                                           ", W=" + std::to_string(W) + ")");
+    return WIPES_OK;
+}
+
+// Scan the per-primitive tile counts (in `perm` order when given), read the instance total back,
+// size the instance buffers, emit the pairs and sort them by tile (stable).
+wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s) {
+    const int64_t N = st->N;
+    const int nb = (int)std::max<int64_t>(1, ceil_div(N, kScanBlockElems));
+    WIPES_TRY(ensure(st->block_sums, sizeof(unsigned long long) * (size_t)nb));
+    WIPES_TRY(ensure(st->total, sizeof(unsigned long long)));
+    const int n_tiles = st->tiles_x * st->tiles_y;
+    WIPES_TRY(ensure(st->ranges, sizeof(uint2) * (size_t)n_tiles));
+    unsigned long long* total = st->total.as<unsigned long long>();
+    if (N > 0) {
+        StageTimer t(st->ctx, WIPES_STAGE_SCAN, s);
+        launch_block_sums(st->counts.as<uint32_t>(), perm, N, st->block_sums.as<unsigned long long>(), s);
+        launch_scan_block_sums(st->block_sums.as<unsigned long long>(), nb, total, s);
+        WIPES_CUDA(cudaMemcpyAsync(st->ctx->h_total, total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        t.stop();
+        WIPES_CUDA(cudaStreamSynchronize(s));
+        st->n_inst = (int64_t)*st->ctx->h_total;
+    } else {
+        st->n_inst = 0;
+    }
+    if (st->n_inst > (int64_t)INT32_MAX)
+        return fail(WIPES_ERR_CAPACITY, "tile instance count " + std::to_string(st->n_inst) + " exceeds 2^31-1");
+    const int64_t I = st->n_inst;
+    for (int k = 0; k < 2; ++k) {
+        WIPES_TRY(ensure(st->keys[k], sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
+        WIPES_TRY(ensure(st->vals[k], sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
+    }
+    WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(I)));
+    if (N > 0) {
+        StageTimer t(st->ctx, WIPES_STAGE_EMIT, s);
+        launch_emit(st->counts.as<uint32_t>(), perm, N, st->rect.as<PixRect>(), st->block_sums.as<unsigned long long>(),
+                    st->tiles_x, st->keys[0].as<uint32_t>(), st->vals[0].as<uint32_t>(), st->offsets.as<uint32_t>(), s);
+    }
+    uint32_t* kb[2] = {st->keys[0].as<uint32_t>(), st->keys[1].as<uint32_t>()};
+    uint32_t* vb[2] = {st->vals[0].as<uint32_t>(), st->vals[1].as<uint32_t>()};
+    {
+        StageTimer t(st->ctx, WIPES_STAGE_TILE_SORT, s);
+        st->sorted = radix_sort_pairs(kb, vb, I, ceil_log2(n_tiles), st->hist.as<uint32_t>(), s);
+    }
+    {
+        StageTimer t(st->ctx, WIPES_STAGE_RANGES, s);
+        launch_tile_ranges(kb[st->sorted], I, st->ranges.as<uint2>(), n_tiles, s);
+    }
+    return WIPES_OK;
+}
+
+wipes_status prepare_state(wipes_state* st, int dims, int64_t N, int H, int W, const wipes_opts* opts) {
+    st->dims = 0;  // invalid until the forward pass is enqueued
+    st->N = N;
+    st->H = H;
+    st->W = W;
+    st->tiles_x = (W + kTile - 1) / kTile;
+    st->tiles_y = (H + kTile - 1) / kTile;
+    st->opts = *opts;
+    const size_t n = (size_t)std::max<int64_t>(N, 1);
+    WIPES_TRY(ensure(st->rec, sizeof(float4) * kRecF4 * n));
+    WIPES_TRY(ensure(st->rect, sizeof(PixRect) * n));
+    WIPES_TRY(ensure(st->counts, sizeof(uint32_t) * n));
+    WIPES_TRY(ensure(st->offsets, sizeof(uint32_t) * n));
+    (void)dims;
+    return WIPES_OK;
+}
+
+BlendOpts3 blend_opts(const wipes_opts& o) {
+    BlendOpts3 b;
+    b.cutoff2 = o.cutoff_sigma * o.cutoff_sigma;
+    b.alpha_min = o.alpha_min;
+    b.alpha_max = o.alpha_max;
+    b.T_min = o.T_min;
+    b.bg[0] = o.bg[0];
+    b.bg[1] = o.bg[1];
+    b.bg[2] = o.bg[2];
+    return b;
+}
+
+wipes_status check_opts(const wipes_opts* o) {
+    if (!o) return fail(WIPES_ERR_INVALID, "opts is NULL");
+    if (!(o->cutoff_sigma > 0.f) || !std::isfinite(o->cutoff_sigma))
+        return fail(WIPES_ERR_INVALID, "cutoff_sigma must be positive and finite");
+    if (!(o->alpha_max > 0.f && o->alpha_max < 1.f))
+        return fail(WIPES_ERR_INVALID, "alpha_max must lie in (0, 1)");
+    if (!(o->alpha_min >= 0.f) || !(o->T_min >= 0.f) || !(o->dilation >= 0.f))
+        return fail(WIPES_ERR_INVALID, "alpha_min, T_min and dilation must be non-negative");
+    if (o->freq_proj_mode != 0) return fail(WIPES_ERR_INVALID, "freq_proj_mode must be 0");
+    return WIPES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void wipes_default_opts(int dims, wipes_opts* out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->cutoff_sigma = 3.0f;
+    out->alpha_min = 1.0f / 255.0f;
+    out->alpha_max = 0.99f;
+    out->T_min = 1e-4f;
+    out->dilation = dims == 3 ? 0.3f : 0.0f;
+}
+
+wipes_status wipes_create(int device, wipes_ctx** out) {
+    if (!out) return fail(WIPES_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    WIPES_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(WIPES_ERR_INVALID, "no CUDA device " + std::to_string(device));
+    DeviceGuard g(device);
+    wipes_ctx* c = new wipes_ctx();
+    c->device = device;
+    cudaError_t e = cudaMallocHost(&c->h_total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_loss_partials, sizeof(float) * kLossBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 2);
+    if (e != cudaSuccess) {
+        if (c->h_total) cudaFreeHost(c->h_total);
+        delete c;
+        return fail(WIPES_ERR_CUDA, std::string("context allocation failed: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return WIPES_OK;
+}
+
+wipes_status wipes_destroy(wipes_ctx* ctx) {
+    if (!ctx) return WIPES_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& b : ctx->pending) {
+        cudaEventDestroy(b.a);
+        cudaEventDestroy(b.b);
+    }
+    for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
+    cudaFreeHost(ctx->h_total);
+    cudaFree(ctx->d_loss_partials);
+    cudaFree(ctx->d_counters);
+    delete ctx;
+    return WIPES_OK;
+}
+
+wipes_status wipes_state_create(wipes_ctx* ctx, wipes_state** out) {
+    if (!ctx || !out) return fail(WIPES_ERR_INVALID, "ctx or out is NULL");
+    wipes_state* st = new wipes_state();
+    st->ctx = ctx;
+    *out = st;
+    return WIPES_OK;
+}
+
+wipes_status wipes_state_destroy(wipes_state* st) {
+    if (!st) return WIPES_OK;
+    DeviceGuard g(st->ctx->device);
+    for (DevBuf* b : st->all) release(*b);
+    release(st->grad_img);
+    delete st;
+    return WIPES_OK;
+}
+
+wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, int H, int W,
+                            const wipes_opts* opts, float* out, void* stream) {
+    if (!ctx || !st || !out || (N > 0 && !params)) return fail(WIPES_ERR_INVALID, "null argument");
+    if (N < 0 || N > (int64_t)INT32_MAX) return fail(WIPES_ERR_INVALID, "N out of range");
+    WIPES_TRY(check_image(H, W));
+    WIPES_TRY(check_opts(opts));
+    if (((uintptr_t)params & 15) != 0) return fail(WIPES_ERR_INVALID, "params must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    WIPES_TRY(prepare_state(st, 2, N, H, W, opts));
+    {
+        StageTimer t(ctx, WIPES_STAGE_FOOTPRINT, s);
+        launch_footprint2d(params, N, W, H, opts->cutoff_sigma, st->rec.as<float4>(), st->rect.as<PixRect>(),
+                           st->counts.as<uint32_t>(), nullptr, s);
+    }
+    WIPES_TRY(bin_and_sort(st, nullptr, s));
+    {
+        StageTimer t(ctx, WIPES_STAGE_BLEND, s);
+        launch_blend2d(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), W, H,
+                       st->tiles_x, st->tiles_y, opts->cutoff_sigma * opts->cutoff_sigma, out, s);
+    }
+    WIPES_CUDA(cudaGetLastError());
+    st->dims = 2;
+    return WIPES_OK;
+}
+
+wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, const wipes_camera* cam,
+                            int H, int W, const wipes_opts* opts, float* out, void* stream) {
+    if (!ctx || !st || !out || !cam || (N > 0 && !params)) return fail(WIPES_ERR_INVALID, "null argument");
+    if (N < 0 || N > (int64_t)INT32_MAX) return fail(WIPES_ERR_INVALID, "N out of range");
+    WIPES_TRY(check_image(H, W));
+    WIPES_TRY(check_opts(opts));
+    if (((uintptr_t)params & 15) != 0) return fail(WIPES_ERR_INVALID, "params must be 16-byte aligned");
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !(cam->near_z > 0.f))
+        return fail(WIPES_ERR_INVALID, "camera needs fx, fy, near_z > 0");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    WIPES_TRY(prepare_state(st, 3, N, H, W, opts));
+    st->cam = *cam;
+    const size_t n = (size_t)std::max<int64_t>(N, 1);
+    for (int k = 0; k < 2; ++k) {
+        WIPES_TRY(ensure(st->dkeys[k], sizeof(uint32_t) * n));
+        WIPES_TRY(ensure(st->dvals[k], sizeof(uint32_t) * n));
+    }
+    WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(N)));
+    const size_t npix = (size_t)H * (size_t)W;
+    WIPES_TRY(ensure(st->T_final, sizeof(float) * npix));
+    WIPES_TRY(ensure(st->last, sizeof(uint32_t) * npix));
+    {
+        StageTimer t(ctx, WIPES_STAGE_FOOTPRINT, s);
+        launch_footprint3d(params, N, *cam, W, H, opts->cutoff_sigma, opts->dilation, st->rec.as<float4>(),
+                           st->rect.as<PixRect>(), st->counts.as<uint32_t>(), st->dkeys[0].as<uint32_t>(), s);
+    }
+    // front-to-back order: stable sort of the primitives by the bits of their camera depth
+    uint32_t* dk[2] = {st->dkeys[0].as<uint32_t>(), st->dkeys[1].as<uint32_t>()};
+    uint32_t* dv[2] = {st->dvals[0].as<uint32_t>(), st->dvals[1].as<uint32_t>()};
+    int cur = 0;
+    {
+        StageTimer t(ctx, WIPES_STAGE_DEPTH_SORT, s);
+        launch_iota(st->dvals[0].as<uint32_t>(), N, s);
+        cur = radix_sort_pairs(dk, dv, N, 32, st->hist.as<uint32_t>(), s);
+    }
+    WIPES_TRY(bin_and_sort(st, dv[cur], s));
+    {
+        StageTimer t(ctx, WIPES_STAGE_BLEND, s);
+        launch_blend3d(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), W, H,
+                       st->tiles_x, st->tiles_y, blend_opts(*opts), out, st->T_final.as<float>(),
+                       st->last.as<uint32_t>(), s);
+    }
+    WIPES_CUDA(cudaGetLastError());
+    st->dims = 3;
+    return WIPES_OK;
+}
+
+wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float* params, const float* dL_dout,
+                                   float* dL_dparams, void* stream) {
+    if (!ctx || !st || !dL_dout || !dL_dparams || (st->N > 0 && !params))
+        return fail(WIPES_ERR_INVALID, "null argument");
+    if (st->dims != 2 && st->dims != 3) return fail(WIPES_ERR_INVALID, "state holds no forward pass");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = st->N;
+    const float cutoff2 = st->opts.cutoff_sigma * st->opts.cutoff_sigma;
+    if (st->dims == 2) {
+        WIPES_TRY(ensure(st->partial, sizeof(float) * 12 * (size_t)std::max<int64_t>(st->n_inst, 1)));
+        {
+            StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
+            launch_backward2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->offsets.as<uint32_t>(),
+                              st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), st->W, st->H, st->tiles_x,
+                              st->tiles_y, cutoff2, dL_dout, st->partial.as<float>(), s);
+        }
+        StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
+        launch_reduce_chain2d(params, N, st->offsets.as<uint32_t>(), st->counts.as<uint32_t>(),
+                              st->partial.as<float>(), dL_dparams, s);
+    } else {
+        WIPES_TRY(ensure(st->grad_img, sizeof(float) * 12 * (size_t)std::max<int64_t>(N, 1)));
+        {
+            StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
+            if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * 12 * (size_t)N, s));
+            launch_backward3d(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(),
+                              st->W, st->H, st->tiles_x, st->tiles_y, blend_opts(st->opts), st->T_final.as<float>(),
+                              st->last.as<uint32_t>(), dL_dout, st->grad_img.as<float>(), s);
+        }
+        StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
+        launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->rec.as<float4>(),
+                       st->grad_img.as<float>(), dL_dparams, s);
+    }
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_deform6d(const float* params6, int64_t N, float t, float* params3, void* stream) {
+    if (N < 0 || (N > 0 && (!params6 || !params3))) return fail(WIPES_ERR_INVALID, "bad argument");
+    launch_deform6d(params6, N, t, params3, (cudaStream_t)stream);
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_deform6d_backward(const float* params6, int64_t N, float t, const float* dL_dparams3,
+                                     float* dL_dparams6, int accumulate, void* stream) {
+    if (N < 0 || (N > 0 && (!params6 || !dL_dparams3 || !dL_dparams6))) return fail(WIPES_ERR_INVALID, "bad argument");
+    launch_deform6d_backward(params6, N, t, dL_dparams3, dL_dparams6, accumulate, (cudaStream_t)stream);
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_l2_loss(wipes_ctx* ctx, const float* img, const float* target, int64_t n, float* loss,
+                           float* dL_dimg, void* stream) {
+    if (!ctx || n <= 0 || !img || !target || !loss || !dL_dimg) return fail(WIPES_ERR_INVALID, "bad argument");
+    DeviceGuard g(ctx->device);
+    StageTimer t(ctx, WIPES_STAGE_LOSS, (cudaStream_t)stream);
+    launch_l2_loss(img, target, n, loss, dL_dimg, ctx->d_loss_partials, (cudaStream_t)stream);
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_state_get_info(const wipes_state* st, wipes_state_info* info) {
+    if (!st || !info) return fail(WIPES_ERR_INVALID, "null argument");
+    info->dims = st->dims;
+    info->H = st->H;
+    info->W = st->W;
+    info->tiles_x = st->tiles_x;
+    info->tiles_y = st->tiles_y;
+    info->N = st->N;
+    info->n_instances = st->n_inst;
+    info->bytes_reserved = (int64_t)st->reserved();
+    return WIPES_OK;
+}
+
+wipes_status wipes_state_copy_lists(const wipes_state* st, uint32_t* tile_ids, uint32_t* prim_ids,
+                                    uint32_t* tile_ranges, void* stream) {
+    if (!st) return fail(WIPES_ERR_INVALID, "null state");
+    if (st->dims == 0) return fail(WIPES_ERR_INVALID, "state holds no forward pass");
+    DeviceGuard g(st->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t I = (size_t)st->n_inst;
+    if (tile_ids && I)
+        WIPES_CUDA(cudaMemcpyAsync(tile_ids, st->keys[st->sorted].p, I * 4, cudaMemcpyDeviceToDevice, s));
+    if (prim_ids && I)
+        WIPES_CUDA(cudaMemcpyAsync(prim_ids, st->vals[st->sorted].p, I * 4, cudaMemcpyDeviceToDevice, s));
+    if (tile_ranges)
+        WIPES_CUDA(cudaMemcpyAsync(tile_ranges, st->ranges.p, (size_t)st->tiles_x * st->tiles_y * sizeof(uint2),
+                                   cudaMemcpyDeviceToDevice, s));
+    return WIPES_OK;
+}
+
+wipes_status wipes_state_copy_pixel_state(const wipes_state* st, float* T_final, uint32_t* last_index, void* stream) {
+    if (!st) return fail(WIPES_ERR_INVALID, "null state");
+    if (st->dims != 3) return fail(WIPES_ERR_INVALID, "state holds no 3D forward pass");
+    DeviceGuard g(st->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t npix = (size_t)st->H * st->W;
+    if (T_final) WIPES_CUDA(cudaMemcpyAsync(T_final, st->T_final.p, npix * 4, cudaMemcpyDeviceToDevice, s));
+    if (last_index) WIPES_CUDA(cudaMemcpyAsync(last_index, st->last.p, npix * 4, cudaMemcpyDeviceToDevice, s));
+    return WIPES_OK;
+}
+
+wipes_status wipes_state_count_pairs(wipes_ctx* ctx, const wipes_state* st, int64_t* visited, int64_t* inside,
+                                     void* stream) {
+    if (!ctx || !st || !visited || !inside) return fail(WIPES_ERR_INVALID, "null argument");
+    if (st->dims == 0) return fail(WIPES_ERR_INVALID, "state holds no forward pass");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    WIPES_CUDA(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * 2, s));
+    launch_count_pairs(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), st->W,
+                       st->H, st->tiles_x, st->tiles_y, st->opts.cutoff_sigma * st->opts.cutoff_sigma,
+                       ctx->d_counters, s);
+    unsigned long long h[2] = {0, 0};
+    WIPES_CUDA(cudaMemcpyAsync(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+    WIPES_CUDA(cudaStreamSynchronize(s));
+    *visited = (int64_t)h[0];
+    *inside = (int64_t)h[1];
+    return WIPES_OK;
+}
+
+wipes_status wipes_set_timing(wipes_ctx* ctx, int enable) {
+    if (!ctx) return fail(WIPES_ERR_INVALID, "null ctx");
+    ctx->timing = enable != 0;
+    return WIPES_OK;
+}
+
+wipes_status wipes_get_timing(wipes_ctx* ctx, double* ms, int64_t* brackets, int reset) {
+    if (!ctx) return fail(WIPES_ERR_INVALID, "null ctx");
+    DeviceGuard g(ctx->device);
+    for (auto& b : ctx->pending) {
+        WIPES_CUDA(cudaEventSynchronize(b.b));
+        float e = 0.f;
+        WIPES_CUDA(cudaEventElapsedTime(&e, b.a, b.b));
+        ctx->stage_ms[b.stage] += e;
+        ctx->stage_n[b.stage] += 1;
+        ctx->free_events.push_back(b.a);
+        ctx->free_events.push_back(b.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < WIPES_STAGE_COUNT; ++k) {
+        if (ms) ms[k] = ctx->stage_ms[k];
+        if (brackets) brackets[k] = ctx->stage_n[k];
+        if (reset) {
+            ctx->stage_ms[k] = 0.0;
+            ctx->stage_n[k] = 0;
+        }
+    }
+    return WIPES_OK;
+}
+
+int64_t wipes_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* wipes_status_string(wipes_status s) {
+    switch (s) {
+        case WIPES_OK: return "ok";
+        case WIPES_ERR_INVALID: return "invalid argument";
+        case WIPES_ERR_CAPACITY: return "capacity exceeded";
+        case WIPES_ERR_CUDA: return "CUDA error";
+        case WIPES_ERR_TIMEOUT: return "device wait timed out";
+        case WIPES_ERR_OOM: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char* wipes_last_error(void) { return g_last_error.c_str(); }
+
+wipes_status wipes_sync_status(wipes_ctx* ctx, void* stream) {
+    if (!ctx) return fail(WIPES_ERR_INVALID, "null ctx");
+    DeviceGuard g(ctx->device);
+    WIPES_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// Binning: scan of per-primitive tile counts, emission of (tile, primitive) pairs, a stable LSD
+// radix sort of the pairs, and per-tile ranges of the sorted list (the tile-sorting pipeline of
+// 3DGS that the paper follows, Sec. 4.1; the paper cites a GPU sort for this step, Sec. 1).
+//
+// Order contract: pairs are emitted in scan order (primitive index in 2D, front-to-back depth
+// order in 3D), and the sort is stable, so each tile's list is ordered by that scan order.
+#include "common.cuh"
+
+namespace wipes {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// Exclusive scan over a 256-thread block; returns the exclusive prefix and writes the block total.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* total, T* s_warp /* [kWarps] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    T warp_base = 0, sum = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const T s = s_warp[w];
+        if (w < warp) warp_base += s;
+        sum += s;
+    }
+    __syncthreads();
+    if (total) *total = sum;
+    return warp_base + inc - x;
+}
+
+// ---------------------------------------------------------------------------------------------
+// scan of tile counts and emission
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kScanItems = kScanBlockElems / kThreads;  // 4
+
+__global__ void __launch_bounds__(kThreads) k_block_sums(const uint32_t* __restrict__ counts,
+                                                         const uint32_t* __restrict__ perm, int64_t n,
+                                                         unsigned long long* __restrict__ block_sums) {
+    __shared__ unsigned long long s_warp[kWarps];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t j = base + k;
+        if (j < n) s += counts[perm ? perm[j] : (uint32_t)j];
+    }
+    unsigned long long total;
+    block_exclusive_scan<unsigned long long>(s, &total, s_warp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long* __restrict__ v, int nb,
+                                                              unsigned long long* __restrict__ total_out) {
+    __shared__ unsigned long long s_warp[kWarps];
+    unsigned long long carry = 0;
+    for (int base = 0; base < nb; base += kThreads) {
+        const int j = base + threadIdx.x;
+        const unsigned long long x = j < nb ? v[j] : 0ull;
+        unsigned long long chunk;
+        const unsigned long long ex = block_exclusive_scan<unsigned long long>(x, &chunk, s_warp);
+        if (j < nb) v[j] = carry + ex;
+        carry += chunk;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ counts,
+                                                   const uint32_t* __restrict__ perm, int64_t n,
+                                                   const PixRect* __restrict__ rect,
+                                                   const unsigned long long* __restrict__ block_offsets, int tiles_x,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   uint32_t* __restrict__ offsets) {
+    __shared__ unsigned long long s_warp[kWarps];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
+    uint32_t prim[kScanItems], cnt[kScanItems];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t j = base + k;
+        prim[k] = j < n ? (perm ? perm[j] : (uint32_t)j) : 0u;
+        cnt[k] = j < n ? counts[prim[k]] : 0u;
+        s += cnt[k];
+    }
+    unsigned long long off = block_offsets[blockIdx.x] + block_exclusive_scan<unsigned long long>(s, nullptr, s_warp);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k >= n) break;
+        offsets[prim[k]] = (uint32_t)off;
+        if (cnt[k]) {
+            const PixRect r = rect[prim[k]];
+            const int tx0 = r.u0 / kTile, tx1 = r.u1 / kTile, ty0 = r.v0 / kTile, ty1 = r.v1 / kTile;
+            uint32_t o = (uint32_t)off;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    keys[o] = (uint32_t)(ty * tiles_x + tx);
+                    vals[o] = prim[k];
+                    ++o;
+                }
+        }
+        off += cnt[k];
+    }
+}
+
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = keys[i];
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    }
+}
+
+__global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------------------------
+// stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass
+// (reduce-then-scan: per-block digit histograms, per-digit scan, stable scatter)
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kThreads * kSortItems;  // 4096 keys per block
+constexpr int kMaxRadix = 256;
+
+__global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                            int nbits, uint32_t* __restrict__ hist, int nb) {
+    __shared__ uint32_t s_cnt[kMaxRadix];
+    const int radix = 1 << nbits;
+    const uint32_t mask = (uint32_t)radix - 1u;
+    for (int d = threadIdx.x; d < radix; d += kThreads) s_cnt[d] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + (int64_t)i * kThreads + threadIdx.x;
+        const bool valid = idx < n;
+        const uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += kThreads) hist[(int64_t)d * nb + blockIdx.x] = s_cnt[d];
+}
+
+// One block per digit: exclusive scan of that digit's counts over the sort blocks.
+__global__ void __launch_bounds__(kThreads) k_radix_scan_digits(uint32_t* __restrict__ hist, int nb,
+                                                                uint32_t* __restrict__ digit_totals) {
+    __shared__ uint32_t s_warp[kWarps];
+    uint32_t* row = hist + (int64_t)blockIdx.x * nb;
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += kThreads) {
+        const int j = base + threadIdx.x;
+        const uint32_t x = j < nb ? row[j] : 0u;
+        uint32_t chunk;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(x, &chunk, s_warp);
+        if (j < nb) row[j] = carry + ex;
+        carry += chunk;
+    }
+    if (threadIdx.x == 0) digit_totals[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __restrict__ keys_in,
+                                                              const uint32_t* __restrict__ vals_in,
+                                                              uint32_t* __restrict__ keys_out,
+                                                              uint32_t* __restrict__ vals_out, int64_t n, int shift,
+                                                              int nbits, const uint32_t* __restrict__ hist,
+                                                              const uint32_t* __restrict__ digit_totals, int nb) {
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_wc[kWarps][kMaxRadix];
+    __shared__ uint32_t s_dstart[kMaxRadix];
+    __shared__ uint32_t s_gbase[kMaxRadix];
+    __shared__ uint32_t s_warp[kWarps];
+    const int radix = 1 << nbits;
+    const uint32_t mask = (uint32_t)radix - 1u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_wc[0][0])[k] = 0u;
+    // global start of each digit = exclusive scan of the digit totals
+    {
+        const uint32_t x = (int)threadIdx.x < radix ? digit_totals[threadIdx.x] : 0u;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(x, nullptr, s_warp);
+        if ((int)threadIdx.x < radix) s_gbase[threadIdx.x] = ex + hist[(int64_t)threadIdx.x * nb + blockIdx.x];
+    }
+    __syncthreads();
+    const int64_t blk = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = blk + (int64_t)warp * (kSortItems * 32);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * 32 + lane;
+        k[i] = idx < n ? keys_in[idx] : 0u;
+        v[i] = idx < n ? vals_in[idx] : 0u;
+    }
+    // stable rank within the warp's run, in element order (item i, then lane)
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * 32 + lane;
+        const bool valid = idx < n;
+        const uint32_t d = valid ? (k[i] >> shift) & mask : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (valid) before = s_wc[warp][d];
+        __syncwarp();
+        if (valid) {
+            rank[i] = before + __popc(peers & lt);
+            if (lane == 31 - __clz(peers)) s_wc[warp][d] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: prefix over warps, then block-local digit starts
+    {
+        uint32_t running = 0;
+        if ((int)threadIdx.x < radix) {
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t t = s_wc[w][threadIdx.x];
+                s_wc[w][threadIdx.x] = running;
+                running += t;
+            }
+        }
+        const uint32_t ex = block_exclusive_scan<uint32_t>(running, nullptr, s_warp);
+        if ((int)threadIdx.x < radix) {
+            s_dstart[threadIdx.x] = ex;
+            s_gbase[threadIdx.x] -= ex;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * 32 + lane;
+        if (idx < n) {
+            const uint32_t d = (k[i] >> shift) & mask;
+            const uint32_t pos = s_dstart[d] + s_wc[warp][d] + rank[i];
+            s_keys[pos] = k[i];
+            s_vals[pos] = v[i];
+        }
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kSortTile, n - blk);
+    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+        const uint32_t key = s_keys[t];
+        const uint32_t d = (key >> shift) & mask;
+        const uint32_t g = s_gbase[d] + (uint32_t)t;
+        keys_out[g] = key;
+        vals_out[g] = s_vals[t];
+    }
+}
+
+}  // namespace
+
+void launch_block_sums(const uint32_t* counts, const uint32_t* perm, int64_t n, unsigned long long* block_sums,
+                       cudaStream_t stream) {
+    if (n == 0) return;
+    k_block_sums<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, block_sums); count_launches(1);
+}
+
+void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total, cudaStream_t stream) {
+    k_scan_block_sums<<<1, kThreads, 0, stream>>>(block_sums, nb, total); count_launches(1);
+}
+
+void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const PixRect* rect,
+                 const unsigned long long* block_offsets, int tiles_x, uint32_t* keys, uint32_t* vals,
+                 uint32_t* offsets, cudaStream_t stream) {
+    if (n == 0) return;
+    k_emit<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, rect, block_offsets, tiles_x, keys,
+                                                                  vals, offsets); count_launches(1);
+}
+
+void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, int n_tiles, cudaStream_t stream) {
+    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, stream);
+    if (n == 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+    k_tile_ranges<<<grid, 256, 0, stream>>>(sorted_keys, n, ranges); count_launches(1);
+}
+
+void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
+    if (n == 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+    k_iota<<<grid, 256, 0, stream>>>(v, n); count_launches(1);
+}
+
+int64_t radix_hist_words(int64_t n) { return (int64_t)kMaxRadix * (int64_t)ceil_div(std::max<int64_t>(n, 1), kSortTile) + kMaxRadix; }
+
+int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream) {
+    if (n <= 1 || bits <= 0) return 0;
+    const int passes = (bits + 7) / 8;
+    const int nb = (int)ceil_div(n, kSortTile);
+    uint32_t* digit_totals = hist + (int64_t)kMaxRadix * nb;
+    int cur = 0, shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int nbits = (bits - shift + (passes - p) - 1) / (passes - p);  // split the remaining bits evenly
+        k_radix_upsweep<<<nb, kThreads, 0, stream>>>(keys[cur], n, shift, nbits, hist, nb); count_launches(1);
+        k_radix_scan_digits<<<1 << nbits, kThreads, 0, stream>>>(hist, nb, digit_totals); count_launches(1);
+        k_radix_downsweep<<<nb, kThreads, 0, stream>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
+                                                       nbits, hist, digit_totals, nb); count_launches(1);
+        cur ^= 1;
+        shift += nbits;
+    }
+    return cur;
+}
+
+}  // namespace wipes

@@ -1,0 +1,261 @@
+// Footprint kernels: per-primitive projection to the image plane, the cutoff ellipse, the covered
+// pixel range and the number of covered tiles (the binning front end of the 3DGS-style pipeline
+// the paper follows, Sec. 4.1), plus the 6D time model.
+//
+// This translation unit is compiled with -fmad=false: every float expression below is a sequence
+// of single IEEE binary32 operations in source order, so the centre, the Cholesky factor of the
+// inverse covariance, the extents and the depth are bit-for-bit reproducible.  The tile lists and
+// the per-pixel cutoff decision depend only on these values.
+#include "common.cuh"
+
+namespace wipes {
+namespace {
+
+__device__ __forceinline__ bool finite4(float a, float b, float c, float d) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+
+__device__ __forceinline__ PixRect covered_pixels(float mx, float my, float ex, float ey, int W, int H) {
+    float xlo = (mx - ex) - 0.5f;
+    float xhi = (mx + ex) - 0.5f;
+    float ylo = (my - ey) - 0.5f;
+    float yhi = (my + ey) - 0.5f;
+    xlo = fminf(fmaxf(xlo, -1.0f), (float)W);
+    xhi = fminf(fmaxf(xhi, -1.0f), (float)W);
+    ylo = fminf(fmaxf(ylo, -1.0f), (float)H);
+    yhi = fminf(fmaxf(yhi, -1.0f), (float)H);
+    PixRect r;
+    r.u0 = max(0, (int)ceilf(xlo));
+    r.u1 = min(W - 1, (int)floorf(xhi));
+    r.v0 = max(0, (int)ceilf(ylo));
+    r.v1 = min(H - 1, (int)floorf(yhi));
+    if (r.u0 > r.u1 || r.v0 > r.v1) { r.u0 = 1; r.u1 = 0; r.v0 = 1; r.v1 = 0; }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t tile_count(const PixRect& r) {
+    if (r.u0 > r.u1) return 0u;
+    return (uint32_t)((r.u1 / kTile - r.u0 / kTile + 1) * (r.v1 / kTile - r.v0 / kTile + 1));
+}
+
+__device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rect, uint32_t* counts,
+                                            uint32_t* depth_keys) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec[i * kRecF4 + 0] = z; rec[i * kRecF4 + 1] = z; rec[i * kRecF4 + 2] = z; rec[i * kRecF4 + 3] = z;
+    PixRect e; e.u0 = 1; e.u1 = 0; e.v0 = 1; e.v1 = 0;
+    rect[i] = e;
+    counts[i] = 0u;
+    if (depth_keys) depth_keys[i] = 0xFFFFFFFFu;
+}
+
+// 2D: Sigma = R(theta) diag(sx^2, sy^2) R(theta)^T; Sigma^-1 = R diag(1/sx^2, 1/sy^2) R^T.
+// Cholesky of Sigma^-1: l11 = sqrt(A), l21 = B / l11, l22 = sqrt(det)/l11 = 1 / (sx sy l11).
+__global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ params, int64_t N, int W, int H,
+                                                     float cutoff, float4* __restrict__ rec, PixRect* __restrict__ rect,
+                                                     uint32_t* __restrict__ counts) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 p0 = params[i * 4 + 0];  // mu_x mu_y s_x s_y
+    const float4 p1 = params[i * 4 + 1];  // theta f_x f_y phi
+    const float4 p2 = params[i * 4 + 2];  // c_r c_g c_b -
+    const float sx = p0.z, sy = p0.w;
+    // cos and sin in binary64, rounded once to binary32
+    const float c = (float)cos((double)p1.x);
+    const float s = (float)sin((double)p1.x);
+    const float sx2 = sx * sx, sy2 = sy * sy;
+    const float ix = 1.0f / sx2, iy = 1.0f / sy2;
+    const float cc = c * c, ss = s * s, cs = c * s;
+    const float A = cc * ix + ss * iy;
+    const float B = cs * (ix - iy);
+    const float l11 = sqrtf(A);
+    const float l21 = B / l11;
+    const float l22 = 1.0f / ((sx * sy) * l11);
+    const float vxx = cc * sx2 + ss * sy2;
+    const float vyy = ss * sx2 + cc * sy2;
+    const float mx = p0.x, my = p0.y;
+    const float ex = (cutoff * sqrtf(vxx)) * kExtMargin;
+    const float ey = (cutoff * sqrtf(vyy)) * kExtMargin;
+    const bool valid = finite4(mx, my, l11, l21) && finite4(l22, ex, ey, 1.0f) && sx > 0.0f && sy > 0.0f &&
+                       l11 > 0.0f && l22 > 0.0f;
+    if (!valid) { write_empty(i, rec, rect, counts, nullptr); return; }
+    const PixRect r = covered_pixels(mx, my, ex, ey, W, H);
+    rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
+    rec[i * kRecF4 + 1] = make_float4(l22, p1.y, p1.z, p1.w * kInvTwoPi);
+    rec[i * kRecF4 + 2] = make_float4(p2.x, p2.y, p2.z, 1.0f);
+    rec[i * kRecF4 + 3] = make_float4(ex, ey, 0.0f, 0.0f);
+    rect[i] = r;
+    counts[i] = tile_count(r);
+}
+
+struct Cam {
+    float V[12];
+    float fx, fy, cx, cy, near_z;
+};
+
+// 3D: camera-frame centre t = V mu + t0; P = J V R(q) S (2x3), Sigma' = P P^T + dil I with the
+// local affine Jacobian J of the perspective map (Sec. 3.1).  det Sigma' is evaluated as
+// |P0 x P1|^2 + dil (|P0|^2 + |P1|^2) + dil^2, a sum of non-negative terms.
+// Cholesky of Sigma'^-1: l22 = 1/sqrt(S11), l11 = sqrt(S11/D), l21 = -S01/sqrt(S11 D).
+// Frequency: fc = V f, f' = (fc_x tz / fx, fc_y tz / fy) (phase gradient on the fronto-parallel
+// plane through the centre; the viewing-axis component is dropped, Sec. 4.1).
+__global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ params, int64_t N, Cam cam, int W,
+                                                     int H, float cutoff, float dil, float4* __restrict__ rec,
+                                                     PixRect* __restrict__ rect, uint32_t* __restrict__ counts,
+                                                     uint32_t* __restrict__ depth_keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4* pp = reinterpret_cast<const float4*>(params + i * WIPES_P3D);
+    const float4 a0 = pp[0], a1 = pp[1], a2 = pp[2], a3 = pp[3], a4 = pp[4];
+    float p[20] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y,
+                   a2.z, a2.w, a3.x, a3.y, a3.z, a3.w, a4.x, a4.y, a4.z, a4.w};
+    const float* V = cam.V;
+    const float tx = ((V[0] * p[0] + V[1] * p[1]) + V[2] * p[2]) + V[3];
+    const float ty = ((V[4] * p[0] + V[5] * p[1]) + V[6] * p[2]) + V[7];
+    const float tz = ((V[8] * p[0] + V[9] * p[1]) + V[10] * p[2]) + V[11];
+    if (!(tz > cam.near_z) || !isfinite(tz) || !isfinite(tx) || !isfinite(ty)) {
+        write_empty(i, rec, rect, counts, depth_keys);
+        return;
+    }
+    float qw = p[6], qx = p[7], qy = p[8], qz = p[9];
+    const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
+    const float r = sqrtf(n2);
+    qw = qw / r; qx = qx / r; qy = qy / r; qz = qz / r;
+    const float xx = qx * qx, yy = qy * qy, zz = qz * qz;
+    const float xy = qx * qy, xz = qx * qz, yz = qy * qz;
+    const float wx = qw * qx, wy = qw * qy, wz = qw * qz;
+    float R[9];
+    R[0] = 1.0f - 2.0f * (yy + zz); R[1] = 2.0f * (xy - wz);        R[2] = 2.0f * (xz + wy);
+    R[3] = 2.0f * (xy + wz);        R[4] = 1.0f - 2.0f * (xx + zz); R[5] = 2.0f * (yz - wx);
+    R[6] = 2.0f * (xz - wy);        R[7] = 2.0f * (yz + wx);        R[8] = 1.0f - 2.0f * (xx + yy);
+    float M[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) M[a * 3 + b] = R[a * 3 + b] * p[3 + b];
+    float Q[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Q[a * 3 + b] = (V[a * 4 + 0] * M[0 * 3 + b] + V[a * 4 + 1] * M[1 * 3 + b]) + V[a * 4 + 2] * M[2 * 3 + b];
+    const float limx = 1.3f * ((0.5f * (float)W) / cam.fx);
+    const float limy = 1.3f * ((0.5f * (float)H) / cam.fy);
+    const float txz = fminf(limx, fmaxf(-limx, tx / tz));
+    const float tyz = fminf(limy, fmaxf(-limy, ty / tz));
+    const float j00 = cam.fx / tz, j02 = -((cam.fx * txz) / tz);
+    const float j11 = cam.fy / tz, j12 = -((cam.fy * tyz) / tz);
+    float P0[3], P1[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        P0[b] = j00 * Q[0 * 3 + b] + j02 * Q[2 * 3 + b];
+        P1[b] = j11 * Q[1 * 3 + b] + j12 * Q[2 * 3 + b];
+    }
+    const float n0 = (P0[0] * P0[0] + P0[1] * P0[1]) + P0[2] * P0[2];
+    const float n1 = (P1[0] * P1[0] + P1[1] * P1[1]) + P1[2] * P1[2];
+    const float s01 = (P0[0] * P1[0] + P0[1] * P1[1]) + P0[2] * P1[2];
+    const float c0 = P0[1] * P1[2] - P0[2] * P1[1];
+    const float c1 = P0[2] * P1[0] - P0[0] * P1[2];
+    const float c2 = P0[0] * P1[1] - P0[1] * P1[0];
+    const float S00 = n0 + dil, S11 = n1 + dil;
+    const float D = (((c0 * c0 + c1 * c1) + c2 * c2) + dil * (n0 + n1)) + dil * dil;
+    const float l22 = 1.0f / sqrtf(S11);
+    const float l11 = sqrtf(S11 / D);
+    const float l21 = -(s01 / sqrtf(S11 * D));
+    const float mx = ((cam.fx * tx) / tz) + cam.cx;
+    const float my = ((cam.fy * ty) / tz) + cam.cy;
+    const float ex = (cutoff * sqrtf(S00)) * kExtMargin;
+    const float ey = (cutoff * sqrtf(S11)) * kExtMargin;
+    const bool valid = finite4(mx, my, l11, l21) && finite4(l22, ex, ey, D) && D > 0.0f && S11 > 0.0f &&
+                       l11 > 0.0f && l22 > 0.0f;
+    if (!valid) { write_empty(i, rec, rect, counts, depth_keys); return; }
+    // projected frequency (not part of any integer decision)
+    const float fcx = (V[0] * p[10] + V[1] * p[11]) + V[2] * p[12];
+    const float fcy = (V[4] * p[10] + V[5] * p[11]) + V[6] * p[12];
+    const PixRect rr = covered_pixels(mx, my, ex, ey, W, H);
+    rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
+    rec[i * kRecF4 + 1] = make_float4(l22, fcx * tz / cam.fx, fcy * tz / cam.fy, p[13] * kInvTwoPi);
+    rec[i * kRecF4 + 2] = make_float4(p[15], p[16], p[17], p[14]);
+    rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, 0.0f);
+    rect[i] = rr;
+    counts[i] = tile_count(rr);
+    depth_keys[i] = __float_as_uint(tz);
+}
+
+__global__ void __launch_bounds__(256) k_deform6d(const float* __restrict__ p6, int64_t N, float t,
+                                                  float* __restrict__ p3) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float* a = p6 + i * WIPES_P6D;
+    float* o = p3 + i * WIPES_P3D;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        // single rounding of mu0 + v t (and of f, phi below): the correctly rounded linear model
+        o[j] = __fmaf_rn(a[20 + j], t, a[j]);
+        o[3 + j] = a[3 + j] * expf(a[27 + j] * t);
+        o[10 + j] = __fmaf_rn(a[23 + j], t, a[10 + j]);
+    }
+#pragma unroll
+    for (int j = 6; j < 10; ++j) o[j] = a[j];
+    o[13] = __fmaf_rn(a[26], t, a[13]);
+#pragma unroll
+    for (int j = 14; j < 20; ++j) o[j] = a[j];
+}
+
+__global__ void __launch_bounds__(256) k_deform6d_backward(const float* __restrict__ p6, int64_t N, float t,
+                                                           const float* __restrict__ g3, float* __restrict__ g6,
+                                                           int accumulate) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float* a = p6 + i * WIPES_P6D;
+    const float* g = g3 + i * WIPES_P3D;
+    float o[WIPES_P6D];
+#pragma unroll
+    for (int j = 0; j < WIPES_P6D; ++j) o[j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 20; ++j) o[j] = g[j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float e = expf(a[27 + j] * t);
+        o[3 + j] = g[3 + j] * e;
+        o[20 + j] = g[j] * t;
+        o[23 + j] = g[10 + j] * t;
+        o[27 + j] = g[3 + j] * a[3 + j] * e * t;
+    }
+    o[26] = g[13] * t;
+    float* out = g6 + i * WIPES_P6D;
+#pragma unroll
+    for (int j = 0; j < WIPES_P6D; ++j) out[j] = accumulate ? out[j] + o[j] : o[j];
+}
+
+}  // namespace
+
+void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, float4* rec, PixRect* rect,
+                        uint32_t* counts, uint32_t* /*depth_keys*/, cudaStream_t stream) {
+    if (N == 0) return;
+    k_footprint2d<<<ceil_div(N, 256), 256, 0, stream>>>(reinterpret_cast<const float4*>(params), N, W, H, cutoff,
+                                                         rec, rect, counts); count_launches(1);
+}
+
+void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
+                        float dilation, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
+                        cudaStream_t stream) {
+    if (N == 0) return;
+    Cam c;
+    for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
+    c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
+    k_footprint3d<<<ceil_div(N, 256), 256, 0, stream>>>(params, N, c, W, H, cutoff, dilation, rec, rect, counts,
+                                                         depth_keys); count_launches(1);
+}
+
+void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream) {
+    if (N == 0) return;
+    k_deform6d<<<ceil_div(N, 256), 256, 0, stream>>>(params6, N, t, params3); count_launches(1);
+}
+
+void launch_deform6d_backward(const float* params6, int64_t N, float t, const float* g3, float* g6, int accumulate,
+                              cudaStream_t stream) {
+    if (N == 0) return;
+    k_deform6d_backward<<<ceil_div(N, 256), 256, 0, stream>>>(params6, N, t, g3, g6, accumulate); count_launches(1);
+}
+
+}  // namespace wipes

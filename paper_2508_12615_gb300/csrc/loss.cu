@@ -1,0 +1,50 @@
+// Mean squared error and its gradient in one pass (deterministic two-stage reduction).
+#include "common.cuh"
+
+namespace wipes {
+namespace {
+
+__global__ void __launch_bounds__(256) k_l2_loss(const float* __restrict__ img, const float* __restrict__ target,
+                                                 int64_t n, float* __restrict__ grad, float* __restrict__ partials) {
+    __shared__ float s_warp[8];
+    const float scale = 2.0f / (float)n;
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = img[i] - target[i];
+        grad[i] = scale * d;
+        acc = fmaf(d, d, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < 8; ++w) s += s_warp[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_l2_finish(const float* __restrict__ partials, int nb, int64_t n, float* __restrict__ loss) {
+    __shared__ double s[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) acc += partials[i];
+    s[threadIdx.x] = acc;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 32; ++i) t += s[i];
+        *loss = (float)(t / (double)n);
+    }
+}
+
+}  // namespace
+
+void launch_l2_loss(const float* img, const float* target, int64_t n, float* loss, float* grad, float* partials,
+                    cudaStream_t stream) {
+    const int nb = (int)std::min<int64_t>(kLossBlocks, std::max<int64_t>(1, ceil_div(n, 256)));
+    k_l2_loss<<<nb, 256, 0, stream>>>(img, target, n, grad, partials); count_launches(1);
+    k_l2_finish<<<1, 32, 0, stream>>>(partials, nb, n, loss); count_launches(1);
+}
+
+}  // namespace wipes

@@ -1,0 +1,411 @@
+// 3D view synthesis: front-to-back alpha blending of projected wavelets over depth-sorted tile
+// lists (Eq. 3 with G' replaced by W', Sec. 4.1), its backward with the transmittance recomputed
+// from the stored final value, and the chain through the EWA projection (Sec. 3.1) and the
+// frequency projection (Sec. 4.1) to the 3D record.
+//
+// Blend rule per pixel, over the tile list in order: skip a primitive outside its cutoff ellipse;
+// alpha = min(alpha_max, o W'); skip alpha < alpha_min; stop before a primitive that would take
+// T (1 - alpha) below T_min; otherwise C += c alpha T, T *= 1 - alpha.  Finally C += T bg.
+#include "common.cuh"
+
+namespace wipes {
+namespace {
+
+constexpr float kNegHalfLog2e = -0.7213475204444817f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float reduced_angle(float t) { return (t - rintf(t)) * kTwoPi; }
+
+__global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restrict__ rec,
+                                                         const uint32_t* __restrict__ sorted_prims,
+                                                         const uint2* __restrict__ ranges, int W, int H, int tiles_x,
+                                                         BlendOpts3 o, float* __restrict__ out,
+                                                         float* __restrict__ T_final, uint32_t* __restrict__ last) {
+    __shared__ float4 s_a[kTilePixels];
+    __shared__ float4 s_b[kTilePixels];
+    __shared__ float4 s_c[kTilePixels];
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int u = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int v = ty * kTile + (threadIdx.x / kTile);
+    const bool inside = u < W && v < H;
+    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    const uint2 range = ranges[tile];
+    bool done = !inside;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    uint32_t seen = 0, last_contrib = 0;
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
+        if (__syncthreads_count(done) == kTilePixels) break;
+        const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
+        if ((int)threadIdx.x < n) {
+            const uint32_t id = sorted_prims[b0 + threadIdx.x];
+            s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
+            s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
+            s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
+        }
+        __syncthreads();
+        for (int j = 0; j < n && !done; ++j) {
+            ++seen;
+            const float4 A = s_a[j];
+            const float4 B = s_b[j];
+            const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
+            if (!(q <= o.cutoff2)) continue;
+            const float dx = px - A.x, dy = py - A.y;
+            const float G = ex2_approx(q * kNegHalfLog2e);
+            const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
+            const float4 C = s_c[j];
+            const float alpha = fminf(o.alpha_max, C.w * w);
+            if (alpha < o.alpha_min) continue;
+            const float test_T = T * (1.f - alpha);
+            if (test_T < o.T_min) { done = true; break; }
+            const float wt = alpha * T;
+            c0 = fmaf(C.x, wt, c0);
+            c1 = fmaf(C.y, wt, c1);
+            c2 = fmaf(C.z, wt, c2);
+            T = test_T;
+            last_contrib = seen;
+        }
+        __syncthreads();
+    }
+    if (inside) {
+        const size_t pix = (size_t)v * W + u;
+        out[pix * 3 + 0] = fmaf(T, o.bg[0], c0);
+        out[pix * 3 + 1] = fmaf(T, o.bg[1], c1);
+        out[pix * 3 + 2] = fmaf(T, o.bg[2], c2);
+        T_final[pix] = T;
+        last[pix] = last_contrib;
+    }
+}
+
+// Image-plane gradient per primitive (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b o
+constexpr int kG = 12;
+
+__global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __restrict__ rec,
+                                                            const uint32_t* __restrict__ sorted_prims,
+                                                            const uint2* __restrict__ ranges, int W, int H, int tiles_x,
+                                                            BlendOpts3 o, const float* __restrict__ T_final,
+                                                            const uint32_t* __restrict__ last,
+                                                            const float* __restrict__ dl_dout,
+                                                            float* __restrict__ grad_img) {
+    __shared__ float4 s_a[kTilePixels];
+    __shared__ float4 s_b[kTilePixels];
+    __shared__ float4 s_c[kTilePixels];
+    __shared__ uint32_t s_id[kTilePixels];
+    __shared__ uint32_t s_max_last;
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int u = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int v = ty * kTile + (threadIdx.x / kTile);
+    const int lane = threadIdx.x & 31;
+    const bool inside = u < W && v < H;
+    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    const uint2 range = ranges[tile];
+    const size_t pix = (size_t)v * W + u;
+    float T = inside ? T_final[pix] : 1.f;
+    const uint32_t my_last = inside ? last[pix] : 0u;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (inside) { g0 = dl_dout[pix * 3 + 0]; g1 = dl_dout[pix * 3 + 1]; g2 = dl_dout[pix * 3 + 2]; }
+    // colour accumulated behind the current primitive, starting with the background term
+    float S0 = T * o.bg[0], S1 = T * o.bg[1], S2 = T * o.bg[2];
+    if (threadIdx.x == 0) s_max_last = 0u;
+    __syncthreads();
+    atomicMax(&s_max_last, my_last);
+    __syncthreads();
+    const uint32_t end = range.x + s_max_last;  // entries past every pixel's last contributor are skipped
+    for (int64_t b_end = end; b_end > (int64_t)range.x; b_end -= kTilePixels) {
+        const uint32_t b0 = (uint32_t)max((int64_t)range.x, b_end - kTilePixels);
+        const int n = (int)((uint32_t)b_end - b0);
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t id = sorted_prims[b0 + threadIdx.x];
+            s_id[threadIdx.x] = id;
+            s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
+            s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
+            s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
+        }
+        __syncthreads();
+        for (int j = n - 1; j >= 0; --j) {
+            const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;  // 1-based position in the tile list
+            bool contrib = false;
+            float gm0 = 0.f, gm1 = 0.f, gl11 = 0.f, gl21 = 0.f, gl22 = 0.f, gfx = 0.f, gfy = 0.f, gph = 0.f;
+            float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gop = 0.f;
+            const float4 A = s_a[j];
+            const float4 B = s_b[j];
+            if (pos <= my_last) {
+                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
+                if (q <= o.cutoff2) {
+                    const float dx = px - A.x, dy = py - A.y;
+                    const float G = ex2_approx(q * kNegHalfLog2e);
+                    const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
+                    const float cs = cos_approx(ang);
+                    const float w = fmaf(0.5f, cs, 0.5f) * G;
+                    const float4 C = s_c[j];
+                    const float raw = C.w * w;
+                    const float alpha = fminf(o.alpha_max, raw);
+                    if (alpha >= o.alpha_min) {
+                        contrib = true;
+                        const float om = 1.f - alpha;
+                        T = T / om;
+                        const float wt = alpha * T;
+                        gc0 = g0 * wt; gc1 = g1 * wt; gc2 = g2 * wt;
+                        const float inv = 1.f / om;
+                        const float galpha = g0 * (C.x * T - S0 * inv) + g1 * (C.y * T - S1 * inv) +
+                                             g2 * (C.z * T - S2 * inv);
+                        S0 = fmaf(C.x, wt, S0);
+                        S1 = fmaf(C.y, wt, S1);
+                        S2 = fmaf(C.z, wt, S2);
+                        if (raw < o.alpha_max) {
+                            gop = galpha * w;
+                            const float gW = galpha * C.w;
+                            const float sn = sin_approx(ang);
+                            const float a = fmaf(A.z, dx, A.w * dy), b = B.x * dy;
+                            const float gq2 = -gW * w;
+                            const float gt = -kPi * gW * G * sn;
+                            const float ga = gq2 * a, gb = gq2 * b;
+                            gl11 = ga * dx;
+                            gl21 = ga * dy;
+                            gl22 = gb * dy;
+                            gm0 = -fmaf(ga, A.z, gt * B.y);
+                            gm1 = -fmaf(ga, A.w, fmaf(gb, B.x, gt * B.z));
+                            gfx = gt * dx;
+                            gfy = gt * dy;
+                            gph = gt;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    gm0 += __shfl_xor_sync(0xffffffffu, gm0, s);
+                    gm1 += __shfl_xor_sync(0xffffffffu, gm1, s);
+                    gl11 += __shfl_xor_sync(0xffffffffu, gl11, s);
+                    gl21 += __shfl_xor_sync(0xffffffffu, gl21, s);
+                    gl22 += __shfl_xor_sync(0xffffffffu, gl22, s);
+                    gfx += __shfl_xor_sync(0xffffffffu, gfx, s);
+                    gfy += __shfl_xor_sync(0xffffffffu, gfy, s);
+                    gph += __shfl_xor_sync(0xffffffffu, gph, s);
+                    gc0 += __shfl_xor_sync(0xffffffffu, gc0, s);
+                    gc1 += __shfl_xor_sync(0xffffffffu, gc1, s);
+                    gc2 += __shfl_xor_sync(0xffffffffu, gc2, s);
+                    gop += __shfl_xor_sync(0xffffffffu, gop, s);
+                }
+                float val = 0.f;
+                val = lane == 0 ? gm0 : val;
+                val = lane == 1 ? gm1 : val;
+                val = lane == 2 ? gl11 : val;
+                val = lane == 3 ? gl21 : val;
+                val = lane == 4 ? gl22 : val;
+                val = lane == 5 ? gfx : val;
+                val = lane == 6 ? gfy : val;
+                val = lane == 7 ? gph : val;
+                val = lane == 8 ? gc0 : val;
+                val = lane == 9 ? gc1 : val;
+                val = lane == 10 ? gc2 : val;
+                val = lane == 11 ? gop : val;
+                if (lane < kG) atomicAdd(grad_img + (size_t)s_id[j] * kG + lane, val);
+            }
+        }
+    }
+}
+
+struct Cam3 {
+    float V[12];
+    float fx, fy, cx, cy, near_z;
+};
+
+// d R(q)_e / d q_m for a unit quaternion q = (w, x, y, z)
+__device__ __forceinline__ void quat_rot_grad(const float q[4], const float gR[9], float gq[4]) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    // row e of R, derivative with respect to (w, x, y, z)
+    const float J[9][4] = {{0.f, 0.f, -4.f * y, -4.f * z},
+                           {-2.f * z, 2.f * y, 2.f * x, -2.f * w},
+                           {2.f * y, 2.f * z, 2.f * w, 2.f * x},
+                           {2.f * z, 2.f * y, 2.f * x, 2.f * w},
+                           {0.f, -4.f * x, 0.f, -4.f * z},
+                           {-2.f * x, -2.f * w, 2.f * z, 2.f * y},
+                           {-2.f * y, 2.f * z, -2.f * w, 2.f * x},
+                           {2.f * x, 2.f * w, 2.f * z, 2.f * y},
+                           {0.f, -4.f * x, -4.f * y, 0.f}};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) s = fmaf(gR[e], J[e][m], s);
+        gq[m] = s;
+    }
+}
+
+// Chain the image-plane gradient (mx, my, L, f', phc, c, o) to the record mu, s, q, f, phi, o, c.
+__global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ params, int64_t N, Cam3 cam, int W, int H,
+                                                 float dil, const float4* __restrict__ rec,
+                                                 const float* __restrict__ grad_img, float* __restrict__ dl_dparams) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float* out = dl_dparams + i * WIPES_P3D;
+    const float4 r0 = rec[(size_t)i * kRecF4 + 0];
+    if (!(r0.z > 0.f)) {  // culled or degenerate: no gradient
+#pragma unroll
+        for (int k = 0; k < WIPES_P3D; ++k) out[k] = 0.f;
+        return;
+    }
+    const float* p = params + i * WIPES_P3D;
+    const float* g = grad_img + (size_t)i * kG;
+    const float g_mx = g[0], g_my = g[1], g11 = g[2], g21 = g[3], g22 = g[4], g_fx = g[5], g_fy = g[6];
+    const float* V = cam.V;
+    const float tx = V[0] * p[0] + V[1] * p[1] + V[2] * p[2] + V[3];
+    const float ty = V[4] * p[0] + V[5] * p[1] + V[6] * p[2] + V[7];
+    const float tz = V[8] * p[0] + V[9] * p[1] + V[10] * p[2] + V[11];
+    const float qn2 = p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9];
+    const float qinv = rsqrtf(qn2);
+    const float qn[4] = {p[6] * qinv, p[7] * qinv, p[8] * qinv, p[9] * qinv};
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                        2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                        2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    const float s[3] = {p[3], p[4], p[5]};
+    float M[9], Q[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) M[a * 3 + b] = R[a * 3 + b] * s[b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Q[a * 3 + b] = V[a * 4 + 0] * M[0 * 3 + b] + V[a * 4 + 1] * M[1 * 3 + b] + V[a * 4 + 2] * M[2 * 3 + b];
+    const float limx = 1.3f * (0.5f * (float)W / cam.fx), limy = 1.3f * (0.5f * (float)H / cam.fy);
+    const float rx = tx / tz, ry = ty / tz;
+    const bool free_x = rx > -limx && rx < limx, free_y = ry > -limy && ry < limy;
+    const float txz = fminf(limx, fmaxf(-limx, rx)), tyz = fminf(limy, fmaxf(-limy, ry));
+    const float j00 = cam.fx / tz, j02 = -cam.fx * txz / tz, j11 = cam.fy / tz, j12 = -cam.fy * tyz / tz;
+    float P0[3], P1[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        P0[b] = j00 * Q[b] + j02 * Q[6 + b];
+        P1[b] = j11 * Q[3 + b] + j12 * Q[6 + b];
+    }
+    const float n0 = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2];
+    const float n1 = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2];
+    const float S01 = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
+    const float c0 = P0[1] * P1[2] - P0[2] * P1[1], c1 = P0[2] * P1[0] - P0[0] * P1[2],
+                c2 = P0[0] * P1[1] - P0[1] * P1[0];
+    const float S00 = n0 + dil, S11 = n1 + dil;
+    const float D = c0 * c0 + c1 * c1 + c2 * c2 + dil * (n0 + n1) + dil * dil;
+    const float l22 = rsqrtf(S11), l11 = sqrtf(S11 / D);
+    const float u = rsqrtf(S11 * D), u3 = u * u * u;
+    // L as a function of (S00, S01, S11), D = S00 S11 - S01^2
+    const float d11_00 = -0.5f * l11 * S11 / D;
+    const float d11_11 = 0.5f * l11 * (1.f / S11 - S00 / D);
+    const float d11_01 = l11 * S01 / D;
+    const float d21_00 = 0.5f * S01 * u3 * S11 * S11;
+    const float d21_11 = 0.5f * S01 * u3 * (D + S11 * S00);
+    const float d21_01 = -u - S01 * S01 * S11 * u3;
+    const float d22_11 = -0.5f * l22 * l22 * l22;
+    const float gS00 = g11 * d11_00 + g21 * d21_00;
+    const float gS11 = g11 * d11_11 + g21 * d21_11 + g22 * d22_11;
+    const float gS01 = g11 * d11_01 + g21 * d21_01;
+    // S00 = |P0|^2 + dil, S11 = |P1|^2 + dil, S01 = P0.P1
+    float gP0[3], gP1[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        gP0[b] = 2.f * gS00 * P0[b] + gS01 * P1[b];
+        gP1[b] = 2.f * gS11 * P1[b] + gS01 * P0[b];
+    }
+    float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f, gQ[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        gj00 += gP0[b] * Q[b];
+        gj02 += gP0[b] * Q[6 + b];
+        gj11 += gP1[b] * Q[3 + b];
+        gj12 += gP1[b] * Q[6 + b];
+        gQ[b] = gP0[b] * j00;
+        gQ[3 + b] = gP1[b] * j11;
+        gQ[6 + b] = gP0[b] * j02 + gP1[b] * j12;
+    }
+    // Q = V M, M = R diag(s)
+    float gR[9], gs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float gM = V[0 * 4 + a] * gQ[0 * 3 + b] + V[1 * 4 + a] * gQ[1 * 3 + b] + V[2 * 4 + a] * gQ[2 * 3 + b];
+            gR[a * 3 + b] = gM * s[b];
+            gs[b] += gM * R[a * 3 + b];
+        }
+    float gqn[4];
+    quat_rot_grad(qn, gR, gqn);
+    const float dot = gqn[0] * qn[0] + gqn[1] * qn[1] + gqn[2] * qn[2] + gqn[3] * qn[3];
+    // camera-frame centre
+    const float fcx = V[0] * p[10] + V[1] * p[11] + V[2] * p[12];
+    const float fcy = V[4] * p[10] + V[5] * p[11] + V[6] * p[12];
+    const float iz = 1.f / tz, iz2 = iz * iz;
+    float gtx = g_mx * cam.fx * iz;
+    float gty = g_my * cam.fy * iz;
+    float gtz = -g_mx * cam.fx * tx * iz2 - g_my * cam.fy * ty * iz2 + g_fx * fcx / cam.fx + g_fy * fcy / cam.fy;
+    gtz += -gj00 * cam.fx * iz2 - gj11 * cam.fy * iz2 + gj02 * cam.fx * txz * iz2 + gj12 * cam.fy * tyz * iz2;
+    if (free_x) {
+        gtx += -gj02 * cam.fx * iz2;
+        gtz += gj02 * cam.fx * tx * iz2 * iz;
+    }
+    if (free_y) {
+        gty += -gj12 * cam.fy * iz2;
+        gtz += gj12 * cam.fy * ty * iz2 * iz;
+    }
+    const float gfc0 = g_fx * tz / cam.fx, gfc1 = g_fy * tz / cam.fy;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out[a] = V[0 * 4 + a] * gtx + V[1 * 4 + a] * gty + V[2 * 4 + a] * gtz;
+        out[3 + a] = gs[a];
+        out[10 + a] = V[0 * 4 + a] * gfc0 + V[1 * 4 + a] * gfc1;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out[6 + m] = (gqn[m] - qn[m] * dot) * qinv;
+    out[13] = g[7] * kInvTwoPi;
+    out[14] = g[11];
+    out[15] = g[8];
+    out[16] = g[9];
+    out[17] = g[10];
+    out[18] = 0.f;
+    out[19] = 0.f;
+}
+
+}  // namespace
+
+void launch_blend3d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H, int tiles_x,
+                    int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last, cudaStream_t stream) {
+    k_blend3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, sorted_prims, ranges, W, H, tiles_x, o, out, T_final,
+                                                              last); count_launches(1);
+}
+
+void launch_backward3d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
+                       int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
+                       const float* dl_dout, float* grad_img, cudaStream_t stream) {
+    k_backward3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, sorted_prims, ranges, W, H, tiles_x, o, T_final,
+                                                                 last, dl_dout, grad_img); count_launches(1);
+}
+
+void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
+                    const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream) {
+    if (N == 0) return;
+    Cam3 c;
+    for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
+    c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
+    k_chain3d<<<ceil_div(N, 128), 128, 0, stream>>>(params, N, c, W, H, dilation, rec, grad_img, dl_dparams); count_launches(1);
+}
+
+}  // namespace wipes

@@ -1,0 +1,44 @@
+"""Shared helpers of the device parity tests (inputs from ``synth``, expectations from ``oracle``)."""
+import numpy as np
+import pytest
+
+FWD_ATOL = 1e-4   # forward image: max abs error per channel (fp32 kernels vs binary64 oracle)
+GRAD_RTOL = 1e-3  # gradients: |g - g*| <= 1e-3 max(|g*|, 1e-3 max_col |g*|)
+
+
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def lib_ready():
+    from paper_2508_12615_gb300 import build
+
+    build.build()
+    import paper_2508_12615_gb300 as w
+
+    return w
+
+
+def grad_close(g, ref, rtol=GRAD_RTOL, floor_frac=1e-3, cols=None):
+    """Column-floored relative check; returns (ok, worst ratio, index)."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if cols is not None:
+        g, ref = g[:, cols], ref[:, cols]
+    floor = floor_frac * np.abs(ref).max(axis=0, keepdims=True)
+    tol = rtol * np.maximum(np.abs(ref), floor)
+    ratio = np.abs(g - ref) / np.maximum(tol, 1e-30)
+    idx = np.unravel_index(np.argmax(ratio), ratio.shape)
+    return bool(np.all(ratio <= 1.0)), float(ratio.max()), idx
+
+
+def sample_pixels(H, W, n, seed):
+    rng = np.random.default_rng(seed)
+    u = rng.integers(0, W, n)
+    v = rng.integers(0, H, n)
+    # always include the image corners and the last ragged tile
+    extra = np.array([[0, 0], [W - 1, 0], [0, H - 1], [W - 1, H - 1]])
+    return np.concatenate([np.stack([u, v], 1), extra]).astype(np.int32)

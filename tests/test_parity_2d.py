@@ -1,0 +1,167 @@
+"""Device parity of the 2D path (summed wavelet field, Eq. 4 with the wavelet of Eq. 5) against the
+binary64 oracle: tile lists bit-exact, forward within 1e-4, gradients within 1e-3 relative."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import FWD_ATOL, grad_close, lib_ready, sample_pixels, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_forward(w, torch, p, H, W):
+    params = torch.from_numpy(p).cuda()
+    st = w.Context.get(0).acquire_state()
+    img = w.forward2d(params, H, W, state=st)
+    torch.cuda.synchronize()
+    return params, st, img
+
+
+CASES = [
+    # (N, H, W, scale range, seed): several tiles and ragged right/bottom edges
+    (300, 70, 100, (1.0, 16.0), 1),
+    (2000, 256, 256, (1.0, 16.0), 1234),  # the 256x256 workload
+    (500, 37, 129, (0.5, 32.0), 3),
+    (64, 16, 16, (0.5, 8.0), 4),           # a single tile
+    (200, 1, 300, (0.5, 4.0), 5),          # one row
+    (200, 300, 1, (0.5, 4.0), 6),          # one column
+]
+
+
+@pytest.mark.parametrize("N,H,W,scale,seed", CASES)
+def test_tile_lists_bit_exact(N, H, W, scale, seed):
+    torch = torch_cuda()
+    w = lib_ready()
+    p = synth.scene2d(N, H, W, seed, scale)
+    _, st, _ = _gpu_forward(w, torch, p, H, W)
+    tiles, prims, ranges = st.lists()
+    ot, op = oracle.tile_lists(2, p, H, W)
+    assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+    assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+    r = ranges.cpu().numpy()
+    tx = (W + 15) // 16
+    for t in range(r.shape[0]):
+        sel = np.nonzero(ot == t)[0]
+        if len(sel):
+            assert (r[t, 0], r[t, 1]) == (sel[0], sel[-1] + 1)
+        else:
+            assert r[t, 0] == r[t, 1]
+    assert tx * ((H + 15) // 16) == r.shape[0]
+
+
+@pytest.mark.parametrize("N,H,W,scale,seed", CASES)
+def test_forward_matches_oracle(N, H, W, scale, seed):
+    torch = torch_cuda()
+    w = lib_ready()
+    p = synth.scene2d(N, H, W, seed, scale)
+    _, _, img = _gpu_forward(w, torch, p, H, W)
+    ref = oracle.render2d(p, H, W, truncated=True)
+    err = np.abs(img.cpu().numpy().astype(np.float64) - ref)
+    assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("N,H,W,scale,seed", CASES)
+def test_backward_matches_oracle(N, H, W, scale, seed):
+    torch = torch_cuda()
+    w = lib_ready()
+    p = synth.scene2d(N, H, W, seed, scale)
+    g = synth.upstream_grad(H, W, seed + 77)
+    params, st, _ = _gpu_forward(w, torch, p, H, W)
+    grad = w.backward(st, params, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref = oracle.grad2d(p, H, W, g, truncated=True)
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, cols=list(range(11)))
+    assert ok, (worst, idx)
+    assert np.all(grad.cpu().numpy()[:, 11:] == 0)
+
+
+def test_autograd_function_matches_direct_calls():
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 48, 80
+    p = synth.scene2d(150, H, W, 9)
+    target = torch.from_numpy(synth.target_gabor(H, W, 10)).cuda()
+    params = torch.from_numpy(p).cuda().requires_grad_(True)
+    img = w.render2d(params, H, W)
+    loss = ((img - target) ** 2).mean()
+    loss.backward()
+    # the same through the ABI calls, with the library's own loss kernel
+    st = w.Context.get(0).acquire_state()
+    img2 = w.forward2d(params.detach(), H, W, state=st)
+    l2, gimg = w.l2_loss(img2, target)
+    g2 = w.backward(st, params.detach(), gimg)
+    torch.cuda.synchronize()
+    assert torch.equal(img.detach(), img2)
+    assert abs(float(l2) - float(loss)) <= 1e-6 * abs(float(loss))
+    np.testing.assert_allclose(params.grad.cpu().numpy(), g2.cpu().numpy(), rtol=1e-5, atol=1e-7)
+
+
+def test_deterministic():
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 96, 112
+    p = synth.scene2d(800, H, W, 11, (0.5, 32.0))
+    g = torch.from_numpy(synth.upstream_grad(H, W, 12)).cuda()
+    outs = []
+    for _ in range(2):
+        params, st, img = _gpu_forward(w, torch, p, H, W)
+        outs.append((img.clone(), w.backward(st, params, g).clone()))
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+def test_edge_cases():
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 40, 50
+    # no primitives: zero image and an empty gradient
+    params = torch.zeros(0, 16, device="cuda")
+    st = w.Context.get(0).acquire_state()
+    img = w.forward2d(params, H, W, state=st)
+    g = w.backward(st, params, torch.ones(H, W, 3, device="cuda"))
+    torch.cuda.synchronize()
+    assert img.abs().max().item() == 0 and g.shape == (0, 16)
+    # off-screen, degenerate (zero or negative scale, NaN) and screen-filling primitives
+    p = synth.scene2d(12, H, W, 13)
+    p[0, :2] = [-500.0, 20.0]
+    p[1, :2] = [25.0, 1e6]
+    p[2, 2] = 0.0
+    p[3, 3] = -1.0
+    p[4, 0] = np.nan
+    p[5, 2:4] = [400.0, 300.0]
+    p[6, 2:4] = [0.05, 40.0]  # very elongated
+    params, st, img = _gpu_forward(w, torch, p, H, W)
+    ref = oracle.render2d(p, H, W, truncated=True)
+    assert np.abs(img.cpu().numpy() - ref).max() <= FWD_ATOL
+    gd = synth.upstream_grad(H, W, 14)
+    grad = w.backward(st, params, torch.from_numpy(gd).cuda()).cpu().numpy()
+    assert np.all(grad[[0, 1, 2, 3, 4]] == 0)
+    ok, worst, idx = grad_close(grad, oracle.grad2d(p, H, W, gd), cols=list(range(11)))
+    assert ok, (worst, idx)
+
+
+def test_full_size_768x512_70k_sampled():
+    """The 768x512, 70,000-primitive image-fitting workload, in the launch configuration the
+    benchmark times: lists bit-exact, sampled pixels and sampled primitive gradients vs the oracle."""
+    torch = torch_cuda()
+    w = lib_ready()
+    p, target = synth.cfg1_inputs()
+    c = synth.CFG1_2D_KODAK
+    H, W = c.H, c.W
+    params, st, img = _gpu_forward(w, torch, p, H, W)
+    tiles, prims, _ = st.lists()
+    ot, op = oracle.tile_lists(2, p, H, W)
+    assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+    assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+    pix = sample_pixels(H, W, 1500, 21)
+    ref = oracle.render2d(p, H, W, pixels=pix)
+    got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    assert np.abs(got - ref).max() <= FWD_ATOL
+    # gradients of a primitive depend only on that primitive and dL/dimage in the summed field
+    g = synth.upstream_grad(H, W, 22, scale=1e-3)
+    grad = w.backward(st, params, torch.from_numpy(g).cuda()).cpu().numpy()
+    sel = np.random.default_rng(23).choice(p.shape[0], 300, replace=False)
+    ref_g = oracle.grad2d(p[sel], H, W, g)
+    ok, worst, idx = grad_close(grad[sel], ref_g, cols=list(range(11)))
+    assert ok, (worst, idx)

@@ -1,0 +1,187 @@
+"""Device parity of the 3D path (EWA projection, frequency projection, front-to-back blending of the
+projected wavelets) and of the 6D time model against the binary64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import FWD_ATOL, grad_close, lib_ready, sample_pixels, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+DEFAULT = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0], np.float32)
+STRICT = np.array([3.0, 0.0, 0.99, 0.0, 0.3, 0.1, 0.2, 0.3], np.float32)  # no alpha floor, no T floor
+
+
+def _opts(w, o):
+    return w.make_opts(3, cutoff_sigma=float(o[0]), alpha_min=float(o[1]), alpha_max=float(o[2]), T_min=float(o[3]),
+                       dilation=float(o[4]), bg=o[5:8])
+
+
+def _gpu(w, torch, p, cam, H, W, o):
+    params = torch.from_numpy(p).cuda()
+    st = w.Context.get(0).acquire_state()
+    img = w.forward3d(params, cam, H, W, _opts(w, o), state=st)
+    torch.cuda.synchronize()
+    return params, st, img
+
+
+CASES = [
+    # (N, H, W, seed, scene kwargs)
+    (400, 72, 88, 31, {}),
+    (1500, 100, 100, 32, {}),
+    (3000, 53, 131, 33, {"scale_range": (0.004, 0.08)}),
+    (300, 16, 16, 34, {}),
+]
+
+
+@pytest.mark.parametrize("N,H,W,seed,kw", CASES)
+def test_tile_lists_bit_exact(N, H, W, seed, kw):
+    torch = torch_cuda()
+    w = lib_ready()
+    p = synth.scene3d(N, seed, **kw)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    _, st, _ = _gpu(w, torch, p, cam, H, W, DEFAULT)
+    tiles, prims, _ = st.lists()
+    ot, op = oracle.tile_lists(3, p, H, W, cam)
+    assert len(ot) > 0
+    assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+    assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+
+
+@pytest.mark.parametrize("N,H,W,seed,kw", CASES)
+@pytest.mark.parametrize("mode", ["default", "strict"])
+def test_forward_matches_oracle(N, H, W, seed, kw, mode):
+    torch = torch_cuda()
+    w = lib_ready()
+    o = DEFAULT if mode == "default" else STRICT
+    p = synth.scene3d(N, seed, **kw)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    _, st, img = _gpu(w, torch, p, cam, H, W, o)
+    C, T, nc, amb = oracle.render3d(p, cam, H, W, o)
+    if mode == "strict":
+        assert not amb.any()
+    assert amb.mean() < 1e-3
+    err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
+    err[amb] = 0
+    assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    Tg, last = st.pixel_state()
+    terr = np.abs(Tg.cpu().numpy() - T)
+    terr[amb] = 0
+    assert terr.max() <= 1e-5
+
+
+@pytest.mark.parametrize("N,H,W,seed,kw", CASES)
+@pytest.mark.parametrize("mode", ["default", "strict"])
+def test_backward_matches_oracle(N, H, W, seed, kw, mode):
+    torch = torch_cuda()
+    w = lib_ready()
+    o = DEFAULT if mode == "default" else STRICT
+    p = synth.scene3d(N, seed, **kw)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    params, st, _ = _gpu(w, torch, p, cam, H, W, o)
+    _, _, _, amb = oracle.render3d(p, cam, H, W, o)
+    g = synth.upstream_grad(H, W, seed + 5)
+    g[amb] = 0.0  # threshold decisions that floating point may take either way carry no gradient
+    grad = w.backward(st, params, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref = oracle.grad3d(p, cam, H, W, g, o)
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, cols=list(range(18)))
+    assert ok, (worst, idx)
+
+
+def test_autograd_function_and_culling():
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 64, 64
+    p = synth.scene3d(500, 41)
+    cam = synth.sphere_cameras(1, H, W, 42)[0]
+    # a primitive behind the camera and one at the near plane are culled: zero gradient
+    eye = -np.linalg.inv(cam[:12].reshape(3, 4)[:, :3].astype(np.float64)) @ cam[:12].reshape(3, 4)[:, 3]
+    fwd = cam[:12].reshape(3, 4)[2, :3]
+    p[0, :3] = eye - 1.0 * fwd
+    p[1, :3] = eye + 0.1 * fwd
+    params = torch.from_numpy(p).cuda().requires_grad_(True)
+    img = w.render3d(params, cam, H, W)
+    (img * torch.from_numpy(synth.upstream_grad(H, W, 43)).cuda()).sum().backward()
+    g = params.grad.cpu().numpy()
+    assert np.all(g[:2] == 0)
+    ref = oracle.grad3d(p, cam, H, W, synth.upstream_grad(H, W, 43))
+    C, T, nc, amb = oracle.render3d(p, cam, H, W)
+    assert amb.mean() < 1e-3
+    if not amb.any():
+        ok, worst, idx = grad_close(g, ref, cols=list(range(18)))
+        assert ok, (worst, idx)
+
+
+def test_empty_and_all_culled():
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 33, 47
+    cam = synth.sphere_cameras(1, H, W, 51)[0]
+    o = STRICT
+    params = torch.zeros(0, 20, device="cuda")
+    st = w.Context.get(0).acquire_state()
+    img = w.forward3d(params, cam, H, W, _opts(w, o), state=st)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(img.cpu().numpy(), np.broadcast_to(o[5:8], (H, W, 3)), rtol=0, atol=0)
+    p = synth.scene3d(50, 52)
+    p[:, :3] += 100.0  # everything far behind or outside
+    params, st, img = _gpu(w, torch, p, cam, H, W, o)
+    C, T, nc, amb = oracle.render3d(p, cam, H, W, o)
+    assert np.abs(img.cpu().numpy() - C).max() <= FWD_ATOL
+
+
+def test_full_size_800x800_300k_sampled():
+    """The 300,000-primitive, 800x800 static-scene workload: bit-exact lists and sampled pixels."""
+    torch = torch_cuda()
+    w = lib_ready()
+    p, cams = synth.cfg2_inputs(n_cams=2)
+    c = synth.CFG2_5D
+    for cam in cams:
+        params, st, img = _gpu(w, torch, p, cam, c.H, c.W, DEFAULT)
+        tiles, prims, _ = st.lists()
+        ot, op = oracle.tile_lists(3, p, c.H, c.W, cam)
+        assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+        assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+        pix = sample_pixels(c.H, c.W, 400, 61)
+        C, T, nc, amb = oracle.render3d(p, cam, c.H, c.W, DEFAULT, pixels=pix)
+        got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
+        err = np.abs(got - C).max(axis=1)
+        err[amb] = 0
+        assert err.max() <= FWD_ATOL
+
+
+def test_deform6d_matches_oracle():
+    torch = torch_cuda()
+    w = lib_ready()
+    p6 = synth.scene6d(5000, 71)
+    for t in [0.0, 0.37, 1.0]:
+        d = w.deform6d(torch.from_numpy(p6).cuda(), t).cpu().numpy()
+        ref = oracle.deform6d(p6, t)
+        np.testing.assert_array_equal(d[:, [0, 1, 2, 10, 11, 12, 13]],
+                                      ref[:, [0, 1, 2, 10, 11, 12, 13]].astype(np.float32))
+        np.testing.assert_allclose(d, ref, rtol=3e-7, atol=1e-12)
+
+
+def test_6d_render_and_gradient_chain():
+    """A (view, time) sample of the dynamic task: deform, render, backward, chain to the rates."""
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 60, 80
+    p6 = synth.scene6d(600, 72)
+    cam = synth.sphere_cameras(1, H, W, 73)[0]
+    t = 0.61
+    params6 = torch.from_numpy(p6).cuda().requires_grad_(True)
+    img = w.render3d(w.deform6d(params6, t), cam, H, W)
+    p3 = oracle.deform6d(p6, t).astype(np.float32)
+    C, T, nc, amb = oracle.render3d(p3, cam, H, W)
+    err = np.abs(img.detach().cpu().numpy() - C).max(axis=2)
+    err[amb] = 0
+    assert err.max() <= FWD_ATOL
+    g = synth.upstream_grad(H, W, 74)
+    g[amb] = 0
+    (img * torch.from_numpy(g).cuda()).sum().backward()
+    ref = oracle.deform6d_grad(p6, t, oracle.grad3d(p3, cam, H, W, g))
+    ok, worst, idx = grad_close(params6.grad.cpu().numpy(), ref, cols=list(range(30)))
+    assert ok, (worst, idx)
