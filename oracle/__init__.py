@@ -118,8 +118,13 @@ def grad2d(params, H, W, dldimg, cutoff=3.0, truncated=True):
     return out
 
 
+AMB_ALPHA_MIN, AMB_T_MIN, AMB_ALPHA_MAX = 1, 2, 4
+
+
 def render3d(params, cam, H, W, opts=None, truncated=True, pixels=None):
-    """Front-to-back blend.  Returns (C, T_final, n_contrib, ambiguous)."""
+    """Front-to-back blend.  Returns (C, T_final, n_contrib, ambiguous) where ambiguous holds the
+    AMB_* bits of threshold decisions taken within the kernels' error margin: bits 0-1 (alpha_min
+    skip, T_min stop) can change the image, bit 2 (alpha_max clamp) only the gradient."""
     params = _f32(params)
     camv = _f32(cam)
     o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
@@ -132,8 +137,8 @@ def render3d(params, cam, H, W, opts=None, truncated=True, pixels=None):
     _load().wo_render3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(pix), npix,
                         _ptr(out), _ptr(T), _ptr(nc), _ptr(amb))
     if pix is None:
-        return out.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), amb.reshape(H, W).astype(bool)
-    return out, T, nc, amb.astype(bool)
+        return out.reshape(H, W, 3), T.reshape(H, W), nc.reshape(H, W), amb.reshape(H, W)
+    return out, T, nc, amb
 
 
 def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True):

@@ -563,16 +563,22 @@ static void scene3_build(const float* params, int64_t N, const float* cam, int H
 
 static void scene3_free(scene3* s) { free(s->k); free(s->w); free(s->order); }
 
+/* Ambiguity margins.  The kernels evaluate alpha in binary32 with approximate exp and cos; over the
+ * workloads here its absolute error stays below AMB_ALPHA.  A transmittance that has passed through
+ * layers of opacity a_i then carries a relative error of at most sum_i AMB_ALPHA / (1 - a_i) plus
+ * one rounding per product. */
 #define AMB_ALPHA 2e-6
-#define AMB_T_REL 2e-4
+#define AMB_ALPHA_MIN 1 /* bit 0: the alpha_min skip could go either way */
+#define AMB_T_MIN 2     /* bit 1: the T_min stop could go either way */
+#define AMB_ALPHA_MAX 4 /* bit 2: the alpha_max clamp could go either way (a kink, not a jump) */
 
 typedef struct { uint32_t prim; double alpha, T, Wv; int clamped; wval e; } contrib;
 
 /* Blend one pixel front to back.  Writes the contributors (when list != NULL), returns their count.
- * *amb is set when a threshold decision is within its ambiguity margin. */
+ * *amb collects the AMB_* bits of the threshold decisions taken within their error margins. */
 static int64_t blend_pixel(const scene3* s, int u, int v, const blend_opts* o, int truncated, double C[3],
                            double* Tout, int* amb, contrib* list) {
-    double T = 1.0;
+    double T = 1.0, Trel = 0.0;
     float k2 = o->cutoff * o->cutoff;
     int64_t n = 0;
     C[0] = C[1] = C[2] = 0.0;
@@ -583,12 +589,14 @@ static int64_t blend_pixel(const scene3* s, int u, int v, const blend_opts* o, i
         wval e;
         eval_wavelet(&s->w[i], u, v, &e);
         double raw = s->w[i].o * e.W;
-        if (fabs(raw - (double)o->amin) < AMB_ALPHA || fabs(raw - (double)o->amax) < AMB_ALPHA) *amb = 1;
+        if (o->amin > 0.0f && fabs(raw - (double)o->amin) < AMB_ALPHA) *amb |= AMB_ALPHA_MIN;
+        if (fabs(raw - (double)o->amax) < AMB_ALPHA) *amb |= AMB_ALPHA_MAX;
         int clamped = raw > (double)o->amax;
         double alpha = clamped ? (double)o->amax : raw;
         if (alpha < (double)o->amin) continue;
         double testT = T * (1.0 - alpha);
-        if (o->Tmin > 0.0f && fabs(testT - (double)o->Tmin) < AMB_T_REL * (double)o->Tmin) *amb = 1;
+        double rel = Trel + AMB_ALPHA / (1.0 - alpha) + 1.2e-7;
+        if (o->Tmin > 0.0f && fabs(testT - (double)o->Tmin) <= 2.0 * rel * testT) *amb |= AMB_T_MIN;
         if (testT < (double)o->Tmin) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += s->w[i].c[ch] * alpha * T;
         if (list) {
@@ -597,13 +605,14 @@ static int64_t blend_pixel(const scene3* s, int u, int v, const blend_opts* o, i
         }
         ++n;
         T = testT;
+        Trel = rel;
     }
     for (int ch = 0; ch < 3; ++ch) C[ch] += T * o->bg[ch];
     *Tout = T;
     return n;
 }
 
-/* out[npix,3], Tout[npix], ncontrib[npix], ambiguous[npix] (any may be NULL except out) */
+/* out[npix,3], Tout[npix], ncontrib[npix], ambiguous[npix] = AMB_* bits (any may be NULL except out) */
 int wo_render3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, int truncated,
                 const int32_t* pix, int64_t npix, double* out, double* Tout, int32_t* ncontrib, uint8_t* ambiguous) {
     blend_opts o = read_opts(opts);

@@ -11,6 +11,9 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0], np.float32)
 STRICT = np.array([3.0, 0.0, 0.99, 0.0, 0.3, 0.1, 0.2, 0.3], np.float32)  # no alpha floor, no T floor
+# Largest share of pixels whose threshold decisions lie within the kernels' error margin (excluded
+# from the comparison and reported); binary32 phase rounding puts alpha errors near 1e-6.
+AMB_SHARE = 1e-2
 
 
 def _opts(w, o):
@@ -58,10 +61,11 @@ def test_forward_matches_oracle(N, H, W, seed, kw, mode):
     p = synth.scene3d(N, seed, **kw)
     cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
     _, st, img = _gpu(w, torch, p, cam, H, W, o)
-    C, T, nc, amb = oracle.render3d(p, cam, H, W, o)
+    C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, o)
+    amb = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
     if mode == "strict":
         assert not amb.any()
-    assert amb.mean() < 1e-3
+    assert amb.mean() < AMB_SHARE
     err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
     err[amb] = 0
     assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
@@ -80,7 +84,9 @@ def test_backward_matches_oracle(N, H, W, seed, kw, mode):
     p = synth.scene3d(N, seed, **kw)
     cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
     params, st, _ = _gpu(w, torch, p, cam, H, W, o)
-    _, _, _, amb = oracle.render3d(p, cam, H, W, o)
+    _, _, _, amb_bits = oracle.render3d(p, cam, H, W, o)
+    amb = amb_bits != 0
+    assert amb.mean() < AMB_SHARE
     g = synth.upstream_grad(H, W, seed + 5)
     g[amb] = 0.0  # threshold decisions that floating point may take either way carry no gradient
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
@@ -108,7 +114,7 @@ def test_autograd_function_and_culling():
     assert np.all(g[:2] == 0)
     ref = oracle.grad3d(p, cam, H, W, synth.upstream_grad(H, W, 43))
     C, T, nc, amb = oracle.render3d(p, cam, H, W)
-    assert amb.mean() < 1e-3
+    assert (amb != 0).mean() < AMB_SHARE
     if not amb.any():
         ok, worst, idx = grad_close(g, ref, cols=list(range(18)))
         assert ok, (worst, idx)
@@ -148,7 +154,7 @@ def test_full_size_800x800_300k_sampled():
         C, T, nc, amb = oracle.render3d(p, cam, c.H, c.W, DEFAULT, pixels=pix)
         got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
         err = np.abs(got - C).max(axis=1)
-        err[amb] = 0
+        err[(amb & 3) != 0] = 0
         assert err.max() <= FWD_ATOL
 
 
@@ -177,10 +183,10 @@ def test_6d_render_and_gradient_chain():
     p3 = oracle.deform6d(p6, t).astype(np.float32)
     C, T, nc, amb = oracle.render3d(p3, cam, H, W)
     err = np.abs(img.detach().cpu().numpy() - C).max(axis=2)
-    err[amb] = 0
+    err[(amb & 3) != 0] = 0
     assert err.max() <= FWD_ATOL
     g = synth.upstream_grad(H, W, 74)
-    g[amb] = 0
+    g[amb != 0] = 0
     (img * torch.from_numpy(g).cuda()).sum().backward()
     ref = oracle.deform6d_grad(p6, t, oracle.grad3d(p3, cam, H, W, g))
     ok, worst, idx = grad_close(params6.grad.cpu().numpy(), ref, cols=list(range(30)))
