@@ -49,9 +49,9 @@ def _load():
         lib.wo_tile_lists.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P, P, i64]
         lib.wo_tile_lists.restype = i64
         lib.wo_render2d.argtypes = [P, i64, i32, i32, f32, i32, P, i64, P]
-        lib.wo_grad2d.argtypes = [P, i64, i32, i32, f32, i32, P, P]
+        lib.wo_grad2d.argtypes = [P, i64, i32, i32, f32, i32, P, P, P]
         lib.wo_render3d.argtypes = [P, i64, P, i32, i32, P, i32, P, i64, P, P, P, P]
-        lib.wo_grad3d.argtypes = [P, i64, P, i32, i32, P, i32, P, P]
+        lib.wo_grad3d.argtypes = [P, i64, P, i32, i32, P, i32, P, P, P]
         lib.wo_project3d.argtypes = [P, i64, P, i32, i32, P, P]
         lib.wo_deform6d.argtypes = [P, i64, f64, P]
         lib.wo_deform6d_grad.argtypes = [P, i64, f64, P, P]
@@ -109,13 +109,15 @@ def render2d(params, H, W, cutoff=3.0, truncated=True, pixels=None):
     return out if pix is not None else out.reshape(H, W, 3)
 
 
-def grad2d(params, H, W, dldimg, cutoff=3.0, truncated=True):
-    """dL/dparams [N,16] for L = sum(dldimg * C)."""
+def grad2d(params, H, W, dldimg, cutoff=3.0, truncated=True, with_abs=False):
+    """dL/dparams [N,16] for L = sum(dldimg * C).  with_abs=True also returns, per parameter, the
+    sum over pixels of |that pixel's contribution| (the scale of a summed gradient's rounding)."""
     params = _f32(params)
     g = _f32(dldimg)
     out = np.zeros((params.shape[0], 16), np.float64)
-    _load().wo_grad2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(g), _ptr(out))
-    return out
+    gabs = np.zeros((params.shape[0], 16), np.float64) if with_abs else None
+    _load().wo_grad2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(g), _ptr(out), _ptr(gabs))
+    return (out, gabs) if with_abs else out
 
 
 AMB_ALPHA_MIN, AMB_T_MIN, AMB_ALPHA_MAX = 1, 2, 4
@@ -141,15 +143,17 @@ def render3d(params, cam, H, W, opts=None, truncated=True, pixels=None):
     return out, T, nc, amb
 
 
-def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True):
-    """dL/dparams [N,20] for L = sum(dldimg * C)."""
+def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True, with_abs=False):
+    """dL/dparams [N,20] for L = sum(dldimg * C) (with_abs as in grad2d)."""
     params = _f32(params)
     camv = _f32(cam)
     o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
     g = _f32(dldimg)
     out = np.zeros((params.shape[0], 20), np.float64)
-    _load().wo_grad3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(g), _ptr(out))
-    return out
+    gabs = np.zeros((params.shape[0], 20), np.float64) if with_abs else None
+    _load().wo_grad3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(g), _ptr(out),
+                      _ptr(gabs))
+    return (out, gabs) if with_abs else out
 
 
 def project3d(params, cam, H, W, opts=None):

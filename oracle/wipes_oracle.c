@@ -480,9 +480,11 @@ static void chain2d(const float* p, const pgrad* g, double* out) {
     out[8] = g->c[0]; out[9] = g->c[1]; out[10] = g->c[2];
 }
 
-/* grad[N,16] of L = sum_pixels dldimg . C */
+/* grad[N,16] of L = sum_pixels dldimg . C.  When gabs is not NULL it receives, per parameter, the
+ * sum over pixels of the absolute value of that pixel's contribution to the gradient: the scale
+ * against which the rounding error of a summed gradient is measured. */
 int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int truncated, const float* dldimg,
-              double* grad) {
+              double* grad, double* gabs) {
     fp32_footprint* k = all_footprints(2, params, N, NULL, H, W, cutoff, 0.0f);
     proj* w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
     for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, &w[i]);
@@ -502,15 +504,31 @@ int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int tr
                 wval e;
                 eval_wavelet(&w[i], u, v, &e);
                 double gW = 0.0;
+                pgrad one;
+                memset(&one, 0, sizeof(one));
                 for (int ch = 0; ch < 3; ++ch) {
-                    g.c[ch] += gp[ch] * e.W;
+                    one.c[ch] = gp[ch] * e.W;
                     gW += gp[ch] * w[i].c[ch];
                 }
-                accum_wavelet_grad(&w[i], &e, gW, &g);
+                accum_wavelet_grad(&w[i], &e, gW, &one);
+                for (int m = 0; m < 2; ++m) { g.mu[m] += one.mu[m]; g.f[m] += one.f[m]; }
+                for (int m = 0; m < 4; ++m) g.K[m] += one.K[m];
+                for (int m = 0; m < 3; ++m) g.c[m] += one.c[m];
+                g.phi += one.phi;
+                if (gabs) {
+                    double t[16];
+                    chain2d(params + i * 16, &one, t);
+                    for (int m = 0; m < 16; ++m) gabs[i * 16 + m] += fabs(t[m]);
+                }
             }
         acc[i] = g;
     }
-    for (int64_t i = 0; i < N; ++i) chain2d(params + i * 16, &acc[i], grad + i * 16);
+    for (int64_t i = 0; i < N; ++i) {
+        /* a degenerate primitive (non-positive scale, or dropped by the cutoff rule) contributes
+           nothing to the image, so its gradient is zero */
+        if (!w[i].valid || (truncated && !k[i].valid)) memset(grad + i * 16, 0, sizeof(double) * 16);
+        else chain2d(params + i * 16, &acc[i], grad + i * 16);
+    }
     free(acc);
     free(w);
     free(k);
@@ -727,9 +745,18 @@ static void chain3d(const proj* w, const float* cam, const pgrad* g, double* out
     out[15] = g->c[0]; out[16] = g->c[1]; out[17] = g->c[2];
 }
 
-/* grad[N,20] of L = sum_pixels dldimg . C.  Pixels with a zero upstream gradient are skipped. */
+static void pgrad_add(pgrad* g, const pgrad* a) {
+    for (int m = 0; m < 2; ++m) { g->mu[m] += a->mu[m]; g->f[m] += a->f[m]; }
+    for (int m = 0; m < 4; ++m) g->K[m] += a->K[m];
+    for (int m = 0; m < 3; ++m) g->c[m] += a->c[m];
+    g->phi += a->phi;
+    g->o += a->o;
+}
+
+/* grad[N,20] of L = sum_pixels dldimg . C.  Pixels with a zero upstream gradient are skipped.
+ * gabs (optional) as in wo_grad2d. */
 int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, int truncated,
-              const float* dldimg, double* grad) {
+              const float* dldimg, double* grad, double* gabs) {
     blend_opts o = read_opts(opts);
     scene3 s;
     scene3_build(params, N, cam, H, W, &o, &s);
@@ -739,6 +766,7 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
     nthreads = omp_get_max_threads();
 #endif
     pgrad* acc = (pgrad*)calloc((size_t)nthreads * (size_t)(N > 0 ? N : 1), sizeof(pgrad));
+    double* abs_acc = gabs ? (double*)calloc((size_t)nthreads * (size_t)(N > 0 ? N : 1) * 20, sizeof(double)) : NULL;
 #pragma omp parallel
     {
         int tid = 0;
@@ -761,16 +789,24 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
             for (int64_t m = n - 1; m >= 0; --m) {
                 contrib* cb = &list[m];
                 proj* w = &s.w[cb->prim];
-                pgrad* g = &my[cb->prim];
+                pgrad one;
+                memset(&one, 0, sizeof(one));
                 double galpha = 0.0;
                 for (int ch = 0; ch < 3; ++ch) {
-                    g->c[ch] += gp[ch] * cb->alpha * cb->T;
+                    one.c[ch] = gp[ch] * cb->alpha * cb->T;
                     galpha += gp[ch] * (w->c[ch] * cb->T - S[ch] / (1.0 - cb->alpha));
                 }
                 for (int ch = 0; ch < 3; ++ch) S[ch] += w->c[ch] * cb->alpha * cb->T;
                 if (!cb->clamped) {
-                    g->o += galpha * cb->Wv;
-                    accum_wavelet_grad(w, &cb->e, galpha * w->o, g);
+                    one.o = galpha * cb->Wv;
+                    accum_wavelet_grad(w, &cb->e, galpha * w->o, &one);
+                }
+                pgrad_add(&my[cb->prim], &one);
+                if (abs_acc) {
+                    double t[20];
+                    chain3d(w, cam, &one, t);
+                    double* a = abs_acc + ((size_t)tid * (size_t)N + cb->prim) * 20;
+                    for (int q = 0; q < 20; ++q) a[q] += fabs(t[q]);
                 }
             }
         }
@@ -789,7 +825,15 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
         }
         if (s.w[i].valid) chain3d(&s.w[i], cam, &g, grad + i * 20);
         else memset(grad + i * 20, 0, sizeof(double) * 20);
+        if (gabs) {
+            for (int q = 0; q < 20; ++q) {
+                double a = 0.0;
+                for (int t = 0; t < nthreads; ++t) a += abs_acc[((size_t)t * (size_t)N + (size_t)i) * 20 + q];
+                gabs[i * 20 + q] = a;
+            }
+        }
     }
+    free(abs_acc);
     free(acc);
     scene3_free(&s);
     return 0;

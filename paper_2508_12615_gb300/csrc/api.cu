@@ -349,8 +349,9 @@ wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params
     WIPES_TRY(bin_and_sort(st, nullptr, s));
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend2d(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), W, H,
-                       st->tiles_x, st->tiles_y, opts->cutoff_sigma * opts->cutoff_sigma, out, s);
+        launch_blend2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->vals[st->sorted].as<uint32_t>(),
+                       st->ranges.as<uint2>(), W, H, st->tiles_x, st->tiles_y, opts->cutoff_sigma * opts->cutoff_sigma,
+                       out, s);
     }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 2;
@@ -396,7 +397,8 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
     WIPES_TRY(bin_and_sort(st, dv[cur], s));
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend3d(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), W, H,
+        launch_blend3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->vals[st->sorted].as<uint32_t>(),
+                       st->ranges.as<uint2>(), W, H,
                        st->tiles_x, st->tiles_y, blend_opts(*opts), out, st->T_final.as<float>(),
                        st->last.as<uint32_t>(), s);
     }
@@ -407,7 +409,7 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
 
 wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float* params, const float* dL_dout,
                                    float* dL_dparams, void* stream) {
-    if (!ctx || !st || !dL_dout || !dL_dparams || (st->N > 0 && !params))
+    if (!ctx || !st || !dL_dout || (st->N > 0 && (!params || !dL_dparams)))
         return fail(WIPES_ERR_INVALID, "null argument");
     if (st->dims != 2 && st->dims != 3) return fail(WIPES_ERR_INVALID, "state holds no forward pass");
     DeviceGuard g(ctx->device);
@@ -430,7 +432,8 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
         {
             StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
             if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * 12 * (size_t)N, s));
-            launch_backward3d(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(),
+            launch_backward3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->vals[st->sorted].as<uint32_t>(),
+                              st->ranges.as<uint2>(),
                               st->W, st->H, st->tiles_x, st->tiles_y, blend_opts(st->opts), st->T_final.as<float>(),
                               st->last.as<uint32_t>(), dL_dout, st->grad_img.as<float>(), s);
         }

@@ -38,6 +38,58 @@ __device__ __forceinline__ float mahalanobis2(float px, float py, float mx, floa
     return __fmaf_rn(a, a, __fmul_rn(b, b));
 }
 
+// Approximate transcendental functions (MUFU): ex2.approx and cos/sin.approx from PTX.
+constexpr float kNegHalfLog2e = -0.7213475204444817f;  // -log2(e) / 2: exp(-q/2) = ex2(q * kNegHalfLog2e)
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// Phase t given in cycles, reduced to an angle in [-pi, pi]: 2 pi (t - rint(t)).
+__device__ __forceinline__ float reduced_angle(float t) { return (t - rintf(t)) * kTwoPi; }
+
+// Sum 16 per-lane values over the warp by recursive halving (reduce-scatter): 15 shuffles
+// instead of 80.  On return lane l holds the warp total of value (l >> 1).
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16, half = 8; off >= 2; off >>= 1, half >>= 1) {
+        const bool hi = lane & off;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = hi ? v[i] : v[half + i];
+            const float keep = hi ? v[half + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Which of the eight 8x4 warp sub-tiles of the 16x16 tile at (x0, y0) a covered pixel range
+// touches: bit w for warp w (columns 8 (w & 1) .. +7, rows 4 (w >> 1) .. +3).
+__device__ __forceinline__ uint32_t subtile_mask(const PixRect& r, int x0, int y0) {
+    uint32_t xo = 0, yo = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) xo |= (uint32_t)(r.u0 <= x0 + 8 * h + 7 && r.u1 >= x0 + 8 * h) << h;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) yo |= (uint32_t)(r.v0 <= y0 + 4 * q + 3 && r.v1 >= y0 + 4 * q) << q;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m |= ((xo >> (w & 1)) & (yo >> (w >> 1)) & 1u) << w;
+    return m;
+}
+
 // Launch helpers ---------------------------------------------------------------------------------
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
@@ -78,8 +130,8 @@ int64_t radix_hist_words(int64_t n);
 int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream);
 
 // raster2d.cu
-void launch_blend2d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
-                    int tiles_x, int tiles_y, float cutoff2, float* out, cudaStream_t stream);
+void launch_blend2d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
+                    int H, int tiles_x, int tiles_y, float cutoff2, float* out, cudaStream_t stream);
 void launch_backward2d(const float4* rec, const PixRect* rect, const uint32_t* offsets, const uint32_t* sorted_prims,
                        const uint2* ranges, int W, int H, int tiles_x, int tiles_y, float cutoff2,
                        const float* dl_dout, float* partial, cudaStream_t stream);
@@ -94,12 +146,12 @@ struct BlendOpts3 {
     float cutoff2, alpha_min, alpha_max, T_min;
     float bg[3];
 };
-void launch_blend3d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
-                    int tiles_x, int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last,
+void launch_blend3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
+                    int H, int tiles_x, int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last,
                     cudaStream_t stream);
-void launch_backward3d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
-                       int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
-                       const float* dl_dout, float* grad_img, cudaStream_t stream);
+void launch_backward3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges,
+                       int W, int H, int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final,
+                       const uint32_t* last, const float* dl_dout, float* grad_img, cudaStream_t stream);
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 

@@ -13,40 +13,25 @@
 namespace wipes {
 namespace {
 
-constexpr float kNegHalfLog2e = -0.7213475204444817f;  // -log2(e) / 2
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float cos_approx(float x) {
-    float y;
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float sin_approx(float x) {
-    float y;
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// phase argument reduced to [-pi, pi]: 2 pi (t - rint(t)) with t in cycles
-__device__ __forceinline__ float reduced_angle(float t) { return (t - rintf(t)) * kTwoPi; }
-
+// Forward.  Warp w of the tile's block owns an 8x4 pixel sub-tile (two columns of sub-tiles by
+// four rows).  When a batch of the tile list is staged, each thread marks which sub-tiles its
+// primitive's covered pixel range touches; a warp then visits only the primitives marked for it.
+// The covered range holds every pixel that passes the cutoff, so skipping is exact.
 __global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restrict__ rec,
+                                                         const PixRect* __restrict__ rect,
                                                          const uint32_t* __restrict__ sorted_prims,
                                                          const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                          float cutoff2, float* __restrict__ out) {
     __shared__ float4 s_a[kTilePixels];  // mx my l11 l21
     __shared__ float4 s_b[kTilePixels];  // l22 fx fy phc
     __shared__ float4 s_c[kTilePixels];  // c_r c_g c_b o
+    __shared__ uint8_t s_mask[kTilePixels];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int u = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int v = ty * kTile + (threadIdx.x / kTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = tx * kTile, y0 = ty * kTile;
+    const int u = x0 + (warp & 1) * 8 + (lane & 7);
+    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
     const uint2 range = ranges[tile];
     float c0 = 0.f, c1 = 0.f, c2 = 0.f;
@@ -58,23 +43,30 @@ __global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restric
             s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
             s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
             s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
+            s_mask[threadIdx.x] = (uint8_t)subtile_mask(rect[id], x0, y0);
         }
         __syncthreads();
         // two-level summation: a batch-local partial sum per channel, added once per batch
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (int j = 0; j < n; ++j) {
-            const float4 A = s_a[j];
-            const float4 B = s_b[j];
-            const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-            if (q <= cutoff2) {
-                const float dx = px - A.x, dy = py - A.y;
-                const float G = ex2_approx(q * kNegHalfLog2e);
-                const float t = fmaf(B.y, dx, fmaf(B.z, dy, B.w));
-                const float w = fmaf(0.5f, cos_approx(reduced_angle(t)), 0.5f) * G;
-                const float4 C = s_c[j];
-                a0 = fmaf(C.x, w, a0);
-                a1 = fmaf(C.y, w, a1);
-                a2 = fmaf(C.z, w, a2);
+        for (int c = 0; c < n; c += 32) {
+            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
+            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
+            while (bal) {
+                const int j = c + __ffs(bal) - 1;
+                bal &= bal - 1u;
+                const float4 A = s_a[j];
+                const float4 B = s_b[j];
+                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
+                if (q <= cutoff2) {
+                    const float dx = px - A.x, dy = py - A.y;
+                    const float G = ex2_approx(q * kNegHalfLog2e);
+                    const float t = fmaf(B.y, dx, fmaf(B.z, dy, B.w));
+                    const float wv = fmaf(0.5f, cos_approx(reduced_angle(t)), 0.5f) * G;
+                    const float4 C = s_c[j];
+                    a0 = fmaf(C.x, wv, a0);
+                    a1 = fmaf(C.y, wv, a1);
+                    a2 = fmaf(C.z, wv, a2);
+                }
             }
         }
         c0 += a0;
@@ -92,6 +84,13 @@ __global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restric
 // Partial gradient slot layout (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b 0
 constexpr int kSlot = 12;
 
+// Backward.  The tile's dL/dimage sits in shared memory; batches of the tile list are staged
+// with each pair's pixel range inside the tile and its emission slot.  One warp takes one pair at
+// a time and walks the pixels of that range.  Per pixel inside the cutoff it accumulates the
+// factored sums  sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy,
+// sum g W  (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
+// b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one warp
+// reduction, since L, f and the centre are constant over the pair.
 __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect,
                                                             const uint32_t* __restrict__ offsets,
@@ -100,91 +99,97 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
                                                             float cutoff2, const float* __restrict__ dl_dout,
                                                             float* __restrict__ partial) {
     __shared__ float s_g[kTilePixels * 3];
+    __shared__ float4 s_a[kTilePixels];
+    __shared__ float4 s_b[kTilePixels];
+    __shared__ float4 s_c[kTilePixels];
+    __shared__ int4 s_reg[kTilePixels];    // ux0, vy0, width, area (pixels of the pair inside the tile)
+    __shared__ uint32_t s_slot[kTilePixels];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int x0 = tx * kTile, y0 = ty * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
-        const int u = tx * kTile + (threadIdx.x & (kTile - 1));
-        const int v = ty * kTile + (threadIdx.x / kTile);
+        const int u = x0 + (threadIdx.x & (kTile - 1));
+        const int v = y0 + (threadIdx.x / kTile);
         const bool in = u < W && v < H;
         const float* g = dl_dout + ((size_t)v * W + u) * 3;
         s_g[threadIdx.x * 3 + 0] = in ? g[0] : 0.f;
         s_g[threadIdx.x * 3 + 1] = in ? g[1] : 0.f;
         s_g[threadIdx.x * 3 + 2] = in ? g[2] : 0.f;
     }
-    __syncthreads();
     const uint2 range = ranges[tile];
-    for (uint32_t i = range.x + warp; i < range.y; i += kTilePixels / 32) {
-        const uint32_t prim = sorted_prims[i];
-        const float4 A = rec[(size_t)prim * kRecF4 + 0];  // mx my l11 l21
-        const float4 B = rec[(size_t)prim * kRecF4 + 1];  // l22 fx fy phc
-        const float4 C = rec[(size_t)prim * kRecF4 + 2];  // colour
-        const PixRect r = rect[prim];
-        const int ux0 = max(r.u0, tx * kTile), ux1 = min(r.u1, tx * kTile + kTile - 1);
-        const int vy0 = max(r.v0, ty * kTile), vy1 = min(r.v1, ty * kTile + kTile - 1);
-        const int w = ux1 - ux0 + 1, area = w * (vy1 - vy0 + 1);
-        const uint32_t slot = offsets[prim] + (uint32_t)((ty - r.v0 / kTile) * (r.u1 / kTile - r.u0 / kTile + 1) +
-                                                         (tx - r.u0 / kTile));
-        const uint32_t mdiv = (65536u + (uint32_t)w - 1u) / (uint32_t)w;  // exact k / w for k < 256
-        float g_mx = 0.f, g_my = 0.f, g_l11 = 0.f, g_l21 = 0.f, g_l22 = 0.f, g_fx = 0.f, g_fy = 0.f, g_ph = 0.f;
-        float g_c0 = 0.f, g_c1 = 0.f, g_c2 = 0.f;
-        for (int k = lane; k < area; k += 32) {
-            const int lv = (int)(((uint32_t)k * mdiv) >> 16);
-            const int u = ux0 + (k - lv * w), v = vy0 + lv;
-            const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-            const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-            if (q <= cutoff2) {
-                const float dx = px - A.x, dy = py - A.y;
-                const float a = fmaf(A.z, dx, A.w * dy), b = B.x * dy;
-                const float G = ex2_approx(q * kNegHalfLog2e);
-                const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
-                const float cs = cos_approx(ang), sn = sin_approx(ang);
-                const float Wv = fmaf(0.5f, cs, 0.5f) * G;
-                const float* g = s_g + ((v - ty * kTile) * kTile + (u - tx * kTile)) * 3;
-                const float gW = fmaf(g[0], C.x, fmaf(g[1], C.y, g[2] * C.z));
-                const float gq2 = -gW * Wv;       // 2 dL/dq  (dW/dq = -W/2)
-                const float gt = -kPi * gW * G * sn;  // dL/dt, t in cycles
-                const float ga = gq2 * a, gb = gq2 * b;
-                g_l11 = fmaf(ga, dx, g_l11);
-                g_l21 = fmaf(ga, dy, g_l21);
-                g_l22 = fmaf(gb, dy, g_l22);
-                g_mx -= fmaf(ga, A.z, gt * B.y);
-                g_my -= fmaf(ga, A.w, fmaf(gb, B.x, gt * B.z));
-                g_fx = fmaf(gt, dx, g_fx);
-                g_fy = fmaf(gt, dy, g_fy);
-                g_ph += gt;
-                g_c0 = fmaf(g[0], Wv, g_c0);
-                g_c1 = fmaf(g[1], Wv, g_c1);
-                g_c2 = fmaf(g[2], Wv, g_c2);
-            }
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
+        const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t prim = sorted_prims[b0 + threadIdx.x];
+            s_a[threadIdx.x] = rec[(size_t)prim * kRecF4 + 0];
+            s_b[threadIdx.x] = rec[(size_t)prim * kRecF4 + 1];
+            s_c[threadIdx.x] = rec[(size_t)prim * kRecF4 + 2];
+            const PixRect r = rect[prim];
+            const int ux0 = max(r.u0, x0), ux1 = min(r.u1, x0 + kTile - 1);
+            const int vy0 = max(r.v0, y0), vy1 = min(r.v1, y0 + kTile - 1);
+            const int w = ux1 - ux0 + 1;
+            s_reg[threadIdx.x] = make_int4(ux0, vy0, w, w * (vy1 - vy0 + 1));
+            s_slot[threadIdx.x] = offsets[prim] + (uint32_t)((ty - r.v0 / kTile) * (r.u1 / kTile - r.u0 / kTile + 1) +
+                                                             (tx - r.u0 / kTile));
         }
+        __syncthreads();
+        for (int j = warp; j < n; j += kTilePixels / 32) {
+            const float4 A = s_a[j];  // mx my l11 l21
+            const float4 B = s_b[j];  // l22 fx fy phc
+            const float4 C = s_c[j];
+            const int4 reg = s_reg[j];
+            const uint32_t mdiv = (65536u + (uint32_t)reg.z - 1u) / (uint32_t)reg.z;  // exact k / w for k < 256
+            float acc[16];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            g_mx += __shfl_xor_sync(0xffffffffu, g_mx, o);
-            g_my += __shfl_xor_sync(0xffffffffu, g_my, o);
-            g_l11 += __shfl_xor_sync(0xffffffffu, g_l11, o);
-            g_l21 += __shfl_xor_sync(0xffffffffu, g_l21, o);
-            g_l22 += __shfl_xor_sync(0xffffffffu, g_l22, o);
-            g_fx += __shfl_xor_sync(0xffffffffu, g_fx, o);
-            g_fy += __shfl_xor_sync(0xffffffffu, g_fy, o);
-            g_ph += __shfl_xor_sync(0xffffffffu, g_ph, o);
-            g_c0 += __shfl_xor_sync(0xffffffffu, g_c0, o);
-            g_c1 += __shfl_xor_sync(0xffffffffu, g_c1, o);
-            g_c2 += __shfl_xor_sync(0xffffffffu, g_c2, o);
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+            for (int k = lane; k < reg.w; k += 32) {
+                const int lv = (int)(((uint32_t)k * mdiv) >> 16);
+                const int u = reg.x + (k - lv * reg.z), v = reg.y + lv;
+                const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+                // the cutoff test in the same operation order as mahalanobis2()
+                const float dx = __fsub_rn(px, A.x), dy = __fsub_rn(py, A.y);
+                const float a = __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy));
+                const float b = __fmul_rn(B.x, dy);
+                const float q = __fmaf_rn(a, a, __fmul_rn(b, b));
+                if (q <= cutoff2) {
+                    const float G = ex2_approx(q * kNegHalfLog2e);
+                    const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
+                    const float cs = cos_approx(ang), sn = sin_approx(ang);
+                    const float Wv = fmaf(0.5f, cs, 0.5f) * G;
+                    const float* g = s_g + ((v - y0) * kTile + (u - x0)) * 3;
+                    const float gW = fmaf(g[0], C.x, fmaf(g[1], C.y, g[2] * C.z));
+                    const float gq2 = -gW * Wv;           // 2 dL/dq  (dW/dq = -W/2)
+                    const float gt = (-kPi * G) * (gW * sn);  // dL/dt, t in cycles
+                    const float ga = gq2 * a, gb = gq2 * b;
+                    acc[0] += ga;
+                    acc[1] += gb;
+                    acc[2] += gt;
+                    acc[3] = fmaf(ga, dx, acc[3]);
+                    acc[4] = fmaf(ga, dy, acc[4]);
+                    acc[5] = fmaf(gb, dy, acc[5]);
+                    acc[6] = fmaf(gt, dx, acc[6]);
+                    acc[7] = fmaf(gt, dy, acc[7]);
+                    acc[8] = fmaf(g[0], Wv, acc[8]);
+                    acc[9] = fmaf(g[1], Wv, acc[9]);
+                    acc[10] = fmaf(g[2], Wv, acc[10]);
+                }
+            }
+            // lane l holds the total of sum (l >> 1); lane l < 12 writes slot l of the pair
+            const float tot = warp_reduce_scatter16(acc);
+            const float sga = __shfl_sync(0xffffffffu, tot, 0);
+            const float sgb = __shfl_sync(0xffffffffu, tot, 2);
+            const float sgt = __shfl_sync(0xffffffffu, tot, 4);
+            // sum feeding each slot: l11 <- ga dx (3), l21 <- ga dy (4), l22 <- gb dy (5), fx <- gt dx (6),
+            // fy <- gt dy (7), phc <- gt (2), colour 8..10
+            const int src = lane == 7 ? 2 : (lane >= 2 && lane <= 6 ? lane + 1 : min(lane, 15));
+            float val = __shfl_sync(0xffffffffu, tot, 2 * src);
+            if (lane == 0) val = -fmaf(A.z, sga, B.y * sgt);
+            if (lane == 1) val = -fmaf(A.w, sga, fmaf(B.x, sgb, B.z * sgt));
+            if (lane == 11) val = 0.f;
+            if (lane < kSlot) partial[(size_t)s_slot[j] * kSlot + lane] = val;
         }
-        float val = 0.f;
-        val = lane == 0 ? g_mx : val;
-        val = lane == 1 ? g_my : val;
-        val = lane == 2 ? g_l11 : val;
-        val = lane == 3 ? g_l21 : val;
-        val = lane == 4 ? g_l22 : val;
-        val = lane == 5 ? g_fx : val;
-        val = lane == 6 ? g_fy : val;
-        val = lane == 7 ? g_ph : val;
-        val = lane == 8 ? g_c0 : val;
-        val = lane == 9 ? g_c1 : val;
-        val = lane == 10 ? g_c2 : val;
-        if (lane < kSlot) partial[(size_t)slot * kSlot + lane] = val;
     }
 }
 
@@ -217,6 +222,11 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     if (lane != 0) return;
     const float* p = params + prim * WIPES_P2D;
     float* out = dl_dparams + prim * WIPES_P2D;
+    if (cnt == 0) {  // off-screen or degenerate: the record's parameters get no gradient
+#pragma unroll
+        for (int k = 0; k < WIPES_P2D; ++k) out[k] = 0.f;
+        return;
+    }
     const float sx = p[2], sy = p[3];
     float s, c;
     sincosf(p[4], &s, &c);
@@ -287,9 +297,10 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
 
 }  // namespace
 
-void launch_blend2d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H, int tiles_x,
-                    int tiles_y, float cutoff2, float* out, cudaStream_t stream) {
-    k_blend2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, sorted_prims, ranges, W, H, tiles_x, cutoff2, out); count_launches(1);
+void launch_blend2d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
+                    int H, int tiles_x, int tiles_y, float cutoff2, float* out, cudaStream_t stream) {
+    k_blend2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, sorted_prims, ranges, W, H, tiles_x, cutoff2,
+                                                              out); count_launches(1);
 }
 
 void launch_backward2d(const float4* rec, const PixRect* rect, const uint32_t* offsets, const uint32_t* sorted_prims,

@@ -11,26 +11,11 @@
 namespace wipes {
 namespace {
 
-constexpr float kNegHalfLog2e = -0.7213475204444817f;
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float cos_approx(float x) {
-    float y;
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float sin_approx(float x) {
-    float y;
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float reduced_angle(float t) { return (t - rintf(t)) * kTwoPi; }
-
+// Forward.  As in 2D, warp w owns an 8x4 pixel sub-tile and visits only the staged primitives
+// whose covered pixel range touches it; positions in the tile list are counted from the list
+// start, so the per-pixel last-contributor index does not depend on the culling.
 __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restrict__ rec,
+                                                         const PixRect* __restrict__ rect,
                                                          const uint32_t* __restrict__ sorted_prims,
                                                          const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                          BlendOpts3 o, float* __restrict__ out,
@@ -38,16 +23,19 @@ __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restric
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
     __shared__ float4 s_c[kTilePixels];
+    __shared__ uint8_t s_mask[kTilePixels];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int u = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int v = ty * kTile + (threadIdx.x / kTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = tx * kTile, y0 = ty * kTile;
+    const int u = x0 + (warp & 1) * 8 + (lane & 7);
+    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
     const uint2 range = ranges[tile];
     bool done = !inside;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    uint32_t seen = 0, last_contrib = 0;
+    uint32_t last_contrib = 0;
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         if (__syncthreads_count(done) == kTilePixels) break;
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
@@ -56,30 +44,37 @@ __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restric
             s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
             s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
             s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
+            s_mask[threadIdx.x] = (uint8_t)subtile_mask(rect[id], x0, y0);
         }
         __syncthreads();
-        for (int j = 0; j < n && !done; ++j) {
-            ++seen;
-            const float4 A = s_a[j];
-            const float4 B = s_b[j];
-            const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-            if (!(q <= o.cutoff2)) continue;
-            const float dx = px - A.x, dy = py - A.y;
-            const float G = ex2_approx(q * kNegHalfLog2e);
-            const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
-            const float4 C = s_c[j];
-            const float alpha = fminf(o.alpha_max, C.w * w);
-            if (alpha < o.alpha_min) continue;
-            const float test_T = T * (1.f - alpha);
-            if (test_T < o.T_min) { done = true; break; }
-            const float wt = alpha * T;
-            c0 = fmaf(C.x, wt, c0);
-            c1 = fmaf(C.y, wt, c1);
-            c2 = fmaf(C.z, wt, c2);
-            T = test_T;
-            last_contrib = seen;
+        for (int c = 0; c < n; c += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
+            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
+            while (bal) {
+                const int j = c + __ffs(bal) - 1;
+                bal &= bal - 1u;
+                if (done) continue;
+                const float4 A = s_a[j];
+                const float4 B = s_b[j];
+                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
+                if (!(q <= o.cutoff2)) continue;
+                const float dx = px - A.x, dy = py - A.y;
+                const float G = ex2_approx(q * kNegHalfLog2e);
+                const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
+                const float4 C = s_c[j];
+                const float alpha = fminf(o.alpha_max, C.w * w);
+                if (alpha < o.alpha_min) continue;
+                const float test_T = T * (1.f - alpha);
+                if (test_T < o.T_min) { done = true; continue; }
+                const float wt = alpha * T;
+                c0 = fmaf(C.x, wt, c0);
+                c1 = fmaf(C.y, wt, c1);
+                c2 = fmaf(C.z, wt, c2);
+                T = test_T;
+                last_contrib = b0 - range.x + (uint32_t)j + 1u;
+            }
         }
-        __syncthreads();
     }
     if (inside) {
         const size_t pix = (size_t)v * W + u;
@@ -94,7 +89,13 @@ __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restric
 // Image-plane gradient per primitive (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b o
 constexpr int kG = 12;
 
+// Backward.  Each pixel walks its tile list back to front from its last contributor, recovering
+// the transmittance in front of each contributor as T_i = T_{i+1} / (1 - alpha_i) from the stored
+// final value.  Warps visit only the primitives marked for their sub-tile; a warp's per-pixel
+// gradients of one primitive are summed by a reduce-scatter and added to the primitive's
+// image-plane gradient with one atomic per component.
 __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __restrict__ rec,
+                                                            const PixRect* __restrict__ rect,
                                                             const uint32_t* __restrict__ sorted_prims,
                                                             const uint2* __restrict__ ranges, int W, int H, int tiles_x,
                                                             BlendOpts3 o, const float* __restrict__ T_final,
@@ -105,12 +106,14 @@ __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __rest
     __shared__ float4 s_b[kTilePixels];
     __shared__ float4 s_c[kTilePixels];
     __shared__ uint32_t s_id[kTilePixels];
+    __shared__ uint8_t s_mask[kTilePixels];
     __shared__ uint32_t s_max_last;
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int u = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int v = ty * kTile + (threadIdx.x / kTile);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x0 = tx * kTile, y0 = ty * kTile;
+    const int u = x0 + (warp & 1) * 8 + (lane & 7);
+    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
     const uint2 range = ranges[tile];
@@ -136,88 +139,72 @@ __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __rest
             s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
             s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
             s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
+            s_mask[threadIdx.x] = (uint8_t)subtile_mask(rect[id], x0, y0);
         }
         __syncthreads();
-        for (int j = n - 1; j >= 0; --j) {
-            const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;  // 1-based position in the tile list
-            bool contrib = false;
-            float gm0 = 0.f, gm1 = 0.f, gl11 = 0.f, gl21 = 0.f, gl22 = 0.f, gfx = 0.f, gfy = 0.f, gph = 0.f;
-            float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gop = 0.f;
-            const float4 A = s_a[j];
-            const float4 B = s_b[j];
-            if (pos <= my_last) {
-                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-                if (q <= o.cutoff2) {
-                    const float dx = px - A.x, dy = py - A.y;
-                    const float G = ex2_approx(q * kNegHalfLog2e);
-                    const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
-                    const float cs = cos_approx(ang);
-                    const float w = fmaf(0.5f, cs, 0.5f) * G;
-                    const float4 C = s_c[j];
-                    const float raw = C.w * w;
-                    const float alpha = fminf(o.alpha_max, raw);
-                    if (alpha >= o.alpha_min) {
-                        contrib = true;
-                        const float om = 1.f - alpha;
-                        T = T / om;
-                        const float wt = alpha * T;
-                        gc0 = g0 * wt; gc1 = g1 * wt; gc2 = g2 * wt;
-                        const float inv = 1.f / om;
-                        const float galpha = g0 * (C.x * T - S0 * inv) + g1 * (C.y * T - S1 * inv) +
-                                             g2 * (C.z * T - S2 * inv);
-                        S0 = fmaf(C.x, wt, S0);
-                        S1 = fmaf(C.y, wt, S1);
-                        S2 = fmaf(C.z, wt, S2);
-                        if (raw < o.alpha_max) {
-                            gop = galpha * w;
-                            const float gW = galpha * C.w;
-                            const float sn = sin_approx(ang);
-                            const float a = fmaf(A.z, dx, A.w * dy), b = B.x * dy;
-                            const float gq2 = -gW * w;
-                            const float gt = -kPi * gW * G * sn;
-                            const float ga = gq2 * a, gb = gq2 * b;
-                            gl11 = ga * dx;
-                            gl21 = ga * dy;
-                            gl22 = gb * dy;
-                            gm0 = -fmaf(ga, A.z, gt * B.y);
-                            gm1 = -fmaf(ga, A.w, fmaf(gb, B.x, gt * B.z));
-                            gfx = gt * dx;
-                            gfy = gt * dy;
-                            gph = gt;
+        for (int c = (n - 1) & ~31; c >= 0; c -= 32) {
+            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
+            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
+            while (bal) {
+                const int hb = 31 - __clz(bal);
+                bal &= ~(1u << hb);
+                const int j = c + hb;
+                const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;  // 1-based position in the tile list
+                bool contrib = false;
+                float acc[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+                const float4 A = s_a[j];
+                const float4 B = s_b[j];
+                if (pos <= my_last) {
+                    const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
+                    if (q <= o.cutoff2) {
+                        const float dx = px - A.x, dy = py - A.y;
+                        const float G = ex2_approx(q * kNegHalfLog2e);
+                        const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
+                        const float cs = cos_approx(ang);
+                        const float w = fmaf(0.5f, cs, 0.5f) * G;
+                        const float4 C = s_c[j];
+                        const float raw = C.w * w;
+                        const float alpha = fminf(o.alpha_max, raw);
+                        if (alpha >= o.alpha_min) {
+                            contrib = true;
+                            const float om = 1.f - alpha;
+                            T = T / om;
+                            const float wt = alpha * T;
+                            acc[8] = g0 * wt;
+                            acc[9] = g1 * wt;
+                            acc[10] = g2 * wt;
+                            const float inv = 1.f / om;
+                            const float galpha = g0 * (C.x * T - S0 * inv) + g1 * (C.y * T - S1 * inv) +
+                                                 g2 * (C.z * T - S2 * inv);
+                            S0 = fmaf(C.x, wt, S0);
+                            S1 = fmaf(C.y, wt, S1);
+                            S2 = fmaf(C.z, wt, S2);
+                            if (raw < o.alpha_max) {
+                                acc[11] = galpha * w;
+                                const float gW = galpha * C.w;
+                                const float sn = sin_approx(ang);
+                                const float a = fmaf(A.z, dx, A.w * dy), b = B.x * dy;
+                                const float gq2 = -gW * w;
+                                const float gt = (-kPi * G) * (gW * sn);
+                                const float ga = gq2 * a, gb = gq2 * b;
+                                acc[2] = ga * dx;
+                                acc[3] = ga * dy;
+                                acc[4] = gb * dy;
+                                acc[0] = -fmaf(ga, A.z, gt * B.y);
+                                acc[1] = -fmaf(ga, A.w, fmaf(gb, B.x, gt * B.z));
+                                acc[5] = gt * dx;
+                                acc[6] = gt * dy;
+                                acc[7] = gt;
+                            }
                         }
                     }
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int s = 16; s > 0; s >>= 1) {
-                    gm0 += __shfl_xor_sync(0xffffffffu, gm0, s);
-                    gm1 += __shfl_xor_sync(0xffffffffu, gm1, s);
-                    gl11 += __shfl_xor_sync(0xffffffffu, gl11, s);
-                    gl21 += __shfl_xor_sync(0xffffffffu, gl21, s);
-                    gl22 += __shfl_xor_sync(0xffffffffu, gl22, s);
-                    gfx += __shfl_xor_sync(0xffffffffu, gfx, s);
-                    gfy += __shfl_xor_sync(0xffffffffu, gfy, s);
-                    gph += __shfl_xor_sync(0xffffffffu, gph, s);
-                    gc0 += __shfl_xor_sync(0xffffffffu, gc0, s);
-                    gc1 += __shfl_xor_sync(0xffffffffu, gc1, s);
-                    gc2 += __shfl_xor_sync(0xffffffffu, gc2, s);
-                    gop += __shfl_xor_sync(0xffffffffu, gop, s);
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float tot = warp_reduce_scatter16(acc);
+                    if ((lane & 1) == 0 && (lane >> 1) < kG) atomicAdd(grad_img + (size_t)s_id[j] * kG + (lane >> 1), tot);
                 }
-                float val = 0.f;
-                val = lane == 0 ? gm0 : val;
-                val = lane == 1 ? gm1 : val;
-                val = lane == 2 ? gl11 : val;
-                val = lane == 3 ? gl21 : val;
-                val = lane == 4 ? gl22 : val;
-                val = lane == 5 ? gfx : val;
-                val = lane == 6 ? gfy : val;
-                val = lane == 7 ? gph : val;
-                val = lane == 8 ? gc0 : val;
-                val = lane == 9 ? gc1 : val;
-                val = lane == 10 ? gc2 : val;
-                val = lane == 11 ? gop : val;
-                if (lane < kG) atomicAdd(grad_img + (size_t)s_id[j] * kG + lane, val);
             }
         }
     }
@@ -386,16 +373,19 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
 
 }  // namespace
 
-void launch_blend3d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H, int tiles_x,
-                    int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last, cudaStream_t stream) {
-    k_blend3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, sorted_prims, ranges, W, H, tiles_x, o, out, T_final,
+void launch_blend3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
+                    int H, int tiles_x, int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last,
+                    cudaStream_t stream) {
+    k_blend3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, sorted_prims, ranges, W, H, tiles_x, o, out,
+                                                              T_final,
                                                               last); count_launches(1);
 }
 
-void launch_backward3d(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
-                       int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
-                       const float* dl_dout, float* grad_img, cudaStream_t stream) {
-    k_backward3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, sorted_prims, ranges, W, H, tiles_x, o, T_final,
+void launch_backward3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges,
+                       int W, int H, int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final,
+                       const uint32_t* last, const float* dl_dout, float* grad_img, cudaStream_t stream) {
+    k_backward3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, sorted_prims, ranges, W, H, tiles_x, o,
+                                                                 T_final,
                                                                  last, dl_dout, grad_img); count_launches(1);
 }
 

@@ -70,8 +70,8 @@ def test_backward_matches_oracle(N, H, W, scale, seed):
     params, st, _ = _gpu_forward(w, torch, p, H, W)
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
-    ref = oracle.grad2d(p, H, W, g, truncated=True)
-    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, cols=list(range(11)))
+    ref, gabs = oracle.grad2d(p, H, W, g, truncated=True, with_abs=True)
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, cols=list(range(11)))
     assert ok, (worst, idx)
     assert np.all(grad.cpu().numpy()[:, 11:] == 0)
 
@@ -137,7 +137,8 @@ def test_edge_cases():
     gd = synth.upstream_grad(H, W, 14)
     grad = w.backward(st, params, torch.from_numpy(gd).cuda()).cpu().numpy()
     assert np.all(grad[[0, 1, 2, 3, 4]] == 0)
-    ok, worst, idx = grad_close(grad, oracle.grad2d(p, H, W, gd), cols=list(range(11)))
+    ref, gabs = oracle.grad2d(p, H, W, gd, with_abs=True)
+    ok, worst, idx = grad_close(grad, ref, gabs, cols=list(range(11)))
     assert ok, (worst, idx)
 
 
@@ -162,6 +163,6 @@ def test_full_size_768x512_70k_sampled():
     g = synth.upstream_grad(H, W, 22, scale=1e-3)
     grad = w.backward(st, params, torch.from_numpy(g).cuda()).cpu().numpy()
     sel = np.random.default_rng(23).choice(p.shape[0], 300, replace=False)
-    ref_g = oracle.grad2d(p[sel], H, W, g)
-    ok, worst, idx = grad_close(grad[sel], ref_g, cols=list(range(11)))
+    ref_g, gabs = oracle.grad2d(p[sel], H, W, g, with_abs=True)
+    ok, worst, idx = grad_close(grad[sel], ref_g, gabs, cols=list(range(11)))
     assert ok, (worst, idx)
