@@ -184,9 +184,10 @@ def deform6d_grad(params6, t, g3):
 
 
 def cutoff_coverage(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
-    """(pairs inside the cutoff, of those outside the covered pixel range, pixels in the ranges)."""
+    """(pairs inside the cutoff, of those outside the covered pixel range, pixels in the ranges,
+    cutoff pairs that the tile ellipse test would drop)."""
     params = _f32(params)
     camv = _f32(cam) if cam is not None else None
-    counts = np.zeros(3, np.int64)
+    counts = np.zeros(4, np.int64)
     _load().wo_cutoff_coverage(dims, _ptr(params), params.shape[0], _ptr(camv), H, W, cutoff, dilation, _ptr(counts))
-    return int(counts[0]), int(counts[1]), int(counts[2])
+    return int(counts[0]), int(counts[1]), int(counts[2]), int(counts[3])

@@ -177,6 +177,61 @@ static float q32(const fp32_footprint* k, int u, int v) {
     return fmaf(a, a, b * b);
 }
 
+/* Does the cutoff ellipse, widened by a 1 % margin on cutoff^2, reach the rectangle spanned by the
+ * pixel centres of columns x0..x1 and rows y0..y1?  With q = A dx^2 + 2 B dx dy + C dy^2
+ * (A = l11^2, B = l11 l21, C = l21^2 + l22^2) the minimum over the rectangle is 0 when the centre
+ * lies inside, else the least of the four edge minima: on an edge of fixed dx the minimiser is
+ * dy = -(B/C) dx clamped to the edge, on an edge of fixed dy it is dx = -(B/A) dy clamped.  Every
+ * pixel centre that passes the binary32 cutoff test lies in a rectangle this returns 1 for (the
+ * margin exceeds the rounding of q32). */
+typedef struct { float rBA, rBC; } edge_ratios;
+
+static edge_ratios footprint_ratios(const fp32_footprint* k) {
+    float A = k->l11 * k->l11, B = k->l11 * k->l21, C = k->l21 * k->l21 + k->l22 * k->l22;
+    edge_ratios r = {-(B / A), -(B / C)};
+    return r;
+}
+
+static int rect_touched(const fp32_footprint* k, edge_ratios rr, int x0, int x1, int y0, int y1, float lim) {
+    float dx0 = ((float)x0 + 0.5f) - k->mx, dx1 = ((float)x1 + 0.5f) - k->mx;
+    float dy0 = ((float)y0 + 0.5f) - k->my, dy1 = ((float)y1 + 0.5f) - k->my;
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return 1;
+    float best = 0.0f;
+    for (int e = 0; e < 4; ++e) {
+        float dx, dy;
+        if (e < 2) {
+            dx = e == 0 ? dx0 : dx1;
+            dy = fminf(fmaxf(rr.rBC * dx, dy0), dy1);
+        } else {
+            dy = e == 2 ? dy0 : dy1;
+            dx = fminf(fmaxf(rr.rBA * dy, dx0), dx1);
+        }
+        float a = k->l11 * dx + k->l21 * dy;
+        float b = k->l22 * dy;
+        float q = a * a + b * b;
+        best = e == 0 ? q : fminf(best, q);
+    }
+    return best <= lim;
+}
+
+static float touch_limit(float cutoff) { return (cutoff * cutoff) * 1.01f; }
+
+/* number of tiles of the covered pixel range that the cutoff ellipse touches */
+static int64_t touched_tiles(const fp32_footprint* k, float lim, uint32_t* tiles, int tiles_x) {
+    if (!k->valid || k->u0 > k->u1) return 0;
+    edge_ratios rr = footprint_ratios(k);
+    int64_t n = 0;
+    for (int ty = k->v0 / TILE; ty <= k->v1 / TILE; ++ty)
+        for (int tx = k->u0 / TILE; tx <= k->u1 / TILE; ++tx) {
+            int x0 = tx * TILE > k->u0 ? tx * TILE : k->u0, x1 = tx * TILE + TILE - 1 < k->u1 ? tx * TILE + TILE - 1 : k->u1;
+            int y0 = ty * TILE > k->v0 ? ty * TILE : k->v0, y1 = ty * TILE + TILE - 1 < k->v1 ? ty * TILE + TILE - 1 : k->v1;
+            if (!rect_touched(k, rr, x0, x1, y0, y1, lim)) continue;
+            if (tiles) tiles[n] = (uint32_t)(ty * tiles_x + tx);
+            ++n;
+        }
+    return n;
+}
+
 static uint32_t f32_bits(float x) { uint32_t b; memcpy(&b, &x, 4); return b; }
 
 /* Exported view of the footprint rule: rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth; rect[N,4] = u0,v0,u1,v1;
@@ -228,23 +283,22 @@ int64_t wo_tile_lists(int dims, const float* params, int64_t N, const float* cam
                       uint32_t* tile_out, uint32_t* prim_out, int64_t cap) {
     fp32_footprint* k = all_footprints(dims, params, N, cam, H, W, cutoff, dil);
     int tiles_x = (W + TILE - 1) / TILE;
+    float lim = touch_limit(cutoff);
     int64_t total = 0;
-    for (int64_t i = 0; i < N; ++i) {
-        if (!k[i].valid || k[i].u0 > k[i].u1) continue;
-        total += (int64_t)(k[i].u1 / TILE - k[i].u0 / TILE + 1) * (k[i].v1 / TILE - k[i].v0 / TILE + 1);
-    }
+    for (int64_t i = 0; i < N; ++i) total += touched_tiles(&k[i], lim, NULL, tiles_x);
     tile_entry* e = (tile_entry*)malloc(sizeof(tile_entry) * (size_t)(total > 0 ? total : 1));
+    uint32_t* tl = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)((W + TILE - 1) / TILE) * (size_t)((H + TILE - 1) / TILE));
     int64_t n = 0;
     for (int64_t i = 0; i < N; ++i) {
-        if (!k[i].valid || k[i].u0 > k[i].u1) continue;
-        for (int ty = k[i].v0 / TILE; ty <= k[i].v1 / TILE; ++ty)
-            for (int tx = k[i].u0 / TILE; tx <= k[i].u1 / TILE; ++tx) {
-                e[n].tile = (uint32_t)(ty * tiles_x + tx);
-                e[n].depth = dims == 3 ? f32_bits(k[i].depth) : 0u;
-                e[n].prim = (uint32_t)i;
-                ++n;
-            }
+        int64_t m = touched_tiles(&k[i], lim, tl, tiles_x);
+        for (int64_t j = 0; j < m; ++j) {
+            e[n].tile = tl[j];
+            e[n].depth = dims == 3 ? f32_bits(k[i].depth) : 0u;
+            e[n].prim = (uint32_t)i;
+            ++n;
+        }
     }
+    free(tl);
     qsort(e, (size_t)n, sizeof(tile_entry), cmp_entry);
     for (int64_t j = 0; j < n && j < cap; ++j) {
         tile_out[j] = e[j].tile;
@@ -908,13 +962,15 @@ int wo_deform6d_grad(const float* params6, int64_t N, double t, const double* g3
 /* ------------------------------------------------------------------------------------------ */
 
 /* counts[0] = pairs inside the cutoff ellipse, counts[1] = of those, pairs outside the pixel range,
- * counts[2] = pixels inside the pixel ranges (pairs the tile lists make a kernel visit at most) */
+ * counts[2] = pixels inside the pixel ranges, counts[3] = cutoff pairs whose tile (or whose own
+ * one-pixel rectangle) the ellipse test rejects */
 int wo_cutoff_coverage(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff,
                        float dil, int64_t* counts) {
     fp32_footprint* k = all_footprints(dims, params, N, cam, H, W, cutoff, dil);
     float k2 = cutoff * cutoff;
-    int64_t inside = 0, outside = 0, rect_px = 0;
-#pragma omp parallel for schedule(dynamic, 16) reduction(+ : inside, outside, rect_px)
+    float lim = touch_limit(cutoff);
+    int64_t inside = 0, outside = 0, rect_px = 0, untouched = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : inside, outside, rect_px, untouched)
     for (int64_t i = 0; i < N; ++i) {
         if (!k[i].valid) continue;
         if (k[i].u0 <= k[i].u1) rect_px += (int64_t)(k[i].u1 - k[i].u0 + 1) * (k[i].v1 - k[i].v0 + 1);
@@ -922,12 +978,20 @@ int wo_cutoff_coverage(int dims, const float* params, int64_t N, const float* ca
             for (int u = 0; u < W; ++u) {
                 if (!(q32(&k[i], u, v) <= k2)) continue;
                 ++inside;
-                if (u < k[i].u0 || u > k[i].u1 || v < k[i].v0 || v > k[i].v1) ++outside;
+                if (u < k[i].u0 || u > k[i].u1 || v < k[i].v0 || v > k[i].v1) { ++outside; continue; }
+                int tx = u / TILE, ty = v / TILE;
+                int x0 = tx * TILE > k[i].u0 ? tx * TILE : k[i].u0;
+                int x1 = tx * TILE + TILE - 1 < k[i].u1 ? tx * TILE + TILE - 1 : k[i].u1;
+                int y0 = ty * TILE > k[i].v0 ? ty * TILE : k[i].v0;
+                int y1 = ty * TILE + TILE - 1 < k[i].v1 ? ty * TILE + TILE - 1 : k[i].v1;
+                edge_ratios rr = footprint_ratios(&k[i]);
+                if (!rect_touched(&k[i], rr, x0, x1, y0, y1, lim) || !rect_touched(&k[i], rr, u, u, v, v, lim)) ++untouched;
             }
     }
     counts[0] = inside;
     counts[1] = outside;
     counts[2] = rect_px;
+    counts[3] = untouched;
     free(k);
     return 0;
 }

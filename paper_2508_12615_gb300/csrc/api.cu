@@ -154,15 +154,23 @@ struct wipes_state {
     wipes_camera cam{};
     int64_t n_inst = 0;
     int sorted = 0;  // which ping-pong buffer holds the sorted lists
-    DevBuf rec, rect, counts, offsets, dkeys[2], dvals[2], block_sums, total, keys[2], vals[2], hist, ranges;
+    DevBuf rec, rect, counts, offsets, dkeys[2], dvals[2], block_sums, total, keys[2], vals[2], inst_prim, hist, ranges;
     DevBuf T_final, last, partial, grad_img;
 
-    DevBuf* all[19] = {&rec, &rect, &counts, &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1], &block_sums,
-                       &total, &keys[0], &keys[1], &vals[0], &vals[1], &hist, &ranges, &T_final, &last, &partial};
+    DevBuf* all[21] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0],
+                       &dvals[1], &block_sums, &total, &keys[0], &keys[1],   &vals[0],   &vals[1],
+                       &inst_prim, &hist, &ranges, &T_final, &last, &partial, &grad_img};
     size_t reserved() const {
-        size_t s = grad_img.cap;
+        size_t s = 0;
         for (DevBuf* b : all) s += b->cap;
         return s;
+    }
+    TileLists lists() const {
+        TileLists t;
+        t.sorted = vals[sorted].as<uint32_t>();
+        t.inst_prim = inst_prim.as<uint32_t>();
+        t.ranges = ranges.as<uint2>();
+        return t;
     }
 };
 
@@ -203,11 +211,14 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
         WIPES_TRY(ensure(st->keys[k], sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
         WIPES_TRY(ensure(st->vals[k], sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
     }
+    WIPES_TRY(ensure(st->inst_prim, sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
     WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(I)));
     if (N > 0) {
         StageTimer t(st->ctx, WIPES_STAGE_EMIT, s);
-        launch_emit(st->counts.as<uint32_t>(), perm, N, st->rect.as<PixRect>(), st->block_sums.as<unsigned long long>(),
-                    st->tiles_x, st->keys[0].as<uint32_t>(), st->vals[0].as<uint32_t>(), st->offsets.as<uint32_t>(), s);
+        launch_emit(st->counts.as<uint32_t>(), perm, N, st->rec.as<float4>(), st->rect.as<PixRect>(),
+                    st->block_sums.as<unsigned long long>(), st->tiles_x, touch_limit(st->opts.cutoff_sigma),
+                    st->keys[0].as<uint32_t>(), st->vals[0].as<uint32_t>(), st->inst_prim.as<uint32_t>(),
+                    st->offsets.as<uint32_t>(), s);
     }
     uint32_t* kb[2] = {st->keys[0].as<uint32_t>(), st->keys[1].as<uint32_t>()};
     uint32_t* vb[2] = {st->vals[0].as<uint32_t>(), st->vals[1].as<uint32_t>()};
@@ -242,6 +253,7 @@ wipes_status prepare_state(wipes_state* st, int dims, int64_t N, int H, int W, c
 BlendOpts3 blend_opts(const wipes_opts& o) {
     BlendOpts3 b;
     b.cutoff2 = o.cutoff_sigma * o.cutoff_sigma;
+    b.lim = touch_limit(o.cutoff_sigma);
     b.alpha_min = o.alpha_min;
     b.alpha_max = o.alpha_max;
     b.T_min = o.T_min;
@@ -326,7 +338,6 @@ wipes_status wipes_state_destroy(wipes_state* st) {
     if (!st) return WIPES_OK;
     DeviceGuard g(st->ctx->device);
     for (DevBuf* b : st->all) release(*b);
-    release(st->grad_img);
     delete st;
     return WIPES_OK;
 }
@@ -349,9 +360,8 @@ wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params
     WIPES_TRY(bin_and_sort(st, nullptr, s));
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->vals[st->sorted].as<uint32_t>(),
-                       st->ranges.as<uint2>(), W, H, st->tiles_x, st->tiles_y, opts->cutoff_sigma * opts->cutoff_sigma,
-                       out, s);
+        launch_blend2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), W, H, st->tiles_x, st->tiles_y,
+                       opts->cutoff_sigma, out, s);
     }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 2;
@@ -397,10 +407,8 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
     WIPES_TRY(bin_and_sort(st, dv[cur], s));
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->vals[st->sorted].as<uint32_t>(),
-                       st->ranges.as<uint2>(), W, H,
-                       st->tiles_x, st->tiles_y, blend_opts(*opts), out, st->T_final.as<float>(),
-                       st->last.as<uint32_t>(), s);
+        launch_blend3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), W, H, st->tiles_x, st->tiles_y,
+                       blend_opts(*opts), out, st->T_final.as<float>(), st->last.as<uint32_t>(), s);
     }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 3;
@@ -415,14 +423,12 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = st->N;
-    const float cutoff2 = st->opts.cutoff_sigma * st->opts.cutoff_sigma;
     if (st->dims == 2) {
         WIPES_TRY(ensure(st->partial, sizeof(float) * 12 * (size_t)std::max<int64_t>(st->n_inst, 1)));
         {
             StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
-            launch_backward2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->offsets.as<uint32_t>(),
-                              st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), st->W, st->H, st->tiles_x,
-                              st->tiles_y, cutoff2, dL_dout, st->partial.as<float>(), s);
+            launch_backward2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), st->W, st->H, st->tiles_x,
+                              st->tiles_y, st->opts.cutoff_sigma, dL_dout, st->partial.as<float>(), s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
         launch_reduce_chain2d(params, N, st->offsets.as<uint32_t>(), st->counts.as<uint32_t>(),
@@ -432,10 +438,9 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
         {
             StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
             if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * 12 * (size_t)N, s));
-            launch_backward3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->vals[st->sorted].as<uint32_t>(),
-                              st->ranges.as<uint2>(),
-                              st->W, st->H, st->tiles_x, st->tiles_y, blend_opts(st->opts), st->T_final.as<float>(),
-                              st->last.as<uint32_t>(), dL_dout, st->grad_img.as<float>(), s);
+            launch_backward3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), st->W, st->H, st->tiles_x,
+                              st->tiles_y, blend_opts(st->opts), st->T_final.as<float>(), st->last.as<uint32_t>(),
+                              dL_dout, st->grad_img.as<float>(), s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
         launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->rec.as<float4>(),
@@ -493,7 +498,7 @@ wipes_status wipes_state_copy_lists(const wipes_state* st, uint32_t* tile_ids, u
     if (tile_ids && I)
         WIPES_CUDA(cudaMemcpyAsync(tile_ids, st->keys[st->sorted].p, I * 4, cudaMemcpyDeviceToDevice, s));
     if (prim_ids && I)
-        WIPES_CUDA(cudaMemcpyAsync(prim_ids, st->vals[st->sorted].p, I * 4, cudaMemcpyDeviceToDevice, s));
+        launch_gather_u32(prim_ids, st->inst_prim.as<uint32_t>(), st->vals[st->sorted].as<uint32_t>(), (int64_t)I, s);
     if (tile_ranges)
         WIPES_CUDA(cudaMemcpyAsync(tile_ranges, st->ranges.p, (size_t)st->tiles_x * st->tiles_y * sizeof(uint2),
                                    cudaMemcpyDeviceToDevice, s));
@@ -518,9 +523,8 @@ wipes_status wipes_state_count_pairs(wipes_ctx* ctx, const wipes_state* st, int6
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     WIPES_CUDA(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * 2, s));
-    launch_count_pairs(st->rec.as<float4>(), st->vals[st->sorted].as<uint32_t>(), st->ranges.as<uint2>(), st->W,
-                       st->H, st->tiles_x, st->tiles_y, st->opts.cutoff_sigma * st->opts.cutoff_sigma,
-                       ctx->d_counters, s);
+    launch_count_pairs(st->rec.as<float4>(), st->lists(), st->W, st->H, st->tiles_x, st->tiles_y,
+                       st->opts.cutoff_sigma * st->opts.cutoff_sigma, ctx->d_counters, s);
     unsigned long long h[2] = {0, 0};
     WIPES_CUDA(cudaMemcpyAsync(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, s));
     WIPES_CUDA(cudaStreamSynchronize(s));

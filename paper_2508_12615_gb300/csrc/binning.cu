@@ -73,14 +73,21 @@ __global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long
     if (threadIdx.x == 0) *total_out = carry;
 }
 
+// Emission.  The block first scans the tile counts of its 1024 scan positions; then each warp
+// takes one primitive at a time and its 32 lanes test 32 tiles of the primitive's covered range
+// at once, writing the touched ones contiguously (ballot + population count), in row-major tile
+// order.  This keeps the large primitives from serialising on one thread.
 __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ counts,
                                                    const uint32_t* __restrict__ perm, int64_t n,
-                                                   const PixRect* __restrict__ rect,
+                                                   const float4* __restrict__ rec, const PixRect* __restrict__ rect,
                                                    const unsigned long long* __restrict__ block_offsets, int tiles_x,
-                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                   uint32_t* __restrict__ offsets) {
+                                                   float lim, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   uint32_t* __restrict__ inst_prim, uint32_t* __restrict__ offsets) {
     __shared__ unsigned long long s_warp[kWarps];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
+    __shared__ uint32_t s_prim[kScanBlockElems];
+    __shared__ uint32_t s_off[kScanBlockElems];
+    const int64_t blk = (int64_t)blockIdx.x * kScanBlockElems;
+    const int64_t base = blk + threadIdx.x * kScanItems;
     uint32_t prim[kScanItems], cnt[kScanItems];
     unsigned long long s = 0;
 #pragma unroll
@@ -93,21 +100,44 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
     unsigned long long off = block_offsets[blockIdx.x] + block_exclusive_scan<unsigned long long>(s, nullptr, s_warp);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k >= n) break;
-        offsets[prim[k]] = (uint32_t)off;
-        if (cnt[k]) {
-            const PixRect r = rect[prim[k]];
-            const int tx0 = r.u0 / kTile, tx1 = r.u1 / kTile, ty0 = r.v0 / kTile, ty1 = r.v1 / kTile;
-            uint32_t o = (uint32_t)off;
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    keys[o] = (uint32_t)(ty * tiles_x + tx);
-                    vals[o] = prim[k];
-                    ++o;
-                }
-        }
+        const int local = threadIdx.x * kScanItems + k;
+        s_prim[local] = cnt[k] ? prim[k] : 0xFFFFFFFFu;
+        s_off[local] = (uint32_t)off;
+        if (base + k < n) offsets[prim[k]] = (uint32_t)off;
         off += cnt[k];
     }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = (int)min((int64_t)kScanBlockElems, n - blk);
+    for (int j = warp; j < m; j += kWarps) {
+        const uint32_t p = s_prim[j];
+        if (p == 0xFFFFFFFFu) continue;
+        const PixRect r = rect[p];
+        const float4 A = rec[(size_t)p * kRecF4 + 0];
+        const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
+        const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
+        const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
+        uint32_t o = s_off[j];
+        for (int t0 = 0; t0 < nt; t0 += 32) {
+            const int t = t0 + lane;
+            const int ty = ty0 + t / nx, tx = tx0 + t % nx;
+            const bool hit = t < nt && tile_touched(e, r, tx, ty, lim);
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const uint32_t w = o + __popc(bal & ((1u << lane) - 1u));
+                keys[w] = (uint32_t)(ty * tiles_x + tx);
+                vals[w] = w;
+                inst_prim[w] = p;
+            }
+            o += __popc(bal);
+        }
+    }
+}
+
+__global__ void k_gather_u32(uint32_t* __restrict__ out, const uint32_t* __restrict__ table,
+                             const uint32_t* __restrict__ idx, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = table[idx[i]];
 }
 
 __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
@@ -271,12 +301,20 @@ void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned lon
     k_scan_block_sums<<<1, kThreads, 0, stream>>>(block_sums, nb, total); count_launches(1);
 }
 
-void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const PixRect* rect,
-                 const unsigned long long* block_offsets, int tiles_x, uint32_t* keys, uint32_t* vals,
-                 uint32_t* offsets, cudaStream_t stream) {
+void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,
+                 const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
+                 uint32_t* inst_prim, uint32_t* offsets, cudaStream_t stream) {
     if (n == 0) return;
-    k_emit<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, rect, block_offsets, tiles_x, keys,
-                                                                  vals, offsets); count_launches(1);
+    k_emit<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, rec, rect, block_offsets, tiles_x,
+                                                                  lim, keys, vals, inst_prim, offsets);
+    count_launches(1);
+}
+
+void launch_gather_u32(uint32_t* out, const uint32_t* table, const uint32_t* idx, int64_t n, cudaStream_t stream) {
+    if (n == 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+    k_gather_u32<<<grid, 256, 0, stream>>>(out, table, idx, n);
+    count_launches(1);
 }
 
 void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, int n_tiles, cudaStream_t stream) {

@@ -76,6 +76,99 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Cutoff test of a rectangle of pixel centres (columns x0..x1, rows y0..y1): does the cutoff
+// ellipse q <= lim (lim = cutoff^2 x 1.01) reach it?  With q = A dx^2 + 2 B dx dy + C dy^2
+// (A = l11^2, B = l11 l21, C = l21^2 + l22^2) the minimum over the rectangle is 0 when the centre
+// lies inside, else the least of the four edge minima: dy = -(B/C) dx clamped on an edge of fixed
+// dx, dx = -(B/A) dy clamped on an edge of fixed dy.  Written with explicit single-rounding
+// operations so that the tile lists built from it are reproducible operation by operation.  The
+// margin exceeds the rounding of the per-pixel test, so a pixel that passes
+// mahalanobis2() <= cutoff^2 always lies in a rectangle accepted here.
+struct Ellipse {
+    float mx, my, l11, l21, l22;
+    float rBA, rBC;  // -(B/A), -(B/C)
+};
+
+__device__ __forceinline__ Ellipse make_ellipse(float mx, float my, float l11, float l21, float l22) {
+    const float A = __fmul_rn(l11, l11), B = __fmul_rn(l11, l21);
+    const float C = __fadd_rn(__fmul_rn(l21, l21), __fmul_rn(l22, l22));
+    Ellipse e;
+    e.mx = mx; e.my = my; e.l11 = l11; e.l21 = l21; e.l22 = l22;
+    e.rBA = -__fdiv_rn(B, A);
+    e.rBC = -__fdiv_rn(B, C);
+    return e;
+}
+
+__device__ __forceinline__ bool rect_touched(const Ellipse& k, int x0, int x1, int y0, int y1, float lim) {
+    const float dx0 = __fsub_rn(__fadd_rn((float)x0, 0.5f), k.mx), dx1 = __fsub_rn(__fadd_rn((float)x1, 0.5f), k.mx);
+    const float dy0 = __fsub_rn(__fadd_rn((float)y0, 0.5f), k.my), dy1 = __fsub_rn(__fadd_rn((float)y1, 0.5f), k.my);
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
+    float best = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float dx, dy;
+        if (e < 2) {
+            dx = e == 0 ? dx0 : dx1;
+            dy = fminf(fmaxf(__fmul_rn(k.rBC, dx), dy0), dy1);
+        } else {
+            dy = e == 2 ? dy0 : dy1;
+            dx = fminf(fmaxf(__fmul_rn(k.rBA, dy), dx0), dx1);
+        }
+        const float a = __fadd_rn(__fmul_rn(k.l11, dx), __fmul_rn(k.l21, dy));
+        const float b = __fmul_rn(k.l22, dy);
+        const float q = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
+        best = e == 0 ? q : fminf(best, q);
+    }
+    return best <= lim;
+}
+
+// Tile (tx, ty) clipped to a covered pixel range, tested with rect_touched().
+__device__ __forceinline__ bool tile_touched(const Ellipse& k, const PixRect& r, int tx, int ty, float lim) {
+    const int x0 = max(tx * kTile, r.u0), x1 = min(tx * kTile + kTile - 1, r.u1);
+    const int y0 = max(ty * kTile, r.v0), y1 = min(ty * kTile + kTile - 1, r.v1);
+    return rect_touched(k, x0, x1, y0, y1, lim);
+}
+
+// Which of the eight 8x4 warp sub-tiles of the 16x16 tile at (x0, y0) the primitive's cutoff
+// ellipse reaches: bit w for warp w (columns 8 (w & 1) .. +7, rows 4 (w >> 1) .. +3).  The same
+// rectangle test as rect_touched() in ordinary (fused) arithmetic; the 1 % margin of lim keeps it
+// conservative.
+__device__ __forceinline__ uint32_t subtile_mask_ellipse(const float4& A4, float l22, const PixRect& r, int x0, int y0,
+                                                         float lim) {
+    const float l11 = A4.z, l21 = A4.w;
+    const float A = l11 * l11, B = l11 * l21, C = fmaf(l21, l21, l22 * l22);
+    const float nBA = -B / A, nBC = -B / C;
+    uint32_t m = 0;
+#pragma unroll 1
+    for (int w = 0; w < 8; ++w) {
+        const int sx0 = max(x0 + 8 * (w & 1), r.u0), sx1 = min(x0 + 8 * (w & 1) + 7, r.u1);
+        const int sy0 = max(y0 + 4 * (w >> 1), r.v0), sy1 = min(y0 + 4 * (w >> 1) + 3, r.v1);
+        if (sx0 > sx1 || sy0 > sy1) continue;
+        const float dx0 = ((float)sx0 + 0.5f) - A4.x, dx1 = ((float)sx1 + 0.5f) - A4.x;
+        const float dy0 = ((float)sy0 + 0.5f) - A4.y, dy1 = ((float)sy1 + 0.5f) - A4.y;
+        bool hit = dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f;
+        if (!hit) {
+            float best = 3.4e38f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float dx, dy;
+                if (e < 2) {
+                    dx = e == 0 ? dx0 : dx1;
+                    dy = fminf(fmaxf(nBC * dx, dy0), dy1);
+                } else {
+                    dy = e == 2 ? dy0 : dy1;
+                    dx = fminf(fmaxf(nBA * dy, dx0), dx1);
+                }
+                const float a = fmaf(l11, dx, l21 * dy), b = l22 * dy;
+                best = fminf(best, fmaf(a, a, b * b));
+            }
+            hit = best <= lim;
+        }
+        if (hit) m |= 1u << w;
+    }
+    return m;
+}
+
 // Which of the eight 8x4 warp sub-tiles of the 16x16 tile at (x0, y0) a covered pixel range
 // touches: bit w for warp w (columns 8 (w & 1) .. +7, rows 4 (w >> 1) .. +3).
 __device__ __forceinline__ uint32_t subtile_mask(const PixRect& r, int x0, int y0) {
@@ -91,6 +184,12 @@ __device__ __forceinline__ uint32_t subtile_mask(const PixRect& r, int x0, int y
 }
 
 // Launch helpers ---------------------------------------------------------------------------------
+
+// Limit of rect_touched(): cutoff^2 widened by 1 %, in binary32 (host side).
+inline float touch_limit(float cutoff) {
+    volatile float k2 = cutoff * cutoff;
+    return k2 * 1.01f;
+}
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -116,10 +215,13 @@ void launch_block_sums(const uint32_t* counts, const uint32_t* perm, int64_t n, 
                        cudaStream_t stream);
 // Exclusive scan of nb block sums in place; total written to *total.
 void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total, cudaStream_t stream);
-// Emit (tile id, primitive) pairs in scan order; offsets[prim] = first instance index of prim.
-void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const PixRect* rect,
-                 const unsigned long long* block_offsets, int tiles_x, uint32_t* keys, uint32_t* vals,
-                 uint32_t* offsets, cudaStream_t stream);
+// Emit one instance per tile the cutoff ellipse reaches, in scan order: keys[e] = tile id,
+// vals[e] = e (the emission index), inst_prim[e] = primitive; offsets[prim] = its first index.
+void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,
+                 const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
+                 uint32_t* inst_prim, uint32_t* offsets, cudaStream_t stream);
+// out[i] = table[idx[i]]
+void launch_gather_u32(uint32_t* out, const uint32_t* table, const uint32_t* idx, int64_t n, cudaStream_t stream);
 void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, int n_tiles, cudaStream_t stream);
 void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream);
 
@@ -130,28 +232,32 @@ int64_t radix_hist_words(int64_t n);
 int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream);
 
 // raster2d.cu
-void launch_blend2d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
-                    int H, int tiles_x, int tiles_y, float cutoff2, float* out, cudaStream_t stream);
-void launch_backward2d(const float4* rec, const PixRect* rect, const uint32_t* offsets, const uint32_t* sorted_prims,
-                       const uint2* ranges, int W, int H, int tiles_x, int tiles_y, float cutoff2,
-                       const float* dl_dout, float* partial, cudaStream_t stream);
+// Tile-list entries are emission indices: the primitive of entry i is inst_prim[sorted[i]].
+struct TileLists {
+    const uint32_t* sorted;     // emission indices in tile order
+    const uint32_t* inst_prim;  // primitive of each emission index
+    const uint2* ranges;        // [start, end) of each tile in `sorted`
+};
+void launch_blend2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                    int tiles_y, float cutoff, float* out, cudaStream_t stream);
+void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                       int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream);
 void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream);
 // counters[0] += visited pairs, counters[1] += pairs inside the cutoff ellipse
-void launch_count_pairs(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
-                        int tiles_x, int tiles_y, float cutoff2, unsigned long long* counters, cudaStream_t stream);
+void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
+                        unsigned long long* counters, cudaStream_t stream);
 
 // raster3d.cu
 struct BlendOpts3 {
-    float cutoff2, alpha_min, alpha_max, T_min;
+    float cutoff2, lim, alpha_min, alpha_max, T_min;
     float bg[3];
 };
-void launch_blend3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
-                    int H, int tiles_x, int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last,
-                    cudaStream_t stream);
-void launch_backward3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges,
-                       int W, int H, int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final,
-                       const uint32_t* last, const float* dl_dout, float* grad_img, cudaStream_t stream);
+void launch_blend3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                    int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last, cudaStream_t stream);
+void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                       int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
+                       const float* dl_dout, float* grad_img, cudaStream_t stream);
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 

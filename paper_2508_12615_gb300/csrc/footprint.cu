@@ -33,9 +33,15 @@ __device__ __forceinline__ PixRect covered_pixels(float mx, float my, float ex, 
     return r;
 }
 
-__device__ __forceinline__ uint32_t tile_count(const PixRect& r) {
+// Number of tiles of the covered pixel range that the cutoff ellipse reaches (tile_touched()).
+__device__ __forceinline__ uint32_t tile_count(float mx, float my, float l11, float l21, float l22, const PixRect& r,
+                                               float lim) {
     if (r.u0 > r.u1) return 0u;
-    return (uint32_t)((r.u1 / kTile - r.u0 / kTile + 1) * (r.v1 / kTile - r.v0 / kTile + 1));
+    const Ellipse k = make_ellipse(mx, my, l11, l21, l22);
+    uint32_t n = 0;
+    for (int ty = r.v0 / kTile; ty <= r.v1 / kTile; ++ty)
+        for (int tx = r.u0 / kTile; tx <= r.u1 / kTile; ++tx) n += tile_touched(k, r, tx, ty, lim);
+    return n;
 }
 
 __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rect, uint32_t* counts,
@@ -51,8 +57,8 @@ __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rec
 // 2D: Sigma = R(theta) diag(sx^2, sy^2) R(theta)^T; Sigma^-1 = R diag(1/sx^2, 1/sy^2) R^T.
 // Cholesky of Sigma^-1: l11 = sqrt(A), l21 = B / l11, l22 = sqrt(det)/l11 = 1 / (sx sy l11).
 __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ params, int64_t N, int W, int H,
-                                                     float cutoff, float4* __restrict__ rec, PixRect* __restrict__ rect,
-                                                     uint32_t* __restrict__ counts) {
+                                                     float cutoff, float lim, float4* __restrict__ rec,
+                                                     PixRect* __restrict__ rect, uint32_t* __restrict__ counts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float4 p0 = params[i * 4 + 0];  // mu_x mu_y s_x s_y
@@ -84,7 +90,7 @@ __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ 
     rec[i * kRecF4 + 2] = make_float4(p2.x, p2.y, p2.z, 1.0f);
     rec[i * kRecF4 + 3] = make_float4(ex, ey, 0.0f, 0.0f);
     rect[i] = r;
-    counts[i] = tile_count(r);
+    counts[i] = tile_count(mx, my, l11, l21, l22, r, lim);
 }
 
 struct Cam {
@@ -99,7 +105,7 @@ struct Cam {
 // Frequency: fc = V f, f' = (fc_x tz / fx, fc_y tz / fy) (phase gradient on the fronto-parallel
 // plane through the centre; the viewing-axis component is dropped, Sec. 4.1).
 __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ params, int64_t N, Cam cam, int W,
-                                                     int H, float cutoff, float dil, float4* __restrict__ rec,
+                                                     int H, float cutoff, float lim, float dil, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts,
                                                      uint32_t* __restrict__ depth_keys) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     rec[i * kRecF4 + 2] = make_float4(p[15], p[16], p[17], p[14]);
     rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, 0.0f);
     rect[i] = rr;
-    counts[i] = tile_count(rr);
+    counts[i] = tile_count(mx, my, l11, l21, l22, rr, lim);
     depth_keys[i] = __float_as_uint(tz);
 }
 
@@ -233,7 +239,7 @@ void launch_footprint2d(const float* params, int64_t N, int W, int H, float cuto
                         uint32_t* counts, uint32_t* /*depth_keys*/, cudaStream_t stream) {
     if (N == 0) return;
     k_footprint2d<<<ceil_div(N, 256), 256, 0, stream>>>(reinterpret_cast<const float4*>(params), N, W, H, cutoff,
-                                                         rec, rect, counts); count_launches(1);
+                                                         touch_limit(cutoff), rec, rect, counts); count_launches(1);
 }
 
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
@@ -243,8 +249,8 @@ void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam,
     Cam c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
-    k_footprint3d<<<ceil_div(N, 256), 256, 0, stream>>>(params, N, c, W, H, cutoff, dilation, rec, rect, counts,
-                                                         depth_keys); count_launches(1);
+    k_footprint3d<<<ceil_div(N, 256), 256, 0, stream>>>(params, N, c, W, H, cutoff, touch_limit(cutoff), dilation,
+                                                         rec, rect, counts, depth_keys); count_launches(1);
 }
 
 void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream) {

@@ -4,24 +4,34 @@
 // Forward: one 256-thread block per 16x16 tile, one pixel per thread; the tile's primitives are
 // staged through shared memory in batches of 256.  Backward: the field is a plain sum, so the
 // gradient of each (tile, primitive) pair is independent of every other pair; one warp takes one
-// pair, walks the pixels of the primitive's covered range inside the tile, reduces its partial
-// gradient in registers and writes it to the pair's emission slot.  A second kernel sums the
-// slots of each primitive (contiguous in emission order) and chains them to the record's
-// parameters: deterministic, no atomics.
+// pair, walks the pixels of the cutoff ellipse inside the tile, reduces its partial gradient in
+// registers and writes it to the pair's emission slot.  A second kernel sums the slots of each
+// primitive (contiguous in emission order) and chains them to the record's parameters:
+// deterministic, no atomics.
 #include "common.cuh"
 
 namespace wipes {
 namespace {
 
+// Stage one tile-list entry: its record and, in `mask`, the warp sub-tiles its ellipse reaches.
+__device__ __forceinline__ uint32_t stage_entry(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
+                                                const TileLists& tl, uint32_t i, int x0, int y0, float lim,
+                                                float4& A, float4& B, float4& C) {
+    const uint32_t prim = tl.inst_prim[tl.sorted[i]];
+    A = rec[(size_t)prim * kRecF4 + 0];
+    B = rec[(size_t)prim * kRecF4 + 1];
+    C = rec[(size_t)prim * kRecF4 + 2];
+    return subtile_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+}
+
 // Forward.  Warp w of the tile's block owns an 8x4 pixel sub-tile (two columns of sub-tiles by
 // four rows).  When a batch of the tile list is staged, each thread marks which sub-tiles its
-// primitive's covered pixel range touches; a warp then visits only the primitives marked for it.
-// The covered range holds every pixel that passes the cutoff, so skipping is exact.
+// primitive's cutoff ellipse reaches; a warp then visits only the primitives marked for it.  The
+// test is conservative (rect_touched), so skipping is exact.
 __global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restrict__ rec,
-                                                         const PixRect* __restrict__ rect,
-                                                         const uint32_t* __restrict__ sorted_prims,
-                                                         const uint2* __restrict__ ranges, int W, int H, int tiles_x,
-                                                         float cutoff2, float* __restrict__ out) {
+                                                         const PixRect* __restrict__ rect, TileLists tl, int W, int H,
+                                                         int tiles_x, float cutoff2, float lim,
+                                                         float* __restrict__ out) {
     __shared__ float4 s_a[kTilePixels];  // mx my l11 l21
     __shared__ float4 s_b[kTilePixels];  // l22 fx fy phc
     __shared__ float4 s_c[kTilePixels];  // c_r c_g c_b o
@@ -33,17 +43,17 @@ __global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restric
     const int u = x0 + (warp & 1) * 8 + (lane & 7);
     const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-    const uint2 range = ranges[tile];
+    const uint2 range = tl.ranges[tile];
     float c0 = 0.f, c1 = 0.f, c2 = 0.f;
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         __syncthreads();
         if ((int)threadIdx.x < n) {
-            const uint32_t id = sorted_prims[b0 + threadIdx.x];
-            s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
-            s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
-            s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)subtile_mask(rect[id], x0, y0);
+            float4 A, B, C;
+            s_mask[threadIdx.x] = (uint8_t)stage_entry(rec, rect, tl, b0 + threadIdx.x, x0, y0, lim, A, B, C);
+            s_a[threadIdx.x] = A;
+            s_b[threadIdx.x] = B;
+            s_c[threadIdx.x] = C;
         }
         __syncthreads();
         // two-level summation: a batch-local partial sum per channel, added once per batch
@@ -84,26 +94,25 @@ __global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restric
 // Partial gradient slot layout (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b 0
 constexpr int kSlot = 12;
 
-// Backward.  The tile's dL/dimage sits in shared memory; batches of the tile list are staged
-// with each pair's pixel range inside the tile and its emission slot.  One warp takes one pair at
-// a time and walks the pixels of that range.  Per pixel inside the cutoff it accumulates the
-// factored sums  sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy,
-// sum g W  (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
+// Backward.  The tile's dL/dimage sits in shared memory; batches of the tile list are staged with
+// the mask of the 8x4 sub-blocks of the tile that each pair's cutoff ellipse reaches (the same
+// decomposition as the forward pass).  One warp takes one pair at a time and walks the marked
+// sub-blocks, one pixel per lane.  Per pixel inside the cutoff a lane accumulates the factored sums
+//   sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy, sum g W
+// (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
 // b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one warp
 // reduction, since L, f and the centre are constant over the pair.
 __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __restrict__ rec,
-                                                            const PixRect* __restrict__ rect,
-                                                            const uint32_t* __restrict__ offsets,
-                                                            const uint32_t* __restrict__ sorted_prims,
-                                                            const uint2* __restrict__ ranges, int W, int H, int tiles_x,
-                                                            float cutoff2, const float* __restrict__ dl_dout,
+                                                            const PixRect* __restrict__ rect, TileLists tl, int W,
+                                                            int H, int tiles_x, float cutoff2, float lim,
+                                                            const float* __restrict__ dl_dout,
                                                             float* __restrict__ partial) {
     __shared__ float s_g[kTilePixels * 3];
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
     __shared__ float4 s_c[kTilePixels];
-    __shared__ int4 s_reg[kTilePixels];    // ux0, vy0, width, area (pixels of the pair inside the tile)
     __shared__ uint32_t s_slot[kTilePixels];
+    __shared__ uint8_t s_mask[kTilePixels];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile;
@@ -117,37 +126,35 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
         s_g[threadIdx.x * 3 + 1] = in ? g[1] : 0.f;
         s_g[threadIdx.x * 3 + 2] = in ? g[2] : 0.f;
     }
-    const uint2 range = ranges[tile];
+    const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         __syncthreads();
         if ((int)threadIdx.x < n) {
-            const uint32_t prim = sorted_prims[b0 + threadIdx.x];
-            s_a[threadIdx.x] = rec[(size_t)prim * kRecF4 + 0];
-            s_b[threadIdx.x] = rec[(size_t)prim * kRecF4 + 1];
+            const uint32_t e = tl.sorted[b0 + threadIdx.x];
+            const uint32_t prim = tl.inst_prim[e];
+            const float4 A = rec[(size_t)prim * kRecF4 + 0];
+            const float4 B = rec[(size_t)prim * kRecF4 + 1];
+            s_a[threadIdx.x] = A;
+            s_b[threadIdx.x] = B;
             s_c[threadIdx.x] = rec[(size_t)prim * kRecF4 + 2];
-            const PixRect r = rect[prim];
-            const int ux0 = max(r.u0, x0), ux1 = min(r.u1, x0 + kTile - 1);
-            const int vy0 = max(r.v0, y0), vy1 = min(r.v1, y0 + kTile - 1);
-            const int w = ux1 - ux0 + 1;
-            s_reg[threadIdx.x] = make_int4(ux0, vy0, w, w * (vy1 - vy0 + 1));
-            s_slot[threadIdx.x] = offsets[prim] + (uint32_t)((ty - r.v0 / kTile) * (r.u1 / kTile - r.u0 / kTile + 1) +
-                                                             (tx - r.u0 / kTile));
+            s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+            s_slot[threadIdx.x] = e;
         }
         __syncthreads();
         for (int j = warp; j < n; j += kTilePixels / 32) {
             const float4 A = s_a[j];  // mx my l11 l21
             const float4 B = s_b[j];  // l22 fx fy phc
             const float4 C = s_c[j];
-            const int4 reg = s_reg[j];
-            const uint32_t mdiv = (65536u + (uint32_t)reg.z - 1u) / (uint32_t)reg.z;  // exact k / w for k < 256
+            uint32_t mask = s_mask[j];
             float acc[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-            for (int k = lane; k < reg.w; k += 32) {
-                const int lv = (int)(((uint32_t)k * mdiv) >> 16);
-                const int u = reg.x + (k - lv * reg.z), v = reg.y + lv;
-                const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+            while (mask) {
+                const int sb = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int lu = (sb & 1) * 8 + (lane & 7), lv = (sb >> 1) * 4 + (lane >> 3);
+                const float px = (float)(x0 + lu) + 0.5f, py = (float)(y0 + lv) + 0.5f;
                 // the cutoff test in the same operation order as mahalanobis2()
                 const float dx = __fsub_rn(px, A.x), dy = __fsub_rn(py, A.y);
                 const float a = __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy));
@@ -158,9 +165,9 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
                     const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
                     const float cs = cos_approx(ang), sn = sin_approx(ang);
                     const float Wv = fmaf(0.5f, cs, 0.5f) * G;
-                    const float* g = s_g + ((v - y0) * kTile + (u - x0)) * 3;
+                    const float* g = s_g + (lv * kTile + lu) * 3;
                     const float gW = fmaf(g[0], C.x, fmaf(g[1], C.y, g[2] * C.z));
-                    const float gq2 = -gW * Wv;           // 2 dL/dq  (dW/dq = -W/2)
+                    const float gq2 = -gW * Wv;               // 2 dL/dq  (dW/dq = -W/2)
                     const float gt = (-kPi * G) * (gW * sn);  // dL/dt, t in cycles
                     const float ga = gq2 * a, gb = gq2 * b;
                     acc[0] += ga;
@@ -262,10 +269,8 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
 }
 
 // Visited and inside-cutoff (pixel, primitive) pairs over the sorted tile lists.
-__global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __restrict__ rec,
-                                                             const uint32_t* __restrict__ sorted_prims,
-                                                             const uint2* __restrict__ ranges, int W, int H,
-                                                             int tiles_x, float cutoff2,
+__global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __restrict__ rec, TileLists tl, int W,
+                                                             int H, int tiles_x, float cutoff2,
                                                              unsigned long long* __restrict__ counters) {
     __shared__ unsigned long long s_sum[2];
     const int tile = blockIdx.x;
@@ -274,13 +279,13 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
     const int v = ty * kTile + (threadIdx.x / kTile);
     const bool in = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-    const uint2 range = ranges[tile];
+    const uint2 range = tl.ranges[tile];
     unsigned long long inside = 0;
     if (threadIdx.x < 2) s_sum[threadIdx.x] = 0ull;
     __syncthreads();
     if (in) {
         for (uint32_t i = range.x; i < range.y; ++i) {
-            const uint32_t id = sorted_prims[i];
+            const uint32_t id = tl.inst_prim[tl.sorted[i]];
             const float4 A = rec[(size_t)id * kRecF4 + 0];
             const float l22 = rec[(size_t)id * kRecF4 + 1].x;
             inside += mahalanobis2(px, py, A.x, A.y, A.z, A.w, l22) <= cutoff2;
@@ -297,29 +302,31 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
 
 }  // namespace
 
-void launch_blend2d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
-                    int H, int tiles_x, int tiles_y, float cutoff2, float* out, cudaStream_t stream) {
-    k_blend2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, sorted_prims, ranges, W, H, tiles_x, cutoff2,
-                                                              out); count_launches(1);
+void launch_blend2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                    int tiles_y, float cutoff, float* out, cudaStream_t stream) {
+    k_blend2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, cutoff * cutoff,
+                                                              touch_limit(cutoff), out);
+    count_launches(1);
 }
 
-void launch_backward2d(const float4* rec, const PixRect* rect, const uint32_t* offsets, const uint32_t* sorted_prims,
-                       const uint2* ranges, int W, int H, int tiles_x, int tiles_y, float cutoff2,
-                       const float* dl_dout, float* partial, cudaStream_t stream) {
-    k_backward2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, offsets, sorted_prims, ranges, W, H,
-                                                                 tiles_x, cutoff2, dl_dout, partial); count_launches(1);
+void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                       int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream) {
+    k_backward2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, cutoff * cutoff,
+                                                                 touch_limit(cutoff), dl_dout, partial);
+    count_launches(1);
 }
 
-void launch_count_pairs(const float4* rec, const uint32_t* sorted_prims, const uint2* ranges, int W, int H,
-                        int tiles_x, int tiles_y, float cutoff2, unsigned long long* counters, cudaStream_t stream) {
-    k_count_pairs<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, sorted_prims, ranges, W, H, tiles_x, cutoff2,
-                                                                  counters); count_launches(1);
+void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
+                        unsigned long long* counters, cudaStream_t stream) {
+    k_count_pairs<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, tl, W, H, tiles_x, cutoff2, counters);
+    count_launches(1);
 }
 
 void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
-    k_reduce_chain2d<<<ceil_div(N * 32, 256), 256, 0, stream>>>(params, N, offsets, counts, partial, dl_dparams); count_launches(1);
+    k_reduce_chain2d<<<ceil_div(N * 32, 256), 256, 0, stream>>>(params, N, offsets, counts, partial, dl_dparams);
+    count_launches(1);
 }
 
 }  // namespace wipes

@@ -15,10 +15,8 @@ namespace {
 // whose covered pixel range touches it; positions in the tile list are counted from the list
 // start, so the per-pixel last-contributor index does not depend on the culling.
 __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restrict__ rec,
-                                                         const PixRect* __restrict__ rect,
-                                                         const uint32_t* __restrict__ sorted_prims,
-                                                         const uint2* __restrict__ ranges, int W, int H, int tiles_x,
-                                                         BlendOpts3 o, float* __restrict__ out,
+                                                         const PixRect* __restrict__ rect, TileLists tl, int W, int H,
+                                                         int tiles_x, BlendOpts3 o, float* __restrict__ out,
                                                          float* __restrict__ T_final, uint32_t* __restrict__ last) {
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
@@ -32,7 +30,7 @@ __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restric
     const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-    const uint2 range = ranges[tile];
+    const uint2 range = tl.ranges[tile];
     bool done = !inside;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
     uint32_t last_contrib = 0;
@@ -40,11 +38,13 @@ __global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restric
         if (__syncthreads_count(done) == kTilePixels) break;
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         if ((int)threadIdx.x < n) {
-            const uint32_t id = sorted_prims[b0 + threadIdx.x];
-            s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
-            s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
+            const uint32_t id = tl.inst_prim[tl.sorted[b0 + threadIdx.x]];
+            const float4 A = rec[(size_t)id * kRecF4 + 0];
+            const float4 B = rec[(size_t)id * kRecF4 + 1];
+            s_a[threadIdx.x] = A;
+            s_b[threadIdx.x] = B;
             s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)subtile_mask(rect[id], x0, y0);
+            s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[id], x0, y0, o.lim);
         }
         __syncthreads();
         for (int c = 0; c < n; c += 32) {
@@ -95,10 +95,9 @@ constexpr int kG = 12;
 // gradients of one primitive are summed by a reduce-scatter and added to the primitive's
 // image-plane gradient with one atomic per component.
 __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __restrict__ rec,
-                                                            const PixRect* __restrict__ rect,
-                                                            const uint32_t* __restrict__ sorted_prims,
-                                                            const uint2* __restrict__ ranges, int W, int H, int tiles_x,
-                                                            BlendOpts3 o, const float* __restrict__ T_final,
+                                                            const PixRect* __restrict__ rect, TileLists tl, int W,
+                                                            int H, int tiles_x, BlendOpts3 o,
+                                                            const float* __restrict__ T_final,
                                                             const uint32_t* __restrict__ last,
                                                             const float* __restrict__ dl_dout,
                                                             float* __restrict__ grad_img) {
@@ -116,7 +115,7 @@ __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __rest
     const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
     const bool inside = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-    const uint2 range = ranges[tile];
+    const uint2 range = tl.ranges[tile];
     const size_t pix = (size_t)v * W + u;
     float T = inside ? T_final[pix] : 1.f;
     const uint32_t my_last = inside ? last[pix] : 0u;
@@ -134,12 +133,14 @@ __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __rest
         const int n = (int)((uint32_t)b_end - b0);
         __syncthreads();
         if ((int)threadIdx.x < n) {
-            const uint32_t id = sorted_prims[b0 + threadIdx.x];
+            const uint32_t id = tl.inst_prim[tl.sorted[b0 + threadIdx.x]];
+            const float4 A = rec[(size_t)id * kRecF4 + 0];
+            const float4 B = rec[(size_t)id * kRecF4 + 1];
             s_id[threadIdx.x] = id;
-            s_a[threadIdx.x] = rec[(size_t)id * kRecF4 + 0];
-            s_b[threadIdx.x] = rec[(size_t)id * kRecF4 + 1];
+            s_a[threadIdx.x] = A;
+            s_b[threadIdx.x] = B;
             s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)subtile_mask(rect[id], x0, y0);
+            s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[id], x0, y0, o.lim);
         }
         __syncthreads();
         for (int c = (n - 1) & ~31; c >= 0; c -= 32) {
@@ -373,19 +374,16 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
 
 }  // namespace
 
-void launch_blend3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges, int W,
-                    int H, int tiles_x, int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last,
-                    cudaStream_t stream) {
-    k_blend3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, sorted_prims, ranges, W, H, tiles_x, o, out,
-                                                              T_final,
+void launch_blend3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                    int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last, cudaStream_t stream) {
+    k_blend3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, o, out, T_final,
                                                               last); count_launches(1);
 }
 
-void launch_backward3d(const float4* rec, const PixRect* rect, const uint32_t* sorted_prims, const uint2* ranges,
-                       int W, int H, int tiles_x, int tiles_y, const BlendOpts3& o, const float* T_final,
-                       const uint32_t* last, const float* dl_dout, float* grad_img, cudaStream_t stream) {
-    k_backward3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, sorted_prims, ranges, W, H, tiles_x, o,
-                                                                 T_final,
+void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
+                       int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
+                       const float* dl_dout, float* grad_img, cudaStream_t stream) {
+    k_backward3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, o, T_final,
                                                                  last, dl_dout, grad_img); count_launches(1);
 }
 

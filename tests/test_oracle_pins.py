@@ -352,17 +352,18 @@ def test_grad3d_matches_central_differences():
 @pytest.mark.parametrize("dims,scale", [(2, (1.0, 16.0)), (2, (0.5, 32.0)), (3, None)])
 def test_cutoff_ellipse_inside_covered_range(dims, scale):
     """Tile culling loses nothing: every pixel that passes the binary32 3-sigma test lies inside the
-    primitive's covered pixel range, including very elongated primitives (scale ratio up to 64)."""
+    primitive's covered pixel range and in a tile (and a one-pixel rectangle) that the ellipse test
+    accepts, including very elongated primitives (scale ratio up to 64)."""
     if dims == 2:
         H, W = 128, 160
         p = synth.scene2d(1500, H, W, 7, scale)
-        inside, outside, rect = oracle.cutoff_coverage(2, p, H, W)
+        inside, outside, rect, dropped = oracle.cutoff_coverage(2, p, H, W)
     else:
         H, W = 96, 112
         p = synth.scene3d(2500, 8)
         cam = synth.sphere_cameras(1, H, W, 9)[0]
-        inside, outside, rect = oracle.cutoff_coverage(3, p, H, W, cam)
-    assert inside > 0 and outside == 0 and rect >= inside
+        inside, outside, rect, dropped = oracle.cutoff_coverage(3, p, H, W, cam)
+    assert inside > 0 and outside == 0 and dropped == 0 and rect >= inside
 
 
 @pytest.mark.parametrize("dims", [2, 3])
@@ -398,8 +399,9 @@ def test_footprint_matches_binary64_projection(dims):
 
 @pytest.mark.parametrize("dims", [2, 3])
 def test_tile_lists_enumerate_covered_tiles_in_order(dims):
-    """The sorted lists hold exactly the tiles each covered pixel range touches, ordered by tile,
-    then camera depth (3D), then primitive index."""
+    """The sorted lists are ordered by tile, then camera depth (3D), then primitive index; every
+    listed tile lies in the primitive's covered pixel range, and every tile holding a pixel well
+    inside the cutoff ellipse (binary64 q <= 9 (1 - 1e-4)) is listed."""
     H, W = 72, 88
     if dims == 2:
         p = synth.scene2d(120, H, W, 17, (1.0, 12.0))
@@ -409,20 +411,37 @@ def test_tile_lists_enumerate_covered_tiles_in_order(dims):
         cam = synth.sphere_cameras(1, H, W, 19)[0]
     rec, rect, valid = oracle.footprints(dims, p, H, W, cam)
     tiles, prims = oracle.tile_lists(dims, p, H, W, cam)
-    tx = (W + 15) // 16
-    expect = []
-    for i in range(len(p)):
+    ntx = (W + 15) // 16
+    depth = rec[:, 7].view(np.uint32) if dims == 3 else np.zeros(len(p), np.uint32)
+    keys = [(int(t), int(depth[i]), int(i)) for t, i in zip(tiles, prims)]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    listed = set((int(t), int(i)) for t, i in zip(tiles, prims))
+    for t, i in listed:
         u0, v0, u1, v1 = rect[i]
-        if not valid[i] or u0 > u1:
+        assert valid[i] and u0 // 16 <= t % ntx <= u1 // 16 and v0 // 16 <= t // ntx <= v1 // 16
+    # binary64 inverse covariance per primitive
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    if dims == 3:
+        pr = oracle.project3d(p, cam, H, W)
+    must = 0
+    for i in range(len(p)):
+        if not valid[i]:
             continue
-        depth = rec[i, 7].view(np.uint32) if dims == 3 else 0
-        for ty in range(v0 // 16, v1 // 16 + 1):
-            for tx_ in range(u0 // 16, u1 // 16 + 1):
-                expect.append((ty * tx + tx_, int(depth), i))
-    expect.sort()
-    assert len(expect) == len(tiles)
-    assert [e[0] for e in expect] == tiles.tolist()
-    assert [e[2] for e in expect] == prims.tolist()
+        if dims == 2:
+            c, sn = math.cos(p[i, 4]), math.sin(p[i, 4])
+            R = np.array([[c, -sn], [sn, c]])
+            K = np.linalg.inv(R @ np.diag(p[i, 2:4].astype(np.float64) ** 2) @ R.T)
+            mu = p[i, :2].astype(np.float64)
+        else:
+            K = np.linalg.inv(np.array([[pr[i, 4], pr[i, 5]], [pr[i, 5], pr[i, 6]]]))
+            mu = pr[i, 2:4]
+        dx, dy = xx - mu[0], yy - mu[1]
+        q = K[0, 0] * dx * dx + 2 * K[0, 1] * dx * dy + K[1, 1] * dy * dy
+        vv, uu = np.nonzero(q <= 9.0 * (1 - 1e-4))
+        for t in set((vv // 16) * ntx + uu // 16):
+            must += 1
+            assert (int(t), i) in listed
+    assert must > 0 and len(listed) >= must
 
 
 # ---------------------------------------------------------------------------------------------
