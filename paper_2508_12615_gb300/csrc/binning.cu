@@ -73,21 +73,14 @@ __global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long
     if (threadIdx.x == 0) *total_out = carry;
 }
 
-// Emission.  The block first scans the tile counts of its 1024 scan positions; then each warp
-// takes one primitive at a time and its 32 lanes test 32 tiles of the primitive's covered range
-// at once, writing the touched ones contiguously (ballot + population count), in row-major tile
-// order.  This keeps the large primitives from serialising on one thread.
-__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ counts,
-                                                   const uint32_t* __restrict__ perm, int64_t n,
-                                                   const float4* __restrict__ rec, const PixRect* __restrict__ rect,
-                                                   const unsigned long long* __restrict__ block_offsets, int tiles_x,
-                                                   float lim, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                   uint32_t* __restrict__ inst_prim, uint32_t* __restrict__ offsets) {
+// First instance index of every primitive: the block-local exclusive scan of the tile counts of
+// its 1024 scan positions plus the block's offset.
+__global__ void __launch_bounds__(kThreads) k_scan_offsets(const uint32_t* __restrict__ counts,
+                                                           const uint32_t* __restrict__ perm, int64_t n,
+                                                           const unsigned long long* __restrict__ block_offsets,
+                                                           uint32_t* __restrict__ offsets) {
     __shared__ unsigned long long s_warp[kWarps];
-    __shared__ uint32_t s_prim[kScanBlockElems];
-    __shared__ uint32_t s_off[kScanBlockElems];
-    const int64_t blk = (int64_t)blockIdx.x * kScanBlockElems;
-    const int64_t base = blk + threadIdx.x * kScanItems;
+    const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
     uint32_t prim[kScanItems], cnt[kScanItems];
     unsigned long long s = 0;
 #pragma unroll
@@ -100,37 +93,43 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
     unsigned long long off = block_offsets[blockIdx.x] + block_exclusive_scan<unsigned long long>(s, nullptr, s_warp);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int local = threadIdx.x * kScanItems + k;
-        s_prim[local] = cnt[k] ? prim[k] : 0xFFFFFFFFu;
-        s_off[local] = (uint32_t)off;
         if (base + k < n) offsets[prim[k]] = (uint32_t)off;
         off += cnt[k];
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int m = (int)min((int64_t)kScanBlockElems, n - blk);
-    for (int j = warp; j < m; j += kWarps) {
-        const uint32_t p = s_prim[j];
-        if (p == 0xFFFFFFFFu) continue;
-        const PixRect r = rect[p];
-        const float4 A = rec[(size_t)p * kRecF4 + 0];
-        const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
-        const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
-        const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
-        uint32_t o = s_off[j];
-        for (int t0 = 0; t0 < nt; t0 += 32) {
-            const int t = t0 + lane;
-            const int ty = ty0 + t / nx, tx = tx0 + t % nx;
-            const bool hit = t < nt && tile_touched(e, r, tx, ty, lim);
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const uint32_t w = o + __popc(bal & ((1u << lane) - 1u));
-                keys[w] = (uint32_t)(ty * tiles_x + tx);
-                vals[w] = w;
-                inst_prim[w] = p;
-            }
-            o += __popc(bal);
+}
+
+// Emission, one warp per scan position: the 32 lanes test 32 tiles of the primitive's covered
+// range at a time and write the touched ones contiguously (ballot + population count), in
+// row-major tile order starting at the primitive's offset.
+__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ counts,
+                                                   const uint32_t* __restrict__ perm, int64_t n,
+                                                   const float4* __restrict__ rec, const PixRect* __restrict__ rect,
+                                                   const uint32_t* __restrict__ offsets, int tiles_x, float lim,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   uint32_t* __restrict__ inst_prim) {
+    const int64_t j = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const uint32_t p = perm ? perm[j] : (uint32_t)j;
+    if (counts[p] == 0u) return;
+    const PixRect r = rect[p];
+    const float4 A = rec[(size_t)p * kRecF4 + 0];
+    const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
+    const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
+    const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
+    uint32_t o = offsets[p];
+    for (int t0 = 0; t0 < nt; t0 += 32) {
+        const int t = t0 + lane;
+        const int ty = ty0 + t / nx, tx = tx0 + t % nx;
+        const bool hit = t < nt && tile_touched(e, r, tx, ty, lim);
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const uint32_t w = o + __popc(bal & ((1u << lane) - 1u));
+            keys[w] = (uint32_t)(ty * tiles_x + tx);
+            vals[w] = w;
+            inst_prim[w] = p;
         }
+        o += __popc(bal);
     }
 }
 
@@ -305,9 +304,10 @@ void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const 
                  const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
                  uint32_t* inst_prim, uint32_t* offsets, cudaStream_t stream) {
     if (n == 0) return;
-    k_emit<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, rec, rect, block_offsets, tiles_x,
-                                                                  lim, keys, vals, inst_prim, offsets);
-    count_launches(1);
+    k_scan_offsets<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, block_offsets, offsets);
+    k_emit<<<ceil_div(n * 32, kThreads), kThreads, 0, stream>>>(counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
+                                                                vals, inst_prim);
+    count_launches(2);
 }
 
 void launch_gather_u32(uint32_t* out, const uint32_t* table, const uint32_t* idx, int64_t n, cudaStream_t stream) {

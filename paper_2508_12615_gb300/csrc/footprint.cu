@@ -33,15 +33,42 @@ __device__ __forceinline__ PixRect covered_pixels(float mx, float my, float ex, 
     return r;
 }
 
-// Number of tiles of the covered pixel range that the cutoff ellipse reaches (tile_touched()).
-__device__ __forceinline__ uint32_t tile_count(float mx, float my, float l11, float l21, float l22, const PixRect& r,
-                                               float lim) {
-    if (r.u0 > r.u1) return 0u;
-    const Ellipse k = make_ellipse(mx, my, l11, l21, l22);
-    uint32_t n = 0;
-    for (int ty = r.v0 / kTile; ty <= r.v1 / kTile; ++ty)
-        for (int tx = r.u0 / kTile; tx <= r.u1 / kTile; ++tx) n += tile_touched(k, r, tx, ty, lim);
-    return n;
+// Number of tiles of each lane's covered pixel range that its cutoff ellipse reaches
+// (tile_touched()), computed by the whole warp: for each lane's primitive in turn, the 32 lanes
+// test 32 tiles at a time.  Every lane of the warp must call it; an empty range counts 0.
+__device__ __forceinline__ uint32_t warp_tile_counts(float mx, float my, float l11, float l21, float l22,
+                                                     const PixRect& r, float lim) {
+    const int lane = threadIdx.x & 31;
+    Ellipse mine;
+    if (r.u0 <= r.u1) mine = make_ellipse(mx, my, l11, l21, l22);
+    else mine = make_ellipse(0.f, 0.f, 1.f, 0.f, 1.f);
+    uint32_t result = 0;
+    for (int k = 0; k < 32; ++k) {
+        PixRect rk;
+        rk.u0 = __shfl_sync(0xffffffffu, r.u0, k);
+        rk.u1 = __shfl_sync(0xffffffffu, r.u1, k);
+        rk.v0 = __shfl_sync(0xffffffffu, r.v0, k);
+        rk.v1 = __shfl_sync(0xffffffffu, r.v1, k);
+        if (rk.u0 > rk.u1) continue;  // uniform across the warp
+        Ellipse e;
+        e.mx = __shfl_sync(0xffffffffu, mine.mx, k);
+        e.my = __shfl_sync(0xffffffffu, mine.my, k);
+        e.l11 = __shfl_sync(0xffffffffu, mine.l11, k);
+        e.l21 = __shfl_sync(0xffffffffu, mine.l21, k);
+        e.l22 = __shfl_sync(0xffffffffu, mine.l22, k);
+        e.rBA = __shfl_sync(0xffffffffu, mine.rBA, k);
+        e.rBC = __shfl_sync(0xffffffffu, mine.rBC, k);
+        const int tx0 = rk.u0 / kTile, ty0 = rk.v0 / kTile;
+        const int nx = rk.u1 / kTile - tx0 + 1, nt = nx * (rk.v1 / kTile - ty0 + 1);
+        uint32_t c = 0;
+        for (int t0 = 0; t0 < nt; t0 += 32) {
+            const int t = t0 + lane;
+            const bool hit = t < nt && tile_touched(e, rk, tx0 + t % nx, ty0 + t / nx, lim);
+            c += __popc(__ballot_sync(0xffffffffu, hit));
+        }
+        if (lane == k) result = c;
+    }
+    return result;
 }
 
 __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rect, uint32_t* counts,
@@ -59,8 +86,9 @@ __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rec
 __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ params, int64_t N, int W, int H,
                                                      float cutoff, float lim, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < N;
+    const int64_t i = live ? i0 : N - 1;  // lanes past the end repeat the last primitive, write nothing
     const float4 p0 = params[i * 4 + 0];  // mu_x mu_y s_x s_y
     const float4 p1 = params[i * 4 + 1];  // theta f_x f_y phi
     const float4 p2 = params[i * 4 + 2];  // c_r c_g c_b -
@@ -83,14 +111,18 @@ __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ 
     const float ey = (cutoff * sqrtf(vyy)) * kExtMargin;
     const bool valid = finite4(mx, my, l11, l21) && finite4(l22, ex, ey, 1.0f) && sx > 0.0f && sy > 0.0f &&
                        l11 > 0.0f && l22 > 0.0f;
+    PixRect r;
+    r.u0 = 1; r.u1 = 0; r.v0 = 1; r.v1 = 0;
+    if (valid && live) r = covered_pixels(mx, my, ex, ey, W, H);
+    const uint32_t cnt = warp_tile_counts(mx, my, l11, l21, l22, r, lim);
+    if (!live) return;
     if (!valid) { write_empty(i, rec, rect, counts, nullptr); return; }
-    const PixRect r = covered_pixels(mx, my, ex, ey, W, H);
     rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
     rec[i * kRecF4 + 1] = make_float4(l22, p1.y, p1.z, p1.w * kInvTwoPi);
     rec[i * kRecF4 + 2] = make_float4(p2.x, p2.y, p2.z, 1.0f);
     rec[i * kRecF4 + 3] = make_float4(ex, ey, 0.0f, 0.0f);
     rect[i] = r;
-    counts[i] = tile_count(mx, my, l11, l21, l22, r, lim);
+    counts[i] = cnt;
 }
 
 struct Cam {
@@ -108,8 +140,9 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
                                                      int H, float cutoff, float lim, float dil, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts,
                                                      uint32_t* __restrict__ depth_keys) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < N;
+    const int64_t i = live ? i0 : N - 1;  // lanes past the end repeat the last primitive, write nothing
     const float4* pp = reinterpret_cast<const float4*>(params + i * WIPES_P3D);
     const float4 a0 = pp[0], a1 = pp[1], a2 = pp[2], a3 = pp[3], a4 = pp[4];
     float p[20] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y,
@@ -118,10 +151,7 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     const float tx = ((V[0] * p[0] + V[1] * p[1]) + V[2] * p[2]) + V[3];
     const float ty = ((V[4] * p[0] + V[5] * p[1]) + V[6] * p[2]) + V[7];
     const float tz = ((V[8] * p[0] + V[9] * p[1]) + V[10] * p[2]) + V[11];
-    if (!(tz > cam.near_z) || !isfinite(tz) || !isfinite(tx) || !isfinite(ty)) {
-        write_empty(i, rec, rect, counts, depth_keys);
-        return;
-    }
+    const bool in_front = tz > cam.near_z && isfinite(tz) && isfinite(tx) && isfinite(ty);
     float qw = p[6], qx = p[7], qy = p[8], qz = p[9];
     const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
     const float r = sqrtf(n2);
@@ -171,19 +201,23 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     const float my = ((cam.fy * ty) / tz) + cam.cy;
     const float ex = (cutoff * sqrtf(S00)) * kExtMargin;
     const float ey = (cutoff * sqrtf(S11)) * kExtMargin;
-    const bool valid = finite4(mx, my, l11, l21) && finite4(l22, ex, ey, D) && D > 0.0f && S11 > 0.0f &&
+    const bool valid = in_front && finite4(mx, my, l11, l21) && finite4(l22, ex, ey, D) && D > 0.0f && S11 > 0.0f &&
                        l11 > 0.0f && l22 > 0.0f;
+    PixRect rr;
+    rr.u0 = 1; rr.u1 = 0; rr.v0 = 1; rr.v1 = 0;
+    if (valid && live) rr = covered_pixels(mx, my, ex, ey, W, H);
+    const uint32_t cnt = warp_tile_counts(mx, my, l11, l21, l22, rr, lim);
+    if (!live) return;
     if (!valid) { write_empty(i, rec, rect, counts, depth_keys); return; }
     // projected frequency (not part of any integer decision)
     const float fcx = (V[0] * p[10] + V[1] * p[11]) + V[2] * p[12];
     const float fcy = (V[4] * p[10] + V[5] * p[11]) + V[6] * p[12];
-    const PixRect rr = covered_pixels(mx, my, ex, ey, W, H);
     rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
     rec[i * kRecF4 + 1] = make_float4(l22, fcx * tz / cam.fx, fcy * tz / cam.fy, p[13] * kInvTwoPi);
     rec[i * kRecF4 + 2] = make_float4(p[15], p[16], p[17], p[14]);
     rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, 0.0f);
     rect[i] = rr;
-    counts[i] = tile_count(mx, my, l11, l21, l22, rr, lim);
+    counts[i] = cnt;
     depth_keys[i] = __float_as_uint(tz);
 }
 

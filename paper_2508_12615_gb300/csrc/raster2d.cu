@@ -212,9 +212,9 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     const int lane = threadIdx.x & 31;
     if (prim >= N) return;
     const uint32_t off = offsets[prim], cnt = counts[prim];
-    float acc[11];
+    float acc[16];
 #pragma unroll
-    for (int k = 0; k < 11; ++k) acc[k] = 0.f;
+    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
     for (uint32_t j = lane; j < cnt; j += 32) {
         const float4* s = reinterpret_cast<const float4*>(partial + (size_t)(off + j) * kSlot);
         const float4 x0 = s[0], x1 = s[1], x2 = s[2];
@@ -222,10 +222,10 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
         acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
         acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z;
     }
+    // lane 2m holds the total of slot m; gather them on lane 0
+    const float tot = warp_reduce_scatter16(acc);
 #pragma unroll
-    for (int k = 0; k < 11; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    for (int k = 0; k < 11; ++k) acc[k] = __shfl_sync(0xffffffffu, tot, 2 * k);
     if (lane != 0) return;
     const float* p = params + prim * WIPES_P2D;
     float* out = dl_dparams + prim * WIPES_P2D;
