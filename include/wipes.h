@@ -125,6 +125,19 @@ wipes_status wipes_deform6d_backward(const float* params6, int64_t N, float t, c
 wipes_status wipes_l2_loss(wipes_ctx* ctx, const float* img, const float* target, int64_t n, float* loss,
                            float* dL_dimg, void* stream);
 
+/* The same loss without allocating device memory (the paper has no counterpart; this serves
+ * callers that cannot call cudaMalloc: work recorded into a CUDA graph, code whose allocator owns
+ * all device memory, hosts that forbid allocation after start-up).  Runs on the calling thread's
+ * current device and needs no context.  Its scratch is a fixed 256 KB array inside the library's
+ * device image (one partial sum per 4096 elements), held by every GPU that loads the library until
+ * the process exits.  Limits: 1 <= n <= 268,435,456 (65,536 x 4,096); larger n returns
+ * WIPES_ERR_INVALID.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls on a device
+ * share the array: calls that overlap on the GPU race.  Each call writes every partial sum before
+ * reading it, so the array needs no clearing. */
+wipes_status wipes_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* loss, float* dL_dimg,
+                                   void* stream);
+
 /* Introspection of the last forward pass on a state (host-side values). */
 typedef struct {
     int32_t dims;          /* 2, 3, or 0 if no forward pass */

@@ -53,6 +53,7 @@ _SIGNATURES = {
     "wipes_deform6d": (c_int, [_P, c_int64, c_float, _P, _P]),
     "wipes_deform6d_backward": (c_int, [_P, c_int64, c_float, _P, _P, c_int, _P]),
     "wipes_l2_loss": (c_int, [_P, _P, _P, c_int64, _P, _P, _P]),
+    "wipes_l2_loss_noalloc": (c_int, [_P, _P, c_int64, _P, _P, _P]),
     "wipes_state_get_info": (c_int, [_P, _P]),
     "wipes_state_copy_lists": (c_int, [_P, _P, _P, _P, _P]),
     "wipes_state_copy_pixel_state": (c_int, [_P, _P, _P, _P]),

@@ -475,6 +475,19 @@ wipes_status wipes_l2_loss(wipes_ctx* ctx, const float* img, const float* target
     return WIPES_OK;
 }
 
+wipes_status wipes_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* loss, float* dL_dimg,
+                                   void* stream) {
+    if (!img || !target || !loss || !dL_dimg) return fail(WIPES_ERR_INVALID, "null argument");
+    const int64_t max_n = l2_loss_noalloc_max_elements();
+    if (n < 1 || n > max_n)
+        return fail(WIPES_ERR_INVALID, "wipes_l2_loss_noalloc: n = " + std::to_string(n) + " is outside 1.." +
+                                           std::to_string(max_n) + " (the fixed scratch holds one partial sum per " +
+                                           "4096 elements, 65536 partial sums)");
+    cudaError_t e = l2_loss_noalloc(img, target, n, loss, dL_dimg, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(WIPES_ERR_CUDA, std::string("wipes_l2_loss_noalloc: ") + cudaGetErrorString(e));
+    return WIPES_OK;
+}
+
 wipes_status wipes_state_get_info(const wipes_state* st, wipes_state_info* info) {
     if (!st || !info) return fail(WIPES_ERR_INVALID, "null argument");
     info->dims = st->dims;

@@ -261,6 +261,11 @@ void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& 
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 
+// loss_noalloc.cu: the same loss with its scratch in a file-scope device array (no allocation)
+int64_t l2_loss_noalloc_max_elements();
+cudaError_t l2_loss_noalloc(const float* img, const float* target, int64_t n, float* loss, float* grad,
+                            cudaStream_t stream);
+
 // loss.cu
 void launch_l2_loss(const float* img, const float* target, int64_t n, float* loss, float* grad, float* partials,
                     cudaStream_t stream);
