@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -33,7 +35,10 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 # FP32-pipe operations (an FMA counts as one) and MUFU operations per (pixel, primitive) pair inside
 # the cutoff ellipse, as the oracle's definition requires them (counted in the design notes).
-OPS_PER_PAIR = {"blend": (19, 2), "bwd_raster": (42, 3)}
+OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend": (25, 2), "bwd_raster": (55, 3)}}
+# DRAM bytes (read + write) per launch from the ncu capture summarised in profiles/, for the kernel
+# build measured there; None when the kernel has changed since.
+TRAFFIC_BYTES = {"k_backward2d": None, "k_blend2d": None}
 
 
 def parse_args():
@@ -42,6 +47,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["2d", "5d", "6d"], default="2d",
+                    help="2d: the 768x512 / 70k image-fitting workload (default, the headline); "
+                         "5d: 800x800 / 300k static scene; 6d: 1352x1014 / 200k dynamic scene, 4 samples per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU work budget of the oracle baseline")
     return ap.parse_args()
@@ -189,12 +197,119 @@ def reference_arm(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+class Workload:
+    """One benchmark workload: inputs resident on the device, a fwd+bwd step, a forward-only
+    pass, and an end-to-end step from pinned host buffers."""
+
+    def __init__(self, kind: str, dev):
+        import torch
+
+        import paper_2508_12615_gb300 as w
+        import synth
+
+        self.kind, self.dev, self.w = kind, dev, w
+        ctx = w.Context.get(dev.index)
+        self.ctx = ctx
+        self.st = w.State(ctx)
+        if kind == "2d":
+            c = synth.CFG1_2D_KODAK
+            p, target = synth.cfg1_inputs()
+            self.name, self.H, self.W, self.seed = WORKLOAD, c.H, c.W, c.seed
+            self.samples = [None]
+            self.opts = w.make_opts(2)
+        elif kind == "5d":
+            c = synth.CFG2_5D
+            p, cams = synth.cfg2_inputs()
+            target = synth.target_noise_edges(c.H, c.W, c.seed + 200)
+            self.name, self.H, self.W, self.seed = "5d_static_800x800_n300000", c.H, c.W, c.seed
+            self.cams = cams
+            self.samples = [(k, None) for k in range(len(cams))]
+            self.opts = w.make_opts(3)
+        else:
+            c = synth.CFG3_6D
+            p, cams, times = synth.cfg3_inputs()
+            target = synth.target_noise_edges(c.H, c.W, c.seed + 200)
+            self.name, self.H, self.W, self.seed = "6d_dynamic_1352x1014_n200000_batch4", c.H, c.W, c.seed
+            self.cams, self.times = cams, times
+            rng = np.random.default_rng(c.seed + 300)
+            self.samples = [(int(rng.integers(len(cams))), float(times[rng.integers(len(times))])) for _ in range(64)]
+            self.opts = w.make_opts(3)
+        self.p, self.target = p, target
+        self.params = torch.from_numpy(p).to(dev)
+        self.target_d = torch.from_numpy(target).to(dev)
+        self.img = torch.empty(self.H, self.W, 3, device=dev)
+        self.gimg = torch.empty_like(self.img)
+        self.loss = torch.empty((), device=dev)
+        self.grad = torch.empty_like(self.params)
+        if kind == "6d":
+            self.p3 = torch.empty(p.shape[0], 20, device=dev)
+            self.g3 = torch.empty_like(self.p3)
+        self.batch = 4 if kind == "6d" else 1
+        self.k = 0
+        self.pixels_per_step = self.H * self.W * self.batch
+
+    def _sample(self):
+        s = self.samples[self.k % len(self.samples)]
+        self.k += 1
+        return s
+
+    def _one(self, params, target, accumulate=False, fwd_only=False):
+        w = self.w
+        if self.kind == "2d":
+            w.forward2d(params, self.H, self.W, self.opts, state=self.st, out=self.img)
+            if fwd_only:
+                return
+            w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
+            w.backward(self.st, params, self.gimg, out=self.grad)
+            return
+        cam_i, t = self._sample()
+        cam = self.cams[cam_i]
+        if self.kind == "5d":
+            w.forward3d(params, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
+            if fwd_only:
+                return
+            w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
+            w.backward(self.st, params, self.gimg, out=self.grad)
+            return
+        from paper_2508_12615_gb300 import _abi
+        from paper_2508_12615_gb300.render import _ptr, _stream
+
+        n = params.shape[0]
+        _abi.call("wipes_deform6d", _ptr(params), n, t, _ptr(self.p3), _stream(self.dev))
+        w.forward3d(self.p3, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
+        if fwd_only:
+            return
+        w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
+        w.backward(self.st, self.p3, self.gimg, out=self.g3)
+        _abi.call("wipes_deform6d_backward", _ptr(params), n, t, _ptr(self.g3), _ptr(self.grad), int(accumulate),
+                  _stream(self.dev))
+
+    def step(self, params=None, target=None):
+        params = self.params if params is None else params
+        target = self.target_d if target is None else target
+        for b in range(self.batch):
+            self._one(params, target, accumulate=b > 0)
+
+    def forward(self):
+        for b in range(self.batch):
+            self._one(self.params, self.target_d, fwd_only=True)
+
+    def count_pairs(self):
+        import torch
+
+        from paper_2508_12615_gb300 import _abi
+
+        self.k = 0
+        self._one(self.params, self.target_d, fwd_only=True)
+        visited, inside = ctypes.c_int64(), ctypes.c_int64()
+        _abi.call("wipes_state_count_pairs", self.ctx.handle, self.st.handle, ctypes.byref(visited),
+                  ctypes.byref(inside), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        return visited.value * self.batch, inside.value * self.batch, self.st.info()["n_instances"] * self.batch
+
+
 def our_arm(args, rank: int, world: int, local_rank: int):
-    import numpy as np
     import torch
 
-    import paper_2508_12615_gb300 as w
-    import synth
     from paper_2508_12615_gb300 import _abi, build
 
     dist = None
@@ -205,31 +320,16 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     lib = _abi.lib()
-
-    c = synth.CFG1_2D_KODAK
-    H, W = c.H, c.W
-    p, target = synth.cfg1_inputs()
-    params = torch.from_numpy(p).to(dev)
-    target_d = torch.from_numpy(target).to(dev)
-    ctx = w.Context.get(local_rank)
-    st = w.State(ctx)
-    img = torch.empty(H, W, 3, device=dev)
-    gimg = torch.empty_like(img)
-    loss = torch.empty((), device=dev)
-    grad = torch.empty_like(params)
+    wl = Workload(args.workload, dev)
+    ctx = wl.ctx
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB of L2
-
-    def step():
-        w.forward2d(params, H, W, state=st, out=img)
-        w.l2_loss(img, target_d, loss=loss, grad=gimg)
-        w.backward(st, params, gimg, out=grad)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
     for _ in range(max(3, args.warmup)):
-        step()
+        wl.step()
     torch.cuda.synchronize()
 
     # fwd+bwd steps, L2 flushed before each, each step bracketed by CUDA events
@@ -246,7 +346,7 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
-        step()
+        wl.step()
         ev[k][1].record()
     torch.cuda.synchronize()
     barrier()
@@ -270,19 +370,19 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     for k in range(args.steps):
         flush.zero_()
         fwd_ev[k][0].record()
-        w.forward2d(params, H, W, state=st, out=img)
+        wl.forward()
         fwd_ev[k][1].record()
     torch.cuda.synchronize()
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in fwd_ev)
 
     # end to end through the public API with host buffers: parameters and target in from pinned
     # host memory, gradient and loss back to pinned host memory, every step
-    p_host = torch.from_numpy(p).pin_memory()
-    t_host = torch.from_numpy(target).pin_memory()
+    p_host = torch.from_numpy(wl.p).pin_memory()
+    t_host = torch.from_numpy(wl.target).pin_memory()
     g_host = torch.empty_like(p_host).pin_memory()
     l_host = torch.empty((), dtype=torch.float32).pin_memory()
-    e2e_params = torch.empty_like(params)
-    e2e_target = torch.empty_like(target_d)
+    e2e_params = torch.empty_like(wl.params)
+    e2e_target = torch.empty_like(wl.target_d)
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for k in range(args.steps):
@@ -290,11 +390,9 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         e_ev[k][0].record()
         e2e_params.copy_(p_host, non_blocking=True)
         e2e_target.copy_(t_host, non_blocking=True)
-        w.forward2d(e2e_params, H, W, state=st, out=img)
-        w.l2_loss(img, e2e_target, loss=loss, grad=gimg)
-        w.backward(st, e2e_params, gimg, out=grad)
-        g_host.copy_(grad, non_blocking=True)
-        l_host.copy_(loss, non_blocking=True)
+        wl.step(e2e_params, e2e_target)
+        g_host.copy_(wl.grad, non_blocking=True)
+        l_host.copy_(wl.loss, non_blocking=True)
         e_ev[k][1].record()
         torch.cuda.current_stream().synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
@@ -308,44 +406,48 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         return
 
     # work counts and the roofline of the dominant kernel
-    w.forward2d(params, H, W, state=st, out=img)
-    visited, inside = ctypes.c_int64(), ctypes.c_int64()
-    _abi.call("wipes_state_count_pairs", ctx.handle, st.handle, ctypes.byref(visited), ctypes.byref(inside),
-              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    info = st.info()
+    visited, inside, instances = wl.count_pairs()
     stages = {name: {"ms_per_launch": (stage_ms[i] / stage_n[i]) if stage_n[i] else None, "launches": int(stage_n[i])}
               for i, name in enumerate(_abi.STAGES) if stage_n[i]}
     dom = max(("blend", "bwd_raster"), key=lambda s: stages[s]["ms_per_launch"])
     pk, pk_kind = peaks()
     clock_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tops = SMS * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
-    fp32_ops, mufu_ops = OPS_PER_PAIR[dom]
-    achieved = inside.value * fp32_ops / (stages[dom]["ms_per_launch"] * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_blend2d" if dom == "blend" else "k_backward2d", "achieved": achieved,
-                "peak": peak_tops, "unit": "Tops/s", "frac": achieved / peak_tops, "traffic": None,
+    dims = "2d" if wl.kind == "2d" else "3d"
+    fp32_ops, mufu_ops = OPS_PER_PAIR[dims][dom]
+    launch_s = stages[dom]["ms_per_launch"] * 1e-3
+    pairs_per_launch = inside / wl.batch
+    achieved = pairs_per_launch * fp32_ops / launch_s / 1e12
+    kernel = {"2d": {"blend": "k_blend2d", "bwd_raster": "k_backward2d"},
+              "3d": {"blend": "k_blend3d", "bwd_raster": "k_backward3d"}}[dims][dom]
+    traffic = TRAFFIC_BYTES.get(kernel) if wl.kind == "2d" else None
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": traffic,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz ({pk_kind} max SM clock)",
-                "work": f"{inside.value} pairs inside the cutoff x {fp32_ops} FP32 + {mufu_ops} MUFU ops",
-                "mufu_frac": inside.value * mufu_ops / (stages[dom]["ms_per_launch"] * 1e-3) /
-                (SMS * 16 * clock_mhz * 1e6)}
+                "work": f"{pairs_per_launch:.0f} pairs inside the cutoff per launch x {fp32_ops} FP32 + "
+                        f"{mufu_ops} MUFU ops",
+                "mufu_frac": pairs_per_launch * mufu_ops / launch_s / (SMS * 16 * clock_mhz * 1e6)}
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        per_step, desc = oracle_step_sample(p, target, H, W, args.cpu_seconds)
+    if world == 1 and not args.no_cpu_baseline and wl.kind == "2d":
+        per_step, desc = oracle_step_sample(wl.p, wl.target, wl.H, wl.W, args.cpu_seconds)
         cpu = {"value": 1.0 / per_step, "unit": "iter/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc}
 
+    n_h2d = int(wl.p.nbytes + wl.target.nbytes)
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": H, "W": W, "primitives": int(p.shape[0]), "seed": c.seed,
-                   "l2": "flushed before every timed step (512 MB write)", "replicas": world},
-        "fwd_mpix_s": H * W / (fwd_ms * 1e-3) / 1e6 * world,
+        "config": {"workload": wl.name, "H": wl.H, "W": wl.W, "primitives": int(wl.p.shape[0]), "seed": wl.seed,
+                   "samples_per_step": wl.batch, "l2": "flushed before every timed step (512 MB write)",
+                   "replicas": world},
+        "fwd_mpix_s": wl.pixels_per_step / (fwd_ms * 1e-3) / 1e6 * world,
         "fwd_ms": fwd_ms,
-        "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": int(p.nbytes + target.nbytes),
-                "d2h_bytes_per_step": int(p.nbytes + 4)},
+        "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": n_h2d,
+                "d2h_bytes_per_step": int(wl.p.nbytes + 4)},
         "gpu_launches": int(launches),
         "stages_ms": {k: v["ms_per_launch"] for k, v in stages.items()},
-        "pairs": {"visited": visited.value, "inside": inside.value, "instances": info["n_instances"]},
+        "pairs": {"visited": visited, "inside": inside, "instances": instances},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -160,8 +160,8 @@ wipes_status wipes_state_copy_pixel_state(const wipes_state* st, float* T_final,
 
 /* Count, over the sorted tile lists of the last forward pass, the (pixel, primitive) pairs a
  * kernel visits (pixel inside the image, primitive in the pixel's tile list) and the pairs inside
- * the cutoff ellipse (the terms of the sums of Eq. 3 / Eq. 4 before any 3D early stop).
- * Synchronises `stream`; results are host values. */
+ * the cutoff ellipse (the terms of the sum of Eq. 4; in 3D the entries of Eq. 3 up to each pixel's
+ * last contributor).  Synchronises `stream`; results are host values. */
 wipes_status wipes_state_count_pairs(wipes_ctx* ctx, const wipes_state* st, int64_t* visited, int64_t* inside,
                                      void* stream);
 

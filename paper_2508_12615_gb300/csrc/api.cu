@@ -537,7 +537,8 @@ wipes_status wipes_state_count_pairs(wipes_ctx* ctx, const wipes_state* st, int6
     cudaStream_t s = (cudaStream_t)stream;
     WIPES_CUDA(cudaMemsetAsync(ctx->d_counters, 0, sizeof(unsigned long long) * 2, s));
     launch_count_pairs(st->rec.as<float4>(), st->lists(), st->W, st->H, st->tiles_x, st->tiles_y,
-                       st->opts.cutoff_sigma * st->opts.cutoff_sigma, ctx->d_counters, s);
+                       st->opts.cutoff_sigma * st->opts.cutoff_sigma,
+                       st->dims == 3 ? st->last.as<uint32_t>() : nullptr, ctx->d_counters, s);
     unsigned long long h[2] = {0, 0};
     WIPES_CUDA(cudaMemcpyAsync(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost, s));
     WIPES_CUDA(cudaStreamSynchronize(s));

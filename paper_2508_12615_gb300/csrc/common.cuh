@@ -246,7 +246,7 @@ void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offse
                            const float* partial, float* dl_dparams, cudaStream_t stream);
 // counters[0] += visited pairs, counters[1] += pairs inside the cutoff ellipse
 void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
-                        unsigned long long* counters, cudaStream_t stream);
+                        const uint32_t* last, unsigned long long* counters, cudaStream_t stream);
 
 // raster3d.cu
 struct BlendOpts3 {

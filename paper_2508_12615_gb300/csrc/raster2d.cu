@@ -102,12 +102,12 @@ constexpr int kSlot = 12;
 // (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
 // b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one warp
 // reduction, since L, f and the centre are constant over the pair.
-__global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
                                                             int H, int tiles_x, float cutoff2, float lim,
                                                             const float* __restrict__ dl_dout,
                                                             float* __restrict__ partial) {
-    __shared__ float s_g[kTilePixels * 3];
+    __shared__ float4 s_g[kTilePixels];  // dL/dimage of the tile, one float4 per pixel (w unused)
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
     __shared__ float4 s_c[kTilePixels];
@@ -122,10 +122,11 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
         const int v = y0 + (threadIdx.x / kTile);
         const bool in = u < W && v < H;
         const float* g = dl_dout + ((size_t)v * W + u) * 3;
-        s_g[threadIdx.x * 3 + 0] = in ? g[0] : 0.f;
-        s_g[threadIdx.x * 3 + 1] = in ? g[1] : 0.f;
-        s_g[threadIdx.x * 3 + 2] = in ? g[2] : 0.f;
+        s_g[threadIdx.x] = in ? make_float4(g[0], g[1], g[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    // per-lane pixel of sub-block 0 (sub-block sb adds 8 (sb & 1) columns and 4 (sb >> 1) rows)
+    const float lane_px = (float)(x0 + (lane & 7)) + 0.5f, lane_py = (float)(y0 + (lane >> 3)) + 0.5f;
+    const int lane_g = (lane >> 3) * kTile + (lane & 7);
     const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
@@ -153,8 +154,8 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
             while (mask) {
                 const int sb = __ffs(mask) - 1;
                 mask &= mask - 1u;
-                const int lu = (sb & 1) * 8 + (lane & 7), lv = (sb >> 1) * 4 + (lane >> 3);
-                const float px = (float)(x0 + lu) + 0.5f, py = (float)(y0 + lv) + 0.5f;
+                // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
+                const float px = lane_px + (float)((sb & 1) * 8), py = lane_py + (float)((sb >> 1) * 4);
                 // the cutoff test in the same operation order as mahalanobis2()
                 const float dx = __fsub_rn(px, A.x), dy = __fsub_rn(py, A.y);
                 const float a = __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy));
@@ -165,8 +166,8 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
                     const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
                     const float cs = cos_approx(ang), sn = sin_approx(ang);
                     const float Wv = fmaf(0.5f, cs, 0.5f) * G;
-                    const float* g = s_g + (lv * kTile + lu) * 3;
-                    const float gW = fmaf(g[0], C.x, fmaf(g[1], C.y, g[2] * C.z));
+                    const float4 g = s_g[lane_g + (sb >> 1) * 4 * kTile + (sb & 1) * 8];
+                    const float gW = fmaf(g.x, C.x, fmaf(g.y, C.y, g.z * C.z));
                     const float gq2 = -gW * Wv;               // 2 dL/dq  (dW/dq = -W/2)
                     const float gt = (-kPi * G) * (gW * sn);  // dL/dt, t in cycles
                     const float ga = gq2 * a, gb = gq2 * b;
@@ -178,9 +179,9 @@ __global__ void __launch_bounds__(kTilePixels) k_backward2d(const float4* __rest
                     acc[5] = fmaf(gb, dy, acc[5]);
                     acc[6] = fmaf(gt, dx, acc[6]);
                     acc[7] = fmaf(gt, dy, acc[7]);
-                    acc[8] = fmaf(g[0], Wv, acc[8]);
-                    acc[9] = fmaf(g[1], Wv, acc[9]);
-                    acc[10] = fmaf(g[2], Wv, acc[10]);
+                    acc[8] = fmaf(g.x, Wv, acc[8]);
+                    acc[9] = fmaf(g.y, Wv, acc[9]);
+                    acc[10] = fmaf(g.z, Wv, acc[10]);
                 }
             }
             // lane l holds the total of sum (l >> 1); lane l < 12 writes slot l of the pair
@@ -268,9 +269,11 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     for (int k = 11; k < WIPES_P2D; ++k) out[k] = 0.f;
 }
 
-// Visited and inside-cutoff (pixel, primitive) pairs over the sorted tile lists.
+// Visited and inside-cutoff (pixel, primitive) pairs over the sorted tile lists; with `last`
+// (3D), only list entries up to each pixel's last contributor count.
 __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __restrict__ rec, TileLists tl, int W,
                                                              int H, int tiles_x, float cutoff2,
+                                                             const uint32_t* __restrict__ last,
                                                              unsigned long long* __restrict__ counters) {
     __shared__ unsigned long long s_sum[2];
     const int tile = blockIdx.x;
@@ -284,13 +287,14 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
     if (threadIdx.x < 2) s_sum[threadIdx.x] = 0ull;
     __syncthreads();
     if (in) {
-        for (uint32_t i = range.x; i < range.y; ++i) {
+        const uint32_t end = last ? range.x + last[(size_t)v * W + u] : range.y;
+        for (uint32_t i = range.x; i < end; ++i) {
             const uint32_t id = tl.inst_prim[tl.sorted[i]];
             const float4 A = rec[(size_t)id * kRecF4 + 0];
             const float l22 = rec[(size_t)id * kRecF4 + 1].x;
             inside += mahalanobis2(px, py, A.x, A.y, A.z, A.w, l22) <= cutoff2;
         }
-        atomicAdd(&s_sum[0], (unsigned long long)(range.y - range.x));
+        atomicAdd(&s_sum[0], (unsigned long long)(end - range.x));
         atomicAdd(&s_sum[1], inside);
     }
     __syncthreads();
@@ -317,8 +321,8 @@ void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& 
 }
 
 void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
-                        unsigned long long* counters, cudaStream_t stream) {
-    k_count_pairs<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, tl, W, H, tiles_x, cutoff2, counters);
+                        const uint32_t* last, unsigned long long* counters, cudaStream_t stream) {
+    k_count_pairs<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, tl, W, H, tiles_x, cutoff2, last, counters);
     count_launches(1);
 }
 
