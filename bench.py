@@ -51,6 +51,8 @@ def parse_args():
                     help="2d: the 768x512 / 70k image-fitting workload (default, the headline); "
                          "5d: 800x800 / 300k static scene; 6d: 1352x1014 / 200k dynamic scene, 4 samples per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-seconds", type=float, default=10.0, help="length of the serving request trace")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU work budget of the oracle baseline")
     return ap.parse_args()
 
@@ -433,6 +435,10 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         per_step, desc = oracle_step_sample(wl.p, wl.target, wl.H, wl.W, args.cpu_seconds)
         cpu = {"value": 1.0 / per_step, "unit": "iter/s", "cores": cpu_cores(), "kind": "oracle", "sample": desc}
 
+    serving = None
+    if world == 1 and not args.no_serving and wl.kind == "2d":
+        serving = serving_run(args, dev)
+
     n_h2d = int(wl.p.nbytes + wl.target.nbytes)
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
@@ -450,10 +456,32 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         "pairs": {"visited": visited, "inside": inside, "instances": instances},
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "serving": serving,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def serving_run(args, dev):
+    """64 resident scenes (2D and 3D, 10k-500k primitives), Poisson arrivals at 2000 requests/s,
+    image sizes uniform over 256^2, 512^2, 800^2 and 1920x1080, HBM budget 120 GB: p50/p99 latency
+    and Mpix/s of the continuous-batching server and of the plain one-request-at-a-time path on the
+    same trace."""
+    import synth
+    from paper_2508_12615_gb300.serve import Server
+
+    t = time.perf_counter()
+    scenes, reqs = synth.serving_workload(n_scenes=64, rate=2000.0, seconds=args.serving_seconds)
+    gen_s = time.perf_counter() - t
+    srv = Server(scenes, device=dev.index, hbm_budget=120e9, max_batch=128, n_streams=2)
+    srv.run_batched(reqs[: min(len(reqs), 200)])  # warm the allocator and the kernels
+    srv = Server(scenes, device=dev.index, hbm_budget=120e9, max_batch=128, n_streams=2)
+    batched = srv.run_batched(reqs).summary()
+    plain = srv.run_plain(reqs).summary()
+    return {"workload": f"64 scenes 10k-500k prims (2D:3D 1:1), Poisson 2000 req/s for {args.serving_seconds:g} s, "
+                        "sizes {256^2, 512^2, 800^2, 1920x1080}, HBM budget 120 GB",
+            "requests": int(len(reqs)), "batched": batched, "plain": plain, "scene_generation_s": gen_s}
 
 
 def main():

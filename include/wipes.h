@@ -83,6 +83,8 @@ void wipes_default_opts(int dims, wipes_opts* out);
 
 /* Create a context on CUDA device `device`.  Errors: INVALID (bad device), CUDA. */
 wipes_status wipes_create(int device, wipes_ctx** out);
+/* Destroy a context; fails with WIPES_ERR_INVALID (and destroys nothing) while states created on
+ * it are alive. */
 wipes_status wipes_destroy(wipes_ctx* ctx);
 
 /* A state holds the device workspace of one forward pass (projected records, sorted tile lists,
@@ -103,6 +105,21 @@ wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params
 wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N,
                             const wipes_camera* cam, int H, int W, const wipes_opts* opts, float* out,
                             void* stream);
+
+/* The forward passes split in two for batching: wipes_prepare2d/3d run everything but the blend
+ * (projection, footprints, tile binning, sort) into `st`; wipes_blend_batch then renders any number
+ * of prepared states, of any mix of 2D and 3D frames and image sizes, in persistent launches
+ * (up to 128 frames per launch): every block takes (frame, tile) items from a device counter.  A
+ * frame renders to the same bits alone (wipes_render2d/3d = prepare + one-frame blend) and in a
+ * batch, because both paths run the same per-tile code.  A state stays valid for further blends and
+ * for wipes_render_backward until it is prepared again; outs[i] is [H_i, W_i, 3] device memory.
+ * At most 64 batch launches may be in flight on one context. */
+wipes_status wipes_prepare2d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, int H, int W,
+                             const wipes_opts* opts, void* stream);
+wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N,
+                             const wipes_camera* cam, int H, int W, const wipes_opts* opts, void* stream);
+wipes_status wipes_blend_batch(wipes_ctx* ctx, const wipes_state* const* states, float* const* outs, int n,
+                               void* stream);
 
 /* Backward of the last forward pass on `st` (explicit gradients, Sec. 1).
  *   params: the same [N,16|20] array the forward pass read, unchanged since.
@@ -184,6 +201,12 @@ enum {
 };
 wipes_status wipes_set_timing(wipes_ctx* ctx, int enable);
 wipes_status wipes_get_timing(wipes_ctx* ctx, double* ms, int64_t* brackets, int reset);
+
+/* Device memory of a context's workspaces (all its states).  With a limit set (bytes > 0; 0 removes
+ * it), a call that would grow the workspaces past the limit fails with WIPES_ERR_OOM before
+ * allocating; the caller can free states and retry.  Reserved bytes count every state buffer. */
+wipes_status wipes_set_memory_limit(wipes_ctx* ctx, int64_t bytes);
+wipes_status wipes_get_memory_reserved(wipes_ctx* ctx, int64_t* bytes);
 
 /* Number of kernels this library has launched since it was loaded (all contexts, all threads). */
 int64_t wipes_kernel_launches(void);

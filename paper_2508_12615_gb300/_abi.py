@@ -50,6 +50,9 @@ _SIGNATURES = {
     "wipes_render2d": (c_int, [_P, _P, _P, c_int64, c_int, c_int, _P, _P, _P]),
     "wipes_render3d": (c_int, [_P, _P, _P, c_int64, _P, c_int, c_int, _P, _P, _P]),
     "wipes_render_backward": (c_int, [_P, _P, _P, _P, _P, _P]),
+    "wipes_prepare2d": (c_int, [_P, _P, _P, c_int64, c_int, c_int, _P, _P]),
+    "wipes_prepare3d": (c_int, [_P, _P, _P, c_int64, _P, c_int, c_int, _P, _P]),
+    "wipes_blend_batch": (c_int, [_P, _P, _P, c_int, _P]),
     "wipes_deform6d": (c_int, [_P, c_int64, c_float, _P, _P]),
     "wipes_deform6d_backward": (c_int, [_P, c_int64, c_float, _P, _P, c_int, _P]),
     "wipes_l2_loss": (c_int, [_P, _P, _P, c_int64, _P, _P, _P]),
@@ -64,6 +67,8 @@ _SIGNATURES = {
     "wipes_set_timing": (c_int, [_P, c_int]),
     "wipes_get_timing": (c_int, [_P, _P, _P, c_int]),
     "wipes_kernel_launches": (c_int64, []),
+    "wipes_set_memory_limit": (c_int, [_P, c_int64]),
+    "wipes_get_memory_reserved": (c_int, [_P, _P]),
 }
 
 STAGES = ["footprint", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend", "bwd_raster", "bwd_chain", "loss"]

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libwipes.so")
 
-SOURCES = ["footprint.cu", "binning.cu", "raster2d.cu", "raster3d.cu", "loss.cu", "loss_noalloc.cu", "api.cu"]
+SOURCES = ["footprint.cu", "binning.cu", "raster2d.cu", "raster3d.cu", "loss.cu", "loss_noalloc.cu", "batch.cu", "api.cu"]
 # The footprint kernels take every integer decision (tile coverage, cutoff, depth order) from
 # binary32 values that must be reproducible operation by operation: no fused multiply-add there.
 PER_FILE_FLAGS = {"footprint.cu": ["-fmad=false"]}

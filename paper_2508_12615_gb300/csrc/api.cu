@@ -36,20 +36,37 @@ wipes_status fail(wipes_status s, const std::string& msg) {
         if (s_ != WIPES_OK) return s_;    \
     } while (0)
 
-// Grow-only device buffer.
+// Device bytes held by the workspaces of one context, and the optional limit on them.
+struct MemAccount {
+    std::atomic<int64_t> reserved{0};
+    std::atomic<int64_t> limit{0};  // 0: no limit
+};
+
+// Grow-only device buffer, accounted to its context.
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
+    MemAccount* acct = nullptr;
     template <typename T>
     T* as() const { return static_cast<T*>(p); }
 };
 
 wipes_status ensure(DevBuf& b, size_t bytes) {
     if (bytes <= b.cap) return WIPES_OK;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    const int64_t limit = b.acct ? b.acct->limit.load() : 0;
+    if (limit > 0 && b.acct->reserved.load() - (int64_t)b.cap + (int64_t)want > limit) {
+        // a tighter request that still fits the limit is taken without headroom
+        want = bytes;
+        if (b.acct->reserved.load() - (int64_t)b.cap + (int64_t)want > limit)
+            return fail(WIPES_ERR_OOM, "workspace memory limit of " + std::to_string(limit) + " bytes reached (" +
+                                           std::to_string(b.acct->reserved.load()) + " reserved, " +
+                                           std::to_string(want) + " more wanted)");
+    }
     if (b.p) cudaFree(b.p);
+    if (b.acct) b.acct->reserved -= (int64_t)b.cap;
     b.p = nullptr;
     b.cap = 0;
-    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -57,11 +74,13 @@ wipes_status ensure(DevBuf& b, size_t bytes) {
         return fail(WIPES_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed: " + cudaGetErrorString(e));
     }
     b.cap = want;
+    if (b.acct) b.acct->reserved += (int64_t)want;
     return WIPES_OK;
 }
 
 void release(DevBuf& b) {
     if (b.p) cudaFree(b.p);
+    if (b.acct) b.acct->reserved -= (int64_t)b.cap;
     b.p = nullptr;
     b.cap = 0;
 }
@@ -87,15 +106,22 @@ struct DeviceGuard {
 
 std::atomic<int64_t> g_launches{0};
 
+// Batch launches in flight on one context use distinct work counters, taken round-robin.
+constexpr unsigned int kBatchCounterSlots = 64;
+
 }  // namespace
 
 void wipes::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct wipes_ctx {
     int device = 0;
+    MemAccount mem;
+    std::atomic<int64_t> live_states{0};  // a context is not destroyed while states refer to it
     unsigned long long* h_total = nullptr;  // pinned readback of the instance count
     float* d_loss_partials = nullptr;
     unsigned long long* d_counters = nullptr;  // pair counters
+    unsigned int* d_batch_counters = nullptr;  // work counters of in-flight batch launches (a ring)
+    unsigned int batch_slot = 0;
     // stage timing
     bool timing = false;
     struct Bracket {
@@ -172,6 +198,7 @@ struct wipes_state {
         t.ranges = ranges.as<uint2>();
         return t;
     }
+    BlendJob job(float* out) const;
 };
 
 namespace {
@@ -250,6 +277,28 @@ wipes_status prepare_state(wipes_state* st, int dims, int64_t N, int H, int W, c
     return WIPES_OK;
 }
 
+BlendOpts3 blend_opts(const wipes_opts& o);
+
+}  // namespace
+
+BlendJob wipes_state::job(float* out) const {
+    BlendJob j;
+    j.rec = rec.as<float4>();
+    j.rect = rect.as<PixRect>();
+    j.tl = lists();
+    j.out = out;
+    j.T_final = T_final.as<float>();
+    j.last = last.as<uint32_t>();
+    j.dims = dims;
+    j.W = W;
+    j.H = H;
+    j.tiles_x = tiles_x;
+    j.o = blend_opts(opts);
+    return j;
+}
+
+namespace {
+
 BlendOpts3 blend_opts(const wipes_opts& o) {
     BlendOpts3 b;
     b.cutoff2 = o.cutoff_sigma * o.cutoff_sigma;
@@ -301,6 +350,7 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     cudaError_t e = cudaMallocHost(&c->h_total, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_loss_partials, sizeof(float) * kLossBlocks);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_batch_counters, sizeof(unsigned int) * kBatchCounterSlots);
     if (e != cudaSuccess) {
         if (c->h_total) cudaFreeHost(c->h_total);
         delete c;
@@ -312,6 +362,9 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
 
 wipes_status wipes_destroy(wipes_ctx* ctx) {
     if (!ctx) return WIPES_OK;
+    if (ctx->live_states.load() != 0)
+        return fail(WIPES_ERR_INVALID, "wipes_destroy: " + std::to_string(ctx->live_states.load()) +
+                                           " states of this context are still alive");
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     for (auto& b : ctx->pending) {
@@ -322,6 +375,7 @@ wipes_status wipes_destroy(wipes_ctx* ctx) {
     cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_loss_partials);
     cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_batch_counters);
     delete ctx;
     return WIPES_OK;
 }
@@ -330,21 +384,27 @@ wipes_status wipes_state_create(wipes_ctx* ctx, wipes_state** out) {
     if (!ctx || !out) return fail(WIPES_ERR_INVALID, "ctx or out is NULL");
     wipes_state* st = new wipes_state();
     st->ctx = ctx;
+    for (DevBuf* b : st->all) b->acct = &ctx->mem;
+    ctx->live_states += 1;
     *out = st;
     return WIPES_OK;
 }
 
 wipes_status wipes_state_destroy(wipes_state* st) {
     if (!st) return WIPES_OK;
-    DeviceGuard g(st->ctx->device);
-    for (DevBuf* b : st->all) release(*b);
+    wipes_ctx* ctx = st->ctx;
+    {
+        DeviceGuard g(ctx->device);
+        for (DevBuf* b : st->all) release(*b);
+    }
     delete st;
+    ctx->live_states -= 1;
     return WIPES_OK;
 }
 
-wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, int H, int W,
-                            const wipes_opts* opts, float* out, void* stream) {
-    if (!ctx || !st || !out || (N > 0 && !params)) return fail(WIPES_ERR_INVALID, "null argument");
+wipes_status wipes_prepare2d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, int H, int W,
+                             const wipes_opts* opts, void* stream) {
+    if (!ctx || !st || (N > 0 && !params)) return fail(WIPES_ERR_INVALID, "null argument");
     if (N < 0 || N > (int64_t)INT32_MAX) return fail(WIPES_ERR_INVALID, "N out of range");
     WIPES_TRY(check_image(H, W));
     WIPES_TRY(check_opts(opts));
@@ -358,19 +418,28 @@ wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params
                            st->counts.as<uint32_t>(), nullptr, s);
     }
     WIPES_TRY(bin_and_sort(st, nullptr, s));
-    {
-        StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend2d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), W, H, st->tiles_x, st->tiles_y,
-                       opts->cutoff_sigma, out, s);
-    }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 2;
     return WIPES_OK;
 }
 
-wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, const wipes_camera* cam,
-                            int H, int W, const wipes_opts* opts, float* out, void* stream) {
-    if (!ctx || !st || !out || !cam || (N > 0 && !params)) return fail(WIPES_ERR_INVALID, "null argument");
+wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, int H, int W,
+                            const wipes_opts* opts, float* out, void* stream) {
+    if (!out) return fail(WIPES_ERR_INVALID, "null argument");
+    WIPES_TRY(wipes_prepare2d(ctx, st, params, N, H, W, opts, stream));
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        StageTimer t(ctx, WIPES_STAGE_BLEND, s);
+        launch_blend2d(st->job(out), st->tiles_y, s);
+    }
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, const wipes_camera* cam,
+                             int H, int W, const wipes_opts* opts, void* stream) {
+    if (!ctx || !st || !cam || (N > 0 && !params)) return fail(WIPES_ERR_INVALID, "null argument");
     if (N < 0 || N > (int64_t)INT32_MAX) return fail(WIPES_ERR_INVALID, "N out of range");
     WIPES_TRY(check_image(H, W));
     WIPES_TRY(check_opts(opts));
@@ -405,13 +474,49 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
         cur = radix_sort_pairs(dk, dv, N, 32, st->hist.as<uint32_t>(), s);
     }
     WIPES_TRY(bin_and_sort(st, dv[cur], s));
-    {
-        StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), W, H, st->tiles_x, st->tiles_y,
-                       blend_opts(*opts), out, st->T_final.as<float>(), st->last.as<uint32_t>(), s);
-    }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 3;
+    return WIPES_OK;
+}
+
+wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, const wipes_camera* cam,
+                            int H, int W, const wipes_opts* opts, float* out, void* stream) {
+    if (!out) return fail(WIPES_ERR_INVALID, "null argument");
+    WIPES_TRY(wipes_prepare3d(ctx, st, params, N, cam, H, W, opts, stream));
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        StageTimer t(ctx, WIPES_STAGE_BLEND, s);
+        launch_blend3d(st->job(out), st->tiles_y, s);
+    }
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_blend_batch(wipes_ctx* ctx, const wipes_state* const* states, float* const* outs, int n,
+                               void* stream) {
+    if (!ctx || n < 0 || (n > 0 && (!states || !outs))) return fail(WIPES_ERR_INVALID, "null argument");
+    for (int i = 0; i < n; ++i) {
+        if (!states[i] || !outs[i]) return fail(WIPES_ERR_INVALID, "null state or output in batch");
+        if (states[i]->dims != 2 && states[i]->dims != 3)
+            return fail(WIPES_ERR_INVALID, "batch entry " + std::to_string(i) + " holds no prepared frame");
+        if (states[i]->ctx != ctx) return fail(WIPES_ERR_INVALID, "batch entry from another context");
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    StageTimer t(ctx, WIPES_STAGE_BLEND, s);
+    BlendJob jobs[kMaxBatchJobs];
+    int tiles_y[kMaxBatchJobs];
+    for (int b0 = 0; b0 < n; b0 += kMaxBatchJobs) {
+        const int m = std::min(kMaxBatchJobs, n - b0);
+        for (int i = 0; i < m; ++i) {
+            jobs[i] = states[b0 + i]->job(outs[b0 + i]);
+            tiles_y[i] = states[b0 + i]->tiles_y;
+        }
+        unsigned int* counter = ctx->d_batch_counters + (ctx->batch_slot++ % kBatchCounterSlots);
+        launch_blend_batch(jobs, tiles_y, m, counter, s);
+    }
+    WIPES_CUDA(cudaGetLastError());
     return WIPES_OK;
 }
 
@@ -578,6 +683,18 @@ wipes_status wipes_get_timing(wipes_ctx* ctx, double* ms, int64_t* brackets, int
 }
 
 int64_t wipes_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+wipes_status wipes_set_memory_limit(wipes_ctx* ctx, int64_t bytes) {
+    if (!ctx || bytes < 0) return fail(WIPES_ERR_INVALID, "bad argument");
+    ctx->mem.limit = bytes;
+    return WIPES_OK;
+}
+
+wipes_status wipes_get_memory_reserved(wipes_ctx* ctx, int64_t* bytes) {
+    if (!ctx || !bytes) return fail(WIPES_ERR_INVALID, "null argument");
+    *bytes = ctx->mem.reserved.load();
+    return WIPES_OK;
+}
 
 const char* wipes_status_string(wipes_status s) {
     switch (s) {

@@ -238,8 +238,22 @@ struct TileLists {
     const uint32_t* inst_prim;  // primitive of each emission index
     const uint2* ranges;        // [start, end) of each tile in `sorted`
 };
-void launch_blend2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
-                    int tiles_y, float cutoff, float* out, cudaStream_t stream);
+// One frame's forward pass over prepared tile lists (2D summed field or 3D front-to-back blend).
+struct BlendOpts3 {
+    float cutoff2, lim, alpha_min, alpha_max, T_min;
+    float bg[3];
+};
+struct BlendJob {
+    const float4* rec;
+    const PixRect* rect;
+    TileLists tl;
+    float* out;
+    float* T_final;  // 3D only
+    uint32_t* last;  // 3D only
+    int dims, W, H, tiles_x;
+    BlendOpts3 o;    // 2D uses cutoff2 and lim only
+};
+void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream);
 void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream);
 void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offsets, const uint32_t* counts,
@@ -249,17 +263,18 @@ void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, in
                         const uint32_t* last, unsigned long long* counters, cudaStream_t stream);
 
 // raster3d.cu
-struct BlendOpts3 {
-    float cutoff2, lim, alpha_min, alpha_max, T_min;
-    float bg[3];
-};
-void launch_blend3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
-                    int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last, cudaStream_t stream);
+void launch_blend3d(const BlendJob& job, int tiles_y, cudaStream_t stream);
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
                        const float* dl_dout, float* grad_img, cudaStream_t stream);
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
+
+// batch.cu: one persistent launch over the tiles of up to kMaxBatchJobs frames; blocks take
+// (frame, tile) items from counter[0], which the launcher resets.
+constexpr int kMaxBatchJobs = 128;
+void launch_blend_batch(const BlendJob* jobs, const int* tiles_y, int n_jobs, unsigned int* counter,
+                        cudaStream_t stream);
 
 // loss_noalloc.cu: the same loss with its scratch in a file-scope device array (no allocation)
 int64_t l2_loss_noalloc_max_elements();

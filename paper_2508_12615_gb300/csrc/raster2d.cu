@@ -8,88 +8,12 @@
 // registers and writes it to the pair's emission slot.  A second kernel sums the slots of each
 // primitive (contiguous in emission order) and chains them to the record's parameters:
 // deterministic, no atomics.
-#include "common.cuh"
+#include "blend_tile.cuh"
 
 namespace wipes {
 namespace {
 
-// Stage one tile-list entry: its record and, in `mask`, the warp sub-tiles its ellipse reaches.
-__device__ __forceinline__ uint32_t stage_entry(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
-                                                const TileLists& tl, uint32_t i, int x0, int y0, float lim,
-                                                float4& A, float4& B, float4& C) {
-    const uint32_t prim = tl.inst_prim[tl.sorted[i]];
-    A = rec[(size_t)prim * kRecF4 + 0];
-    B = rec[(size_t)prim * kRecF4 + 1];
-    C = rec[(size_t)prim * kRecF4 + 2];
-    return subtile_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
-}
-
-// Forward.  Warp w of the tile's block owns an 8x4 pixel sub-tile (two columns of sub-tiles by
-// four rows).  When a batch of the tile list is staged, each thread marks which sub-tiles its
-// primitive's cutoff ellipse reaches; a warp then visits only the primitives marked for it.  The
-// test is conservative (rect_touched), so skipping is exact.
-__global__ void __launch_bounds__(kTilePixels) k_blend2d(const float4* __restrict__ rec,
-                                                         const PixRect* __restrict__ rect, TileLists tl, int W, int H,
-                                                         int tiles_x, float cutoff2, float lim,
-                                                         float* __restrict__ out) {
-    __shared__ float4 s_a[kTilePixels];  // mx my l11 l21
-    __shared__ float4 s_b[kTilePixels];  // l22 fx fy phc
-    __shared__ float4 s_c[kTilePixels];  // c_r c_g c_b o
-    __shared__ uint8_t s_mask[kTilePixels];
-    const int tile = blockIdx.x;
-    const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = tx * kTile, y0 = ty * kTile;
-    const int u = x0 + (warp & 1) * 8 + (lane & 7);
-    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
-    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-    const uint2 range = tl.ranges[tile];
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
-        const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
-        __syncthreads();
-        if ((int)threadIdx.x < n) {
-            float4 A, B, C;
-            s_mask[threadIdx.x] = (uint8_t)stage_entry(rec, rect, tl, b0 + threadIdx.x, x0, y0, lim, A, B, C);
-            s_a[threadIdx.x] = A;
-            s_b[threadIdx.x] = B;
-            s_c[threadIdx.x] = C;
-        }
-        __syncthreads();
-        // two-level summation: a batch-local partial sum per channel, added once per batch
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (int c = 0; c < n; c += 32) {
-            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
-            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
-            while (bal) {
-                const int j = c + __ffs(bal) - 1;
-                bal &= bal - 1u;
-                const float4 A = s_a[j];
-                const float4 B = s_b[j];
-                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-                if (q <= cutoff2) {
-                    const float dx = px - A.x, dy = py - A.y;
-                    const float G = ex2_approx(q * kNegHalfLog2e);
-                    const float t = fmaf(B.y, dx, fmaf(B.z, dy, B.w));
-                    const float wv = fmaf(0.5f, cos_approx(reduced_angle(t)), 0.5f) * G;
-                    const float4 C = s_c[j];
-                    a0 = fmaf(C.x, wv, a0);
-                    a1 = fmaf(C.y, wv, a1);
-                    a2 = fmaf(C.z, wv, a2);
-                }
-            }
-        }
-        c0 += a0;
-        c1 += a1;
-        c2 += a2;
-    }
-    if (u < W && v < H) {
-        float* o = out + ((size_t)v * W + u) * 3;
-        o[0] = c0;
-        o[1] = c1;
-        o[2] = c2;
-    }
-}
+__global__ void __launch_bounds__(kTilePixels) k_blend2d(BlendJob job) { blend2d_tile(job, blockIdx.x); }
 
 // Partial gradient slot layout (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b 0
 constexpr int kSlot = 12;
@@ -306,10 +230,8 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
 
 }  // namespace
 
-void launch_blend2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
-                    int tiles_y, float cutoff, float* out, cudaStream_t stream) {
-    k_blend2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, cutoff * cutoff,
-                                                              touch_limit(cutoff), out);
+void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream) {
+    k_blend2d<<<job.tiles_x * tiles_y, kTilePixels, 0, stream>>>(job);
     count_launches(1);
 }
 

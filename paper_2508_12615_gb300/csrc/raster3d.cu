@@ -6,85 +6,12 @@
 // Blend rule per pixel, over the tile list in order: skip a primitive outside its cutoff ellipse;
 // alpha = min(alpha_max, o W'); skip alpha < alpha_min; stop before a primitive that would take
 // T (1 - alpha) below T_min; otherwise C += c alpha T, T *= 1 - alpha.  Finally C += T bg.
-#include "common.cuh"
+#include "blend_tile.cuh"
 
 namespace wipes {
 namespace {
 
-// Forward.  As in 2D, warp w owns an 8x4 pixel sub-tile and visits only the staged primitives
-// whose covered pixel range touches it; positions in the tile list are counted from the list
-// start, so the per-pixel last-contributor index does not depend on the culling.
-__global__ void __launch_bounds__(kTilePixels) k_blend3d(const float4* __restrict__ rec,
-                                                         const PixRect* __restrict__ rect, TileLists tl, int W, int H,
-                                                         int tiles_x, BlendOpts3 o, float* __restrict__ out,
-                                                         float* __restrict__ T_final, uint32_t* __restrict__ last) {
-    __shared__ float4 s_a[kTilePixels];
-    __shared__ float4 s_b[kTilePixels];
-    __shared__ float4 s_c[kTilePixels];
-    __shared__ uint8_t s_mask[kTilePixels];
-    const int tile = blockIdx.x;
-    const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = tx * kTile, y0 = ty * kTile;
-    const int u = x0 + (warp & 1) * 8 + (lane & 7);
-    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside = u < W && v < H;
-    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
-    const uint2 range = tl.ranges[tile];
-    bool done = !inside;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    uint32_t last_contrib = 0;
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
-        if (__syncthreads_count(done) == kTilePixels) break;
-        const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
-        if ((int)threadIdx.x < n) {
-            const uint32_t id = tl.inst_prim[tl.sorted[b0 + threadIdx.x]];
-            const float4 A = rec[(size_t)id * kRecF4 + 0];
-            const float4 B = rec[(size_t)id * kRecF4 + 1];
-            s_a[threadIdx.x] = A;
-            s_b[threadIdx.x] = B;
-            s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[id], x0, y0, o.lim);
-        }
-        __syncthreads();
-        for (int c = 0; c < n; c += 32) {
-            if (__all_sync(0xffffffffu, done)) break;
-            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
-            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
-            while (bal) {
-                const int j = c + __ffs(bal) - 1;
-                bal &= bal - 1u;
-                if (done) continue;
-                const float4 A = s_a[j];
-                const float4 B = s_b[j];
-                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-                if (!(q <= o.cutoff2)) continue;
-                const float dx = px - A.x, dy = py - A.y;
-                const float G = ex2_approx(q * kNegHalfLog2e);
-                const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
-                const float4 C = s_c[j];
-                const float alpha = fminf(o.alpha_max, C.w * w);
-                if (alpha < o.alpha_min) continue;
-                const float test_T = T * (1.f - alpha);
-                if (test_T < o.T_min) { done = true; continue; }
-                const float wt = alpha * T;
-                c0 = fmaf(C.x, wt, c0);
-                c1 = fmaf(C.y, wt, c1);
-                c2 = fmaf(C.z, wt, c2);
-                T = test_T;
-                last_contrib = b0 - range.x + (uint32_t)j + 1u;
-            }
-        }
-    }
-    if (inside) {
-        const size_t pix = (size_t)v * W + u;
-        out[pix * 3 + 0] = fmaf(T, o.bg[0], c0);
-        out[pix * 3 + 1] = fmaf(T, o.bg[1], c1);
-        out[pix * 3 + 2] = fmaf(T, o.bg[2], c2);
-        T_final[pix] = T;
-        last[pix] = last_contrib;
-    }
-}
+__global__ void __launch_bounds__(kTilePixels) k_blend3d(BlendJob job) { blend3d_tile(job, blockIdx.x); }
 
 // Image-plane gradient per primitive (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b o
 constexpr int kG = 12;
@@ -374,10 +301,9 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
 
 }  // namespace
 
-void launch_blend3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
-                    int tiles_y, const BlendOpts3& o, float* out, float* T_final, uint32_t* last, cudaStream_t stream) {
-    k_blend3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, o, out, T_final,
-                                                              last); count_launches(1);
+void launch_blend3d(const BlendJob& job, int tiles_y, cudaStream_t stream) {
+    k_blend3d<<<job.tiles_x * tiles_y, kTilePixels, 0, stream>>>(job);
+    count_launches(1);
 }
 
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,

@@ -223,3 +223,52 @@ def cfg2_inputs(n_cams: int = 16):
 def cfg3_inputs(n_cams: int = 16):
     c = CFG3_6D
     return scene6d(c.n, c.seed), sphere_cameras(n_cams, c.H, c.W, c.seed + 100), time_stamps(300)
+
+
+# ------------------------------------------------------------------------------------------------
+# serving workload
+# ------------------------------------------------------------------------------------------------
+
+SERVING_SIZES = ((256, 256), (512, 512), (800, 800), (1080, 1920))  # (H, W)
+
+
+@dataclass
+class ServingScene:
+    dims: int
+    n: int
+    seed: int
+    params: dict      # size index -> [N,16] (2D, generated at that size) or the single [N,20] under key 0 (3D)
+    cameras: dict     # size index -> [16,17] (3D only)
+
+
+def serving_workload(n_scenes: int = 64, rate: float = 2000.0, seconds: float = 10.0, seed: int = 1238,
+                     n_range=(10_000, 500_000), n_cams: int = 16):
+    """Resident scenes and a Poisson request trace for the serving benchmark.
+
+    Scenes: N log-uniform in n_range, 2D and 3D alternating (1:1); a 2D scene is drawn as the
+    768x512 image-fitting scene (scales 0.5-32 px) at each serving size from one seed, a 3D scene
+    as the 800x800 static scene with n_cams seeded cameras on the radius-4 sphere per size.
+    Requests: Poisson arrivals at `rate` per second for `seconds`; each picks a scene, an image
+    size uniformly from SERVING_SIZES and (3D) a camera.  Returns (scenes, requests) with requests
+    an int/float array [R, 4]: arrival time (s), scene, size index, camera index."""
+    rng = _rng(seed)
+    scenes = []
+    for k in range(n_scenes):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        s = seed * 1000 + k
+        if k % 2 == 0:
+            params = {i: scene2d(n, H, W, s, (0.5, 32.0)) for i, (H, W) in enumerate(SERVING_SIZES)}
+            scenes.append(ServingScene(2, n, s, params, {}))
+        else:
+            cams = {i: sphere_cameras(n_cams, H, W, s + 1) for i, (H, W) in enumerate(SERVING_SIZES)}
+            scenes.append(ServingScene(3, n, s, {0: scene3d(n, s)}, cams))
+    gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 1.5) + 16)
+    t = np.cumsum(gaps)
+    t = t[t < seconds]
+    m = len(t)
+    req = np.zeros((m, 4), np.float64)
+    req[:, 0] = t
+    req[:, 1] = rng.integers(0, n_scenes, m)
+    req[:, 2] = rng.integers(0, len(SERVING_SIZES), m)
+    req[:, 3] = rng.integers(0, n_cams, m)
+    return scenes, req

@@ -14,6 +14,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device and the compiled library")
+    config.addinivalue_line("markers", "timeout(seconds): per-test time limit (pytest-timeout, when installed)")
 
 
 @pytest.fixture(scope="session")
