@@ -36,9 +36,11 @@ SMS = 152
 # FP32-pipe operations (an FMA counts as one) and MUFU operations per (pixel, primitive) pair inside
 # the cutoff ellipse, as the oracle's definition requires them (counted in the design notes).
 OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend": (25, 2), "bwd_raster": (55, 3)}}
-# DRAM bytes (read + write) per launch from the ncu capture summarised in profiles/, for the kernel
-# build measured there; None when the kernel has changed since.
-TRAFFIC_BYTES = {"k_backward2d": None, "k_blend2d": None}
+# DRAM bytes (read + write) per launch, per (workload, kernel), from the ncu captures summarised in
+# profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
+# entry is removed when its kernel changes.
+TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_434_112 + 465_408, ("2d", "k_blend2d"): 12_481_792,
+                 ("5d", "k_backward3d"): 38_496_000 + 13_056}
 
 
 def parse_args():
@@ -167,6 +169,23 @@ def oracle_step_sample(p, target, H, W, budget_s: float):
 def cpu_cores() -> int:
     env = os.environ.get("OMP_NUM_THREADS")
     return int(env) if env and env.isdigit() else (os.cpu_count() or 1)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time: every rank contributes its own, all receive the maximum."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, ms: float) -> float:
+    """Steps per second of the whole job: each of the `world` replicas ran `steps` steps within
+    the slowest rank's `ms`."""
+    return world * steps / (ms / 1000.0)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -360,12 +379,8 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     stage_n = (ctypes.c_int64 * 10)()
     lib.wipes_get_timing(ctx.handle, stage_ms, stage_n, 1)
     lib.wipes_set_timing(ctx.handle, 0)
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = whole_job_rate(world, args.steps, total_ms)
 
     # forward only (Mpix/s)
     fwd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -397,12 +412,8 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         l_host.copy_(wl.loss, non_blocking=True)
         e_ev[k][1].record()
         torch.cuda.current_stream().synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e_ev)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev), dist, dev)
+    e2e_value = whole_job_rate(world, args.steps, e2e_ms)
 
     if rank != 0:
         return
@@ -422,7 +433,7 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     achieved = pairs_per_launch * fp32_ops / launch_s / 1e12
     kernel = {"2d": {"blend": "k_blend2d", "bwd_raster": "k_backward2d"},
               "3d": {"blend": "k_blend3d", "bwd_raster": "k_backward3d"}}[dims][dom]
-    traffic = TRAFFIC_BYTES.get(kernel) if wl.kind == "2d" else None
+    traffic = TRAFFIC_BYTES.get((wl.kind, kernel))
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz ({pk_kind} max SM clock)",
