@@ -181,11 +181,11 @@ struct wipes_state {
     int64_t n_inst = 0;
     int sorted = 0;  // which ping-pong buffer holds the sorted lists
     DevBuf rec, rect, counts, offsets, dkeys[2], dvals[2], block_sums, total, keys[2], vals[2], inst_prim, hist, ranges;
-    DevBuf T_final, last, partial, grad_img;
+    DevBuf sprim, order, T_final, last, partial, grad_img;
 
-    DevBuf* all[21] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0],
-                       &dvals[1], &block_sums, &total, &keys[0], &keys[1],   &vals[0],   &vals[1],
-                       &inst_prim, &hist, &ranges, &T_final, &last, &partial, &grad_img};
+    DevBuf* all[23] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
+                       &block_sums, &total, &keys[0], &keys[1],   &vals[0],   &vals[1],   &inst_prim, &hist,
+                       &ranges,  &sprim,   &order,     &T_final, &last,     &partial,  &grad_img};
     size_t reserved() const {
         size_t s = 0;
         for (DevBuf* b : all) s += b->cap;
@@ -194,7 +194,7 @@ struct wipes_state {
     TileLists lists() const {
         TileLists t;
         t.sorted = vals[sorted].as<uint32_t>();
-        t.inst_prim = inst_prim.as<uint32_t>();
+        t.prim = sprim.as<uint32_t>();
         t.ranges = ranges.as<uint2>();
         return t;
     }
@@ -239,6 +239,7 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
         WIPES_TRY(ensure(st->vals[k], sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
     }
     WIPES_TRY(ensure(st->inst_prim, sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
+    WIPES_TRY(ensure(st->sprim, sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
     WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(I)));
     if (N > 0) {
         StageTimer t(st->ctx, WIPES_STAGE_EMIT, s);
@@ -251,7 +252,8 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
     uint32_t* vb[2] = {st->vals[0].as<uint32_t>(), st->vals[1].as<uint32_t>()};
     {
         StageTimer t(st->ctx, WIPES_STAGE_TILE_SORT, s);
-        st->sorted = radix_sort_pairs(kb, vb, I, ceil_log2(n_tiles), st->hist.as<uint32_t>(), s);
+        st->sorted = radix_sort_pairs(kb, vb, I, ceil_log2(n_tiles), st->hist.as<uint32_t>(), s,
+                                      st->inst_prim.as<uint32_t>(), st->sprim.as<uint32_t>());
     }
     {
         StageTimer t(st->ctx, WIPES_STAGE_RANGES, s);
@@ -474,6 +476,12 @@ wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* param
         cur = radix_sort_pairs(dk, dv, N, 32, st->hist.as<uint32_t>(), s);
     }
     WIPES_TRY(bin_and_sort(st, dv[cur], s));
+    {
+        StageTimer t(ctx, WIPES_STAGE_RANGES, s);
+        const int n_tiles = st->tiles_x * st->tiles_y;
+        WIPES_TRY(ensure(st->order, sizeof(uint32_t) * (size_t)n_tiles));
+        launch_tile_order(st->ranges.as<uint2>(), n_tiles, st->order.as<uint32_t>(), s);
+    }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 3;
     return WIPES_OK;
@@ -487,7 +495,7 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
     cudaStream_t s = (cudaStream_t)stream;
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend3d(st->job(out), st->tiles_y, s);
+        launch_blend3d(st->job(out), st->tiles_y, st->order.as<uint32_t>(), s);
     }
     WIPES_CUDA(cudaGetLastError());
     return WIPES_OK;
@@ -545,7 +553,7 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
             if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * 12 * (size_t)N, s));
             launch_backward3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), st->W, st->H, st->tiles_x,
                               st->tiles_y, blend_opts(st->opts), st->T_final.as<float>(), st->last.as<uint32_t>(),
-                              dL_dout, st->grad_img.as<float>(), s);
+                              dL_dout, st->grad_img.as<float>(), st->order.as<uint32_t>(), s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
         launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->rec.as<float4>(),
@@ -615,8 +623,7 @@ wipes_status wipes_state_copy_lists(const wipes_state* st, uint32_t* tile_ids, u
     const size_t I = (size_t)st->n_inst;
     if (tile_ids && I)
         WIPES_CUDA(cudaMemcpyAsync(tile_ids, st->keys[st->sorted].p, I * 4, cudaMemcpyDeviceToDevice, s));
-    if (prim_ids && I)
-        launch_gather_u32(prim_ids, st->inst_prim.as<uint32_t>(), st->vals[st->sorted].as<uint32_t>(), (int64_t)I, s);
+    if (prim_ids && I) WIPES_CUDA(cudaMemcpyAsync(prim_ids, st->sprim.p, I * 4, cudaMemcpyDeviceToDevice, s));
     if (tile_ranges)
         WIPES_CUDA(cudaMemcpyAsync(tile_ranges, st->ranges.p, (size_t)st->tiles_x * st->tiles_y * sizeof(uint2),
                                    cudaMemcpyDeviceToDevice, s));

@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __
                                                               uint32_t* __restrict__ keys_out,
                                                               uint32_t* __restrict__ vals_out, int64_t n, int shift,
                                                               int nbits, const uint32_t* __restrict__ hist,
-                                                              const uint32_t* __restrict__ digit_totals, int nb) {
+                                                              const uint32_t* __restrict__ digit_totals, int nb,
+                                                              const uint32_t* __restrict__ table,
+                                                              uint32_t* __restrict__ gathered) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wc[kWarps][kMaxRadix];
@@ -283,8 +285,41 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __
         const uint32_t key = s_keys[t];
         const uint32_t d = (key >> shift) & mask;
         const uint32_t g = s_gbase[d] + (uint32_t)t;
+        const uint32_t val = s_vals[t];
         keys_out[g] = key;
-        vals_out[g] = s_vals[t];
+        vals_out[g] = val;
+        if (table) gathered[g] = table[val];
+    }
+}
+
+// Order of the tiles for the blend kernels, longest list first: tiles are bucketed by the bit
+// length of their list length and the buckets laid out in decreasing order (the order inside a
+// bucket is arbitrary).  The block scheduler starts blocks in index order, so the tiles with the
+// most work start first and short tiles fill in at the end.  One block does all tiles.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 33;
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint2* __restrict__ ranges, int n_tiles,
+                                                              uint32_t* __restrict__ order) {
+    __shared__ uint32_t s_cnt[kOrderBuckets];
+    __shared__ uint32_t s_cur[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += kOrderThreads) {
+        const uint2 r = ranges[t];
+        atomicAdd(&s_cnt[32 - __clz(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = kOrderBuckets - 1; b >= 0; --b) {
+            s_cur[b] = run;
+            run += s_cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += kOrderThreads) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&s_cur[32 - __clz(r.y - r.x)], 1u)] = (uint32_t)t;
     }
 }
 
@@ -324,6 +359,11 @@ void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, i
     k_tile_ranges<<<grid, 256, 0, stream>>>(sorted_keys, n, ranges); count_launches(1);
 }
 
+void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream) {
+    k_tile_order<<<1, kOrderThreads, 0, stream>>>(ranges, n_tiles, order);
+    count_launches(1);
+}
+
 void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
     if (n == 0) return;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
@@ -332,8 +372,12 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
 
 int64_t radix_hist_words(int64_t n) { return (int64_t)kMaxRadix * (int64_t)ceil_div(std::max<int64_t>(n, 1), kSortTile) + kMaxRadix; }
 
-int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream) {
-    if (n <= 1 || bits <= 0) return 0;
+int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream,
+                     const uint32_t* table, uint32_t* gathered) {
+    if (n <= 1 || bits <= 0) {
+        if (table) launch_gather_u32(gathered, table, vals[0], n, stream);
+        return 0;
+    }
     const int passes = (bits + 7) / 8;
     const int nb = (int)ceil_div(n, kSortTile);
     uint32_t* digit_totals = hist + (int64_t)kMaxRadix * nb;
@@ -342,8 +386,11 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         const int nbits = (bits - shift + (passes - p) - 1) / (passes - p);  // split the remaining bits evenly
         k_radix_upsweep<<<nb, kThreads, 0, stream>>>(keys[cur], n, shift, nbits, hist, nb); count_launches(1);
         k_radix_scan_digits<<<1 << nbits, kThreads, 0, stream>>>(hist, nb, digit_totals); count_launches(1);
+        const bool last_pass = p == passes - 1;
         k_radix_downsweep<<<nb, kThreads, 0, stream>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
-                                                       nbits, hist, digit_totals, nb); count_launches(1);
+                                                       nbits, hist, digit_totals, nb, last_pass ? table : nullptr,
+                                                       last_pass ? gathered : nullptr);
+        count_launches(1);
         cur ^= 1;
         shift += nbits;
     }

@@ -11,7 +11,7 @@ namespace wipes {
 __device__ __forceinline__ uint32_t stage_entry(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
                                                 const TileLists& tl, uint32_t i, int x0, int y0, float lim,
                                                 float4& A, float4& B, float4& C) {
-    const uint32_t prim = tl.inst_prim[tl.sorted[i]];
+    const uint32_t prim = tl.prim[i];
     A = rec[(size_t)prim * kRecF4 + 0];
     B = rec[(size_t)prim * kRecF4 + 1];
     C = rec[(size_t)prim * kRecF4 + 2];
@@ -88,18 +88,58 @@ __device__ __forceinline__ void blend2d_tile(const BlendJob& job, int tile) {
 }
 
 
-// Forward.  As in 2D, warp w owns an 8x4 pixel sub-tile and visits only the staged primitives
-// whose covered pixel range touches it; positions in the tile list are counted from the list
-// start, so the per-pixel last-contributor index does not depend on the culling.
+// One pixel's state in the 3D front-to-back blend.
+struct Px3 {
+    float T, c0, c1, c2;
+    uint32_t last;  // 1-based tile-list position of the last entry that contributed (0: none)
+    bool done;      // the next contribution would have taken T below T_min
+};
+
+// One tile-list entry at one pixel (Eq. 3 with W'): nothing outside the cutoff ellipse or below
+// alpha_min; stop before an entry that would take T below T_min; else add c alpha T and update T.
+// `pos` is the entry's 1-based position in the tile list.  Every 3D forward kernel blends through
+// this function, so a pixel gets the same bits whatever the block shape.
+__device__ __forceinline__ void blend3d_pair(Px3& s, float px, float py, const float4& A, const float4& B,
+                                             const float4& C, const BlendOpts3& o, uint32_t pos) {
+    const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
+    if (!(q <= o.cutoff2)) return;
+    const float dx = px - A.x, dy = py - A.y;
+    const float G = ex2_approx(q * kNegHalfLog2e);
+    const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
+    const float alpha = fminf(o.alpha_max, C.w * w);
+    if (alpha < o.alpha_min) return;
+    const float test_T = s.T * (1.f - alpha);
+    if (test_T < o.T_min) {
+        s.done = true;
+        return;
+    }
+    const float wt = alpha * s.T;
+    s.c0 = fmaf(C.x, wt, s.c0);
+    s.c1 = fmaf(C.y, wt, s.c1);
+    s.c2 = fmaf(C.z, wt, s.c2);
+    s.T = test_T;
+    s.last = pos;
+}
+
+__device__ __forceinline__ void store_px3(const BlendJob& job, int u, int v, const Px3& s) {
+    const size_t pix = (size_t)v * job.W + u;
+    job.out[pix * 3 + 0] = fmaf(s.T, job.o.bg[0], s.c0);
+    job.out[pix * 3 + 1] = fmaf(s.T, job.o.bg[1], s.c1);
+    job.out[pix * 3 + 2] = fmaf(s.T, job.o.bg[2], s.c2);
+    job.T_final[pix] = s.T;
+    job.last[pix] = s.last;
+}
+
+// Forward over a whole 16x16 tile (256 threads; used by the batch kernel).  As in 2D, warp w owns
+// an 8x4 pixel sub-tile and visits only the staged primitives whose cutoff ellipse reaches it;
+// positions in the tile list are counted from the list start, so the per-pixel last-contributor
+// index does not depend on the culling.
 __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
     const float4* __restrict__ rec = job.rec;
     const PixRect* __restrict__ rect = job.rect;
     const TileLists& tl = job.tl;
     const int W = job.W, H = job.H, tiles_x = job.tiles_x;
     const BlendOpts3& o = job.o;
-    float* __restrict__ out = job.out;
-    float* __restrict__ T_final = job.T_final;
-    uint32_t* __restrict__ last = job.last;
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
     __shared__ float4 s_c[kTilePixels];
@@ -112,14 +152,12 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
     const bool inside = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
     const uint2 range = tl.ranges[tile];
-    bool done = !inside;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    uint32_t last_contrib = 0;
+    Px3 s{1.f, 0.f, 0.f, 0.f, 0u, !inside};
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
-        if (__syncthreads_count(done) == kTilePixels) break;
+        if (__syncthreads_count(s.done) == kTilePixels) break;
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         if ((int)threadIdx.x < n) {
-            const uint32_t id = tl.inst_prim[tl.sorted[b0 + threadIdx.x]];
+            const uint32_t id = tl.prim[b0 + threadIdx.x];
             const float4 A = rec[(size_t)id * kRecF4 + 0];
             const float4 B = rec[(size_t)id * kRecF4 + 1];
             s_a[threadIdx.x] = A;
@@ -129,42 +167,87 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
         }
         __syncthreads();
         for (int c = 0; c < n; c += 32) {
-            if (__all_sync(0xffffffffu, done)) break;
+            if (__all_sync(0xffffffffu, s.done)) break;
             const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
             uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
             while (bal) {
                 const int j = c + __ffs(bal) - 1;
                 bal &= bal - 1u;
-                if (done) continue;
-                const float4 A = s_a[j];
-                const float4 B = s_b[j];
-                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-                if (!(q <= o.cutoff2)) continue;
-                const float dx = px - A.x, dy = py - A.y;
-                const float G = ex2_approx(q * kNegHalfLog2e);
-                const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
-                const float4 C = s_c[j];
-                const float alpha = fminf(o.alpha_max, C.w * w);
-                if (alpha < o.alpha_min) continue;
-                const float test_T = T * (1.f - alpha);
-                if (test_T < o.T_min) { done = true; continue; }
-                const float wt = alpha * T;
-                c0 = fmaf(C.x, wt, c0);
-                c1 = fmaf(C.y, wt, c1);
-                c2 = fmaf(C.z, wt, c2);
-                T = test_T;
-                last_contrib = b0 - range.x + (uint32_t)j + 1u;
+                if (s.done) continue;
+                blend3d_pair(s, px, py, s_a[j], s_b[j], s_c[j], o, b0 - range.x + (uint32_t)j + 1u);
             }
         }
     }
-    if (inside) {
-        const size_t pix = (size_t)v * W + u;
-        out[pix * 3 + 0] = fmaf(T, o.bg[0], c0);
-        out[pix * 3 + 1] = fmaf(T, o.bg[1], c1);
-        out[pix * 3 + 2] = fmaf(T, o.bg[2], c2);
-        T_final[pix] = T;
-        last[pix] = last_contrib;
+    if (inside) store_px3(job, u, v, s);
+}
+
+// Forward over one 8x8 quad of a 16x16 tile, for blocks of kQuadThreads (two warps; warp k owns
+// rows 4k .. 4k + 3 of the quad).  Long tile lists then spread over four blocks, which the
+// scheduler can place on four SMs.  Batches of 64 entries are staged in shared memory; the
+// records of the next batch are loaded into registers (from primitive ids fetched one batch
+// earlier still) while the current batch is blended, so the gathers overlap the arithmetic.
+constexpr int kQuadThreads = 64;
+
+__device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int quad) {
+    const float4* __restrict__ rec = job.rec;
+    const PixRect* __restrict__ rect = job.rect;
+    const TileLists& tl = job.tl;
+    const BlendOpts3& o = job.o;
+    __shared__ float4 s_a[kQuadThreads];
+    __shared__ float4 s_b[kQuadThreads];
+    __shared__ float4 s_c[kQuadThreads];
+    __shared__ uint8_t s_mask[kQuadThreads];
+    const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int x0 = tx * kTile + (quad & 1) * 8, y0 = ty * kTile + (quad >> 1) * 8;
+    const int u = x0 + (lane & 7), v = y0 + warp * 4 + (lane >> 3);
+    const bool inside = u < job.W && v < job.H;
+    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    const uint2 range = tl.ranges[tile];
+    Px3 s{1.f, 0.f, 0.f, 0.f, 0u, !inside};
+    // registers of the software pipeline: records of the batch to stage next, primitive id of the
+    // batch after it
+    float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
+    PixRect nR{0, 0, -1, -1};
+    uint32_t np = 0u;
+    if (range.x + t < range.y) {
+        const uint32_t p = tl.prim[range.x + t];
+        nA = rec[(size_t)p * kRecF4 + 0];
+        nB = rec[(size_t)p * kRecF4 + 1];
+        nC = rec[(size_t)p * kRecF4 + 2];
+        nR = rect[p];
     }
+    if (range.x + kQuadThreads + t < range.y) np = tl.prim[range.x + kQuadThreads + t];
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += kQuadThreads) {
+        if (__syncthreads_count(s.done) == kQuadThreads) break;
+        const int n = (int)min((uint32_t)kQuadThreads, range.y - b0);
+        if (t < n) {
+            s_a[t] = nA;
+            s_b[t] = nB;
+            s_c[t] = nC;
+            s_mask[t] = (uint8_t)quad_mask_ellipse(nA, nB.x, nR, x0, y0, o.lim);
+        }
+        __syncthreads();
+        if (b0 + kQuadThreads + t < range.y) {
+            nA = rec[(size_t)np * kRecF4 + 0];
+            nB = rec[(size_t)np * kRecF4 + 1];
+            nC = rec[(size_t)np * kRecF4 + 2];
+            nR = rect[np];
+        }
+        if (b0 + 2 * kQuadThreads + t < range.y) np = tl.prim[b0 + 2 * kQuadThreads + t];
+        for (int c = 0; c < n; c += 32) {
+            if (__all_sync(0xffffffffu, s.done)) break;
+            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
+            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
+            while (bal) {
+                const int j = c + __ffs(bal) - 1;
+                bal &= bal - 1u;
+                if (s.done) continue;
+                blend3d_pair(s, px, py, s_a[j], s_b[j], s_c[j], o, b0 - range.x + (uint32_t)j + 1u);
+            }
+        }
+    }
+    if (inside) store_px3(job, u, v, s);
 }
 
 

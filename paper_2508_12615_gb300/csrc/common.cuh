@@ -129,43 +129,63 @@ __device__ __forceinline__ bool tile_touched(const Ellipse& k, const PixRect& r,
     return rect_touched(k, x0, x1, y0, y1, lim);
 }
 
-// Which of the eight 8x4 warp sub-tiles of the 16x16 tile at (x0, y0) the primitive's cutoff
-// ellipse reaches: bit w for warp w (columns 8 (w & 1) .. +7, rows 4 (w >> 1) .. +3).  The same
-// rectangle test as rect_touched() in ordinary (fused) arithmetic; the 1 % margin of lim keeps it
-// conservative.
-__device__ __forceinline__ uint32_t subtile_mask_ellipse(const float4& A4, float l22, const PixRect& r, int x0, int y0,
-                                                         float lim) {
+// Does the primitive's cutoff ellipse reach the bw x bh pixel box at (bx, by), clipped to its
+// covered range?  The same rectangle test as rect_touched() in ordinary (fused) arithmetic; the
+// 1 % margin of lim keeps it conservative.  nBA, nBC from ellipse_edge_ratios().
+__device__ __forceinline__ bool box_touched_ellipse(const float4& A4, float l22, float nBA, float nBC,
+                                                    const PixRect& r, int bx, int by, int bw, int bh, float lim) {
+    const float l11 = A4.z, l21 = A4.w;
+    const int sx0 = max(bx, r.u0), sx1 = min(bx + bw - 1, r.u1);
+    const int sy0 = max(by, r.v0), sy1 = min(by + bh - 1, r.v1);
+    if (sx0 > sx1 || sy0 > sy1) return false;
+    const float dx0 = ((float)sx0 + 0.5f) - A4.x, dx1 = ((float)sx1 + 0.5f) - A4.x;
+    const float dy0 = ((float)sy0 + 0.5f) - A4.y, dy1 = ((float)sy1 + 0.5f) - A4.y;
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return true;
+    float best = 3.4e38f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float dx, dy;
+        if (e < 2) {
+            dx = e == 0 ? dx0 : dx1;
+            dy = fminf(fmaxf(nBC * dx, dy0), dy1);
+        } else {
+            dy = e == 2 ? dy0 : dy1;
+            dx = fminf(fmaxf(nBA * dy, dx0), dx1);
+        }
+        const float a = fmaf(l11, dx, l21 * dy), b = l22 * dy;
+        best = fminf(best, fmaf(a, a, b * b));
+    }
+    return best <= lim;
+}
+
+__device__ __forceinline__ void ellipse_edge_ratios(const float4& A4, float l22, float& nBA, float& nBC) {
     const float l11 = A4.z, l21 = A4.w;
     const float A = l11 * l11, B = l11 * l21, C = fmaf(l21, l21, l22 * l22);
-    const float nBA = -B / A, nBC = -B / C;
+    nBA = -B / A;
+    nBC = -B / C;
+}
+
+// Which of the eight 8x4 warp sub-tiles of the 16x16 tile at (x0, y0) the primitive's cutoff
+// ellipse reaches: bit w for warp w (columns 8 (w & 1) .. +7, rows 4 (w >> 1) .. +3).
+__device__ __forceinline__ uint32_t subtile_mask_ellipse(const float4& A4, float l22, const PixRect& r, int x0, int y0,
+                                                         float lim) {
+    float nBA, nBC;
+    ellipse_edge_ratios(A4, l22, nBA, nBC);
     uint32_t m = 0;
 #pragma unroll 1
-    for (int w = 0; w < 8; ++w) {
-        const int sx0 = max(x0 + 8 * (w & 1), r.u0), sx1 = min(x0 + 8 * (w & 1) + 7, r.u1);
-        const int sy0 = max(y0 + 4 * (w >> 1), r.v0), sy1 = min(y0 + 4 * (w >> 1) + 3, r.v1);
-        if (sx0 > sx1 || sy0 > sy1) continue;
-        const float dx0 = ((float)sx0 + 0.5f) - A4.x, dx1 = ((float)sx1 + 0.5f) - A4.x;
-        const float dy0 = ((float)sy0 + 0.5f) - A4.y, dy1 = ((float)sy1 + 0.5f) - A4.y;
-        bool hit = dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f;
-        if (!hit) {
-            float best = 3.4e38f;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float dx, dy;
-                if (e < 2) {
-                    dx = e == 0 ? dx0 : dx1;
-                    dy = fminf(fmaxf(nBC * dx, dy0), dy1);
-                } else {
-                    dy = e == 2 ? dy0 : dy1;
-                    dx = fminf(fmaxf(nBA * dy, dx0), dx1);
-                }
-                const float a = fmaf(l11, dx, l21 * dy), b = l22 * dy;
-                best = fminf(best, fmaf(a, a, b * b));
-            }
-            hit = best <= lim;
-        }
-        if (hit) m |= 1u << w;
-    }
+    for (int w = 0; w < 8; ++w)
+        if (box_touched_ellipse(A4, l22, nBA, nBC, r, x0 + 8 * (w & 1), y0 + 4 * (w >> 1), 8, 4, lim)) m |= 1u << w;
+    return m;
+}
+
+// The same test for the two 8x4 sub-tiles of the 8x8 quad at (x0, y0): bit 0 rows 0..3, bit 1
+// rows 4..7.  Sub-tile k of quad (qx, qy) is sub-tile 4 qy + 2 k + qx of the 16x16 tile.
+__device__ __forceinline__ uint32_t quad_mask_ellipse(const float4& A4, float l22, const PixRect& r, int x0, int y0,
+                                                      float lim) {
+    float nBA, nBC;
+    ellipse_edge_ratios(A4, l22, nBA, nBC);
+    uint32_t m = box_touched_ellipse(A4, l22, nBA, nBC, r, x0, y0, 8, 4, lim) ? 1u : 0u;
+    if (box_touched_ellipse(A4, l22, nBA, nBC, r, x0, y0 + 4, 8, 4, lim)) m |= 2u;
     return m;
 }
 
@@ -227,16 +247,20 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream);
 
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  Uses (keys[0], vals[0]) as
 // input and (keys[1], vals[1]) as ping-pong space; returns which buffer index holds the result.
-// `hist` must hold radix_hist_words(n) words.
+// `hist` must hold radix_hist_words(n) words.  With a table, the last pass also writes
+// gathered[i] = table[sorted value i].
 int64_t radix_hist_words(int64_t n);
-int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream);
+int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream,
+                     const uint32_t* table = nullptr, uint32_t* gathered = nullptr);
+// order[0 .. n_tiles) = the tiles, longest list first (see k_tile_order)
+void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream);
 
 // raster2d.cu
-// Tile-list entries are emission indices: the primitive of entry i is inst_prim[sorted[i]].
+// Tile lists: entry i of the sorted list is emission index sorted[i] of primitive prim[i].
 struct TileLists {
-    const uint32_t* sorted;     // emission indices in tile order
-    const uint32_t* inst_prim;  // primitive of each emission index
-    const uint2* ranges;        // [start, end) of each tile in `sorted`
+    const uint32_t* sorted;  // emission indices in tile order
+    const uint32_t* prim;    // primitive of each sorted entry
+    const uint2* ranges;     // [start, end) of each tile in `sorted`
 };
 // One frame's forward pass over prepared tile lists (2D summed field or 3D front-to-back blend).
 struct BlendOpts3 {
@@ -262,11 +286,11 @@ void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offse
 void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
                         const uint32_t* last, unsigned long long* counters, cudaStream_t stream);
 
-// raster3d.cu
-void launch_blend3d(const BlendJob& job, int tiles_y, cudaStream_t stream);
+// raster3d.cu: one 64-thread block per 8x8 quad, tiles in `order` (launch_tile_order)
+void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cudaStream_t stream);
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
-                       const float* dl_dout, float* grad_img, cudaStream_t stream);
+                       const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream);
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 

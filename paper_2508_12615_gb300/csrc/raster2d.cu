@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __r
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t e = tl.sorted[b0 + threadIdx.x];
-            const uint32_t prim = tl.inst_prim[e];
+            const uint32_t prim = tl.prim[b0 + threadIdx.x];
             const float4 A = rec[(size_t)prim * kRecF4 + 0];
             const float4 B = rec[(size_t)prim * kRecF4 + 1];
             s_a[threadIdx.x] = A;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
     if (in) {
         const uint32_t end = last ? range.x + last[(size_t)v * W + u] : range.y;
         for (uint32_t i = range.x; i < end; ++i) {
-            const uint32_t id = tl.inst_prim[tl.sorted[i]];
+            const uint32_t id = tl.prim[i];
             const float4 A = rec[(size_t)id * kRecF4 + 0];
             const float l22 = rec[(size_t)id * kRecF4 + 1].x;
             inside += mahalanobis2(px, py, A.x, A.y, A.z, A.w, l22) <= cutoff2;

@@ -11,35 +11,40 @@
 namespace wipes {
 namespace {
 
-__global__ void __launch_bounds__(kTilePixels) k_blend3d(BlendJob job) { blend3d_tile(job, blockIdx.x); }
+// One block per 8x8 quad, tiles taken in the given order (longest list first).
+__global__ void __launch_bounds__(kQuadThreads) k_blend3d(BlendJob job, const uint32_t* __restrict__ order) {
+    blend3d_quad(job, (int)order[blockIdx.x >> 2], (int)(blockIdx.x & 3u));
+}
 
 // Image-plane gradient per primitive (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b o
 constexpr int kG = 12;
 
 // Backward.  Each pixel walks its tile list back to front from its last contributor, recovering
 // the transmittance in front of each contributor as T_i = T_{i+1} / (1 - alpha_i) from the stored
-// final value.  Warps visit only the primitives marked for their sub-tile; a warp's per-pixel
-// gradients of one primitive are summed by a reduce-scatter and added to the primitive's
-// image-plane gradient with one atomic per component.
-__global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __restrict__ rec,
-                                                            const PixRect* __restrict__ rect, TileLists tl, int W,
-                                                            int H, int tiles_x, BlendOpts3 o,
-                                                            const float* __restrict__ T_final,
-                                                            const uint32_t* __restrict__ last,
-                                                            const float* __restrict__ dl_dout,
-                                                            float* __restrict__ grad_img) {
-    __shared__ float4 s_a[kTilePixels];
-    __shared__ float4 s_b[kTilePixels];
-    __shared__ float4 s_c[kTilePixels];
-    __shared__ uint32_t s_id[kTilePixels];
-    __shared__ uint8_t s_mask[kTilePixels];
+// final value.  Blocks of kQuadThreads take one 8x8 quad of a tile (tiles in the given order,
+// longest list first); warps visit only the entries marked for their 8x4 sub-tile, and a warp's
+// per-pixel gradients of one primitive are summed by a reduce-scatter and added to the
+// primitive's image-plane gradient with one atomic per component.  As in the forward pass, the
+// records of the next batch are loaded while the current one is processed.
+__global__ void __launch_bounds__(kQuadThreads) k_backward3d(const float4* __restrict__ rec,
+                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
+                                                             int H, int tiles_x, BlendOpts3 o,
+                                                             const float* __restrict__ T_final,
+                                                             const uint32_t* __restrict__ last,
+                                                             const float* __restrict__ dl_dout,
+                                                             float* __restrict__ grad_img,
+                                                             const uint32_t* __restrict__ order) {
+    __shared__ float4 s_a[kQuadThreads];
+    __shared__ float4 s_b[kQuadThreads];
+    __shared__ float4 s_c[kQuadThreads];
+    __shared__ uint32_t s_id[kQuadThreads];
+    __shared__ uint8_t s_mask[kQuadThreads];
     __shared__ uint32_t s_max_last;
-    const int tile = blockIdx.x;
+    const int tile = (int)order[blockIdx.x >> 2], quad = (int)(blockIdx.x & 3u);
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = tx * kTile, y0 = ty * kTile;
-    const int u = x0 + (warp & 1) * 8 + (lane & 7);
-    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int x0 = tx * kTile + (quad & 1) * 8, y0 = ty * kTile + (quad >> 1) * 8;
+    const int u = x0 + (lane & 7), v = y0 + warp * 4 + (lane >> 3);
     const bool inside = u < W && v < H;
     const float px = (float)u + 0.5f, py = (float)v + 0.5f;
     const uint2 range = tl.ranges[tile];
@@ -50,26 +55,48 @@ __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __rest
     if (inside) { g0 = dl_dout[pix * 3 + 0]; g1 = dl_dout[pix * 3 + 1]; g2 = dl_dout[pix * 3 + 2]; }
     // colour accumulated behind the current primitive, starting with the background term
     float S0 = T * o.bg[0], S1 = T * o.bg[1], S2 = T * o.bg[2];
-    if (threadIdx.x == 0) s_max_last = 0u;
+    if (t == 0) s_max_last = 0u;
     __syncthreads();
     atomicMax(&s_max_last, my_last);
     __syncthreads();
-    const uint32_t end = range.x + s_max_last;  // entries past every pixel's last contributor are skipped
-    for (int64_t b_end = end; b_end > (int64_t)range.x; b_end -= kTilePixels) {
-        const uint32_t b0 = (uint32_t)max((int64_t)range.x, b_end - kTilePixels);
-        const int n = (int)((uint32_t)b_end - b0);
+    // entries past every pixel's last contributor are skipped; batches run [b0, b_end) downwards
+    const uint32_t end = range.x + s_max_last;
+    uint32_t b_end = end;
+    uint32_t b0 = end - min(end - range.x, (uint32_t)kQuadThreads);
+    // software pipeline: records (and id) of the batch to stage next, id of the batch after it
+    float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
+    PixRect nR{0, 0, -1, -1};
+    uint32_t nid = 0u, np = 0u;
+    if (b0 + t < b_end) {
+        nid = tl.prim[b0 + t];
+        nA = rec[(size_t)nid * kRecF4 + 0];
+        nB = rec[(size_t)nid * kRecF4 + 1];
+        nC = rec[(size_t)nid * kRecF4 + 2];
+        nR = rect[nid];
+    }
+    uint32_t nb0 = b0 - min(b0 - range.x, (uint32_t)kQuadThreads);  // start of the next batch
+    if (nb0 + t < b0) np = tl.prim[nb0 + t];
+    while (b_end > range.x) {
+        const int n = (int)(b_end - b0);
         __syncthreads();
-        if ((int)threadIdx.x < n) {
-            const uint32_t id = tl.inst_prim[tl.sorted[b0 + threadIdx.x]];
-            const float4 A = rec[(size_t)id * kRecF4 + 0];
-            const float4 B = rec[(size_t)id * kRecF4 + 1];
-            s_id[threadIdx.x] = id;
-            s_a[threadIdx.x] = A;
-            s_b[threadIdx.x] = B;
-            s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[id], x0, y0, o.lim);
+        if (t < n) {
+            s_id[t] = nid;
+            s_a[t] = nA;
+            s_b[t] = nB;
+            s_c[t] = nC;
+            s_mask[t] = (uint8_t)quad_mask_ellipse(nA, nB.x, nR, x0, y0, o.lim);
         }
         __syncthreads();
+        // loads for the next two batches: [nb0, b0) and [nnb0, nb0)
+        const uint32_t nnb0 = nb0 - min(nb0 - range.x, (uint32_t)kQuadThreads);
+        if (nb0 + t < b0) {
+            nid = np;
+            nA = rec[(size_t)nid * kRecF4 + 0];
+            nB = rec[(size_t)nid * kRecF4 + 1];
+            nC = rec[(size_t)nid * kRecF4 + 2];
+            nR = rect[nid];
+        }
+        if (nnb0 + t < nb0) np = tl.prim[nnb0 + t];
         for (int c = (n - 1) & ~31; c >= 0; c -= 32) {
             const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
             uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
@@ -135,6 +162,9 @@ __global__ void __launch_bounds__(kTilePixels) k_backward3d(const float4* __rest
                 }
             }
         }
+        b_end = b0;
+        b0 = nb0;
+        nb0 = nnb0;
     }
 }
 
@@ -301,16 +331,17 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
 
 }  // namespace
 
-void launch_blend3d(const BlendJob& job, int tiles_y, cudaStream_t stream) {
-    k_blend3d<<<job.tiles_x * tiles_y, kTilePixels, 0, stream>>>(job);
+void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cudaStream_t stream) {
+    k_blend3d<<<4 * job.tiles_x * tiles_y, kQuadThreads, 0, stream>>>(job, order);
     count_launches(1);
 }
 
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
-                       const float* dl_dout, float* grad_img, cudaStream_t stream) {
-    k_backward3d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, o, T_final,
-                                                                 last, dl_dout, grad_img); count_launches(1);
+                       const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream) {
+    k_backward3d<<<4 * tiles_x * tiles_y, kQuadThreads, 0, stream>>>(rec, rect, tl, W, H, tiles_x, o, T_final,
+                                                                      last, dl_dout, grad_img, order);
+    count_launches(1);
 }
 
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
