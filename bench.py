@@ -352,9 +352,8 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         wl.step()
     torch.cuda.synchronize()
 
-    # fwd+bwd steps, L2 flushed before each, each step bracketed by CUDA events
-    lib.wipes_set_timing(ctx.handle, 1)
-    lib.wipes_get_timing(ctx.handle, None, None, 1)
+    # fwd+bwd steps, L2 flushed before each, each step bracketed by CUDA events (no events between
+    # the stages here: the library's stage brackets are taken in a separate pass below)
     launches0 = lib.wipes_kernel_launches()
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
@@ -374,6 +373,13 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     clocks = sampler.stop() if sampler else None
     launches = lib.wipes_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    # per-stage times: more steps with the library's CUDA-event brackets around each stage
+    lib.wipes_set_timing(ctx.handle, 1)
+    lib.wipes_get_timing(ctx.handle, None, None, 1)
+    for _ in range(max(3, min(args.steps, 20))):
+        flush.zero_()
+        wl.step()
+    torch.cuda.synchronize()
     stage_ms = (ctypes.c_double * 10)()
     stage_n = (ctypes.c_int64 * 10)()
     lib.wipes_get_timing(ctx.handle, stage_ms, stage_n, 1)

@@ -16,6 +16,7 @@ struct BatchTable {
 
 __global__ void __launch_bounds__(kTilePixels) k_blend_batch(const __grid_constant__ BatchTable table,
                                                              unsigned int* __restrict__ counter) {
+    pdl_enter();
     __shared__ unsigned int s_item;
     __shared__ int s_job;
     const unsigned int total = table.start[table.n_jobs];
@@ -64,7 +65,7 @@ void launch_blend_batch(const BlendJob* jobs, const int* tiles_y, int n_jobs, un
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned grid = (unsigned)std::min<long long>((long long)std::max(1, per_sm) * std::max(1, sms), s);
-    k_blend_batch<<<grid, kTilePixels, 0, stream>>>(t, counter);
+    launch_pdl(k_blend_batch, grid, kTilePixels, 0, stream, t, counter);
     count_launches(1);
 }
 

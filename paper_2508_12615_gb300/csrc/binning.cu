@@ -45,6 +45,7 @@ constexpr int kScanItems = kScanBlockElems / kThreads;  // 4
 __global__ void __launch_bounds__(kThreads) k_block_sums(const uint32_t* __restrict__ counts,
                                                          const uint32_t* __restrict__ perm, int64_t n,
                                                          unsigned long long* __restrict__ block_sums) {
+    pdl_enter();
     __shared__ unsigned long long s_warp[kWarps];
     const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
     unsigned long long s = 0;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_block_sums(const uint32_t* __restr
 
 __global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long* __restrict__ v, int nb,
                                                               unsigned long long* __restrict__ total_out) {
+    pdl_enter();
     __shared__ unsigned long long s_warp[kWarps];
     unsigned long long carry = 0;
     for (int base = 0; base < nb; base += kThreads) {
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_offsets(const uint32_t* __res
                                                            const uint32_t* __restrict__ perm, int64_t n,
                                                            const unsigned long long* __restrict__ block_offsets,
                                                            uint32_t* __restrict__ offsets) {
+    pdl_enter();
     __shared__ unsigned long long s_warp[kWarps];
     const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
     uint32_t prim[kScanItems], cnt[kScanItems];
@@ -107,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ offsets, int tiles_x, float lim,
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    uint32_t* __restrict__ inst_prim) {
+    pdl_enter();
     const int64_t j = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= n) return;
@@ -135,11 +139,13 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
 
 __global__ void k_gather_u32(uint32_t* __restrict__ out, const uint32_t* __restrict__ table,
                              const uint32_t* __restrict__ idx, int64_t n) {
+    pdl_enter();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = table[idx[i]];
 }
 
 __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+    pdl_enter();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = keys[i];
         if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
@@ -148,6 +154,7 @@ __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int64_t n, uint
 }
 
 __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
+    pdl_enter();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = (uint32_t)i;
 }
@@ -163,6 +170,7 @@ constexpr int kMaxRadix = 256;
 
 __global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                                             int nbits, uint32_t* __restrict__ hist, int nb) {
+    pdl_enter();
     __shared__ uint32_t s_cnt[kMaxRadix];
     const int radix = 1 << nbits;
     const uint32_t mask = (uint32_t)radix - 1u;
@@ -185,6 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t* __re
 // One block per digit: exclusive scan of that digit's counts over the sort blocks.
 __global__ void __launch_bounds__(kThreads) k_radix_scan_digits(uint32_t* __restrict__ hist, int nb,
                                                                 uint32_t* __restrict__ digit_totals) {
+    pdl_enter();
     __shared__ uint32_t s_warp[kWarps];
     uint32_t* row = hist + (int64_t)blockIdx.x * nb;
     uint32_t carry = 0;
@@ -207,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __
                                                               const uint32_t* __restrict__ digit_totals, int nb,
                                                               const uint32_t* __restrict__ table,
                                                               uint32_t* __restrict__ gathered) {
+    pdl_enter();
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wc[kWarps][kMaxRadix];
@@ -300,6 +310,7 @@ constexpr int kOrderThreads = 1024;
 constexpr int kOrderBuckets = 33;
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint2* __restrict__ ranges, int n_tiles,
                                                               uint32_t* __restrict__ order) {
+    pdl_enter();
     __shared__ uint32_t s_cnt[kOrderBuckets];
     __shared__ uint32_t s_cur[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0u;
@@ -328,19 +339,19 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint2* __res
 void launch_block_sums(const uint32_t* counts, const uint32_t* perm, int64_t n, unsigned long long* block_sums,
                        cudaStream_t stream) {
     if (n == 0) return;
-    k_block_sums<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, block_sums); count_launches(1);
+    launch_pdl(k_block_sums, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_sums); count_launches(1);
 }
 
 void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total, cudaStream_t stream) {
-    k_scan_block_sums<<<1, kThreads, 0, stream>>>(block_sums, nb, total); count_launches(1);
+    launch_pdl(k_scan_block_sums, 1, kThreads, 0, stream, block_sums, nb, total); count_launches(1);
 }
 
 void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,
                  const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
                  uint32_t* inst_prim, uint32_t* offsets, cudaStream_t stream) {
     if (n == 0) return;
-    k_scan_offsets<<<ceil_div(n, kScanBlockElems), kThreads, 0, stream>>>(counts, perm, n, block_offsets, offsets);
-    k_emit<<<ceil_div(n * 32, kThreads), kThreads, 0, stream>>>(counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
+    launch_pdl(k_scan_offsets, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_offsets, offsets);
+    launch_pdl(k_emit, ceil_div(n * 32, kThreads), kThreads, 0, stream, counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
                                                                 vals, inst_prim);
     count_launches(2);
 }
@@ -348,7 +359,7 @@ void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const 
 void launch_gather_u32(uint32_t* out, const uint32_t* table, const uint32_t* idx, int64_t n, cudaStream_t stream) {
     if (n == 0) return;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
-    k_gather_u32<<<grid, 256, 0, stream>>>(out, table, idx, n);
+    launch_pdl(k_gather_u32, grid, 256, 0, stream, out, table, idx, n);
     count_launches(1);
 }
 
@@ -356,18 +367,18 @@ void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, i
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, stream);
     if (n == 0) return;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
-    k_tile_ranges<<<grid, 256, 0, stream>>>(sorted_keys, n, ranges); count_launches(1);
+    launch_pdl(k_tile_ranges, grid, 256, 0, stream, sorted_keys, n, ranges); count_launches(1);
 }
 
 void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream) {
-    k_tile_order<<<1, kOrderThreads, 0, stream>>>(ranges, n_tiles, order);
+    launch_pdl(k_tile_order, 1, kOrderThreads, 0, stream, ranges, n_tiles, order);
     count_launches(1);
 }
 
 void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
     if (n == 0) return;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
-    k_iota<<<grid, 256, 0, stream>>>(v, n); count_launches(1);
+    launch_pdl(k_iota, grid, 256, 0, stream, v, n); count_launches(1);
 }
 
 int64_t radix_hist_words(int64_t n) { return (int64_t)kMaxRadix * (int64_t)ceil_div(std::max<int64_t>(n, 1), kSortTile) + kMaxRadix; }
@@ -384,10 +395,10 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
     int cur = 0, shift = 0;
     for (int p = 0; p < passes; ++p) {
         const int nbits = (bits - shift + (passes - p) - 1) / (passes - p);  // split the remaining bits evenly
-        k_radix_upsweep<<<nb, kThreads, 0, stream>>>(keys[cur], n, shift, nbits, hist, nb); count_launches(1);
-        k_radix_scan_digits<<<1 << nbits, kThreads, 0, stream>>>(hist, nb, digit_totals); count_launches(1);
+        launch_pdl(k_radix_upsweep, nb, kThreads, 0, stream, keys[cur], n, shift, nbits, hist, nb); count_launches(1);
+        launch_pdl(k_radix_scan_digits, 1 << nbits, kThreads, 0, stream, hist, nb, digit_totals); count_launches(1);
         const bool last_pass = p == passes - 1;
-        k_radix_downsweep<<<nb, kThreads, 0, stream>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
+        launch_pdl(k_radix_downsweep, nb, kThreads, 0, stream, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
                                                        nbits, hist, digit_totals, nb, last_pass ? table : nullptr,
                                                        last_pass ? gathered : nullptr);
         count_launches(1);

@@ -205,6 +205,34 @@ __device__ __forceinline__ uint32_t subtile_mask(const PixRect& r, int x0, int y
 
 // Launch helpers ---------------------------------------------------------------------------------
 
+// Programmatic dependent launch.  Every kernel of the library starts with pdl_enter(): it waits
+// until the kernel before it on the stream has completed and its writes are visible, then allows
+// the kernel after it to be scheduled.  Kernels are launched with launch_pdl(), which lets the
+// hardware start that scheduling while the previous kernel drains, so a chain of short dependent
+// kernels does not pay a full launch latency at every boundary.  Work on the stream that is not a
+// kernel launched this way (copies, memsets, events, other libraries' kernels) keeps the usual
+// stream order.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Limit of rect_touched(): cutoff^2 widened by 1 %, in binary32 (host side).
 inline float touch_limit(float cutoff) {
     volatile float k2 = cutoff * cutoff;

@@ -86,6 +86,7 @@ __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rec
 __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ params, int64_t N, int W, int H,
                                                      float cutoff, float lim, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts) {
+    pdl_enter();
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i0 < N;
     const int64_t i = live ? i0 : N - 1;  // lanes past the end repeat the last primitive, write nothing
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
                                                      int H, float cutoff, float lim, float dil, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts,
                                                      uint32_t* __restrict__ depth_keys) {
+    pdl_enter();
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i0 < N;
     const int64_t i = live ? i0 : N - 1;  // lanes past the end repeat the last primitive, write nothing
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
 
 __global__ void __launch_bounds__(256) k_deform6d(const float* __restrict__ p6, int64_t N, float t,
                                                   float* __restrict__ p3) {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float* a = p6 + i * WIPES_P6D;
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(256) k_deform6d(const float* __restrict__ p6, 
 __global__ void __launch_bounds__(256) k_deform6d_backward(const float* __restrict__ p6, int64_t N, float t,
                                                            const float* __restrict__ g3, float* __restrict__ g6,
                                                            int accumulate) {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float* a = p6 + i * WIPES_P6D;
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(256) k_deform6d_backward(const float* __restri
 void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, float4* rec, PixRect* rect,
                         uint32_t* counts, uint32_t* /*depth_keys*/, cudaStream_t stream) {
     if (N == 0) return;
-    k_footprint2d<<<ceil_div(N, 256), 256, 0, stream>>>(reinterpret_cast<const float4*>(params), N, W, H, cutoff,
+    launch_pdl(k_footprint2d, ceil_div(N, 256), 256, 0, stream, reinterpret_cast<const float4*>(params), N, W, H, cutoff,
                                                          touch_limit(cutoff), rec, rect, counts); count_launches(1);
 }
 
@@ -283,19 +287,19 @@ void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam,
     Cam c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
-    k_footprint3d<<<ceil_div(N, 256), 256, 0, stream>>>(params, N, c, W, H, cutoff, touch_limit(cutoff), dilation,
+    launch_pdl(k_footprint3d, ceil_div(N, 256), 256, 0, stream, params, N, c, W, H, cutoff, touch_limit(cutoff), dilation,
                                                          rec, rect, counts, depth_keys); count_launches(1);
 }
 
 void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream) {
     if (N == 0) return;
-    k_deform6d<<<ceil_div(N, 256), 256, 0, stream>>>(params6, N, t, params3); count_launches(1);
+    launch_pdl(k_deform6d, ceil_div(N, 256), 256, 0, stream, params6, N, t, params3); count_launches(1);
 }
 
 void launch_deform6d_backward(const float* params6, int64_t N, float t, const float* g3, float* g6, int accumulate,
                               cudaStream_t stream) {
     if (N == 0) return;
-    k_deform6d_backward<<<ceil_div(N, 256), 256, 0, stream>>>(params6, N, t, g3, g6, accumulate); count_launches(1);
+    launch_pdl(k_deform6d_backward, ceil_div(N, 256), 256, 0, stream, params6, N, t, g3, g6, accumulate); count_launches(1);
 }
 
 }  // namespace wipes

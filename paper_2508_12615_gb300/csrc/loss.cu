@@ -6,6 +6,7 @@ namespace {
 
 __global__ void __launch_bounds__(256) k_l2_loss(const float* __restrict__ img, const float* __restrict__ target,
                                                  int64_t n, float* __restrict__ grad, float* __restrict__ partials) {
+    pdl_enter();
     __shared__ float s_warp[8];
     const float scale = 2.0f / (float)n;
     float acc = 0.f;
@@ -26,6 +27,7 @@ __global__ void __launch_bounds__(256) k_l2_loss(const float* __restrict__ img, 
 }
 
 __global__ void k_l2_finish(const float* __restrict__ partials, int nb, int64_t n, float* __restrict__ loss) {
+    pdl_enter();
     __shared__ double s[32];
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) acc += partials[i];
@@ -43,8 +45,8 @@ __global__ void k_l2_finish(const float* __restrict__ partials, int nb, int64_t 
 void launch_l2_loss(const float* img, const float* target, int64_t n, float* loss, float* grad, float* partials,
                     cudaStream_t stream) {
     const int nb = (int)std::min<int64_t>(kLossBlocks, std::max<int64_t>(1, ceil_div(n, 256)));
-    k_l2_loss<<<nb, 256, 0, stream>>>(img, target, n, grad, partials); count_launches(1);
-    k_l2_finish<<<1, 32, 0, stream>>>(partials, nb, n, loss); count_launches(1);
+    launch_pdl(k_l2_loss, nb, 256, 0, stream, img, target, n, grad, partials); count_launches(1);
+    launch_pdl(k_l2_finish, 1, 32, 0, stream, partials, nb, n, loss); count_launches(1);
 }
 
 }  // namespace wipes

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_l2_loss_blocks(const float*
                                                                     const float* __restrict__ target, int64_t n,
                                                                     float* __restrict__ grad,
                                                                     float* __restrict__ partials) {
+    pdl_enter();
     __shared__ float s_warp[kNoAllocThreads / 32];
     const float scale = 2.0f / (float)n;
     const int64_t base = (int64_t)blockIdx.x * kNoAllocBlockElems + threadIdx.x;
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_l2_loss_blocks(const float*
 // Sum the block partials in a fixed order (binary64 accumulation) and divide by n.
 __global__ void __launch_bounds__(kNoAllocThreads) k_l2_loss_total(const float* __restrict__ partials, int nb,
                                                                    int64_t n, float* __restrict__ loss) {
+    pdl_enter();
     __shared__ double s[kNoAllocThreads];
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += kNoAllocThreads) acc += partials[i];
@@ -100,8 +102,8 @@ cudaError_t l2_loss_noalloc(const float* img, const float* target, int64_t n, fl
     cudaError_t e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return e;
     const int nb = (int)ceil_div(n, kNoAllocBlockElems);
-    k_l2_loss_blocks<<<nb, kNoAllocThreads, 0, stream>>>(img, target, n, grad, scratch);
-    k_l2_loss_total<<<1, kNoAllocThreads, 0, stream>>>(scratch, nb, n, loss);
+    launch_pdl(k_l2_loss_blocks, nb, kNoAllocThreads, 0, stream, img, target, n, grad, scratch);
+    launch_pdl(k_l2_loss_total, 1, kNoAllocThreads, 0, stream, scratch, nb, n, loss);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -13,7 +13,7 @@
 namespace wipes {
 namespace {
 
-__global__ void __launch_bounds__(kTilePixels) k_blend2d(BlendJob job) { blend2d_tile(job, blockIdx.x); }
+__global__ void __launch_bounds__(kTilePixels) k_blend2d(BlendJob job) { pdl_enter(); blend2d_tile(job, blockIdx.x); }
 
 // Partial gradient slot layout (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b 0
 constexpr int kSlot = 12;
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __r
                                                             int H, int tiles_x, float cutoff2, float lim,
                                                             const float* __restrict__ dl_dout,
                                                             float* __restrict__ partial) {
+    pdl_enter();
     __shared__ float4 s_g[kTilePixels];  // dL/dimage of the tile, one float4 per pixel (w unused)
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
                                                         const uint32_t* __restrict__ counts,
                                                         const float* __restrict__ partial,
                                                         float* __restrict__ dl_dparams) {
+    pdl_enter();
     const int64_t prim = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (prim >= N) return;
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
                                                              int H, int tiles_x, float cutoff2,
                                                              const uint32_t* __restrict__ last,
                                                              unsigned long long* __restrict__ counters) {
+    pdl_enter();
     __shared__ unsigned long long s_sum[2];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -231,27 +234,27 @@ __global__ void __launch_bounds__(kTilePixels) k_count_pairs(const float4* __res
 }  // namespace
 
 void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream) {
-    k_blend2d<<<job.tiles_x * tiles_y, kTilePixels, 0, stream>>>(job);
+    launch_pdl(k_blend2d, job.tiles_x * tiles_y, kTilePixels, 0, stream, job);
     count_launches(1);
 }
 
 void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream) {
-    k_backward2d<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, rect, tl, W, H, tiles_x, cutoff * cutoff,
+    launch_pdl(k_backward2d, tiles_x * tiles_y, kTilePixels, 0, stream, rec, rect, tl, W, H, tiles_x, cutoff * cutoff,
                                                                  touch_limit(cutoff), dl_dout, partial);
     count_launches(1);
 }
 
 void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
                         const uint32_t* last, unsigned long long* counters, cudaStream_t stream) {
-    k_count_pairs<<<tiles_x * tiles_y, kTilePixels, 0, stream>>>(rec, tl, W, H, tiles_x, cutoff2, last, counters);
+    launch_pdl(k_count_pairs, tiles_x * tiles_y, kTilePixels, 0, stream, rec, tl, W, H, tiles_x, cutoff2, last, counters);
     count_launches(1);
 }
 
 void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
-    k_reduce_chain2d<<<ceil_div(N * 32, 256), 256, 0, stream>>>(params, N, offsets, counts, partial, dl_dparams);
+    launch_pdl(k_reduce_chain2d, ceil_div(N * 32, 256), 256, 0, stream, params, N, offsets, counts, partial, dl_dparams);
     count_launches(1);
 }
 

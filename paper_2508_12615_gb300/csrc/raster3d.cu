@@ -13,6 +13,7 @@ namespace {
 
 // One block per 8x8 quad, tiles taken in the given order (longest list first).
 __global__ void __launch_bounds__(kQuadThreads) k_blend3d(BlendJob job, const uint32_t* __restrict__ order) {
+    pdl_enter();
     blend3d_quad(job, (int)order[blockIdx.x >> 2], (int)(blockIdx.x & 3u));
 }
 
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_backward3d(const float4* __res
                                                              const float* __restrict__ dl_dout,
                                                              float* __restrict__ grad_img,
                                                              const uint32_t* __restrict__ order) {
+    pdl_enter();
     __shared__ float4 s_a[kQuadThreads];
     __shared__ float4 s_b[kQuadThreads];
     __shared__ float4 s_c[kQuadThreads];
@@ -199,6 +201,7 @@ __device__ __forceinline__ void quat_rot_grad(const float q[4], const float gR[9
 __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ params, int64_t N, Cam3 cam, int W, int H,
                                                  float dil, const float4* __restrict__ rec,
                                                  const float* __restrict__ grad_img, float* __restrict__ dl_dparams) {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float* out = dl_dparams + i * WIPES_P3D;
@@ -332,14 +335,14 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
 }  // namespace
 
 void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cudaStream_t stream) {
-    k_blend3d<<<4 * job.tiles_x * tiles_y, kQuadThreads, 0, stream>>>(job, order);
+    launch_pdl(k_blend3d, 4 * job.tiles_x * tiles_y, kQuadThreads, 0, stream, job, order);
     count_launches(1);
 }
 
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
                        const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream) {
-    k_backward3d<<<4 * tiles_x * tiles_y, kQuadThreads, 0, stream>>>(rec, rect, tl, W, H, tiles_x, o, T_final,
+    launch_pdl(k_backward3d, 4 * tiles_x * tiles_y, kQuadThreads, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final,
                                                                       last, dl_dout, grad_img, order);
     count_launches(1);
 }
@@ -350,7 +353,7 @@ void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int
     Cam3 c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
-    k_chain3d<<<ceil_div(N, 128), 128, 0, stream>>>(params, N, c, W, H, dilation, rec, grad_img, dl_dparams); count_launches(1);
+    launch_pdl(k_chain3d, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, rec, grad_img, dl_dparams); count_launches(1);
 }
 
 }  // namespace wipes
