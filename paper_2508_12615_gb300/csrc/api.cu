@@ -117,7 +117,8 @@ struct wipes_ctx {
     int device = 0;
     MemAccount mem;
     std::atomic<int64_t> live_states{0};  // a context is not destroyed while states refer to it
-    unsigned long long* h_total = nullptr;  // pinned readback of the instance count
+    unsigned long long* h_total = nullptr;  // pinned readback: [0] instance count, [1] device error word
+    unsigned int* d_error = nullptr;        // device error word: bit 0 = a bounded device wait ran out
     float* d_loss_partials = nullptr;
     unsigned long long* d_counters = nullptr;  // pair counters
     unsigned int* d_batch_counters = nullptr;  // work counters of in-flight batch launches (a ring)
@@ -210,6 +211,15 @@ wipes_status check_image(int H, int W) {
     return WIPES_OK;
 }
 
+// The device error word as last read back into h_total[1]: a set bit is reported once and cleared.
+wipes_status take_device_error(wipes_ctx* ctx, cudaStream_t s) {
+    if (ctx->h_total[1] == 0) return WIPES_OK;
+    ctx->h_total[1] = 0;
+    WIPES_CUDA(cudaMemsetAsync(ctx->d_error, 0, sizeof(unsigned long long), s));
+    return fail(WIPES_ERR_TIMEOUT, "a bounded device wait ran out (radix sort look-back); results of the "
+                                   "calls since the last check are undefined");
+}
+
 // Scan the per-primitive tile counts (in `perm` order when given), read the instance total back,
 // size the instance buffers, emit the pairs and sort them by tile (stable).
 wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s) {
@@ -225,9 +235,12 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
         launch_block_sums(st->counts.as<uint32_t>(), perm, N, st->block_sums.as<unsigned long long>(), s);
         launch_scan_block_sums(st->block_sums.as<unsigned long long>(), nb, total, s);
         WIPES_CUDA(cudaMemcpyAsync(st->ctx->h_total, total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        WIPES_CUDA(cudaMemcpyAsync(st->ctx->h_total + 1, st->ctx->d_error, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, s));
         t.stop();
         WIPES_CUDA(cudaStreamSynchronize(s));
-        st->n_inst = (int64_t)*st->ctx->h_total;
+        st->n_inst = (int64_t)st->ctx->h_total[0];
+        WIPES_TRY(take_device_error(st->ctx, s));
     } else {
         st->n_inst = 0;
     }
@@ -252,7 +265,7 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
     uint32_t* vb[2] = {st->vals[0].as<uint32_t>(), st->vals[1].as<uint32_t>()};
     {
         StageTimer t(st->ctx, WIPES_STAGE_TILE_SORT, s);
-        st->sorted = radix_sort_pairs(kb, vb, I, ceil_log2(n_tiles), st->hist.as<uint32_t>(), s,
+        st->sorted = radix_sort_pairs(kb, vb, I, ceil_log2(n_tiles), st->hist.as<uint32_t>(), st->ctx->d_error, s,
                                       st->inst_prim.as<uint32_t>(), st->sprim.as<uint32_t>());
     }
     {
@@ -349,7 +362,9 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     DeviceGuard g(device);
     wipes_ctx* c = new wipes_ctx();
     c->device = device;
-    cudaError_t e = cudaMallocHost(&c->h_total, sizeof(unsigned long long));
+    cudaError_t e = cudaMallocHost(&c->h_total, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_error, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_error, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_loss_partials, sizeof(float) * kLossBlocks);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_batch_counters, sizeof(unsigned int) * kBatchCounterSlots);
@@ -377,6 +392,7 @@ wipes_status wipes_destroy(wipes_ctx* ctx) {
     cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_loss_partials);
     cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_error);
     cudaFree(ctx->d_batch_counters);
     delete ctx;
     return WIPES_OK;
@@ -473,7 +489,7 @@ wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* param
     {
         StageTimer t(ctx, WIPES_STAGE_DEPTH_SORT, s);
         launch_iota(st->dvals[0].as<uint32_t>(), N, s);
-        cur = radix_sort_pairs(dk, dv, N, 32, st->hist.as<uint32_t>(), s);
+        cur = radix_sort_pairs(dk, dv, N, 32, st->hist.as<uint32_t>(), ctx->d_error, s);
     }
     WIPES_TRY(bin_and_sort(st, dv[cur], s));
     {
@@ -720,9 +736,12 @@ const char* wipes_last_error(void) { return g_last_error.c_str(); }
 wipes_status wipes_sync_status(wipes_ctx* ctx, void* stream) {
     if (!ctx) return fail(WIPES_ERR_INVALID, "null ctx");
     DeviceGuard g(ctx->device);
-    WIPES_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    WIPES_CUDA(cudaStreamSynchronize(s));
     WIPES_CUDA(cudaGetLastError());
-    return WIPES_OK;
+    WIPES_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->d_error, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    WIPES_CUDA(cudaStreamSynchronize(s));
+    return take_device_error(ctx, s);
 }
 
 }  // extern "C"

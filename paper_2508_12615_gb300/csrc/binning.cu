@@ -160,62 +160,87 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass
-// (reduce-then-scan: per-block digit histograms, per-digit scan, stable scatter)
+// stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass, one kernel per
+// pass.  k_sort_histogram counts every pass's digits over all keys once.  In a pass, blocks take
+// tiles of 4096 keys in index order from a counter, rank their keys stably, publish each digit's
+// count for their tile and obtain the counts of all earlier tiles by a decoupled look-back over
+// the published words (a word holds a tile's count, or the inclusive prefix up to that tile,
+// with a flag in its top bits).  Every look-back wait is bounded: when it runs out, the block
+// sets bit 0 of the error word and stops looking; the host reports WIPES_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------------------------
 
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kThreads * kSortItems;  // 4096 keys per block
 constexpr int kMaxRadix = 256;
+constexpr int kMaxPasses = 4;
+constexpr unsigned long long kAggregate = 1ull << 62, kPrefix = 2ull << 62, kCountMask = (1ull << 62) - 1ull;
+constexpr int kMaxLookbackPolls = 1 << 21;
+constexpr int kLookback = 8;
 
-__global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                            int nbits, uint32_t* __restrict__ hist, int nb) {
+struct SortPlan {
+    int passes;
+    int shift[kMaxPasses];
+    int nbits[kMaxPasses];
+};
+
+// Workspace (32-bit words): digit totals [kMaxPasses][kMaxRadix] | tile counters [kMaxPasses] |
+// look-back words [kMaxPasses][tiles][kMaxRadix] (64-bit, 8-byte aligned).
+__host__ __device__ inline int64_t sort_status_offset_words() { return (int64_t)kMaxPasses * kMaxRadix + kMaxPasses; }
+
+// A look-back word carries its own value (count and flag in one 64-bit word) and nothing else is
+// read on its account, so relaxed gpu-scope accesses suffice; unlike acquire loads they let the
+// loads of several predecessors be in flight at once.
+__device__ __forceinline__ void store_word(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long load_word(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_histogram(const uint32_t* __restrict__ keys, int64_t n,
+                                                             SortPlan plan, uint32_t* __restrict__ totals) {
     pdl_enter();
-    __shared__ uint32_t s_cnt[kMaxRadix];
-    const int radix = 1 << nbits;
-    const uint32_t mask = (uint32_t)radix - 1u;
-    for (int d = threadIdx.x; d < radix; d += kThreads) s_cnt[d] = 0u;
+    __shared__ uint32_t s_cnt[kMaxPasses][kMaxRadix];
+    for (int k = threadIdx.x; k < kMaxPasses * kMaxRadix; k += kThreads) (&s_cnt[0][0])[k] = 0u;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
     const int lane = threadIdx.x & 31;
-#pragma unroll 4
-    for (int i = 0; i < kSortItems; ++i) {
-        const int64_t idx = base + (int64_t)i * kThreads + threadIdx.x;
-        const bool valid = idx < n;
-        const uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+    constexpr int kUnroll = 4;
+    for (int64_t base = (int64_t)blockIdx.x * kThreads * kUnroll; base < n;
+         base += (int64_t)gridDim.x * kThreads * kUnroll) {
+        uint32_t key[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t idx = base + u * kThreads + threadIdx.x;
+            key[u] = idx < n ? keys[idx] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool valid = base + u * kThreads + threadIdx.x < n;
+            for (int p = 0; p < plan.passes; ++p) {
+                const uint32_t d = valid ? (key[u] >> plan.shift[p]) & ((1u << plan.nbits[p]) - 1u) : 0xFFFFu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[p][d], (uint32_t)__popc(peers));
+            }
+        }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += kThreads) hist[(int64_t)d * nb + blockIdx.x] = s_cnt[d];
+    for (int p = 0; p < plan.passes; ++p)
+        for (int d = threadIdx.x; d < (1 << plan.nbits[p]); d += kThreads)
+            if (s_cnt[p][d]) atomicAdd(&totals[p * kMaxRadix + d], s_cnt[p][d]);
 }
 
-// One block per digit: exclusive scan of that digit's counts over the sort blocks.
-__global__ void __launch_bounds__(kThreads) k_radix_scan_digits(uint32_t* __restrict__ hist, int nb,
-                                                                uint32_t* __restrict__ digit_totals) {
-    pdl_enter();
-    __shared__ uint32_t s_warp[kWarps];
-    uint32_t* row = hist + (int64_t)blockIdx.x * nb;
-    uint32_t carry = 0;
-    for (int base = 0; base < nb; base += kThreads) {
-        const int j = base + threadIdx.x;
-        const uint32_t x = j < nb ? row[j] : 0u;
-        uint32_t chunk;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(x, &chunk, s_warp);
-        if (j < nb) row[j] = carry + ex;
-        carry += chunk;
-    }
-    if (threadIdx.x == 0) digit_totals[blockIdx.x] = carry;
-}
-
-__global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __restrict__ keys_in,
-                                                              const uint32_t* __restrict__ vals_in,
-                                                              uint32_t* __restrict__ keys_out,
-                                                              uint32_t* __restrict__ vals_out, int64_t n, int shift,
-                                                              int nbits, const uint32_t* __restrict__ hist,
-                                                              const uint32_t* __restrict__ digit_totals, int nb,
-                                                              const uint32_t* __restrict__ table,
-                                                              uint32_t* __restrict__ gathered) {
+__global__ void __launch_bounds__(kThreads) k_sort_pass(const uint32_t* __restrict__ keys_in,
+                                                        const uint32_t* __restrict__ vals_in,
+                                                        uint32_t* __restrict__ keys_out,
+                                                        uint32_t* __restrict__ vals_out, int64_t n, int shift,
+                                                        int nbits, const uint32_t* __restrict__ totals,
+                                                        unsigned int* __restrict__ tile_counter,
+                                                        unsigned long long* __restrict__ status,
+                                                        unsigned int* __restrict__ error,
+                                                        const uint32_t* __restrict__ table,
+                                                        uint32_t* __restrict__ gathered) {
     pdl_enter();
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
@@ -223,18 +248,21 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __
     __shared__ uint32_t s_dstart[kMaxRadix];
     __shared__ uint32_t s_gbase[kMaxRadix];
     __shared__ uint32_t s_warp[kWarps];
+    __shared__ uint32_t s_tile;
     const int radix = 1 << nbits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
     for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_wc[0][0])[k] = 0u;
     // global start of each digit = exclusive scan of the digit totals
     {
-        const uint32_t x = (int)threadIdx.x < radix ? digit_totals[threadIdx.x] : 0u;
+        const uint32_t x = (int)threadIdx.x < radix ? totals[threadIdx.x] : 0u;
         const uint32_t ex = block_exclusive_scan<uint32_t>(x, nullptr, s_warp);
-        if ((int)threadIdx.x < radix) s_gbase[threadIdx.x] = ex + hist[(int64_t)threadIdx.x * nb + blockIdx.x];
+        if ((int)threadIdx.x < radix) s_gbase[threadIdx.x] = ex;
     }
     __syncthreads();
-    const int64_t blk = (int64_t)blockIdx.x * kSortTile;
+    const uint32_t tile = s_tile;
+    const int64_t blk = (int64_t)tile * kSortTile;
     const int64_t base = blk + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
@@ -261,17 +289,58 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __
         __syncwarp();
     }
     __syncthreads();
-    // per digit: prefix over warps, then block-local digit starts
-    {
-        uint32_t running = 0;
-        if ((int)threadIdx.x < radix) {
+    // per digit: prefix over warps, the tile's count, the counts of all earlier tiles (look-back)
+    uint32_t running = 0;
+    if ((int)threadIdx.x < radix) {
+        const int d = threadIdx.x;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t t = s_wc[w][threadIdx.x];
-                s_wc[w][threadIdx.x] = running;
-                running += t;
-            }
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = s_wc[w][d];
+            s_wc[w][d] = running;
+            running += t;
         }
+        unsigned long long* mine = status + (size_t)tile * kMaxRadix + d;
+        unsigned long long before = 0;
+        if (tile == 0) {
+            store_word(mine, kPrefix | running);
+        } else {
+            store_word(mine, kAggregate | running);
+            // walk back kLookback tiles per step (their words are loaded together), adding
+            // aggregates until an inclusive prefix; a tile that has published nothing yet is polled
+            int polls = 0;
+            for (int64_t t = (int64_t)tile - 1; t >= 0;) {
+                unsigned long long w[kLookback];
+#pragma unroll
+                for (int j = 0; j < kLookback; ++j)
+                    w[j] = t - j >= 0 ? load_word(status + (size_t)(t - j) * kMaxRadix + d) : kPrefix;
+                bool done = false;
+                int used = 0;
+#pragma unroll
+                for (int j = 0; j < kLookback; ++j) {
+                    if (done || used < j) continue;  // stopped at a prefix or at an unpublished tile
+                    if (w[j] & kPrefix) {
+                        if (t - j >= 0) before += w[j] & kCountMask;
+                        done = true;
+                    } else if (w[j] & kAggregate) {
+                        before += w[j] & kCountMask;
+                        used = j + 1;
+                    }
+                }
+                if (done) break;
+                t -= used;
+                if (used == 0) {
+                    if (++polls > kMaxLookbackPolls) {
+                        atomicOr(error, 1u);
+                        break;
+                    }
+                    if (polls > 64) __nanosleep(128);
+                }
+            }
+            store_word(mine, kPrefix | (before + running));
+        }
+        s_gbase[d] += (uint32_t)before;
+    }
+    {
         const uint32_t ex = block_exclusive_scan<uint32_t>(running, nullptr, s_warp);
         if ((int)threadIdx.x < radix) {
             s_dstart[threadIdx.x] = ex;
@@ -295,6 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t* __
         const uint32_t key = s_keys[t];
         const uint32_t d = (key >> shift) & mask;
         const uint32_t g = s_gbase[d] + (uint32_t)t;
+        if ((int64_t)g >= n) continue;  // only after a look-back that ran out (error word set)
         const uint32_t val = s_vals[t];
         keys_out[g] = key;
         vals_out[g] = val;
@@ -381,29 +451,42 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
     launch_pdl(k_iota, grid, 256, 0, stream, v, n); count_launches(1);
 }
 
-int64_t radix_hist_words(int64_t n) { return (int64_t)kMaxRadix * (int64_t)ceil_div(std::max<int64_t>(n, 1), kSortTile) + kMaxRadix; }
+int64_t radix_hist_words(int64_t n) {
+    const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kSortTile);
+    return sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
+}
 
-int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream,
-                     const uint32_t* table, uint32_t* gathered) {
+int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, unsigned int* error,
+                     cudaStream_t stream, const uint32_t* table, uint32_t* gathered) {
     if (n <= 1 || bits <= 0) {
         if (table) launch_gather_u32(gathered, table, vals[0], n, stream);
         return 0;
     }
-    const int passes = (bits + 7) / 8;
-    const int nb = (int)ceil_div(n, kSortTile);
-    uint32_t* digit_totals = hist + (int64_t)kMaxRadix * nb;
-    int cur = 0, shift = 0;
-    for (int p = 0; p < passes; ++p) {
-        const int nbits = (bits - shift + (passes - p) - 1) / (passes - p);  // split the remaining bits evenly
-        launch_pdl(k_radix_upsweep, nb, kThreads, 0, stream, keys[cur], n, shift, nbits, hist, nb); count_launches(1);
-        launch_pdl(k_radix_scan_digits, 1 << nbits, kThreads, 0, stream, hist, nb, digit_totals); count_launches(1);
-        const bool last_pass = p == passes - 1;
-        launch_pdl(k_radix_downsweep, nb, kThreads, 0, stream, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
-                                                       nbits, hist, digit_totals, nb, last_pass ? table : nullptr,
-                                                       last_pass ? gathered : nullptr);
+    SortPlan plan{};
+    plan.passes = (bits + 7) / 8;
+    for (int p = 0, shift = 0; p < plan.passes; ++p) {
+        plan.nbits[p] = (bits - shift + (plan.passes - p) - 1) / (plan.passes - p);  // split the remaining bits evenly
+        plan.shift[p] = shift;
+        shift += plan.nbits[p];
+    }
+    const int64_t tiles = ceil_div(n, kSortTile);
+    uint32_t* totals = hist;
+    unsigned int* counters = hist + (int64_t)kMaxPasses * kMaxRadix;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(hist + sort_status_offset_words());
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)sort_status_offset_words() +
+                                 sizeof(unsigned long long) * (size_t)(plan.passes * tiles * kMaxRadix), stream);
+    const unsigned hgrid = (unsigned)std::min<int64_t>(ceil_div(n, kThreads * 4), 152 * 4);
+    launch_pdl(k_sort_histogram, hgrid, kThreads, 0, stream, keys[0], n, plan, totals);
+    count_launches(1);
+    int cur = 0;
+    for (int p = 0; p < plan.passes; ++p) {
+        const bool last_pass = p == plan.passes - 1;
+        launch_pdl(k_sort_pass, (unsigned)tiles, kThreads, 0, stream, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
+                   plan.shift[p], plan.nbits[p], totals + p * kMaxRadix, counters + p,
+                   status + (size_t)p * tiles * kMaxRadix, error, last_pass ? table : nullptr,
+                   last_pass ? gathered : nullptr);
         count_launches(1);
         cur ^= 1;
-        shift += nbits;
     }
     return cur;
 }

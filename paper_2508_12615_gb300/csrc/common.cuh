@@ -275,11 +275,12 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream);
 
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  Uses (keys[0], vals[0]) as
 // input and (keys[1], vals[1]) as ping-pong space; returns which buffer index holds the result.
-// `hist` must hold radix_hist_words(n) words.  With a table, the last pass also writes
-// gathered[i] = table[sorted value i].
+// `hist` must hold radix_hist_words(n) words (8-byte aligned).  With a table, the last pass also
+// writes gathered[i] = table[sorted value i].  A look-back wait that runs out sets bit 0 of
+// *error (device memory) and leaves the result undefined.
 int64_t radix_hist_words(int64_t n);
-int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, cudaStream_t stream,
-                     const uint32_t* table = nullptr, uint32_t* gathered = nullptr);
+int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, unsigned int* error,
+                     cudaStream_t stream, const uint32_t* table = nullptr, uint32_t* gathered = nullptr);
 // order[0 .. n_tiles) = the tiles, longest list first (see k_tile_order)
 void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream);
 
