@@ -215,8 +215,17 @@ int64_t wipes_kernel_launches(void);
 const char* wipes_status_string(wipes_status s);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* wipes_last_error(void);
-/* Synchronise `stream` and report any pending CUDA error. */
+/* Synchronise `stream` and report any pending CUDA error, then any error latched on the device
+ * since the last check: WIPES_ERR_TIMEOUT when a bounded device wait (the radix sort's look-back
+ * over earlier tiles) ran out; the results of the calls enqueued since are then undefined.  A
+ * latched error is reported once. */
 wipes_status wipes_sync_status(wipes_ctx* ctx, void* stream);
+
+/* Diagnostic: run one radix-sort pass on scratch data in which the tile before the block's tile
+ * never publishes its counts, so that the block's bounded look-back runs out (after well under a
+ * second).  Returns WIPES_ERR_TIMEOUT when the wait ran out and was reported, as it should; the
+ * context stays usable.  Allocates and frees about 200 KB of scratch; synchronises `stream`. */
+wipes_status wipes_selftest_sort_timeout(wipes_ctx* ctx, void* stream);
 
 #ifdef __cplusplus
 }

@@ -63,6 +63,7 @@ _SIGNATURES = {
     "wipes_status_string": (c_char_p, [c_int]),
     "wipes_last_error": (c_char_p, []),
     "wipes_sync_status": (c_int, [_P, _P]),
+    "wipes_selftest_sort_timeout": (c_int, [_P, _P]),
     "wipes_state_count_pairs": (c_int, [_P, _P, _P, _P, _P]),
     "wipes_set_timing": (c_int, [_P, c_int]),
     "wipes_get_timing": (c_int, [_P, _P, _P, c_int]),

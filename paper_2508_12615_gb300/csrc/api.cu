@@ -744,4 +744,18 @@ wipes_status wipes_sync_status(wipes_ctx* ctx, void* stream) {
     return take_device_error(ctx, s);
 }
 
+wipes_status wipes_selftest_sort_timeout(wipes_ctx* ctx, void* stream) {
+    if (!ctx) return fail(WIPES_ERR_INVALID, "null ctx");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // report (and clear) anything latched before, so that the result is this probe's
+    WIPES_TRY(wipes_sync_status(ctx, stream));
+    void* ws = nullptr;
+    WIPES_CUDA(cudaMalloc(&ws, sizeof(uint32_t) * (size_t)sort_timeout_probe_words()));
+    sort_timeout_probe(static_cast<uint32_t*>(ws), ctx->d_error, s);
+    const wipes_status st = wipes_sync_status(ctx, stream);
+    cudaFree(ws);
+    return st;
+}
+
 }  // extern "C"

@@ -491,4 +491,25 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
     return cur;
 }
 
+// Scratch words of sort_timeout_probe(): keys and values in and out for two tiles, the digit
+// totals, the pass's tile counter and the look-back words of two tiles.
+int64_t sort_timeout_probe_words() { return 4 * 2 * kSortTile + sort_status_offset_words() + 2 * 2 * kMaxRadix; }
+
+void sort_timeout_probe(uint32_t* ws, unsigned int* error, cudaStream_t stream) {
+    const int64_t n = 2 * kSortTile;
+    uint32_t* keys_in = ws;
+    uint32_t* vals_in = ws + n;
+    uint32_t* keys_out = ws + 2 * n;
+    uint32_t* vals_out = ws + 3 * n;
+    uint32_t* hist = ws + 4 * n;  // 8-byte aligned: 4 n words from an aligned base
+    unsigned int* counter = hist + (int64_t)kMaxPasses * kMaxRadix;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(hist + sort_status_offset_words());
+    cudaMemsetAsync(ws, 0, sizeof(uint32_t) * (size_t)sort_timeout_probe_words(), stream);
+    // the pass's counter starts at 1: the single block takes tile 1 and tile 0 is never published
+    cudaMemsetAsync(counter, 1, 1, stream);
+    launch_pdl(k_sort_pass, 1u, kThreads, 0, stream, keys_in, vals_in, keys_out, vals_out, n, 0, 8, hist, counter,
+               status, error, (const uint32_t*)nullptr, (uint32_t*)nullptr);
+    count_launches(1);
+}
+
 }  // namespace wipes

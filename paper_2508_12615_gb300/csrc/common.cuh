@@ -281,6 +281,10 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream);
 int64_t radix_hist_words(int64_t n);
 int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, unsigned int* error,
                      cudaStream_t stream, const uint32_t* table = nullptr, uint32_t* gathered = nullptr);
+// Diagnostic: one sort pass over sort_timeout_probe_words() words of scratch whose predecessor
+// tile never publishes; its look-back runs out and sets bit 0 of *error.
+int64_t sort_timeout_probe_words();
+void sort_timeout_probe(uint32_t* ws, unsigned int* error, cudaStream_t stream);
 // order[0 .. n_tiles) = the tiles, longest list first (see k_tile_order)
 void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream);
 
