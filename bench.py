@@ -48,9 +48,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["2d", "5d", "6d"], default="2d",
-                    help="2d: the 768x512 / 70k image-fitting workload (default, the headline); "
-                         "5d: 800x800 / 300k static scene; 6d: 1352x1014 / 200k dynamic scene, 4 samples per step")
+    ap.add_argument("--workload", choices=["2d", "2dchol", "5d", "6d"], default="2d",
+                    help="2d: the 768x512 / 70k image-fitting workload (default, the headline); 2dchol: the "
+                         "same with the Cholesky covariance record; 5d: 800x800 / 300k static scene; 6d: "
+                         "1352x1014 / 200k dynamic scene, 4 samples per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=10.0, help="length of the serving request trace")
@@ -237,6 +238,13 @@ class Workload:
             self.name, self.H, self.W, self.seed = WORKLOAD, c.H, c.W, c.seed
             self.samples = [None]
             self.opts = w.make_opts(2)
+        elif kind == "2dchol":
+            c = synth.CFG1_2D_KODAK
+            _, target = synth.cfg1_inputs()
+            p = synth.scene2d_cholesky(c.n, c.H, c.W, c.seed, (0.5, 32.0))
+            self.name, self.H, self.W, self.seed = "2d_cholesky_768x512_n70000", c.H, c.W, c.seed
+            self.samples = [None]
+            self.opts = w.make_opts(2, cov2d=1)
         elif kind == "5d":
             c = synth.CFG2_5D
             p, cams = synth.cfg2_inputs()
@@ -275,7 +283,7 @@ class Workload:
 
     def _one(self, params, target, accumulate=False, fwd_only=False):
         w = self.w
-        if self.kind == "2d":
+        if self.kind in ("2d", "2dchol"):
             w.forward2d(params, self.H, self.W, self.opts, state=self.st, out=self.img)
             if fwd_only:
                 return
@@ -431,7 +439,7 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     pk, pk_kind = peaks()
     clock_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tops = SMS * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
-    dims = "2d" if wl.kind == "2d" else "3d"
+    dims = "2d" if wl.kind in ("2d", "2dchol") else "3d"
     fp32_ops, mufu_ops = OPS_PER_PAIR[dims][dom]
     launch_s = stages[dom]["ms_per_launch"] * 1e-3
     pairs_per_launch = inside / wl.batch

@@ -25,7 +25,9 @@
  *
  * Record layouts:
  *   2D [N,16]: mu_x, mu_y, s_x, s_y, theta, f_x, f_y, phi, c_r, c_g, c_b, (5 unused)
- *              Sigma = R(theta) diag(s_x^2, s_y^2) R(theta)^T (RS form, Sec. 5.1)
+ *              Sigma = R(theta) diag(s_x^2, s_y^2) R(theta)^T (RS form, Sec. 5.1), or with
+ *              wipes_opts.cov2d = 1: mu_x, mu_y, l1, l2, l3, f_x, f_y, phi, c_r, c_g, c_b, (5 unused),
+ *              Sigma = L L^T with L = [[l1, 0], [l2, l3]], l1 l3 != 0 (Cholesky form, Sec. 5.1)
  *   3D [N,20]: mu(3), s(3), q(w,x,y,z), f(3), phi, opacity, c(3), (2 unused)
  *              Sigma = R(q/|q|) S S^T R^T (Sec. 3.1); q need not be normalised
  *   6D [N,32]: the 3D record followed by v(3), df(3), dphi, dlog_s(3), (2 unused)
@@ -66,7 +68,7 @@ typedef struct {
 } wipes_camera;
 
 /* Rendering options.  Defaults (wipes_default_opts): cutoff_sigma 3, alpha_min 1/255,
- * alpha_max 0.99, T_min 1e-4, dilation 0.3 px^2 (3D) / 0 (2D), bg 0, freq_proj_mode 0. */
+ * alpha_max 0.99, T_min 1e-4, dilation 0.3 px^2 (3D) / 0 (2D), bg 0, freq_proj_mode 0, cov2d 0. */
 typedef struct {
     float cutoff_sigma;     /* a primitive counts at a pixel iff its squared Mahalanobis distance <= cutoff^2 */
     float alpha_min;        /* 3D: alpha below this is skipped */
@@ -75,7 +77,7 @@ typedef struct {
     float dilation;         /* 3D: added to the diagonal of Sigma' (px^2); ignored in 2D */
     float bg[3];            /* 3D: background colour, weighted by the final transmittance */
     int32_t freq_proj_mode; /* 3D: 0 = phase gradient on the fronto-parallel plane (only mode) */
-    int32_t reserved;
+    int32_t cov2d;          /* 2D: 0 = RS record (s_x, s_y, theta), 1 = Cholesky record (l1, l2, l3) */
 } wipes_opts;
 
 /* Fill `out` with the defaults for dims = 2 or 3. */

@@ -48,8 +48,8 @@ def _load():
         lib.wo_footprints.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P, P, P]
         lib.wo_tile_lists.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P, P, i64]
         lib.wo_tile_lists.restype = i64
-        lib.wo_render2d.argtypes = [P, i64, i32, i32, f32, i32, P, i64, P]
-        lib.wo_grad2d.argtypes = [P, i64, i32, i32, f32, i32, P, P, P]
+        lib.wo_render2d.argtypes = [P, i64, i32, i32, f32, i32, P, i64, i32, P]
+        lib.wo_grad2d.argtypes = [P, i64, i32, i32, f32, i32, P, i32, P, P]
         lib.wo_render3d.argtypes = [P, i64, P, i32, i32, P, i32, P, i64, P, P, P, P]
         lib.wo_grad3d.argtypes = [P, i64, P, i32, i32, P, i32, P, P, P]
         lib.wo_project3d.argtypes = [P, i64, P, i32, i32, P, P]
@@ -64,32 +64,40 @@ def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
+def _kind(dims, cov2d):
+    """Record kind of the C functions: 2 = 2D (RS), 3 = 3D, 4 = 2D with a Cholesky covariance."""
+    return 4 if dims == 2 and cov2d else dims
+
+
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def footprints(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
-    """binary32 footprint rule: (rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth, rect[N,4] = u0,v0,u1,v1, valid[N])."""
+def footprints(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
+    """binary32 footprint rule: (rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth, rect[N,4] = u0,v0,u1,v1, valid[N]).
+    cov2d=1: 2D records carry the Cholesky factor (l1, l2, l3) of Sigma instead of (s_x, s_y, theta)."""
     params = _f32(params)
     n = params.shape[0]
     rec = np.zeros((n, 8), np.float32)
     rect = np.zeros((n, 4), np.int32)
     valid = np.zeros(n, np.int32)
     camv = _f32(cam) if cam is not None else None
-    _load().wo_footprints(dims, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(rec), _ptr(rect), _ptr(valid))
+    _load().wo_footprints(_kind(dims, cov2d), _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(rec), _ptr(rect),
+                          _ptr(valid))
     return rec, rect, valid
 
 
-def tile_lists(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
+def tile_lists(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
     """Sorted (tile, primitive) pairs: by tile, then camera depth (3D), then primitive index."""
     params = _f32(params)
     n = params.shape[0]
     camv = _f32(cam) if cam is not None else None
     lib = _load()
-    total = lib.wo_tile_lists(dims, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, None, None, 0)
+    kind = _kind(dims, cov2d)
+    total = lib.wo_tile_lists(kind, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, None, None, 0)
     tiles = np.zeros(max(total, 1), np.uint32)
     prims = np.zeros(max(total, 1), np.uint32)
-    lib.wo_tile_lists(dims, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(tiles), _ptr(prims), total)
+    lib.wo_tile_lists(kind, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(tiles), _ptr(prims), total)
     return tiles[:total], prims[:total]
 
 
@@ -100,23 +108,25 @@ def _pix(pixels):
     return p, p.shape[0]
 
 
-def render2d(params, H, W, cutoff=3.0, truncated=True, pixels=None):
-    """Summed wavelet field, [H,W,3] (or [npix,3] at the given (u, v) pixels)."""
+def render2d(params, H, W, cutoff=3.0, truncated=True, pixels=None, cov2d=0):
+    """Summed wavelet field, [H,W,3] (or [npix,3] at the given (u, v) pixels).  cov2d as in footprints."""
     params = _f32(params)
     pix, npix = _pix(pixels)
     out = np.zeros((npix if pix is not None else H * W, 3), np.float64)
-    _load().wo_render2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(pix), npix, _ptr(out))
+    _load().wo_render2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(pix), npix, int(cov2d),
+                        _ptr(out))
     return out if pix is not None else out.reshape(H, W, 3)
 
 
-def grad2d(params, H, W, dldimg, cutoff=3.0, truncated=True, with_abs=False):
+def grad2d(params, H, W, dldimg, cutoff=3.0, truncated=True, with_abs=False, cov2d=0):
     """dL/dparams [N,16] for L = sum(dldimg * C).  with_abs=True also returns, per parameter, the
     sum over pixels of |that pixel's contribution| (the scale of a summed gradient's rounding)."""
     params = _f32(params)
     g = _f32(dldimg)
     out = np.zeros((params.shape[0], 16), np.float64)
     gabs = np.zeros((params.shape[0], 16), np.float64) if with_abs else None
-    _load().wo_grad2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(g), _ptr(out), _ptr(gabs))
+    _load().wo_grad2d(_ptr(params), params.shape[0], H, W, cutoff, int(truncated), _ptr(g), int(cov2d), _ptr(out),
+                      _ptr(gabs))
     return (out, gabs) if with_abs else out
 
 
@@ -183,11 +193,12 @@ def deform6d_grad(params6, t, g3):
     return out
 
 
-def cutoff_coverage(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3):
+def cutoff_coverage(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
     """(pairs inside the cutoff, of those outside the covered pixel range, pixels in the ranges,
     cutoff pairs that the tile ellipse test would drop)."""
     params = _f32(params)
     camv = _f32(cam) if cam is not None else None
     counts = np.zeros(4, np.int64)
-    _load().wo_cutoff_coverage(dims, _ptr(params), params.shape[0], _ptr(camv), H, W, cutoff, dilation, _ptr(counts))
+    _load().wo_cutoff_coverage(_kind(dims, cov2d), _ptr(params), params.shape[0], _ptr(camv), H, W, cutoff, dilation,
+                               _ptr(counts))
     return int(counts[0]), int(counts[1]), int(counts[2]), int(counts[3])

@@ -106,6 +106,40 @@ static void footprint2d(const float* p, float cutoff, int W, int H, fp32_footpri
     else { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
 }
 
+/* 2D Cholesky record (GaussianImage's second construction, Sec. 5.1): mu(2) l1 l2 l3 f(2) phi c(3),
+ * Sigma = L L^T with L = [[l1, 0], [l2, l3]], so Sigma = [[l1^2, l1 l2], [l1 l2, l2^2 + l3^2]] and
+ * Sigma^-1 = [[u, -l1 l2], [-l1 l2, l1^2]] / (l1 l3)^2 with u = l2^2 + l3^2.  Its lower Cholesky
+ * factor: l11 = sqrt(u) / |l1 l3|, l21 = -l1 l2 / (|l1 l3| sqrt(u)), l22 = 1 / sqrt(u). */
+static void footprint2d_chol(const float* p, float cutoff, int W, int H, fp32_footprint* k) {
+    float a = p[2], b = p[3], c = p[4];
+    float u = b * b + c * c;
+    float su = sqrtf(u);
+    float aac = fabsf(a * c);
+    float l11 = su / aac;
+    float l21 = -(a * b) / (aac * su);
+    float l22 = 1.0f / su;
+    float vxx = a * a;
+    k->mx = p[0];
+    k->my = p[1];
+    k->l11 = l11; k->l21 = l21; k->l22 = l22;
+    k->ex = (cutoff * sqrtf(vxx)) * EXT_MARGIN;
+    k->ey = (cutoff * su) * EXT_MARGIN;
+    k->depth = 0.0f;
+    k->valid = finite4(k->mx, k->my, l11, l21) && finite4(l22, k->ex, k->ey, 1.0f) && aac > 0.0f && l11 > 0.0f &&
+               l22 > 0.0f;
+    if (k->valid) footprint_pixrect(k, W, H);
+    else { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
+}
+
+/* Record kinds of the functions below: KIND_2D_RS = 2 (mu s theta f phi c), KIND_3D = 3,
+ * KIND_2D_CHOL = 4 (mu l1 l2 l3 f phi c). */
+#define KIND_2D_RS 2
+#define KIND_3D 3
+#define KIND_2D_CHOL 4
+
+static void footprint_of(int kind, const float* params, int64_t i, const float* cam, float cutoff, float dil, int W,
+                         int H, fp32_footprint* k);
+
 /* 3D record: mu(3) s(3) q(4: w,x,y,z) f(3) phi opacity c(3); camera: V[12] fx fy cx cy near */
 static void footprint3d(const float* p, const float* cam, float cutoff, float dil, int W, int H, fp32_footprint* k) {
     const float* V = cam;
@@ -169,6 +203,13 @@ static void footprint3d(const float* p, const float* cam, float cutoff, float di
 }
 
 /* binary32 squared Mahalanobis distance of pixel (u, v) from the footprint centre */
+static void footprint_of(int kind, const float* params, int64_t i, const float* cam, float cutoff, float dil, int W,
+                         int H, fp32_footprint* k) {
+    if (kind == KIND_2D_RS) footprint2d(params + i * 16, cutoff, W, H, k);
+    else if (kind == KIND_2D_CHOL) footprint2d_chol(params + i * 16, cutoff, W, H, k);
+    else footprint3d(params + i * 20, cam, cutoff, dil, W, H, k);
+}
+
 static float q32(const fp32_footprint* k, int u, int v) {
     float dx = ((float)u + 0.5f) - k->mx;
     float dy = ((float)v + 0.5f) - k->my;
@@ -235,13 +276,12 @@ static int64_t touched_tiles(const fp32_footprint* k, float lim, uint32_t* tiles
 static uint32_t f32_bits(float x) { uint32_t b; memcpy(&b, &x, 4); return b; }
 
 /* Exported view of the footprint rule: rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth; rect[N,4] = u0,v0,u1,v1;
- * valid[N].  dims = 2 or 3; cam and dil are ignored in 2D. */
-int wo_footprints(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
+ * valid[N].  kind = KIND_2D_RS, KIND_3D or KIND_2D_CHOL; cam and dil are ignored in 2D. */
+int wo_footprints(int kind, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
                   float* rec, int32_t* rect, int32_t* valid) {
     for (int64_t i = 0; i < N; ++i) {
         fp32_footprint k;
-        if (dims == 2) footprint2d(params + i * 16, cutoff, W, H, &k);
-        else footprint3d(params + i * 20, cam, cutoff, dil, W, H, &k);
+        footprint_of(kind, params, i, cam, cutoff, dil, W, H, &k);
         if (rec) {
             float* r = rec + i * 8;
             r[0] = k.mx; r[1] = k.my; r[2] = k.l11; r[3] = k.l21; r[4] = k.l22; r[5] = k.ex; r[6] = k.ey; r[7] = k.depth;
@@ -268,20 +308,18 @@ static int cmp_entry(const void* a, const void* b) {
     return 0;
 }
 
-static fp32_footprint* all_footprints(int dims, const float* params, int64_t N, const float* cam, int H, int W,
+static fp32_footprint* all_footprints(int kind, const float* params, int64_t N, const float* cam, int H, int W,
                                       float cutoff, float dil) {
     fp32_footprint* k = (fp32_footprint*)malloc(sizeof(fp32_footprint) * (size_t)(N > 0 ? N : 1));
-    for (int64_t i = 0; i < N; ++i) {
-        if (dims == 2) footprint2d(params + i * 16, cutoff, W, H, &k[i]);
-        else footprint3d(params + i * 20, cam, cutoff, dil, W, H, &k[i]);
-    }
+    for (int64_t i = 0; i < N; ++i) footprint_of(kind, params, i, cam, cutoff, dil, W, H, &k[i]);
     return k;
 }
 
 /* Returns the number of entries (also when it exceeds cap; then only cap are written). */
-int64_t wo_tile_lists(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
+int64_t wo_tile_lists(int kind, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
                       uint32_t* tile_out, uint32_t* prim_out, int64_t cap) {
-    fp32_footprint* k = all_footprints(dims, params, N, cam, H, W, cutoff, dil);
+    const int dims = kind == KIND_3D ? 3 : 2;
+    fp32_footprint* k = all_footprints(kind, params, N, cam, H, W, cutoff, dil);
     int tiles_x = (W + TILE - 1) / TILE;
     float lim = touch_limit(cutoff);
     int64_t total = 0;
@@ -353,21 +391,31 @@ typedef struct {
     int unclamped_x, unclamped_y;
 } proj;
 
-static void project2d(const float* p, proj* w) {
-    double sx = p[2], sy = p[3], th = p[4];
-    double c = cos(th), s = sin(th);
-    /* Sigma = R diag(sx^2, sy^2) R^T  (Sec. 3.1, Sigma = R S S^T R^T) */
-    double Sig[4] = {c * c * sx * sx + s * s * sy * sy, c * s * (sx * sx - sy * sy),
-                     c * s * (sx * sx - sy * sy), s * s * sx * sx + c * c * sy * sy};
+/* cov2d = 0: record mu s(2) theta ..., Sigma = R diag(sx^2, sy^2) R^T (Sec. 3.1, Sigma = R S S^T R^T);
+ * cov2d = 1: record mu l1 l2 l3 ..., Sigma = L L^T with L = [[l1, 0], [l2, l3]] (Cholesky, Sec. 5.1). */
+static void project2d(const float* p, int cov2d, proj* w) {
+    double Sig[4];
     memset(w, 0, sizeof(*w));
-    w->valid = sx > 0 && sy > 0 && isfinite(sx) && isfinite(sy);
+    if (cov2d) {
+        double a = p[2], b = p[3], c = p[4];
+        Sig[0] = a * a; Sig[1] = a * b; Sig[2] = a * b; Sig[3] = b * b + c * c;
+        w->valid = a != 0.0 && c != 0.0 && isfinite(a) && isfinite(b) && isfinite(c);
+    } else {
+        double sx = p[2], sy = p[3], th = p[4];
+        double c = cos(th), s = sin(th);
+        Sig[0] = c * c * sx * sx + s * s * sy * sy;
+        Sig[1] = c * s * (sx * sx - sy * sy);
+        Sig[2] = Sig[1];
+        Sig[3] = s * s * sx * sx + c * c * sy * sy;
+        w->valid = sx > 0 && sy > 0 && isfinite(sx) && isfinite(sy);
+    }
     mat2_inv(Sig, w->K);
     w->mu[0] = p[0]; w->mu[1] = p[1];
     w->f[0] = p[5]; w->f[1] = p[6];
     w->phi = p[7];
     w->o = 1.0;
     w->c[0] = p[8]; w->c[1] = p[9]; w->c[2] = p[10];
-    w->s[0] = sx; w->s[1] = sy;
+    w->s[0] = p[2]; w->s[1] = p[3];
 }
 
 static void quat_to_rot(const double q[4], double R[9]) {
@@ -474,10 +522,10 @@ static int pixel_of(const int32_t* pix, int64_t j, int W, int* u, int* v) {
 /* out[npix,3] (or [H*W,3] when pix is NULL).  truncated: include a primitive at a pixel only if the
  * binary32 footprint rule puts the pixel inside its cutoff ellipse; otherwise every primitive counts. */
 int wo_render2d(const float* params, int64_t N, int H, int W, float cutoff, int truncated, const int32_t* pix,
-                int64_t npix, double* out) {
-    fp32_footprint* k = all_footprints(2, params, N, NULL, H, W, cutoff, 0.0f);
+                int64_t npix, int cov2d, double* out) {
+    fp32_footprint* k = all_footprints(cov2d ? KIND_2D_CHOL : KIND_2D_RS, params, N, NULL, H, W, cutoff, 0.0f);
     proj* w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
-    for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, &w[i]);
+    for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, cov2d, &w[i]);
     float k2 = cutoff * cutoff;
     int64_t np = pix ? npix : (int64_t)H * W;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -500,8 +548,37 @@ int wo_render2d(const float* params, int64_t N, int H, int W, float cutoff, int 
     return 0;
 }
 
-/* chain the image-plane gradient of a 2D primitive to its record: mu(2) s(2) theta f(2) phi c(3) */
-static void chain2d(const float* p, const pgrad* g, double* out) {
+/* the gradient with respect to the Cholesky record entries (l1, l2, l3): K = Sigma^-1, so for each
+ * entry dK = -K dSigma K with dSigma/dl1 = [[2 l1, l2], [l2, 0]], dSigma/dl2 = [[0, l1], [l1, 2 l2]],
+ * dSigma/dl3 = [[0, 0], [0, 2 l3]] */
+static void chain2d_chol(const float* p, const pgrad* g, double gl[3]) {
+    double a = p[2], b = p[3], c = p[4];
+    double Sig[4] = {a * a, a * b, a * b, b * b + c * c}, K[4];
+    mat2_inv(Sig, K);
+    double dS[3][4] = {{2 * a, b, b, 0}, {0, a, a, 2 * b}, {0, 0, 0, 2 * c}};
+    for (int j = 0; j < 3; ++j) {
+        double t1[4], dK[4];
+        matmul(K, dS[j], t1, 2, 2, 2);
+        matmul(t1, K, dK, 2, 2, 2);
+        gl[j] = 0.0;
+        for (int m = 0; m < 4; ++m) gl[j] -= g->K[m] * dK[m];
+    }
+}
+
+/* chain the image-plane gradient of a 2D primitive to its record: mu(2) s(2) theta f(2) phi c(3)
+ * (cov2d = 0) or mu(2) l1 l2 l3 f(2) phi c(3) (cov2d = 1) */
+static void chain2d(const float* p, int cov2d, const pgrad* g, double* out) {
+    if (cov2d) {
+        double gl[3];
+        chain2d_chol(p, g, gl);
+        memset(out, 0, sizeof(double) * 16);
+        out[0] = g->mu[0]; out[1] = g->mu[1];
+        out[2] = gl[0]; out[3] = gl[1]; out[4] = gl[2];
+        out[5] = g->f[0]; out[6] = g->f[1];
+        out[7] = g->phi;
+        out[8] = g->c[0]; out[9] = g->c[1]; out[10] = g->c[2];
+        return;
+    }
     double sx = p[2], sy = p[3], th = p[4];
     double c = cos(th), s = sin(th);
     double R[4] = {c, -s, s, c}, Rt[4] = {c, s, -s, c};
@@ -538,10 +615,10 @@ static void chain2d(const float* p, const pgrad* g, double* out) {
  * sum over pixels of the absolute value of that pixel's contribution to the gradient: the scale
  * against which the rounding error of a summed gradient is measured. */
 int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int truncated, const float* dldimg,
-              double* grad, double* gabs) {
-    fp32_footprint* k = all_footprints(2, params, N, NULL, H, W, cutoff, 0.0f);
+              int cov2d, double* grad, double* gabs) {
+    fp32_footprint* k = all_footprints(cov2d ? KIND_2D_CHOL : KIND_2D_RS, params, N, NULL, H, W, cutoff, 0.0f);
     proj* w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
-    for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, &w[i]);
+    for (int64_t i = 0; i < N; ++i) project2d(params + i * 16, cov2d, &w[i]);
     pgrad* acc = (pgrad*)calloc((size_t)(N > 0 ? N : 1), sizeof(pgrad));
     float k2 = cutoff * cutoff;
     /* primitive-major so that each accumulator has one writer */
@@ -571,7 +648,7 @@ int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int tr
                 g.phi += one.phi;
                 if (gabs) {
                     double t[16];
-                    chain2d(params + i * 16, &one, t);
+                    chain2d(params + i * 16, cov2d, &one, t);
                     for (int m = 0; m < 16; ++m) gabs[i * 16 + m] += fabs(t[m]);
                 }
             }
@@ -581,7 +658,7 @@ int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int tr
         /* a degenerate primitive (non-positive scale, or dropped by the cutoff rule) contributes
            nothing to the image, so its gradient is zero */
         if (!w[i].valid || (truncated && !k[i].valid)) memset(grad + i * 16, 0, sizeof(double) * 16);
-        else chain2d(params + i * 16, &acc[i], grad + i * 16);
+        else chain2d(params + i * 16, cov2d, &acc[i], grad + i * 16);
     }
     free(acc);
     free(w);
@@ -964,9 +1041,9 @@ int wo_deform6d_grad(const float* params6, int64_t N, double t, const double* g3
 /* counts[0] = pairs inside the cutoff ellipse, counts[1] = of those, pairs outside the pixel range,
  * counts[2] = pixels inside the pixel ranges, counts[3] = cutoff pairs whose tile (or whose own
  * one-pixel rectangle) the ellipse test rejects */
-int wo_cutoff_coverage(int dims, const float* params, int64_t N, const float* cam, int H, int W, float cutoff,
+int wo_cutoff_coverage(int kind, const float* params, int64_t N, const float* cam, int H, int W, float cutoff,
                        float dil, int64_t* counts) {
-    fp32_footprint* k = all_footprints(dims, params, N, cam, H, W, cutoff, dil);
+    fp32_footprint* k = all_footprints(kind, params, N, cam, H, W, cutoff, dil);
     float k2 = cutoff * cutoff;
     float lim = touch_limit(cutoff);
     int64_t inside = 0, outside = 0, rect_px = 0, untouched = 0;

@@ -336,6 +336,7 @@ wipes_status check_opts(const wipes_opts* o) {
     if (!(o->alpha_min >= 0.f) || !(o->T_min >= 0.f) || !(o->dilation >= 0.f))
         return fail(WIPES_ERR_INVALID, "alpha_min, T_min and dilation must be non-negative");
     if (o->freq_proj_mode != 0) return fail(WIPES_ERR_INVALID, "freq_proj_mode must be 0");
+    if (o->cov2d != 0 && o->cov2d != 1) return fail(WIPES_ERR_INVALID, "cov2d must be 0 (RS) or 1 (Cholesky)");
     return WIPES_OK;
 }
 
@@ -432,7 +433,7 @@ wipes_status wipes_prepare2d(wipes_ctx* ctx, wipes_state* st, const float* param
     WIPES_TRY(prepare_state(st, 2, N, H, W, opts));
     {
         StageTimer t(ctx, WIPES_STAGE_FOOTPRINT, s);
-        launch_footprint2d(params, N, W, H, opts->cutoff_sigma, st->rec.as<float4>(), st->rect.as<PixRect>(),
+        launch_footprint2d(params, N, W, H, opts->cutoff_sigma, opts->cov2d, st->rec.as<float4>(), st->rect.as<PixRect>(),
                            st->counts.as<uint32_t>(), nullptr, s);
     }
     WIPES_TRY(bin_and_sort(st, nullptr, s));
@@ -560,7 +561,7 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
                               st->tiles_y, st->opts.cutoff_sigma, dL_dout, st->partial.as<float>(), s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
-        launch_reduce_chain2d(params, N, st->offsets.as<uint32_t>(), st->counts.as<uint32_t>(),
+        launch_reduce_chain2d(params, N, st->opts.cov2d, st->offsets.as<uint32_t>(), st->counts.as<uint32_t>(),
                               st->partial.as<float>(), dL_dparams, s);
     } else {
         WIPES_TRY(ensure(st->grad_img, sizeof(float) * 12 * (size_t)std::max<int64_t>(N, 1)));

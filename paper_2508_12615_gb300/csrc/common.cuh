@@ -247,7 +247,7 @@ void count_launches(int n);
 // Launchers implemented in the kernel translation units (all enqueue on `stream`).
 
 // footprint.cu
-void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, float4* rec, PixRect* rect,
+void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, int cov2d, float4* rec, PixRect* rect,
                         uint32_t* counts, uint32_t* depth_keys, cudaStream_t stream);
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
                         float dilation, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
@@ -313,7 +313,7 @@ struct BlendJob {
 void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream);
 void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream);
-void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offsets, const uint32_t* counts,
+void launch_reduce_chain2d(const float* params, int64_t N, int cov2d, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream);
 // counters[0] += visited pairs, counters[1] += pairs inside the cutoff ellipse
 void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,

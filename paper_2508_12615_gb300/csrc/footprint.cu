@@ -81,37 +81,56 @@ __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rec
     if (depth_keys) depth_keys[i] = 0xFFFFFFFFu;
 }
 
-// 2D: Sigma = R(theta) diag(sx^2, sy^2) R(theta)^T; Sigma^-1 = R diag(1/sx^2, 1/sy^2) R^T.
-// Cholesky of Sigma^-1: l11 = sqrt(A), l21 = B / l11, l22 = sqrt(det)/l11 = 1 / (sx sy l11).
+// 2D, RS record (cov2d = 0): Sigma = R(theta) diag(sx^2, sy^2) R(theta)^T;
+// Sigma^-1 = R diag(1/sx^2, 1/sy^2) R^T, whose Cholesky factor is l11 = sqrt(A), l21 = B / l11,
+// l22 = sqrt(det)/l11 = 1 / (sx sy l11).
+// 2D, Cholesky record (cov2d = 1, Sec. 5.1): Sigma = L L^T, L = [[l1, 0], [l2, l3]]; with
+// u = l2^2 + l3^2 = Sigma_yy: l11 = sqrt(u) / |l1 l3|, l21 = -l1 l2 / (|l1 l3| sqrt(u)), l22 = 1/sqrt(u).
 __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ params, int64_t N, int W, int H,
-                                                     float cutoff, float lim, float4* __restrict__ rec,
+                                                     float cutoff, int cov2d, float lim, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts) {
     pdl_enter();
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i0 < N;
     const int64_t i = live ? i0 : N - 1;  // lanes past the end repeat the last primitive, write nothing
-    const float4 p0 = params[i * 4 + 0];  // mu_x mu_y s_x s_y
-    const float4 p1 = params[i * 4 + 1];  // theta f_x f_y phi
+    const float4 p0 = params[i * 4 + 0];  // mu_x mu_y s_x s_y   | mu_x mu_y l1 l2
+    const float4 p1 = params[i * 4 + 1];  // theta f_x f_y phi   | l3 f_x f_y phi
     const float4 p2 = params[i * 4 + 2];  // c_r c_g c_b -
-    const float sx = p0.z, sy = p0.w;
-    // cos and sin in binary64, rounded once to binary32
-    const float c = (float)cos((double)p1.x);
-    const float s = (float)sin((double)p1.x);
-    const float sx2 = sx * sx, sy2 = sy * sy;
-    const float ix = 1.0f / sx2, iy = 1.0f / sy2;
-    const float cc = c * c, ss = s * s, cs = c * s;
-    const float A = cc * ix + ss * iy;
-    const float B = cs * (ix - iy);
-    const float l11 = sqrtf(A);
-    const float l21 = B / l11;
-    const float l22 = 1.0f / ((sx * sy) * l11);
-    const float vxx = cc * sx2 + ss * sy2;
-    const float vyy = ss * sx2 + cc * sy2;
+    float l11, l21, l22, ex, ey;
+    bool shape_ok;
+    if (cov2d) {
+        const float a = p0.z, b = p0.w, c = p1.x;
+        const float u = b * b + c * c;
+        const float su = sqrtf(u);
+        const float aac = fabsf(a * c);
+        l11 = su / aac;
+        l21 = -(a * b) / (aac * su);
+        l22 = 1.0f / su;
+        const float vxx = a * a;
+        ex = (cutoff * sqrtf(vxx)) * kExtMargin;
+        ey = (cutoff * su) * kExtMargin;
+        shape_ok = aac > 0.0f;
+    } else {
+        const float sx = p0.z, sy = p0.w;
+        // cos and sin in binary64, rounded once to binary32
+        const float c = (float)cos((double)p1.x);
+        const float s = (float)sin((double)p1.x);
+        const float sx2 = sx * sx, sy2 = sy * sy;
+        const float ix = 1.0f / sx2, iy = 1.0f / sy2;
+        const float cc = c * c, ss = s * s, cs = c * s;
+        const float A = cc * ix + ss * iy;
+        const float B = cs * (ix - iy);
+        l11 = sqrtf(A);
+        l21 = B / l11;
+        l22 = 1.0f / ((sx * sy) * l11);
+        const float vxx = cc * sx2 + ss * sy2;
+        const float vyy = ss * sx2 + cc * sy2;
+        ex = (cutoff * sqrtf(vxx)) * kExtMargin;
+        ey = (cutoff * sqrtf(vyy)) * kExtMargin;
+        shape_ok = sx > 0.0f && sy > 0.0f;
+    }
     const float mx = p0.x, my = p0.y;
-    const float ex = (cutoff * sqrtf(vxx)) * kExtMargin;
-    const float ey = (cutoff * sqrtf(vyy)) * kExtMargin;
-    const bool valid = finite4(mx, my, l11, l21) && finite4(l22, ex, ey, 1.0f) && sx > 0.0f && sy > 0.0f &&
-                       l11 > 0.0f && l22 > 0.0f;
+    const bool valid = finite4(mx, my, l11, l21) && finite4(l22, ex, ey, 1.0f) && shape_ok && l11 > 0.0f && l22 > 0.0f;
     PixRect r;
     r.u0 = 1; r.u1 = 0; r.v0 = 1; r.v1 = 0;
     if (valid && live) r = covered_pixels(mx, my, ex, ey, W, H);
@@ -273,11 +292,12 @@ __global__ void __launch_bounds__(256) k_deform6d_backward(const float* __restri
 
 }  // namespace
 
-void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, float4* rec, PixRect* rect,
+void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, int cov2d, float4* rec, PixRect* rect,
                         uint32_t* counts, uint32_t* /*depth_keys*/, cudaStream_t stream) {
     if (N == 0) return;
     launch_pdl(k_footprint2d, ceil_div(N, 256), 256, 0, stream, reinterpret_cast<const float4*>(params), N, W, H, cutoff,
-                                                         touch_limit(cutoff), rec, rect, counts); count_launches(1);
+               cov2d, touch_limit(cutoff), rec, rect, counts);
+    count_launches(1);
 }
 
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,

@@ -126,10 +126,40 @@ __global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __r
     }
 }
 
+// The RS part of the 2D chain: (g11, g21, g22) on L to (s_x, s_y, theta).
+__device__ __forceinline__ void chain_rs(const float* p, float g11, float g21, float g22, float* out) {
+    const float sx = p[2], sy = p[3];
+    float s, c;
+    sincosf(p[4], &s, &c);
+    const float ix = 1.0f / (sx * sx), iy = 1.0f / (sy * sy);
+    const float A = c * c * ix + s * s * iy;
+    const float B = c * s * (ix - iy);
+    const float l11 = sqrtf(A), l21 = B / l11, l22 = 1.0f / (sx * sy * l11);
+    // partial derivatives of A and B
+    const float dA_th = -2.0f * B, dA_sx = -2.0f * c * c * ix / sx, dA_sy = -2.0f * s * s * iy / sy;
+    const float dB_th = (c * c - s * s) * (ix - iy), dB_sx = -2.0f * c * s * ix / sx, dB_sy = 2.0f * c * s * iy / sy;
+    const float h = 0.5f / l11;
+    const float d11_th = dA_th * h, d11_sx = dA_sx * h, d11_sy = dA_sy * h;
+    const float d21_th = (dB_th - l21 * d11_th) / l11;
+    const float d21_sx = (dB_sx - l21 * d11_sx) / l11;
+    const float d21_sy = (dB_sy - l21 * d11_sy) / l11;
+    const float d22_th = -l22 * d11_th / l11;
+    const float d22_sx = -l22 * (1.0f / sx + d11_sx / l11);
+    const float d22_sy = -l22 * (1.0f / sy + d11_sy / l11);
+    out[2] = g11 * d11_sx + g21 * d21_sx + g22 * d22_sx;
+    out[3] = g11 * d11_sy + g21 * d21_sy + g22 * d22_sy;
+    out[4] = g11 * d11_th + g21 * d21_th + g22 * d22_th;
+}
+
 // One warp per primitive: sum its slots, then chain (mx, my, L, f, phc, c) to the record
 // mu, s, theta, f, phi, c.  L depends on (theta, s_x, s_y) through
-// A = c^2/sx^2 + s^2/sy^2, B = c s (1/sx^2 - 1/sy^2), l11 = sqrt(A), l21 = B/l11, l22 = 1/(sx sy l11).
-__global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict__ params, int64_t N,
+// A = c^2/sx^2 + s^2/sy^2, B = c s (1/sx^2 - 1/sy^2), l11 = sqrt(A), l21 = B/l11, l22 = 1/(sx sy l11);
+// for the Cholesky record (cov2d = 1) on (l1, l2, l3) through, with u = l2^2 + l3^2, s = sqrt(u):
+// l11 = s / |l1 l3|, l21 = -sgn(l1) l2 / (|l3| s), l22 = 1 / s, so that
+//   dl11/dl1 = -l11/l1, dl11/dl2 = l11 l2/u, dl11/dl3 = l11 (l3/u - 1/l3),
+//   dl21/dl2 = -sgn(l1) l3^2 / (|l3| s u), dl21/dl3 = -l21 (1/l3 + l3/u),
+//   dl22/dl2 = -l2 / (s u), dl22/dl3 = -l3 / (s u).
+__global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict__ params, int64_t N, int cov2d,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint32_t* __restrict__ counts,
                                                         const float* __restrict__ partial,
@@ -161,30 +191,21 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
         for (int k = 0; k < WIPES_P2D; ++k) out[k] = 0.f;
         return;
     }
-    const float sx = p[2], sy = p[3];
-    float s, c;
-    sincosf(p[4], &s, &c);
-    const float ix = 1.0f / (sx * sx), iy = 1.0f / (sy * sy);
-    const float A = c * c * ix + s * s * iy;
-    const float B = c * s * (ix - iy);
-    const float l11 = sqrtf(A), l21 = B / l11, l22 = 1.0f / (sx * sy * l11);
-    // partial derivatives of A and B
-    const float dA_th = -2.0f * B, dA_sx = -2.0f * c * c * ix / sx, dA_sy = -2.0f * s * s * iy / sy;
-    const float dB_th = (c * c - s * s) * (ix - iy), dB_sx = -2.0f * c * s * ix / sx, dB_sy = 2.0f * c * s * iy / sy;
-    const float h = 0.5f / l11;
-    const float d11_th = dA_th * h, d11_sx = dA_sx * h, d11_sy = dA_sy * h;
-    const float d21_th = (dB_th - l21 * d11_th) / l11;
-    const float d21_sx = (dB_sx - l21 * d11_sx) / l11;
-    const float d21_sy = (dB_sy - l21 * d11_sy) / l11;
-    const float d22_th = -l22 * d11_th / l11;
-    const float d22_sx = -l22 * (1.0f / sx + d11_sx / l11);
-    const float d22_sy = -l22 * (1.0f / sy + d11_sy / l11);
     const float g11 = acc[2], g21 = acc[3], g22 = acc[4];
+    if (cov2d) {
+        const float a = p[2], b = p[3], c = p[4];
+        const float u = b * b + c * c, sq = sqrtf(u), aac = fabsf(a * c);
+        const float l11 = sq / aac, l21 = -(a * b) / (aac * sq);
+        const float isu = 1.0f / (sq * u);
+        const float sgn_a = a < 0.0f ? -1.0f : 1.0f;
+        out[2] = g11 * (-l11 / a);
+        out[3] = g11 * (l11 * b / u) + g21 * (-sgn_a * c * c * isu / fabsf(c)) + g22 * (-b * isu);
+        out[4] = g11 * (l11 * (c / u - 1.0f / c)) + g21 * (-l21 * (1.0f / c + c / u)) + g22 * (-c * isu);
+    } else {
+        chain_rs(p, g11, g21, g22, out);
+    }
     out[0] = acc[0];
     out[1] = acc[1];
-    out[2] = g11 * d11_sx + g21 * d21_sx + g22 * d22_sx;
-    out[3] = g11 * d11_sy + g21 * d21_sy + g22 * d22_sy;
-    out[4] = g11 * d11_th + g21 * d21_th + g22 * d22_th;
     out[5] = acc[5];
     out[6] = acc[6];
     out[7] = acc[7] * kInvTwoPi;
@@ -194,6 +215,7 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
 #pragma unroll
     for (int k = 11; k < WIPES_P2D; ++k) out[k] = 0.f;
 }
+
 
 // Visited and inside-cutoff (pixel, primitive) pairs over the sorted tile lists; with `last`
 // (3D), only list entries up to each pixel's last contributor count.
@@ -251,10 +273,11 @@ void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, in
     count_launches(1);
 }
 
-void launch_reduce_chain2d(const float* params, int64_t N, const uint32_t* offsets, const uint32_t* counts,
+void launch_reduce_chain2d(const float* params, int64_t N, int cov2d, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
-    launch_pdl(k_reduce_chain2d, ceil_div(N * 32, 256), 256, 0, stream, params, N, offsets, counts, partial, dl_dparams);
+    launch_pdl(k_reduce_chain2d, ceil_div(N * 32, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial,
+               dl_dparams);
     count_launches(1);
 }
 

@@ -62,6 +62,27 @@ def scene2d(n: int, H: int, W: int, seed: int, scale_range=(1.0, 16.0), max_freq
     return p
 
 
+def scene2d_cholesky(n: int, H: int, W: int, seed: int, scale_range=(1.0, 16.0), max_freq=0.5) -> np.ndarray:
+    """2D wavelet primitives in the Cholesky record (mu, l1, l2, l3, f, phi, c): centres, frequency,
+    phase and colours drawn as in scene2d; the diagonal entries l1, l3 log-uniform over the scale
+    range with a random sign, the off-diagonal l2 uniform in [-l, l] with l log-uniform over the
+    same range."""
+    rng = _rng(seed)
+    p = np.zeros((n, P2D), dtype=np.float32)
+    p[:, 0] = rng.uniform(0.0, W, n)
+    p[:, 1] = rng.uniform(0.0, H, n)
+    p[:, 2] = _log_uniform(rng, scale_range[0], scale_range[1], n) * rng.choice([-1.0, 1.0], n)
+    p[:, 3] = rng.uniform(-1.0, 1.0, n) * _log_uniform(rng, scale_range[0], scale_range[1], n)
+    p[:, 4] = _log_uniform(rng, scale_range[0], scale_range[1], n) * rng.choice([-1.0, 1.0], n)
+    fm = rng.uniform(0.0, max_freq, n)
+    fd = rng.uniform(0.0, 2.0 * math.pi, n)
+    p[:, 5] = fm * np.cos(fd)
+    p[:, 6] = fm * np.sin(fd)
+    p[:, 7] = rng.uniform(0.0, 2.0 * math.pi, n)
+    p[:, 8:11] = rng.uniform(0.0, 1.0, (n, 3))
+    return p
+
+
 def target_gabor(H: int, W: int, seed: int, n_patches: int = 50) -> np.ndarray:
     """Target image [H,W,3]: 0.5 plus a sum of isotropic Gabor patches (Gaussian window times a
     signed cosine carrier) with random centre, width, wave vector, phase and colour amplitude."""

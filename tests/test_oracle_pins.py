@@ -168,6 +168,84 @@ def test_grad2d_matches_central_differences():
 
 
 # ---------------------------------------------------------------------------------------------
+# 2D Cholesky covariance (GaussianImage's second construction, Sec. 5.1): Sigma = L L^T
+# ---------------------------------------------------------------------------------------------
+
+def _rs_to_cholesky(p):
+    """The same primitives in the Cholesky record: L = chol(R diag(s^2) R^T), in binary64."""
+    q = p.astype(np.float64).copy()
+    for i in range(len(p)):
+        c, s = math.cos(p[i, 4]), math.sin(p[i, 4])
+        R = np.array([[c, -s], [s, c]])
+        L = np.linalg.cholesky(R @ np.diag(p[i, 2:4].astype(np.float64) ** 2) @ R.T)
+        q[i, 2], q[i, 3], q[i, 4] = L[0, 0], L[1, 0], L[1, 1]
+    return q
+
+
+def test_cholesky_and_rs_constructions_render_the_same_field():
+    """A Cholesky record built from an RS record by numpy's Cholesky factorisation describes the
+    same Sigma, so the untruncated fields agree up to the rounding of the records to binary32."""
+    H, W = 40, 48
+    p = synth.scene2d(40, H, W, 21, (1.0, 8.0))
+    q = _rs_to_cholesky(p)
+    a = oracle.render2d(p, H, W, truncated=False)
+    b = oracle.render2d(q, H, W, truncated=False, cov2d=1)
+    assert np.abs(a - b).max() <= 2e-5 * max(1.0, np.abs(a).max())
+    ga = oracle.grad2d(p, H, W, synth.upstream_grad(H, W, 22), truncated=False)
+    gb = oracle.grad2d(q, H, W, synth.upstream_grad(H, W, 22), truncated=False, cov2d=1)
+    for cols in ([0, 1], [5, 6, 7], [8, 9, 10]):  # parameters the two records share
+        np.testing.assert_allclose(gb[:, cols], ga[:, cols], rtol=1e-4, atol=1e-4 * np.abs(ga[:, cols]).max())
+
+
+def test_cholesky_sign_flips_leave_sigma_and_the_image_unchanged():
+    """(l1, l2, l3) -> (-l1, -l2, -l3) and l3 -> -l3 leave L L^T unchanged: identical images, also
+    truncated (the binary32 footprint rule sees the same squares and products), and the gradient
+    with respect to the flipped entries changes sign."""
+    H, W = 36, 44
+    p = synth.scene2d_cholesky(60, H, W, 23, (1.0, 8.0))
+    g = synth.upstream_grad(H, W, 24)
+    base = oracle.render2d(p, H, W, cov2d=1)
+    gb = oracle.grad2d(p, H, W, g, cov2d=1)
+    for flip in ([2, 3, 4], [4]):
+        q = p.copy()
+        q[:, flip] = -q[:, flip]
+        assert np.array_equal(oracle.render2d(q, H, W, cov2d=1), base)
+        assert np.array_equal(oracle.tile_lists(2, q, H, W, cov2d=1)[0], oracle.tile_lists(2, p, H, W, cov2d=1)[0])
+        gq = oracle.grad2d(q, H, W, g, cov2d=1)
+        np.testing.assert_allclose(gq[:, flip], -gb[:, flip], rtol=1e-9, atol=1e-12)
+
+
+def test_cholesky_grad_matches_central_differences():
+    """The Cholesky chain rule (dK = -K dSigma K) equals central differences of the binary64
+    forward, every parameter of every primitive, no truncation."""
+    H, W = 24, 28
+    p = synth.scene2d_cholesky(5, H, W, 25, (1.5, 5.0))
+    g = synth.upstream_grad(H, W, 26)
+    an = oracle.grad2d(p, H, W, g, truncated=False, cov2d=1)
+    cols = list(range(11))
+    fd = _central_fd(lambda pp: float((oracle.render2d(pp, H, W, truncated=False, cov2d=1) * g).sum()), p,
+                     range(len(p)), cols)
+    err = np.abs(an[:, cols] - fd)
+    tol = 2e-6 * np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max(axis=0, keepdims=True))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-300)).max()
+
+
+def test_cholesky_footprint_covers_the_cutoff_ellipse():
+    """The Cholesky footprint rule's extents and tile test lose no pixel of the binary32 cutoff
+    test, down to elongated primitives, and its L reproduces the binary64 Sigma^-1."""
+    H, W = 112, 128
+    p = synth.scene2d_cholesky(1200, H, W, 27, (0.5, 32.0))
+    inside, outside, rect, dropped = oracle.cutoff_coverage(2, p, H, W, cov2d=1)
+    assert inside > 0 and outside == 0 and dropped == 0 and rect >= inside
+    rec, _, valid = oracle.footprints(2, p[:200], H, W, cov2d=1)
+    for i in np.nonzero(valid)[0]:
+        L0 = np.array([[p[i, 2], 0.0], [p[i, 3], p[i, 4]]], np.float64)
+        K = np.linalg.inv(L0 @ L0.T)
+        L = np.array([[rec[i, 2], 0.0], [rec[i, 3], rec[i, 4]]], np.float64)
+        np.testing.assert_allclose(L @ L.T, K, rtol=2e-5, atol=2e-5 * np.abs(K).max())
+
+
+# ---------------------------------------------------------------------------------------------
 # 3D projection (Sec. 3.1 EWA, Sec. 4.1 frequency), blending (Eq. 3 with W')
 # ---------------------------------------------------------------------------------------------
 
