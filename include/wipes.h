@@ -76,7 +76,9 @@ typedef struct {
     float T_min;            /* 3D: blending stops before a primitive that takes T below this */
     float dilation;         /* 3D: added to the diagonal of Sigma' (px^2); ignored in 2D */
     float bg[3];            /* 3D: background colour, weighted by the final transmittance */
-    int32_t freq_proj_mode; /* 3D: 0 = phase gradient on the fronto-parallel plane (only mode) */
+    int32_t freq_proj_mode; /* 3D: 0 = phase gradient on the fronto-parallel plane through the centre,
+                               f' = (fc_x t_z / f_x, fc_y t_z / f_y) with fc = W f; 1 = the literal
+                               f' = J W f (the covariance's ray-space map, Sec. 4.1) */
     int32_t cov2d;          /* 2D: 0 = RS record (s_x, s_y, theta), 1 = Cholesky record (l1, l2, l3) */
 } wipes_opts;
 

@@ -23,8 +23,15 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# opts vector layout shared by the 3D calls: cutoff, alpha_min, alpha_max, T_min, dilation, bg(3)
-DEFAULT_OPTS_3D = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0], dtype=np.float32)
+# opts vector layout shared by the 3D calls: cutoff, alpha_min, alpha_max, T_min, dilation, bg(3),
+# frequency projection mode (0: phase gradient on the fronto-parallel plane, 1: literal J W f)
+DEFAULT_OPTS_3D = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 0.0], dtype=np.float32)
+
+
+def _opts3(opts):
+    """The 9-entry options vector (an 8-entry vector gets frequency projection mode 0)."""
+    o = _f32(DEFAULT_OPTS_3D if opts is None else opts).ravel()
+    return o if o.size == 9 else np.concatenate([o, np.zeros(9 - o.size, np.float32)])
 
 
 def build(force: bool = False) -> str:
@@ -139,7 +146,7 @@ def render3d(params, cam, H, W, opts=None, truncated=True, pixels=None):
     skip, T_min stop) can change the image, bit 2 (alpha_max clamp) only the gradient."""
     params = _f32(params)
     camv = _f32(cam)
-    o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
+    o = _opts3(opts)
     pix, npix = _pix(pixels)
     m = npix if pix is not None else H * W
     out = np.zeros((m, 3), np.float64)
@@ -157,7 +164,7 @@ def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True, with_abs=False)
     """dL/dparams [N,20] for L = sum(dldimg * C) (with_abs as in grad2d)."""
     params = _f32(params)
     camv = _f32(cam)
-    o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
+    o = _opts3(opts)
     g = _f32(dldimg)
     out = np.zeros((params.shape[0], 20), np.float64)
     gabs = np.zeros((params.shape[0], 20), np.float64) if with_abs else None
@@ -170,7 +177,7 @@ def project3d(params, cam, H, W, opts=None):
     """[N,16]: valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), 0, 0."""
     params = _f32(params)
     camv = _f32(cam)
-    o = _f32(DEFAULT_OPTS_3D if opts is None else opts)
+    o = _opts3(opts)
     out = np.zeros((params.shape[0], 16), np.float64)
     _load().wo_project3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), _ptr(out))
     return out

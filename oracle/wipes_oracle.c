@@ -389,6 +389,7 @@ typedef struct {
     /* 3D chain-rule intermediates */
     double t[3], R[9], M[9], V[9], Sc[9], J[6], fc[3], qn[4], qnorm, s[3];
     int unclamped_x, unclamped_y;
+    int fmode;       /* frequency projection mode of project3d */
 } proj;
 
 /* cov2d = 0: record mu s(2) theta ..., Sigma = R diag(sx^2, sy^2) R^T (Sec. 3.1, Sigma = R S S^T R^T);
@@ -425,7 +426,10 @@ static void quat_to_rot(const double q[4], double R[9]) {
     R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-static void project3d(const float* p, const float* cam, int H, int W, double dil, int valid32, proj* w) {
+/* fmode 0: f' = (fc_x tz / fx, fc_y tz / fy), the phase gradient on the fronto-parallel plane through
+ * the centre (reading of Sec. 4.1); fmode 1: f' = J fc, the frequency put through the same W and J
+ * as the covariance, read literally (Sec. 4.1). */
+static void project3d(const float* p, const float* cam, int H, int W, double dil, int fmode, int valid32, proj* w) {
     memset(w, 0, sizeof(*w));
     w->valid = valid32;
     double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
@@ -469,8 +473,14 @@ static void project3d(const float* p, const float* cam, int H, int W, double dil
     w->mu[0] = fx * tx / tz + cx;
     w->mu[1] = fy * ty / tz + cy;
     for (int i = 0; i < 3; ++i) w->fc[i] = w->V[i * 3 + 0] * p[10] + w->V[i * 3 + 1] * p[11] + w->V[i * 3 + 2] * p[12];
-    w->f[0] = w->fc[0] * tz / fx;
-    w->f[1] = w->fc[1] * tz / fy;
+    if (fmode) {
+        w->f[0] = J[0] * w->fc[0] + J[1] * w->fc[1] + J[2] * w->fc[2];
+        w->f[1] = J[3] * w->fc[0] + J[4] * w->fc[1] + J[5] * w->fc[2];
+    } else {
+        w->f[0] = w->fc[0] * tz / fx;
+        w->f[1] = w->fc[1] * tz / fy;
+    }
+    w->fmode = fmode;
     w->phi = p[13];
     w->o = p[14];
     w->c[0] = p[15]; w->c[1] = p[16]; w->c[2] = p[17];
@@ -670,11 +680,12 @@ int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int tr
 /* 3D: projection and front-to-back alpha blending                                             */
 /* ------------------------------------------------------------------------------------------ */
 
-/* opts[8] = cutoff, alpha_min, alpha_max, T_min, dilation, bg_r, bg_g, bg_b */
-typedef struct { float cutoff, amin, amax, Tmin, dil; double bg[3]; } blend_opts;
+/* opts[9] = cutoff, alpha_min, alpha_max, T_min, dilation, bg_r, bg_g, bg_b, frequency projection
+ * mode (0: phase gradient on the fronto-parallel plane; 1: the literal f' = (J W f)_xy) */
+typedef struct { float cutoff, amin, amax, Tmin, dil; double bg[3]; int fmode; } blend_opts;
 
 static blend_opts read_opts(const float* o) {
-    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}};
+    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}, o[8] != 0.0f};
     return b;
 }
 
@@ -700,7 +711,7 @@ static void scene3_build(const float* params, int64_t N, const float* cam, int H
     order_entry* e = (order_entry*)malloc(sizeof(order_entry) * (size_t)(N > 0 ? N : 1));
     int64_t n = 0;
     for (int64_t i = 0; i < N; ++i) {
-        project3d(params + i * 20, cam, H, W, o->dil, s->k[i].valid, &s->w[i]);
+        project3d(params + i * 20, cam, H, W, o->dil, o->fmode, s->k[i].valid, &s->w[i]);
         if (s->k[i].valid) { e[n].depth = f32_bits(s->k[i].depth); e[n].prim = (uint32_t)i; ++n; }
     }
     qsort(e, (size_t)n, sizeof(order_entry), cmp_order);
@@ -849,8 +860,20 @@ static void chain3d(const proj* w, const float* cam, const pgrad* g, double* out
     gt[2] += -g->mu[0] * fx * tx / (tz * tz);
     gt[1] += g->mu[1] * fy / tz;
     gt[2] += -g->mu[1] * fy * ty / (tz * tz);
-    double gfc[3] = {g->f[0] * tz / fx, g->f[1] * tz / fy, 0.0};
-    gt[2] += g->f[0] * w->fc[0] / fx + g->f[1] * w->fc[1] / fy;
+    double gfc[3];
+    if (w->fmode) {
+        /* f' = J fc: dL/dfc = J^T dL/df', and dL/dJ gains dL/df' fc^T */
+        for (int k = 0; k < 3; ++k) {
+            gfc[k] = w->J[k] * g->f[0] + w->J[3 + k] * g->f[1];
+            gJ[k] += g->f[0] * w->fc[k];
+            gJ[3 + k] += g->f[1] * w->fc[k];
+        }
+    } else {
+        gfc[0] = g->f[0] * tz / fx;
+        gfc[1] = g->f[1] * tz / fy;
+        gfc[2] = 0.0;
+        gt[2] += g->f[0] * w->fc[0] / fx + g->f[1] * w->fc[1] / fy;
+    }
     /* J = [[fx/tz, 0, -fx txz/tz], [0, fy/tz, -fy tyz/tz]], txz = clamp(tx/tz) */
     double txz = -w->J[2] * tz / fx, tyz = -w->J[5] * tz / fy;
     gt[2] += gJ[0] * (-fx / (tz * tz));
@@ -978,7 +1001,7 @@ int wo_project3d(const float* params, int64_t N, const float* cam, int H, int W,
         fp32_footprint k;
         footprint3d(params + i * 20, cam, o.cutoff, o.dil, W, H, &k);
         proj w;
-        project3d(params + i * 20, cam, H, W, o.dil, k.valid, &w);
+        project3d(params + i * 20, cam, H, W, o.dil, o.fmode, k.valid, &w);
         double S2[4];
         mat2_inv(w.K, S2);
         double* r = out + i * 16;

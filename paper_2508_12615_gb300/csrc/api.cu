@@ -335,7 +335,8 @@ wipes_status check_opts(const wipes_opts* o) {
         return fail(WIPES_ERR_INVALID, "alpha_max must lie in (0, 1)");
     if (!(o->alpha_min >= 0.f) || !(o->T_min >= 0.f) || !(o->dilation >= 0.f))
         return fail(WIPES_ERR_INVALID, "alpha_min, T_min and dilation must be non-negative");
-    if (o->freq_proj_mode != 0) return fail(WIPES_ERR_INVALID, "freq_proj_mode must be 0");
+    if (o->freq_proj_mode != 0 && o->freq_proj_mode != 1)
+        return fail(WIPES_ERR_INVALID, "freq_proj_mode must be 0 (fronto-parallel phase gradient) or 1 (literal J W f)");
     if (o->cov2d != 0 && o->cov2d != 1) return fail(WIPES_ERR_INVALID, "cov2d must be 0 (RS) or 1 (Cholesky)");
     return WIPES_OK;
 }
@@ -480,7 +481,8 @@ wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* param
     WIPES_TRY(ensure(st->last, sizeof(uint32_t) * npix));
     {
         StageTimer t(ctx, WIPES_STAGE_FOOTPRINT, s);
-        launch_footprint3d(params, N, *cam, W, H, opts->cutoff_sigma, opts->dilation, st->rec.as<float4>(),
+        launch_footprint3d(params, N, *cam, W, H, opts->cutoff_sigma, opts->dilation, opts->freq_proj_mode,
+                           st->rec.as<float4>(),
                            st->rect.as<PixRect>(), st->counts.as<uint32_t>(), st->dkeys[0].as<uint32_t>(), s);
     }
     // front-to-back order: stable sort of the primitives by the bits of their camera depth
@@ -573,7 +575,7 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
                               dL_dout, st->grad_img.as<float>(), st->order.as<uint32_t>(), s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
-        launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->rec.as<float4>(),
+        launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->opts.freq_proj_mode, st->rec.as<float4>(),
                        st->grad_img.as<float>(), dL_dparams, s);
     }
     WIPES_CUDA(cudaGetLastError());

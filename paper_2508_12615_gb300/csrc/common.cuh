@@ -250,7 +250,7 @@ void count_launches(int n);
 void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, int cov2d, float4* rec, PixRect* rect,
                         uint32_t* counts, uint32_t* depth_keys, cudaStream_t stream);
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
-                        float dilation, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
+                        float dilation, int fmode, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
                         cudaStream_t stream);
 void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream);
 void launch_deform6d_backward(const float* params6, int64_t N, float t, const float* g3, float* g6, int accumulate,
@@ -324,7 +324,7 @@ void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cud
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
                        const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream);
-void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
+void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation, int fmode,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 
 // batch.cu: one persistent launch over the tiles of up to kMaxBatchJobs frames; blocks take

@@ -154,10 +154,12 @@ struct Cam {
 // local affine Jacobian J of the perspective map (Sec. 3.1).  det Sigma' is evaluated as
 // |P0 x P1|^2 + dil (|P0|^2 + |P1|^2) + dil^2, a sum of non-negative terms.
 // Cholesky of Sigma'^-1: l22 = 1/sqrt(S11), l11 = sqrt(S11/D), l21 = -S01/sqrt(S11 D).
-// Frequency: fc = V f, f' = (fc_x tz / fx, fc_y tz / fy) (phase gradient on the fronto-parallel
-// plane through the centre; the viewing-axis component is dropped, Sec. 4.1).
+// Frequency: fc = V f; fmode 0: f' = (fc_x tz / fx, fc_y tz / fy) (phase gradient on the
+// fronto-parallel plane through the centre; the viewing-axis component is dropped, Sec. 4.1);
+// fmode 1: f' = J fc (the same W and J as the covariance, read literally, Sec. 4.1).
 __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ params, int64_t N, Cam cam, int W,
-                                                     int H, float cutoff, float lim, float dil, float4* __restrict__ rec,
+                                                     int H, float cutoff, float lim, float dil, int fmode,
+                                                     float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts,
                                                      uint32_t* __restrict__ depth_keys) {
     pdl_enter();
@@ -233,8 +235,17 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     // projected frequency (not part of any integer decision)
     const float fcx = (V[0] * p[10] + V[1] * p[11]) + V[2] * p[12];
     const float fcy = (V[4] * p[10] + V[5] * p[11]) + V[6] * p[12];
+    float fpx, fpy;
+    if (fmode) {
+        const float fcz = (V[8] * p[10] + V[9] * p[11]) + V[10] * p[12];
+        fpx = j00 * fcx + j02 * fcz;
+        fpy = j11 * fcy + j12 * fcz;
+    } else {
+        fpx = fcx * tz / cam.fx;
+        fpy = fcy * tz / cam.fy;
+    }
     rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
-    rec[i * kRecF4 + 1] = make_float4(l22, fcx * tz / cam.fx, fcy * tz / cam.fy, p[13] * kInvTwoPi);
+    rec[i * kRecF4 + 1] = make_float4(l22, fpx, fpy, p[13] * kInvTwoPi);
     rec[i * kRecF4 + 2] = make_float4(p[15], p[16], p[17], p[14]);
     rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, 0.0f);
     rect[i] = rr;
@@ -301,14 +312,15 @@ void launch_footprint2d(const float* params, int64_t N, int W, int H, float cuto
 }
 
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
-                        float dilation, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
+                        float dilation, int fmode, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
                         cudaStream_t stream) {
     if (N == 0) return;
     Cam c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
     launch_pdl(k_footprint3d, ceil_div(N, 256), 256, 0, stream, params, N, c, W, H, cutoff, touch_limit(cutoff), dilation,
-                                                         rec, rect, counts, depth_keys); count_launches(1);
+               fmode, rec, rect, counts, depth_keys);
+    count_launches(1);
 }
 
 void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream) {

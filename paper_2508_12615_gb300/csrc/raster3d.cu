@@ -199,7 +199,7 @@ __device__ __forceinline__ void quat_rot_grad(const float q[4], const float gR[9
 
 // Chain the image-plane gradient (mx, my, L, f', phc, c, o) to the record mu, s, q, f, phi, o, c.
 __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ params, int64_t N, Cam3 cam, int W, int H,
-                                                 float dil, const float4* __restrict__ rec,
+                                                 float dil, int fmode, const float4* __restrict__ rec,
                                                  const float* __restrict__ grad_img, float* __restrict__ dl_dparams) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,13 +298,22 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
     float gqn[4];
     quat_rot_grad(qn, gR, gqn);
     const float dot = gqn[0] * qn[0] + gqn[1] * qn[1] + gqn[2] * qn[2] + gqn[3] * qn[3];
-    // camera-frame centre
+    // camera-frame frequency; with f' = J fc (fmode 1) dL/dJ gains dL/df' fc^T
     const float fcx = V[0] * p[10] + V[1] * p[11] + V[2] * p[12];
     const float fcy = V[4] * p[10] + V[5] * p[11] + V[6] * p[12];
+    const float fcz = V[8] * p[10] + V[9] * p[11] + V[10] * p[12];
+    if (fmode) {
+        gj00 += g_fx * fcx;
+        gj02 += g_fx * fcz;
+        gj11 += g_fy * fcy;
+        gj12 += g_fy * fcz;
+    }
+    // camera-frame centre
     const float iz = 1.f / tz, iz2 = iz * iz;
     float gtx = g_mx * cam.fx * iz;
     float gty = g_my * cam.fy * iz;
-    float gtz = -g_mx * cam.fx * tx * iz2 - g_my * cam.fy * ty * iz2 + g_fx * fcx / cam.fx + g_fy * fcy / cam.fy;
+    float gtz = -g_mx * cam.fx * tx * iz2 - g_my * cam.fy * ty * iz2;
+    if (!fmode) gtz += g_fx * fcx / cam.fx + g_fy * fcy / cam.fy;
     gtz += -gj00 * cam.fx * iz2 - gj11 * cam.fy * iz2 + gj02 * cam.fx * txz * iz2 + gj12 * cam.fy * tyz * iz2;
     if (free_x) {
         gtx += -gj02 * cam.fx * iz2;
@@ -314,12 +323,14 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
         gty += -gj12 * cam.fy * iz2;
         gtz += gj12 * cam.fy * ty * iz2 * iz;
     }
-    const float gfc0 = g_fx * tz / cam.fx, gfc1 = g_fy * tz / cam.fy;
+    const float gfc0 = fmode ? g_fx * j00 : g_fx * tz / cam.fx;
+    const float gfc1 = fmode ? g_fy * j11 : g_fy * tz / cam.fy;
+    const float gfc2 = fmode ? g_fx * j02 + g_fy * j12 : 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         out[a] = V[0 * 4 + a] * gtx + V[1 * 4 + a] * gty + V[2 * 4 + a] * gtz;
         out[3 + a] = gs[a];
-        out[10 + a] = V[0 * 4 + a] * gfc0 + V[1 * 4 + a] * gfc1;
+        out[10 + a] = V[0 * 4 + a] * gfc0 + V[1 * 4 + a] * gfc1 + V[2 * 4 + a] * gfc2;
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) out[6 + m] = (gqn[m] - qn[m] * dot) * qinv;
@@ -347,13 +358,14 @@ void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& 
     count_launches(1);
 }
 
-void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation,
+void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation, int fmode,
                     const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
     Cam3 c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
-    launch_pdl(k_chain3d, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, rec, grad_img, dl_dparams); count_launches(1);
+    launch_pdl(k_chain3d, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, fmode, rec, grad_img,
+               dl_dparams); count_launches(1);
 }
 
 }  // namespace wipes

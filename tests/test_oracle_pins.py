@@ -424,6 +424,59 @@ def test_grad3d_matches_central_differences():
 
 
 # ---------------------------------------------------------------------------------------------
+# literal frequency projection (opt-in reading of Sec. 4.1): f' = J W f
+# ---------------------------------------------------------------------------------------------
+
+OPTS_LITERAL = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 1.0], np.float32)
+
+
+def test_literal_frequency_projection_closed_forms():
+    """Putting f through the covariance's map J (Sec. 4.1 read literally): on the optical axis a
+    frequency facing the camera becomes (fx f_x / tz, fy f_y / tz), where the default reading
+    gives (f_x tz / fx, f_y tz / fy); off axis a frequency along the view axis becomes
+    f_z (-fx tx / tz^2, -fy ty / tz^2), the third column of J, where the default drops it."""
+    H, W = 200, 240
+    fx, fy = 300.0, 280.0
+    cam = cam_identity(H, W, fx=fx, fy=fy)
+    p = rec3d((0, 0, 5.0), (0.1, 0.1, 0.1), (1, 0, 0, 0), (0.25, -0.5, 0.0), 0.0, 0.5, (1, 1, 1))
+    np.testing.assert_allclose(oracle.project3d(p, cam, H, W, OPTS_LITERAL)[0, 7:9], [fx * 0.25 / 5, -fy * 0.5 / 5],
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle.project3d(p, cam, H, W)[0, 7:9], [0.25 * 5 / fx, -0.5 * 5 / fy], rtol=1e-12)
+    tx, ty, tz, fz = 0.7, -0.4, 4.0, 0.3
+    p = rec3d((tx, ty, tz), (0.05,) * 3, (1, 0, 0, 0), (0.0, 0.0, fz), 0.0, 0.5, (1, 1, 1))
+    tx, ty, tz, fz = (float(np.float32(v)) for v in (tx, ty, tz, fz))
+    np.testing.assert_allclose(oracle.project3d(p, cam, H, W, OPTS_LITERAL)[0, 7:9],
+                               [-fx * tx / tz ** 2 * fz, -fy * ty / tz ** 2 * fz], rtol=1e-12)
+    np.testing.assert_allclose(oracle.project3d(p, cam, H, W)[0, 7:9], [0.0, 0.0], atol=1e-15)
+
+
+def test_literal_frequency_grad_matches_central_differences():
+    """The gradient with f' = J W f (through J's dependence on the centre, and W^T J^T to f)
+    against central differences of the binary64 forward (no thresholds)."""
+    H, W = 28, 32
+    p = synth.scene3d(6, 43, scale_range=(0.03, 0.08), max_freq=0.05, extent=0.3)
+    p[:, 14] = np.linspace(0.3, 0.8, 6)
+    cam = synth.camera(synth.look_at((0.4, -2.2, 0.9)), H, W, 50.0)
+    g = synth.upstream_grad(H, W, 44)
+    opts = OPTS_EXACT.copy()
+    opts = np.concatenate([opts, [1.0]]).astype(np.float32)
+    an = oracle.grad3d(p, cam, H, W, g, opts, truncated=False)
+    cols = list(range(18))
+    floor = [0.3] * 3 + [0.03] * 3 + [0.5] * 4 + [0.05] * 3 + [1.0] + [0.3] + [0.3] * 3
+
+    def L(pp):
+        return float((oracle.render3d(pp, cam, H, W, opts, truncated=False)[0] * g).sum())
+
+    fd = _central_fd(L, p, range(len(p)), cols, floor=floor)
+    err = np.abs(an[:, cols] - fd)
+    tol = 1e-5 * np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max(axis=0, keepdims=True))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-300)).max()
+    # the mode matters: the default reading gives a different frequency gradient here
+    an0 = oracle.grad3d(p, cam, H, W, g, OPTS_EXACT, truncated=False)
+    assert np.abs(an0[:, 10:13] - an[:, 10:13]).max() > 1e-3 * np.abs(an[:, 10:13]).max()
+
+
+# ---------------------------------------------------------------------------------------------
 # binary32 footprint rule and tile lists (the 3DGS-style pipeline the paper follows, Sec. 4.1)
 # ---------------------------------------------------------------------------------------------
 

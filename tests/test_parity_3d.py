@@ -16,9 +16,12 @@ STRICT = np.array([3.0, 0.0, 0.99, 0.0, 0.3, 0.1, 0.2, 0.3], np.float32)  # no a
 AMB_SHARE = 1e-2
 
 
+LITERAL = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 1.0], np.float32)  # f' = J W f
+
+
 def _opts(w, o):
     return w.make_opts(3, cutoff_sigma=float(o[0]), alpha_min=float(o[1]), alpha_max=float(o[2]), T_min=float(o[3]),
-                       dilation=float(o[4]), bg=o[5:8])
+                       dilation=float(o[4]), bg=o[5:8], freq_proj_mode=int(o[8]) if len(o) > 8 else 0)
 
 
 def _gpu(w, torch, p, cam, H, W, o):
@@ -92,6 +95,34 @@ def test_backward_matches_oracle(N, H, W, seed, kw, mode):
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
     ref, gabs = oracle.grad3d(p, cam, H, W, g, o, with_abs=True)
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
+    assert ok, (worst, idx)
+
+
+@pytest.mark.parametrize("N,H,W,seed", [(600, 72, 88, 35), (1500, 100, 100, 36)])
+def test_literal_frequency_projection_matches_oracle(N, H, W, seed):
+    """freq_proj_mode 1 (f' = J W f): forward and gradients against the oracle.  The literal map
+    multiplies f by about fx / tz, so the scene's frequencies are scaled down to keep f' near
+    a cycle per pixel."""
+    torch = torch_cuda()
+    w = lib_ready()
+    p = synth.scene3d(N, seed, max_freq=0.02)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    params, st, img = _gpu(w, torch, p, cam, H, W, LITERAL)
+    C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, LITERAL)
+    amb_img = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
+    assert amb_img.mean() < AMB_SHARE
+    err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
+    err[amb_img] = 0
+    assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    # the mode changes the image (the frequencies are not negligible)
+    C0 = oracle.render3d(p, cam, H, W, DEFAULT)[0]
+    assert np.abs(C0 - C).max() > 10 * FWD_ATOL
+    g = synth.upstream_grad(H, W, seed + 5)
+    g[amb_bits != 0] = 0.0
+    grad = w.backward(st, params, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, gabs = oracle.grad3d(p, cam, H, W, g, LITERAL, with_abs=True)
     ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
     assert ok, (worst, idx)
 
