@@ -48,10 +48,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["2d", "2dchol", "5d", "6d"], default="2d",
+    ap.add_argument("--workload", choices=["2d", "2dchol", "5d", "5dsh", "6d"], default="2d",
                     help="2d: the 768x512 / 70k image-fitting workload (default, the headline); 2dchol: the "
-                         "same with the Cholesky covariance record; 5d: 800x800 / 300k static scene; 6d: "
-                         "1352x1014 / 200k dynamic scene, 4 samples per step")
+                         "same with the Cholesky covariance record; 5d: 800x800 / 300k static scene; 5dsh: the "
+                         "same with degree-3 spherical-harmonic colour; 6d: 1352x1014 / 200k dynamic scene, 4 "
+                         "samples per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=10.0, help="length of the serving request trace")
@@ -245,14 +246,18 @@ class Workload:
             self.name, self.H, self.W, self.seed = "2d_cholesky_768x512_n70000", c.H, c.W, c.seed
             self.samples = [None]
             self.opts = w.make_opts(2, cov2d=1)
-        elif kind == "5d":
+        elif kind in ("5d", "5dsh"):
             c = synth.CFG2_5D
             p, cams = synth.cfg2_inputs()
+            if kind == "5dsh":
+                p = synth.scene3d_sh(c.n, c.seed, degree=3)
             target = synth.target_noise_edges(c.H, c.W, c.seed + 200)
             self.name, self.H, self.W, self.seed = "5d_static_800x800_n300000", c.H, c.W, c.seed
+            if kind == "5dsh":
+                self.name = "5d_static_sh3_800x800_n300000"
             self.cams = cams
             self.samples = [(k, None) for k in range(len(cams))]
-            self.opts = w.make_opts(3)
+            self.opts = w.make_opts(3, sh_degree=3 if kind == "5dsh" else 0)
         else:
             c = synth.CFG3_6D
             p, cams, times = synth.cfg3_inputs()
@@ -292,7 +297,7 @@ class Workload:
             return
         cam_i, t = self._sample()
         cam = self.cams[cam_i]
-        if self.kind == "5d":
+        if self.kind in ("5d", "5dsh"):
             w.forward3d(params, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
             if fwd_only:
                 return

@@ -30,6 +30,12 @@
  *              Sigma = L L^T with L = [[l1, 0], [l2, l3]], l1 l3 != 0 (Cholesky form, Sec. 5.1)
  *   3D [N,20]: mu(3), s(3), q(w,x,y,z), f(3), phi, opacity, c(3), (2 unused)
  *              Sigma = R(q/|q|) S S^T R^T (Sec. 3.1); q need not be normalised
+ *   3D with spherical-harmonic colour (wipes_opts.sh_degree = d in 1..3) [N,68]: the 3D record, whose
+ *              c(3) are the degree-0 coefficients, then the coefficients of basis functions
+ *              k = 1..15 (degree l = 1..3, order m = -l..l), three channels each: [20 + 3 (k-1) + ch];
+ *              coefficients above degree d are ignored (and get zero gradient).  Colour per channel:
+ *              max(0, 1/2 + sum_k Y_k(dir) sh_k) with the real spherical harmonics Y_k (Condon-Shortley
+ *              phase) at the unit vector dir from the camera centre to mu (the colour of 3DGS, Sec. 3.1)
  *   6D [N,32]: the 3D record followed by v(3), df(3), dphi, dlog_s(3), (2 unused)
  */
 #ifndef WIPES_H
@@ -46,6 +52,7 @@ extern "C" {
 #define WIPES_P2D 16       /* floats per 2D record */
 #define WIPES_P3D 20       /* floats per 3D record */
 #define WIPES_P6D 32       /* floats per 6D record */
+#define WIPES_P3D_SH 68    /* floats per 3D record with spherical-harmonic colour */
 
 typedef enum {
     WIPES_OK = 0,
@@ -68,7 +75,8 @@ typedef struct {
 } wipes_camera;
 
 /* Rendering options.  Defaults (wipes_default_opts): cutoff_sigma 3, alpha_min 1/255,
- * alpha_max 0.99, T_min 1e-4, dilation 0.3 px^2 (3D) / 0 (2D), bg 0, freq_proj_mode 0, cov2d 0. */
+ * alpha_max 0.99, T_min 1e-4, dilation 0.3 px^2 (3D) / 0 (2D), bg 0, freq_proj_mode 0, cov2d 0,
+ * sh_degree 0. */
 typedef struct {
     float cutoff_sigma;     /* a primitive counts at a pixel iff its squared Mahalanobis distance <= cutoff^2 */
     float alpha_min;        /* 3D: alpha below this is skipped */
@@ -80,6 +88,8 @@ typedef struct {
                                f' = (fc_x t_z / f_x, fc_y t_z / f_y) with fc = W f; 1 = the literal
                                f' = J W f (the covariance's ray-space map, Sec. 4.1) */
     int32_t cov2d;          /* 2D: 0 = RS record (s_x, s_y, theta), 1 = Cholesky record (l1, l2, l3) */
+    int32_t sh_degree;      /* 3D: 0 = RGB colour of the [N,20] record; 1..3 = spherical-harmonic colour of
+                               that degree from [N,68] records (params and dL/dparams) */
 } wipes_opts;
 
 /* Fill `out` with the defaults for dims = 2 or 3. */

@@ -24,14 +24,20 @@ _lock = threading.Lock()
 _lib = None
 
 # opts vector layout shared by the 3D calls: cutoff, alpha_min, alpha_max, T_min, dilation, bg(3),
-# frequency projection mode (0: phase gradient on the fronto-parallel plane, 1: literal J W f)
-DEFAULT_OPTS_3D = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 0.0], dtype=np.float32)
+# frequency projection mode (0: phase gradient on the fronto-parallel plane, 1: literal J W f),
+# spherical-harmonic colour degree (0: the record's RGB; 1..3: records of P3D_SH floats)
+DEFAULT_OPTS_3D = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 0.0, 0.0], dtype=np.float32)
+P3D_SH = 68
 
 
 def _opts3(opts):
-    """The 9-entry options vector (an 8-entry vector gets frequency projection mode 0)."""
+    """The 10-entry options vector (shorter vectors get mode 0 and RGB colour)."""
     o = _f32(DEFAULT_OPTS_3D if opts is None else opts).ravel()
-    return o if o.size == 9 else np.concatenate([o, np.zeros(9 - o.size, np.float32)])
+    return o if o.size == 10 else np.concatenate([o, np.zeros(10 - o.size, np.float32)])
+
+
+def _stride3(opts):
+    return P3D_SH if _opts3(opts)[9] else 20
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +69,7 @@ def _load():
         lib.wo_deform6d.argtypes = [P, i64, f64, P]
         lib.wo_deform6d_grad.argtypes = [P, i64, f64, P, P]
         lib.wo_cutoff_coverage.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P]
+        lib.wo_sh_basis.argtypes = [P, i64, P]
         _lib = lib
     return _lib
 
@@ -71,16 +78,19 @@ def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
-def _kind(dims, cov2d):
-    """Record kind of the C functions: 2 = 2D (RS), 3 = 3D, 4 = 2D with a Cholesky covariance."""
-    return 4 if dims == 2 and cov2d else dims
+def _kind(dims, cov2d=0, sh=0):
+    """Record kind of the C functions: 2 = 2D (RS), 3 = 3D, 4 = 2D with a Cholesky covariance,
+    5 = 3D with spherical-harmonic colour (P3D_SH floats per record)."""
+    if dims == 2:
+        return 4 if cov2d else 2
+    return 5 if sh else 3
 
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def footprints(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
+def footprints(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0, sh=0):
     """binary32 footprint rule: (rec[N,8] = mx,my,l11,l21,l22,ex,ey,depth, rect[N,4] = u0,v0,u1,v1, valid[N]).
     cov2d=1: 2D records carry the Cholesky factor (l1, l2, l3) of Sigma instead of (s_x, s_y, theta)."""
     params = _f32(params)
@@ -89,18 +99,18 @@ def footprints(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
     rect = np.zeros((n, 4), np.int32)
     valid = np.zeros(n, np.int32)
     camv = _f32(cam) if cam is not None else None
-    _load().wo_footprints(_kind(dims, cov2d), _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(rec), _ptr(rect),
+    _load().wo_footprints(_kind(dims, cov2d, sh), _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, _ptr(rec), _ptr(rect),
                           _ptr(valid))
     return rec, rect, valid
 
 
-def tile_lists(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
+def tile_lists(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0, sh=0):
     """Sorted (tile, primitive) pairs: by tile, then camera depth (3D), then primitive index."""
     params = _f32(params)
     n = params.shape[0]
     camv = _f32(cam) if cam is not None else None
     lib = _load()
-    kind = _kind(dims, cov2d)
+    kind = _kind(dims, cov2d, sh)
     total = lib.wo_tile_lists(kind, _ptr(params), n, _ptr(camv), H, W, cutoff, dilation, None, None, 0)
     tiles = np.zeros(max(total, 1), np.uint32)
     prims = np.zeros(max(total, 1), np.uint32)
@@ -166,8 +176,9 @@ def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True, with_abs=False)
     camv = _f32(cam)
     o = _opts3(opts)
     g = _f32(dldimg)
-    out = np.zeros((params.shape[0], 20), np.float64)
-    gabs = np.zeros((params.shape[0], 20), np.float64) if with_abs else None
+    P = _stride3(opts)
+    out = np.zeros((params.shape[0], P), np.float64)
+    gabs = np.zeros((params.shape[0], P), np.float64) if with_abs else None
     _load().wo_grad3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(g), _ptr(out),
                       _ptr(gabs))
     return (out, gabs) if with_abs else out
@@ -200,12 +211,20 @@ def deform6d_grad(params6, t, g3):
     return out
 
 
-def cutoff_coverage(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0):
+def sh_basis(dirs):
+    """Real spherical harmonics up to degree 3 (16 per direction) at unit vectors dirs[n,3]."""
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((d.shape[0], 16), np.float64)
+    _load().wo_sh_basis(_ptr(d), d.shape[0], _ptr(out))
+    return out
+
+
+def cutoff_coverage(dims, params, H, W, cam=None, cutoff=3.0, dilation=0.3, cov2d=0, sh=0):
     """(pairs inside the cutoff, of those outside the covered pixel range, pixels in the ranges,
     cutoff pairs that the tile ellipse test would drop)."""
     params = _f32(params)
     camv = _f32(cam) if cam is not None else None
     counts = np.zeros(4, np.int64)
-    _load().wo_cutoff_coverage(_kind(dims, cov2d), _ptr(params), params.shape[0], _ptr(camv), H, W, cutoff, dilation,
+    _load().wo_cutoff_coverage(_kind(dims, cov2d, sh), _ptr(params), params.shape[0], _ptr(camv), H, W, cutoff, dilation,
                                _ptr(counts))
     return int(counts[0]), int(counts[1]), int(counts[2]), int(counts[3])

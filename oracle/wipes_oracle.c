@@ -136,6 +136,8 @@ static void footprint2d_chol(const float* p, float cutoff, int W, int H, fp32_fo
 #define KIND_2D_RS 2
 #define KIND_3D 3
 #define KIND_2D_CHOL 4
+#define KIND_3D_SH 5 /* 3D record followed by spherical-harmonic coefficients: 68 floats */
+#define P3D_SH 68
 
 static void footprint_of(int kind, const float* params, int64_t i, const float* cam, float cutoff, float dil, int W,
                          int H, fp32_footprint* k);
@@ -207,7 +209,7 @@ static void footprint_of(int kind, const float* params, int64_t i, const float* 
                          int H, fp32_footprint* k) {
     if (kind == KIND_2D_RS) footprint2d(params + i * 16, cutoff, W, H, k);
     else if (kind == KIND_2D_CHOL) footprint2d_chol(params + i * 16, cutoff, W, H, k);
-    else footprint3d(params + i * 20, cam, cutoff, dil, W, H, k);
+    else footprint3d(params + i * (kind == KIND_3D_SH ? P3D_SH : 20), cam, cutoff, dil, W, H, k);
 }
 
 static float q32(const fp32_footprint* k, int u, int v) {
@@ -318,7 +320,7 @@ static fp32_footprint* all_footprints(int kind, const float* params, int64_t N, 
 /* Returns the number of entries (also when it exceeds cap; then only cap are written). */
 int64_t wo_tile_lists(int kind, const float* params, int64_t N, const float* cam, int H, int W, float cutoff, float dil,
                       uint32_t* tile_out, uint32_t* prim_out, int64_t cap) {
-    const int dims = kind == KIND_3D ? 3 : 2;
+    const int dims = kind == KIND_3D || kind == KIND_3D_SH ? 3 : 2;
     fp32_footprint* k = all_footprints(kind, params, N, cam, H, W, cutoff, dil);
     int tiles_x = (W + TILE - 1) / TILE;
     float lim = touch_limit(cutoff);
@@ -390,6 +392,8 @@ typedef struct {
     double t[3], R[9], M[9], V[9], Sc[9], J[6], fc[3], qn[4], qnorm, s[3];
     int unclamped_x, unclamped_y;
     int fmode;       /* frequency projection mode of project3d */
+    int sh;          /* SH degree of the colour (0: the record's RGB) */
+    double dir[3], dist, raw[3];  /* SH colour: unit direction camera -> centre, its length, unclamped colour */
 } proj;
 
 /* cov2d = 0: record mu s(2) theta ..., Sigma = R diag(sx^2, sy^2) R^T (Sec. 3.1, Sigma = R S S^T R^T);
@@ -429,6 +433,47 @@ static void quat_to_rot(const double q[4], double R[9]) {
 /* fmode 0: f' = (fc_x tz / fx, fc_y tz / fy), the phase gradient on the fronto-parallel plane through
  * the centre (reading of Sec. 4.1); fmode 1: f' = J fc, the frequency put through the same W and J
  * as the covariance, read literally (Sec. 4.1). */
+/* Real spherical harmonics up to degree 3 at the unit vector d = (x, y, z), Condon-Shortley phase,
+ * ordered l = 0..3 and m = -l..l within a degree (the view-dependent colour of 3DGS that the paper's
+ * 3D primitives carry, Sec. 3.1), and their partial derivatives with respect to x, y, z (the
+ * polynomials differentiated as functions on R^3). */
+static void sh_basis(const double d[3], double Y[16], double dY[16][3]) {
+    const double x = d[0], y = d[1], z = d[2];
+    const double k0 = 0.5 * sqrt(1.0 / PI), k1 = sqrt(3.0 / (4.0 * PI));
+    const double k2a = 0.5 * sqrt(15.0 / PI), k2b = 0.25 * sqrt(5.0 / PI), k2c = 0.25 * sqrt(15.0 / PI);
+    const double k3a = 0.25 * sqrt(35.0 / (2.0 * PI)), k3b = 0.5 * sqrt(105.0 / PI);
+    const double k3c = 0.25 * sqrt(21.0 / (2.0 * PI)), k3d = 0.25 * sqrt(7.0 / PI), k3e = 0.25 * sqrt(105.0 / PI);
+    const double xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = k0;
+    Y[1] = -k1 * y; Y[2] = k1 * z; Y[3] = -k1 * x;
+    Y[4] = k2a * x * y; Y[5] = -k2a * y * z; Y[6] = k2b * (2 * zz - xx - yy); Y[7] = -k2a * x * z;
+    Y[8] = k2c * (xx - yy);
+    Y[9] = -k3a * y * (3 * xx - yy); Y[10] = k3b * x * y * z; Y[11] = -k3c * y * (4 * zz - xx - yy);
+    Y[12] = k3d * z * (2 * zz - 3 * xx - 3 * yy); Y[13] = -k3c * x * (4 * zz - xx - yy); Y[14] = k3e * z * (xx - yy);
+    Y[15] = -k3a * x * (xx - 3 * yy);
+    const double g[16][3] = {{0, 0, 0},
+                             {0, -k1, 0}, {0, 0, k1}, {-k1, 0, 0},
+                             {k2a * y, k2a * x, 0}, {0, -k2a * z, -k2a * y}, {-2 * k2b * x, -2 * k2b * y, 4 * k2b * z},
+                             {-k2a * z, 0, -k2a * x}, {2 * k2c * x, -2 * k2c * y, 0},
+                             {-6 * k3a * x * y, -3 * k3a * (xx - yy), 0},
+                             {k3b * y * z, k3b * x * z, k3b * x * y},
+                             {2 * k3c * x * y, -k3c * (4 * zz - xx - 3 * yy), -8 * k3c * y * z},
+                             {-6 * k3d * x * z, -6 * k3d * y * z, k3d * (6 * zz - 3 * xx - 3 * yy)},
+                             {-k3c * (4 * zz - 3 * xx - yy), 2 * k3c * x * y, -8 * k3c * x * z},
+                             {2 * k3e * x * z, -2 * k3e * y * z, k3e * (xx - yy)},
+                             {-3 * k3a * (xx - yy), 6 * k3a * x * y, 0}};
+    if (dY) memcpy(dY, g, sizeof(g));
+}
+
+/* exported for tests: Y[n,16] at n unit vectors */
+int wo_sh_basis(const double* dirs, int64_t n, double* Y) {
+    for (int64_t i = 0; i < n; ++i) sh_basis(dirs + 3 * i, Y + 16 * i, NULL);
+    return 0;
+}
+
+/* view-dependent colour of an SH record: the coefficient of basis k for channel ch */
+static double sh_coef(const float* p, int k, int ch) { return k == 0 ? (double)p[15 + ch] : (double)p[20 + 3 * (k - 1) + ch]; }
+
 static void project3d(const float* p, const float* cam, int H, int W, double dil, int fmode, int valid32, proj* w) {
     memset(w, 0, sizeof(*w));
     w->valid = valid32;
@@ -484,6 +529,27 @@ static void project3d(const float* p, const float* cam, int H, int W, double dil
     w->phi = p[13];
     w->o = p[14];
     w->c[0] = p[15]; w->c[1] = p[16]; w->c[2] = p[17];
+}
+
+/* SH colour (degree sh >= 1): c = max(0, 1/2 + sum_k Y_k(dir) sh_k), dir the unit vector from the
+ * camera centre -V^T t0 to mu (as 3DGS evaluates it) */
+static void sh_colour(const float* p, const float* cam, int sh, proj* w) {
+    double cpos[3];
+    for (int j = 0; j < 3; ++j)
+        cpos[j] = -((double)cam[0 * 4 + j] * cam[3] + (double)cam[1 * 4 + j] * cam[7] + (double)cam[2 * 4 + j] * cam[11]);
+    double v[3] = {p[0] - cpos[0], p[1] - cpos[1], p[2] - cpos[2]};
+    w->dist = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int j = 0; j < 3; ++j) w->dir[j] = v[j] / w->dist;
+    double Y[16];
+    sh_basis(w->dir, Y, NULL);
+    const int nk = (sh + 1) * (sh + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        double r = 0.5;
+        for (int k = 0; k < nk; ++k) r += Y[k] * sh_coef(p, k, ch);
+        w->raw[ch] = r;
+        w->c[ch] = r > 0.0 ? r : 0.0;
+    }
+    w->sh = sh;
 }
 
 /* W'(x) and its pieces at pixel (u, v) */
@@ -680,12 +746,13 @@ int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int tr
 /* 3D: projection and front-to-back alpha blending                                             */
 /* ------------------------------------------------------------------------------------------ */
 
-/* opts[9] = cutoff, alpha_min, alpha_max, T_min, dilation, bg_r, bg_g, bg_b, frequency projection
- * mode (0: phase gradient on the fronto-parallel plane; 1: the literal f' = (J W f)_xy) */
-typedef struct { float cutoff, amin, amax, Tmin, dil; double bg[3]; int fmode; } blend_opts;
+/* opts[10] = cutoff, alpha_min, alpha_max, T_min, dilation, bg_r, bg_g, bg_b, frequency projection
+ * mode (0: phase gradient on the fronto-parallel plane; 1: the literal f' = (J W f)_xy), degree of
+ * the spherical-harmonic colour (0: the record's RGB colour; 1..3: SH records of P3D_SH floats) */
+typedef struct { float cutoff, amin, amax, Tmin, dil; double bg[3]; int fmode, sh; } blend_opts;
 
 static blend_opts read_opts(const float* o) {
-    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}, o[8] != 0.0f};
+    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}, o[8] != 0.0f, (int)o[9]};
     return b;
 }
 
@@ -705,13 +772,17 @@ typedef struct {
     int64_t nvalid;
 } scene3;
 
+static int rec3_stride(const blend_opts* o) { return o->sh ? P3D_SH : 20; }
+
 static void scene3_build(const float* params, int64_t N, const float* cam, int H, int W, const blend_opts* o, scene3* s) {
-    s->k = all_footprints(3, params, N, cam, H, W, o->cutoff, o->dil);
+    const int P = rec3_stride(o);
+    s->k = all_footprints(o->sh ? KIND_3D_SH : KIND_3D, params, N, cam, H, W, o->cutoff, o->dil);
     s->w = (proj*)malloc(sizeof(proj) * (size_t)(N > 0 ? N : 1));
     order_entry* e = (order_entry*)malloc(sizeof(order_entry) * (size_t)(N > 0 ? N : 1));
     int64_t n = 0;
     for (int64_t i = 0; i < N; ++i) {
-        project3d(params + i * 20, cam, H, W, o->dil, o->fmode, s->k[i].valid, &s->w[i]);
+        project3d(params + i * P, cam, H, W, o->dil, o->fmode, s->k[i].valid, &s->w[i]);
+        if (o->sh) sh_colour(params + i * P, cam, o->sh, &s->w[i]);
         if (s->k[i].valid) { e[n].depth = f32_bits(s->k[i].depth); e[n].prim = (uint32_t)i; ++n; }
     }
     qsort(e, (size_t)n, sizeof(order_entry), cmp_order);
@@ -812,10 +883,10 @@ static void quat_rot_jac(const double q[4], double dR[36]) {
 
 /* chain the image-plane gradient of a 3D primitive to its record:
  * mu(3) s(3) q(4) f(3) phi opacity c(3) */
-static void chain3d(const proj* w, const float* cam, const pgrad* g, double* out) {
+static void chain3d(const proj* w, const float* p, const float* cam, const pgrad* g, double* out) {
     double fx = cam[12], fy = cam[13];
     double tx = w->t[0], ty = w->t[1], tz = w->t[2];
-    memset(out, 0, sizeof(double) * 20);
+    memset(out, 0, sizeof(double) * (w->sh ? P3D_SH : 20));
     /* K = Sigma'^-1:  dL/dSigma' = -K (dL/dK) K */
     double t1[4], gS2[4];
     matmul(w->K, g->K, t1, 2, 2, 2);
@@ -897,6 +968,25 @@ static void chain3d(const proj* w, const float* cam, const pgrad* g, double* out
     out[13] = g->phi;
     out[14] = g->o;
     out[15] = g->c[0]; out[16] = g->c[1]; out[17] = g->c[2];
+    if (w->sh) {
+        /* c_ch = max(0, 1/2 + sum_k Y_k(dir) sh_k,ch): dL/dsh_k,ch = dL/dc_ch Y_k where unclamped, and the
+           centre gains dL/ddir (I - dir dir^T) / |mu - camera centre| */
+        double Y[16], dY[16][3], gdir[3] = {0, 0, 0};
+        sh_basis(w->dir, Y, dY);
+        const int nk = (w->sh + 1) * (w->sh + 1);
+        for (int ch = 0; ch < 3; ++ch) {
+            const double gc = w->raw[ch] > 0.0 ? g->c[ch] : 0.0;
+            for (int k = 0; k < nk; ++k) {
+                const double v = gc * Y[k];
+                if (k == 0) out[15 + ch] = v;
+                else out[20 + 3 * (k - 1) + ch] = v;
+                const double a = gc * sh_coef(p, k, ch);
+                for (int j = 0; j < 3; ++j) gdir[j] += a * dY[k][j];
+            }
+        }
+        const double dd = gdir[0] * w->dir[0] + gdir[1] * w->dir[1] + gdir[2] * w->dir[2];
+        for (int j = 0; j < 3; ++j) out[j] += (gdir[j] - dd * w->dir[j]) / w->dist;
+    }
 }
 
 static void pgrad_add(pgrad* g, const pgrad* a) {
@@ -907,7 +997,8 @@ static void pgrad_add(pgrad* g, const pgrad* a) {
     g->o += a->o;
 }
 
-/* grad[N,20] of L = sum_pixels dldimg . C.  Pixels with a zero upstream gradient are skipped.
+/* grad[N,20] (or [N,P3D_SH] with SH colour) of L = sum_pixels dldimg . C.  Pixels with a zero upstream
+ * gradient are skipped.
  * gabs (optional) as in wo_grad2d. */
 int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, int truncated,
               const float* dldimg, double* grad, double* gabs) {
@@ -919,8 +1010,9 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
     extern int omp_get_max_threads(void);
     nthreads = omp_get_max_threads();
 #endif
+    const int P = rec3_stride(&o);
     pgrad* acc = (pgrad*)calloc((size_t)nthreads * (size_t)(N > 0 ? N : 1), sizeof(pgrad));
-    double* abs_acc = gabs ? (double*)calloc((size_t)nthreads * (size_t)(N > 0 ? N : 1) * 20, sizeof(double)) : NULL;
+    double* abs_acc = gabs ? (double*)calloc((size_t)nthreads * (size_t)(N > 0 ? N : 1) * P, sizeof(double)) : NULL;
 #pragma omp parallel
     {
         int tid = 0;
@@ -957,10 +1049,10 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
                 }
                 pgrad_add(&my[cb->prim], &one);
                 if (abs_acc) {
-                    double t[20];
-                    chain3d(w, cam, &one, t);
-                    double* a = abs_acc + ((size_t)tid * (size_t)N + cb->prim) * 20;
-                    for (int q = 0; q < 20; ++q) a[q] += fabs(t[q]);
+                    double t[P3D_SH];
+                    chain3d(w, params + (size_t)cb->prim * P, cam, &one, t);
+                    double* a = abs_acc + ((size_t)tid * (size_t)N + cb->prim) * P;
+                    for (int q = 0; q < P; ++q) a[q] += fabs(t[q]);
                 }
             }
         }
@@ -977,13 +1069,13 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
             g.phi += a->phi;
             g.o += a->o;
         }
-        if (s.w[i].valid) chain3d(&s.w[i], cam, &g, grad + i * 20);
-        else memset(grad + i * 20, 0, sizeof(double) * 20);
+        if (s.w[i].valid) chain3d(&s.w[i], params + i * P, cam, &g, grad + i * P);
+        else memset(grad + i * P, 0, sizeof(double) * P);
         if (gabs) {
-            for (int q = 0; q < 20; ++q) {
+            for (int q = 0; q < P; ++q) {
                 double a = 0.0;
-                for (int t = 0; t < nthreads; ++t) a += abs_acc[((size_t)t * (size_t)N + (size_t)i) * 20 + q];
-                gabs[i * 20 + q] = a;
+                for (int t = 0; t < nthreads; ++t) a += abs_acc[((size_t)t * (size_t)N + (size_t)i) * P + q];
+                gabs[i * P + q] = a;
             }
         }
     }
@@ -997,11 +1089,13 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
  * valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), 0, 0 */
 int wo_project3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, double* out) {
     blend_opts o = read_opts(opts);
+    const int P = rec3_stride(&o);
     for (int64_t i = 0; i < N; ++i) {
         fp32_footprint k;
-        footprint3d(params + i * 20, cam, o.cutoff, o.dil, W, H, &k);
+        footprint3d(params + i * P, cam, o.cutoff, o.dil, W, H, &k);
         proj w;
-        project3d(params + i * 20, cam, H, W, o.dil, o.fmode, k.valid, &w);
+        project3d(params + i * P, cam, H, W, o.dil, o.fmode, k.valid, &w);
+        if (o.sh) sh_colour(params + i * P, cam, o.sh, &w);
         double S2[4];
         mat2_inv(w.K, S2);
         double* r = out + i * 16;

@@ -27,7 +27,8 @@ class WipesError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("cutoff_sigma", c_float), ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float),
-                ("dilation", c_float), ("bg", c_float * 3), ("freq_proj_mode", c_int32), ("cov2d", c_int32)]
+                ("dilation", c_float), ("bg", c_float * 3), ("freq_proj_mode", c_int32), ("cov2d", c_int32),
+                ("sh_degree", c_int32)]
 
 
 class Camera(ctypes.Structure):

@@ -338,6 +338,7 @@ wipes_status check_opts(const wipes_opts* o) {
     if (o->freq_proj_mode != 0 && o->freq_proj_mode != 1)
         return fail(WIPES_ERR_INVALID, "freq_proj_mode must be 0 (fronto-parallel phase gradient) or 1 (literal J W f)");
     if (o->cov2d != 0 && o->cov2d != 1) return fail(WIPES_ERR_INVALID, "cov2d must be 0 (RS) or 1 (Cholesky)");
+    if (o->sh_degree < 0 || o->sh_degree > 3) return fail(WIPES_ERR_INVALID, "sh_degree must lie in 0..3");
     return WIPES_OK;
 }
 
@@ -482,7 +483,7 @@ wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* param
     {
         StageTimer t(ctx, WIPES_STAGE_FOOTPRINT, s);
         launch_footprint3d(params, N, *cam, W, H, opts->cutoff_sigma, opts->dilation, opts->freq_proj_mode,
-                           st->rec.as<float4>(),
+                           opts->sh_degree, st->rec.as<float4>(),
                            st->rect.as<PixRect>(), st->counts.as<uint32_t>(), st->dkeys[0].as<uint32_t>(), s);
     }
     // front-to-back order: stable sort of the primitives by the bits of their camera depth
@@ -575,7 +576,8 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
                               dL_dout, st->grad_img.as<float>(), st->order.as<uint32_t>(), s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
-        launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->opts.freq_proj_mode, st->rec.as<float4>(),
+        launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->opts.freq_proj_mode,
+                       st->opts.sh_degree, st->rec.as<float4>(),
                        st->grad_img.as<float>(), dL_dparams, s);
     }
     WIPES_CUDA(cudaGetLastError());

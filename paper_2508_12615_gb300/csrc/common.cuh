@@ -76,6 +76,67 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// View-dependent colour (the spherical-harmonic colour of 3DGS that the paper's 3D primitives carry,
+// Sec. 3.1).  Real spherical harmonics of degree <= 3 at the unit vector (x, y, z), Condon-Shortley
+// phase, ordered by degree l and order m = -l..l; the constants are the normalisations
+// 1/2 sqrt(1/pi), sqrt(3/(4 pi)), 1/2 sqrt(15/pi), 1/4 sqrt(5/pi), 1/4 sqrt(15/pi),
+// 1/4 sqrt(35/(2 pi)), 1/2 sqrt(105/pi), 1/4 sqrt(21/(2 pi)), 1/4 sqrt(7/pi), 1/4 sqrt(105/pi).
+constexpr int kShMaxCoeffs = 16;
+struct ShConst {
+    static constexpr float c0 = 0.28209479177387814f, c1 = 0.4886025119029199f;
+    static constexpr float c2a = 1.0925484305920792f, c2b = 0.31539156525252005f, c2c = 0.5462742152960396f;
+    static constexpr float c3a = 0.5900435899266435f, c3b = 2.890611442640554f, c3c = 0.4570457994644658f;
+    static constexpr float c3d = 0.3731763325901154f, c3e = 1.445305721320277f;
+};
+
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float Y[kShMaxCoeffs]) {
+    using K = ShConst;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = K::c0;
+    Y[1] = -K::c1 * y;
+    Y[2] = K::c1 * z;
+    Y[3] = -K::c1 * x;
+    Y[4] = K::c2a * x * y;
+    Y[5] = -K::c2a * y * z;
+    Y[6] = K::c2b * (2.f * zz - xx - yy);
+    Y[7] = -K::c2a * x * z;
+    Y[8] = K::c2c * (xx - yy);
+    Y[9] = -K::c3a * y * (3.f * xx - yy);
+    Y[10] = K::c3b * x * y * z;
+    Y[11] = -K::c3c * y * (4.f * zz - xx - yy);
+    Y[12] = K::c3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -K::c3c * x * (4.f * zz - xx - yy);
+    Y[14] = K::c3e * z * (xx - yy);
+    Y[15] = -K::c3a * x * (xx - 3.f * yy);
+}
+
+// Partial derivatives dY_k/dx, dY_k/dy, dY_k/dz of the polynomials above.
+__device__ __forceinline__ void sh_eval_grad(float x, float y, float z, float gx[kShMaxCoeffs], float gy[kShMaxCoeffs],
+                                             float gz[kShMaxCoeffs]) {
+    using K = ShConst;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx[0] = 0.f; gy[0] = 0.f; gz[0] = 0.f;
+    gx[1] = 0.f; gy[1] = -K::c1; gz[1] = 0.f;
+    gx[2] = 0.f; gy[2] = 0.f; gz[2] = K::c1;
+    gx[3] = -K::c1; gy[3] = 0.f; gz[3] = 0.f;
+    gx[4] = K::c2a * y; gy[4] = K::c2a * x; gz[4] = 0.f;
+    gx[5] = 0.f; gy[5] = -K::c2a * z; gz[5] = -K::c2a * y;
+    gx[6] = -2.f * K::c2b * x; gy[6] = -2.f * K::c2b * y; gz[6] = 4.f * K::c2b * z;
+    gx[7] = -K::c2a * z; gy[7] = 0.f; gz[7] = -K::c2a * x;
+    gx[8] = 2.f * K::c2c * x; gy[8] = -2.f * K::c2c * y; gz[8] = 0.f;
+    gx[9] = -6.f * K::c3a * x * y; gy[9] = -3.f * K::c3a * (xx - yy); gz[9] = 0.f;
+    gx[10] = K::c3b * y * z; gy[10] = K::c3b * x * z; gz[10] = K::c3b * x * y;
+    gx[11] = 2.f * K::c3c * x * y; gy[11] = -K::c3c * (4.f * zz - xx - 3.f * yy); gz[11] = -8.f * K::c3c * y * z;
+    gx[12] = -6.f * K::c3d * x * z; gy[12] = -6.f * K::c3d * y * z; gz[12] = K::c3d * (6.f * zz - 3.f * xx - 3.f * yy);
+    gx[13] = -K::c3c * (4.f * zz - 3.f * xx - yy); gy[13] = 2.f * K::c3c * x * y; gz[13] = -8.f * K::c3c * x * z;
+    gx[14] = 2.f * K::c3e * x * z; gy[14] = -2.f * K::c3e * y * z; gz[14] = K::c3e * (xx - yy);
+    gx[15] = -3.f * K::c3a * (xx - yy); gy[15] = 6.f * K::c3a * x * y; gz[15] = 0.f;
+}
+
+// SH coefficient k (0..15) of channel ch in an [N, WIPES_P3D_SH] record: the record colour for
+// k = 0, then three channels per basis function.
+__device__ __forceinline__ int sh_slot(int k, int ch) { return k == 0 ? 15 + ch : 20 + 3 * (k - 1) + ch; }
+
 // Cutoff test of a rectangle of pixel centres (columns x0..x1, rows y0..y1): does the cutoff
 // ellipse q <= lim (lim = cutoff^2 x 1.01) reach it?  With q = A dx^2 + 2 B dx dy + C dy^2
 // (A = l11^2, B = l11 l21, C = l21^2 + l22^2) the minimum over the rectangle is 0 when the centre
@@ -241,6 +302,13 @@ inline float touch_limit(float cutoff) {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Camera centre in world coordinates, -R^T t for the view matrix [R | t].
+inline void camera_centre(const wipes_camera& cam, float out[3]) {
+    for (int j = 0; j < 3; ++j)
+        out[j] = -(cam.viewmat[0 * 4 + j] * cam.viewmat[3] + cam.viewmat[1 * 4 + j] * cam.viewmat[7] +
+                   cam.viewmat[2 * 4 + j] * cam.viewmat[11]);
+}
+
 // Library-wide count of kernel launches (every launcher adds the kernels it enqueues).
 void count_launches(int n);
 
@@ -250,8 +318,8 @@ void count_launches(int n);
 void launch_footprint2d(const float* params, int64_t N, int W, int H, float cutoff, int cov2d, float4* rec, PixRect* rect,
                         uint32_t* counts, uint32_t* depth_keys, cudaStream_t stream);
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
-                        float dilation, int fmode, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
-                        cudaStream_t stream);
+                        float dilation, int fmode, int sh_degree, float4* rec, PixRect* rect, uint32_t* counts,
+                        uint32_t* depth_keys, cudaStream_t stream);
 void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream);
 void launch_deform6d_backward(const float* params6, int64_t N, float t, const float* g3, float* g6, int accumulate,
                               cudaStream_t stream);
@@ -325,7 +393,7 @@ void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& 
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
                        const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream);
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation, int fmode,
-                    const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
+                    int sh_degree, const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 
 // batch.cu: one persistent launch over the tiles of up to kMaxBatchJobs frames; blocks take
 // (frame, tile) items from counter[0], which the launcher resets.

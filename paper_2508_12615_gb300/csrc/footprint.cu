@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ 
 struct Cam {
     float V[12];
     float fx, fy, cx, cy, near_z;
+    float cpos[3];  // camera centre in world coordinates (spherical-harmonic colour)
 };
 
 // 3D: camera-frame centre t = V mu + t0; P = J V R(q) S (2x3), Sigma' = P P^T + dil I with the
@@ -157,16 +158,19 @@ struct Cam {
 // Frequency: fc = V f; fmode 0: f' = (fc_x tz / fx, fc_y tz / fy) (phase gradient on the
 // fronto-parallel plane through the centre; the viewing-axis component is dropped, Sec. 4.1);
 // fmode 1: f' = J fc (the same W and J as the covariance, read literally, Sec. 4.1).
+// Colour: the record's c, or with sh_degree > 0 (records of WIPES_P3D_SH floats)
+// max(0, 1/2 + sum_k Y_k(dir) sh_k) per channel, dir the unit vector from the camera centre to mu.
 __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ params, int64_t N, Cam cam, int W,
                                                      int H, float cutoff, float lim, float dil, int fmode,
-                                                     float4* __restrict__ rec,
+                                                     int sh_degree, float4* __restrict__ rec,
                                                      PixRect* __restrict__ rect, uint32_t* __restrict__ counts,
                                                      uint32_t* __restrict__ depth_keys) {
     pdl_enter();
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i0 < N;
     const int64_t i = live ? i0 : N - 1;  // lanes past the end repeat the last primitive, write nothing
-    const float4* pp = reinterpret_cast<const float4*>(params + i * WIPES_P3D);
+    const int stride = sh_degree ? WIPES_P3D_SH : WIPES_P3D;
+    const float4* pp = reinterpret_cast<const float4*>(params + i * stride);
     const float4 a0 = pp[0], a1 = pp[1], a2 = pp[2], a3 = pp[3], a4 = pp[4];
     float p[20] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y,
                    a2.z, a2.w, a3.x, a3.y, a3.z, a3.w, a4.x, a4.y, a4.z, a4.w};
@@ -244,9 +248,26 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
         fpx = fcx * tz / cam.fx;
         fpy = fcy * tz / cam.fy;
     }
+    float col[3] = {p[15], p[16], p[17]};
+    if (sh_degree) {
+        const float vx = p[0] - cam.cpos[0], vy = p[1] - cam.cpos[1], vz = p[2] - cam.cpos[2];
+        const float dist = sqrtf(vx * vx + vy * vy + vz * vz);
+        float Y[kShMaxCoeffs];
+        sh_eval(vx / dist, vy / dist, vz / dist, Y);
+        const int nk = (sh_degree + 1) * (sh_degree + 1);
+        const float* q = params + i * stride;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float r = 0.5f;
+#pragma unroll
+            for (int k = 0; k < kShMaxCoeffs; ++k)
+                if (k < nk) r += Y[k] * q[sh_slot(k, ch)];
+            col[ch] = fmaxf(r, 0.f);
+        }
+    }
     rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
     rec[i * kRecF4 + 1] = make_float4(l22, fpx, fpy, p[13] * kInvTwoPi);
-    rec[i * kRecF4 + 2] = make_float4(p[15], p[16], p[17], p[14]);
+    rec[i * kRecF4 + 2] = make_float4(col[0], col[1], col[2], p[14]);
     rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, 0.0f);
     rect[i] = rr;
     counts[i] = cnt;
@@ -312,14 +333,15 @@ void launch_footprint2d(const float* params, int64_t N, int W, int H, float cuto
 }
 
 void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float cutoff,
-                        float dilation, int fmode, float4* rec, PixRect* rect, uint32_t* counts, uint32_t* depth_keys,
-                        cudaStream_t stream) {
+                        float dilation, int fmode, int sh_degree, float4* rec, PixRect* rect, uint32_t* counts,
+                        uint32_t* depth_keys, cudaStream_t stream) {
     if (N == 0) return;
     Cam c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
+    camera_centre(cam, c.cpos);
     launch_pdl(k_footprint3d, ceil_div(N, 256), 256, 0, stream, params, N, c, W, H, cutoff, touch_limit(cutoff), dilation,
-               fmode, rec, rect, counts, depth_keys);
+               fmode, sh_degree, rec, rect, counts, depth_keys);
     count_launches(1);
 }
 

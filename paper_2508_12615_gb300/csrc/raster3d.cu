@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_backward3d(const float4* __res
 struct Cam3 {
     float V[12];
     float fx, fy, cx, cy, near_z;
+    float cpos[3];  // camera centre in world coordinates
 };
 
 // d R(q)_e / d q_m for a unit quaternion q = (w, x, y, z)
@@ -198,20 +199,22 @@ __device__ __forceinline__ void quat_rot_grad(const float q[4], const float gR[9
 }
 
 // Chain the image-plane gradient (mx, my, L, f', phc, c, o) to the record mu, s, q, f, phi, o, c.
+// With sh_degree > 0 the records and gradients hold WIPES_P3D_SH floats: dL/dsh_k = dL/dc Y_k(dir)
+// where the colour was not clamped, and mu gains dL/ddir (I - dir dir^T) / |mu - camera centre|.
 __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ params, int64_t N, Cam3 cam, int W, int H,
-                                                 float dil, int fmode, const float4* __restrict__ rec,
+                                                 float dil, int fmode, int sh_degree, const float4* __restrict__ rec,
                                                  const float* __restrict__ grad_img, float* __restrict__ dl_dparams) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    float* out = dl_dparams + i * WIPES_P3D;
+    const int stride = sh_degree ? WIPES_P3D_SH : WIPES_P3D;
+    float* out = dl_dparams + i * stride;
     const float4 r0 = rec[(size_t)i * kRecF4 + 0];
     if (!(r0.z > 0.f)) {  // culled or degenerate: no gradient
-#pragma unroll
-        for (int k = 0; k < WIPES_P3D; ++k) out[k] = 0.f;
+        for (int k = 0; k < stride; ++k) out[k] = 0.f;
         return;
     }
-    const float* p = params + i * WIPES_P3D;
+    const float* p = params + i * stride;
     const float* g = grad_img + (size_t)i * kG;
     const float g_mx = g[0], g_my = g[1], g11 = g[2], g21 = g[3], g22 = g[4], g_fx = g[5], g_fy = g[6];
     const float* V = cam.V;
@@ -341,6 +344,38 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
     out[17] = g[10];
     out[18] = 0.f;
     out[19] = 0.f;
+    if (sh_degree) {
+        const float vx = p[0] - cam.cpos[0], vy = p[1] - cam.cpos[1], vz = p[2] - cam.cpos[2];
+        const float dist = sqrtf(vx * vx + vy * vy + vz * vz);
+        const float dx = vx / dist, dy = vy / dist, dz = vz / dist;
+        float Y[kShMaxCoeffs], Yx[kShMaxCoeffs], Yy[kShMaxCoeffs], Yz[kShMaxCoeffs];
+        sh_eval(dx, dy, dz, Y);
+        sh_eval_grad(dx, dy, dz, Yx, Yy, Yz);
+        const int nk = (sh_degree + 1) * (sh_degree + 1);
+        float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < kShMaxCoeffs; ++k)
+                if (k < nk) raw += Y[k] * p[sh_slot(k, ch)];
+            const float gc = raw > 0.f ? g[8 + ch] : 0.f;
+#pragma unroll
+            for (int k = 0; k < kShMaxCoeffs; ++k) {
+                if (k >= nk) continue;
+                const float c = p[sh_slot(k, ch)];
+                out[sh_slot(k, ch)] = gc * Y[k];
+                gdx += gc * c * Yx[k];
+                gdy += gc * c * Yy[k];
+                gdz += gc * c * Yz[k];
+            }
+        }
+        for (int k = 20 + 3 * (nk - 1); k < WIPES_P3D_SH; ++k) out[k] = 0.f;
+        const float dd = gdx * dx + gdy * dy + gdz * dz;
+        out[0] += (gdx - dd * dx) / dist;
+        out[1] += (gdy - dd * dy) / dist;
+        out[2] += (gdz - dd * dz) / dist;
+    }
 }
 
 }  // namespace
@@ -359,13 +394,14 @@ void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& 
 }
 
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation, int fmode,
-                    const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream) {
+                    int sh_degree, const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
     Cam3 c;
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
-    launch_pdl(k_chain3d, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, fmode, rec, grad_img,
-               dl_dparams); count_launches(1);
+    camera_centre(cam, c.cpos);
+    launch_pdl(k_chain3d, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, fmode, sh_degree, rec,
+               grad_img, dl_dparams); count_launches(1);
 }
 
 }  // namespace wipes

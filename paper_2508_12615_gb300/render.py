@@ -18,7 +18,7 @@ import torch
 
 from . import _abi
 
-P2D, P3D, P6D = 16, 20, 32
+P2D, P3D, P6D, P3D_SH = 16, 20, 32, 68
 
 
 class Context:
@@ -147,11 +147,12 @@ def forward2d(params: torch.Tensor, H: int, W: int, opts: _abi.Opts | None = Non
 
 def forward3d(params: torch.Tensor, camera, H: int, W: int, opts: _abi.Opts | None = None,
               state: State | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
-    """Front-to-back blended image [H,W,3] (no autograd).  camera: 17 floats."""
-    params = _check(params, P3D, "params")
+    """Front-to-back blended image [H,W,3] (no autograd).  camera: 17 floats.  params [N,20], or
+    [N,68] with spherical-harmonic colour (opts.sh_degree > 0)."""
+    opts = opts or make_opts(3)
+    params = _check(params, P3D_SH if opts.sh_degree else P3D, "params")
     ctx = Context.get(params.device)
     state = state or ctx.acquire_state()
-    opts = opts or make_opts(3)
     cam = _abi.camera_struct(camera.tolist() if hasattr(camera, "tolist") else camera)
     if out is None:
         out = torch.empty(H, W, 3, dtype=torch.float32, device=params.device)

@@ -148,6 +148,24 @@ def scene3d(n: int, seed: int, scale_range=(0.002, 0.05), max_freq=40.0, extent=
     return p
 
 
+P3D_SH = 68  # 3D record followed by the 15 higher spherical-harmonic coefficients per channel
+
+
+def scene3d_sh(n: int, seed: int, degree: int = 3, sh_sigma: float = 0.15, **kw) -> np.ndarray:
+    """3D primitives with spherical-harmonic colour: the scene3d record (its colour c serves as the
+    degree-0 coefficients, drawn so that the constant part of the colour is uniform in [0, 1])
+    followed by the coefficients of degrees 1..degree, N(0, sh_sigma) each (zero above degree)."""
+    base = scene3d(n, seed, **kw)
+    rng = _rng(seed + 7919)
+    p = np.zeros((n, P3D_SH), dtype=np.float32)
+    p[:, :P3D] = base
+    y00 = 0.5 / math.sqrt(math.pi)
+    p[:, 15:18] = (base[:, 15:18] - 0.5) / y00
+    nk = (degree + 1) ** 2 - 1
+    p[:, 20:20 + 3 * nk] = rng.normal(0.0, sh_sigma, (n, 3 * nk))
+    return p
+
+
 def scene6d(n: int, seed: int, rate_sigma=0.05, **kw) -> np.ndarray:
     """6D primitives: a 3D scene plus per-primitive linear rates over a unit time span for the
     centre (v), frequency (df), phase (dphi) and log-scale (dlog_s), each N(0, rate_sigma)."""

@@ -44,7 +44,7 @@ def test_no_cuda_needed_for_host_helpers(lib):
 
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(_abi.Camera) == 17 * 4
-    assert ctypes.sizeof(_abi.Opts) == 10 * 4
+    assert ctypes.sizeof(_abi.Opts) == 11 * 4
     assert ctypes.sizeof(_abi.StateInfo) == 5 * 4 + 4 + 3 * 8  # int32 x5, padding, int64 x3
 
 

@@ -477,6 +477,93 @@ def test_literal_frequency_grad_matches_central_differences():
 
 
 # ---------------------------------------------------------------------------------------------
+# spherical-harmonic colour (the view-dependent colour of 3DGS, Sec. 3.1)
+# ---------------------------------------------------------------------------------------------
+
+OPTS_SH3 = np.array([3.0, 0.0, 1.0, 0.0, 0.3, 0.0, 0.0, 0.0, 0.0, 3.0], np.float32)  # exact, SH degree 3
+
+
+def test_sh_basis_is_orthonormal_on_the_sphere():
+    """Gauss-Legendre in cos(theta) times uniform azimuth integrates products of degree <= 3
+    harmonics exactly: the 16 functions are orthonormal."""
+    ct, wt = np.polynomial.legendre.leggauss(8)
+    ph = np.arange(16) * (2 * math.pi / 16)
+    st = np.sqrt(1 - ct * ct)
+    d = np.stack([np.outer(st, np.cos(ph)).ravel(), np.outer(st, np.sin(ph)).ravel(), np.repeat(ct, 16)], 1)
+    w = np.repeat(wt, 16) * (2 * math.pi / 16)
+    Y = oracle.sh_basis(d)
+    np.testing.assert_allclose((Y * w[:, None]).T @ Y, np.eye(16), atol=1e-12)
+
+
+def test_sh_basis_matches_scipy_real_harmonics():
+    """The basis is scipy's complex spherical harmonics (with the Condon-Shortley phase) made real:
+    sqrt(2) Im Y_l^|m| for m < 0, Y_l^0, sqrt(2) Re Y_l^m for m > 0, ordered m = -l..l."""
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    polar, az = np.arccos(d[:, 2]), np.arctan2(d[:, 1], d[:, 0])
+    Y = oracle.sh_basis(d)
+    k = 0
+    for l in range(4):
+        for m in range(-l, l + 1):
+            c = sp.sph_harm_y(l, abs(m), polar, az)
+            ref = c.real if m == 0 else math.sqrt(2) * (c.imag if m < 0 else c.real)
+            np.testing.assert_allclose(Y[:, k], ref, atol=1e-12)
+            k += 1
+
+
+def test_sh_record_with_only_the_constant_term_renders_the_rgb_record():
+    """Degree-0 coefficients (c - 1/2) / Y_0^0 and nothing else reproduce the plain colour c."""
+    H, W = 40, 44
+    p = synth.scene3d(300, 51)
+    q = np.zeros((len(p), synth.P3D_SH), np.float32)
+    q[:, :20] = p
+    q[:, 15:18] = (p[:, 15:18].astype(np.float64) - 0.5) / (0.5 / math.sqrt(math.pi))
+    cam = synth.sphere_cameras(1, H, W, 52)[0]
+    a = oracle.render3d(p, cam, H, W, OPTS_EXACT, truncated=False)[0]
+    b = oracle.render3d(q, cam, H, W, OPTS_SH3, truncated=False)[0]
+    assert np.abs(a - b).max() <= 1e-6
+
+
+def test_sh_colour_is_taken_in_the_direction_from_the_camera_to_the_centre():
+    """A camera at (0, -5, 0) looking at a primitive at the origin sees it in direction +y: with a
+    single degree-1 coefficient s on the basis function of index 1, the centre pixel shows
+    1/2 + Y_1(0, 1, 0) s (times opacity, the primitive's peak)."""
+    H, W = 41, 41
+    cam = synth.camera(synth.look_at((0.0, -5.0, 0.0)), H, W, 50.0)
+    q = np.zeros((1, synth.P3D_SH), np.float32)
+    q[0, :18] = [0, 0, 0, 0.05, 0.05, 0.05, 1, 0, 0, 0, 0, 0, 0, 0, 0.5, 0, 0, 0]
+    q[0, 15:18] = 0.0
+    q[0, 20:23] = 0.3  # band 1, m = -1
+    C = oracle.render3d(q, cam, H, W, OPTS_SH3, truncated=False)[0]
+    y1 = oracle.sh_basis(np.array([[0.0, 1.0, 0.0]]))[0, 1]
+    # the centre pixel sits on mu' (q = 0, W' = 1): alpha = opacity 0.5, C = 0.5 c
+    np.testing.assert_allclose(C[20, 20], 0.5 * (0.5 + y1 * np.float32(0.3)), rtol=1e-9)
+
+
+def test_sh_grad_matches_central_differences():
+    """Gradient of the SH colour (coefficients, and the centre through the view direction) against
+    central differences of the binary64 forward."""
+    H, W = 26, 30
+    p = synth.scene3d_sh(5, 53, scale_range=(0.03, 0.08), max_freq=6.0, extent=0.3)
+    p[:, 14] = np.linspace(0.3, 0.8, 5)
+    cam = synth.camera(synth.look_at((0.4, -2.2, 0.9)), H, W, 50.0)
+    g = synth.upstream_grad(H, W, 54)
+    an = oracle.grad3d(p, cam, H, W, g, OPTS_SH3, truncated=False)
+    cols = [0, 1, 2, 15, 16, 17] + list(range(20, 65))
+    floor = [0.3] * synth.P3D_SH
+
+    def L(pp):
+        return float((oracle.render3d(pp, cam, H, W, OPTS_SH3, truncated=False)[0] * g).sum())
+
+    fd = _central_fd(L, p, range(len(p)), cols, floor=floor)
+    err = np.abs(an[:, cols] - fd)
+    tol = 1e-5 * np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max(axis=0, keepdims=True))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-300)).max()
+
+
+# ---------------------------------------------------------------------------------------------
 # binary32 footprint rule and tile lists (the 3DGS-style pipeline the paper follows, Sec. 4.1)
 # ---------------------------------------------------------------------------------------------
 

@@ -19,9 +19,13 @@ AMB_SHARE = 1e-2
 LITERAL = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 1.0], np.float32)  # f' = J W f
 
 
+SH3 = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 0.0, 3.0], np.float32)  # SH colour, degree 3
+
+
 def _opts(w, o):
     return w.make_opts(3, cutoff_sigma=float(o[0]), alpha_min=float(o[1]), alpha_max=float(o[2]), T_min=float(o[3]),
-                       dilation=float(o[4]), bg=o[5:8], freq_proj_mode=int(o[8]) if len(o) > 8 else 0)
+                       dilation=float(o[4]), bg=o[5:8], freq_proj_mode=int(o[8]) if len(o) > 8 else 0,
+                       sh_degree=int(o[9]) if len(o) > 9 else 0)
 
 
 def _gpu(w, torch, p, cam, H, W, o):
@@ -125,6 +129,36 @@ def test_literal_frequency_projection_matches_oracle(N, H, W, seed):
     ref, gabs = oracle.grad3d(p, cam, H, W, g, LITERAL, with_abs=True)
     ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
     assert ok, (worst, idx)
+
+
+@pytest.mark.parametrize("N,H,W,seed,degree", [(600, 72, 88, 37, 3), (1500, 100, 100, 38, 3), (800, 64, 96, 39, 1)])
+def test_spherical_harmonic_colour_matches_oracle(N, H, W, seed, degree):
+    """sh_degree > 0 ([N,68] records): the view-dependent colour, forward and gradients of every
+    coefficient (zero above the degree) and of the centre through the view direction."""
+    torch = torch_cuda()
+    w = lib_ready()
+    o = SH3.copy()
+    o[9] = degree
+    p = synth.scene3d_sh(N, seed, degree=3)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    params, st, img = _gpu(w, torch, p, cam, H, W, o)
+    C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, o)
+    amb_img = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
+    assert amb_img.mean() < AMB_SHARE
+    err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
+    err[amb_img] = 0
+    assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    g = synth.upstream_grad(H, W, seed + 5)
+    g[amb_bits != 0] = 0.0
+    grad = w.backward(st, params, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert grad.shape == (N, synth.P3D_SH)
+    ref, gabs = oracle.grad3d(p, cam, H, W, g, o, with_abs=True)
+    cols = list(range(18)) + list(range(20, 20 + 3 * ((degree + 1) ** 2 - 1)))
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=cols)
+    assert ok, (worst, idx)
+    unused = [c for c in range(synth.P3D_SH) if c not in cols]
+    assert np.all(grad.cpu().numpy()[:, unused] == 0)
 
 
 def test_autograd_function_and_culling():
