@@ -166,6 +166,26 @@ def scene3d_sh(n: int, seed: int, degree: int = 3, sh_sigma: float = 0.15, **kw)
     return p
 
 
+# layer shapes (out, in) of the deformation network (positional encoding of the centre with 10
+# frequencies and of time with 6, 76 inputs zero-padded to 80; 8 layers of 256 with the encoding
+# concatenated again at layer 5; 13 outputs)
+MLP_SHAPES = [(256, 80)] + [(256, 256)] * 4 + [(256, 336)] + [(256, 256)] * 2 + [(13, 256)]
+
+
+def deform_mlp_theta(seed: int, head_scale: float = 0.1) -> np.ndarray:
+    """Packed float32 parameters of the deformation network: per layer W (out x in, row-major)
+    then b, drawn U(-1/sqrt(in), 1/sqrt(in)) (the usual default of a linear layer); the output
+    layer scaled by head_scale so that the deformations start small."""
+    rng = _rng(seed)
+    parts = []
+    for li, (o, i) in enumerate(MLP_SHAPES):
+        lim = 1.0 / math.sqrt(i)
+        sc = head_scale if li == len(MLP_SHAPES) - 1 else 1.0
+        parts.append(rng.uniform(-lim, lim, o * i) * sc)
+        parts.append(rng.uniform(-lim, lim, o) * sc)
+    return np.concatenate(parts).astype(np.float32)
+
+
 def scene6d(n: int, seed: int, rate_sigma=0.05, **kw) -> np.ndarray:
     """6D primitives: a 3D scene plus per-primitive linear rates over a unit time span for the
     centre (v), frequency (df), phase (dphi) and log-scale (dlog_s), each N(0, rate_sigma)."""
