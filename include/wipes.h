@@ -235,6 +235,25 @@ const char* wipes_last_error(void);
  * latched error is reported once. */
 wipes_status wipes_sync_status(wipes_ctx* ctx, void* stream);
 
+/* 6D deformation network F_theta (Sec. 4.3): (dx, df, dSigma) = F_theta(gamma(x), gamma(t)).  The paper
+ * gives only an MLP with positional encoding gamma; the network here: gamma(p) = (p, sin(2^k p),
+ * cos(2^k p)) with k < 10 for the centre and k < 6 for t (76 inputs, padded to 80), 8 ReLU layers of
+ * width 256, layer 5 taking (gamma, h_4), and 13 outputs (dx, dq, dlog s, df).  The deformed record
+ * is mu + dx, q + dq, s exp(dlog s), f + df, the other fields unchanged.  theta: packed float32
+ * parameters, per layer (out x in: 256x80, 4 x 256x256, 256x336, 2 x 256x256, 13x256) W row-major
+ * then b; wipes_deform_mlp_param_count() floats.  The products run in bfloat16 with fp32
+ * accumulation (cuBLASLt; the hidden layers' biases are applied in bfloat16, the output layer's in
+ * fp32); activations are kept in `st` for the backward. */
+int64_t wipes_deform_mlp_param_count(void);
+/* params3: canonical [N,20] records; params_out: deformed [N,20] records (device, 16-byte aligned). */
+wipes_status wipes_deform_mlp(wipes_ctx* ctx, wipes_state* st, const float* params3, int64_t N, float t,
+                              const float* theta, float* params_out, void* stream);
+/* From dL/d(deformed records) [N,20] of the last wipes_deform_mlp on `st` (same params3): dL/dtheta
+ * [param_count] and dL/dparams3 [N,20], accumulated into the outputs when accumulate != 0, else
+ * overwritten. */
+wipes_status wipes_deform_mlp_backward(wipes_ctx* ctx, wipes_state* st, const float* params3, const float* dL_dout,
+                                       float* dL_dtheta, float* dL_dparams3, int accumulate, void* stream);
+
 /* Diagnostic: run one radix-sort pass on scratch data in which the tile before the block's tile
  * never publishes its counts, so that the block's bounded look-back runs out (after well under a
  * second).  Returns WIPES_ERR_TIMEOUT when the wait ran out and was reported, as it should; the

@@ -14,8 +14,8 @@ The deformed 3D record: mu + dx, q + dq, s * exp(dlog s), f + df; phase, opacity
 
 Precision.  The device path runs the products in bfloat16 with fp32 accumulation.  ``bf16=True``
 reproduces its roundings: every matrix-product operand (encoding, weights, hidden activations,
-upstream gradients) is rounded to bfloat16 where the device rounds it, and everything else is
-binary64.  ``bf16=False`` is the exact binary64 network, against which central differences pin
+upstream gradients) and the hidden layers' biases are rounded to bfloat16 where the device rounds
+them, and everything else is binary64.  ``bf16=False`` is the exact binary64 network, against which central differences pin
 the gradient.  theta is the packed float32 parameter vector: for each layer W (out x in,
 row-major) then b (out).
 """
@@ -32,6 +32,9 @@ SKIP = 5  # layer 5 takes (gamma, h_4)
 OUT = 13
 # (out, in) of every linear layer, in order
 SHAPES = [(WIDTH, IN_PAD)] + [(WIDTH, WIDTH)] * 4 + [(WIDTH, IN_PAD + WIDTH)] + [(WIDTH, WIDTH)] * 2 + [(OUT, WIDTH)]
+# relative margin of the ReLU decisions: fp32 accumulation of K <= 336 products rounds by a few
+# 2^-24 of the sum of |terms| in practice (the worst case is K 2^-24 = 2e-5)
+AMB_REL = 4e-6
 
 
 def theta_size() -> int:
@@ -85,17 +88,21 @@ def forward(mu, t, theta, bf16_ops=True):
     layers = unpack(theta)
     g = R(encode(mu, t))
     hs, x = [], g
+    amb = np.zeros(g.shape[0], bool)
     for l in range(N_HIDDEN):
         W, b = layers[l]
         if l == SKIP:
             x = np.concatenate([g, hs[4]], axis=1)
-        z = x @ R(W).T + b
+        z = x @ R(W).T + R(b)
+        # a pre-activation this close to 0 (relative to the magnitude of its terms) can take the
+        # ReLU either way under a different summation order
+        amb |= (np.abs(z) <= AMB_REL * (np.abs(x) @ np.abs(R(W)).T + np.abs(R(b)))).any(axis=1)
         h = R(np.maximum(z, 0.0))
         hs.append(h)
         x = h
     W, b = layers[N_HIDDEN]
     d = x @ R(W).T + b
-    return d, {"g": g, "hs": hs, "layers": layers, "R": R}
+    return d, {"g": g, "hs": hs, "layers": layers, "R": R, "amb_rows": amb}
 
 
 def apply(params3, d):
@@ -123,13 +130,30 @@ def apply_backward(params3, d, g_out):
     return gd, gp
 
 
-def backward(mu, cache, gd, theta_like=None):
-    """(dL/dtheta packed [P], dL/dmu [N,3]) of L given dL/dd [N,13], for the cache of forward()."""
+def _max_row_term(a, x, chunk=64):
+    """max over rows r of |a[r, u]| |x[r, i]| for every (u, i): the largest single-row term."""
+    out = np.zeros((a.shape[1], x.shape[1]))
+    aa, xx = np.abs(a), np.abs(x)
+    for r0 in range(0, a.shape[0], chunk):
+        out = np.maximum(out, (aa[r0:r0 + chunk, :, None] * xx[r0:r0 + chunk, None, :]).max(axis=0))
+    return out
+
+
+def backward(mu, cache, gd, with_abs=False):
+    """(dL/dtheta packed [P], dL/dmu [N,3]) of L given dL/dd [N,13], for the cache of forward().
+    with_abs: also the packed sums of |products| (|dz|^T |x| and sum |dz|), the scale of each entry,
+    and the packed largest single-row term (max over rows of |dh| |x| and |dh|, dh taken before the
+    ReLU mask): the most one row can change an entry when its ReLU decision goes the other way."""
     R, layers, hs, g = cache["R"], cache["layers"], cache["hs"], cache["g"]
     grads = [None] * len(layers)
+    absg = [None] * len(layers)
+    maxg = [None] * len(layers)
     dy = R(gd)
     W, _ = layers[N_HIDDEN]
     grads[N_HIDDEN] = (dy.T @ hs[-1], dy.sum(0))
+    absg[N_HIDDEN] = (np.abs(dy).T @ np.abs(hs[-1]), np.abs(dy).sum(0))
+    if with_abs:
+        maxg[N_HIDDEN] = (_max_row_term(dy, hs[-1]), np.abs(dy).max(0))
     dh = R(dy @ R(W))
     dg = np.zeros_like(g)
     for l in range(N_HIDDEN - 1, -1, -1):
@@ -137,6 +161,9 @@ def backward(mu, cache, gd, theta_like=None):
         dz = np.where(hs[l] > 0.0, dh, 0.0)
         x = np.concatenate([g, hs[4]], axis=1) if l == SKIP else (g if l == 0 else hs[l - 1])
         grads[l] = (dz.T @ x, dz.sum(0))
+        absg[l] = (np.abs(dz).T @ np.abs(x), np.abs(dz).sum(0))
+        if with_abs:
+            maxg[l] = (_max_row_term(dh, x), np.abs(dh).max(0))
         dx = R(dz @ R(W))
         if l == SKIP:
             dg += dx[:, :IN_PAD]
@@ -153,6 +180,9 @@ def backward(mu, cache, gd, theta_like=None):
         dmu += dg[:, 3 + 6 * k: 6 + 6 * k] * f * np.cos(f * m)
         dmu -= dg[:, 6 + 6 * k: 9 + 6 * k] * f * np.sin(f * m)
     packed = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    if with_abs:
+        pack = lambda parts: np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in parts])  # noqa: E731
+        return packed, dmu, pack(absg), pack(maxg)
     return packed, dmu
 
 

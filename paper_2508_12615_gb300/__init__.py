@@ -4,8 +4,10 @@
 Importing the package does not load the CUDA library; the first call does, and fails loudly if
 ``libwipes.so`` has not been built (``paper_2508_12615_gb300.build.build()``).
 """
-from .render import (Context, Deform6D, Render2D, Render3D, State, backward, deform6d, forward2d, forward3d,
-                     l2_loss, make_opts, render2d, render3d)
+from .render import (Context, Deform6D, DeformMLP, Render2D, Render3D, State, backward, deform6d, deform_field,
+                     deform_mlp, deform_mlp_backward, deform_mlp_param_count, forward2d, forward3d, l2_loss,
+                     make_opts, render2d, render3d)
 
-__all__ = ["Context", "State", "Render2D", "Render3D", "Deform6D", "render2d", "render3d", "deform6d", "forward2d",
-           "forward3d", "backward", "l2_loss", "make_opts"]
+__all__ = ["Context", "State", "Render2D", "Render3D", "Deform6D", "DeformMLP", "render2d", "render3d", "deform6d",
+           "deform_field", "deform_mlp", "deform_mlp_backward", "deform_mlp_param_count", "forward2d", "forward3d",
+           "backward", "l2_loss", "make_opts"]

@@ -65,6 +65,9 @@ _SIGNATURES = {
     "wipes_last_error": (c_char_p, []),
     "wipes_sync_status": (c_int, [_P, _P]),
     "wipes_selftest_sort_timeout": (c_int, [_P, _P]),
+    "wipes_deform_mlp_param_count": (ctypes.c_int64, []),
+    "wipes_deform_mlp": (c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "wipes_deform_mlp_backward": (c_int, [_P, _P, _P, _P, _P, _P, c_int, _P]),
     "wipes_state_count_pairs": (c_int, [_P, _P, _P, _P, _P]),
     "wipes_set_timing": (c_int, [_P, c_int]),
     "wipes_get_timing": (c_int, [_P, _P, _P, c_int]),

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libwipes.so")
 
-SOURCES = ["footprint.cu", "binning.cu", "raster2d.cu", "raster3d.cu", "loss.cu", "loss_noalloc.cu", "batch.cu", "api.cu"]
+SOURCES = ["footprint.cu", "binning.cu", "raster2d.cu", "raster3d.cu", "loss.cu", "loss_noalloc.cu", "batch.cu", "mlp.cu",
+           "api.cu"]
 # The footprint kernels take every integer decision (tile coverage, cutoff, depth order) from
 # binary32 values that must be reproducible operation by operation: no fused multiply-add there.
 PER_FILE_FLAGS = {"footprint.cu": ["-fmad=false"]}
@@ -63,7 +64,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB_PATH + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
+    # the deformation network's products run through cuBLASLt from the same toolkit
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-L", cuda_lib, "-lcublasLt",
+           "-Xlinker", "-rpath," + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

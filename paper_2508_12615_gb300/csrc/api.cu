@@ -9,6 +9,8 @@
 #include <cstring>
 #include <string>
 
+#include <mutex>
+
 #include "common.cuh"
 
 using namespace wipes;
@@ -123,6 +125,8 @@ struct wipes_ctx {
     unsigned long long* d_counters = nullptr;  // pair counters
     unsigned int* d_batch_counters = nullptr;  // work counters of in-flight batch launches (a ring)
     unsigned int batch_slot = 0;
+    MlpLt* mlp = nullptr;  // cuBLASLt state of the deformation network, created on first use
+    std::mutex mlp_mu;
     // stage timing
     bool timing = false;
     struct Bracket {
@@ -183,10 +187,13 @@ struct wipes_state {
     int sorted = 0;  // which ping-pong buffer holds the sorted lists
     DevBuf rec, rect, counts, offsets, dkeys[2], dvals[2], block_sums, total, keys[2], vals[2], inst_prim, hist, ranges;
     DevBuf sprim, order, T_final, last, partial, grad_img;
+    DevBuf mlp_act, mlp_scratch, mlp_d, mlp_theta16;  // deformation network: activations kept for the backward
+    int64_t mlp_N = -1;                               // primitives of the last network forward (-1: none)
 
-    DevBuf* all[23] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
+    DevBuf* all[27] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
                        &block_sums, &total, &keys[0], &keys[1],   &vals[0],   &vals[1],   &inst_prim, &hist,
-                       &ranges,  &sprim,   &order,     &T_final, &last,     &partial,  &grad_img};
+                       &ranges,  &sprim,   &order,     &T_final, &last,     &partial,  &grad_img, &mlp_act,
+                       &mlp_scratch, &mlp_d, &mlp_theta16};
     size_t reserved() const {
         size_t s = 0;
         for (DevBuf* b : all) s += b->cap;
@@ -396,6 +403,7 @@ wipes_status wipes_destroy(wipes_ctx* ctx) {
     cudaFree(ctx->d_loss_partials);
     cudaFree(ctx->d_counters);
     cudaFree(ctx->d_error);
+    mlp_lt_destroy(ctx->mlp);
     cudaFree(ctx->d_batch_counters);
     delete ctx;
     return WIPES_OK;
@@ -747,6 +755,59 @@ wipes_status wipes_sync_status(wipes_ctx* ctx, void* stream) {
     WIPES_CUDA(cudaMemcpyAsync(ctx->h_total + 1, ctx->d_error, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     WIPES_CUDA(cudaStreamSynchronize(s));
     return take_device_error(ctx, s);
+}
+
+int64_t wipes_deform_mlp_param_count(void) { return mlp_param_count(); }
+
+wipes_status wipes_deform_mlp(wipes_ctx* ctx, wipes_state* st, const float* params3, int64_t N, float t,
+                              const float* theta, float* params_out, void* stream) {
+    if (!ctx || !st || !theta || (N > 0 && (!params3 || !params_out))) return fail(WIPES_ERR_INVALID, "null argument");
+    if (N < 0 || N > (int64_t)INT32_MAX) return fail(WIPES_ERR_INVALID, "N out of range");
+    if (!std::isfinite(t)) return fail(WIPES_ERR_INVALID, "t must be finite");
+    if (((uintptr_t)params3 & 15) || ((uintptr_t)theta & 15) || ((uintptr_t)params_out & 15))
+        return fail(WIPES_ERR_INVALID, "params3, theta and params_out must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mlp_mu);
+        if (!ctx->mlp) {
+            std::string err;
+            ctx->mlp = mlp_lt_create(&err);
+            if (!ctx->mlp) return fail(WIPES_ERR_CUDA, err);
+        }
+    }
+    const MlpSizes z = mlp_sizes(std::max<int64_t>(N, 1));
+    WIPES_TRY(ensure(st->mlp_act, z.act));
+    WIPES_TRY(ensure(st->mlp_d, z.out));
+    WIPES_TRY(ensure(st->mlp_theta16, z.theta16));
+    st->mlp_N = -1;
+    const std::string e = mlp_forward(*ctx->mlp, params3, N, t, theta, st->mlp_theta16.p, st->mlp_act.p,
+                                      st->mlp_d.as<float>(), params_out, s);
+    if (!e.empty()) return fail(WIPES_ERR_CUDA, e);
+    WIPES_CUDA(cudaGetLastError());
+    st->mlp_N = N;
+    return WIPES_OK;
+}
+
+wipes_status wipes_deform_mlp_backward(wipes_ctx* ctx, wipes_state* st, const float* params3, const float* dL_dout,
+                                       float* dL_dtheta, float* dL_dparams3, int accumulate, void* stream) {
+    if (!ctx || !st || !dL_dtheta) return fail(WIPES_ERR_INVALID, "null argument");
+    if (st->mlp_N < 0) return fail(WIPES_ERR_INVALID, "state holds no deformation-network forward pass");
+    const int64_t N = st->mlp_N;
+    if (N > 0 && (!params3 || !dL_dout || !dL_dparams3)) return fail(WIPES_ERR_INVALID, "null argument");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const MlpSizes z = mlp_sizes(std::max<int64_t>(N, 1));
+    WIPES_TRY(ensure(st->mlp_scratch, z.scratch));
+    if (N == 0) {
+        if (!accumulate) WIPES_CUDA(cudaMemsetAsync(dL_dtheta, 0, sizeof(float) * (size_t)mlp_param_count(), s));
+        return WIPES_OK;
+    }
+    const std::string e = mlp_backward(*ctx->mlp, params3, N, st->mlp_theta16.p, st->mlp_act.p, st->mlp_d.as<float>(),
+                                       st->mlp_scratch.p, dL_dout, dL_dtheta, dL_dparams3, accumulate, s);
+    if (!e.empty()) return fail(WIPES_ERR_CUDA, e);
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
 }
 
 wipes_status wipes_selftest_sort_timeout(wipes_ctx* ctx, void* stream) {

@@ -1,0 +1,442 @@
+// 6D deformation network (Sec. 4.3): (dx, df, dSigma) = F_theta(gamma(x), gamma(t)) per primitive,
+// and its backward to the network parameters and the canonical records.
+//
+// Network (the paper gives only "an MLP with positional encoding, as Deformable 3D Gaussians"):
+//   gamma(p) = (p, sin(2^k p), cos(2^k p), k < L) per coordinate, L = 10 for the centre, 6 for t:
+//     76 inputs, zero-padded to 80;
+//   8 ReLU layers of width 256; layer 5 takes (gamma, h_4) (skip connection);
+//   13 outputs: dx (3), dq (4), dlog s (3), df (3);
+//   deformed record: mu + dx, q + dq, s exp(dlog s), f + df (phase, opacity, colour kept).
+// Parameters theta: packed float32, per layer W (out x in, row-major) then b (out).
+//
+// The products are dense contractions over 200k-row activation matrices: they run on the tensor
+// cores through cuBLASLt (bfloat16 operands, fp32 accumulation, bias + ReLU fused in the epilogue
+// for the hidden layers, whose biases are used in bfloat16 like their weights).  Activations are kept in bfloat16 for the backward pass.  Layouts: every
+// activation matrix is row-major [N, width]; in cuBLASLt's column-major terms that is a
+// [width, N] matrix, so Y = X W^T + b is  Y^T (out x N) = W (out x in, i.e. column-major in x out
+// read transposed) * X^T (in x N).  The skip input lives in one [N, 336] buffer: columns 0..79 the
+// encoding (written by the encoder), columns 80..335 the output h_4 of layer 4.
+#include <cublasLt.h>
+#include <cuda_bf16.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "common.cuh"
+
+namespace wipes {
+
+namespace {
+
+constexpr int kLx = 10, kLt = 6;
+constexpr int kIn = 3 * (1 + 2 * kLx) + (1 + 2 * kLt);  // 76
+constexpr int kInPad = 80;
+constexpr int kWidth = 256;
+constexpr int kHidden = 8;
+constexpr int kSkipLayer = 5;
+constexpr int kOut = 13;
+constexpr int kOutPad = 16;
+constexpr int kX5 = kInPad + kWidth;  // 336
+
+struct LayerShape {
+    int out, in;
+};
+constexpr LayerShape kShapes[kHidden + 1] = {{kWidth, kInPad}, {kWidth, kWidth}, {kWidth, kWidth}, {kWidth, kWidth},
+                                             {kWidth, kWidth}, {kWidth, kX5},    {kWidth, kWidth}, {kWidth, kWidth},
+                                             {kOut, kWidth}};
+
+int64_t layer_offset(int l) {
+    int64_t k = 0;
+    for (int i = 0; i < l; ++i) k += (int64_t)kShapes[i].out * kShapes[i].in + kShapes[i].out;
+    return k;
+}
+
+// gamma(mu, t) into columns 0..79 of the [N, 336] bf16 buffer; one thread per (row, column).
+__global__ void __launch_bounds__(256) k_mlp_encode(const float* __restrict__ params3, int64_t N, float t,
+                                                    __nv_bfloat16* __restrict__ x5) {
+    pdl_enter();
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * kInPad) return;
+    const int64_t row = idx / kInPad;
+    const int c = (int)(idx - row * kInPad);
+    float v = 0.f;
+    if (c < 3) {
+        v = params3[row * WIPES_P3D + c];
+    } else if (c < 3 + 6 * kLx) {
+        const int k = (c - 3) / 6, r = (c - 3) % 6;
+        const float x = params3[row * WIPES_P3D + (r % 3)] * (float)(1 << k);
+        v = r < 3 ? sinf(x) : cosf(x);
+    } else if (c == 3 + 6 * kLx) {
+        v = t;
+    } else if (c < kIn) {
+        const int k = (c - 4 - 6 * kLx) / 2, r = (c - 4 - 6 * kLx) % 2;
+        const float x = t * (float)(1 << k);
+        v = r == 0 ? sinf(x) : cosf(x);
+    }
+    x5[row * kX5 + c] = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(256) k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 int64_t n) {
+    pdl_enter();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// deformed record from the canonical record and the network outputs d [N, 16] (13 used)
+__global__ void __launch_bounds__(256) k_mlp_apply(const float* __restrict__ params3, int64_t N,
+                                                   const float* __restrict__ d, float* __restrict__ out) {
+    pdl_enter();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float* p = params3 + i * WIPES_P3D;
+    const float* e = d + i * kOutPad;
+    float* o = out + i * WIPES_P3D;
+#pragma unroll
+    for (int k = 0; k < WIPES_P3D; ++k) o[k] = p[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o[k] = p[k] + e[k];
+        o[3 + k] = p[3 + k] * expf(e[7 + k]);
+        o[10 + k] = p[10 + k] + e[10 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[6 + k] = p[6 + k] + e[3 + k];
+}
+
+// dL/dd (bfloat16, the backward's product operand) and the direct part of dL/dparams3; the output
+// bias gradient is the column sum of the rounded dL/dd
+__global__ void __launch_bounds__(256) k_mlp_apply_backward(const float* __restrict__ params3, int64_t N,
+                                                            const float* __restrict__ d,
+                                                            const float* __restrict__ g_out,
+                                                            __nv_bfloat16* __restrict__ gd,
+                                                            float* __restrict__ g_params3, int accumulate,
+                                                            float* __restrict__ db_head) {
+    pdl_enter();
+    __shared__ float s_db[kOutPad];
+    if (threadIdx.x < kOutPad) s_db[threadIdx.x] = 0.f;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        const float* p = params3 + i * WIPES_P3D;
+        const float* e = d + i * kOutPad;
+        const float* g = g_out + i * WIPES_P3D;
+        float gdv[kOutPad];
+#pragma unroll
+        for (int k = 0; k < kOutPad; ++k) gdv[k] = 0.f;
+        float gp[WIPES_P3D];
+#pragma unroll
+        for (int k = 0; k < WIPES_P3D; ++k) gp[k] = g[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float es = expf(e[7 + k]);
+            gdv[k] = g[k];
+            gdv[7 + k] = g[3 + k] * p[3 + k] * es;
+            gdv[10 + k] = g[10 + k];
+            gp[3 + k] = g[3 + k] * es;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gdv[3 + k] = g[6 + k];
+        __nv_bfloat16* gdr = gd + i * kOutPad;
+#pragma unroll
+        for (int k = 0; k < kOutPad; ++k) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(gdv[k]);
+            gdr[k] = b;
+            if (k < kOut) atomicAdd(&s_db[k], __bfloat162float(b));
+        }
+        float* go = g_params3 + i * WIPES_P3D;
+#pragma unroll
+        for (int k = 0; k < WIPES_P3D; ++k) go[k] = accumulate ? go[k] + gp[k] : gp[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kOut) atomicAdd(&db_head[threadIdx.x], s_db[threadIdx.x]);
+}
+
+// dz = dh where h > 0 (ReLU), and the bias gradient (column sums of dz); one thread per column of a
+// 256-wide activation matrix, each block over a run of rows
+constexpr int kReluRows = 64;
+__global__ void __launch_bounds__(kWidth) k_relu_backward(const __nv_bfloat16* __restrict__ dh, int ld_dh,
+                                                          const __nv_bfloat16* __restrict__ h, int ld_h, int64_t N,
+                                                          __nv_bfloat16* __restrict__ dz, float* __restrict__ db) {
+    pdl_enter();
+    const int c = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * kReluRows;
+    const int64_t r1 = min(N, r0 + kReluRows);
+    float s = 0.f;
+    for (int64_t r = r0; r < r1; ++r) {
+        const __nv_bfloat16 v = __bfloat162float(h[r * ld_h + c]) > 0.f ? dh[r * ld_dh + c] : __float2bfloat16_rn(0.f);
+        dz[r * kWidth + c] = v;
+        s += __bfloat162float(v);
+    }
+    atomicAdd(&db[c], s);
+}
+
+// dL/dmu through gamma: d/dx (x, sin(2^k x), cos(2^k x)) = (1, 2^k cos, -2^k sin); the encoding's
+// gradient is the sum of layer 0's (dg0 [N, 80]) and layer 5's (columns 0..79 of dx5 [N, 336])
+__global__ void __launch_bounds__(256) k_mlp_encode_backward(const float* __restrict__ params3, int64_t N,
+                                                             const __nv_bfloat16* __restrict__ dg0,
+                                                             const __nv_bfloat16* __restrict__ dx5,
+                                                             float* __restrict__ g_params3) {
+    pdl_enter();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const __nv_bfloat16* a = dg0 + i * kInPad;
+    const __nv_bfloat16* b = dx5 + i * kX5;
+    float gm[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gm[j] = __bfloat162float(a[j]) + __bfloat162float(b[j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float x = params3[i * WIPES_P3D + j];
+#pragma unroll
+        for (int k = 0; k < kLx; ++k) {
+            const float f = (float)(1 << k);
+            const float gs = __bfloat162float(a[3 + 6 * k + j]) + __bfloat162float(b[3 + 6 * k + j]);
+            const float gc = __bfloat162float(a[6 + 6 * k + j]) + __bfloat162float(b[6 + 6 * k + j]);
+            float sn, cs;
+            sincosf(f * x, &sn, &cs);
+            gm[j] += f * (gs * cs - gc * sn);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g_params3[i * WIPES_P3D + j] += gm[j];
+}
+
+// ---------------------------------------------------------------------------------------------
+// cuBLASLt products (column-major views, see the header comment)
+// ---------------------------------------------------------------------------------------------
+
+#define LT_TRY(x)                                                                                        \
+    do {                                                                                                 \
+        cublasStatus_t st_ = (x);                                                                        \
+        if (st_ != CUBLAS_STATUS_SUCCESS) return std::string("cuBLASLt: " #x " failed with status ") + \
+                                                 std::to_string((int)st_);                               \
+    } while (0)
+
+struct GemmKey {
+    int ta, tb, m, n, k, lda, ldb, ldc, dtype, epi;
+    bool operator<(const GemmKey& o) const {
+        return std::tie(ta, tb, m, n, k, lda, ldb, ldc, dtype, epi) <
+               std::tie(o.ta, o.tb, o.m, o.n, o.k, o.lda, o.ldb, o.ldc, o.dtype, o.epi);
+    }
+};
+
+}  // namespace
+
+struct MlpLt {
+    cublasLtHandle_t h = nullptr;
+    void* ws = nullptr;
+    size_t ws_size = 32u << 20;
+    std::map<GemmKey, cublasLtMatmulHeuristicResult_t> algos;
+    std::mutex mu;
+};
+
+namespace {
+
+// D (m x n, column-major, type dtype) = alpha op(A) op(B) (+ beta D) [+ bias, ReLU]; A, B bfloat16.
+// The bias (when given) has the type of D: bfloat16 for the hidden layers, fp32 for the output layer.
+std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A, int lda, const void* B, int ldb,
+                 void* D, int ldc, cudaDataType_t dtype, float beta, cublasLtEpilogue_t epi, const void* bias,
+                 cudaStream_t stream) {
+    cublasLtMatmulDesc_t desc = nullptr;
+    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
+    LT_TRY(cublasLtMatmulDescCreate(&desc, CUBLAS_COMPUTE_32F, CUDA_R_32F));
+    const cublasOperation_t opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N, opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
+    LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_TRANSA, &opa, sizeof(opa)));
+    LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb)));
+    LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE, &epi, sizeof(epi)));
+    if (bias) LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &bias, sizeof(bias)));
+    LT_TRY(cublasLtMatrixLayoutCreate(&la, CUDA_R_16BF, ta ? k : m, ta ? m : k, lda));
+    LT_TRY(cublasLtMatrixLayoutCreate(&lb, CUDA_R_16BF, tb ? n : k, tb ? k : n, ldb));
+    LT_TRY(cublasLtMatrixLayoutCreate(&lc, dtype, m, n, ldc));
+    const GemmKey key{ta, tb, m, n, k, lda, ldb, ldc, (int)dtype, (int)epi};
+    cublasLtMatmulHeuristicResult_t res{};
+    {
+        std::lock_guard<std::mutex> g(lt.mu);
+        auto it = lt.algos.find(key);
+        if (it != lt.algos.end()) {
+            res = it->second;
+        } else {
+            cublasLtMatmulPreference_t pref = nullptr;
+            LT_TRY(cublasLtMatmulPreferenceCreate(&pref));
+            LT_TRY(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &lt.ws_size,
+                                                        sizeof(lt.ws_size)));
+            int found = 0;
+            const cublasStatus_t hs = cublasLtMatmulAlgoGetHeuristic(lt.h, desc, la, lb, lc, lc, pref, 1, &res, &found);
+            cublasLtMatmulPreferenceDestroy(pref);
+            if (hs != CUBLAS_STATUS_SUCCESS || found == 0)
+                return "cuBLASLt: no algorithm for the product (m=" + std::to_string(m) + ", n=" + std::to_string(n) +
+                       ", k=" + std::to_string(k) + ")";
+            lt.algos[key] = res;
+        }
+    }
+    const float alpha = 1.f;
+    const cublasStatus_t st = cublasLtMatmul(lt.h, desc, &alpha, A, la, B, lb, &beta, D, lc, D, lc, &res.algo, lt.ws,
+                                             lt.ws_size, stream);
+    cublasLtMatrixLayoutDestroy(la);
+    cublasLtMatrixLayoutDestroy(lb);
+    cublasLtMatrixLayoutDestroy(lc);
+    cublasLtMatmulDescDestroy(desc);
+    if (st != CUBLAS_STATUS_SUCCESS) return "cuBLASLt: matmul failed with status " + std::to_string((int)st);
+    count_launches(1);
+    return "";
+}
+
+// forward product of layer l: Y [N, out] (row-major, ldy) = X [N, in] (ldx) W^T + b, ReLU for hidden
+// layers (bias b in bfloat16 for them, fp32 for the output layer)
+std::string layer_forward(MlpLt& lt, int l, const __nv_bfloat16* w, const void* b, const void* x, int ldx, void* y,
+                          int ldy, int64_t N, cudaStream_t s) {
+    const LayerShape sh = kShapes[l];
+    const bool head = l == kHidden;
+    return gemm(lt, true, false, sh.out, (int)N, sh.in, w, sh.in, x, ldx, y, ldy, head ? CUDA_R_32F : CUDA_R_16BF,
+                0.f, head ? CUBLASLT_EPILOGUE_BIAS : CUBLASLT_EPILOGUE_RELU_BIAS, b, s);
+}
+
+}  // namespace
+
+MlpLt* mlp_lt_create(std::string* err) {
+    MlpLt* lt = new MlpLt();
+    if (cublasLtCreate(&lt->h) != CUBLAS_STATUS_SUCCESS) {
+        *err = "cublasLtCreate failed";
+        delete lt;
+        return nullptr;
+    }
+    if (cudaMalloc(&lt->ws, lt->ws_size) != cudaSuccess) {
+        *err = "cuBLASLt workspace allocation failed";
+        cublasLtDestroy(lt->h);
+        delete lt;
+        return nullptr;
+    }
+    return lt;
+}
+
+void mlp_lt_destroy(MlpLt* lt) {
+    if (!lt) return;
+    cudaFree(lt->ws);
+    cublasLtDestroy(lt->h);
+    delete lt;
+}
+
+int64_t mlp_param_count() { return layer_offset(kHidden + 1); }
+
+MlpSizes mlp_sizes(int64_t N) {
+    MlpSizes z;
+    z.act = (size_t)N * (kX5 + 7 * kWidth) * sizeof(__nv_bfloat16);
+    z.scratch = (size_t)N * (3 * kWidth + kX5 + kInPad + kOutPad) * sizeof(__nv_bfloat16);
+    z.out = (size_t)N * kOutPad * sizeof(float);
+    z.theta16 = (size_t)mlp_param_count() * sizeof(__nv_bfloat16);
+    return z;
+}
+
+namespace {
+// activation buffer: x5 [N, 336] then h0..h3, h5..h7 [N, 256] each
+__nv_bfloat16* act_x5(void* act) { return static_cast<__nv_bfloat16*>(act); }
+__nv_bfloat16* act_h(void* act, int64_t N, int l) {
+    const int slot = l < 4 ? l : l - 1;  // h0..h3 -> 0..3, h5..h7 -> 4..6 (h4 lives in x5)
+    return act_x5(act) + (size_t)N * kX5 + (size_t)slot * N * kWidth;
+}
+}  // namespace
+
+std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, const float* theta, void* theta16_buf,
+                        void* act, float* d, float* params_out, cudaStream_t s) {
+    if (N == 0) return "";
+    __nv_bfloat16* w16 = static_cast<__nv_bfloat16*>(theta16_buf);
+    const int64_t P = mlp_param_count();
+    launch_pdl(k_to_bf16, (unsigned)std::min<int64_t>(ceil_div(P, 256), 1024), 256, 0, s, theta, w16, P);
+    count_launches(1);
+    __nv_bfloat16* x5 = act_x5(act);
+    launch_pdl(k_mlp_encode, ceil_div(N * kInPad, 256), 256, 0, s, params3, N, t, x5);
+    count_launches(1);
+    for (int l = 0; l <= kHidden; ++l) {
+        // input: the encoding (layer 0, the first 80 columns of x5), (gamma, h4) (layer 5, all of
+        // x5), else the previous layer's output; layer 4 writes h4 into columns 80.. of x5
+        const void* x = (l == 0 || l == kSkipLayer) ? (const void*)x5 : (const void*)act_h(act, N, l - 1);
+        const int ldx = (l == 0 || l == kSkipLayer) ? kX5 : kWidth;
+        void* y = l == kHidden ? (void*)d : (l == 4 ? (void*)(x5 + kInPad) : (void*)act_h(act, N, l));
+        const int ldy = l == kHidden ? kOutPad : (l == 4 ? kX5 : kWidth);
+        const int64_t boff = layer_offset(l) + (int64_t)kShapes[l].out * kShapes[l].in;
+        const void* bias = l == kHidden ? (const void*)(theta + boff) : (const void*)(w16 + boff);
+        const std::string e = layer_forward(lt, l, w16 + layer_offset(l), bias, x, ldx, y, ldy, N, s);
+        if (!e.empty()) return e;
+    }
+    launch_pdl(k_mlp_apply, ceil_div(N, 256), 256, 0, s, params3, N, (const float*)d, params_out);
+    count_launches(1);
+    return "";
+}
+
+std::string mlp_backward(MlpLt& lt, const float* params3, int64_t N, const void* theta16_buf, const void* act,
+                         const float* d, void* scratch, const float* g_out, float* g_theta, float* g_params3,
+                         int accumulate, cudaStream_t s) {
+    if (N == 0) return "";
+    const __nv_bfloat16* w16 = static_cast<const __nv_bfloat16*>(theta16_buf);
+    const __nv_bfloat16* x5 = static_cast<const __nv_bfloat16*>(act);
+    void* actm = const_cast<void*>(act);
+    // scratch: dh0, dh1 (ping-pong), dz [N, 256]; dx5 [N, 336]; dg0 [N, 80]; gd [N, 16]
+    __nv_bfloat16* dh[2] = {static_cast<__nv_bfloat16*>(scratch), static_cast<__nv_bfloat16*>(scratch) + (size_t)N * kWidth};
+    __nv_bfloat16* dz = dh[1] + (size_t)N * kWidth;
+    __nv_bfloat16* dx5 = dz + (size_t)N * kWidth;
+    __nv_bfloat16* dg0 = dx5 + (size_t)N * kX5;
+    __nv_bfloat16* gd = dg0 + (size_t)N * kInPad;
+    const float beta = accumulate ? 1.f : 0.f;
+    if (!accumulate) cudaMemsetAsync(g_theta, 0, sizeof(float) * (size_t)mlp_param_count(), s);
+    float* db_head = g_theta + layer_offset(kHidden) + (int64_t)kOut * kWidth;
+    launch_pdl(k_mlp_apply_backward, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3, accumulate,
+               db_head);
+    count_launches(1);
+    std::string e;
+    // head: dW_8 += gd^T h7, dh7 = gd W_8
+    {
+        const int l = kHidden;
+        e = gemm(lt, false, true, kWidth, kOut, (int)N, act_h(actm, N, 7), kWidth, gd, kOutPad,
+                 g_theta + layer_offset(l), kWidth, CUDA_R_32F, 1.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        if (!e.empty()) return e;
+        e = gemm(lt, false, false, kWidth, (int)N, kOut, w16 + layer_offset(l), kWidth, gd, kOutPad, dh[0], kWidth,
+                 CUDA_R_16BF, 0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        if (!e.empty()) return e;
+    }
+    // dh for the current layer: cur (ld) ; for layer 4 it is columns 80.. of dx5
+    const __nv_bfloat16* cur = dh[0];
+    int ld_cur = kWidth;
+    int ping = 1;
+    for (int l = kHidden - 1; l >= 0; --l) {
+        const LayerShape sh = kShapes[l];
+        const __nv_bfloat16* hl = l == 4 ? x5 + kInPad : act_h(actm, N, l);
+        const int ld_h = l == 4 ? kX5 : kWidth;
+        float* gW = g_theta + layer_offset(l);
+        float* gb = gW + (int64_t)sh.out * sh.in;
+        launch_pdl(k_relu_backward, ceil_div(N, kReluRows), kWidth, 0, s, cur, ld_cur, hl, ld_h, N, dz, gb);
+        count_launches(1);
+        // dW_l += dz^T x_l  (column-major: [in, out] = x^T(in x N) dz(N x out))
+        const void* xin = (l == 0 || l == kSkipLayer) ? (const void*)x5 : (const void*)act_h(actm, N, l - 1);
+        const int ldx = (l == 0 || l == kSkipLayer) ? kX5 : kWidth;
+        e = gemm(lt, false, true, sh.in, sh.out, (int)N, xin, ldx, dz, kWidth, gW, sh.in, CUDA_R_32F, 1.f,
+                 CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        if (!e.empty()) return e;
+        // dx_l = dz W_l  (column-major: [in, N] = W^T... W row-major [out, in] is column-major [in, out])
+        void* dxl;
+        int ld_dx;
+        if (l == kSkipLayer) { dxl = dx5; ld_dx = kX5; }
+        else if (l == 0) { dxl = dg0; ld_dx = kInPad; }
+        else { dxl = dh[ping]; ld_dx = kWidth; }
+        e = gemm(lt, false, false, sh.in, (int)N, sh.out, w16 + layer_offset(l), sh.in, dz, kWidth, dxl, ld_dx,
+                 CUDA_R_16BF, 0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        if (!e.empty()) return e;
+        if (l == kSkipLayer) {
+            cur = dx5 + kInPad;
+            ld_cur = kX5;
+        } else if (l > 0) {
+            cur = dh[ping];
+            ld_cur = kWidth;
+            ping ^= 1;
+        }
+    }
+    (void)beta;
+    launch_pdl(k_mlp_encode_backward, ceil_div(N, 256), 256, 0, s, params3, N, (const __nv_bfloat16*)dg0,
+               (const __nv_bfloat16*)dx5, g_params3);
+    count_launches(1);
+    return "";
+}
+
+}  // namespace wipes

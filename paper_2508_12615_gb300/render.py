@@ -252,6 +252,60 @@ class Deform6D(torch.autograd.Function):
         return g6, None
 
 
+def deform_mlp_param_count() -> int:
+    """Number of float32 parameters of the 6D deformation network."""
+    return int(_abi.lib().wipes_deform_mlp_param_count())
+
+
+def deform_mlp(params3: torch.Tensor, t: float, theta: torch.Tensor, state: State | None = None,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Deformed [N,20] records at time t from canonical ones through the network with parameters
+    theta (no autograd); the activations stay in ``state`` for deform_mlp_backward."""
+    params3 = _check(params3, P3D, "params3")
+    theta = theta.contiguous()
+    if theta.dtype != torch.float32 or theta.numel() != deform_mlp_param_count():
+        raise ValueError("theta must be float32 with deform_mlp_param_count() entries")
+    ctx = Context.get(params3.device)
+    state = state or ctx.acquire_state()
+    if out is None:
+        out = torch.empty_like(params3)
+    _abi.call("wipes_deform_mlp", ctx.handle, state.handle, _ptr(params3), params3.shape[0], float(t), _ptr(theta),
+              _ptr(out), _stream(params3.device))
+    return out
+
+
+def deform_mlp_backward(state: State, params3: torch.Tensor, grad_out: torch.Tensor,
+                        grad_theta: torch.Tensor | None = None, grad_params3: torch.Tensor | None = None,
+                        accumulate: bool = False):
+    """(dL/dtheta, dL/dparams3) of the last deform_mlp on ``state`` given dL/d(deformed records)."""
+    grad_out = grad_out.contiguous()
+    dev = params3.device
+    if grad_theta is None:
+        grad_theta = torch.zeros(deform_mlp_param_count(), dtype=torch.float32, device=dev)
+    if grad_params3 is None:
+        grad_params3 = torch.zeros_like(params3)
+    _abi.call("wipes_deform_mlp_backward", state.ctx.handle, state.handle, _ptr(params3), _ptr(grad_out),
+              _ptr(grad_theta), _ptr(grad_params3), int(accumulate), _stream(dev))
+    return grad_theta, grad_params3
+
+
+class DeformMLP(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, params3, theta, t):
+        lease = _Lease(Context.get(params3.device))
+        out = deform_mlp(params3.contiguous(), t, theta, lease.state)
+        ctx.lease = lease
+        ctx.save_for_backward(params3)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        (params3,) = ctx.saved_tensors
+        g_theta, g_params = deform_mlp_backward(ctx.lease.state, params3.contiguous(), grad)
+        ctx.lease.release()
+        return g_params, g_theta, None
+
+
 def render2d(params: torch.Tensor, H: int, W: int, opts: _abi.Opts | None = None) -> torch.Tensor:
     """Differentiable 2D render: image [H,W,3] from [N,16] wavelet records."""
     return Render2D.apply(params, H, W, opts)
@@ -260,6 +314,11 @@ def render2d(params: torch.Tensor, H: int, W: int, opts: _abi.Opts | None = None
 def render3d(params: torch.Tensor, camera, H: int, W: int, opts: _abi.Opts | None = None) -> torch.Tensor:
     """Differentiable 3D render: image [H,W,3] from [N,20] wavelet records seen by ``camera``."""
     return Render3D.apply(params, camera, H, W, opts)
+
+
+def deform_field(params3: torch.Tensor, theta: torch.Tensor, t: float) -> torch.Tensor:
+    """Differentiable 6D deformation by the network: [N,20] canonical records at time t -> [N,20]."""
+    return DeformMLP.apply(params3, theta, t)
 
 
 def deform6d(params6: torch.Tensor, t: float) -> torch.Tensor:
