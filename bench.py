@@ -48,11 +48,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["2d", "2dchol", "5d", "5dsh", "6d"], default="2d",
+    ap.add_argument("--workload", choices=["2d", "2dchol", "5d", "5dsh", "6d", "6dmlp"], default="2d",
                     help="2d: the 768x512 / 70k image-fitting workload (default, the headline); 2dchol: the "
                          "same with the Cholesky covariance record; 5d: 800x800 / 300k static scene; 5dsh: the "
                          "same with degree-3 spherical-harmonic colour; 6d: 1352x1014 / 200k dynamic scene, 4 "
-                         "samples per step")
+                         "samples per step (linear time model); 6dmlp: the same scene deformed by the network")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=10.0, help="length of the serving request trace")
@@ -261,8 +261,15 @@ class Workload:
         else:
             c = synth.CFG3_6D
             p, cams, times = synth.cfg3_inputs()
+            if kind == "6dmlp":  # canonical records and the deformation network's parameters
+                p = np.ascontiguousarray(p[:, :20])
+                self.theta = torch.from_numpy(synth.deform_mlp_theta(c.seed + 400)).to(dev)
+                self.gtheta = torch.zeros_like(self.theta)
+                self.st_mlp = w.State(ctx)
             target = synth.target_noise_edges(c.H, c.W, c.seed + 200)
             self.name, self.H, self.W, self.seed = "6d_dynamic_1352x1014_n200000_batch4", c.H, c.W, c.seed
+            if kind == "6dmlp":
+                self.name = "6d_dynamic_mlp_1352x1014_n200000_batch4"
             self.cams, self.times = cams, times
             rng = np.random.default_rng(c.seed + 300)
             self.samples = [(int(rng.integers(len(cams))), float(times[rng.integers(len(times))])) for _ in range(64)]
@@ -274,10 +281,10 @@ class Workload:
         self.gimg = torch.empty_like(self.img)
         self.loss = torch.empty((), device=dev)
         self.grad = torch.empty_like(self.params)
-        if kind == "6d":
+        if kind in ("6d", "6dmlp"):
             self.p3 = torch.empty(p.shape[0], 20, device=dev)
             self.g3 = torch.empty_like(self.p3)
-        self.batch = 4 if kind == "6d" else 1
+        self.batch = 4 if kind in ("6d", "6dmlp") else 1
         self.k = 0
         self.pixels_per_step = self.H * self.W * self.batch
 
@@ -308,6 +315,16 @@ class Workload:
         from paper_2508_12615_gb300.render import _ptr, _stream
 
         n = params.shape[0]
+        if self.kind == "6dmlp":
+            w.deform_mlp(params, t, self.theta, state=self.st_mlp, out=self.p3)
+            w.forward3d(self.p3, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
+            if fwd_only:
+                return
+            w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
+            w.backward(self.st, self.p3, self.gimg, out=self.g3)
+            w.deform_mlp_backward(self.st_mlp, params, self.g3, grad_theta=self.gtheta, grad_params3=self.grad,
+                                  accumulate=accumulate)
+            return
         _abi.call("wipes_deform6d", _ptr(params), n, t, _ptr(self.p3), _stream(self.dev))
         w.forward3d(self.p3, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
         if fwd_only:
@@ -342,6 +359,8 @@ class Workload:
 
 def our_arm(args, rank: int, world: int, local_rank: int):
     import torch
+
+    import synth
 
     from paper_2508_12615_gb300 import _abi, build
 
@@ -393,8 +412,8 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         flush.zero_()
         wl.step()
     torch.cuda.synchronize()
-    stage_ms = (ctypes.c_double * 10)()
-    stage_n = (ctypes.c_int64 * 10)()
+    stage_ms = (ctypes.c_double * len(_abi.STAGES))()
+    stage_n = (ctypes.c_int64 * len(_abi.STAGES))()
     lib.wipes_get_timing(ctx.handle, stage_ms, stage_n, 1)
     lib.wipes_set_timing(ctx.handle, 0)
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
@@ -459,6 +478,21 @@ def our_arm(args, rank: int, world: int, local_rank: int):
                         f"{mufu_ops} MUFU ops",
                 "mufu_frac": pairs_per_launch * mufu_ops / launch_s / (SMS * 16 * clock_mhz * 1e6)}
 
+    # the deformation network's products (tensor cores, bf16): 2 N sum(in x out) flops forward, twice
+    # that backward (input and weight gradients)
+    roofline_mlp = None
+    if wl.kind == "6dmlp" and "mlp_fwd" in stages:
+        macs = sum(o * i for o, i in synth.MLP_SHAPES) * wl.p.shape[0]
+        t_f = stages["mlp_fwd"]["ms_per_launch"] * 1e-3
+        t_b = stages["mlp_bwd"]["ms_per_launch"] * 1e-3
+        ach = 6.0 * macs / (t_f + t_b) / 1e12
+        peak_bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
+        roofline_mlp = {"bound": "tensor", "kernel": "deformation network GEMMs (cuBLASLt bf16)", "achieved": ach,
+                        "peak": peak_bf16, "unit": "TFLOP/s", "frac": ach / peak_bf16, "traffic": None,
+                        "peak_source": f"{pk_kind} bf16 GEMM throughput (sustained)",
+                        "work": f"6 x {macs:.3g} multiply-adds per sample (forward, input and weight gradients)",
+                        "fwd_tflops": 2.0 * macs / t_f / 1e12, "bwd_tflops": 4.0 * macs / t_b / 1e12}
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline and wl.kind == "2d":
         per_step, desc = oracle_step_sample(wl.p, wl.target, wl.H, wl.W, args.cpu_seconds)
@@ -484,6 +518,7 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         "stages_ms": {k: v["ms_per_launch"] for k, v in stages.items()},
         "pairs": {"visited": visited, "inside": inside, "instances": instances},
         "roofline": roofline,
+        **({"roofline_mlp": roofline_mlp} if roofline_mlp else {}),
         "cpu_baseline": cpu,
         "serving": serving,
         "clocks": clocks,

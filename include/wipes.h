@@ -211,7 +211,9 @@ enum {
     WIPES_STAGE_BWD_RASTER = 7,  /* backward rasterization */
     WIPES_STAGE_BWD_CHAIN = 8,   /* backward reduction and chain to the record parameters */
     WIPES_STAGE_LOSS = 9,        /* wipes_l2_loss */
-    WIPES_STAGE_COUNT = 10
+    WIPES_STAGE_MLP_FWD = 10,    /* wipes_deform_mlp */
+    WIPES_STAGE_MLP_BWD = 11,    /* wipes_deform_mlp_backward */
+    WIPES_STAGE_COUNT = 12
 };
 wipes_status wipes_set_timing(wipes_ctx* ctx, int enable);
 wipes_status wipes_get_timing(wipes_ctx* ctx, double* ms, int64_t* brackets, int reset);

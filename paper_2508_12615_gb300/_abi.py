@@ -76,7 +76,8 @@ _SIGNATURES = {
     "wipes_get_memory_reserved": (c_int, [_P, _P]),
 }
 
-STAGES = ["footprint", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend", "bwd_raster", "bwd_chain", "loss"]
+STAGES = ["footprint", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend", "bwd_raster", "bwd_chain", "loss",
+          "mlp_fwd", "mlp_bwd"]
 
 _lib = None
 

@@ -781,6 +781,7 @@ wipes_status wipes_deform_mlp(wipes_ctx* ctx, wipes_state* st, const float* para
     WIPES_TRY(ensure(st->mlp_d, z.out));
     WIPES_TRY(ensure(st->mlp_theta16, z.theta16));
     st->mlp_N = -1;
+    StageTimer tm(ctx, WIPES_STAGE_MLP_FWD, s);
     const std::string e = mlp_forward(*ctx->mlp, params3, N, t, theta, st->mlp_theta16.p, st->mlp_act.p,
                                       st->mlp_d.as<float>(), params_out, s);
     if (!e.empty()) return fail(WIPES_ERR_CUDA, e);
@@ -803,6 +804,7 @@ wipes_status wipes_deform_mlp_backward(wipes_ctx* ctx, wipes_state* st, const fl
         if (!accumulate) WIPES_CUDA(cudaMemsetAsync(dL_dtheta, 0, sizeof(float) * (size_t)mlp_param_count(), s));
         return WIPES_OK;
     }
+    StageTimer tm(ctx, WIPES_STAGE_MLP_BWD, s);
     const std::string e = mlp_backward(*ctx->mlp, params3, N, st->mlp_theta16.p, st->mlp_act.p, st->mlp_d.as<float>(),
                                        st->mlp_scratch.p, dL_dout, dL_dtheta, dL_dparams3, accumulate, s);
     if (!e.empty()) return fail(WIPES_ERR_CUDA, e);

@@ -85,14 +85,21 @@ __global__ void __launch_bounds__(256) k_to_bf16(const float* __restrict__ src, 
         dst[i] = __float2bfloat16_rn(src[i]);
 }
 
-// deformed record from the canonical record and the network outputs d [N, 16] (13 used)
+// deformed record from the canonical record and the network outputs d [N, 16] (13 used): the
+// output layer's bias b is added here, and d keeps the biased outputs for the backward
 __global__ void __launch_bounds__(256) k_mlp_apply(const float* __restrict__ params3, int64_t N,
-                                                   const float* __restrict__ d, float* __restrict__ out) {
+                                                   float* __restrict__ d, const float* __restrict__ b,
+                                                   float* __restrict__ out) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float* p = params3 + i * WIPES_P3D;
-    const float* e = d + i * kOutPad;
+    float e[kOut];
+#pragma unroll
+    for (int k = 0; k < kOut; ++k) {
+        e[k] = d[i * kOutPad + k] + b[k];
+        d[i * kOutPad + k] = e[k];
+    }
     float* o = out + i * WIPES_P3D;
 #pragma unroll
     for (int k = 0; k < WIPES_P3D; ++k) o[k] = p[k];
@@ -154,36 +161,73 @@ __global__ void __launch_bounds__(256) k_mlp_apply_backward(const float* __restr
     if (threadIdx.x < kOut) atomicAdd(&db_head[threadIdx.x], s_db[threadIdx.x]);
 }
 
-// dz = dh where h > 0 (ReLU), and the bias gradient (column sums of dz); one thread per column of a
-// 256-wide activation matrix, each block over a run of rows
-constexpr int kReluRows = 64;
-__global__ void __launch_bounds__(kWidth) k_relu_backward(const __nv_bfloat16* __restrict__ dh, int ld_dh,
-                                                          const __nv_bfloat16* __restrict__ h, int ld_h, int64_t N,
-                                                          __nv_bfloat16* __restrict__ dz, float* __restrict__ db) {
+// the output layer's weights += rows 0..12 of the padded [16, 256] weight gradient
+__global__ void __launch_bounds__(256) k_mlp_add_head_dw(const float* __restrict__ dw_head16,
+                                                         float* __restrict__ g_theta, int64_t head_off) {
     pdl_enter();
     const int c = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * kReluRows;
-    const int64_t r1 = min(N, r0 + kReluRows);
-    float s = 0.f;
-    for (int64_t r = r0; r < r1; ++r) {
-        const __nv_bfloat16 v = __bfloat162float(h[r * ld_h + c]) > 0.f ? dh[r * ld_dh + c] : __float2bfloat16_rn(0.f);
-        dz[r * kWidth + c] = v;
-        s += __bfloat162float(v);
+    for (int o = 0; o < kOut; ++o) g_theta[head_off + (int64_t)o * kWidth + c] += dw_head16[o * kWidth + c];
+}
+
+// the output layer's weights in bfloat16, zero-padded from 13 to 16 rows (aligned product shapes)
+__global__ void __launch_bounds__(256) k_mlp_head16(const float* __restrict__ w_head, __nv_bfloat16* __restrict__ out) {
+    pdl_enter();
+    const int c = threadIdx.x;
+    for (int o = 0; o < kOutPad; ++o) out[o * kWidth + c] = __float2bfloat16_rn(o < kOut ? w_head[o * kWidth + c] : 0.f);
+}
+
+// dz = dh where h > 0 (ReLU) and the bias gradient (column sums of dz) of a 256-wide layer: a warp
+// takes a row, each lane 8 columns with 16-byte accesses; the block sums its column totals in
+// shared memory and adds them with one atomic per column
+constexpr int kReluBlocks = 304;
+__global__ void __launch_bounds__(256) k_relu_backward(const __nv_bfloat16* __restrict__ dh, int ld_dh,
+                                                       const __nv_bfloat16* __restrict__ h, int ld_h, int64_t N,
+                                                       __nv_bfloat16* __restrict__ dz, float* __restrict__ db) {
+    pdl_enter();
+    __shared__ float s_db[8][kWidth];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + g; r < N; r += (int64_t)gridDim.x * 8) {
+        const uint4 vh = *reinterpret_cast<const uint4*>(h + r * ld_h + 8 * lane);
+        const uint4 vd = *reinterpret_cast<const uint4*>(dh + r * ld_dh + 8 * lane);
+        const __nv_bfloat162* ph = reinterpret_cast<const __nv_bfloat162*>(&vh);
+        const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&vd);
+        uint4 vo;
+        __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&vo);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 fh = __bfloat1622float2(ph[k]);
+            float2 fd = __bfloat1622float2(pd[k]);
+            fd.x = fh.x > 0.f ? fd.x : 0.f;
+            fd.y = fh.y > 0.f ? fd.y : 0.f;
+            po[k] = __floats2bfloat162_rn(fd.x, fd.y);  // exact: fd is a bfloat16 value or 0
+            acc[2 * k] += fd.x;
+            acc[2 * k + 1] += fd.y;
+        }
+        *reinterpret_cast<uint4*>(dz + r * kWidth + 8 * lane) = vo;
     }
-    atomicAdd(&db[c], s);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s_db[g][8 * lane + k] = acc[k];
+    __syncthreads();
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += s_db[q][threadIdx.x];
+    atomicAdd(&db[threadIdx.x], sum);
 }
 
 // dL/dmu through gamma: d/dx (x, sin(2^k x), cos(2^k x)) = (1, 2^k cos, -2^k sin); the encoding's
-// gradient is the sum of layer 0's (dg0 [N, 80]) and layer 5's (columns 0..79 of dx5 [N, 336])
+// gradient is the sum of layer 0's (dg0 [N, 80]) and layer 5's through its skip input (dgs [N, 80])
 __global__ void __launch_bounds__(256) k_mlp_encode_backward(const float* __restrict__ params3, int64_t N,
                                                              const __nv_bfloat16* __restrict__ dg0,
-                                                             const __nv_bfloat16* __restrict__ dx5,
+                                                             const __nv_bfloat16* __restrict__ dgs,
                                                              float* __restrict__ g_params3) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const __nv_bfloat16* a = dg0 + i * kInPad;
-    const __nv_bfloat16* b = dx5 + i * kX5;
+    const __nv_bfloat16* b = dgs + i * kInPad;
     float gm[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) gm[j] = __bfloat162float(a[j]) + __bfloat162float(b[j]);
@@ -239,7 +283,7 @@ namespace {
 // The bias (when given) has the type of D: bfloat16 for the hidden layers, fp32 for the output layer.
 std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A, int lda, const void* B, int ldb,
                  void* D, int ldc, cudaDataType_t dtype, float beta, cublasLtEpilogue_t epi, const void* bias,
-                 cudaStream_t stream) {
+                 cudaStream_t stream, void* aux = nullptr) {
     cublasLtMatmulDesc_t desc = nullptr;
     cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
     LT_TRY(cublasLtMatmulDescCreate(&desc, CUBLAS_COMPUTE_32F, CUDA_R_32F));
@@ -248,6 +292,12 @@ std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A
     LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb)));
     LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE, &epi, sizeof(epi)));
     if (bias) LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &bias, sizeof(bias)));
+    if (aux) {
+        // ReLU bit-mask, one bit per element of D (m rows), leading dimension in bits
+        const int64_t aux_ld = kWidth;
+        LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE_AUX_POINTER, &aux, sizeof(aux)));
+        LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE_AUX_LD, &aux_ld, sizeof(aux_ld)));
+    }
     LT_TRY(cublasLtMatrixLayoutCreate(&la, CUDA_R_16BF, ta ? k : m, ta ? m : k, lda));
     LT_TRY(cublasLtMatrixLayoutCreate(&lb, CUDA_R_16BF, tb ? n : k, tb ? k : n, ldb));
     LT_TRY(cublasLtMatrixLayoutCreate(&lc, dtype, m, n, ldc));
@@ -285,13 +335,15 @@ std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A
 }
 
 // forward product of layer l: Y [N, out] (row-major, ldy) = X [N, in] (ldx) W^T + b, ReLU for hidden
-// layers (bias b in bfloat16 for them, fp32 for the output layer)
+// layers (bias b in bfloat16 for them, fp32 for the output layer), whose ReLU bit-mask goes to mask
 std::string layer_forward(MlpLt& lt, int l, const __nv_bfloat16* w, const void* b, const void* x, int ldx, void* y,
                           int ldy, int64_t N, cudaStream_t s) {
     const LayerShape sh = kShapes[l];
-    const bool head = l == kHidden;
-    return gemm(lt, true, false, sh.out, (int)N, sh.in, w, sh.in, x, ldx, y, ldy, head ? CUDA_R_32F : CUDA_R_16BF,
-                0.f, head ? CUBLASLT_EPILOGUE_BIAS : CUBLASLT_EPILOGUE_RELU_BIAS, b, s);
+    if (l == kHidden)  // output layer: the padded [16, 256] weights, bias added by k_mlp_apply
+        return gemm(lt, true, false, kOutPad, (int)N, kWidth, w, kWidth, x, ldx, y, ldy, CUDA_R_32F, 0.f,
+                    CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+    return gemm(lt, true, false, sh.out, (int)N, sh.in, w, sh.in, x, ldx, y, ldy, CUDA_R_16BF, 0.f,
+                CUBLASLT_EPILOGUE_RELU_BIAS, b, s);
 }
 
 }  // namespace
@@ -321,12 +373,20 @@ void mlp_lt_destroy(MlpLt* lt) {
 
 int64_t mlp_param_count() { return layer_offset(kHidden + 1); }
 
+// element offset of the padded output layer in the bfloat16 parameter buffer (8 elements = 16 bytes)
+int64_t head16_offset() { return (mlp_param_count() + 7) / 8 * 8; }
+
 MlpSizes mlp_sizes(int64_t N) {
     MlpSizes z;
+    // activations: x5 and seven 256-wide layers
     z.act = (size_t)N * (kX5 + 7 * kWidth) * sizeof(__nv_bfloat16);
-    z.scratch = (size_t)N * (3 * kWidth + kX5 + kInPad + kOutPad) * sizeof(__nv_bfloat16);
+    // dh [N, 256], dz [N, 256], encoding gradients [N, 80] x 2, dL/dd [N, 16]; the padded output
+    // layer's weight gradient [16, 256] (fp32)
+    z.scratch = (size_t)N * (2 * kWidth + 2 * kInPad + kOutPad) * sizeof(__nv_bfloat16) +
+                kOutPad * kWidth * sizeof(float);
     z.out = (size_t)N * kOutPad * sizeof(float);
-    z.theta16 = (size_t)mlp_param_count() * sizeof(__nv_bfloat16);
+    // the bfloat16 parameters, then (16-byte aligned) the padded [16, 256] output layer
+    z.theta16 = (size_t)(head16_offset() + kOutPad * kWidth) * sizeof(__nv_bfloat16);
     return z;
 }
 
@@ -345,7 +405,8 @@ std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, con
     __nv_bfloat16* w16 = static_cast<__nv_bfloat16*>(theta16_buf);
     const int64_t P = mlp_param_count();
     launch_pdl(k_to_bf16, (unsigned)std::min<int64_t>(ceil_div(P, 256), 1024), 256, 0, s, theta, w16, P);
-    count_launches(1);
+    launch_pdl(k_mlp_head16, 1u, kWidth, 0, s, theta + layer_offset(kHidden), w16 + head16_offset());
+    count_launches(2);
     __nv_bfloat16* x5 = act_x5(act);
     launch_pdl(k_mlp_encode, ceil_div(N * kInPad, 256), 256, 0, s, params3, N, t, x5);
     count_launches(1);
@@ -357,11 +418,12 @@ std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, con
         void* y = l == kHidden ? (void*)d : (l == 4 ? (void*)(x5 + kInPad) : (void*)act_h(act, N, l));
         const int ldy = l == kHidden ? kOutPad : (l == 4 ? kX5 : kWidth);
         const int64_t boff = layer_offset(l) + (int64_t)kShapes[l].out * kShapes[l].in;
-        const void* bias = l == kHidden ? (const void*)(theta + boff) : (const void*)(w16 + boff);
-        const std::string e = layer_forward(lt, l, w16 + layer_offset(l), bias, x, ldx, y, ldy, N, s);
+        const __nv_bfloat16* wl = l == kHidden ? w16 + head16_offset() : w16 + layer_offset(l);
+        const std::string e = layer_forward(lt, l, wl, w16 + boff, x, ldx, y, ldy, N, s);
         if (!e.empty()) return e;
     }
-    launch_pdl(k_mlp_apply, ceil_div(N, 256), 256, 0, s, params3, N, (const float*)d, params_out);
+    launch_pdl(k_mlp_apply, ceil_div(N, 256), 256, 0, s, params3, N, d,
+               theta + layer_offset(kHidden) + (int64_t)kOut * kWidth, params_out);
     count_launches(1);
     return "";
 }
@@ -371,71 +433,65 @@ std::string mlp_backward(MlpLt& lt, const float* params3, int64_t N, const void*
                          int accumulate, cudaStream_t s) {
     if (N == 0) return "";
     const __nv_bfloat16* w16 = static_cast<const __nv_bfloat16*>(theta16_buf);
-    const __nv_bfloat16* x5 = static_cast<const __nv_bfloat16*>(act);
+    const __nv_bfloat16* whead16 = w16 + head16_offset();  // [16, 256], rows 13..15 zero
     void* actm = const_cast<void*>(act);
-    // scratch: dh0, dh1 (ping-pong), dz [N, 256]; dx5 [N, 336]; dg0 [N, 80]; gd [N, 16]
-    __nv_bfloat16* dh[2] = {static_cast<__nv_bfloat16*>(scratch), static_cast<__nv_bfloat16*>(scratch) + (size_t)N * kWidth};
-    __nv_bfloat16* dz = dh[1] + (size_t)N * kWidth;
-    __nv_bfloat16* dx5 = dz + (size_t)N * kWidth;
-    __nv_bfloat16* dg0 = dx5 + (size_t)N * kX5;
-    __nv_bfloat16* gd = dg0 + (size_t)N * kInPad;
-    const float beta = accumulate ? 1.f : 0.f;
+    const __nv_bfloat16* x5 = act_x5(actm);
+    // scratch layout (see mlp_sizes)
+    __nv_bfloat16* dh = static_cast<__nv_bfloat16*>(scratch);  // [N, 256] before the ReLU mask
+    __nv_bfloat16* dz = dh + (size_t)N * kWidth;                // [N, 256] after it
+    __nv_bfloat16* dg0 = dz + (size_t)N * kWidth;               // [N, 80] through layer 0
+    __nv_bfloat16* dgs = dg0 + (size_t)N * kInPad;              // [N, 80] through the skip input of layer 5
+    __nv_bfloat16* gd = dgs + (size_t)N * kInPad;               // [N, 16]
+    float* dw_head16 = reinterpret_cast<float*>(gd + (size_t)N * kOutPad);  // [16, 256]
     if (!accumulate) cudaMemsetAsync(g_theta, 0, sizeof(float) * (size_t)mlp_param_count(), s);
     float* db_head = g_theta + layer_offset(kHidden) + (int64_t)kOut * kWidth;
     launch_pdl(k_mlp_apply_backward, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3, accumulate,
                db_head);
     count_launches(1);
     std::string e;
-    // head: dW_8 += gd^T h7, dh7 = gd W_8
-    {
-        const int l = kHidden;
-        e = gemm(lt, false, true, kWidth, kOut, (int)N, act_h(actm, N, 7), kWidth, gd, kOutPad,
-                 g_theta + layer_offset(l), kWidth, CUDA_R_32F, 1.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        if (!e.empty()) return e;
-        e = gemm(lt, false, false, kWidth, (int)N, kOut, w16 + layer_offset(l), kWidth, gd, kOutPad, dh[0], kWidth,
-                 CUDA_R_16BF, 0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        if (!e.empty()) return e;
-    }
-    // dh for the current layer: cur (ld) ; for layer 4 it is columns 80.. of dx5
-    const __nv_bfloat16* cur = dh[0];
-    int ld_cur = kWidth;
-    int ping = 1;
+    // output layer (padded to 16 rows): dW_8 = gd^T h7 into [16, 256]; dh7 = gd W_8
+    e = gemm(lt, false, true, kWidth, kOutPad, (int)N, act_h(actm, N, 7), kWidth, gd, kOutPad, dw_head16, kWidth,
+             CUDA_R_32F, 0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+    if (!e.empty()) return e;
+    e = gemm(lt, false, false, kWidth, (int)N, kOutPad, whead16, kWidth, gd, kOutPad, dh, kWidth, CUDA_R_16BF, 0.f,
+             CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+    if (!e.empty()) return e;
     for (int l = kHidden - 1; l >= 0; --l) {
         const LayerShape sh = kShapes[l];
+        const __nv_bfloat16* wl = w16 + layer_offset(l);
         const __nv_bfloat16* hl = l == 4 ? x5 + kInPad : act_h(actm, N, l);
         const int ld_h = l == 4 ? kX5 : kWidth;
-        float* gW = g_theta + layer_offset(l);
-        float* gb = gW + (int64_t)sh.out * sh.in;
-        launch_pdl(k_relu_backward, ceil_div(N, kReluRows), kWidth, 0, s, cur, ld_cur, hl, ld_h, N, dz, gb);
+        float* gb = g_theta + layer_offset(l) + (int64_t)sh.out * sh.in;
+        launch_pdl(k_relu_backward, (unsigned)std::min<int64_t>(kReluBlocks, ceil_div(N, 8)), 256, 0, s,
+                   (const __nv_bfloat16*)dh, kWidth, hl, ld_h, N, dz, gb);
         count_launches(1);
-        // dW_l += dz^T x_l  (column-major: [in, out] = x^T(in x N) dz(N x out))
+        // dW_l += dz_l^T x_l  (column-major [in, out] = x^T (in x N) dz (N x out))
         const void* xin = (l == 0 || l == kSkipLayer) ? (const void*)x5 : (const void*)act_h(actm, N, l - 1);
         const int ldx = (l == 0 || l == kSkipLayer) ? kX5 : kWidth;
-        e = gemm(lt, false, true, sh.in, sh.out, (int)N, xin, ldx, dz, kWidth, gW, sh.in, CUDA_R_32F, 1.f,
-                 CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        e = gemm(lt, false, true, sh.in, sh.out, (int)N, xin, ldx, dz, kWidth, g_theta + layer_offset(l), sh.in,
+                 CUDA_R_32F, 1.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
         if (!e.empty()) return e;
-        // dx_l = dz W_l  (column-major: [in, N] = W^T... W row-major [out, in] is column-major [in, out])
-        void* dxl;
-        int ld_dx;
-        if (l == kSkipLayer) { dxl = dx5; ld_dx = kX5; }
-        else if (l == 0) { dxl = dg0; ld_dx = kInPad; }
-        else { dxl = dh[ping]; ld_dx = kWidth; }
-        e = gemm(lt, false, false, sh.in, (int)N, sh.out, w16 + layer_offset(l), sh.in, dz, kWidth, dxl, ld_dx,
-                 CUDA_R_16BF, 0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        if (!e.empty()) return e;
-        if (l == kSkipLayer) {
-            cur = dx5 + kInPad;
-            ld_cur = kX5;
-        } else if (l > 0) {
-            cur = dh[ping];
-            ld_cur = kWidth;
-            ping ^= 1;
+        // input gradient dz_l W_l (W_l row-major [out, in] = column-major [in, out]) into dh for layer
+        // l - 1; layer 5 splits it into the encoding's part and h4's, layer 0 has only the encoding's
+        if (l == 0) {
+            e = gemm(lt, false, false, kInPad, (int)N, kWidth, wl, kInPad, dz, kWidth, dg0, kInPad, CUDA_R_16BF, 0.f,
+                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        } else if (l == kSkipLayer) {
+            e = gemm(lt, false, false, kInPad, (int)N, kWidth, wl, kX5, dz, kWidth, dgs, kInPad, CUDA_R_16BF, 0.f,
+                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+            if (!e.empty()) return e;
+            e = gemm(lt, false, false, kWidth, (int)N, kWidth, wl + kInPad, kX5, dz, kWidth, dh, kWidth, CUDA_R_16BF,
+                     0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
+        } else {
+            e = gemm(lt, false, false, kWidth, (int)N, kWidth, wl, kWidth, dz, kWidth, dh, kWidth, CUDA_R_16BF, 0.f,
+                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
         }
+        if (!e.empty()) return e;
     }
-    (void)beta;
+    launch_pdl(k_mlp_add_head_dw, 1u, kWidth, 0, s, (const float*)dw_head16, g_theta, layer_offset(kHidden));
     launch_pdl(k_mlp_encode_backward, ceil_div(N, 256), 256, 0, s, params3, N, (const __nv_bfloat16*)dg0,
-               (const __nv_bfloat16*)dx5, g_params3);
-    count_launches(1);
+               (const __nv_bfloat16*)dgs, g_params3);
+    count_launches(2);
     return "";
 }
 
