@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=10.0, help="length of the serving request trace")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU work budget of the oracle baseline")
+    ap.add_argument("--no-sort-bw", action="store_true", help="skip the radix-sort bandwidth measurement")
+    ap.add_argument("--sort-n", type=int, default=1 << 25, help="pairs of the sort bandwidth measurement")
+    ap.add_argument("--only-sort", action="store_true",
+                    help="print only the sort bandwidth measurement (one JSON object) and exit")
     return ap.parse_args()
 
 
@@ -503,6 +507,19 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     if world == 1 and not args.no_serving and wl.kind == "2d":
         serving = serving_run(args, dev)
 
+    # the path's sort: its share of the step on this workload, and its bandwidth on a large input
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    sort = {"peak_gbs": hbm, "peak_source": f"{pk_kind} HBM copy bandwidth"}
+    if "tile_sort" in stages:
+        passes = max(1, (ceil_log2(((wl.W + 15) // 16) * ((wl.H + 15) // 16)) + 7) // 8)
+        n_inst = instances / wl.batch
+        b = n_inst * (4 + 16 * passes + 8)
+        t = stages["tile_sort"]["ms_per_launch"] * 1e-3
+        sort["tile_sort"] = {"pairs": n_inst, "passes": passes, "ms": t * 1e3, "algorithmic_bytes": b,
+                             "gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+    if world == 1 and not args.no_sort_bw:
+        sort["large"] = sort_bandwidth(args, dev, ctx, hbm)
+
     n_h2d = int(wl.p.nbytes + wl.target.nbytes)
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
@@ -522,10 +539,49 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         **({"roofline_mlp": roofline_mlp} if roofline_mlp else {}),
         "cpu_baseline": cpu,
         "serving": serving,
+        "sort": sort,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
+
+
+def ceil_log2(x: int) -> int:
+    return max(0, (int(x) - 1).bit_length())
+
+
+def sort_bandwidth(args, dev, ctx, hbm_gbs: float) -> dict:
+    """wipes_sort_pairs on args.sort_n random 32-bit keys with 32-bit values (4 passes of 8 bits):
+    algorithmic bytes per pair = 4 (the histogram reads every key once) + 16 per pass (read key and
+    value, write both), over the mean CUDA-event time of the sort call.  Every sort starts from the
+    same unsorted input, copied in before the timed call."""
+    import torch
+
+    from paper_2508_12615_gb300 import State, sort_pairs
+
+    n = int(args.sort_n)
+    g = torch.Generator(device=dev).manual_seed(1239)
+    keys0 = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device=dev, generator=g)
+    vals0 = torch.arange(n, dtype=torch.int32, device=dev)
+    keys, vals = torch.empty_like(keys0), torch.empty_like(vals0)
+    st = State(ctx)
+    times = []
+    for it in range(13):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sort_pairs(keys, vals, 32, state=st)
+        b.record()
+        torch.cuda.synchronize()
+        if it >= 3:
+            times.append(a.elapsed_time(b))
+    ms = statistics.mean(times)
+    passes = 4
+    byts = n * (4 + 16 * passes)
+    del st, keys0, vals0, keys, vals
+    return {"pairs": n, "key_bits": 32, "passes": passes, "ms": ms, "algorithmic_bytes": byts,
+            "gbs": byts / (ms * 1e-3) / 1e9, "frac": byts / (ms * 1e-3) / 1e9 / hbm_gbs}
 
 
 def serving_run(args, dev):
@@ -556,6 +612,17 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.only_sort:
+        import torch
+
+        import paper_2508_12615_gb300 as w
+
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        pk, pk_kind = peaks()
+        print(json.dumps(sort_bandwidth(args, dev, w.Context.get(dev.index), float(pk.get("hbm_gbs", 6800.0)))),
+              flush=True)
         return
     if world > 1:
         import torch

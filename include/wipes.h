@@ -213,7 +213,8 @@ enum {
     WIPES_STAGE_LOSS = 9,        /* wipes_l2_loss */
     WIPES_STAGE_MLP_FWD = 10,    /* wipes_deform_mlp */
     WIPES_STAGE_MLP_BWD = 11,    /* wipes_deform_mlp_backward */
-    WIPES_STAGE_COUNT = 12
+    WIPES_STAGE_SORT = 12,       /* wipes_sort_pairs */
+    WIPES_STAGE_COUNT = 13
 };
 wipes_status wipes_set_timing(wipes_ctx* ctx, int enable);
 wipes_status wipes_get_timing(wipes_ctx* ctx, double* ms, int64_t* brackets, int reset);
@@ -255,6 +256,19 @@ wipes_status wipes_deform_mlp(wipes_ctx* ctx, wipes_state* st, const float* para
  * overwritten. */
 wipes_status wipes_deform_mlp_backward(wipes_ctx* ctx, wipes_state* st, const float* params3, const float* dL_dout,
                                        float* dL_dtheta, float* dL_dparams3, int accumulate, void* stream);
+
+/* The path's sort (Sec. 1: the GPU sort that orders the tile lists; also the depth sort of the 3D
+ * primitives) as a call of its own, for tests and measurement.  Sorts the n (key, value) pairs in
+ * keys[n], vals[n] (device, uint32, caller-owned) in place by the low key_bits bits of the key
+ * (1..32), stably: pairs with equal low bits keep their input order; the high bits ride along.
+ * One pass per 8 bits or fewer (the bits split evenly over ceil(key_bits / 8) passes) after one
+ * histogram kernel.  `st` provides the second buffers (2 n words, kept for reuse) and the look-back
+ * workspace; its render data are untouched.  An odd pass count ends with one device copy back.
+ * Errors: WIPES_ERR_INVALID for n outside 0..2^31-1, key_bits outside 1..32 or null buffers;
+ * WIPES_ERR_OOM under the context's memory limit.  Asynchronous on `stream`; a look-back wait that
+ * ran out is reported by the next wipes_sync_status() as WIPES_ERR_TIMEOUT. */
+wipes_status wipes_sort_pairs(wipes_ctx* ctx, wipes_state* st, uint32_t* keys, uint32_t* vals, int64_t n,
+                              int key_bits, void* stream);
 
 /* Diagnostic: run one radix-sort pass on scratch data in which the tile before the block's tile
  * never publishes its counts, so that the block's bounded look-back runs out (after well under a

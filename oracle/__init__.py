@@ -211,6 +211,17 @@ def deform6d_grad(params6, t, g3):
     return out
 
 
+def sort_pairs(keys, vals, key_bits):
+    """The sort of the path (Sec. 1: the GPU sort that orders the tile lists, and the 3D depth
+    sort): (key, value) pairs of 32-bit words ordered stably by the low key_bits bits of the key,
+    pairs with equal low bits in input order.  Returns the sorted (keys, vals) as uint32."""
+    k = np.ascontiguousarray(keys).view(np.uint32).ravel()
+    v = np.ascontiguousarray(vals).view(np.uint32).ravel()
+    mask = np.uint32(0xFFFFFFFF) if key_bits >= 32 else np.uint32((1 << key_bits) - 1)
+    order = np.argsort(k & mask, kind="stable")
+    return k[order], v[order]
+
+
 def sh_basis(dirs):
     """Real spherical harmonics up to degree 3 (16 per direction) at unit vectors dirs[n,3]."""
     d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "wipes_last_error": (c_char_p, []),
     "wipes_sync_status": (c_int, [_P, _P]),
     "wipes_selftest_sort_timeout": (c_int, [_P, _P]),
+    "wipes_sort_pairs": (c_int, [_P, _P, _P, _P, ctypes.c_int64, c_int, _P]),
     "wipes_deform_mlp_param_count": (ctypes.c_int64, []),
     "wipes_deform_mlp": (c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
     "wipes_deform_mlp_backward": (c_int, [_P, _P, _P, _P, _P, _P, c_int, _P]),
@@ -77,7 +78,7 @@ _SIGNATURES = {
 }
 
 STAGES = ["footprint", "depth_sort", "scan", "emit", "tile_sort", "ranges", "blend", "bwd_raster", "bwd_chain", "loss",
-          "mlp_fwd", "mlp_bwd"]
+          "mlp_fwd", "mlp_bwd", "sort"]
 
 _lib = None
 

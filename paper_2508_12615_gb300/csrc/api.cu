@@ -189,11 +189,12 @@ struct wipes_state {
     DevBuf sprim, order, T_final, last, partial, grad_img;
     DevBuf mlp_act, mlp_scratch, mlp_d, mlp_theta16;  // deformation network: activations kept for the backward
     int64_t mlp_N = -1;                               // primitives of the last network forward (-1: none)
+    DevBuf sort_k, sort_v;                            // second buffers of wipes_sort_pairs
 
-    DevBuf* all[27] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
+    DevBuf* all[29] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
                        &block_sums, &total, &keys[0], &keys[1],   &vals[0],   &vals[1],   &inst_prim, &hist,
                        &ranges,  &sprim,   &order,     &T_final, &last,     &partial,  &grad_img, &mlp_act,
-                       &mlp_scratch, &mlp_d, &mlp_theta16};
+                       &mlp_scratch, &mlp_d, &mlp_theta16, &sort_k, &sort_v};
     size_t reserved() const {
         size_t s = 0;
         for (DevBuf* b : all) s += b->cap;
@@ -587,6 +588,31 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
         launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->opts.freq_proj_mode,
                        st->opts.sh_degree, st->rec.as<float4>(),
                        st->grad_img.as<float>(), dL_dparams, s);
+    }
+    WIPES_CUDA(cudaGetLastError());
+    return WIPES_OK;
+}
+
+wipes_status wipes_sort_pairs(wipes_ctx* ctx, wipes_state* st, uint32_t* keys, uint32_t* vals, int64_t n,
+                              int key_bits, void* stream) {
+    if (!ctx || !st || st->ctx != ctx) return fail(WIPES_ERR_INVALID, "wipes_sort_pairs: bad context or state");
+    if (n < 0 || n > (int64_t)INT32_MAX || key_bits < 1 || key_bits > 32 || (n > 0 && (!keys || !vals)))
+        return fail(WIPES_ERR_INVALID, "wipes_sort_pairs: need 0 <= n <= 2^31-1, 1 <= key_bits <= 32 and buffers");
+    if (n <= 1) return WIPES_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    WIPES_TRY(ensure(st->sort_k, sizeof(uint32_t) * (size_t)n));
+    WIPES_TRY(ensure(st->sort_v, sizeof(uint32_t) * (size_t)n));
+    WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(n)));
+    uint32_t* kb[2] = {keys, st->sort_k.as<uint32_t>()};
+    uint32_t* vb[2] = {vals, st->sort_v.as<uint32_t>()};
+    {
+        StageTimer t(ctx, WIPES_STAGE_SORT, s);
+        const int cur = radix_sort_pairs(kb, vb, n, key_bits, st->hist.as<uint32_t>(), ctx->d_error, s);
+        if (cur == 1) {  // an odd number of passes ends in the second buffers
+            WIPES_CUDA(cudaMemcpyAsync(keys, kb[1], sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+            WIPES_CUDA(cudaMemcpyAsync(vals, vb[1], sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        }
     }
     WIPES_CUDA(cudaGetLastError());
     return WIPES_OK;

@@ -199,52 +199,65 @@ __device__ __forceinline__ unsigned long long load_word(const unsigned long long
     return v;
 }
 
+// Digit counts of every pass over all keys.  Each warp counts into its own shared histogram with
+// plain shared-memory atomics (equal digits within one instruction are serialised by the hardware,
+// different warps never contend); a thread reads four consecutive keys with one 16-byte load when
+// the array is 16-byte aligned.
 __global__ void __launch_bounds__(kThreads) k_sort_histogram(const uint32_t* __restrict__ keys, int64_t n,
                                                              SortPlan plan, uint32_t* __restrict__ totals) {
     pdl_enter();
-    __shared__ uint32_t s_cnt[kMaxPasses][kMaxRadix];
-    for (int k = threadIdx.x; k < kMaxPasses * kMaxRadix; k += kThreads) (&s_cnt[0][0])[k] = 0u;
+    __shared__ uint32_t s_cnt[kWarps][kMaxPasses * kMaxRadix];
+    for (int k = threadIdx.x; k < kWarps * kMaxPasses * kMaxRadix; k += kThreads) (&s_cnt[0][0])[k] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    constexpr int kUnroll = 4;
-    for (int64_t base = (int64_t)blockIdx.x * kThreads * kUnroll; base < n;
-         base += (int64_t)gridDim.x * kThreads * kUnroll) {
-        uint32_t key[kUnroll];
+    uint32_t* my = s_cnt[threadIdx.x >> 5];
+    auto count = [&](uint32_t key) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int64_t idx = base + u * kThreads + threadIdx.x;
-            key[u] = idx < n ? keys[idx] : 0u;
+        for (int p = 0; p < kMaxPasses; ++p)
+            if (p < plan.passes)
+                atomicAdd(&my[p * kMaxRadix + ((key >> plan.shift[p]) & ((1u << plan.nbits[p]) - 1u))], 1u);
+    };
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    if ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0) {
+        const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+        const int64_t n4 = n >> 2;
+        for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < n4; q += stride) {
+            const uint4 v = k4[q];
+            count(v.x);
+            count(v.y);
+            count(v.z);
+            count(v.w);
         }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const bool valid = base + u * kThreads + threadIdx.x < n;
-            for (int p = 0; p < plan.passes; ++p) {
-                const uint32_t d = valid ? (key[u] >> plan.shift[p]) & ((1u << plan.nbits[p]) - 1u) : 0xFFFFu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
-                if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[p][d], (uint32_t)__popc(peers));
-            }
-        }
+        for (int64_t idx = (n4 << 2) + (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < n; idx += stride)
+            count(keys[idx]);
+    } else {
+        for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < n; idx += stride) count(keys[idx]);
     }
     __syncthreads();
-    for (int p = 0; p < plan.passes; ++p)
-        for (int d = threadIdx.x; d < (1 << plan.nbits[p]); d += kThreads)
-            if (s_cnt[p][d]) atomicAdd(&totals[p * kMaxRadix + d], s_cnt[p][d]);
+    for (int k = threadIdx.x; k < plan.passes * kMaxRadix; k += kThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) sum += s_cnt[w][k];
+        if (sum) atomicAdd(&totals[k], sum);
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) k_sort_pass(const uint32_t* __restrict__ keys_in,
-                                                        const uint32_t* __restrict__ vals_in,
-                                                        uint32_t* __restrict__ keys_out,
-                                                        uint32_t* __restrict__ vals_out, int64_t n, int shift,
-                                                        int nbits, const uint32_t* __restrict__ totals,
-                                                        unsigned int* __restrict__ tile_counter,
-                                                        unsigned long long* __restrict__ status,
-                                                        unsigned int* __restrict__ error,
-                                                        const uint32_t* __restrict__ table,
-                                                        uint32_t* __restrict__ gathered) {
+__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __restrict__ keys_in,
+                                                           const uint32_t* __restrict__ vals_in,
+                                                           uint32_t* __restrict__ keys_out,
+                                                           uint32_t* __restrict__ vals_out, int64_t n, int shift,
+                                                           int nbits, const uint32_t* __restrict__ totals,
+                                                           unsigned int* __restrict__ tile_counter,
+                                                           unsigned long long* __restrict__ status,
+                                                           unsigned int* __restrict__ error,
+                                                           const uint32_t* __restrict__ table,
+                                                           uint32_t* __restrict__ gathered) {
     pdl_enter();
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wc[kWarps][kMaxRadix];
+    __shared__ uint32_t s_cnt[kMaxRadix];
+    __shared__ uint32_t s_match[kWarps][kMaxRadix];
+    for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_match[0][0])[k] = 0u;
     __shared__ uint32_t s_dstart[kMaxRadix];
     __shared__ uint32_t s_gbase[kMaxRadix];
     __shared__ uint32_t s_warp[kWarps];
@@ -254,6 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(const uint32_t* __restri
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
     for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_wc[0][0])[k] = 0u;
+    if ((int)threadIdx.x < kMaxRadix) s_cnt[threadIdx.x] = 0u;
     // global start of each digit = exclusive scan of the digit totals
     {
         const uint32_t x = (int)threadIdx.x < radix ? totals[threadIdx.x] : 0u;
@@ -265,46 +279,64 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(const uint32_t* __restri
     const int64_t blk = (int64_t)tile * kSortTile;
     const int64_t base = blk + (int64_t)warp * (kSortItems * 32);
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t k[kSortItems], v[kSortItems], rank[kSortItems];
+    // the keys wait in s_vals at their tile-local position (item i of warp w's run at
+    // w * 32 kSortItems + 32 i + lane) until they are placed; the values are read at the end
+    const int run = warp * (kSortItems * 32) + lane;
+    uint32_t pos[kSortItems];
+    {
+        uint32_t k[kSortItems];
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        const int64_t idx = base + i * 32 + lane;
-        k[i] = idx < n ? keys_in[idx] : 0u;
-        v[i] = idx < n ? vals_in[idx] : 0u;
+        for (int i = 0; i < kSortItems; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            k[i] = idx < n ? keys_in[idx] : 0u;
+        }
+        // the tile's digit counts first, so that later tiles can use them as early as possible
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            s_vals[run + 32 * i] = k[i];
+            if (base + i * 32 + lane < n) atomicAdd(&s_cnt[(k[i] >> shift) & mask], 1u);
+        }
     }
+    __syncthreads();
+    // publish the tile's digit counts at once, so that later tiles can use them as early as possible
+    unsigned long long* mine = status + (size_t)tile * kMaxRadix + threadIdx.x;
+    const uint32_t running = (int)threadIdx.x < radix ? s_cnt[threadIdx.x] : 0u;
+    if ((int)threadIdx.x < radix) store_word(mine, (tile == 0 ? kPrefix : kAggregate) | running);
     // stable rank within the warp's run, in element order (item i, then lane)
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         const int64_t idx = base + i * 32 + lane;
         const bool valid = idx < n;
-        const uint32_t d = valid ? (k[i] >> shift) & mask : 0xFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = valid ? (s_vals[run + 32 * i] >> shift) & mask : 0xFFFFu;
+        // the lanes of this item with the same digit: each sets its bit in the digit's word of the
+        // warp's peer table, reads the word back, and the last of them clears it
+        if (valid) atomicOr(&s_match[warp][d], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = valid ? s_match[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == 31 - __clz(peers)) s_match[warp][d] = 0u;
         uint32_t before = 0;
         if (valid) before = s_wc[warp][d];
         __syncwarp();
         if (valid) {
-            rank[i] = before + __popc(peers & lt);
+            pos[i] = before + __popc(peers & lt);
             if (lane == 31 - __clz(peers)) s_wc[warp][d] = before + __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
-    // per digit: prefix over warps, the tile's count, the counts of all earlier tiles (look-back)
-    uint32_t running = 0;
+    // per digit: prefix over warps, then the counts of all earlier tiles (look-back)
     if ((int)threadIdx.x < radix) {
         const int d = threadIdx.x;
+        uint32_t acc = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
             const uint32_t t = s_wc[w][d];
-            s_wc[w][d] = running;
-            running += t;
+            s_wc[w][d] = acc;
+            acc += t;
         }
-        unsigned long long* mine = status + (size_t)tile * kMaxRadix + d;
         unsigned long long before = 0;
-        if (tile == 0) {
-            store_word(mine, kPrefix | running);
-        } else {
-            store_word(mine, kAggregate | running);
+        if (tile != 0) {
             // walk back kLookback tiles per step (their words are loaded together), adding
             // aggregates until an inclusive prefix; a tile that has published nothing yet is polled
             int polls = 0;
@@ -348,15 +380,29 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(const uint32_t* __restri
         }
     }
     __syncthreads();
+    // keys to their place in the tile's digit order, then the values (read only now, so that they
+    // occupy no registers during the ranking)
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         const int64_t idx = base + i * 32 + lane;
         if (idx < n) {
-            const uint32_t d = (k[i] >> shift) & mask;
-            const uint32_t pos = s_dstart[d] + s_wc[warp][d] + rank[i];
-            s_keys[pos] = k[i];
-            s_vals[pos] = v[i];
+            const uint32_t key = s_vals[run + 32 * i];
+            const uint32_t d = (key >> shift) & mask;
+            pos[i] += s_dstart[d] + s_wc[warp][d];
+            s_keys[pos[i]] = key;
         }
+    }
+    {
+        uint32_t v[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            v[i] = idx < n ? vals_in[idx] : 0u;
+        }
+        __syncthreads();  // every key has left s_vals
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i)
+            if (base + i * 32 + lane < n) s_vals[pos[i]] = v[i];
     }
     __syncthreads();
     const int cnt = (int)min((int64_t)kSortTile, n - blk);

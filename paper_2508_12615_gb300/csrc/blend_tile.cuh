@@ -18,10 +18,14 @@ __device__ __forceinline__ uint32_t stage_entry(const float4* __restrict__ rec, 
     return subtile_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
 }
 
-// Forward.  Warp w of the tile's block owns an 8x4 pixel sub-tile (two columns of sub-tiles by
-// four rows).  When a batch of the tile list is staged, each thread marks which sub-tiles its
-// primitive's cutoff ellipse reaches; a warp then visits only the primitives marked for it.  The
-// test is conservative (rect_touched), so skipping is exact.
+// Forward.  The 16x16 tile is four 8x8 quadrants.  Warp w serves quadrant w & 3 and, of each
+// staged batch, the 32-entry chunks of parity w >> 2; lane l owns the two pixels (l & 7, l >> 3)
+// and (l & 7, (l >> 3) + 4) of its quadrant and evaluates both at once in packed f32x2
+// arithmetic.  When a batch is staged, each thread marks which quadrants its primitive's cutoff
+// ellipse reaches (exact in binary32, conservative) and stores the record with every value
+// duplicated, so that a warp reads ready-made pairs by broadcast.  A warp visits only the entries
+// marked for its quadrant.  Per pixel, the sum runs over the batch (a batch-local partial, added
+// once per batch), and at the end the two warps of a quadrant add their totals in a fixed order.
 __device__ __forceinline__ void blend2d_tile(const BlendJob& job, int tile) {
     const float4* __restrict__ rec = job.rec;
     const PixRect* __restrict__ rect = job.rect;
@@ -29,61 +33,94 @@ __device__ __forceinline__ void blend2d_tile(const BlendJob& job, int tile) {
     const int W = job.W, H = job.H, tiles_x = job.tiles_x;
     const float cutoff2 = job.o.cutoff2, lim = job.o.lim;
     float* __restrict__ out = job.out;
-    __shared__ float4 s_a[kTilePixels];  // mx my l11 l21
-    __shared__ float4 s_b[kTilePixels];  // l22 fx fy phc
-    __shared__ float4 s_c[kTilePixels];  // c_r c_g c_b o
+    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, 0), each value twice
+    __shared__ ulonglong2 s_e[6][kTilePixels];
     __shared__ uint8_t s_mask[kTilePixels];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int quad = warp & 3, half = warp >> 2;
     const int x0 = tx * kTile, y0 = ty * kTile;
-    const int u = x0 + (warp & 1) * 8 + (lane & 7);
-    const int v = y0 + (warp >> 1) * 4 + (lane >> 3);
-    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    const int u = x0 + (quad & 1) * 8 + (lane & 7);
+    const int v = y0 + (quad >> 1) * 8 + (lane >> 3);  // and v + 4
+    const f2 PX = f2_dup((float)u + 0.5f);
+    const f2 PY = f2_pack((float)v + 0.5f, (float)(v + 4) + 0.5f);
+    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
     const uint2 range = tl.ranges[tile];
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    f2 c0 = f2_dup(0.f), c1 = c0, c2 = c0;
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         __syncthreads();
         if ((int)threadIdx.x < n) {
-            float4 A, B, C;
-            s_mask[threadIdx.x] = (uint8_t)stage_entry(rec, rect, tl, b0 + threadIdx.x, x0, y0, lim, A, B, C);
-            s_a[threadIdx.x] = A;
-            s_b[threadIdx.x] = B;
-            s_c[threadIdx.x] = C;
+            const uint32_t prim = tl.prim[b0 + threadIdx.x];
+            const float4 A = rec[(size_t)prim * kRecF4 + 0];
+            const float4 B = rec[(size_t)prim * kRecF4 + 1];
+            const float4 C = rec[(size_t)prim * kRecF4 + 2];
+            s_mask[threadIdx.x] = (uint8_t)quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+            s_e[0][threadIdx.x] = dup2(A.x, A.y);
+            s_e[1][threadIdx.x] = dup2(A.z, A.w);
+            s_e[2][threadIdx.x] = dup2(B.x, B.y);
+            s_e[3][threadIdx.x] = dup2(B.z, B.w);
+            s_e[4][threadIdx.x] = dup2(C.x, C.y);
+            s_e[5][threadIdx.x] = dup2(C.z, 0.f);
         }
         __syncthreads();
-        // two-level summation: a batch-local partial sum per channel, added once per batch
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (int c = 0; c < n; c += 32) {
+        f2 a0 = f2_dup(0.f), a1 = a0, a2 = a0;
+        for (int c = half * 32; c < n; c += 64) {
             const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
-            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
+            uint32_t bal = __ballot_sync(0xffffffffu, (m >> quad) & 1u);
             while (bal) {
                 const int j = c + __ffs(bal) - 1;
                 bal &= bal - 1u;
-                const float4 A = s_a[j];
-                const float4 B = s_b[j];
-                const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-                if (q <= cutoff2) {
-                    const float dx = px - A.x, dy = py - A.y;
-                    const float G = ex2_approx(q * kNegHalfLog2e);
-                    const float t = fmaf(B.y, dx, fmaf(B.z, dy, B.w));
-                    const float wv = fmaf(0.5f, cos_approx(reduced_angle(t)), 0.5f) * G;
-                    const float4 C = s_c[j];
-                    a0 = fmaf(C.x, wv, a0);
-                    a1 = fmaf(C.y, wv, a1);
-                    a2 = fmaf(C.z, wv, a2);
-                }
+                const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]);
+                const f2x2 e2 = ld_f2x2(&s_e[2][j]), e3 = ld_f2x2(&s_e[3][j]);
+                // the cutoff test in the operation order of mahalanobis2()
+                const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
+                const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+                const f2 b = f2_mul(e2.x, dy);
+                const f2 q = f2_fma(a, a, f2_mul(b, b));
+                // outside the cutoff the envelope is taken as ex2(-inf) = 0, so the entry adds 0
+                const f2 e = f2_mul(q, K);
+                const float glo = ex2_approx(f2_lo(q) <= cutoff2 ? f2_lo(e) : -INFINITY);
+                const float ghi = ex2_approx(f2_hi(q) <= cutoff2 ? f2_hi(e) : -INFINITY);
+                const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+                const f2 cs = f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang)));
+                const f2 wv = f2_mul(f2_fma(HALF, cs, HALF), f2_pack(glo, ghi));
+                const f2x2 e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
+                a0 = f2_fma(e4.x, wv, a0);
+                a1 = f2_fma(e4.y, wv, a1);
+                a2 = f2_fma(e5.x, wv, a2);
             }
         }
-        c0 += a0;
-        c1 += a1;
-        c2 += a2;
+        c0 = f2_add(c0, a0);
+        c1 = f2_add(c1, a1);
+        c2 = f2_add(c2, a2);
     }
-    if (u < W && v < H) {
-        float* o = out + ((size_t)v * W + u) * 3;
-        o[0] = c0;
-        o[1] = c1;
-        o[2] = c2;
+    // the second warp of each quadrant hands its sums to the first
+    __syncthreads();
+    f2* s_sum = reinterpret_cast<f2*>(&s_e[0][0]);
+    const int slot = (quad * 32 + lane) * 3;
+    if (half == 1) {
+        s_sum[slot + 0] = c0;
+        s_sum[slot + 1] = c1;
+        s_sum[slot + 2] = c2;
+    }
+    __syncthreads();
+    if (half == 0) {
+        c0 = f2_add(c0, s_sum[slot + 0]);
+        c1 = f2_add(c1, s_sum[slot + 1]);
+        c2 = f2_add(c2, s_sum[slot + 2]);
+        if (u < W && v < H) {
+            float* o = out + ((size_t)v * W + u) * 3;
+            o[0] = f2_lo(c0);
+            o[1] = f2_lo(c1);
+            o[2] = f2_lo(c2);
+        }
+        if (u < W && v + 4 < H) {
+            float* o = out + ((size_t)(v + 4) * W + u) * 3;
+            o[0] = f2_hi(c0);
+            o[1] = f2_hi(c1);
+            o[2] = f2_hi(c2);
+        }
     }
 }
 

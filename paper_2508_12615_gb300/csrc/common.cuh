@@ -61,6 +61,79 @@ __device__ __forceinline__ float sin_approx(float x) {
 // Phase t given in cycles, reduced to an angle in [-pi, pi]: 2 pi (t - rint(t)).
 __device__ __forceinline__ float reduced_angle(float t) { return (t - rintf(t)) * kTwoPi; }
 
+// Packed pairs of binary32 values for sm_100-family f32x2 arithmetic: one instruction performs
+// the same correctly rounded operation on both halves, so a lane evaluates two pixels for the
+// issue cost of one.  Each result is bit-identical to the scalar operation (fma fused, add, sub
+// and mul rounded to nearest even).
+struct f2 {
+    unsigned long long r;
+};
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v.r) : "f"(lo), "f"(hi));
+    return v;
+}
+__device__ __forceinline__ f2 f2_dup(float x) { return f2_pack(x, x); }
+__device__ __forceinline__ float f2_lo(f2 v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v.r));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v.r));
+    return hi;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+// A staged pair of packed values (16 bytes, one shared-memory vector load).
+struct f2x2 {
+    f2 x, y;
+};
+__device__ __forceinline__ f2x2 ld_f2x2(const ulonglong2* p) {
+    const ulonglong2 v = *p;
+    return f2x2{f2{v.x}, f2{v.y}};
+}
+// The same load kept in place (not hoisted out of a loop): for values that are cheaper to read
+// again from shared memory than to hold in registers.
+__device__ __forceinline__ f2x2 ld_f2x2_here(const ulonglong2* p) {
+    f2x2 v;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(v.x.r), "=l"(v.y.r)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
+__device__ __forceinline__ ulonglong2 dup2(float a, float b) { return make_ulonglong2(f2_dup(a).r, f2_dup(b).r); }
+
+// Round to the nearest integer (ties to even) for |t| < 2^22 on the FMA pipe: adding 1.5 2^23
+// leaves no fraction bits, and the rounding of that addition is the rounding to an integer.
+// Phases are a few hundred cycles at most, far inside that range.
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+// Packed phase reduction: 2 pi (t - rint(t)) per half.
+__device__ __forceinline__ f2 f2_reduced_angle(f2 t) {
+    const f2 M = f2_dup(kRoundMagic);
+    const f2 r = f2_sub(f2_add(t, M), M);
+    return f2_mul(f2_sub(t, r), f2_dup(kTwoPi));
+}
+
 // Sum 16 per-lane values over the warp by recursive halving (reduce-scatter): 15 shuffles
 // instead of 80.  On return lane l holds the warp total of value (l >> 1).
 __device__ __forceinline__ float warp_reduce_scatter16(float v[16]) {
@@ -238,6 +311,19 @@ __device__ __forceinline__ uint32_t subtile_mask_ellipse(const float4& A4, float
 #pragma unroll 1
     for (int w = 0; w < 8; ++w)
         if (box_touched_ellipse(A4, l22, nBA, nBC, r, x0 + 8 * (w & 1), y0 + 4 * (w >> 1), 8, 4, lim)) m |= 1u << w;
+    return m;
+}
+
+// Which of the four 8x8 quadrants of the 16x16 tile at (x0, y0) the primitive's cutoff ellipse
+// reaches: bit k for columns 8 (k & 1) .. +7, rows 8 (k >> 1) .. +7.
+__device__ __forceinline__ uint32_t quadrant_mask_ellipse(const float4& A4, float l22, const PixRect& r, int x0,
+                                                          int y0, float lim) {
+    float nBA, nBC;
+    ellipse_edge_ratios(A4, l22, nBA, nBC);
+    uint32_t m = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k)
+        if (box_touched_ellipse(A4, l22, nBA, nBC, r, x0 + 8 * (k & 1), y0 + 8 * (k >> 1), 8, 8, lim)) m |= 1u << k;
     return m;
 }
 

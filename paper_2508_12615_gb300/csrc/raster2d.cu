@@ -18,40 +18,51 @@ __global__ void __launch_bounds__(kTilePixels) k_blend2d(BlendJob job) { pdl_ent
 // Partial gradient slot layout (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b 0
 constexpr int kSlot = 12;
 
-// Backward.  The tile's dL/dimage sits in shared memory; batches of the tile list are staged with
-// the mask of the 8x4 sub-blocks of the tile that each pair's cutoff ellipse reaches (the same
-// decomposition as the forward pass).  One warp takes one pair at a time and walks the marked
-// sub-blocks, one pixel per lane.  Per pixel inside the cutoff a lane accumulates the factored sums
+// Backward.  The tile's dL/dimage sits in shared memory, stored by pixel pairs in the layout of
+// the forward pass (quadrant k, lane l: pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the
+// 8x8 quadrant).  Batches of the tile list are staged with the mask of the quadrants that each
+// pair's cutoff ellipse reaches.  One warp takes one (tile, primitive) pair at a time and walks the
+// marked quadrants, two pixels per lane in packed f32x2 arithmetic.  Per pixel inside the cutoff a
+// lane accumulates the factored sums
 //   sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy, sum g W
 // (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
 // b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one warp
-// reduction, since L, f and the centre are constant over the pair.
-__global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __restrict__ rec,
+// reduction, since L, f and the centre are constant over the pair.  The sums are taken of
+// -ga, -gb and -gt / pi (one multiplication less per pixel) and scaled once per pair.
+__global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
                                                             int H, int tiles_x, float cutoff2, float lim,
                                                             const float* __restrict__ dl_dout,
                                                             float* __restrict__ partial) {
     pdl_enter();
-    __shared__ float4 s_g[kTilePixels];  // dL/dimage of the tile, one float4 per pixel (w unused)
-    __shared__ float4 s_a[kTilePixels];
-    __shared__ float4 s_b[kTilePixels];
-    __shared__ float4 s_c[kTilePixels];
+    __shared__ ulonglong2 s_g[2][kTilePixels / 2];  // (g_r, g_g) and (g_b, 0) pairs by pixel pair
+    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, 0), each value twice
+    __shared__ ulonglong2 s_e[6][kTilePixels];
     __shared__ uint32_t s_slot[kTilePixels];
     __shared__ uint8_t s_mask[kTilePixels];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    {
-        const int u = x0 + (threadIdx.x & (kTile - 1));
-        const int v = y0 + (threadIdx.x / kTile);
-        const bool in = u < W && v < H;
-        const float* g = dl_dout + ((size_t)v * W + u) * 3;
-        s_g[threadIdx.x] = in ? make_float4(g[0], g[1], g[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (threadIdx.x < kTilePixels / 2) {
+        const int k = threadIdx.x >> 5;
+        const int u = x0 + (k & 1) * 8 + (lane & 7);
+        const int v = y0 + (k >> 1) * 8 + (lane >> 3);
+        float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
+        if (u < W && v < H) {
+            const float* g = dl_dout + ((size_t)v * W + u) * 3;
+            g0[0] = g[0], g0[1] = g[1], g0[2] = g[2];
+        }
+        if (u < W && v + 4 < H) {
+            const float* g = dl_dout + ((size_t)(v + 4) * W + u) * 3;
+            g1[0] = g[0], g1[1] = g[1], g1[2] = g[2];
+        }
+        s_g[0][threadIdx.x] = make_ulonglong2(f2_pack(g0[0], g1[0]).r, f2_pack(g0[1], g1[1]).r);
+        s_g[1][threadIdx.x] = make_ulonglong2(f2_pack(g0[2], g1[2]).r, 0ull);
     }
-    // per-lane pixel of sub-block 0 (sub-block sb adds 8 (sb & 1) columns and 4 (sb >> 1) rows)
+    // the lane's pixels in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1) rows)
     const float lane_px = (float)(x0 + (lane & 7)) + 0.5f, lane_py = (float)(y0 + (lane >> 3)) + 0.5f;
-    const int lane_g = (lane >> 3) * kTile + (lane & 7);
+    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
     const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
@@ -61,56 +72,74 @@ __global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __r
             const uint32_t prim = tl.prim[b0 + threadIdx.x];
             const float4 A = rec[(size_t)prim * kRecF4 + 0];
             const float4 B = rec[(size_t)prim * kRecF4 + 1];
-            s_a[threadIdx.x] = A;
-            s_b[threadIdx.x] = B;
-            s_c[threadIdx.x] = rec[(size_t)prim * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+            const float4 C = rec[(size_t)prim * kRecF4 + 2];
+            s_e[0][threadIdx.x] = dup2(A.x, A.y);
+            s_e[1][threadIdx.x] = dup2(A.z, A.w);
+            s_e[2][threadIdx.x] = dup2(B.x, B.y);
+            s_e[3][threadIdx.x] = dup2(B.z, B.w);
+            s_e[4][threadIdx.x] = dup2(C.x, C.y);
+            s_e[5][threadIdx.x] = dup2(C.z, 0.f);
+            s_mask[threadIdx.x] = (uint8_t)quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
             s_slot[threadIdx.x] = e;
         }
         __syncthreads();
         for (int j = warp; j < n; j += kTilePixels / 32) {
-            const float4 A = s_a[j];  // mx my l11 l21
-            const float4 B = s_b[j];  // l22 fx fy phc
-            const float4 C = s_c[j];
             uint32_t mask = s_mask[j];
-            float acc[16];
+            f2 acc[11];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+            for (int i = 0; i < 11; ++i) acc[i] = f2_dup(0.f);
             while (mask) {
-                const int sb = __ffs(mask) - 1;
+                const int k = __ffs(mask) - 1;
                 mask &= mask - 1u;
                 // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
-                const float px = lane_px + (float)((sb & 1) * 8), py = lane_py + (float)((sb >> 1) * 4);
-                // the cutoff test in the same operation order as mahalanobis2()
-                const float dx = __fsub_rn(px, A.x), dy = __fsub_rn(py, A.y);
-                const float a = __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy));
-                const float b = __fmul_rn(B.x, dy);
-                const float q = __fmaf_rn(a, a, __fmul_rn(b, b));
-                if (q <= cutoff2) {
-                    const float G = ex2_approx(q * kNegHalfLog2e);
-                    const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
-                    const float cs = cos_approx(ang), sn = sin_approx(ang);
-                    const float Wv = fmaf(0.5f, cs, 0.5f) * G;
-                    const float4 g = s_g[lane_g + (sb >> 1) * 4 * kTile + (sb & 1) * 8];
-                    const float gW = fmaf(g.x, C.x, fmaf(g.y, C.y, g.z * C.z));
-                    const float gq2 = -gW * Wv;               // 2 dL/dq  (dW/dq = -W/2)
-                    const float gt = (-kPi * G) * (gW * sn);  // dL/dt, t in cycles
-                    const float ga = gq2 * a, gb = gq2 * b;
-                    acc[0] += ga;
-                    acc[1] += gb;
-                    acc[2] += gt;
-                    acc[3] = fmaf(ga, dx, acc[3]);
-                    acc[4] = fmaf(ga, dy, acc[4]);
-                    acc[5] = fmaf(gb, dy, acc[5]);
-                    acc[6] = fmaf(gt, dx, acc[6]);
-                    acc[7] = fmaf(gt, dy, acc[7]);
-                    acc[8] = fmaf(g.x, Wv, acc[8]);
-                    acc[9] = fmaf(g.y, Wv, acc[9]);
-                    acc[10] = fmaf(g.z, Wv, acc[10]);
-                }
+                const float px = lane_px + (float)((k & 1) * 8), py = lane_py + (float)((k >> 1) * 8);
+                // the cutoff test in the operation order of mahalanobis2()
+                // the pair's record, read again for each quadrant rather than held in registers
+                const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
+                const f2x2 e2 = ld_f2x2_here(&s_e[2][j]), e3 = ld_f2x2_here(&s_e[3][j]);
+                const f2 dx = f2_sub(f2_dup(px), e0.x), dy = f2_sub(f2_pack(py, py + 4.0f), e0.y);
+                const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+                const f2 b = f2_mul(e2.x, dy);
+                const f2 q = f2_fma(a, a, f2_mul(b, b));
+                // outside the cutoff the envelope is taken as ex2(-inf) = 0: every term below is 0
+                const f2 e = f2_mul(q, K);
+                const float glo = ex2_approx(f2_lo(q) <= cutoff2 ? f2_lo(e) : -INFINITY);
+                const float ghi = ex2_approx(f2_hi(q) <= cutoff2 ? f2_hi(e) : -INFINITY);
+                const f2 G = f2_pack(glo, ghi);
+                const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+                const float alo = f2_lo(ang), ahi = f2_hi(ang);
+                const f2 cs = f2_pack(cos_approx(alo), cos_approx(ahi));
+                const f2 sn = f2_pack(sin_approx(alo), sin_approx(ahi));
+                const f2 Wv = f2_mul(f2_fma(HALF, cs, HALF), G);
+                const f2x2 g01 = ld_f2x2(&s_g[0][k * 32 + lane]);
+                const f2 gb_ = ld_f2x2(&s_g[1][k * 32 + lane]).x;
+                const f2x2 e4 = ld_f2x2_here(&s_e[4][j]), e5 = ld_f2x2_here(&s_e[5][j]);
+                const f2 gW = f2_fma(g01.x, e4.x, f2_fma(g01.y, e4.y, f2_mul(gb_, e5.x)));
+                const f2 hq = f2_mul(gW, Wv);              // -2 dL/dq  (dW/dq = -W/2)
+                const f2 ht = f2_mul(G, f2_mul(gW, sn));  // -dL/dt / pi, t in cycles
+                const f2 ha = f2_mul(hq, a), hb = f2_mul(hq, b);
+                acc[0] = f2_add(acc[0], ha);
+                acc[1] = f2_add(acc[1], hb);
+                acc[2] = f2_add(acc[2], ht);
+                acc[3] = f2_fma(ha, dx, acc[3]);
+                acc[4] = f2_fma(ha, dy, acc[4]);
+                acc[5] = f2_fma(hb, dy, acc[5]);
+                acc[6] = f2_fma(ht, dx, acc[6]);
+                acc[7] = f2_fma(ht, dy, acc[7]);
+                acc[8] = f2_fma(g01.x, Wv, acc[8]);
+                acc[9] = f2_fma(g01.y, Wv, acc[9]);
+                acc[10] = f2_fma(gb_, Wv, acc[10]);
             }
+            // the lane's two pixels, then the sums of ga, gb, gt from the scaled ones
+            float sums[16];
+#pragma unroll
+            for (int i = 0; i < 11; ++i) sums[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
+#pragma unroll
+            for (int i = 11; i < 16; ++i) sums[i] = 0.f;
+            sums[0] = -sums[0], sums[1] = -sums[1], sums[3] = -sums[3], sums[4] = -sums[4], sums[5] = -sums[5];
+            sums[2] *= -kPi, sums[6] *= -kPi, sums[7] *= -kPi;
             // lane l holds the total of sum (l >> 1); lane l < 12 writes slot l of the pair
-            const float tot = warp_reduce_scatter16(acc);
+            const float tot = warp_reduce_scatter16(sums);
             const float sga = __shfl_sync(0xffffffffu, tot, 0);
             const float sgb = __shfl_sync(0xffffffffu, tot, 2);
             const float sgt = __shfl_sync(0xffffffffu, tot, 4);
@@ -118,8 +147,11 @@ __global__ void __launch_bounds__(kTilePixels, 5) k_backward2d(const float4* __r
             // fy <- gt dy (7), phc <- gt (2), colour 8..10
             const int src = lane == 7 ? 2 : (lane >= 2 && lane <= 6 ? lane + 1 : min(lane, 15));
             float val = __shfl_sync(0xffffffffu, tot, 2 * src);
-            if (lane == 0) val = -fmaf(A.z, sga, B.y * sgt);
-            if (lane == 1) val = -fmaf(A.w, sga, fmaf(B.x, sgb, B.z * sgt));
+            const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
+            const float l11 = f2_lo(e1.x), l21 = f2_lo(e1.y), l22 = f2_lo(e2.x), fx = f2_lo(e2.y);
+            const float fy = f2_lo(ld_f2x2(&s_e[3][j]).x);
+            if (lane == 0) val = -fmaf(l11, sga, fx * sgt);
+            if (lane == 1) val = -fmaf(l21, sga, fmaf(l22, sgb, fy * sgt));
             if (lane == 11) val = 0.f;
             if (lane < kSlot) partial[(size_t)s_slot[j] * kSlot + lane] = val;
         }

@@ -252,6 +252,20 @@ class Deform6D(torch.autograd.Function):
         return g6, None
 
 
+def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, state: State | None = None) -> None:
+    """Sort (key, value) pairs of 32-bit words in place, stably by the low ``key_bits`` bits of the
+    key, with the path's radix sort.  ``keys`` and ``vals``: contiguous int32 or uint32 device
+    tensors of the same length (the bits are taken as unsigned)."""
+    for name, t in (("keys", keys), ("vals", vals)):
+        if t.dtype not in (torch.int32, torch.uint32) or not t.is_cuda or not t.is_contiguous() or t.dim() != 1:
+            raise ValueError(f"{name} must be a contiguous 1-D int32/uint32 CUDA tensor")
+    if keys.numel() != vals.numel():
+        raise ValueError("keys and vals must have the same length")
+    st = state if state is not None else State(Context.get(keys.device))
+    _abi.call("wipes_sort_pairs", st.ctx.handle, st.handle, _ptr(keys), _ptr(vals), keys.numel(), int(key_bits),
+              _stream(keys.device.index))
+
+
 def deform_mlp_param_count() -> int:
     """Number of float32 parameters of the 6D deformation network."""
     return int(_abi.lib().wipes_deform_mlp_param_count())
