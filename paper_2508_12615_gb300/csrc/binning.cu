@@ -4,6 +4,8 @@
 //
 // Order contract: pairs are emitted in scan order (primitive index in 2D, front-to-back depth
 // order in 3D), and the sort is stable, so each tile's list is ordered by that scan order.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace wipes {
@@ -13,8 +15,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
 // Exclusive scan over a 256-thread block; returns the exclusive prefix and writes the block total.
-template <typename T>
-__device__ __forceinline__ T block_exclusive_scan(T x, T* total, T* s_warp /* [kWarps] */) {
+template <typename T, int NW = kWarps>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* total, T* s_warp /* [NW] */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T inc = x;
 #pragma unroll
@@ -26,7 +28,7 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* total, T* s_warp /* [k
     __syncthreads();
     T warp_base = 0, sum = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
         const T s = s_warp[w];
         if (w < warp) warp_base += s;
         sum += s;
@@ -162,7 +164,7 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
 // ---------------------------------------------------------------------------------------------
 // stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass, one kernel per
 // pass.  k_sort_histogram counts every pass's digits over all keys once.  In a pass, blocks take
-// tiles of 4096 keys in index order from a counter, rank their keys stably, publish each digit's
+// tiles of 8192 keys in index order from a counter, rank their keys stably, publish each digit's
 // count for their tile and obtain the counts of all earlier tiles by a decoupled look-back over
 // the published words (a word holds a tile's count, or the inclusive prefix up to that tile,
 // with a flag in its top bits).  Every look-back wait is bounded: when it runs out, the block
@@ -170,7 +172,9 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
 // ---------------------------------------------------------------------------------------------
 
 constexpr int kSortItems = 16;
-constexpr int kSortTile = kThreads * kSortItems;  // 4096 keys per block
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 8192 keys per block
 constexpr int kMaxRadix = 256;
 constexpr int kMaxPasses = 4;
 constexpr unsigned long long kAggregate = 1ull << 62, kPrefix = 2ull << 62, kCountMask = (1ull << 62) - 1ull;
@@ -241,88 +245,82 @@ __global__ void __launch_bounds__(kThreads) k_sort_histogram(const uint32_t* __r
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __restrict__ keys_in,
-                                                           const uint32_t* __restrict__ vals_in,
-                                                           uint32_t* __restrict__ keys_out,
-                                                           uint32_t* __restrict__ vals_out, int64_t n, int shift,
-                                                           int nbits, const uint32_t* __restrict__ totals,
-                                                           unsigned int* __restrict__ tile_counter,
-                                                           unsigned long long* __restrict__ status,
-                                                           unsigned int* __restrict__ error,
-                                                           const uint32_t* __restrict__ table,
-                                                           uint32_t* __restrict__ gathered) {
-    pdl_enter();
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_wc[kWarps][kMaxRadix];
-    __shared__ uint32_t s_cnt[kMaxRadix];
-    __shared__ uint32_t s_match[kWarps][kMaxRadix];
-    for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_match[0][0])[k] = 0u;
-    __shared__ uint32_t s_dstart[kMaxRadix];
-    __shared__ uint32_t s_gbase[kMaxRadix];
-    __shared__ uint32_t s_warp[kWarps];
-    __shared__ uint32_t s_tile;
-    const int radix = 1 << nbits;
+// Shared memory of k_sort_pass (dynamic, 16-byte aligned words): keys and values of the tile,
+// the per-warp digit counts, then the small per-digit arrays.  The two peer tables of the ranking
+// live in the key area, which is free until the keys are placed.
+constexpr int kSortSmemWords = 2 * kSortTile + kSortWarps * kMaxRadix + 3 * kMaxRadix + kSortWarps + 4;
+constexpr size_t kSortSmemBytes = sizeof(uint32_t) * kSortSmemWords;
+static_assert(2 * kSortWarps * kMaxRadix <= kSortTile, "the peer tables must fit in the key area");
+
+struct SortPassArgs {
+    const uint32_t* keys_in;
+    const uint32_t* vals_in;
+    uint32_t* keys_out;
+    uint32_t* vals_out;
+    int64_t n;
+    int shift, nbits;
+    const uint32_t* totals;
+    unsigned int* tile_counter;
+    unsigned long long* status;
+    unsigned int* error;
+    const uint32_t* table;  // optional: gathered[g] = table[value] for each placed pair
+    uint32_t* gathered;
+};
+
+// One tile of a pass.  FULL: the tile holds kSortTile keys (every tile but the last), so no
+// element needs a bounds check.  Item i of warp w's run is tile element w * 32 kSortItems + 32 i +
+// lane, so that a warp's loads and the element order of its ranking agree.
+template <bool FULL>
+__device__ __forceinline__ void sort_tile(const SortPassArgs& a, uint32_t tile, int cnt, uint32_t* s_keys,
+                                          uint32_t* s_vals, uint32_t (*s_wc)[kMaxRadix], uint32_t* s_cnt,
+                                          uint32_t* s_dstart, uint32_t* s_gbase, uint32_t* s_warp) {
+    const int radix = 1 << a.nbits;
     const uint32_t mask = (uint32_t)radix - 1u;
+    const int shift = a.shift;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-    for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_wc[0][0])[k] = 0u;
-    if ((int)threadIdx.x < kMaxRadix) s_cnt[threadIdx.x] = 0u;
-    // global start of each digit = exclusive scan of the digit totals
-    {
-        const uint32_t x = (int)threadIdx.x < radix ? totals[threadIdx.x] : 0u;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(x, nullptr, s_warp);
-        if ((int)threadIdx.x < radix) s_gbase[threadIdx.x] = ex;
-    }
-    __syncthreads();
-    const uint32_t tile = s_tile;
     const int64_t blk = (int64_t)tile * kSortTile;
-    const int64_t base = blk + (int64_t)warp * (kSortItems * 32);
-    const uint32_t lt = (1u << lane) - 1u;
-    // the keys wait in s_vals at their tile-local position (item i of warp w's run at
-    // w * 32 kSortItems + 32 i + lane) until they are placed; the values are read at the end
     const int run = warp * (kSortItems * 32) + lane;
-    uint32_t pos[kSortItems];
+    const uint32_t* keys_in = a.keys_in + blk;
+    auto valid = [&](int i) { return FULL || run + 32 * i < cnt; };
+    // the keys wait in s_vals at their element position until they are placed; the tile's digit
+    // counts are taken first so that later tiles can use them as early as possible
     {
         uint32_t k[kSortItems];
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const int64_t idx = base + i * 32 + lane;
-            k[i] = idx < n ? keys_in[idx] : 0u;
-        }
-        // the tile's digit counts first, so that later tiles can use them as early as possible
+        for (int i = 0; i < kSortItems; ++i) k[i] = valid(i) ? keys_in[run + 32 * i] : 0u;
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             s_vals[run + 32 * i] = k[i];
-            if (base + i * 32 + lane < n) atomicAdd(&s_cnt[(k[i] >> shift) & mask], 1u);
+            if (valid(i)) atomicAdd(&s_cnt[(k[i] >> shift) & mask], 1u);
         }
     }
     __syncthreads();
-    // publish the tile's digit counts at once, so that later tiles can use them as early as possible
-    unsigned long long* mine = status + (size_t)tile * kMaxRadix + threadIdx.x;
+    unsigned long long* mine = a.status + (size_t)tile * kMaxRadix + threadIdx.x;
     const uint32_t running = (int)threadIdx.x < radix ? s_cnt[threadIdx.x] : 0u;
     if ((int)threadIdx.x < radix) store_word(mine, (tile == 0 ? kPrefix : kAggregate) | running);
-    // stable rank within the warp's run, in element order (item i, then lane)
+    // stable rank within the warp's run, in element order (item i, then lane).  The lanes of an
+    // item with the same digit find each other through the warp's peer table: each sets its bit in
+    // the digit's word and reads the word back; the last of them then clears it and advances the
+    // digit's running count.  Items alternate between two tables, so a table word is cleared a full
+    // item before it is used again.
+    uint32_t(*s_peer)[kSortWarps][kMaxRadix] = reinterpret_cast<uint32_t(*)[kSortWarps][kMaxRadix]>(s_keys);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t pos[kSortItems];
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const int64_t idx = base + i * 32 + lane;
-        const bool valid = idx < n;
-        const uint32_t d = valid ? (s_vals[run + 32 * i] >> shift) & mask : 0xFFFFu;
-        // the lanes of this item with the same digit: each sets its bit in the digit's word of the
-        // warp's peer table, reads the word back, and the last of them clears it
-        if (valid) atomicOr(&s_match[warp][d], 1u << lane);
+        const bool ok = valid(i);
+        const uint32_t d = (s_vals[run + 32 * i] >> shift) & mask;
+        uint32_t* peer = &s_peer[i & 1][warp][d];
+        if (ok) atomicOr(peer, 1u << lane);
         __syncwarp();
-        const uint32_t peers = valid ? s_match[warp][d] : 0u;
+        const uint32_t peers = ok ? *peer : 0u;
+        const uint32_t before = s_wc[warp][d];
         __syncwarp();
-        if (valid && lane == 31 - __clz(peers)) s_match[warp][d] = 0u;
-        uint32_t before = 0;
-        if (valid) before = s_wc[warp][d];
-        __syncwarp();
-        if (valid) {
-            pos[i] = before + __popc(peers & lt);
-            if (lane == 31 - __clz(peers)) s_wc[warp][d] = before + __popc(peers);
+        pos[i] = before + __popc(peers & lt);
+        if (ok && lane == 31 - __clz(peers)) {
+            *peer = 0u;
+            s_wc[warp][d] = before + __popc(peers);
         }
-        __syncwarp();
     }
     __syncthreads();
     // per digit: prefix over warps, then the counts of all earlier tiles (look-back)
@@ -330,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __res
         const int d = threadIdx.x;
         uint32_t acc = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
+        for (int w = 0; w < kSortWarps; ++w) {
             const uint32_t t = s_wc[w][d];
             s_wc[w][d] = acc;
             acc += t;
@@ -344,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __res
                 unsigned long long w[kLookback];
 #pragma unroll
                 for (int j = 0; j < kLookback; ++j)
-                    w[j] = t - j >= 0 ? load_word(status + (size_t)(t - j) * kMaxRadix + d) : kPrefix;
+                    w[j] = t - j >= 0 ? load_word(a.status + (size_t)(t - j) * kMaxRadix + d) : kPrefix;
                 bool done = false;
                 int used = 0;
 #pragma unroll
@@ -362,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __res
                 t -= used;
                 if (used == 0) {
                     if (++polls > kMaxLookbackPolls) {
-                        atomicOr(error, 1u);
+                        atomicOr(a.error, 1u);
                         break;
                     }
                     if (polls > 64) __nanosleep(128);
@@ -373,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __res
         s_gbase[d] += (uint32_t)before;
     }
     {
-        const uint32_t ex = block_exclusive_scan<uint32_t>(running, nullptr, s_warp);
+        const uint32_t ex = block_exclusive_scan<uint32_t, kSortWarps>(running, nullptr, s_warp);
         if ((int)threadIdx.x < radix) {
             s_dstart[threadIdx.x] = ex;
             s_gbase[threadIdx.x] -= ex;
@@ -384,8 +382,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __res
     // occupy no registers during the ranking)
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const int64_t idx = base + i * 32 + lane;
-        if (idx < n) {
+        if (valid(i)) {
             const uint32_t key = s_vals[run + 32 * i];
             const uint32_t d = (key >> shift) & mask;
             pos[i] += s_dstart[d] + s_wc[warp][d];
@@ -393,29 +390,57 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(const uint32_t* __res
         }
     }
     {
+        const uint32_t* vals_in = a.vals_in + blk;
         uint32_t v[kSortItems];
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const int64_t idx = base + i * 32 + lane;
-            v[i] = idx < n ? vals_in[idx] : 0u;
-        }
+        for (int i = 0; i < kSortItems; ++i) v[i] = valid(i) ? vals_in[run + 32 * i] : 0u;
         __syncthreads();  // every key has left s_vals
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i)
-            if (base + i * 32 + lane < n) s_vals[pos[i]] = v[i];
+            if (valid(i)) s_vals[pos[i]] = v[i];
     }
     __syncthreads();
-    const int cnt = (int)min((int64_t)kSortTile, n - blk);
-    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+    const int64_t n = a.n;
+    for (int t = threadIdx.x; t < (FULL ? kSortTile : cnt); t += kSortThreads) {
         const uint32_t key = s_keys[t];
-        const uint32_t d = (key >> shift) & mask;
-        const uint32_t g = s_gbase[d] + (uint32_t)t;
+        const uint32_t g = s_gbase[(key >> shift) & mask] + (uint32_t)t;
         if ((int64_t)g >= n) continue;  // only after a look-back that ran out (error word set)
         const uint32_t val = s_vals[t];
-        keys_out[g] = key;
-        vals_out[g] = val;
-        if (table) gathered[g] = table[val];
+        a.keys_out[g] = key;
+        a.vals_out[g] = val;
+        if (a.table) a.gathered[g] = a.table[val];
     }
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(const __grid_constant__ SortPassArgs a) {
+    pdl_enter();
+    extern __shared__ uint4 s_sort_raw[];
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_sort_raw);
+    uint32_t* s_vals = s_keys + kSortTile;
+    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kSortTile);
+    uint32_t* s_cnt = s_vals + kSortTile + kSortWarps * kMaxRadix;
+    uint32_t* s_dstart = s_cnt + kMaxRadix;
+    uint32_t* s_gbase = s_dstart + kMaxRadix;
+    uint32_t* s_warp = s_gbase + kMaxRadix;
+    uint32_t* s_tile_p = s_warp + kSortWarps;
+    const int radix = 1 << a.nbits;
+    if (threadIdx.x == 0) *s_tile_p = atomicAdd(a.tile_counter, 1u);
+    for (int k = threadIdx.x; k < 2 * kSortWarps * kMaxRadix; k += kSortThreads) s_keys[k] = 0u;  // peer tables
+    for (int k = threadIdx.x; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_wc[0][0])[k] = 0u;
+    if ((int)threadIdx.x < kMaxRadix) s_cnt[threadIdx.x] = 0u;
+    // global start of each digit = exclusive scan of the digit totals
+    {
+        const uint32_t x = (int)threadIdx.x < radix ? a.totals[threadIdx.x] : 0u;
+        const uint32_t ex = block_exclusive_scan<uint32_t, kSortWarps>(x, nullptr, s_warp);
+        if ((int)threadIdx.x < radix) s_gbase[threadIdx.x] = ex;
+    }
+    __syncthreads();
+    const uint32_t tile = *s_tile_p;
+    const int64_t left = a.n - (int64_t)tile * kSortTile;
+    if (left >= kSortTile)
+        sort_tile<true>(a, tile, kSortTile, s_keys, s_vals, s_wc, s_cnt, s_dstart, s_gbase, s_warp);
+    else
+        sort_tile<false>(a, tile, (int)left, s_keys, s_vals, s_wc, s_cnt, s_dstart, s_gbase, s_warp);
 }
 
 // Order of the tiles for the blend kernels, longest list first: tiles are bucketed by the bit
@@ -502,6 +527,15 @@ int64_t radix_hist_words(int64_t n) {
     return sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
 }
 
+// The pass kernel's shared memory is above the 48 KB default: raise its limit once per process
+// (the attribute is per device; the library uses the device that is current at its first sort).
+void sort_pass_attributes() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmemBytes);
+    });
+}
+
 int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, uint32_t* hist, unsigned int* error,
                      cudaStream_t stream, const uint32_t* table, uint32_t* gathered) {
     if (n <= 1 || bits <= 0) {
@@ -515,6 +549,7 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         plan.shift[p] = shift;
         shift += plan.nbits[p];
     }
+    sort_pass_attributes();
     const int64_t tiles = ceil_div(n, kSortTile);
     uint32_t* totals = hist;
     unsigned int* counters = hist + (int64_t)kMaxPasses * kMaxRadix;
@@ -527,10 +562,10 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
     int cur = 0;
     for (int p = 0; p < plan.passes; ++p) {
         const bool last_pass = p == plan.passes - 1;
-        launch_pdl(k_sort_pass, (unsigned)tiles, kThreads, 0, stream, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
-                   plan.shift[p], plan.nbits[p], totals + p * kMaxRadix, counters + p,
-                   status + (size_t)p * tiles * kMaxRadix, error, last_pass ? table : nullptr,
-                   last_pass ? gathered : nullptr);
+        SortPassArgs pa{keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, plan.shift[p], plan.nbits[p],
+                        totals + p * kMaxRadix, counters + p, status + (size_t)p * tiles * kMaxRadix, error,
+                        last_pass ? table : nullptr, last_pass ? gathered : nullptr};
+        launch_pdl(k_sort_pass, (unsigned)tiles, kSortThreads, kSortSmemBytes, stream, pa);
         count_launches(1);
         cur ^= 1;
     }
@@ -553,8 +588,9 @@ void sort_timeout_probe(uint32_t* ws, unsigned int* error, cudaStream_t stream) 
     cudaMemsetAsync(ws, 0, sizeof(uint32_t) * (size_t)sort_timeout_probe_words(), stream);
     // the pass's counter starts at 1: the single block takes tile 1 and tile 0 is never published
     cudaMemsetAsync(counter, 1, 1, stream);
-    launch_pdl(k_sort_pass, 1u, kThreads, 0, stream, keys_in, vals_in, keys_out, vals_out, n, 0, 8, hist, counter,
-               status, error, (const uint32_t*)nullptr, (uint32_t*)nullptr);
+    sort_pass_attributes();
+    SortPassArgs pa{keys_in, vals_in, keys_out, vals_out, n, 0, 8, hist, counter, status, error, nullptr, nullptr};
+    launch_pdl(k_sort_pass, 1u, kSortThreads, kSortSmemBytes, stream, pa);
     count_launches(1);
 }
 

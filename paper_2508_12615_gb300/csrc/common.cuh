@@ -74,16 +74,8 @@ __device__ __forceinline__ f2 f2_pack(float lo, float hi) {
     return v;
 }
 __device__ __forceinline__ f2 f2_dup(float x) { return f2_pack(x, x); }
-__device__ __forceinline__ float f2_lo(f2 v) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v.r));
-    return lo;
-}
-__device__ __forceinline__ float f2_hi(f2 v) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v.r));
-    return hi;
-}
+__device__ __forceinline__ float f2_lo(f2 v) { return __uint_as_float((unsigned)(v.r & 0xffffffffull)); }
+__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((unsigned)(v.r >> 32)); }
 __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
     f2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
