@@ -162,8 +162,10 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass, one kernel per
-// pass.  k_sort_histogram counts every pass's digits over all keys once.  In a pass, blocks take
+// stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass, in one of two
+// schemes that rank a tile of 8192 keys the same way (radix_sort_pairs picks one per call).
+// Onesweep, one kernel per pass: k_sort_histogram counts every pass's digits over all keys once.
+// In a pass, blocks take
 // tiles of 8192 keys in index order from a counter, rank their keys stably, publish each digit's
 // count for their tile and obtain the counts of all earlier tiles by a decoupled look-back over
 // the published words (a word holds a tile's count, or the inclusive prefix up to that tile,
@@ -522,9 +524,222 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
     launch_pdl(k_iota, grid, 256, 0, stream, v, n); count_launches(1);
 }
 
+// ---------------------------------------------------------------------------------------------
+// The same sort by reduce-then-scan, with no wait between blocks.  The input is cut into chunks of
+// whole tiles, one chunk per block of the last kernel (two blocks per SM).  Per pass:
+//   k_sort_upsweep     block c counts the digits of chunk c;
+//   k_sort_chunk_scan  block d scans digit d's counts over the chunks: the digit's count in all
+//                      earlier chunks, and its total;
+//   k_sort_downsweep   block c walks chunk c tile by tile: it ranks each tile stably in shared
+//                      memory and writes each pair to (digits below d overall) + (digit d in
+//                      earlier chunks) + (digit d earlier in this chunk) + its rank in the tile.
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kChunkBlocksPerSm = 2;
+constexpr int64_t kOnesweepMaxKeys = (int64_t)1 << 22;  // onesweep only below this many keys (and > 2 passes)
+
+// Chunks and whole tiles per chunk for n keys.
+int sort_chunks(int64_t n, int* tiles_per_chunk) {
+    const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kSortTile);
+    const int64_t target = std::min<int64_t>(tiles, (int64_t)152 * kChunkBlocksPerSm);
+    const int64_t tpc = ceil_div(tiles, target);
+    *tiles_per_chunk = (int)tpc;
+    return (int)ceil_div(tiles, tpc);
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                           int nbits, int64_t chunk_keys, int chunks,
+                                                           uint32_t* __restrict__ counts /* [radix][chunks] */) {
+    pdl_enter();
+    __shared__ uint32_t s_cnt[kWarps][kMaxRadix];
+    for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_cnt[0][0])[k] = 0u;
+    __syncthreads();
+    uint32_t* my = s_cnt[threadIdx.x >> 5];
+    const uint32_t mask = (1u << nbits) - 1u;
+    const int64_t lo = (int64_t)blockIdx.x * chunk_keys, hi = min(n, lo + chunk_keys);
+    if ((reinterpret_cast<uintptr_t>(keys + lo) & 15u) == 0) {
+        const uint4* k4 = reinterpret_cast<const uint4*>(keys + lo);
+        const int64_t q4 = (hi - lo) >> 2;
+#pragma unroll 4
+        for (int64_t q = threadIdx.x; q < q4; q += kThreads) {
+            const uint4 v = k4[q];
+            atomicAdd(&my[(v.x >> shift) & mask], 1u);
+            atomicAdd(&my[(v.y >> shift) & mask], 1u);
+            atomicAdd(&my[(v.z >> shift) & mask], 1u);
+            atomicAdd(&my[(v.w >> shift) & mask], 1u);
+        }
+        for (int64_t i = lo + (q4 << 2) + threadIdx.x; i < hi; i += kThreads) atomicAdd(&my[(keys[i] >> shift) & mask], 1u);
+    } else {
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) atomicAdd(&my[(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < (1 << nbits); d += kThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) sum += s_cnt[w][d];
+        counts[(size_t)d * chunks + blockIdx.x] = sum;
+    }
+}
+
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_sort_chunk_scan(const uint32_t* __restrict__ counts, int chunks,
+                                                                  uint32_t* __restrict__ bases,
+                                                                  uint32_t* __restrict__ totals) {
+    pdl_enter();
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    const int d = blockIdx.x;
+    uint32_t run = 0;
+    for (int c0 = 0; c0 < chunks; c0 += kScanThreads) {
+        const int c = c0 + threadIdx.x;
+        const uint32_t x = c < chunks ? counts[(size_t)d * chunks + c] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<uint32_t, kScanThreads / 32>(x, &total, s_warp);
+        if (c < chunks) bases[(size_t)d * chunks + c] = run + ex;
+        run += total;
+    }
+    if (threadIdx.x == 0) totals[d] = run;
+}
+
+struct SortDownArgs {
+    const uint32_t* keys_in;
+    const uint32_t* vals_in;
+    uint32_t* keys_out;
+    uint32_t* vals_out;
+    int64_t n;
+    int shift, nbits;
+    int chunks, tiles_per_chunk;
+    const uint32_t* bases;   // [radix][chunks]: the digit's count in earlier chunks
+    const uint32_t* totals;  // [radix]
+    const uint32_t* table;   // optional: gathered[g] = table[value] for each placed pair
+    uint32_t* gathered;
+};
+
+// One tile of a chunk (see sort_tile for the element layout and the ranking).  s_base[d]: where
+// the chunk's next digit-d pair goes.
+template <bool FULL>
+__device__ __forceinline__ void down_tile(const SortDownArgs& a, int64_t tile, int cnt, uint32_t* s_keys,
+                                          uint32_t* s_vals, uint32_t (*s_wc)[kMaxRadix], uint32_t* s_dstart,
+                                          uint32_t* s_base, uint32_t* s_gofs, uint32_t* s_warp) {
+    const int radix = 1 << a.nbits;
+    const uint32_t mask = (uint32_t)radix - 1u;
+    const int shift = a.shift;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t blk = tile * kSortTile;
+    const int run = warp * (kSortItems * 32) + lane;
+    auto valid = [&](int i) { return FULL || run + 32 * i < cnt; };
+    uint32_t(*s_peer)[kSortWarps][kMaxRadix] = reinterpret_cast<uint32_t(*)[kSortWarps][kMaxRadix]>(s_keys);
+    for (int k = threadIdx.x; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_wc[0][0])[k] = 0u;
+    for (int k = threadIdx.x; k < 2 * kSortWarps * kMaxRadix; k += kSortThreads) s_keys[k] = 0u;
+    {
+        const uint32_t* keys_in = a.keys_in + blk;
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) s_vals[run + 32 * i] = valid(i) ? keys_in[run + 32 * i] : 0u;
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t pos[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const bool ok = valid(i);
+        const uint32_t d = (s_vals[run + 32 * i] >> shift) & mask;
+        uint32_t* peer = &s_peer[i & 1][warp][d];
+        if (ok) atomicOr(peer, 1u << lane);
+        __syncwarp();
+        const uint32_t peers = ok ? *peer : 0u;
+        const uint32_t before = s_wc[warp][d];
+        __syncwarp();
+        pos[i] = before + __popc(peers & lt);
+        if (ok && lane == 31 - __clz(peers)) {
+            *peer = 0u;
+            s_wc[warp][d] = before + __popc(peers);
+        }
+    }
+    __syncthreads();
+    uint32_t count = 0;
+    if ((int)threadIdx.x < radix) {
+        const int d = threadIdx.x;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t t = s_wc[w][d];
+            s_wc[w][d] = count;
+            count += t;
+        }
+    }
+    {
+        const uint32_t ex = block_exclusive_scan<uint32_t, kSortWarps>(count, nullptr, s_warp);
+        if ((int)threadIdx.x < radix) {
+            s_dstart[threadIdx.x] = ex;
+            s_gofs[threadIdx.x] = s_base[threadIdx.x] - ex;
+            s_base[threadIdx.x] += count;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        if (valid(i)) {
+            const uint32_t key = s_vals[run + 32 * i];
+            const uint32_t d = (key >> shift) & mask;
+            pos[i] += s_dstart[d] + s_wc[warp][d];
+            s_keys[pos[i]] = key;
+        }
+    }
+    {
+        const uint32_t* vals_in = a.vals_in + blk;
+        uint32_t v[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) v[i] = valid(i) ? vals_in[run + 32 * i] : 0u;
+        __syncthreads();  // every key has left s_vals
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i)
+            if (valid(i)) s_vals[pos[i]] = v[i];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < (FULL ? kSortTile : cnt); t += kSortThreads) {
+        const uint32_t key = s_keys[t];
+        const uint32_t g = s_gofs[(key >> shift) & mask] + (uint32_t)t;
+        const uint32_t val = s_vals[t];
+        a.keys_out[g] = key;
+        a.vals_out[g] = val;
+        if (a.table) a.gathered[g] = a.table[val];
+    }
+    __syncthreads();  // the tile's buffers are free for the next tile
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort_downsweep(const __grid_constant__ SortDownArgs a) {
+    pdl_enter();
+    extern __shared__ uint4 s_sort_raw[];
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_sort_raw);
+    uint32_t* s_vals = s_keys + kSortTile;
+    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kSortTile);
+    uint32_t* s_dstart = s_vals + kSortTile + kSortWarps * kMaxRadix;
+    uint32_t* s_base = s_dstart + kMaxRadix;
+    uint32_t* s_gofs = s_base + kMaxRadix;
+    uint32_t* s_warp = s_gofs + kMaxRadix;
+    const int radix = 1 << a.nbits;
+    // where this chunk's first pair of each digit goes
+    {
+        const uint32_t x = (int)threadIdx.x < radix ? a.totals[threadIdx.x] : 0u;
+        const uint32_t ex = block_exclusive_scan<uint32_t, kSortWarps>(x, nullptr, s_warp);
+        if ((int)threadIdx.x < radix) s_base[threadIdx.x] = ex + a.bases[(size_t)threadIdx.x * a.chunks + blockIdx.x];
+    }
+    __syncthreads();
+    const int64_t tiles = (a.n + kSortTile - 1) / kSortTile;
+    const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_chunk, t1 = min(tiles, t0 + a.tiles_per_chunk);
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t left = a.n - tile * kSortTile;
+        if (left >= kSortTile)
+            down_tile<true>(a, tile, kSortTile, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
+        else
+            down_tile<false>(a, tile, (int)left, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
+    }
+}
+
 int64_t radix_hist_words(int64_t n) {
     const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kSortTile);
-    return sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
+    const int64_t onesweep = sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
+    int tpc = 0;
+    const int64_t chunked = 2 * (int64_t)kMaxRadix * sort_chunks(n, &tpc) + kMaxRadix;
+    return std::max(onesweep, chunked);
 }
 
 // The pass kernel's shared memory is above the 48 KB default: raise its limit once per process
@@ -533,6 +748,7 @@ void sort_pass_attributes() {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmemBytes);
+        cudaFuncSetAttribute(k_sort_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmemBytes);
     });
 }
 
@@ -550,6 +766,30 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         shift += plan.nbits[p];
     }
     sort_pass_attributes();
+    // Reduce-then-scan costs three launches per pass, onesweep one (plus one histogram): for a
+    // short sort of many passes the launches dominate and onesweep is the faster of the two;
+    // otherwise reduce-then-scan, which never waits on another block, is.
+    if (plan.passes <= 2 || n >= kOnesweepMaxKeys) {
+        int tpc = 0;
+        const int chunks = sort_chunks(n, &tpc);
+        uint32_t* counts = hist;
+        uint32_t* bases = hist + (size_t)kMaxRadix * chunks;
+        uint32_t* totals = bases + (size_t)kMaxRadix * chunks;
+        int cur = 0;
+        for (int p = 0; p < plan.passes; ++p) {
+            const bool last_pass = p == plan.passes - 1;
+            launch_pdl(k_sort_upsweep, (unsigned)chunks, kThreads, 0, stream, (const uint32_t*)keys[cur], n, plan.shift[p],
+                       plan.nbits[p], (int64_t)tpc * kSortTile, chunks, counts);
+            launch_pdl(k_sort_chunk_scan, (unsigned)(1 << plan.nbits[p]), kScanThreads, 0, stream, (const uint32_t*)counts,
+                       chunks, bases, totals);
+            SortDownArgs da{keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, plan.shift[p], plan.nbits[p], chunks,
+                            tpc, bases, totals, last_pass ? table : nullptr, last_pass ? gathered : nullptr};
+            launch_pdl(k_sort_downsweep, (unsigned)chunks, kSortThreads, kSortSmemBytes, stream, da);
+            count_launches(3);
+            cur ^= 1;
+        }
+        return cur;
+    }
     const int64_t tiles = ceil_div(n, kSortTile);
     uint32_t* totals = hist;
     unsigned int* counters = hist + (int64_t)kMaxPasses * kMaxRadix;
