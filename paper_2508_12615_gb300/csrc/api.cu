@@ -42,6 +42,18 @@ wipes_status fail(wipes_status s, const std::string& msg) {
 struct MemAccount {
     std::atomic<int64_t> reserved{0};
     std::atomic<int64_t> limit{0};  // 0: no limit
+    cudaMemPool_t pool = nullptr;   // stream-ordered pool of the context's workspace buffers
+};
+
+// Workspace buffers come from the context's memory pool in stream order, on the stream of the call
+// that grows them (set by AllocStream at the entry points): a new state costs no cudaMalloc.
+// Frees wait for the whole device first, as cudaFree does, because a buffer may be in use by work
+// on any stream.
+thread_local cudaStream_t t_alloc_stream = nullptr;
+struct AllocStream {
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+    ~AllocStream() { t_alloc_stream = prev; }
 };
 
 // Grow-only device buffer, accounted to its context.
@@ -52,6 +64,20 @@ struct DevBuf {
     template <typename T>
     T* as() const { return static_cast<T*>(p); }
 };
+
+void free_buf(DevBuf& b, bool device_idle = false) {
+    if (b.p) {
+        if (b.acct && b.acct->pool) {
+            if (!device_idle) cudaDeviceSynchronize();
+            cudaFreeAsync(b.p, nullptr);
+        } else {
+            cudaFree(b.p);
+        }
+    }
+    if (b.acct) b.acct->reserved -= (int64_t)b.cap;
+    b.p = nullptr;
+    b.cap = 0;
+}
 
 wipes_status ensure(DevBuf& b, size_t bytes) {
     if (bytes <= b.cap) return WIPES_OK;
@@ -65,11 +91,9 @@ wipes_status ensure(DevBuf& b, size_t bytes) {
                                            std::to_string(b.acct->reserved.load()) + " reserved, " +
                                            std::to_string(want) + " more wanted)");
     }
-    if (b.p) cudaFree(b.p);
-    if (b.acct) b.acct->reserved -= (int64_t)b.cap;
-    b.p = nullptr;
-    b.cap = 0;
-    cudaError_t e = cudaMalloc(&b.p, want);
+    free_buf(b);
+    cudaError_t e = b.acct && b.acct->pool ? cudaMallocFromPoolAsync(&b.p, want, b.acct->pool, t_alloc_stream)
+                                           : cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
@@ -80,12 +104,7 @@ wipes_status ensure(DevBuf& b, size_t bytes) {
     return WIPES_OK;
 }
 
-void release(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
-    if (b.acct) b.acct->reserved -= (int64_t)b.cap;
-    b.p = nullptr;
-    b.cap = 0;
-}
+void release(DevBuf& b, bool device_idle = false) { free_buf(b, device_idle); }
 
 int ceil_log2(int64_t x) {
     int b = 0;
@@ -379,8 +398,20 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_loss_partials, sizeof(float) * kLossBlocks);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_batch_counters, sizeof(unsigned int) * kBatchCounterSlots);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&c->mem.pool, &props);
+        // keep freed workspace for reuse instead of returning it to the driver at every sync (a
+        // trim of many GB stalls the device); the pool holds at most the largest workspace reached
+        uint64_t keep = ~(uint64_t)0;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(c->mem.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     if (e != cudaSuccess) {
         if (c->h_total) cudaFreeHost(c->h_total);
+        if (c->mem.pool) cudaMemPoolDestroy(c->mem.pool);
         delete c;
         return fail(WIPES_ERR_CUDA, std::string("context allocation failed: ") + cudaGetErrorString(e));
     }
@@ -406,6 +437,7 @@ wipes_status wipes_destroy(wipes_ctx* ctx) {
     cudaFree(ctx->d_error);
     mlp_lt_destroy(ctx->mlp);
     cudaFree(ctx->d_batch_counters);
+    if (ctx->mem.pool) cudaMemPoolDestroy(ctx->mem.pool);
     delete ctx;
     return WIPES_OK;
 }
@@ -425,7 +457,8 @@ wipes_status wipes_state_destroy(wipes_state* st) {
     wipes_ctx* ctx = st->ctx;
     {
         DeviceGuard g(ctx->device);
-        for (DevBuf* b : st->all) release(*b);
+        cudaDeviceSynchronize();  // once for all buffers of the state
+        for (DevBuf* b : st->all) release(*b, true);
     }
     delete st;
     ctx->live_states -= 1;
@@ -441,6 +474,7 @@ wipes_status wipes_prepare2d(wipes_ctx* ctx, wipes_state* st, const float* param
     if (((uintptr_t)params & 15) != 0) return fail(WIPES_ERR_INVALID, "params must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     WIPES_TRY(prepare_state(st, 2, N, H, W, opts));
     {
         StageTimer t(ctx, WIPES_STAGE_FOOTPRINT, s);
@@ -459,6 +493,7 @@ wipes_status wipes_render2d(wipes_ctx* ctx, wipes_state* st, const float* params
     WIPES_TRY(wipes_prepare2d(ctx, st, params, N, H, W, opts, stream));
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
         launch_blend2d(st->job(out), st->tiles_y, s);
@@ -478,6 +513,7 @@ wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* param
         return fail(WIPES_ERR_INVALID, "camera needs fx, fy, near_z > 0");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     WIPES_TRY(prepare_state(st, 3, N, H, W, opts));
     st->cam = *cam;
     const size_t n = (size_t)std::max<int64_t>(N, 1);
@@ -522,6 +558,7 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
     WIPES_TRY(wipes_prepare3d(ctx, st, params, N, cam, H, W, opts, stream));
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
         launch_blend3d(st->job(out), st->tiles_y, st->order.as<uint32_t>(), s);
@@ -564,6 +601,7 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
     if (st->dims != 2 && st->dims != 3) return fail(WIPES_ERR_INVALID, "state holds no forward pass");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     const int64_t N = st->N;
     if (st->dims == 2) {
         WIPES_TRY(ensure(st->partial, sizeof(float) * 12 * (size_t)std::max<int64_t>(st->n_inst, 1)));
@@ -601,6 +639,7 @@ wipes_status wipes_sort_pairs(wipes_ctx* ctx, wipes_state* st, uint32_t* keys, u
     if (n <= 1) return WIPES_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     WIPES_TRY(ensure(st->sort_k, sizeof(uint32_t) * (size_t)n));
     WIPES_TRY(ensure(st->sort_v, sizeof(uint32_t) * (size_t)n));
     WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(n)));
@@ -794,6 +833,7 @@ wipes_status wipes_deform_mlp(wipes_ctx* ctx, wipes_state* st, const float* para
         return fail(WIPES_ERR_INVALID, "params3, theta and params_out must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     {
         std::lock_guard<std::mutex> lk(ctx->mlp_mu);
         if (!ctx->mlp) {
@@ -824,6 +864,7 @@ wipes_status wipes_deform_mlp_backward(wipes_ctx* ctx, wipes_state* st, const fl
     if (N > 0 && (!params3 || !dL_dout || !dL_dparams3)) return fail(WIPES_ERR_INVALID, "null argument");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    AllocStream alloc_stream(s);
     const MlpSizes z = mlp_sizes(std::max<int64_t>(N, 1));
     WIPES_TRY(ensure(st->mlp_scratch, z.scratch));
     if (N == 0) {
