@@ -39,7 +39,7 @@ OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend":
 # DRAM bytes (read + write) per launch, per (workload, kernel), from the ncu captures summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
 # entry is removed when its kernel changes.
-TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_434_368 + 409_856, ("2d", "k_blend2d"): 9_051_904,
+TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_395_712 + 587_008, ("2d", "k_blend2d"): 9_052_928,
                  ("5d", "k_backward3d"): 34_066_432 + 19_456, ("5d", "k_blend3d"): 16_343_808 + 5_120}
 
 
