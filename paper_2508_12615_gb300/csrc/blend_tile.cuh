@@ -218,73 +218,110 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
     if (inside) store_px3(job, u, v, s);
 }
 
-// Forward over one 8x8 quad of a 16x16 tile, for blocks of kQuadThreads (two warps; warp k owns
-// rows 4k .. 4k + 3 of the quad).  Long tile lists then spread over four blocks, which the
-// scheduler can place on four SMs.  Batches of 64 entries are staged in shared memory; the
-// records of the next batch are loaded into registers (from primitive ids fetched one batch
-// earlier still) while the current batch is blended, so the gathers overlap the arithmetic.
-constexpr int kQuadThreads = 64;
+// Forward over one 8x8 quad of a 16x16 tile, for a block of one warp: lane l owns the pixels
+// (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the quad and blends both at once in packed f32x2
+// arithmetic, each pixel with exactly the operations of blend3d_pair (so a pixel gets the same
+// bits here and in blend3d_tile).  Long tile lists spread over four blocks, which the scheduler
+// can place on four SMs.  Batches of 32 entries are staged in shared memory with every value
+// twice, marked by whether the entry's cutoff ellipse reaches the quad; the records of the next
+// batch are loaded into registers (from primitive ids fetched one batch earlier still) while the
+// current batch is blended, so the gathers overlap the arithmetic.
+constexpr int kQuadThreads = 32;
 
 __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int quad) {
     const float4* __restrict__ rec = job.rec;
     const PixRect* __restrict__ rect = job.rect;
     const TileLists& tl = job.tl;
     const BlendOpts3& o = job.o;
-    __shared__ float4 s_a[kQuadThreads];
-    __shared__ float4 s_b[kQuadThreads];
-    __shared__ float4 s_c[kQuadThreads];
-    __shared__ uint8_t s_mask[kQuadThreads];
+    // staged entry: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, o), each value twice
+    __shared__ ulonglong2 s_e[6][kQuadThreads];
     const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int lane = threadIdx.x & 31;
     const int x0 = tx * kTile + (quad & 1) * 8, y0 = ty * kTile + (quad >> 1) * 8;
-    const int u = x0 + (lane & 7), v = y0 + warp * 4 + (lane >> 3);
-    const bool inside = u < job.W && v < job.H;
-    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    const int u = x0 + (lane & 7), v = y0 + (lane >> 3);  // and v + 4
+    const bool in0 = u < job.W && v < job.H, in1 = u < job.W && v + 4 < job.H;
+    const f2 PX = f2_dup((float)u + 0.5f), PY = f2_pack((float)v + 0.5f, (float)(v + 4) + 0.5f);
+    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f), ONE = f2_dup(1.f);
     const uint2 range = tl.ranges[tile];
-    Px3 s{1.f, 0.f, 0.f, 0.f, 0u, !inside};
+    f2 T = f2_dup(1.f), c0 = f2_dup(0.f), c1 = c0, c2 = c0;
+    uint32_t last0 = 0u, last1 = 0u;
+    bool done0 = !in0, done1 = !in1;
     // registers of the software pipeline: records of the batch to stage next, primitive id of the
     // batch after it
     float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
     PixRect nR{0, 0, -1, -1};
     uint32_t np = 0u;
-    if (range.x + t < range.y) {
-        const uint32_t p = tl.prim[range.x + t];
+    if (range.x + lane < range.y) {
+        const uint32_t p = tl.prim[range.x + lane];
         nA = rec[(size_t)p * kRecF4 + 0];
         nB = rec[(size_t)p * kRecF4 + 1];
         nC = rec[(size_t)p * kRecF4 + 2];
         nR = rect[p];
     }
-    if (range.x + kQuadThreads + t < range.y) np = tl.prim[range.x + kQuadThreads + t];
+    if (range.x + kQuadThreads + lane < range.y) np = tl.prim[range.x + kQuadThreads + lane];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kQuadThreads) {
-        if (__syncthreads_count(s.done) == kQuadThreads) break;
+        if (__all_sync(0xffffffffu, done0 && done1)) break;
         const int n = (int)min((uint32_t)kQuadThreads, range.y - b0);
-        if (t < n) {
-            s_a[t] = nA;
-            s_b[t] = nB;
-            s_c[t] = nC;
-            s_mask[t] = (uint8_t)quad_mask_ellipse(nA, nB.x, nR, x0, y0, o.lim);
+        __syncwarp();
+        bool hit = false;
+        if (lane < n) {
+            s_e[0][lane] = dup2(nA.x, nA.y);
+            s_e[1][lane] = dup2(nA.z, nA.w);
+            s_e[2][lane] = dup2(nB.x, nB.y);
+            s_e[3][lane] = dup2(nB.z, nB.w);
+            s_e[4][lane] = dup2(nC.x, nC.y);
+            s_e[5][lane] = dup2(nC.z, nC.w);
+            float nBA, nBC;
+            ellipse_edge_ratios(nA, nB.x, nBA, nBC);
+            hit = box_touched_ellipse(nA, nB.x, nBA, nBC, nR, x0, y0, 8, 8, o.lim);
         }
-        __syncthreads();
-        if (b0 + kQuadThreads + t < range.y) {
+        uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        __syncwarp();
+        if (b0 + kQuadThreads + lane < range.y) {
             nA = rec[(size_t)np * kRecF4 + 0];
             nB = rec[(size_t)np * kRecF4 + 1];
             nC = rec[(size_t)np * kRecF4 + 2];
             nR = rect[np];
         }
-        if (b0 + 2 * kQuadThreads + t < range.y) np = tl.prim[b0 + 2 * kQuadThreads + t];
-        for (int c = 0; c < n; c += 32) {
-            if (__all_sync(0xffffffffu, s.done)) break;
-            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
-            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
-            while (bal) {
-                const int j = c + __ffs(bal) - 1;
-                bal &= bal - 1u;
-                if (s.done) continue;
-                blend3d_pair(s, px, py, s_a[j], s_b[j], s_c[j], o, b0 - range.x + (uint32_t)j + 1u);
-            }
+        if (b0 + 2 * kQuadThreads + lane < range.y) np = tl.prim[b0 + 2 * kQuadThreads + lane];
+        while (bal) {
+            const int j = __ffs(bal) - 1;
+            bal &= bal - 1u;
+            const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
+            // the cutoff test in the operation order of mahalanobis2()
+            const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
+            const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+            const f2 b = f2_mul(e2.x, dy);
+            const f2 q = f2_fma(a, a, f2_mul(b, b));
+            const bool ok0 = !done0 && f2_lo(q) <= o.cutoff2, ok1 = !done1 && f2_hi(q) <= o.cutoff2;
+            if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
+            const f2x2 e3 = ld_f2x2(&s_e[3][j]), e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
+            const f2 e = f2_mul(q, K);
+            const f2 G = f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e)));
+            const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+            const f2 w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang))), HALF), G);
+            const f2 raw = f2_mul(e5.y, w);
+            const float al0 = fminf(o.alpha_max, f2_lo(raw)), al1 = fminf(o.alpha_max, f2_hi(raw));
+            const bool k0 = ok0 && al0 >= o.alpha_min, k1 = ok1 && al1 >= o.alpha_min;
+            const f2 alpha = f2_pack(al0, al1);
+            const f2 test_T = f2_mul(T, f2_sub(ONE, alpha));
+            // stop before an entry that would take T below T_min
+            const bool s0 = k0 && f2_lo(test_T) < o.T_min, s1 = k1 && f2_hi(test_T) < o.T_min;
+            done0 |= s0;
+            done1 |= s1;
+            const bool p0 = k0 && !s0, p1 = k1 && !s1;
+            const f2 wt = f2_pack(p0 ? al0 * f2_lo(T) : 0.f, p1 ? al1 * f2_hi(T) : 0.f);
+            c0 = f2_fma(e4.x, wt, c0);
+            c1 = f2_fma(e4.y, wt, c1);
+            c2 = f2_fma(e5.x, wt, c2);
+            T = f2_pack(p0 ? f2_lo(test_T) : f2_lo(T), p1 ? f2_hi(test_T) : f2_hi(T));
+            const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;
+            if (p0) last0 = pos;
+            if (p1) last1 = pos;
         }
     }
-    if (inside) store_px3(job, u, v, s);
+    if (in0) store_px3(job, u, v, Px3{f2_lo(T), f2_lo(c0), f2_lo(c1), f2_lo(c2), last0, done0});
+    if (in1) store_px3(job, u, v + 4, Px3{f2_hi(T), f2_hi(c0), f2_hi(c1), f2_hi(c2), last1, done1});
 }
 
 

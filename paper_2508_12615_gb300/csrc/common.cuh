@@ -53,6 +53,12 @@ __device__ __forceinline__ float cos_approx(float x) {
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// 1 / x to within 1 ulp (MUFU reciprocal)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float sin_approx(float x) {
     float y;
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -20,149 +20,164 @@ __global__ void __launch_bounds__(kQuadThreads) k_blend3d(BlendJob job, const ui
 // Image-plane gradient per primitive (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b o
 constexpr int kG = 12;
 
-// Backward.  Each pixel walks its tile list back to front from its last contributor, recovering
-// the transmittance in front of each contributor as T_i = T_{i+1} / (1 - alpha_i) from the stored
-// final value.  Blocks of kQuadThreads take one 8x8 quad of a tile (tiles in the given order,
-// longest list first); warps visit only the entries marked for their 8x4 sub-tile, and a warp's
-// per-pixel gradients of one primitive are summed by a reduce-scatter and added to the
-// primitive's image-plane gradient with one atomic per component.  As in the forward pass, the
-// records of the next batch are loaded while the current one is processed.
-__global__ void __launch_bounds__(kQuadThreads) k_backward3d(const float4* __restrict__ rec,
-                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
-                                                             int H, int tiles_x, BlendOpts3 o,
-                                                             const float* __restrict__ T_final,
-                                                             const uint32_t* __restrict__ last,
-                                                             const float* __restrict__ dl_dout,
-                                                             float* __restrict__ grad_img,
-                                                             const uint32_t* __restrict__ order) {
+// Record of one staged entry with every value twice, for packed arithmetic over a lane's two
+// pixels: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, o).
+__device__ __forceinline__ void stage_dup(ulonglong2 (*s_e)[32], int i, const float4& A, const float4& B,
+                                          const float4& C) {
+    s_e[0][i] = dup2(A.x, A.y);
+    s_e[1][i] = dup2(A.z, A.w);
+    s_e[2][i] = dup2(B.x, B.y);
+    s_e[3][i] = dup2(B.z, B.w);
+    s_e[4][i] = dup2(C.x, C.y);
+    s_e[5][i] = dup2(C.z, C.w);
+}
+
+// Backward.  One warp per 8x8 quad of a tile (quads of the tiles in the given order, longest list
+// first); lane l owns the pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the quad and works
+// on both at once in packed f32x2 arithmetic.  Each pixel walks its tile list back to front from
+// its last contributor, recovering the transmittance in front of each contributor as
+// T_i = T_{i+1} / (1 - alpha_i) from the stored final value.  The warp's 64 per-pixel gradients of
+// one primitive are summed by a reduce-scatter and added to the primitive's image-plane gradient
+// with one atomic per component.  Batches of 32 entries are staged in shared memory with the bit
+// "the cutoff ellipse reaches the quad"; the records of the next batch are loaded while the
+// current one is processed.
+__global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
+                                                   TileLists tl, int W, int H, int tiles_x, BlendOpts3 o,
+                                                   const float* __restrict__ T_final,
+                                                   const uint32_t* __restrict__ last,
+                                                   const float* __restrict__ dl_dout,
+                                                   float* __restrict__ grad_img,
+                                                   const uint32_t* __restrict__ order) {
     pdl_enter();
-    __shared__ float4 s_a[kQuadThreads];
-    __shared__ float4 s_b[kQuadThreads];
-    __shared__ float4 s_c[kQuadThreads];
-    __shared__ uint32_t s_id[kQuadThreads];
-    __shared__ uint8_t s_mask[kQuadThreads];
-    __shared__ uint32_t s_max_last;
+    __shared__ ulonglong2 s_e[6][32];
+    __shared__ uint32_t s_id[32];
     const int tile = (int)order[blockIdx.x >> 2], quad = (int)(blockIdx.x & 3u);
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int lane = threadIdx.x & 31;
     const int x0 = tx * kTile + (quad & 1) * 8, y0 = ty * kTile + (quad >> 1) * 8;
-    const int u = x0 + (lane & 7), v = y0 + warp * 4 + (lane >> 3);
-    const bool inside = u < W && v < H;
-    const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    const int u = x0 + (lane & 7), v = y0 + (lane >> 3);  // and v + 4
+    const bool in0 = u < W && v < H, in1 = u < W && v + 4 < H;
+    const size_t pix0 = (size_t)v * W + u, pix1 = pix0 + (size_t)4 * W;
+    const f2 PX = f2_dup((float)u + 0.5f), PY = f2_pack((float)v + 0.5f, (float)(v + 4) + 0.5f);
     const uint2 range = tl.ranges[tile];
-    const size_t pix = (size_t)v * W + u;
-    float T = inside ? T_final[pix] : 1.f;
-    const uint32_t my_last = inside ? last[pix] : 0u;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (inside) { g0 = dl_dout[pix * 3 + 0]; g1 = dl_dout[pix * 3 + 1]; g2 = dl_dout[pix * 3 + 2]; }
+    f2 T = f2_pack(in0 ? T_final[pix0] : 1.f, in1 ? T_final[pix1] : 1.f);
+    const uint32_t last0 = in0 ? last[pix0] : 0u, last1 = in1 ? last[pix1] : 0u;
+    f2 g0 = f2_dup(0.f), g1 = g0, g2 = g0;
+    if (in0 || in1) {
+        const float* a0 = dl_dout + pix0 * 3;
+        const float* a1 = dl_dout + pix1 * 3;
+        g0 = f2_pack(in0 ? a0[0] : 0.f, in1 ? a1[0] : 0.f);
+        g1 = f2_pack(in0 ? a0[1] : 0.f, in1 ? a1[1] : 0.f);
+        g2 = f2_pack(in0 ? a0[2] : 0.f, in1 ? a1[2] : 0.f);
+    }
     // colour accumulated behind the current primitive, starting with the background term
-    float S0 = T * o.bg[0], S1 = T * o.bg[1], S2 = T * o.bg[2];
-    if (t == 0) s_max_last = 0u;
-    __syncthreads();
-    atomicMax(&s_max_last, my_last);
-    __syncthreads();
+    f2 S0 = f2_mul(T, f2_dup(o.bg[0])), S1 = f2_mul(T, f2_dup(o.bg[1])), S2 = f2_mul(T, f2_dup(o.bg[2]));
+    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f), ONE = f2_dup(1.f), NEG1 = f2_dup(-1.f);
+    const f2 NPI = f2_dup(-kPi);
     // entries past every pixel's last contributor are skipped; batches run [b0, b_end) downwards
-    const uint32_t end = range.x + s_max_last;
+    const uint32_t max_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
+    const uint32_t end = range.x + max_last;
     uint32_t b_end = end;
-    uint32_t b0 = end - min(end - range.x, (uint32_t)kQuadThreads);
+    uint32_t b0 = end - min(end - range.x, 32u);
     // software pipeline: records (and id) of the batch to stage next, id of the batch after it
     float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
     PixRect nR{0, 0, -1, -1};
     uint32_t nid = 0u, np = 0u;
-    if (b0 + t < b_end) {
-        nid = tl.prim[b0 + t];
+    if (b0 + lane < b_end) {
+        nid = tl.prim[b0 + lane];
         nA = rec[(size_t)nid * kRecF4 + 0];
         nB = rec[(size_t)nid * kRecF4 + 1];
         nC = rec[(size_t)nid * kRecF4 + 2];
         nR = rect[nid];
     }
-    uint32_t nb0 = b0 - min(b0 - range.x, (uint32_t)kQuadThreads);  // start of the next batch
-    if (nb0 + t < b0) np = tl.prim[nb0 + t];
+    uint32_t nb0 = b0 - min(b0 - range.x, 32u);  // start of the next batch
+    if (nb0 + lane < b0) np = tl.prim[nb0 + lane];
     while (b_end > range.x) {
         const int n = (int)(b_end - b0);
-        __syncthreads();
-        if (t < n) {
-            s_id[t] = nid;
-            s_a[t] = nA;
-            s_b[t] = nB;
-            s_c[t] = nC;
-            s_mask[t] = (uint8_t)quad_mask_ellipse(nA, nB.x, nR, x0, y0, o.lim);
+        __syncwarp();
+        bool hit = false;
+        if (lane < n) {
+            s_id[lane] = nid;
+            stage_dup(s_e, lane, nA, nB, nC);
+            float nBA, nBC;
+            ellipse_edge_ratios(nA, nB.x, nBA, nBC);
+            hit = box_touched_ellipse(nA, nB.x, nBA, nBC, nR, x0, y0, 8, 8, o.lim);
         }
-        __syncthreads();
+        uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        __syncwarp();
         // loads for the next two batches: [nb0, b0) and [nnb0, nb0)
-        const uint32_t nnb0 = nb0 - min(nb0 - range.x, (uint32_t)kQuadThreads);
-        if (nb0 + t < b0) {
+        const uint32_t nnb0 = nb0 - min(nb0 - range.x, 32u);
+        if (nb0 + lane < b0) {
             nid = np;
             nA = rec[(size_t)nid * kRecF4 + 0];
             nB = rec[(size_t)nid * kRecF4 + 1];
             nC = rec[(size_t)nid * kRecF4 + 2];
             nR = rect[nid];
         }
-        if (nnb0 + t < nb0) np = tl.prim[nnb0 + t];
-        for (int c = (n - 1) & ~31; c >= 0; c -= 32) {
-            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
-            uint32_t bal = __ballot_sync(0xffffffffu, (m >> warp) & 1u);
-            while (bal) {
-                const int hb = 31 - __clz(bal);
-                bal &= ~(1u << hb);
-                const int j = c + hb;
-                const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;  // 1-based position in the tile list
-                bool contrib = false;
-                float acc[16];
+        if (nnb0 + lane < nb0) np = tl.prim[nnb0 + lane];
+        while (bal) {
+            const int j = 31 - __clz(bal);
+            bal &= ~(1u << j);
+            const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;  // 1-based position in the tile list
+            const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
+            const f2x2 e3 = ld_f2x2(&s_e[3][j]), e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
+            // the cutoff test in the operation order of mahalanobis2()
+            const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
+            const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+            const f2 b = f2_mul(e2.x, dy);
+            const f2 q = f2_fma(a, a, f2_mul(b, b));
+            const f2 e = f2_mul(q, K);
+            const bool c0 = in0 && pos <= last0 && f2_lo(q) <= o.cutoff2;
+            const bool c1 = in1 && pos <= last1 && f2_hi(q) <= o.cutoff2;
+            const f2 G = f2_pack(ex2_approx(c0 ? f2_lo(e) : -INFINITY), ex2_approx(c1 ? f2_hi(e) : -INFINITY));
+            const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+            const float al = f2_lo(ang), ah = f2_hi(ang);
+            const f2 w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(al), cos_approx(ah)), HALF), G);
+            const f2 raw = f2_mul(e5.y, w);
+            const float alpha0 = fminf(o.alpha_max, f2_lo(raw)), alpha1 = fminf(o.alpha_max, f2_hi(raw));
+            const bool k0 = c0 && alpha0 >= o.alpha_min, k1 = c1 && alpha1 >= o.alpha_min;
+            if (!__any_sync(0xffffffffu, k0 || k1)) continue;
+            // a pixel for which the entry is no contributor gets alpha 0: T, S unchanged, no terms
+            const f2 alpha = f2_pack(k0 ? alpha0 : 0.f, k1 ? alpha1 : 0.f);
+            const f2 om = f2_sub(ONE, alpha);
+            const f2 inv = f2_pack(k0 ? rcp_approx(f2_lo(om)) : 1.f, k1 ? rcp_approx(f2_hi(om)) : 1.f);
+            T = f2_mul(T, inv);  // transmittance in front of the entry
+            const f2 wt = f2_mul(alpha, T);
+            f2 acc[kG];
+            acc[8] = f2_mul(g0, wt);
+            acc[9] = f2_mul(g1, wt);
+            acc[10] = f2_mul(g2, wt);
+            const f2 x0c = f2_fma(e4.x, T, f2_mul(NEG1, f2_mul(S0, inv)));
+            const f2 x1c = f2_fma(e4.y, T, f2_mul(NEG1, f2_mul(S1, inv)));
+            const f2 x2c = f2_fma(e5.x, T, f2_mul(NEG1, f2_mul(S2, inv)));
+            const f2 galpha = f2_fma(g0, x0c, f2_fma(g1, x1c, f2_mul(g2, x2c)));
+            S0 = f2_fma(e4.x, wt, S0);
+            S1 = f2_fma(e4.y, wt, S1);
+            S2 = f2_fma(e5.x, wt, S2);
+            // through alpha = o W' (zero where alpha was clamped to alpha_max)
+            const f2 gal = f2_pack(k0 && f2_lo(raw) < o.alpha_max ? f2_lo(galpha) : 0.f,
+                                   k1 && f2_hi(raw) < o.alpha_max ? f2_hi(galpha) : 0.f);
+            acc[11] = f2_mul(gal, w);
+            const f2 gW = f2_mul(gal, e5.y);
+            const f2 sn = f2_pack(sin_approx(al), sin_approx(ah));
+            const f2 gq2 = f2_mul(NEG1, f2_mul(gW, w));          // 2 dL/dq  (dW/dq = -W/2)
+            const f2 gt = f2_mul(f2_mul(NPI, G), f2_mul(gW, sn));  // dL/dt, t in cycles
+            const f2 ga = f2_mul(gq2, a), gb = f2_mul(gq2, b);
+            acc[2] = f2_mul(ga, dx);
+            acc[3] = f2_mul(ga, dy);
+            acc[4] = f2_mul(gb, dy);
+            acc[0] = f2_mul(NEG1, f2_fma(ga, e1.x, f2_mul(gt, e2.y)));
+            acc[1] = f2_mul(NEG1, f2_fma(ga, e1.y, f2_fma(gb, e2.x, f2_mul(gt, e3.x))));
+            acc[5] = f2_mul(gt, dx);
+            acc[6] = f2_mul(gt, dy);
+            acc[7] = gt;
+            float tot16[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-                const float4 A = s_a[j];
-                const float4 B = s_b[j];
-                if (pos <= my_last) {
-                    const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
-                    if (q <= o.cutoff2) {
-                        const float dx = px - A.x, dy = py - A.y;
-                        const float G = ex2_approx(q * kNegHalfLog2e);
-                        const float ang = reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)));
-                        const float cs = cos_approx(ang);
-                        const float w = fmaf(0.5f, cs, 0.5f) * G;
-                        const float4 C = s_c[j];
-                        const float raw = C.w * w;
-                        const float alpha = fminf(o.alpha_max, raw);
-                        if (alpha >= o.alpha_min) {
-                            contrib = true;
-                            const float om = 1.f - alpha;
-                            T = T / om;
-                            const float wt = alpha * T;
-                            acc[8] = g0 * wt;
-                            acc[9] = g1 * wt;
-                            acc[10] = g2 * wt;
-                            const float inv = 1.f / om;
-                            const float galpha = g0 * (C.x * T - S0 * inv) + g1 * (C.y * T - S1 * inv) +
-                                                 g2 * (C.z * T - S2 * inv);
-                            S0 = fmaf(C.x, wt, S0);
-                            S1 = fmaf(C.y, wt, S1);
-                            S2 = fmaf(C.z, wt, S2);
-                            if (raw < o.alpha_max) {
-                                acc[11] = galpha * w;
-                                const float gW = galpha * C.w;
-                                const float sn = sin_approx(ang);
-                                const float a = fmaf(A.z, dx, A.w * dy), b = B.x * dy;
-                                const float gq2 = -gW * w;
-                                const float gt = (-kPi * G) * (gW * sn);
-                                const float ga = gq2 * a, gb = gq2 * b;
-                                acc[2] = ga * dx;
-                                acc[3] = ga * dy;
-                                acc[4] = gb * dy;
-                                acc[0] = -fmaf(ga, A.z, gt * B.y);
-                                acc[1] = -fmaf(ga, A.w, fmaf(gb, B.x, gt * B.z));
-                                acc[5] = gt * dx;
-                                acc[6] = gt * dy;
-                                acc[7] = gt;
-                            }
-                        }
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float tot = warp_reduce_scatter16(acc);
-                    if ((lane & 1) == 0 && (lane >> 1) < kG) atomicAdd(grad_img + (size_t)s_id[j] * kG + (lane >> 1), tot);
-                }
-            }
+            for (int i = 0; i < kG; ++i) tot16[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
+#pragma unroll
+            for (int i = kG; i < 16; ++i) tot16[i] = 0.f;
+            const float tot = warp_reduce_scatter16(tot16);
+            if ((lane & 1) == 0 && (lane >> 1) < kG) atomicAdd(grad_img + (size_t)s_id[j] * kG + (lane >> 1), tot);
         }
         b_end = b0;
         b0 = nb0;
@@ -388,8 +403,8 @@ void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cud
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
                        const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream) {
-    launch_pdl(k_backward3d, 4 * tiles_x * tiles_y, kQuadThreads, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final,
-                                                                      last, dl_dout, grad_img, order);
+    launch_pdl(k_backward3d, 4 * tiles_x * tiles_y, 32, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout,
+               grad_img, order);
     count_launches(1);
 }
 
