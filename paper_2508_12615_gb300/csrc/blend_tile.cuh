@@ -228,6 +228,53 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
 // current batch is blended, so the gathers overlap the arithmetic.
 constexpr int kQuadThreads = 32;
 
+// One entry at a lane's two pixels, before the transmittance: cutoff, alpha (packed as in
+// blend3d_pair: q, envelope, phase, modulation, alpha = min(alpha_max, o W')).
+struct Eval3 {
+    f2 q, alpha;
+};
+__device__ __forceinline__ void eval3_entry(Eval3& r, const ulonglong2 (*s_e)[kQuadThreads], int j, f2 PX, f2 PY,
+                                            const BlendOpts3& o) {
+    const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
+    const f2x2 e3 = ld_f2x2(&s_e[3][j]), e5 = ld_f2x2(&s_e[5][j]);
+    // the cutoff test in the operation order of mahalanobis2()
+    const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
+    const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+    const f2 b = f2_mul(e2.x, dy);
+    r.q = f2_fma(a, a, f2_mul(b, b));
+    const f2 e = f2_mul(r.q, f2_dup(kNegHalfLog2e));
+    const f2 G = f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e)));
+    const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+    const f2 HALF = f2_dup(0.5f);
+    const f2 w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang))), HALF), G);
+    const f2 raw = f2_mul(e5.y, w);
+    r.alpha = f2_pack(fminf(o.alpha_max, f2_lo(raw)), fminf(o.alpha_max, f2_hi(raw)));
+}
+// The entry's effect on the pixels' state, in list order (blend3d_pair's skip, stop and update).
+__device__ __forceinline__ void apply3_entry(const Eval3& r, const ulonglong2 (*s_e)[kQuadThreads], int j,
+                                             const BlendOpts3& o, f2& T, f2& c0, f2& c1, f2& c2, uint32_t& last0,
+                                             uint32_t& last1, bool& done0, bool& done1, uint32_t pos) {
+    const float al0 = f2_lo(r.alpha), al1 = f2_hi(r.alpha);
+    const bool k0 = !done0 && f2_lo(r.q) <= o.cutoff2 && al0 >= o.alpha_min;
+    const bool k1 = !done1 && f2_hi(r.q) <= o.cutoff2 && al1 >= o.alpha_min;
+    if (!__any_sync(0xffffffffu, k0 || k1)) return;
+    const f2 test_T = f2_mul(T, f2_sub(f2_dup(1.f), r.alpha));
+    // stop before an entry that would take T below T_min
+    const bool s0 = k0 && f2_lo(test_T) < o.T_min, s1 = k1 && f2_hi(test_T) < o.T_min;
+    done0 |= s0;
+    done1 |= s1;
+    const bool p0 = k0 && !s0, p1 = k1 && !s1;
+    const f2 wt = f2_pack(p0 ? al0 * f2_lo(T) : 0.f, p1 ? al1 * f2_hi(T) : 0.f);
+    const f2x2 e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
+    c0 = f2_fma(e4.x, wt, c0);
+    c1 = f2_fma(e4.y, wt, c1);
+    c2 = f2_fma(e5.x, wt, c2);
+    T = f2_pack(p0 ? f2_lo(test_T) : f2_lo(T), p1 ? f2_hi(test_T) : f2_hi(T));
+    if (p0) last0 = pos;
+    if (p1) last1 = pos;
+}
+
+
 __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int quad) {
     const float4* __restrict__ rec = job.rec;
     const PixRect* __restrict__ rect = job.rect;
@@ -241,7 +288,6 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
     const int u = x0 + (lane & 7), v = y0 + (lane >> 3);  // and v + 4
     const bool in0 = u < job.W && v < job.H, in1 = u < job.W && v + 4 < job.H;
     const f2 PX = f2_dup((float)u + 0.5f), PY = f2_pack((float)v + 0.5f, (float)(v + 4) + 0.5f);
-    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f), ONE = f2_dup(1.f);
     const uint2 range = tl.ranges[tile];
     f2 T = f2_dup(1.f), c0 = f2_dup(0.f), c1 = c0, c2 = c0;
     uint32_t last0 = 0u, last1 = 0u;
@@ -284,40 +330,20 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
             nR = rect[np];
         }
         if (b0 + 2 * kQuadThreads + lane < range.y) np = tl.prim[b0 + 2 * kQuadThreads + lane];
+        // two entries per step: their envelope, phase and alpha do not depend on each other, only
+        // the transmittance update does, so evaluating them together doubles the independent work
+        // in flight; the updates then follow in list order
         while (bal) {
-            const int j = __ffs(bal) - 1;
+            const int j1 = __ffs(bal) - 1;
             bal &= bal - 1u;
-            const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
-            // the cutoff test in the operation order of mahalanobis2()
-            const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
-            const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
-            const f2 b = f2_mul(e2.x, dy);
-            const f2 q = f2_fma(a, a, f2_mul(b, b));
-            const bool ok0 = !done0 && f2_lo(q) <= o.cutoff2, ok1 = !done1 && f2_hi(q) <= o.cutoff2;
-            if (!__any_sync(0xffffffffu, ok0 || ok1)) continue;
-            const f2x2 e3 = ld_f2x2(&s_e[3][j]), e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
-            const f2 e = f2_mul(q, K);
-            const f2 G = f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e)));
-            const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
-            const f2 w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang))), HALF), G);
-            const f2 raw = f2_mul(e5.y, w);
-            const float al0 = fminf(o.alpha_max, f2_lo(raw)), al1 = fminf(o.alpha_max, f2_hi(raw));
-            const bool k0 = ok0 && al0 >= o.alpha_min, k1 = ok1 && al1 >= o.alpha_min;
-            const f2 alpha = f2_pack(al0, al1);
-            const f2 test_T = f2_mul(T, f2_sub(ONE, alpha));
-            // stop before an entry that would take T below T_min
-            const bool s0 = k0 && f2_lo(test_T) < o.T_min, s1 = k1 && f2_hi(test_T) < o.T_min;
-            done0 |= s0;
-            done1 |= s1;
-            const bool p0 = k0 && !s0, p1 = k1 && !s1;
-            const f2 wt = f2_pack(p0 ? al0 * f2_lo(T) : 0.f, p1 ? al1 * f2_hi(T) : 0.f);
-            c0 = f2_fma(e4.x, wt, c0);
-            c1 = f2_fma(e4.y, wt, c1);
-            c2 = f2_fma(e5.x, wt, c2);
-            T = f2_pack(p0 ? f2_lo(test_T) : f2_lo(T), p1 ? f2_hi(test_T) : f2_hi(T));
-            const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;
-            if (p0) last0 = pos;
-            if (p1) last1 = pos;
+            const int j2 = bal ? __ffs(bal) - 1 : -1;
+            if (bal) bal &= bal - 1u;
+            Eval3 ea, eb;
+            eval3_entry(ea, s_e, j1, PX, PY, o);
+            if (j2 >= 0) eval3_entry(eb, s_e, j2, PX, PY, o);
+            apply3_entry(ea, s_e, j1, o, T, c0, c1, c2, last0, last1, done0, done1, b0 - range.x + (uint32_t)j1 + 1u);
+            if (j2 >= 0)
+                apply3_entry(eb, s_e, j2, o, T, c0, c1, c2, last0, last1, done0, done1, b0 - range.x + (uint32_t)j2 + 1u);
         }
     }
     if (in0) store_px3(job, u, v, Px3{f2_lo(T), f2_lo(c0), f2_lo(c1), f2_lo(c2), last0, done0});

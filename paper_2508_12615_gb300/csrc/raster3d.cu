@@ -32,6 +32,88 @@ __device__ __forceinline__ void stage_dup(ulonglong2 (*s_e)[32], int i, const fl
     s_e[5][i] = dup2(C.z, C.w);
 }
 
+// One entry at a lane's two pixels, before the transmittance: the offsets, the cutoff form, the
+// envelope, the modulation, alpha and whether the entry contributes to each pixel.
+struct BwdEval {
+    f2 dx, dy, a, b, G, w, raw, sn;
+    float alpha0, alpha1;
+    bool k0, k1;
+};
+__device__ __forceinline__ void bwd_eval(BwdEval& r, const ulonglong2 (*s_e)[32], int j, f2 PX, f2 PY,
+                                         const BlendOpts3& o, bool live0, bool live1) {
+    const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
+    const f2x2 e3 = ld_f2x2(&s_e[3][j]), e5 = ld_f2x2(&s_e[5][j]);
+    // the cutoff test in the operation order of mahalanobis2()
+    r.dx = f2_sub(PX, e0.x);
+    r.dy = f2_sub(PY, e0.y);
+    r.a = f2_fma(e1.x, r.dx, f2_mul(e1.y, r.dy));
+    r.b = f2_mul(e2.x, r.dy);
+    const f2 q = f2_fma(r.a, r.a, f2_mul(r.b, r.b));
+    const f2 e = f2_mul(q, f2_dup(kNegHalfLog2e));
+    const bool c0 = live0 && f2_lo(q) <= o.cutoff2, c1 = live1 && f2_hi(q) <= o.cutoff2;
+    r.G = f2_pack(ex2_approx(c0 ? f2_lo(e) : -INFINITY), ex2_approx(c1 ? f2_hi(e) : -INFINITY));
+    const f2 ang = f2_reduced_angle(f2_fma(e2.y, r.dx, f2_fma(e3.x, r.dy, e3.y)));
+    const float al = f2_lo(ang), ah = f2_hi(ang);
+    const f2 HALF = f2_dup(0.5f);
+    r.w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(al), cos_approx(ah)), HALF), r.G);
+    r.sn = f2_pack(sin_approx(al), sin_approx(ah));
+    r.raw = f2_mul(e5.y, r.w);
+    r.alpha0 = fminf(o.alpha_max, f2_lo(r.raw));
+    r.alpha1 = fminf(o.alpha_max, f2_hi(r.raw));
+    r.k0 = c0 && r.alpha0 >= o.alpha_min;
+    r.k1 = c1 && r.alpha1 >= o.alpha_min;
+}
+// The entry's gradient at the lane's pixels, with the transmittance recovered in front of it and
+// the colour behind it advanced; the warp's sum is added to the primitive's image-plane gradient.
+__device__ __forceinline__ void bwd_apply(const BwdEval& r, const ulonglong2 (*s_e)[32], int j, const BlendOpts3& o,
+                                          f2& T, f2& S0, f2& S1, f2& S2, f2 g0, f2 g1, f2 g2, float* grad) {
+    if (!__any_sync(0xffffffffu, r.k0 || r.k1)) return;
+    const int lane = threadIdx.x & 31;
+    const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]), e3 = ld_f2x2(&s_e[3][j]);
+    const f2x2 e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
+    const f2 ONE = f2_dup(1.f), NEG1 = f2_dup(-1.f);
+    // a pixel for which the entry is no contributor gets alpha 0: T, S unchanged, no terms
+    const f2 alpha = f2_pack(r.k0 ? r.alpha0 : 0.f, r.k1 ? r.alpha1 : 0.f);
+    const f2 om = f2_sub(ONE, alpha);
+    const f2 inv = f2_pack(r.k0 ? rcp_approx(f2_lo(om)) : 1.f, r.k1 ? rcp_approx(f2_hi(om)) : 1.f);
+    T = f2_mul(T, inv);  // transmittance in front of the entry
+    const f2 wt = f2_mul(alpha, T);
+    f2 acc[kG];
+    acc[8] = f2_mul(g0, wt);
+    acc[9] = f2_mul(g1, wt);
+    acc[10] = f2_mul(g2, wt);
+    const f2 x0c = f2_fma(e4.x, T, f2_mul(NEG1, f2_mul(S0, inv)));
+    const f2 x1c = f2_fma(e4.y, T, f2_mul(NEG1, f2_mul(S1, inv)));
+    const f2 x2c = f2_fma(e5.x, T, f2_mul(NEG1, f2_mul(S2, inv)));
+    const f2 galpha = f2_fma(g0, x0c, f2_fma(g1, x1c, f2_mul(g2, x2c)));
+    S0 = f2_fma(e4.x, wt, S0);
+    S1 = f2_fma(e4.y, wt, S1);
+    S2 = f2_fma(e5.x, wt, S2);
+    // through alpha = o W' (zero where alpha was clamped to alpha_max)
+    const f2 gal = f2_pack(r.k0 && f2_lo(r.raw) < o.alpha_max ? f2_lo(galpha) : 0.f,
+                           r.k1 && f2_hi(r.raw) < o.alpha_max ? f2_hi(galpha) : 0.f);
+    acc[11] = f2_mul(gal, r.w);
+    const f2 gW = f2_mul(gal, e5.y);
+    const f2 gq2 = f2_mul(NEG1, f2_mul(gW, r.w));                       // 2 dL/dq  (dW/dq = -W/2)
+    const f2 gt = f2_mul(f2_mul(f2_dup(-kPi), r.G), f2_mul(gW, r.sn));  // dL/dt, t in cycles
+    const f2 ga = f2_mul(gq2, r.a), gb = f2_mul(gq2, r.b);
+    acc[2] = f2_mul(ga, r.dx);
+    acc[3] = f2_mul(ga, r.dy);
+    acc[4] = f2_mul(gb, r.dy);
+    acc[0] = f2_mul(NEG1, f2_fma(ga, e1.x, f2_mul(gt, e2.y)));
+    acc[1] = f2_mul(NEG1, f2_fma(ga, e1.y, f2_fma(gb, e2.x, f2_mul(gt, e3.x))));
+    acc[5] = f2_mul(gt, r.dx);
+    acc[6] = f2_mul(gt, r.dy);
+    acc[7] = gt;
+    float tot16[16];
+#pragma unroll
+    for (int i = 0; i < kG; ++i) tot16[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
+#pragma unroll
+    for (int i = kG; i < 16; ++i) tot16[i] = 0.f;
+    const float tot = warp_reduce_scatter16(tot16);
+    if ((lane & 1) == 0 && (lane >> 1) < kG) atomicAdd(grad + (lane >> 1), tot);
+}
+
 // Backward.  One warp per 8x8 quad of a tile (quads of the tiles in the given order, longest list
 // first); lane l owns the pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the quad and works
 // on both at once in packed f32x2 arithmetic.  Each pixel walks its tile list back to front from
@@ -72,8 +154,6 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
     }
     // colour accumulated behind the current primitive, starting with the background term
     f2 S0 = f2_mul(T, f2_dup(o.bg[0])), S1 = f2_mul(T, f2_dup(o.bg[1])), S2 = f2_mul(T, f2_dup(o.bg[2]));
-    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f), ONE = f2_dup(1.f), NEG1 = f2_dup(-1.f);
-    const f2 NPI = f2_dup(-kPi);
     // entries past every pixel's last contributor are skipped; batches run [b0, b_end) downwards
     const uint32_t max_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
     const uint32_t end = range.x + max_last;
@@ -115,69 +195,21 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
             nR = rect[nid];
         }
         if (nnb0 + lane < nb0) np = tl.prim[nnb0 + lane];
+        // two entries per step (back to front): their envelope, phase and alpha do not depend on
+        // each other, so they are evaluated together; the transmittance recovery, the colour behind
+        // and the gradient terms then follow in list order
         while (bal) {
-            const int j = 31 - __clz(bal);
-            bal &= ~(1u << j);
-            const uint32_t pos = b0 - range.x + (uint32_t)j + 1u;  // 1-based position in the tile list
-            const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
-            const f2x2 e3 = ld_f2x2(&s_e[3][j]), e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
-            // the cutoff test in the operation order of mahalanobis2()
-            const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
-            const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
-            const f2 b = f2_mul(e2.x, dy);
-            const f2 q = f2_fma(a, a, f2_mul(b, b));
-            const f2 e = f2_mul(q, K);
-            const bool c0 = in0 && pos <= last0 && f2_lo(q) <= o.cutoff2;
-            const bool c1 = in1 && pos <= last1 && f2_hi(q) <= o.cutoff2;
-            const f2 G = f2_pack(ex2_approx(c0 ? f2_lo(e) : -INFINITY), ex2_approx(c1 ? f2_hi(e) : -INFINITY));
-            const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
-            const float al = f2_lo(ang), ah = f2_hi(ang);
-            const f2 w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(al), cos_approx(ah)), HALF), G);
-            const f2 raw = f2_mul(e5.y, w);
-            const float alpha0 = fminf(o.alpha_max, f2_lo(raw)), alpha1 = fminf(o.alpha_max, f2_hi(raw));
-            const bool k0 = c0 && alpha0 >= o.alpha_min, k1 = c1 && alpha1 >= o.alpha_min;
-            if (!__any_sync(0xffffffffu, k0 || k1)) continue;
-            // a pixel for which the entry is no contributor gets alpha 0: T, S unchanged, no terms
-            const f2 alpha = f2_pack(k0 ? alpha0 : 0.f, k1 ? alpha1 : 0.f);
-            const f2 om = f2_sub(ONE, alpha);
-            const f2 inv = f2_pack(k0 ? rcp_approx(f2_lo(om)) : 1.f, k1 ? rcp_approx(f2_hi(om)) : 1.f);
-            T = f2_mul(T, inv);  // transmittance in front of the entry
-            const f2 wt = f2_mul(alpha, T);
-            f2 acc[kG];
-            acc[8] = f2_mul(g0, wt);
-            acc[9] = f2_mul(g1, wt);
-            acc[10] = f2_mul(g2, wt);
-            const f2 x0c = f2_fma(e4.x, T, f2_mul(NEG1, f2_mul(S0, inv)));
-            const f2 x1c = f2_fma(e4.y, T, f2_mul(NEG1, f2_mul(S1, inv)));
-            const f2 x2c = f2_fma(e5.x, T, f2_mul(NEG1, f2_mul(S2, inv)));
-            const f2 galpha = f2_fma(g0, x0c, f2_fma(g1, x1c, f2_mul(g2, x2c)));
-            S0 = f2_fma(e4.x, wt, S0);
-            S1 = f2_fma(e4.y, wt, S1);
-            S2 = f2_fma(e5.x, wt, S2);
-            // through alpha = o W' (zero where alpha was clamped to alpha_max)
-            const f2 gal = f2_pack(k0 && f2_lo(raw) < o.alpha_max ? f2_lo(galpha) : 0.f,
-                                   k1 && f2_hi(raw) < o.alpha_max ? f2_hi(galpha) : 0.f);
-            acc[11] = f2_mul(gal, w);
-            const f2 gW = f2_mul(gal, e5.y);
-            const f2 sn = f2_pack(sin_approx(al), sin_approx(ah));
-            const f2 gq2 = f2_mul(NEG1, f2_mul(gW, w));          // 2 dL/dq  (dW/dq = -W/2)
-            const f2 gt = f2_mul(f2_mul(NPI, G), f2_mul(gW, sn));  // dL/dt, t in cycles
-            const f2 ga = f2_mul(gq2, a), gb = f2_mul(gq2, b);
-            acc[2] = f2_mul(ga, dx);
-            acc[3] = f2_mul(ga, dy);
-            acc[4] = f2_mul(gb, dy);
-            acc[0] = f2_mul(NEG1, f2_fma(ga, e1.x, f2_mul(gt, e2.y)));
-            acc[1] = f2_mul(NEG1, f2_fma(ga, e1.y, f2_fma(gb, e2.x, f2_mul(gt, e3.x))));
-            acc[5] = f2_mul(gt, dx);
-            acc[6] = f2_mul(gt, dy);
-            acc[7] = gt;
-            float tot16[16];
-#pragma unroll
-            for (int i = 0; i < kG; ++i) tot16[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
-#pragma unroll
-            for (int i = kG; i < 16; ++i) tot16[i] = 0.f;
-            const float tot = warp_reduce_scatter16(tot16);
-            if ((lane & 1) == 0 && (lane >> 1) < kG) atomicAdd(grad_img + (size_t)s_id[j] * kG + (lane >> 1), tot);
+            const int j1 = 31 - __clz(bal);
+            bal &= ~(1u << j1);
+            const int j2 = bal ? 31 - __clz(bal) : -1;
+            if (bal) bal &= ~(1u << j2);
+            const uint32_t pos1 = b0 - range.x + (uint32_t)j1 + 1u;  // 1-based positions in the tile list
+            const uint32_t pos2 = b0 - range.x + (uint32_t)j2 + 1u;
+            BwdEval ea, eb;
+            bwd_eval(ea, s_e, j1, PX, PY, o, in0 && pos1 <= last0, in1 && pos1 <= last1);
+            if (j2 >= 0) bwd_eval(eb, s_e, j2, PX, PY, o, in0 && pos2 <= last0, in1 && pos2 <= last1);
+            bwd_apply(ea, s_e, j1, o, T, S0, S1, S2, g0, g1, g2, grad_img + (size_t)s_id[j1] * kG);
+            if (j2 >= 0) bwd_apply(eb, s_e, j2, o, T, S0, S1, S2, g0, g1, g2, grad_img + (size_t)s_id[j2] * kG);
         }
         b_end = b0;
         b0 = nb0;
