@@ -483,20 +483,29 @@ def our_arm(args, rank: int, world: int, local_rank: int):
                         f"{mufu_ops} MUFU ops",
                 "mufu_frac": pairs_per_launch * mufu_ops / launch_s / (SMS * 16 * clock_mhz * 1e6)}
 
-    # the deformation network's products (tensor cores, bf16): 2 N sum(in x out) flops forward, twice
-    # that backward (input and weight gradients)
+    # the deformation network: its layers do 2 x 256 x K flops per row against (K + 256) x 2 bytes
+    # (K <= 336), about 127 flop per byte, below the GPU's balance point (measured bf16 peak over HBM
+    # copy bandwidth, about 250): the chain of products is bound by HBM.  Bytes per row that this
+    # layer-by-layer implementation moves (bfloat16 activations and gradients, fp32 records):
+    #   forward  160 encode + 672 + 4 x 1024 + 1184 + 2 x 1024 hidden + 576 head + 224 apply = 8960
+    #   backward 336 apply + 1088 head + 7 x (1536 ReLU pass + products) ... = 30192
     roofline_mlp = None
     if wl.kind == "6dmlp" and "mlp_fwd" in stages:
-        macs = sum(o * i for o, i in synth.MLP_SHAPES) * wl.p.shape[0]
+        rows = wl.p.shape[0]
+        macs = sum(o * i for o, i in synth.MLP_SHAPES) * rows
         t_f = stages["mlp_fwd"]["ms_per_launch"] * 1e-3
         t_b = stages["mlp_bwd"]["ms_per_launch"] * 1e-3
-        ach = 6.0 * macs / (t_f + t_b) / 1e12
+        byts = (8960 + 30192) * rows
+        hbm = float(pk.get("hbm_gbs", 6800.0))
         peak_bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
-        roofline_mlp = {"bound": "tensor", "kernel": "deformation network GEMMs (cuBLASLt bf16)", "achieved": ach,
-                        "peak": peak_bf16, "unit": "TFLOP/s", "frac": ach / peak_bf16, "traffic": None,
-                        "peak_source": f"{pk_kind} bf16 GEMM throughput (sustained)",
-                        "work": f"6 x {macs:.3g} multiply-adds per sample (forward, input and weight gradients)",
-                        "fwd_tflops": 2.0 * macs / t_f / 1e12, "bwd_tflops": 4.0 * macs / t_b / 1e12}
+        ach = byts / (t_f + t_b) / 1e9
+        roofline_mlp = {"bound": "hbm", "kernel": "deformation network (encode, 9 layers, apply; forward and backward)",
+                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                        "peak_source": f"{pk_kind} HBM copy bandwidth",
+                        "work": f"{byts / rows:.0f} bytes per row moved by the layer-by-layer products x {rows} rows",
+                        "tensor_tflops": 6.0 * macs / (t_f + t_b) / 1e12,
+                        "tensor_frac": 6.0 * macs / (t_f + t_b) / 1e12 / peak_bf16,
+                        "fwd_gbs": 8960 * rows / t_f / 1e9, "bwd_gbs": 30192 * rows / t_b / 1e9}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline and wl.kind == "2d":

@@ -313,12 +313,52 @@ std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A
             LT_TRY(cublasLtMatmulPreferenceCreate(&pref));
             LT_TRY(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &lt.ws_size,
                                                         sizeof(lt.ws_size)));
+            // the heuristic's candidates are timed once on this product and the fastest is kept:
+            // its first choice is slow for some epilogues
+            constexpr int kCandidates = 12;
+            cublasLtMatmulHeuristicResult_t cand[kCandidates];
             int found = 0;
-            const cublasStatus_t hs = cublasLtMatmulAlgoGetHeuristic(lt.h, desc, la, lb, lc, lc, pref, 1, &res, &found);
+            const cublasStatus_t hs =
+                cublasLtMatmulAlgoGetHeuristic(lt.h, desc, la, lb, lc, lc, pref, kCandidates, cand, &found);
             cublasLtMatmulPreferenceDestroy(pref);
             if (hs != CUBLAS_STATUS_SUCCESS || found == 0)
                 return "cuBLASLt: no algorithm for the product (m=" + std::to_string(m) + ", n=" + std::to_string(n) +
                        ", k=" + std::to_string(k) + ")";
+            res = cand[0];
+            if (found > 1) {
+                // trials write D (and the epilogue outputs) with beta 0: into a scratch copy when the
+                // call accumulates (beta != 0), else into D itself, which the real call rewrites
+                void* Dt = D;
+                const size_t d_bytes = (size_t)ldc * n * (dtype == CUDA_R_32F ? 4 : 2);
+                if (beta != 0.f && cudaMallocAsync(&Dt, d_bytes, stream) != cudaSuccess) Dt = nullptr;
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                const float one = 1.f, zero = 0.f;
+                float best = 1e30f;
+                for (int c = 0; Dt && c < found; ++c) {
+                    float ms_sum = 0.f;
+                    bool ok = true;
+                    for (int rep = 0; rep < 3 && ok; ++rep) {
+                        cudaEventRecord(e0, stream);
+                        ok = cublasLtMatmul(lt.h, desc, &one, A, la, B, lb, &zero, Dt, lc, Dt, lc, &cand[c].algo, lt.ws,
+                                            lt.ws_size, stream) == CUBLAS_STATUS_SUCCESS;
+                        cudaEventRecord(e1, stream);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0) ms_sum += ms;  // the first run warms up
+                    }
+                    if (ok && ms_sum < best) {
+                        best = ms_sum;
+                        res = cand[c];
+                    }
+                }
+                cudaGetLastError();
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (Dt && Dt != D) cudaFreeAsync(Dt, stream);
+            }
             lt.algos[key] = res;
         }
     }
