@@ -488,7 +488,8 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     # copy bandwidth, about 250): the chain of products is bound by HBM.  Bytes per row that this
     # layer-by-layer implementation moves (bfloat16 activations and gradients, fp32 records):
     #   forward  160 encode + 672 + 4 x 1024 + 1184 + 2 x 1024 hidden + 576 head + 224 apply = 8960
-    #   backward 336 apply + 1088 head + 7 x (1536 ReLU pass + products) ... = 30192
+    #   backward 336 apply + 1088 head + 28288 for the 8 hidden layers (1536 ReLU pass, 1024 + 2 K
+    #            for the two products each) + 480 encoding = 30192
     roofline_mlp = None
     if wl.kind == "6dmlp" and "mlp_fwd" in stages:
         rows = wl.p.shape[0]
