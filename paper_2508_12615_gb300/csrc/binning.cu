@@ -103,9 +103,12 @@ __global__ void __launch_bounds__(kThreads) k_scan_offsets(const uint32_t* __res
     }
 }
 
-// Emission, one warp per scan position: the 32 lanes test 32 tiles of the primitive's covered
-// range at a time and write the touched ones contiguously (ballot + population count), in
-// row-major tile order starting at the primitive's offset.
+// Emission, one thread per scan position: a primitive writes the tiles of its covered range that
+// its cutoff ellipse reaches, in row-major tile order, from its offset on.  When its count equals
+// the number of tiles of the range (the common case for small footprints) every tile is reached and
+// none needs the test; a range of at most kEmitSmall tiles is tested by the thread; larger ones are
+// emitted by the whole warp, one after another, 32 tiles at a time (ballot + population count).
+constexpr int kEmitSmall = 16;
 __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ counts,
                                                    const uint32_t* __restrict__ perm, int64_t n,
                                                    const float4* __restrict__ rec, const PixRect* __restrict__ rect,
@@ -113,29 +116,75 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    uint32_t* __restrict__ inst_prim) {
     pdl_enter();
-    const int64_t j = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (j >= n) return;
-    const uint32_t p = perm ? perm[j] : (uint32_t)j;
-    if (counts[p] == 0u) return;
-    const PixRect r = rect[p];
-    const float4 A = rec[(size_t)p * kRecF4 + 0];
-    const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
-    const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
-    const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
-    uint32_t o = offsets[p];
-    for (int t0 = 0; t0 < nt; t0 += 32) {
-        const int t = t0 + lane;
-        const int ty = ty0 + t / nx, tx = tx0 + t % nx;
-        const bool hit = t < nt && tile_touched(e, r, tx, ty, lim);
-        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-            const uint32_t w = o + __popc(bal & ((1u << lane) - 1u));
-            keys[w] = (uint32_t)(ty * tiles_x + tx);
-            vals[w] = w;
-            inst_prim[w] = p;
+    uint32_t p = 0u, cnt = 0u, o = 0u;
+    PixRect r{1, 1, 0, 0};
+    int tx0 = 0, ty0 = 0, nx = 1, nt = 0;
+    bool big = false;
+    if (j < n) {
+        p = perm ? perm[j] : (uint32_t)j;
+        cnt = counts[p];
+        if (cnt) {
+            r = rect[p];
+            o = offsets[p];
+            tx0 = r.u0 / kTile;
+            ty0 = r.v0 / kTile;
+            nx = r.u1 / kTile - tx0 + 1;
+            nt = nx * (r.v1 / kTile - ty0 + 1);
+            if ((int)cnt == nt) {
+                for (int t = 0; t < nt; ++t) {
+                    const uint32_t w = o + (uint32_t)t;
+                    keys[w] = (uint32_t)((ty0 + t / nx) * tiles_x + tx0 + t % nx);
+                    vals[w] = w;
+                    inst_prim[w] = p;
+                }
+            } else if (nt <= kEmitSmall) {
+                const float4 A = rec[(size_t)p * kRecF4 + 0];
+                const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
+                uint32_t w = o;
+                for (int t = 0; t < nt; ++t) {
+                    const int ty = ty0 + t / nx, tx = tx0 + t % nx;
+                    if (tile_touched(e, r, tx, ty, lim)) {
+                        keys[w] = (uint32_t)(ty * tiles_x + tx);
+                        vals[w] = w;
+                        inst_prim[w] = p;
+                        ++w;
+                    }
+                }
+            } else {
+                big = true;
+            }
         }
-        o += __popc(bal);
+    }
+    uint32_t bigs = __ballot_sync(0xffffffffu, big);
+    while (bigs) {
+        const int k = __ffs(bigs) - 1;
+        bigs &= bigs - 1u;
+        const uint32_t pk = __shfl_sync(0xffffffffu, p, k);
+        PixRect rk;
+        rk.u0 = __shfl_sync(0xffffffffu, r.u0, k);
+        rk.u1 = __shfl_sync(0xffffffffu, r.u1, k);
+        rk.v0 = __shfl_sync(0xffffffffu, r.v0, k);
+        rk.v1 = __shfl_sync(0xffffffffu, r.v1, k);
+        uint32_t ok = __shfl_sync(0xffffffffu, o, k);
+        const float4 A = rec[(size_t)pk * kRecF4 + 0];
+        const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)pk * kRecF4 + 1].x);
+        const int kx0 = rk.u0 / kTile, ky0 = rk.v0 / kTile;
+        const int knx = rk.u1 / kTile - kx0 + 1, knt = knx * (rk.v1 / kTile - ky0 + 1);
+        for (int t0 = 0; t0 < knt; t0 += 32) {
+            const int t = t0 + lane;
+            const int ty = ky0 + t / knx, tx = kx0 + t % knx;
+            const bool hit = t < knt && tile_touched(e, rk, tx, ty, lim);
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const uint32_t w = ok + __popc(bal & ((1u << lane) - 1u));
+                keys[w] = (uint32_t)(ty * tiles_x + tx);
+                vals[w] = w;
+                inst_prim[w] = pk;
+            }
+            ok += __popc(bal);
+        }
     }
 }
 
@@ -494,8 +543,8 @@ void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const 
                  uint32_t* inst_prim, uint32_t* offsets, cudaStream_t stream) {
     if (n == 0) return;
     launch_pdl(k_scan_offsets, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_offsets, offsets);
-    launch_pdl(k_emit, ceil_div(n * 32, kThreads), kThreads, 0, stream, counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
-                                                                vals, inst_prim);
+    launch_pdl(k_emit, ceil_div(n, kThreads), kThreads, 0, stream, counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
+               vals, inst_prim);
     count_launches(2);
 }
 

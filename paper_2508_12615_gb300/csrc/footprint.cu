@@ -34,22 +34,36 @@ __device__ __forceinline__ PixRect covered_pixels(float mx, float my, float ex, 
 }
 
 // Number of tiles of each lane's covered pixel range that its cutoff ellipse reaches
-// (tile_touched()), computed by the whole warp: for each lane's primitive in turn, the 32 lanes
-// test 32 tiles at a time.  Every lane of the warp must call it; an empty range counts 0.
+// (tile_touched()).  A lane whose range spans at most kSmallRangeTiles tiles tests them itself (the
+// common case: most footprints cover a few tiles); the ranges above that are counted by the whole
+// warp, one after another, 32 tiles at a time.  Every lane of the warp must call it; an empty range
+// counts 0.
+constexpr int kSmallRangeTiles = 16;
 __device__ __forceinline__ uint32_t warp_tile_counts(float mx, float my, float l11, float l21, float l22,
                                                      const PixRect& r, float lim) {
     const int lane = threadIdx.x & 31;
-    Ellipse mine;
-    if (r.u0 <= r.u1) mine = make_ellipse(mx, my, l11, l21, l22);
-    else mine = make_ellipse(0.f, 0.f, 1.f, 0.f, 1.f);
     uint32_t result = 0;
-    for (int k = 0; k < 32; ++k) {
+    bool big = false;
+    Ellipse mine = make_ellipse(0.f, 0.f, 1.f, 0.f, 1.f);
+    if (r.u0 <= r.u1) {
+        mine = make_ellipse(mx, my, l11, l21, l22);
+        const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
+        const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
+        if (nt <= kSmallRangeTiles) {
+            for (int t = 0; t < nt; ++t) result += tile_touched(mine, r, tx0 + t % nx, ty0 + t / nx, lim) ? 1u : 0u;
+        } else {
+            big = true;
+        }
+    }
+    uint32_t bigs = __ballot_sync(0xffffffffu, big);
+    while (bigs) {
+        const int k = __ffs(bigs) - 1;
+        bigs &= bigs - 1u;
         PixRect rk;
         rk.u0 = __shfl_sync(0xffffffffu, r.u0, k);
         rk.u1 = __shfl_sync(0xffffffffu, r.u1, k);
         rk.v0 = __shfl_sync(0xffffffffu, r.v0, k);
         rk.v1 = __shfl_sync(0xffffffffu, r.v1, k);
-        if (rk.u0 > rk.u1) continue;  // uniform across the warp
         Ellipse e;
         e.mx = __shfl_sync(0xffffffffu, mine.mx, k);
         e.my = __shfl_sync(0xffffffffu, mine.my, k);
