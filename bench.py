@@ -487,16 +487,17 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     # (K <= 336), about 127 flop per byte, below the GPU's balance point (measured bf16 peak over HBM
     # copy bandwidth, about 250): the chain of products is bound by HBM.  Bytes per row that this
     # layer-by-layer implementation moves (bfloat16 activations and gradients, fp32 records):
-    #   forward  160 encode + 672 + 4 x 1024 + 1184 + 2 x 1024 hidden + 576 head + 224 apply = 8960
-    #   backward 336 apply + 1088 head + 28288 for the 8 hidden layers (1536 ReLU pass, 1024 + 2 K
-    #            for the two products each) + 480 encoding = 30192
+    #   forward  160 encode + 672 + 4 x 1024 + 1184 + 2 x 1024 hidden + 8 x 32 ReLU bit-masks + 576 head
+    #            + 224 apply = 9216
+    #   backward 336 apply + 1088 head + 24448 for the 8 hidden layers (1056 ReLU pass: gradient in
+    #            and out, mask byte; 1024 + 2 K for the two products each) + 480 encoding = 26352
     roofline_mlp = None
     if wl.kind == "6dmlp" and "mlp_fwd" in stages:
         rows = wl.p.shape[0]
         macs = sum(o * i for o, i in synth.MLP_SHAPES) * rows
         t_f = stages["mlp_fwd"]["ms_per_launch"] * 1e-3
         t_b = stages["mlp_bwd"]["ms_per_launch"] * 1e-3
-        byts = (8960 + 30192) * rows
+        byts = (9216 + 26352) * rows
         hbm = float(pk.get("hbm_gbs", 6800.0))
         peak_bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
         ach = byts / (t_f + t_b) / 1e9
@@ -506,7 +507,7 @@ def our_arm(args, rank: int, world: int, local_rank: int):
                         "work": f"{byts / rows:.0f} bytes per row moved by the layer-by-layer products x {rows} rows",
                         "tensor_tflops": 6.0 * macs / (t_f + t_b) / 1e12,
                         "tensor_frac": 6.0 * macs / (t_f + t_b) / 1e12 / peak_bf16,
-                        "fwd_gbs": 8960 * rows / t_f / 1e9, "bwd_gbs": 30192 * rows / t_b / 1e9}
+                        "fwd_gbs": 9216 * rows / t_f / 1e9, "bwd_gbs": 26352 * rows / t_b / 1e9}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline and wl.kind == "2d":

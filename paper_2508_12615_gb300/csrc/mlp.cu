@@ -176,12 +176,13 @@ __global__ void __launch_bounds__(256) k_mlp_head16(const float* __restrict__ w_
     for (int o = 0; o < kOutPad; ++o) out[o * kWidth + c] = __float2bfloat16_rn(o < kOut ? w_head[o * kWidth + c] : 0.f);
 }
 
-// dz = dh where h > 0 (ReLU) and the bias gradient (column sums of dz) of a 256-wide layer: a warp
-// takes a row, each lane 8 columns with 16-byte accesses; the block sums its column totals in
-// shared memory and adds them with one atomic per column
+// dz = dh where the layer's activation was positive (its ReLU bit-mask from the forward product)
+// and the bias gradient (column sums of dz) of a 256-wide layer: a warp takes a row, each lane 8
+// columns with a 16-byte access and one mask byte; the block sums its column totals in shared
+// memory and adds them with one atomic per column
 constexpr int kReluBlocks = 304;
 __global__ void __launch_bounds__(256) k_relu_backward(const __nv_bfloat16* __restrict__ dh, int ld_dh,
-                                                       const __nv_bfloat16* __restrict__ h, int ld_h, int64_t N,
+                                                       const uint8_t* __restrict__ mask, int64_t N,
                                                        __nv_bfloat16* __restrict__ dz, float* __restrict__ db) {
     pdl_enter();
     __shared__ float s_db[8][kWidth];
@@ -190,18 +191,16 @@ __global__ void __launch_bounds__(256) k_relu_backward(const __nv_bfloat16* __re
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.f;
     for (int64_t r = (int64_t)blockIdx.x * 8 + g; r < N; r += (int64_t)gridDim.x * 8) {
-        const uint4 vh = *reinterpret_cast<const uint4*>(h + r * ld_h + 8 * lane);
+        const uint32_t mb = mask[r * (kWidth / 8) + lane];  // activations 8 lane .. 8 lane + 7 of row r
         const uint4 vd = *reinterpret_cast<const uint4*>(dh + r * ld_dh + 8 * lane);
-        const __nv_bfloat162* ph = reinterpret_cast<const __nv_bfloat162*>(&vh);
         const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&vd);
         uint4 vo;
         __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&vo);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float2 fh = __bfloat1622float2(ph[k]);
             float2 fd = __bfloat1622float2(pd[k]);
-            fd.x = fh.x > 0.f ? fd.x : 0.f;
-            fd.y = fh.y > 0.f ? fd.y : 0.f;
+            fd.x = (mb >> (2 * k)) & 1u ? fd.x : 0.f;
+            fd.y = (mb >> (2 * k + 1)) & 1u ? fd.y : 0.f;
             po[k] = __floats2bfloat162_rn(fd.x, fd.y);  // exact: fd is a bfloat16 value or 0
             acc[2 * k] += fd.x;
             acc[2 * k + 1] += fd.y;
@@ -377,13 +376,13 @@ std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A
 // forward product of layer l: Y [N, out] (row-major, ldy) = X [N, in] (ldx) W^T + b, ReLU for hidden
 // layers (bias b in bfloat16 for them, fp32 for the output layer), whose ReLU bit-mask goes to mask
 std::string layer_forward(MlpLt& lt, int l, const __nv_bfloat16* w, const void* b, const void* x, int ldx, void* y,
-                          int ldy, int64_t N, cudaStream_t s) {
+                          int ldy, int64_t N, void* mask, cudaStream_t s) {
     const LayerShape sh = kShapes[l];
     if (l == kHidden)  // output layer: the padded [16, 256] weights, bias added by k_mlp_apply
         return gemm(lt, true, false, kOutPad, (int)N, kWidth, w, kWidth, x, ldx, y, ldy, CUDA_R_32F, 0.f,
                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
     return gemm(lt, true, false, sh.out, (int)N, sh.in, w, sh.in, x, ldx, y, ldy, CUDA_R_16BF, 0.f,
-                CUBLASLT_EPILOGUE_RELU_BIAS, b, s);
+                CUBLASLT_EPILOGUE_RELU_AUX_BIAS, b, s, mask);
 }
 
 }  // namespace
@@ -413,13 +412,18 @@ void mlp_lt_destroy(MlpLt* lt) {
 
 int64_t mlp_param_count() { return layer_offset(kHidden + 1); }
 
+namespace {
+// bytes of one hidden layer's ReLU bit-mask: 256 bits (32 bytes) per row, rows padded to 128
+size_t mask_bytes(int64_t N) { return (size_t)((N + 127) / 128 * 128) * (kWidth / 8); }
+}  // namespace
+
 // element offset of the padded output layer in the bfloat16 parameter buffer (8 elements = 16 bytes)
 int64_t head16_offset() { return (mlp_param_count() + 7) / 8 * 8; }
 
 MlpSizes mlp_sizes(int64_t N) {
     MlpSizes z;
-    // activations: x5 and seven 256-wide layers
-    z.act = (size_t)N * (kX5 + 7 * kWidth) * sizeof(__nv_bfloat16);
+    // activations: x5 and seven 256-wide layers, then the eight hidden layers' ReLU bit-masks
+    z.act = (size_t)N * (kX5 + 7 * kWidth) * sizeof(__nv_bfloat16) + mask_bytes(N) * kHidden;
     // dh [N, 256], dz [N, 256], encoding gradients [N, 80] x 2, dL/dd [N, 16]; the padded output
     // layer's weight gradient [16, 256] (fp32)
     z.scratch = (size_t)N * (2 * kWidth + 2 * kInPad + kOutPad) * sizeof(__nv_bfloat16) +
@@ -436,6 +440,11 @@ __nv_bfloat16* act_x5(void* act) { return static_cast<__nv_bfloat16*>(act); }
 __nv_bfloat16* act_h(void* act, int64_t N, int l) {
     const int slot = l < 4 ? l : l - 1;  // h0..h3 -> 0..3, h5..h7 -> 4..6 (h4 lives in x5)
     return act_x5(act) + (size_t)N * kX5 + (size_t)slot * N * kWidth;
+}
+// ReLU bit-mask of hidden layer l, written by its forward product: bit m + 256 n is set when
+// activation m of row n is positive (row n's 256 bits are bytes 32 n .. 32 n + 31)
+uint8_t* act_mask(void* act, int64_t N, int l) {
+    return reinterpret_cast<uint8_t*>(act_x5(act) + (size_t)N * (kX5 + 7 * kWidth)) + (size_t)l * mask_bytes(N);
 }
 }  // namespace
 
@@ -459,7 +468,8 @@ std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, con
         const int ldy = l == kHidden ? kOutPad : (l == 4 ? kX5 : kWidth);
         const int64_t boff = layer_offset(l) + (int64_t)kShapes[l].out * kShapes[l].in;
         const __nv_bfloat16* wl = l == kHidden ? w16 + head16_offset() : w16 + layer_offset(l);
-        const std::string e = layer_forward(lt, l, wl, w16 + boff, x, ldx, y, ldy, N, s);
+        const std::string e =
+            layer_forward(lt, l, wl, w16 + boff, x, ldx, y, ldy, N, l == kHidden ? nullptr : act_mask(act, N, l), s);
         if (!e.empty()) return e;
     }
     launch_pdl(k_mlp_apply, ceil_div(N, 256), 256, 0, s, params3, N, d,
@@ -499,11 +509,9 @@ std::string mlp_backward(MlpLt& lt, const float* params3, int64_t N, const void*
     for (int l = kHidden - 1; l >= 0; --l) {
         const LayerShape sh = kShapes[l];
         const __nv_bfloat16* wl = w16 + layer_offset(l);
-        const __nv_bfloat16* hl = l == 4 ? x5 + kInPad : act_h(actm, N, l);
-        const int ld_h = l == 4 ? kX5 : kWidth;
         float* gb = g_theta + layer_offset(l) + (int64_t)sh.out * sh.in;
         launch_pdl(k_relu_backward, (unsigned)std::min<int64_t>(kReluBlocks, ceil_div(N, 8)), 256, 0, s,
-                   (const __nv_bfloat16*)dh, kWidth, hl, ld_h, N, dz, gb);
+                   (const __nv_bfloat16*)dh, kWidth, (const uint8_t*)act_mask(actm, N, l), N, dz, gb);
         count_launches(1);
         // dW_l += dz_l^T x_l  (column-major [in, out] = x^T (in x N) dz (N x out))
         const void* xin = (l == 0 || l == kSkipLayer) ? (const void*)x5 : (const void*)act_h(actm, N, l - 1);
