@@ -197,25 +197,35 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
                                                         const float* __restrict__ partial,
                                                         float* __restrict__ dl_dparams) {
     pdl_enter();
-    const int64_t prim = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (prim >= N) return;
-    const uint32_t off = offsets[prim], cnt = counts[prim];
-    float acc[16];
+    // a warp takes 32 consecutive primitives: it sums the slots of each in turn (lanes over the
+    // slots, coalesced), keeping the 11 totals of primitive k in s_tot[warp][k]; then lane k chains
+    // primitive k, all 32 at once
+    __shared__ float s_tot[8][32][12];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t prim0 = (((int64_t)blockIdx.x * blockDim.x) >> 5 << 5) + (int64_t)warp * 32;
+    for (int k = 0; k < 32; ++k) {
+        const int64_t pk = prim0 + k;
+        if (pk >= N) break;  // uniform across the warp
+        const uint32_t off = offsets[pk], cnt = counts[pk];
+        float acc[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
-    for (uint32_t j = lane; j < cnt; j += 32) {
-        const float4* s = reinterpret_cast<const float4*>(partial + (size_t)(off + j) * kSlot);
-        const float4 x0 = s[0], x1 = s[1], x2 = s[2];
-        acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
-        acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
-        acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z;
+        for (int m = 0; m < 16; ++m) acc[m] = 0.f;
+        for (uint32_t j = lane; j < cnt; j += 32) {
+            const float4* src = reinterpret_cast<const float4*>(partial + (size_t)(off + j) * kSlot);
+            const float4 x0 = src[0], x1 = src[1], x2 = src[2];
+            acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
+            acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
+            acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z;
+        }
+        // lane 2m holds the total of slot m
+        const float tot = warp_reduce_scatter16(acc);
+        if ((lane & 1) == 0 && (lane >> 1) < 11) s_tot[warp][k][lane >> 1] = tot;
     }
-    // lane 2m holds the total of slot m; gather them on lane 0
-    const float tot = warp_reduce_scatter16(acc);
-#pragma unroll
-    for (int k = 0; k < 11; ++k) acc[k] = __shfl_sync(0xffffffffu, tot, 2 * k);
-    if (lane != 0) return;
+    __syncwarp();
+    const int64_t prim = prim0 + lane;
+    if (prim >= N) return;
+    const float* t = s_tot[warp][lane];
+    const uint32_t cnt = counts[prim];
     const float* p = params + prim * WIPES_P2D;
     float* out = dl_dparams + prim * WIPES_P2D;
     if (cnt == 0) {  // off-screen or degenerate: the record's parameters get no gradient
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
         for (int k = 0; k < WIPES_P2D; ++k) out[k] = 0.f;
         return;
     }
-    const float g11 = acc[2], g21 = acc[3], g22 = acc[4];
+    const float g11 = t[2], g21 = t[3], g22 = t[4];
     if (cov2d) {
         const float a = p[2], b = p[3], c = p[4];
         const float u = b * b + c * c, sq = sqrtf(u), aac = fabsf(a * c);
@@ -236,14 +246,14 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     } else {
         chain_rs(p, g11, g21, g22, out);
     }
-    out[0] = acc[0];
-    out[1] = acc[1];
-    out[5] = acc[5];
-    out[6] = acc[6];
-    out[7] = acc[7] * kInvTwoPi;
-    out[8] = acc[8];
-    out[9] = acc[9];
-    out[10] = acc[10];
+    out[0] = t[0];
+    out[1] = t[1];
+    out[5] = t[5];
+    out[6] = t[6];
+    out[7] = t[7] * kInvTwoPi;
+    out[8] = t[8];
+    out[9] = t[9];
+    out[10] = t[10];
 #pragma unroll
     for (int k = 11; k < WIPES_P2D; ++k) out[k] = 0.f;
 }
@@ -308,8 +318,7 @@ void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, in
 void launch_reduce_chain2d(const float* params, int64_t N, int cov2d, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
-    launch_pdl(k_reduce_chain2d, ceil_div(N * 32, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial,
-               dl_dparams);
+    launch_pdl(k_reduce_chain2d, ceil_div(N, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial, dl_dparams);
     count_launches(1);
 }
 
