@@ -43,8 +43,8 @@ OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend":
 # DRAM bytes (read + write) per launch, per (workload, kernel), from the ncu captures summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
 # entry is removed when its kernel changes.
-TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_395_712 + 587_008, ("2d", "k_blend2d"): 9_052_928,
-                 ("5d", "k_backward3d"): 34_066_432 + 19_456, ("5d", "k_blend3d"): 16_343_808 + 5_120}
+TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_391_616 + 597_248, ("2d", "k_blend2d"): 9_052_928,
+                 ("5d", "k_backward3d"): 34_064_640 + 4_352, ("5d", "k_blend3d"): 16_066_816 + 6_656}
 
 
 def parse_args():
