@@ -125,9 +125,9 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
  * of prepared states, of any mix of 2D and 3D frames and image sizes, in persistent launches
  * (up to 128 frames per launch): every block takes (frame, tile) items from a device counter.  A
  * frame renders to the same bits alone (wipes_render2d/3d = prepare + one-frame blend) and in a
- * batch, because both paths run the same per-tile code.  A state stays valid for further blends and
- * for wipes_render_backward until it is prepared again; outs[i] is [H_i, W_i, 3] device memory.
- * At most 64 batch launches may be in flight on one context. */
+ * batch, because both paths run the same per-pixel code.  A state stays valid for further blends
+ * until it is prepared again (and a 2D state for wipes_render_backward); outs[i] is [H_i, W_i, 3]
+ * device memory.  At most 64 batch launches may be in flight on one context. */
 wipes_status wipes_prepare2d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N, int H, int W,
                              const wipes_opts* opts, void* stream);
 wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* params, int64_t N,
@@ -138,7 +138,11 @@ wipes_status wipes_blend_batch(wipes_ctx* ctx, const wipes_state* const* states,
 /* Backward of the last forward pass on `st` (explicit gradients, Sec. 1).
  *   params: the same [N,16|20] array the forward pass read, unchanged since.
  *   dL_dout [H,W,3] device.  dL_dparams [N,16|20] device, overwritten (unused columns are 0).
- *   Errors: INVALID if `st` holds no forward pass. */
+ *   3D: the walk back along a pixel's list runs in chunks of 256 entries at once, each from the
+ *   pixel's transmittance and colour that the one-frame forward recorded at the chunk's end; so a
+ *   3D backward needs wipes_render3d as the last forward on `st` (not prepare + batch).
+ *   Errors: INVALID if `st` holds no forward pass, or (3D) its lists were not blended by
+ *   wipes_render3d since they were prepared. */
 wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float* params, const float* dL_dout,
                                    float* dL_dparams, void* stream);
 

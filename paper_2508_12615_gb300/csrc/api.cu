@@ -209,11 +209,17 @@ struct wipes_state {
     DevBuf mlp_act, mlp_scratch, mlp_d, mlp_theta16;  // deformation network: activations kept for the backward
     int64_t mlp_N = -1;                               // primitives of the last network forward (-1: none)
     DevBuf sort_k, sort_v;                            // second buffers of wipes_sort_pairs
+    // 3D backward in chunks: its items (tile, chunk), each tile's first item, the item count, and
+    // the pixels' state at chunk boundaries and final colour recorded by the one-frame forward
+    DevBuf bwd_items, item_base, n_items, bnd, cfin;
+    int64_t max_items = 0;
+    bool bnd_valid = false;  // the last forward on this state recorded bnd and cfin
 
-    DevBuf* all[29] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
+    DevBuf* all[34] = {&rec,     &rect,    &counts,    &offsets, &dkeys[0], &dkeys[1], &dvals[0], &dvals[1],
                        &block_sums, &total, &keys[0], &keys[1],   &vals[0],   &vals[1],   &inst_prim, &hist,
                        &ranges,  &sprim,   &order,     &T_final, &last,     &partial,  &grad_img, &mlp_act,
-                       &mlp_scratch, &mlp_d, &mlp_theta16, &sort_k, &sort_v};
+                       &mlp_scratch, &mlp_d, &mlp_theta16, &sort_k, &sort_v, &bwd_items, &item_base,
+                       &n_items,  &bnd,     &cfin};
     size_t reserved() const {
         size_t s = 0;
         for (DevBuf* b : all) s += b->cap;
@@ -545,10 +551,17 @@ wipes_status wipes_prepare3d(wipes_ctx* ctx, wipes_state* st, const float* param
         StageTimer t(ctx, WIPES_STAGE_RANGES, s);
         const int n_tiles = st->tiles_x * st->tiles_y;
         WIPES_TRY(ensure(st->order, sizeof(uint32_t) * (size_t)n_tiles));
-        launch_tile_order(st->ranges.as<uint2>(), n_tiles, st->order.as<uint32_t>(), s);
+        // the backward's items: at most one per tile plus one per kBwdChunk instances
+        st->max_items = n_tiles + (st->n_inst + kBwdChunk - 1) / kBwdChunk + 1;
+        WIPES_TRY(ensure(st->bwd_items, sizeof(uint2) * (size_t)st->max_items));
+        WIPES_TRY(ensure(st->item_base, sizeof(uint32_t) * (size_t)n_tiles));
+        WIPES_TRY(ensure(st->n_items, 2 * sizeof(uint32_t)));  // item count, work counter
+        launch_tile_order(st->ranges.as<uint2>(), n_tiles, st->order.as<uint32_t>(), st->bwd_items.as<uint2>(),
+                          st->item_base.as<uint32_t>(), st->n_items.as<uint32_t>(), s);
     }
     WIPES_CUDA(cudaGetLastError());
     st->dims = 3;
+    st->bnd_valid = false;  // until a one-frame forward over these lists records them
     return WIPES_OK;
 }
 
@@ -559,11 +572,18 @@ wipes_status wipes_render3d(wipes_ctx* ctx, wipes_state* st, const float* params
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     AllocStream alloc_stream(s);
+    WIPES_TRY(ensure(st->bnd, sizeof(float4) * kTilePixels * (size_t)st->max_items));
+    WIPES_TRY(ensure(st->cfin, sizeof(float) * 3 * (size_t)H * (size_t)W));
     {
         StageTimer t(ctx, WIPES_STAGE_BLEND, s);
-        launch_blend3d(st->job(out), st->tiles_y, st->order.as<uint32_t>(), s);
+        BlendJob job = st->job(out);
+        job.item_base = st->item_base.as<uint32_t>();
+        job.bnd = st->bnd.as<float4>();
+        job.cfin = st->cfin.as<float>();
+        launch_blend3d(job, st->tiles_y, st->order.as<uint32_t>(), s);
     }
     WIPES_CUDA(cudaGetLastError());
+    st->bnd_valid = true;
     return WIPES_OK;
 }
 
@@ -599,6 +619,8 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
     if (!ctx || !st || !dL_dout || (st->N > 0 && (!params || !dL_dparams)))
         return fail(WIPES_ERR_INVALID, "null argument");
     if (st->dims != 2 && st->dims != 3) return fail(WIPES_ERR_INVALID, "state holds no forward pass");
+    if (st->dims == 3 && !st->bnd_valid)
+        return fail(WIPES_ERR_INVALID, "the 3D backward needs a one-frame forward (wipes_render3d) on the state");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     AllocStream alloc_stream(s);
@@ -618,9 +640,11 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
         {
             StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
             if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * 12 * (size_t)N, s));
+            const BwdChunks ch{st->bwd_items.as<uint2>(), st->n_items.as<uint32_t>(), st->item_base.as<uint32_t>(),
+                               st->bnd.as<float4>(), st->cfin.as<float>(), st->n_items.as<unsigned int>() + 1};
             launch_backward3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), st->W, st->H, st->tiles_x,
-                              st->tiles_y, blend_opts(st->opts), st->T_final.as<float>(), st->last.as<uint32_t>(),
-                              dL_dout, st->grad_img.as<float>(), st->order.as<uint32_t>(), s);
+                              blend_opts(st->opts), st->T_final.as<float>(), st->last.as<uint32_t>(), dL_dout,
+                              st->grad_img.as<float>(), ch, st->max_items, s);
         }
         StageTimer t(ctx, WIPES_STAGE_BWD_CHAIN, s);
         launch_chain3d(params, N, st->cam, st->W, st->H, st->opts.dilation, st->opts.freq_proj_mode,

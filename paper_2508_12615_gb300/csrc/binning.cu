@@ -497,32 +497,51 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(const __grid_cons
 // Order of the tiles for the blend kernels, longest list first: tiles are bucketed by the bit
 // length of their list length and the buckets laid out in decreasing order (the order inside a
 // bucket is arbitrary).  The block scheduler starts blocks in index order, so the tiles with the
-// most work start first and short tiles fill in at the end.  One block does all tiles.
+// most work start first and short tiles fill in at the end.  The same pass lists the 3D backward's
+// work items in that order: tile t with a list of len entries has bwd_chunks(len) chunks (none when
+// empty), items item_base[t] .. item_base[t] + chunks - 1 = (t, chunk).  One block does all
+// tiles.
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderBuckets = 33;
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint2* __restrict__ ranges, int n_tiles,
-                                                              uint32_t* __restrict__ order) {
+                                                              uint32_t* __restrict__ order, uint2* __restrict__ items,
+                                                              uint32_t* __restrict__ item_base,
+                                                              uint32_t* __restrict__ n_items) {
     pdl_enter();
     __shared__ uint32_t s_cnt[kOrderBuckets];
     __shared__ uint32_t s_cur[kOrderBuckets];
-    if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0u;
+    __shared__ uint32_t s_icnt[kOrderBuckets];
+    __shared__ uint32_t s_icur[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0u, s_icnt[threadIdx.x] = 0u;
     __syncthreads();
     for (int t = threadIdx.x; t < n_tiles; t += kOrderThreads) {
         const uint2 r = ranges[t];
-        atomicAdd(&s_cnt[32 - __clz(r.y - r.x)], 1u);
+        const uint32_t len = r.y - r.x, b = 32 - __clz(len);
+        atomicAdd(&s_cnt[b], 1u);
+        if (len) atomicAdd(&s_icnt[b], bwd_chunks(len));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t run = 0;
+        uint32_t run = 0, irun = 0;
         for (int b = kOrderBuckets - 1; b >= 0; --b) {
             s_cur[b] = run;
             run += s_cnt[b];
+            s_icur[b] = irun;
+            irun += s_icnt[b];
         }
+        if (n_items) *n_items = irun;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < n_tiles; t += kOrderThreads) {
         const uint2 r = ranges[t];
-        order[atomicAdd(&s_cur[32 - __clz(r.y - r.x)], 1u)] = (uint32_t)t;
+        const uint32_t len = r.y - r.x, b = 32 - __clz(len);
+        order[atomicAdd(&s_cur[b], 1u)] = (uint32_t)t;
+        if (items && len) {
+            const uint32_t k_n = bwd_chunks(len);
+            const uint32_t base = atomicAdd(&s_icur[b], k_n);
+            item_base[t] = base;
+            for (uint32_t k = 0; k < k_n; ++k) items[base + k] = make_uint2((uint32_t)t, k);
+        }
     }
 }
 
@@ -562,8 +581,9 @@ void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, i
     launch_pdl(k_tile_ranges, grid, 256, 0, stream, sorted_keys, n, ranges); count_launches(1);
 }
 
-void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream) {
-    launch_pdl(k_tile_order, 1, kOrderThreads, 0, stream, ranges, n_tiles, order);
+void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint2* items, uint32_t* item_base,
+                       uint32_t* n_items, cudaStream_t stream) {
+    launch_pdl(k_tile_order, 1, kOrderThreads, 0, stream, ranges, n_tiles, order, items, item_base, n_items);
     count_launches(1);
 }
 

@@ -440,7 +440,17 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
 int64_t sort_timeout_probe_words();
 void sort_timeout_probe(uint32_t* ws, unsigned int* error, cudaStream_t stream);
 // order[0 .. n_tiles) = the tiles, longest list first (see k_tile_order)
-void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t stream);
+// 3D backward: tile lists longer than kBwdChunkFrom entries are walked in chunks of kBwdChunk
+// entries at once (a multiple of the 3D blend's batch of 32); shorter ones in one piece
+constexpr int kBwdChunk = 256;
+constexpr int kBwdChunkFrom = 256;
+__host__ __device__ inline uint32_t bwd_chunks(uint32_t len) {
+    return len == 0u ? 0u : (len > (uint32_t)kBwdChunkFrom ? (len + kBwdChunk - 1) / kBwdChunk : 1u);
+}
+// tiles longest list first; and the 3D backward's items (tile, chunk) in that order (items,
+// item_base[tile] = the tile's first item, *n_items) when `items` is given
+void launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint2* items, uint32_t* item_base,
+                       uint32_t* n_items, cudaStream_t stream);
 
 // raster2d.cu
 // Tile lists: entry i of the sorted list is emission index sorted[i] of primitive prim[i].
@@ -463,6 +473,12 @@ struct BlendJob {
     uint32_t* last;  // 3D only
     int dims, W, H, tiles_x;
     BlendOpts3 o;    // 2D uses cutoff2 and lim only
+    // 3D one-frame forward, for the chunked backward: every pixel's (T, colour) before list entry
+    // k kBwdChunk, k >= 1, at bnd[(item_base[tile] + k) 256 + pixel of the tile], and its final
+    // colour without the background at cfin (3 floats per pixel); unused when bnd is null
+    const uint32_t* item_base = nullptr;
+    float4* bnd = nullptr;
+    float* cfin = nullptr;
 };
 void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream);
 void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
@@ -473,11 +489,20 @@ void launch_reduce_chain2d(const float* params, int64_t N, int cov2d, const uint
 void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, int tiles_x, int tiles_y, float cutoff2,
                         const uint32_t* last, unsigned long long* counters, cudaStream_t stream);
 
-// raster3d.cu: one 64-thread block per 8x8 quad, tiles in `order` (launch_tile_order)
+// raster3d.cu: one warp per 8x8 quad, tiles in `order` (launch_tile_order); the backward one warp
+// per (quad, chunk of kBwdChunk list entries), items from launch_tile_order, at most max_items
+struct BwdChunks {
+    const uint2* items;
+    const uint32_t* n_items;
+    const uint32_t* item_base;
+    const float4* bnd;
+    const float* cfin;
+    unsigned int* counter;  // work counter of the persistent backward (zeroed at its launch)
+};
 void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cudaStream_t stream);
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
-                       int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
-                       const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream);
+                       const BlendOpts3& o, const float* T_final, const uint32_t* last, const float* dl_dout,
+                       float* grad_img, const BwdChunks& ch, int64_t max_items, cudaStream_t stream);
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation, int fmode,
                     int sh_degree, const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 

@@ -123,17 +123,15 @@ __device__ __forceinline__ void bwd_apply(const BwdEval& r, const ulonglong2 (*s
 // with one atomic per component.  Batches of 32 entries are staged in shared memory with the bit
 // "the cutoff ellipse reaches the quad"; the records of the next batch are loaded while the
 // current one is processed.
-__global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
-                                                   TileLists tl, int W, int H, int tiles_x, BlendOpts3 o,
-                                                   const float* __restrict__ T_final,
-                                                   const uint32_t* __restrict__ last,
-                                                   const float* __restrict__ dl_dout,
-                                                   float* __restrict__ grad_img,
-                                                   const uint32_t* __restrict__ order) {
-    pdl_enter();
-    __shared__ ulonglong2 s_e[6][32];
-    __shared__ uint32_t s_id[32];
-    const int tile = (int)order[blockIdx.x >> 2], quad = (int)(blockIdx.x & 3u);
+__device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
+                                           const TileLists& tl, int W, int H, int tiles_x, const BlendOpts3& o,
+                                           const float* __restrict__ T_final, const uint32_t* __restrict__ last,
+                                           const float* __restrict__ dl_dout, float* __restrict__ grad_img,
+                                           const BwdChunks& ch, ulonglong2 (*s_e)[32], uint32_t* s_id,
+                                           uint32_t item, int quad) {
+    const uint2 it = ch.items[item];  // (tile, chunk)
+    const int tile = (int)it.x;
+    const uint32_t chunk = it.y;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31;
     const int x0 = tx * kTile + (quad & 1) * 8, y0 = ty * kTile + (quad >> 1) * 8;
@@ -142,8 +140,33 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
     const size_t pix0 = (size_t)v * W + u, pix1 = pix0 + (size_t)4 * W;
     const f2 PX = f2_dup((float)u + 0.5f), PY = f2_pack((float)v + 0.5f, (float)(v + 4) + 0.5f);
     const uint2 range = tl.ranges[tile];
-    f2 T = f2_pack(in0 ? T_final[pix0] : 1.f, in1 ? T_final[pix1] : 1.f);
     const uint32_t last0 = in0 ? last[pix0] : 0u, last1 = in1 ? last[pix1] : 0u;
+    // entries past every pixel's last contributor are skipped; this item walks [c_lo, min(c_hi,
+    // max last)) of the tile list (chunk kBwdChunk .. its end, the list's end for the last chunk),
+    // back to front
+    const uint32_t max_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
+    const uint32_t n_chunks = bwd_chunks(range.y - range.x);
+    const uint32_t c_lo = chunk * kBwdChunk, c_hi = chunk + 1 == n_chunks ? range.y - range.x : c_lo + kBwdChunk;
+    if (c_lo >= max_last) return;  // uniform across the warp
+    // a pixel whose last contributor lies past this chunk starts from its state after the chunk,
+    // recorded by the forward pass; the others from the final transmittance
+    const float Tf0 = in0 ? T_final[pix0] : 1.f, Tf1 = in1 ? T_final[pix1] : 1.f;
+    const bool rec0 = last0 > c_hi, rec1 = last1 > c_hi;
+    float4 B0 = make_float4(Tf0, 0.f, 0.f, 0.f), B1 = make_float4(Tf1, 0.f, 0.f, 0.f);
+    float Cf0[3] = {0.f, 0.f, 0.f}, Cf1[3] = {0.f, 0.f, 0.f};
+    if (rec0 || rec1) {
+        const float4* rowb = ch.bnd + (size_t)(ch.item_base[tile] + chunk + 1) * kTilePixels;
+        const int px_in_tile = (quad & 1) * 8 + (lane & 7) + ((quad >> 1) * 8 + (lane >> 3)) * kTile;
+        if (rec0) {
+            B0 = rowb[px_in_tile];
+            for (int k = 0; k < 3; ++k) Cf0[k] = ch.cfin[pix0 * 3 + k];
+        }
+        if (rec1) {
+            B1 = rowb[px_in_tile + 4 * kTile];
+            for (int k = 0; k < 3; ++k) Cf1[k] = ch.cfin[pix1 * 3 + k];
+        }
+    }
+    f2 T = f2_pack(B0.x, B1.x);
     f2 g0 = f2_dup(0.f), g1 = g0, g2 = g0;
     if (in0 || in1) {
         const float* a0 = dl_dout + pix0 * 3;
@@ -152,13 +175,17 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
         g1 = f2_pack(in0 ? a0[1] : 0.f, in1 ? a1[1] : 0.f);
         g2 = f2_pack(in0 ? a0[2] : 0.f, in1 ? a1[2] : 0.f);
     }
-    // colour accumulated behind the current primitive, starting with the background term
-    f2 S0 = f2_mul(T, f2_dup(o.bg[0])), S1 = f2_mul(T, f2_dup(o.bg[1])), S2 = f2_mul(T, f2_dup(o.bg[2]));
-    // entries past every pixel's last contributor are skipped; batches run [b0, b_end) downwards
-    const uint32_t max_last = __reduce_max_sync(0xffffffffu, max(last0, last1));
-    const uint32_t end = range.x + max_last;
+    // colour accumulated behind the current primitive: the background term, plus (for a pixel
+    // starting after the chunk) the colour of the entries after the chunk
+    const f2 TF = f2_pack(Tf0, Tf1);
+    f2 S0 = f2_fma(TF, f2_dup(o.bg[0]), f2_pack(rec0 ? Cf0[0] - B0.y : 0.f, rec1 ? Cf1[0] - B1.y : 0.f));
+    f2 S1 = f2_fma(TF, f2_dup(o.bg[1]), f2_pack(rec0 ? Cf0[1] - B0.z : 0.f, rec1 ? Cf1[1] - B1.z : 0.f));
+    f2 S2 = f2_fma(TF, f2_dup(o.bg[2]), f2_pack(rec0 ? Cf0[2] - B0.w : 0.f, rec1 ? Cf1[2] - B1.w : 0.f));
+    // batches run [b0, b_end) downwards over the chunk's part below max last
+    const uint32_t lo = range.x + c_lo;
+    const uint32_t end = range.x + min(c_hi, max_last);
     uint32_t b_end = end;
-    uint32_t b0 = end - min(end - range.x, 32u);
+    uint32_t b0 = end - min(end - lo, 32u);
     // software pipeline: records (and id) of the batch to stage next, id of the batch after it
     float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
     PixRect nR{0, 0, -1, -1};
@@ -170,9 +197,9 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
         nC = rec[(size_t)nid * kRecF4 + 2];
         nR = rect[nid];
     }
-    uint32_t nb0 = b0 - min(b0 - range.x, 32u);  // start of the next batch
+    uint32_t nb0 = b0 - min(b0 - lo, 32u);  // start of the next batch
     if (nb0 + lane < b0) np = tl.prim[nb0 + lane];
-    while (b_end > range.x) {
+    while (b_end > lo) {
         const int n = (int)(b_end - b0);
         __syncwarp();
         bool hit = false;
@@ -186,7 +213,7 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
         uint32_t bal = __ballot_sync(0xffffffffu, hit);
         __syncwarp();
         // loads for the next two batches: [nb0, b0) and [nnb0, nb0)
-        const uint32_t nnb0 = nb0 - min(nb0 - range.x, 32u);
+        const uint32_t nnb0 = nb0 - min(nb0 - lo, 32u);
         if (nb0 + lane < b0) {
             nid = np;
             nA = rec[(size_t)nid * kRecF4 + 0];
@@ -214,6 +241,29 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
         b_end = b0;
         b0 = nb0;
         nb0 = nnb0;
+    }
+}
+
+// Persistent: each warp takes (item, quad) units in order from a counter until they run out, so no
+// block is spent on an item past the last one.
+__global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
+                                                   TileLists tl, int W, int H, int tiles_x, BlendOpts3 o,
+                                                   const float* __restrict__ T_final,
+                                                   const uint32_t* __restrict__ last,
+                                                   const float* __restrict__ dl_dout,
+                                                   float* __restrict__ grad_img, BwdChunks ch) {
+    pdl_enter();
+    __shared__ ulonglong2 s_e[6][32];
+    __shared__ uint32_t s_id[32];
+    const uint32_t n_units = 4u * *ch.n_items;
+    for (;;) {
+        uint32_t unit = 0u;
+        if ((threadIdx.x & 31) == 0) unit = atomicAdd(ch.counter, 1u);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= n_units) break;
+        __syncwarp();
+        bwd3d_unit(rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout, grad_img, ch, s_e, s_id, unit >> 2,
+                   (int)(unit & 3u));
     }
 }
 
@@ -433,10 +483,17 @@ void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cud
 }
 
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
-                       int tiles_y, const BlendOpts3& o, const float* T_final, const uint32_t* last,
-                       const float* dl_dout, float* grad_img, const uint32_t* order, cudaStream_t stream) {
-    launch_pdl(k_backward3d, 4 * tiles_x * tiles_y, 32, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout,
-               grad_img, order);
+                       const BlendOpts3& o, const float* T_final, const uint32_t* last, const float* dl_dout,
+                       float* grad_img, const BwdChunks& ch, int64_t max_items, cudaStream_t stream) {
+    if (max_items <= 0) return;
+    cudaMemsetAsync(ch.counter, 0, sizeof(unsigned int), stream);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward3d, 32, 0);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>((int64_t)std::max(1, per_sm) * std::max(1, sms), 4 * max_items);
+    launch_pdl(k_backward3d, (unsigned)grid, 32, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout,
+               grad_img, ch);
     count_launches(1);
 }
 
