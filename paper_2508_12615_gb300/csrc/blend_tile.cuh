@@ -163,6 +163,11 @@ __device__ __forceinline__ void store_px3(const BlendJob& job, int u, int v, con
     job.out[pix * 3 + 0] = fmaf(s.T, job.o.bg[0], s.c0);
     job.out[pix * 3 + 1] = fmaf(s.T, job.o.bg[1], s.c1);
     job.out[pix * 3 + 2] = fmaf(s.T, job.o.bg[2], s.c2);
+    if (job.cfin) {  // the colour without the background, for the chunked backward
+        job.cfin[pix * 3 + 0] = s.c0;
+        job.cfin[pix * 3 + 1] = s.c1;
+        job.cfin[pix * 3 + 2] = s.c2;
+    }
     job.T_final[pix] = s.T;
     job.last[pix] = s.last;
 }
@@ -305,15 +310,19 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
         nR = rect[p];
     }
     if (range.x + kQuadThreads + lane < range.y) np = tl.prim[range.x + kQuadThreads + lane];
+    // the chunked backward's boundaries: the pixels' state before list entries kBwdChunk, 2 kBwdChunk,
+    // ... of a list of more than one chunk, recorded when the walk reaches them
+    const uint32_t n_bnd = job.bnd ? bwd_chunks(range.y - range.x) : 0u;
+    uint32_t next_bnd = n_bnd > 1u ? range.x + kBwdChunk : 0xFFFFFFFFu;
+    float4* rowb = n_bnd > 1u ? job.bnd + (size_t)job.item_base[tile] * kTilePixels : nullptr;
+    const int px_in_tile = (quad & 1) * 8 + (lane & 7) + ((quad >> 1) * 8 + (lane >> 3)) * kTile;
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kQuadThreads) {
         if (__all_sync(0xffffffffu, done0 && done1)) break;
-        // every kBwdChunk entries: the pixels' state for the chunked backward
-        if (job.bnd && b0 > range.x && (b0 - range.x) % kBwdChunk == 0 &&
-            (b0 - range.x) / kBwdChunk < bwd_chunks(range.y - range.x)) {
-            float4* rowb = job.bnd + (size_t)(job.item_base[tile] + (b0 - range.x) / kBwdChunk) * kTilePixels;
-            const int px_in_tile = (quad & 1) * 8 + (lane & 7) + ((quad >> 1) * 8 + (lane >> 3)) * kTile;
+        if (b0 == next_bnd) {
+            rowb += kTilePixels;
             rowb[px_in_tile] = make_float4(f2_lo(T), f2_lo(c0), f2_lo(c1), f2_lo(c2));
             rowb[px_in_tile + 4 * kTile] = make_float4(f2_hi(T), f2_hi(c0), f2_hi(c1), f2_hi(c2));
+            next_bnd += kBwdChunk;
         }
         const int n = (int)min((uint32_t)kQuadThreads, range.y - b0);
         __syncwarp();
@@ -352,16 +361,6 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
             apply3_entry(ea, s_e, j1, o, T, c0, c1, c2, last0, last1, done0, done1, b0 - range.x + (uint32_t)j1 + 1u);
             if (j2 >= 0)
                 apply3_entry(eb, s_e, j2, o, T, c0, c1, c2, last0, last1, done0, done1, b0 - range.x + (uint32_t)j2 + 1u);
-        }
-    }
-    if (job.cfin) {
-        if (in0) {
-            float* cf = job.cfin + ((size_t)v * job.W + u) * 3;
-            cf[0] = f2_lo(c0), cf[1] = f2_lo(c1), cf[2] = f2_lo(c2);
-        }
-        if (in1) {
-            float* cf = job.cfin + ((size_t)(v + 4) * job.W + u) * 3;
-            cf[0] = f2_hi(c0), cf[1] = f2_hi(c1), cf[2] = f2_hi(c2);
         }
     }
     if (in0) store_px3(job, u, v, Px3{f2_lo(T), f2_lo(c0), f2_lo(c1), f2_lo(c2), last0, done0});
