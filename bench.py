@@ -44,7 +44,7 @@ OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend":
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
 # entry is removed when its kernel changes.
 TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_391_616 + 597_248, ("2d", "k_blend2d"): 9_052_928,
-                 ("5d", "k_backward3d"): 34_064_640 + 4_352, ("5d", "k_blend3d"): 16_066_816 + 6_656}
+                 ("5d", "k_backward3d"): 27_144_448 + 768, ("5d", "k_blend3d"): 16_071_168 + 70_912}
 
 
 def parse_args():
@@ -157,19 +157,29 @@ def oracle_step_sample(p, target, H, W, budget_s: float):
     oracle.grad2d(sub, H, W, g)
     t_bwd_prim = (time.perf_counter() - t0) / len(sub)
     full = t_fwd_px * H * W + t_bwd_prim * n
+
+    def sample(frac):
+        n_rows = max(1, int(round(H * frac)))
+        n_prims = max(1, int(round(n * frac)))
+        pix = np.stack(np.meshgrid(np.arange(W), np.arange(n_rows)), -1).reshape(-1, 2).astype(np.int32)
+        t0 = time.perf_counter()
+        img_rows = oracle.render2d(p, H, W, pixels=pix)
+        t_f = time.perf_counter() - t0
+        # upstream gradient of the mean squared error on the sampled rows
+        gimg = np.zeros((H, W, 3), np.float32)
+        gimg[:n_rows] = (2.0 / (H * W * 3)) * (img_rows.reshape(n_rows, W, 3) - target[:n_rows])
+        t0 = time.perf_counter()
+        oracle.grad2d(p[:n_prims], H, W, gimg)
+        t_b = time.perf_counter() - t0
+        return n_rows, n_prims, t_f, t_b
+
     frac = min(1.0, budget_s / max(full, 1e-9))
-    n_rows = max(1, int(round(H * frac)))
-    n_prims = max(1, int(round(n * frac)))
-    pix = np.stack(np.meshgrid(np.arange(W), np.arange(n_rows)), -1).reshape(-1, 2).astype(np.int32)
-    t0 = time.perf_counter()
-    img_rows = oracle.render2d(p, H, W, pixels=pix)
-    t_f = time.perf_counter() - t0
-    # upstream gradient of the mean squared error on the sampled rows
-    gimg = np.zeros((H, W, 3), np.float32)
-    gimg[:n_rows] = (2.0 / (H * W * 3)) * (img_rows.reshape(n_rows, W, 3) - target[:n_rows])
-    t0 = time.perf_counter()
-    oracle.grad2d(p[:n_prims], H, W, gimg)
-    t_b = time.perf_counter() - t0
+    n_rows, n_prims, t_f, t_b = sample(frac)
+    # the tiny calibration samples overstate the per-item cost (thread start-up, cold caches): when
+    # the sample took well under the budget, size it again from its own measured rate
+    if frac < 1.0 and t_f + t_b < 0.5 * budget_s:
+        est = t_f * (H / n_rows) + t_b * (n / n_prims)
+        n_rows, n_prims, t_f, t_b = sample(min(1.0, 0.9 * budget_s / max(est, 1e-9)))
     per_step = t_f * (H / n_rows) + t_b * (n / n_prims)
     desc = (f"forward on {n_rows} of {H} rows and backward for {n_prims} of {n} primitives "
             f"({t_f + t_b:.1f} s of CPU work), scaled to one full step")
