@@ -277,7 +277,7 @@ wipes_status wipes_sort_pairs(wipes_ctx* ctx, wipes_state* st, uint32_t* keys, u
 /* Diagnostic: run one radix-sort pass on scratch data in which the tile before the block's tile
  * never publishes its counts, so that the block's bounded look-back runs out (after well under a
  * second).  Returns WIPES_ERR_TIMEOUT when the wait ran out and was reported, as it should; the
- * context stays usable.  Allocates and frees about 400 KB of scratch; synchronises `stream`. */
+ * context stays usable.  Allocates and frees about 140 KB of scratch; synchronises `stream`. */
 wipes_status wipes_selftest_sort_timeout(wipes_ctx* ctx, void* stream);
 
 #ifdef __cplusplus

@@ -212,10 +212,10 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
 
 // ---------------------------------------------------------------------------------------------
 // stable LSD radix sort of 32-bit keys with 32-bit values, up to 8 bits per pass, in one of two
-// schemes that rank a tile of 8192 keys the same way (radix_sort_pairs picks one per call).
+// schemes that rank a tile of keys the same way (radix_sort_pairs picks one per call).
 // Onesweep, one kernel per pass: k_sort_histogram counts every pass's digits over all keys once.
 // In a pass, blocks take
-// tiles of 8192 keys in index order from a counter, rank their keys stably, publish each digit's
+// tiles of 4096 keys in index order from a counter, rank their keys stably, publish each digit's
 // count for their tile and obtain the counts of all earlier tiles by a decoupled look-back over
 // the published words (a word holds a tile's count, or the inclusive prefix up to that tile,
 // with a flag in its top bits).  Every look-back wait is bounded: when it runs out, the block
@@ -225,7 +225,11 @@ __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
 constexpr int kSortItems = 16;
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 8192 keys per block
+constexpr int kSortTile = kSortThreads * kSortItems;  // 8192 keys per block (reduce-then-scan)
+// Onesweep serves the short sorts of many passes, whose time is the latency of a block's tile:
+// half the tile puts twice the blocks to work (300k keys: 74 blocks instead of 37).
+constexpr int kPassItems = 8;
+constexpr int kPassTile = kSortThreads * kPassItems;  // 4096 keys per block (onesweep)
 constexpr int kMaxRadix = 256;
 constexpr int kMaxPasses = 4;
 constexpr unsigned long long kAggregate = 1ull << 62, kPrefix = 2ull << 62, kCountMask = (1ull << 62) - 1ull;
@@ -296,12 +300,17 @@ __global__ void __launch_bounds__(kThreads) k_sort_histogram(const uint32_t* __r
     }
 }
 
-// Shared memory of k_sort_pass (dynamic, 16-byte aligned words): keys and values of the tile,
-// the per-warp digit counts, then the small per-digit arrays.  The two peer tables of the ranking
-// live in the key area, which is free until the keys are placed.
+// Shared memory of k_sort_downsweep (dynamic, 16-byte aligned words): keys and values of the
+// tile, the per-warp digit counts, then the small per-digit arrays.  The two peer tables of the
+// ranking live in the key area, which is free until the keys are placed.
 constexpr int kSortSmemWords = 2 * kSortTile + kSortWarps * kMaxRadix + 3 * kMaxRadix + kSortWarps + 4;
 constexpr size_t kSortSmemBytes = sizeof(uint32_t) * kSortSmemWords;
 static_assert(2 * kSortWarps * kMaxRadix <= kSortTile, "the peer tables must fit in the key area");
+// k_sort_pass: the same arrays for its smaller tile, and the peer tables after them (they do not
+// fit in its key area).
+constexpr int kPassPeerWords = 2 * kPassTile + kSortWarps * kMaxRadix + 3 * kMaxRadix + kSortWarps + 4;
+constexpr size_t kPassSmemBytes = sizeof(uint32_t) * (kPassPeerWords + 2 * kSortWarps * kMaxRadix);
+static_assert(kPassPeerWords % 4 == 0, "the peer tables start 16-byte aligned");
 
 struct SortPassArgs {
     const uint32_t* keys_in;
@@ -318,8 +327,8 @@ struct SortPassArgs {
     uint32_t* gathered;
 };
 
-// One tile of a pass.  FULL: the tile holds kSortTile keys (every tile but the last), so no
-// element needs a bounds check.  Item i of warp w's run is tile element w * 32 kSortItems + 32 i +
+// One tile of a pass.  FULL: the tile holds kPassTile keys (every tile but the last), so no
+// element needs a bounds check.  Item i of warp w's run is tile element w * 32 kPassItems + 32 i +
 // lane, so that a warp's loads and the element order of its ranking agree.
 template <bool FULL>
 __device__ __forceinline__ void sort_tile(const SortPassArgs& a, uint32_t tile, int cnt, uint32_t* s_keys,
@@ -329,18 +338,18 @@ __device__ __forceinline__ void sort_tile(const SortPassArgs& a, uint32_t tile, 
     const uint32_t mask = (uint32_t)radix - 1u;
     const int shift = a.shift;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t blk = (int64_t)tile * kSortTile;
-    const int run = warp * (kSortItems * 32) + lane;
+    const int64_t blk = (int64_t)tile * kPassTile;
+    const int run = warp * (kPassItems * 32) + lane;
     const uint32_t* keys_in = a.keys_in + blk;
     auto valid = [&](int i) { return FULL || run + 32 * i < cnt; };
     // the keys wait in s_vals at their element position until they are placed; the tile's digit
     // counts are taken first so that later tiles can use them as early as possible
     {
-        uint32_t k[kSortItems];
+        uint32_t k[kPassItems];
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) k[i] = valid(i) ? keys_in[run + 32 * i] : 0u;
+        for (int i = 0; i < kPassItems; ++i) k[i] = valid(i) ? keys_in[run + 32 * i] : 0u;
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
+        for (int i = 0; i < kPassItems; ++i) {
             s_vals[run + 32 * i] = k[i];
             if (valid(i)) atomicAdd(&s_cnt[(k[i] >> shift) & mask], 1u);
         }
@@ -354,11 +363,11 @@ __device__ __forceinline__ void sort_tile(const SortPassArgs& a, uint32_t tile, 
     // the digit's word and reads the word back; the last of them then clears it and advances the
     // digit's running count.  Items alternate between two tables, so a table word is cleared a full
     // item before it is used again.
-    uint32_t(*s_peer)[kSortWarps][kMaxRadix] = reinterpret_cast<uint32_t(*)[kSortWarps][kMaxRadix]>(s_keys);
+    uint32_t(*s_peer)[kSortWarps][kMaxRadix] = reinterpret_cast<uint32_t(*)[kSortWarps][kMaxRadix]>(s_keys + kPassPeerWords);
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t pos[kSortItems];
+    uint32_t pos[kPassItems];
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
+    for (int i = 0; i < kPassItems; ++i) {
         const bool ok = valid(i);
         const uint32_t d = (s_vals[run + 32 * i] >> shift) & mask;
         uint32_t* peer = &s_peer[i & 1][warp][d];
@@ -432,7 +441,7 @@ __device__ __forceinline__ void sort_tile(const SortPassArgs& a, uint32_t tile, 
     // keys to their place in the tile's digit order, then the values (read only now, so that they
     // occupy no registers during the ranking)
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
+    for (int i = 0; i < kPassItems; ++i) {
         if (valid(i)) {
             const uint32_t key = s_vals[run + 32 * i];
             const uint32_t d = (key >> shift) & mask;
@@ -442,17 +451,17 @@ __device__ __forceinline__ void sort_tile(const SortPassArgs& a, uint32_t tile, 
     }
     {
         const uint32_t* vals_in = a.vals_in + blk;
-        uint32_t v[kSortItems];
+        uint32_t v[kPassItems];
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) v[i] = valid(i) ? vals_in[run + 32 * i] : 0u;
+        for (int i = 0; i < kPassItems; ++i) v[i] = valid(i) ? vals_in[run + 32 * i] : 0u;
         __syncthreads();  // every key has left s_vals
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i)
+        for (int i = 0; i < kPassItems; ++i)
             if (valid(i)) s_vals[pos[i]] = v[i];
     }
     __syncthreads();
     const int64_t n = a.n;
-    for (int t = threadIdx.x; t < (FULL ? kSortTile : cnt); t += kSortThreads) {
+    for (int t = threadIdx.x; t < (FULL ? kPassTile : cnt); t += kSortThreads) {
         const uint32_t key = s_keys[t];
         const uint32_t g = s_gbase[(key >> shift) & mask] + (uint32_t)t;
         if ((int64_t)g >= n) continue;  // only after a look-back that ran out (error word set)
@@ -467,16 +476,16 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(const __grid_cons
     pdl_enter();
     extern __shared__ uint4 s_sort_raw[];
     uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_sort_raw);
-    uint32_t* s_vals = s_keys + kSortTile;
-    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kSortTile);
-    uint32_t* s_cnt = s_vals + kSortTile + kSortWarps * kMaxRadix;
+    uint32_t* s_vals = s_keys + kPassTile;
+    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kPassTile);
+    uint32_t* s_cnt = s_vals + kPassTile + kSortWarps * kMaxRadix;
     uint32_t* s_dstart = s_cnt + kMaxRadix;
     uint32_t* s_gbase = s_dstart + kMaxRadix;
     uint32_t* s_warp = s_gbase + kMaxRadix;
     uint32_t* s_tile_p = s_warp + kSortWarps;
     const int radix = 1 << a.nbits;
     if (threadIdx.x == 0) *s_tile_p = atomicAdd(a.tile_counter, 1u);
-    for (int k = threadIdx.x; k < 2 * kSortWarps * kMaxRadix; k += kSortThreads) s_keys[k] = 0u;  // peer tables
+    for (int k = threadIdx.x; k < 2 * kSortWarps * kMaxRadix; k += kSortThreads) s_keys[kPassPeerWords + k] = 0u;
     for (int k = threadIdx.x; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_wc[0][0])[k] = 0u;
     if ((int)threadIdx.x < kMaxRadix) s_cnt[threadIdx.x] = 0u;
     // global start of each digit = exclusive scan of the digit totals
@@ -487,9 +496,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(const __grid_cons
     }
     __syncthreads();
     const uint32_t tile = *s_tile_p;
-    const int64_t left = a.n - (int64_t)tile * kSortTile;
-    if (left >= kSortTile)
-        sort_tile<true>(a, tile, kSortTile, s_keys, s_vals, s_wc, s_cnt, s_dstart, s_gbase, s_warp);
+    const int64_t left = a.n - (int64_t)tile * kPassTile;
+    if (left >= kPassTile)
+        sort_tile<true>(a, tile, kPassTile, s_keys, s_vals, s_wc, s_cnt, s_dstart, s_gbase, s_warp);
     else
         sort_tile<false>(a, tile, (int)left, s_keys, s_vals, s_wc, s_cnt, s_dstart, s_gbase, s_warp);
 }
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_downsweep(const __grid
 }
 
 int64_t radix_hist_words(int64_t n) {
-    const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kSortTile);
+    const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kPassTile);
     const int64_t onesweep = sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
     int tpc = 0;
     const int64_t chunked = 2 * (int64_t)kMaxRadix * sort_chunks(n, &tpc) + kMaxRadix;
@@ -816,7 +825,7 @@ int64_t radix_hist_words(int64_t n) {
 void sort_pass_attributes() {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmemBytes);
+        cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemBytes);
         cudaFuncSetAttribute(k_sort_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmemBytes);
     });
 }
@@ -859,7 +868,7 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         }
         return cur;
     }
-    const int64_t tiles = ceil_div(n, kSortTile);
+    const int64_t tiles = ceil_div(n, kPassTile);
     uint32_t* totals = hist;
     unsigned int* counters = hist + (int64_t)kMaxPasses * kMaxRadix;
     unsigned long long* status = reinterpret_cast<unsigned long long*>(hist + sort_status_offset_words());
@@ -874,7 +883,7 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         SortPassArgs pa{keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, plan.shift[p], plan.nbits[p],
                         totals + p * kMaxRadix, counters + p, status + (size_t)p * tiles * kMaxRadix, error,
                         last_pass ? table : nullptr, last_pass ? gathered : nullptr};
-        launch_pdl(k_sort_pass, (unsigned)tiles, kSortThreads, kSortSmemBytes, stream, pa);
+        launch_pdl(k_sort_pass, (unsigned)tiles, kSortThreads, kPassSmemBytes, stream, pa);
         count_launches(1);
         cur ^= 1;
     }
@@ -883,10 +892,10 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
 
 // Scratch words of sort_timeout_probe(): keys and values in and out for two tiles, the digit
 // totals, the pass's tile counter and the look-back words of two tiles.
-int64_t sort_timeout_probe_words() { return 4 * 2 * kSortTile + sort_status_offset_words() + 2 * 2 * kMaxRadix; }
+int64_t sort_timeout_probe_words() { return 4 * 2 * kPassTile + sort_status_offset_words() + 2 * 2 * kMaxRadix; }
 
 void sort_timeout_probe(uint32_t* ws, unsigned int* error, cudaStream_t stream) {
-    const int64_t n = 2 * kSortTile;
+    const int64_t n = 2 * kPassTile;
     uint32_t* keys_in = ws;
     uint32_t* vals_in = ws + n;
     uint32_t* keys_out = ws + 2 * n;
@@ -899,7 +908,7 @@ void sort_timeout_probe(uint32_t* ws, unsigned int* error, cudaStream_t stream) 
     cudaMemsetAsync(counter, 1, 1, stream);
     sort_pass_attributes();
     SortPassArgs pa{keys_in, vals_in, keys_out, vals_out, n, 0, 8, hist, counter, status, error, nullptr, nullptr};
-    launch_pdl(k_sort_pass, 1u, kSortThreads, kSortSmemBytes, stream, pa);
+    launch_pdl(k_sort_pass, 1u, kSortThreads, kPassSmemBytes, stream, pa);
     count_launches(1);
 }
 

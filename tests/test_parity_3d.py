@@ -185,6 +185,41 @@ def test_autograd_function_and_culling():
         assert ok, (worst, idx)
 
 
+def test_backward_needs_a_recording_forward():
+    """The 3D backward starts its list chunks from states that the one-frame forward records; on a
+    state whose lists came from the serving preparation it refuses with WIPES_ERR_INVALID, and a
+    forward on the same state makes it work again."""
+    torch = torch_cuda()
+    w = lib_ready()
+    import ctypes
+
+    from paper_2508_12615_gb300 import _abi
+
+    H, W = 60, 70
+    p = synth.scene3d(1200, 45)
+    cam = synth.sphere_cameras(1, H, W, 46)[0]
+    params = torch.from_numpy(p).cuda()
+    g = torch.from_numpy(synth.upstream_grad(H, W, 47)).cuda()
+    ctx = w.Context.get(0)
+    st = ctx.acquire_state()
+    c = _abi.camera_struct(cam.tolist())
+    opts = _opts(w, DEFAULT)
+    _abi.call("wipes_prepare3d", ctx.handle, st.handle, ctypes.c_void_p(params.data_ptr()), p.shape[0],
+              ctypes.byref(c), H, W, ctypes.byref(opts), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    with pytest.raises(_abi.WipesError) as e:
+        w.backward(st, params, g)
+    assert e.value.status == 1
+    w.forward3d(params, cam, H, W, opts, state=st)
+    grad = w.backward(st, params, g)
+    torch.cuda.synchronize()
+    fresh = ctx.acquire_state()
+    w.forward3d(params, cam, H, W, opts, state=fresh)
+    ref = w.backward(fresh, params, g)
+    torch.cuda.synchronize()
+    # the image-plane gradients are summed with atomics: equal up to the order of the additions
+    assert (grad - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
+
+
 def test_empty_and_all_culled():
     torch = torch_cuda()
     w = lib_ready()
