@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(256) k_mlp_head16(const float* __restrict__ w_
 // and the bias gradient (column sums of dz) of a 256-wide layer: a warp takes a row, each lane 8
 // columns with a 16-byte access and one mask byte; the block sums its column totals in shared
 // memory and adds them with one atomic per column
-constexpr int kReluBlocks = 304;
+constexpr int kReluBlocks = 152 * 4;
+constexpr int kReluRows = 4;  // rows a warp has in flight: its loads are issued before any is used
 __global__ void __launch_bounds__(256) k_relu_backward(const __nv_bfloat16* __restrict__ dh, int ld_dh,
                                                        const uint8_t* __restrict__ mask, int64_t N,
                                                        __nv_bfloat16* __restrict__ dz, float* __restrict__ db) {
@@ -190,22 +191,37 @@ __global__ void __launch_bounds__(256) k_relu_backward(const __nv_bfloat16* __re
     float acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-    for (int64_t r = (int64_t)blockIdx.x * 8 + g; r < N; r += (int64_t)gridDim.x * 8) {
-        const uint32_t mb = mask[r * (kWidth / 8) + lane];  // activations 8 lane .. 8 lane + 7 of row r
-        const uint4 vd = *reinterpret_cast<const uint4*>(dh + r * ld_dh + 8 * lane);
-        const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&vd);
-        uint4 vo;
-        __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&vo);
+    const int64_t stride = (int64_t)gridDim.x * 8;
+    for (int64_t r0 = (int64_t)blockIdx.x * 8 + g; r0 < N; r0 += kReluRows * stride) {
+        uint4 vd[kReluRows];
+        uint32_t mb[kReluRows];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float2 fd = __bfloat1622float2(pd[k]);
-            fd.x = (mb >> (2 * k)) & 1u ? fd.x : 0.f;
-            fd.y = (mb >> (2 * k + 1)) & 1u ? fd.y : 0.f;
-            po[k] = __floats2bfloat162_rn(fd.x, fd.y);  // exact: fd is a bfloat16 value or 0
-            acc[2 * k] += fd.x;
-            acc[2 * k + 1] += fd.y;
+        for (int j = 0; j < kReluRows; ++j) {
+            const int64_t r = r0 + j * stride;
+            vd[j] = make_uint4(0u, 0u, 0u, 0u);
+            mb[j] = 0u;
+            if (r < N) {
+                mb[j] = mask[r * (kWidth / 8) + lane];  // activations 8 lane .. 8 lane + 7 of row r
+                vd[j] = *reinterpret_cast<const uint4*>(dh + r * ld_dh + 8 * lane);
+            }
         }
-        *reinterpret_cast<uint4*>(dz + r * kWidth + 8 * lane) = vo;
+#pragma unroll
+        for (int j = 0; j < kReluRows; ++j) {
+            const int64_t r = r0 + j * stride;
+            const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&vd[j]);
+            uint4 vo;
+            __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&vo);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float2 fd = __bfloat1622float2(pd[k]);
+                fd.x = (mb[j] >> (2 * k)) & 1u ? fd.x : 0.f;
+                fd.y = (mb[j] >> (2 * k + 1)) & 1u ? fd.y : 0.f;
+                po[k] = __floats2bfloat162_rn(fd.x, fd.y);  // exact: fd is a bfloat16 value or 0
+                acc[2 * k] += fd.x;
+                acc[2 * k + 1] += fd.y;
+            }
+            if (r < N) *reinterpret_cast<uint4*>(dz + r * kWidth + 8 * lane) = vo;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) s_db[g][8 * lane + k] = acc[k];
