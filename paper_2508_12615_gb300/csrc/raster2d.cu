@@ -191,6 +191,8 @@ __device__ __forceinline__ void chain_rs(const float* p, float g11, float g21, f
 //   dl11/dl1 = -l11/l1, dl11/dl2 = l11 l2/u, dl11/dl3 = l11 (l3/u - 1/l3),
 //   dl21/dl2 = -sgn(l1) l3^2 / (|l3| s u), dl21/dl3 = -l21 (1/l3 + l3/u),
 //   dl22/dl2 = -l2 / (s u), dl22/dl3 = -l3 / (s u).
+// VEC: the output rows are 16-byte aligned and go out as four 16-byte stores.
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict__ params, int64_t N, int cov2d,
                                                         const uint32_t* __restrict__ offsets,
                                                         const uint32_t* __restrict__ counts,
@@ -227,14 +229,14 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     const float* t = s_tot[warp][lane];
     const uint32_t cnt = counts[prim];
     const float* p = params + prim * WIPES_P2D;
-    float* out = dl_dparams + prim * WIPES_P2D;
-    if (cnt == 0) {  // off-screen or degenerate: the record's parameters get no gradient
+    float* out_row = dl_dparams + prim * WIPES_P2D;
+    float out[WIPES_P2D];
 #pragma unroll
-        for (int k = 0; k < WIPES_P2D; ++k) out[k] = 0.f;
-        return;
-    }
+    for (int k = 0; k < WIPES_P2D; ++k) out[k] = 0.f;
     const float g11 = t[2], g21 = t[3], g22 = t[4];
-    if (cov2d) {
+    if (cnt == 0) {
+        // off-screen or degenerate: the record's parameters get no gradient
+    } else if (cov2d) {
         const float a = p[2], b = p[3], c = p[4];
         const float u = b * b + c * c, sq = sqrtf(u), aac = fabsf(a * c);
         const float l11 = sq / aac, l21 = -(a * b) / (aac * sq);
@@ -246,16 +248,24 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     } else {
         chain_rs(p, g11, g21, g22, out);
     }
-    out[0] = t[0];
-    out[1] = t[1];
-    out[5] = t[5];
-    out[6] = t[6];
-    out[7] = t[7] * kInvTwoPi;
-    out[8] = t[8];
-    out[9] = t[9];
-    out[10] = t[10];
+    if (cnt != 0) {
+        out[0] = t[0];
+        out[1] = t[1];
+        out[5] = t[5];
+        out[6] = t[6];
+        out[7] = t[7] * kInvTwoPi;
+        out[8] = t[8];
+        out[9] = t[9];
+        out[10] = t[10];
+    }
+    if (VEC) {
 #pragma unroll
-    for (int k = 11; k < WIPES_P2D; ++k) out[k] = 0.f;
+        for (int q = 0; q < WIPES_P2D / 4; ++q)
+            reinterpret_cast<float4*>(out_row)[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < WIPES_P2D; ++k) out_row[k] = out[k];
+    }
 }
 
 
@@ -318,7 +328,12 @@ void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, in
 void launch_reduce_chain2d(const float* params, int64_t N, int cov2d, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
-    launch_pdl(k_reduce_chain2d, ceil_div(N, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial, dl_dparams);
+    if ((reinterpret_cast<uintptr_t>(dl_dparams) & 15u) == 0)
+        launch_pdl(k_reduce_chain2d<true>, ceil_div(N, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial,
+                   dl_dparams);
+    else
+        launch_pdl(k_reduce_chain2d<false>, ceil_div(N, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial,
+                   dl_dparams);
     count_launches(1);
 }
 

@@ -298,6 +298,36 @@ __device__ __forceinline__ void quat_rot_grad(const float q[4], const float gR[9
 // Chain the image-plane gradient (mx, my, L, f', phc, c, o) to the record mu, s, q, f, phi, o, c.
 // With sh_degree > 0 the records and gradients hold WIPES_P3D_SH floats: dL/dsh_k = dL/dc Y_k(dir)
 // where the colour was not clamped, and mu gains dL/ddir (I - dir dir^T) / |mu - camera centre|.
+// n consecutive floats of a row in 16-byte pieces (VEC: the row is 16-byte aligned) or one by one
+template <bool VEC, int n>
+__device__ __forceinline__ void load_row(float* dst, const float* __restrict__ src) {
+    if (VEC) {
+#pragma unroll
+        for (int q = 0; q < n / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(src)[q];
+            dst[4 * q] = v.x, dst[4 * q + 1] = v.y, dst[4 * q + 2] = v.z, dst[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < n; ++k) dst[k] = src[k];
+    }
+}
+template <bool VEC, int n>
+__device__ __forceinline__ void store_row(float* dst, const float* v) {
+    if (VEC) {
+#pragma unroll
+        for (int q = 0; q < n / 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < n; ++k) dst[k] = v[k];
+    }
+}
+
+// One thread per primitive.  Its record, image-plane gradient and output row move in 16-byte
+// pieces when the caller's parameter and gradient rows are 16-byte aligned (VEC), so that each
+// load or store instruction covers whole sectors of the rows.
+template <bool VEC>
 __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ params, int64_t N, Cam3 cam, int W, int H,
                                                  float dil, int fmode, int sh_degree, const float4* __restrict__ rec,
                                                  const float* __restrict__ grad_img, float* __restrict__ dl_dparams) {
@@ -305,14 +335,18 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int stride = sh_degree ? WIPES_P3D_SH : WIPES_P3D;
-    float* out = dl_dparams + i * stride;
+    float* out_row = dl_dparams + i * stride;
     const float4 r0 = rec[(size_t)i * kRecF4 + 0];
     if (!(r0.z > 0.f)) {  // culled or degenerate: no gradient
-        for (int k = 0; k < stride; ++k) out[k] = 0.f;
+        for (int k = 0; k < stride; ++k) out_row[k] = 0.f;
         return;
     }
-    const float* p = params + i * stride;
-    const float* g = grad_img + (size_t)i * kG;
+    float p[WIPES_P3D];  // the record's geometry, frequency, phase, opacity and base colour
+    load_row<VEC, WIPES_P3D>(p, params + i * stride);
+    const float* p_sh = params + i * stride;  // the SH coefficients are read where they are used
+    float g[kG];
+    load_row<true, kG>(g, grad_img + (size_t)i * kG);
+    float out[WIPES_P3D];
     const float g_mx = g[0], g_my = g[1], g11 = g[2], g21 = g[3], g22 = g[4], g_fx = g[5], g_fy = g[6];
     const float* V = cam.V;
     const float tx = V[0] * p[0] + V[1] * p[1] + V[2] * p[2] + V[3];
@@ -449,30 +483,39 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
         sh_eval(dx, dy, dz, Y);
         sh_eval_grad(dx, dy, dz, Yx, Yy, Yz);
         const int nk = (sh_degree + 1) * (sh_degree + 1);
-        float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+        float gdx = 0.f, gdy = 0.f, gdz = 0.f, gc[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float raw = 0.5f;
 #pragma unroll
             for (int k = 0; k < kShMaxCoeffs; ++k)
-                if (k < nk) raw += Y[k] * p[sh_slot(k, ch)];
-            const float gc = raw > 0.f ? g[8 + ch] : 0.f;
+                if (k < nk) raw += Y[k] * p_sh[sh_slot(k, ch)];
+            gc[ch] = raw > 0.f ? g[8 + ch] : 0.f;
 #pragma unroll
             for (int k = 0; k < kShMaxCoeffs; ++k) {
                 if (k >= nk) continue;
-                const float c = p[sh_slot(k, ch)];
-                out[sh_slot(k, ch)] = gc * Y[k];
-                gdx += gc * c * Yx[k];
-                gdy += gc * c * Yy[k];
-                gdz += gc * c * Yz[k];
+                const float c = p_sh[sh_slot(k, ch)];
+                gdx += gc[ch] * c * Yx[k];
+                gdy += gc[ch] * c * Yy[k];
+                gdz += gc[ch] * c * Yz[k];
             }
+            out[15 + ch] = gc[ch] * Y[0];
         }
-        for (int k = 20 + 3 * (nk - 1); k < WIPES_P3D_SH; ++k) out[k] = 0.f;
         const float dd = gdx * dx + gdy * dy + gdz * dz;
         out[0] += (gdx - dd * dx) / dist;
         out[1] += (gdy - dd * dy) / dist;
         out[2] += (gdz - dd * dz) / dist;
+        // the coefficients of degree >= 1: slot 20 + 3 (k - 1) + ch, zero past the record's degree
+        constexpr int kShSlots = WIPES_P3D_SH - WIPES_P3D;
+        float osh[kShSlots];
+#pragma unroll
+        for (int sl = 0; sl < kShSlots; ++sl) {
+            const int k = sl / 3 + 1, ch = sl % 3;
+            osh[sl] = (k < kShMaxCoeffs && k < nk) ? gc[ch] * Y[k] : 0.f;
+        }
+        store_row<VEC, kShSlots>(out_row + WIPES_P3D, osh);
     }
+    store_row<VEC, WIPES_P3D>(out_row, out);
 }
 
 }  // namespace
@@ -504,8 +547,14 @@ void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int
     for (int k = 0; k < 12; ++k) c.V[k] = cam.viewmat[k];
     c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy; c.near_z = cam.near_z;
     camera_centre(cam, c.cpos);
-    launch_pdl(k_chain3d, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, fmode, sh_degree, rec,
-               grad_img, dl_dparams); count_launches(1);
+    const bool vec = ((reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(dl_dparams)) & 15u) == 0;
+    if (vec)
+        launch_pdl(k_chain3d<true>, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, fmode, sh_degree,
+                   rec, grad_img, dl_dparams);
+    else
+        launch_pdl(k_chain3d<false>, ceil_div(N, 128), 128, 0, stream, params, N, c, W, H, dilation, fmode, sh_degree,
+                   rec, grad_img, dl_dparams);
+    count_launches(1);
 }
 
 }  // namespace wipes
