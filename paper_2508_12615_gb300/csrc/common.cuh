@@ -208,6 +208,32 @@ __device__ __forceinline__ void sh_eval_grad(float x, float y, float z, float gx
 
 // SH coefficient k (0..15) of channel ch in an [N, WIPES_P3D_SH] record: the record colour for
 // k = 0, then three channels per basis function.
+// n consecutive floats of a row in 16-byte pieces (VEC: the row is 16-byte aligned) or one by one
+template <bool VEC, int n>
+__device__ __forceinline__ void load_row(float* dst, const float* __restrict__ src) {
+    if (VEC) {
+#pragma unroll
+        for (int q = 0; q < n / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(src)[q];
+            dst[4 * q] = v.x, dst[4 * q + 1] = v.y, dst[4 * q + 2] = v.z, dst[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < n; ++k) dst[k] = src[k];
+    }
+}
+template <bool VEC, int n>
+__device__ __forceinline__ void store_row(float* dst, const float* v) {
+    if (VEC) {
+#pragma unroll
+        for (int q = 0; q < n / 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < n; ++k) dst[k] = v[k];
+    }
+}
+
 __device__ __forceinline__ int sh_slot(int k, int ch) { return k == 0 ? 15 + ch : 20 + 3 * (k - 1) + ch; }
 
 // Cutoff test of a rectangle of pixel centres (columns x0..x1, rows y0..y1): does the cutoff

@@ -269,7 +269,11 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
         float Y[kShMaxCoeffs];
         sh_eval(vx / dist, vy / dist, vz / dist, Y);
         const int nk = (sh_degree + 1) * (sh_degree + 1);
-        const float* q = params + i * stride;
+        // the coefficients of degree >= 1 (slots 20 .. 67, the row 16-byte aligned) in 16-byte pieces
+        float q[WIPES_P3D_SH];
+#pragma unroll
+        for (int k = 15; k < 18; ++k) q[k] = p[k];
+        load_row<true, WIPES_P3D_SH - WIPES_P3D>(q + WIPES_P3D, params + i * stride + WIPES_P3D);
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float r = 0.5f;
@@ -288,13 +292,15 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     depth_keys[i] = __float_as_uint(tz);
 }
 
+// VEC (both kernels): the caller's rows are 16-byte aligned and move in 16-byte pieces.
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_deform6d(const float* __restrict__ p6, int64_t N, float t,
                                                   float* __restrict__ p3) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float* a = p6 + i * WIPES_P6D;
-    float* o = p3 + i * WIPES_P3D;
+    float a[WIPES_P6D], o[WIPES_P3D];
+    load_row<VEC, WIPES_P6D>(a, p6 + i * WIPES_P6D);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         // single rounding of mu0 + v t (and of f, phi below): the correctly rounded linear model
@@ -307,17 +313,19 @@ __global__ void __launch_bounds__(256) k_deform6d(const float* __restrict__ p6, 
     o[13] = __fmaf_rn(a[26], t, a[13]);
 #pragma unroll
     for (int j = 14; j < 20; ++j) o[j] = a[j];
+    store_row<VEC, WIPES_P3D>(p3 + i * WIPES_P3D, o);
 }
 
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_deform6d_backward(const float* __restrict__ p6, int64_t N, float t,
                                                            const float* __restrict__ g3, float* __restrict__ g6,
                                                            int accumulate) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float* a = p6 + i * WIPES_P6D;
-    const float* g = g3 + i * WIPES_P3D;
-    float o[WIPES_P6D];
+    float a[WIPES_P6D], g[WIPES_P3D], o[WIPES_P6D];
+    load_row<VEC, WIPES_P6D>(a, p6 + i * WIPES_P6D);
+    load_row<VEC, WIPES_P3D>(g, g3 + i * WIPES_P3D);
 #pragma unroll
     for (int j = 0; j < WIPES_P6D; ++j) o[j] = 0.0f;
 #pragma unroll
@@ -332,8 +340,13 @@ __global__ void __launch_bounds__(256) k_deform6d_backward(const float* __restri
     }
     o[26] = g[13] * t;
     float* out = g6 + i * WIPES_P6D;
+    if (accumulate) {
+        float prev[WIPES_P6D];
+        load_row<VEC, WIPES_P6D>(prev, out);
 #pragma unroll
-    for (int j = 0; j < WIPES_P6D; ++j) out[j] = accumulate ? out[j] + o[j] : o[j];
+        for (int j = 0; j < WIPES_P6D; ++j) o[j] = prev[j] + o[j];
+    }
+    store_row<VEC, WIPES_P6D>(out, o);
 }
 
 }  // namespace
@@ -361,13 +374,23 @@ void launch_footprint3d(const float* params, int64_t N, const wipes_camera& cam,
 
 void launch_deform6d(const float* params6, int64_t N, float t, float* params3, cudaStream_t stream) {
     if (N == 0) return;
-    launch_pdl(k_deform6d, ceil_div(N, 256), 256, 0, stream, params6, N, t, params3); count_launches(1);
+    if (((reinterpret_cast<uintptr_t>(params6) | reinterpret_cast<uintptr_t>(params3)) & 15u) == 0)
+        launch_pdl(k_deform6d<true>, ceil_div(N, 256), 256, 0, stream, params6, N, t, params3);
+    else
+        launch_pdl(k_deform6d<false>, ceil_div(N, 256), 256, 0, stream, params6, N, t, params3);
+    count_launches(1);
 }
 
 void launch_deform6d_backward(const float* params6, int64_t N, float t, const float* g3, float* g6, int accumulate,
                               cudaStream_t stream) {
     if (N == 0) return;
-    launch_pdl(k_deform6d_backward, ceil_div(N, 256), 256, 0, stream, params6, N, t, g3, g6, accumulate); count_launches(1);
+    const uintptr_t ptrs = reinterpret_cast<uintptr_t>(params6) | reinterpret_cast<uintptr_t>(g3) |
+                           reinterpret_cast<uintptr_t>(g6);
+    if ((ptrs & 15u) == 0)
+        launch_pdl(k_deform6d_backward<true>, ceil_div(N, 256), 256, 0, stream, params6, N, t, g3, g6, accumulate);
+    else
+        launch_pdl(k_deform6d_backward<false>, ceil_div(N, 256), 256, 0, stream, params6, N, t, g3, g6, accumulate);
+    count_launches(1);
 }
 
 }  // namespace wipes

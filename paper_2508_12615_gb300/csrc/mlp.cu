@@ -86,21 +86,21 @@ __global__ void __launch_bounds__(256) k_to_bf16(const float* __restrict__ src, 
 }
 
 // deformed record from the canonical record and the network outputs d [N, 16] (13 used): the
-// output layer's bias b is added here, and d keeps the biased outputs for the backward
+// output layer's bias b is added here, and d keeps the biased outputs for the backward.  VEC: the
+// caller's record rows are 16-byte aligned and move in 16-byte pieces (d always does).
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_mlp_apply(const float* __restrict__ params3, int64_t N,
                                                    float* __restrict__ d, const float* __restrict__ b,
                                                    float* __restrict__ out) {
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float* p = params3 + i * WIPES_P3D;
-    float e[kOut];
+    float p[WIPES_P3D], e[kOutPad], o[WIPES_P3D];
+    load_row<VEC, WIPES_P3D>(p, params3 + i * WIPES_P3D);
+    load_row<true, kOutPad>(e, d + i * kOutPad);
 #pragma unroll
-    for (int k = 0; k < kOut; ++k) {
-        e[k] = d[i * kOutPad + k] + b[k];
-        d[i * kOutPad + k] = e[k];
-    }
-    float* o = out + i * WIPES_P3D;
+    for (int k = 0; k < kOut; ++k) e[k] += b[k];
+    store_row<true, kOutPad>(d + i * kOutPad, e);
 #pragma unroll
     for (int k = 0; k < WIPES_P3D; ++k) o[k] = p[k];
 #pragma unroll
@@ -111,10 +111,12 @@ __global__ void __launch_bounds__(256) k_mlp_apply(const float* __restrict__ par
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) o[6 + k] = p[6 + k] + e[3 + k];
+    store_row<VEC, WIPES_P3D>(out + i * WIPES_P3D, o);
 }
 
 // dL/dd (bfloat16, the backward's product operand) and the direct part of dL/dparams3; the output
-// bias gradient is the column sum of the rounded dL/dd
+// bias gradient is the column sum of the rounded dL/dd (summed over the warp, then the block)
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_mlp_apply_backward(const float* __restrict__ params3, int64_t N,
                                                             const float* __restrict__ d,
                                                             const float* __restrict__ g_out,
@@ -126,10 +128,14 @@ __global__ void __launch_bounds__(256) k_mlp_apply_backward(const float* __restr
     if (threadIdx.x < kOutPad) s_db[threadIdx.x] = 0.f;
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float gdr[kOutPad];  // the rounded dL/dd of this row (0 past N)
+#pragma unroll
+    for (int k = 0; k < kOutPad; ++k) gdr[k] = 0.f;
     if (i < N) {
-        const float* p = params3 + i * WIPES_P3D;
-        const float* e = d + i * kOutPad;
-        const float* g = g_out + i * WIPES_P3D;
+        float p[WIPES_P3D], e[kOutPad], g[WIPES_P3D];
+        load_row<VEC, WIPES_P3D>(p, params3 + i * WIPES_P3D);
+        load_row<true, kOutPad>(e, d + i * kOutPad);
+        load_row<VEC, WIPES_P3D>(g, g_out + i * WIPES_P3D);
         float gdv[kOutPad];
 #pragma unroll
         for (int k = 0; k < kOutPad; ++k) gdv[k] = 0.f;
@@ -146,16 +152,33 @@ __global__ void __launch_bounds__(256) k_mlp_apply_backward(const float* __restr
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) gdv[3 + k] = g[6 + k];
-        __nv_bfloat16* gdr = gd + i * kOutPad;
+        uint32_t packed[kOutPad / 2];
 #pragma unroll
-        for (int k = 0; k < kOutPad; ++k) {
-            const __nv_bfloat16 b = __float2bfloat16_rn(gdv[k]);
-            gdr[k] = b;
-            if (k < kOut) atomicAdd(&s_db[k], __bfloat162float(b));
+        for (int k = 0; k < kOutPad; k += 2) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(gdv[k], gdv[k + 1]);
+            packed[k / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+            const float2 f2v = __bfloat1622float2(b2);
+            gdr[k] = f2v.x;
+            gdr[k + 1] = f2v.y;
         }
+        uint4* gd4 = reinterpret_cast<uint4*>(gd + i * kOutPad);
+        gd4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        gd4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         float* go = g_params3 + i * WIPES_P3D;
+        if (accumulate) {
+            float prev[WIPES_P3D];
+            load_row<VEC, WIPES_P3D>(prev, go);
 #pragma unroll
-        for (int k = 0; k < WIPES_P3D; ++k) go[k] = accumulate ? go[k] + gp[k] : gp[k];
+            for (int k = 0; k < WIPES_P3D; ++k) gp[k] = prev[k] + gp[k];
+        }
+        store_row<VEC, WIPES_P3D>(go, gp);
+    }
+#pragma unroll
+    for (int k = 0; k < kOut; ++k) {
+        float v = gdr[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_db[k], v);
     }
     __syncthreads();
     if (threadIdx.x < kOut) atomicAdd(&db_head[threadIdx.x], s_db[threadIdx.x]);
@@ -488,8 +511,11 @@ std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, con
             layer_forward(lt, l, wl, w16 + boff, x, ldx, y, ldy, N, l == kHidden ? nullptr : act_mask(act, N, l), s);
         if (!e.empty()) return e;
     }
-    launch_pdl(k_mlp_apply, ceil_div(N, 256), 256, 0, s, params3, N, d,
-               theta + layer_offset(kHidden) + (int64_t)kOut * kWidth, params_out);
+    const float* b_head = theta + layer_offset(kHidden) + (int64_t)kOut * kWidth;
+    if (((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(params_out)) & 15u) == 0)
+        launch_pdl(k_mlp_apply<true>, ceil_div(N, 256), 256, 0, s, params3, N, d, b_head, params_out);
+    else
+        launch_pdl(k_mlp_apply<false>, ceil_div(N, 256), 256, 0, s, params3, N, d, b_head, params_out);
     count_launches(1);
     return "";
 }
@@ -511,8 +537,14 @@ std::string mlp_backward(MlpLt& lt, const float* params3, int64_t N, const void*
     float* dw_head16 = reinterpret_cast<float*>(gd + (size_t)N * kOutPad);  // [16, 256]
     if (!accumulate) cudaMemsetAsync(g_theta, 0, sizeof(float) * (size_t)mlp_param_count(), s);
     float* db_head = g_theta + layer_offset(kHidden) + (int64_t)kOut * kWidth;
-    launch_pdl(k_mlp_apply_backward, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3, accumulate,
-               db_head);
+    const uintptr_t rows = reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(g_out) |
+                           reinterpret_cast<uintptr_t>(g_params3);
+    if ((rows & 15u) == 0)
+        launch_pdl(k_mlp_apply_backward<true>, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3,
+                   accumulate, db_head);
+    else
+        launch_pdl(k_mlp_apply_backward<false>, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3,
+                   accumulate, db_head);
     count_launches(1);
     std::string e;
     // output layer (padded to 16 rows): dW_8 = gd^T h7 into [16, 256]; dh7 = gd W_8

@@ -298,32 +298,6 @@ __device__ __forceinline__ void quat_rot_grad(const float q[4], const float gR[9
 // Chain the image-plane gradient (mx, my, L, f', phc, c, o) to the record mu, s, q, f, phi, o, c.
 // With sh_degree > 0 the records and gradients hold WIPES_P3D_SH floats: dL/dsh_k = dL/dc Y_k(dir)
 // where the colour was not clamped, and mu gains dL/ddir (I - dir dir^T) / |mu - camera centre|.
-// n consecutive floats of a row in 16-byte pieces (VEC: the row is 16-byte aligned) or one by one
-template <bool VEC, int n>
-__device__ __forceinline__ void load_row(float* dst, const float* __restrict__ src) {
-    if (VEC) {
-#pragma unroll
-        for (int q = 0; q < n / 4; ++q) {
-            const float4 v = reinterpret_cast<const float4*>(src)[q];
-            dst[4 * q] = v.x, dst[4 * q + 1] = v.y, dst[4 * q + 2] = v.z, dst[4 * q + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < n; ++k) dst[k] = src[k];
-    }
-}
-template <bool VEC, int n>
-__device__ __forceinline__ void store_row(float* dst, const float* v) {
-    if (VEC) {
-#pragma unroll
-        for (int q = 0; q < n / 4; ++q)
-            reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < n; ++k) dst[k] = v[k];
-    }
-}
-
 // One thread per primitive.  Its record, image-plane gradient and output row move in 16-byte
 // pieces when the caller's parameter and gradient rows are 16-byte aligned (VEC), so that each
 // load or store instruction covers whole sectors of the rows.
