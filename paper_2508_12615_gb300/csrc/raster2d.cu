@@ -18,17 +18,37 @@ __global__ void __launch_bounds__(kTilePixels) k_blend2d(BlendJob job) { pdl_ent
 // Partial gradient slot layout (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b 0
 constexpr int kSlot = 12;
 
+// Reduce-scatter within each half-warp: 16 values over its 16 lanes; lane h of a half ends with the
+// half's total of value h.
+__device__ __forceinline__ float half_reduce_scatter16(float v[16]) {
+    const int hl = threadIdx.x & 15;
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+        const bool hi = hl & off;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const float send = hi ? v[i] : v[off + i];
+            const float keep = hi ? v[off + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0];
+}
+
 // Backward.  The tile's dL/dimage sits in shared memory, stored by pixel pairs in the layout of
-// the forward pass (quadrant k, lane l: pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the
-// 8x8 quadrant).  Batches of the tile list are staged with the mask of the quadrants that each
-// pair's cutoff ellipse reaches.  One warp takes one (tile, primitive) pair at a time and walks the
-// marked quadrants, two pixels per lane in packed f32x2 arithmetic.  Per pixel inside the cutoff a
-// lane accumulates the factored sums
+// the forward pass (quadrant k, pair l: pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the 8x8
+// quadrant).  Batches of the tile list are staged with the mask of the quadrants that each pair's
+// cutoff ellipse reaches, and ordered by the number of those quadrants.  Each half-warp takes one
+// (tile, primitive) pair, so a warp works on two pairs that reach equally many quadrants; a lane
+// covers four pixels of a quadrant, column h & 7 and rows r, r + 4 (pixel pair r) and r + 2, r + 6
+// (pixel pair r + 2), r = h >> 3, in packed f32x2 arithmetic.  Per pixel inside the cutoff a lane
+// accumulates the factored sums
 //   sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy, sum g W
 // (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
-// b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one warp
-// reduction, since L, f and the centre are constant over the pair.  The sums are taken of
-// -ga, -gb and -gt / pi (one multiplication less per pixel) and scaled once per pair.
+// b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one half-warp
+// reduction, since L, f and the centre are constant over the pair, and one reduction pass serves
+// both halves.  The sums are taken of -ga, -gb and -gt / pi (one multiplication less per pixel) and
+// scaled once per pair.
 __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
                                                             int H, int tiles_x, float cutoff2, float lim,
@@ -40,10 +60,13 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
     __shared__ ulonglong2 s_e[6][kTilePixels];
     __shared__ uint32_t s_slot[kTilePixels];
     __shared__ uint8_t s_mask[kTilePixels];
+    __shared__ uint16_t s_order[kTilePixels];  // staged entries, most quadrants first
+    __shared__ uint32_t s_nq[5];               // staged entries that reach 0 .. 4 quadrants
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hl = lane & 15, half = lane >> 4;
     if (threadIdx.x < kTilePixels / 2) {
         const int k = threadIdx.x >> 5;
         const int u = x0 + (k & 1) * 8 + (lane & 7);
@@ -60,13 +83,18 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
         s_g[0][threadIdx.x] = make_ulonglong2(f2_pack(g0[0], g1[0]).r, f2_pack(g0[1], g1[1]).r);
         s_g[1][threadIdx.x] = make_ulonglong2(f2_pack(g0[2], g1[2]).r, 0ull);
     }
-    // the lane's pixels in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1) rows)
-    const float lane_px = (float)(x0 + (lane & 7)) + 0.5f, lane_py = (float)(y0 + (lane >> 3)) + 0.5f;
+    if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;
+    // the lane's pixels in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1) rows), and
+    // its two pixel pairs' places in the pair layout
+    const float lane_px = (float)(x0 + (hl & 7)) + 0.5f, lane_py = (float)(y0 + (hl >> 3)) + 0.5f;
+    const int gp0 = (hl & 7) + 8 * (hl >> 3), gp1 = gp0 + 16;
     const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
     const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         __syncthreads();
+        int my_q = 0;
+        uint32_t my_rank = 0u;
         if ((int)threadIdx.x < n) {
             const uint32_t e = tl.sorted[b0 + threadIdx.x];
             const uint32_t prim = tl.prim[b0 + threadIdx.x];
@@ -79,58 +107,79 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             s_e[3][threadIdx.x] = dup2(B.z, B.w);
             s_e[4][threadIdx.x] = dup2(C.x, C.y);
             s_e[5][threadIdx.x] = dup2(C.z, 0.f);
-            s_mask[threadIdx.x] = (uint8_t)quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+            const uint32_t m = quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+            s_mask[threadIdx.x] = (uint8_t)m;
             s_slot[threadIdx.x] = e;
+            my_q = __popc(m);
+            my_rank = atomicAdd(&s_nq[my_q], 1u);
         }
         __syncthreads();
-        for (int j = warp; j < n; j += kTilePixels / 32) {
-            uint32_t mask = s_mask[j];
+        if ((int)threadIdx.x < n) {
+            uint32_t pos = my_rank;
+            for (int q = 4; q > my_q; --q) pos += s_nq[q];
+            s_order[pos] = (uint16_t)threadIdx.x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;  // read by no one until the next batch's counts
+        const int npairs = (n + 1) >> 1;
+        for (int pi = warp; pi < npairs; pi += kTilePixels / 32) {
+            const int idx = 2 * pi + half;
+            const bool has = idx < n;
+            const int j = has ? (int)s_order[idx] : 0;
+            uint32_t mask = has ? (uint32_t)s_mask[j] : 0u;
             f2 acc[11];
 #pragma unroll
             for (int i = 0; i < 11; ++i) acc[i] = f2_dup(0.f);
-            while (mask) {
-                const int k = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
-                const float px = lane_px + (float)((k & 1) * 8), py = lane_py + (float)((k >> 1) * 8);
-                // the cutoff test in the operation order of mahalanobis2()
-                // the pair's record, read again for each quadrant rather than held in registers
-                const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
-                const f2x2 e2 = ld_f2x2_here(&s_e[2][j]), e3 = ld_f2x2_here(&s_e[3][j]);
-                const f2 dx = f2_sub(f2_dup(px), e0.x), dy = f2_sub(f2_pack(py, py + 4.0f), e0.y);
-                const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
-                const f2 b = f2_mul(e2.x, dy);
-                const f2 q = f2_fma(a, a, f2_mul(b, b));
-                // outside the cutoff the envelope is taken as ex2(-inf) = 0: every term below is 0
-                const f2 e = f2_mul(q, K);
-                const float glo = ex2_approx(f2_lo(q) <= cutoff2 ? f2_lo(e) : -INFINITY);
-                const float ghi = ex2_approx(f2_hi(q) <= cutoff2 ? f2_hi(e) : -INFINITY);
-                const f2 G = f2_pack(glo, ghi);
-                const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
-                const float alo = f2_lo(ang), ahi = f2_hi(ang);
-                const f2 cs = f2_pack(cos_approx(alo), cos_approx(ahi));
-                const f2 sn = f2_pack(sin_approx(alo), sin_approx(ahi));
-                const f2 Wv = f2_mul(f2_fma(HALF, cs, HALF), G);
-                const f2x2 g01 = ld_f2x2(&s_g[0][k * 32 + lane]);
-                const f2 gb_ = ld_f2x2(&s_g[1][k * 32 + lane]).x;
-                const f2x2 e4 = ld_f2x2_here(&s_e[4][j]), e5 = ld_f2x2_here(&s_e[5][j]);
-                const f2 gW = f2_fma(g01.x, e4.x, f2_fma(g01.y, e4.y, f2_mul(gb_, e5.x)));
-                const f2 hq = f2_mul(gW, Wv);              // -2 dL/dq  (dW/dq = -W/2)
-                const f2 ht = f2_mul(G, f2_mul(gW, sn));  // -dL/dt / pi, t in cycles
-                const f2 ha = f2_mul(hq, a), hb = f2_mul(hq, b);
-                acc[0] = f2_add(acc[0], ha);
-                acc[1] = f2_add(acc[1], hb);
-                acc[2] = f2_add(acc[2], ht);
-                acc[3] = f2_fma(ha, dx, acc[3]);
-                acc[4] = f2_fma(ha, dy, acc[4]);
-                acc[5] = f2_fma(hb, dy, acc[5]);
-                acc[6] = f2_fma(ht, dx, acc[6]);
-                acc[7] = f2_fma(ht, dy, acc[7]);
-                acc[8] = f2_fma(g01.x, Wv, acc[8]);
-                acc[9] = f2_fma(g01.y, Wv, acc[9]);
-                acc[10] = f2_fma(gb_, Wv, acc[10]);
+            while (__any_sync(0xffffffffu, mask != 0u)) {
+                if (mask) {
+                    const int k = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
+                    const float px = lane_px + (float)((k & 1) * 8), pyq = lane_py + (float)((k >> 1) * 8);
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp) {
+                        const float py = pyq + (float)(2 * pp);
+                        // the pair's record, read again for each pixel pair rather than held in registers
+                        const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
+                        const f2x2 e2 = ld_f2x2_here(&s_e[2][j]), e3 = ld_f2x2_here(&s_e[3][j]);
+                        // the cutoff test in the operation order of mahalanobis2()
+                        const f2 dx = f2_sub(f2_dup(px), e0.x), dy = f2_sub(f2_pack(py, py + 4.0f), e0.y);
+                        const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+                        const f2 b = f2_mul(e2.x, dy);
+                        const f2 q = f2_fma(a, a, f2_mul(b, b));
+                        // outside the cutoff the envelope is taken as ex2(-inf) = 0: every term below is 0
+                        const f2 e = f2_mul(q, K);
+                        const float glo = ex2_approx(f2_lo(q) <= cutoff2 ? f2_lo(e) : -INFINITY);
+                        const float ghi = ex2_approx(f2_hi(q) <= cutoff2 ? f2_hi(e) : -INFINITY);
+                        const f2 G = f2_pack(glo, ghi);
+                        const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+                        const float alo = f2_lo(ang), ahi = f2_hi(ang);
+                        const f2 cs = f2_pack(cos_approx(alo), cos_approx(ahi));
+                        const f2 sn = f2_pack(sin_approx(alo), sin_approx(ahi));
+                        const f2 Wv = f2_mul(f2_fma(HALF, cs, HALF), G);
+                        const int gi = k * 32 + (pp ? gp1 : gp0);
+                        const f2x2 g01 = ld_f2x2(&s_g[0][gi]);
+                        const f2 gb_ = ld_f2x2(&s_g[1][gi]).x;
+                        const f2x2 e4 = ld_f2x2_here(&s_e[4][j]), e5 = ld_f2x2_here(&s_e[5][j]);
+                        const f2 gW = f2_fma(g01.x, e4.x, f2_fma(g01.y, e4.y, f2_mul(gb_, e5.x)));
+                        const f2 hq = f2_mul(gW, Wv);              // -2 dL/dq  (dW/dq = -W/2)
+                        const f2 ht = f2_mul(G, f2_mul(gW, sn));  // -dL/dt / pi, t in cycles
+                        const f2 ha = f2_mul(hq, a), hb = f2_mul(hq, b);
+                        acc[0] = f2_add(acc[0], ha);
+                        acc[1] = f2_add(acc[1], hb);
+                        acc[2] = f2_add(acc[2], ht);
+                        acc[3] = f2_fma(ha, dx, acc[3]);
+                        acc[4] = f2_fma(ha, dy, acc[4]);
+                        acc[5] = f2_fma(hb, dy, acc[5]);
+                        acc[6] = f2_fma(ht, dx, acc[6]);
+                        acc[7] = f2_fma(ht, dy, acc[7]);
+                        acc[8] = f2_fma(g01.x, Wv, acc[8]);
+                        acc[9] = f2_fma(g01.y, Wv, acc[9]);
+                        acc[10] = f2_fma(gb_, Wv, acc[10]);
+                    }
+                }
             }
-            // the lane's two pixels, then the sums of ga, gb, gt from the scaled ones
+            // the lane's pixels, then the sums of ga, gb, gt from the scaled ones
             float sums[16];
 #pragma unroll
             for (int i = 0; i < 11; ++i) sums[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
@@ -138,22 +187,25 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             for (int i = 11; i < 16; ++i) sums[i] = 0.f;
             sums[0] = -sums[0], sums[1] = -sums[1], sums[3] = -sums[3], sums[4] = -sums[4], sums[5] = -sums[5];
             sums[2] *= -kPi, sums[6] *= -kPi, sums[7] *= -kPi;
-            // lane l holds the total of sum (l >> 1); lane l < 12 writes slot l of the pair
-            const float tot = warp_reduce_scatter16(sums);
-            const float sga = __shfl_sync(0xffffffffu, tot, 0);
-            const float sgb = __shfl_sync(0xffffffffu, tot, 2);
-            const float sgt = __shfl_sync(0xffffffffu, tot, 4);
+            // lane h of the half holds the half's total of sum h; lane h < 12 writes slot h of the pair
+            const float tot = half_reduce_scatter16(sums);
+            const int base = half * 16;
+            const float sga = __shfl_sync(0xffffffffu, tot, base + 0);
+            const float sgb = __shfl_sync(0xffffffffu, tot, base + 1);
+            const float sgt = __shfl_sync(0xffffffffu, tot, base + 2);
             // sum feeding each slot: l11 <- ga dx (3), l21 <- ga dy (4), l22 <- gb dy (5), fx <- gt dx (6),
             // fy <- gt dy (7), phc <- gt (2), colour 8..10
-            const int src = lane == 7 ? 2 : (lane >= 2 && lane <= 6 ? lane + 1 : min(lane, 15));
-            float val = __shfl_sync(0xffffffffu, tot, 2 * src);
-            const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
-            const float l11 = f2_lo(e1.x), l21 = f2_lo(e1.y), l22 = f2_lo(e2.x), fx = f2_lo(e2.y);
-            const float fy = f2_lo(ld_f2x2(&s_e[3][j]).x);
-            if (lane == 0) val = -fmaf(l11, sga, fx * sgt);
-            if (lane == 1) val = -fmaf(l21, sga, fmaf(l22, sgb, fy * sgt));
-            if (lane == 11) val = 0.f;
-            if (lane < kSlot) partial[(size_t)s_slot[j] * kSlot + lane] = val;
+            const int src = hl == 7 ? 2 : (hl >= 2 && hl <= 6 ? hl + 1 : hl);
+            float val = __shfl_sync(0xffffffffu, tot, base + src);
+            if (has && hl < kSlot) {
+                const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
+                const float l11 = f2_lo(e1.x), l21 = f2_lo(e1.y), l22 = f2_lo(e2.x), fx = f2_lo(e2.y);
+                const float fy = f2_lo(ld_f2x2(&s_e[3][j]).x);
+                if (hl == 0) val = -fmaf(l11, sga, fx * sgt);
+                if (hl == 1) val = -fmaf(l21, sga, fmaf(l22, sgb, fy * sgt));
+                if (hl == 11) val = 0.f;
+                partial[(size_t)s_slot[j] * kSlot + hl] = val;
+            }
         }
     }
 }
