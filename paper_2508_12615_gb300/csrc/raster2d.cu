@@ -251,29 +251,30 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
                                                         const float* __restrict__ partial,
                                                         float* __restrict__ dl_dparams) {
     pdl_enter();
-    // a warp takes 32 consecutive primitives: it sums the slots of each in turn (lanes over the
-    // slots, coalesced), keeping the 11 totals of primitive k in s_tot[warp][k]; then lane k chains
-    // primitive k, all 32 at once
+    // a warp takes 32 consecutive primitives: its half-warps sum the slots of two of them at a time
+    // (lanes over the slots, coalesced), keeping the 11 totals of primitive k in s_tot[warp][k];
+    // then lane k chains primitive k, all 32 at once
     __shared__ float s_tot[8][32][12];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hl = lane & 15, half = lane >> 4;
     const int64_t prim0 = (((int64_t)blockIdx.x * blockDim.x) >> 5 << 5) + (int64_t)warp * 32;
-    for (int k = 0; k < 32; ++k) {
-        const int64_t pk = prim0 + k;
-        if (pk >= N) break;  // uniform across the warp
-        const uint32_t off = offsets[pk], cnt = counts[pk];
+    for (int k2 = 0; k2 < 32; k2 += 2) {
+        if (prim0 + k2 >= N) break;  // uniform across the warp
+        const int64_t pk = prim0 + k2 + half;
+        const uint32_t off = pk < N ? offsets[pk] : 0u, cnt = pk < N ? counts[pk] : 0u;
         float acc[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) acc[m] = 0.f;
-        for (uint32_t j = lane; j < cnt; j += 32) {
+        for (uint32_t j = hl; j < cnt; j += 16) {
             const float4* src = reinterpret_cast<const float4*>(partial + (size_t)(off + j) * kSlot);
             const float4 x0 = src[0], x1 = src[1], x2 = src[2];
             acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
             acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
             acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z;
         }
-        // lane 2m holds the total of slot m
-        const float tot = warp_reduce_scatter16(acc);
-        if ((lane & 1) == 0 && (lane >> 1) < 11) s_tot[warp][k][lane >> 1] = tot;
+        // lane h of each half holds the half's total of slot h
+        const float tot = half_reduce_scatter16(acc);
+        if (hl < 11 && pk < N) s_tot[warp][k2 + half][hl] = tot;
     }
     __syncwarp();
     const int64_t prim = prim0 + lane;
