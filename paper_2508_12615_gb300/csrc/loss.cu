@@ -10,7 +10,25 @@ __global__ void __launch_bounds__(256) k_l2_loss(const float* __restrict__ img, 
     __shared__ float s_warp[8];
     const float scale = 2.0f / (float)n;
     float acc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t done = 0;  // elements handled four at a time
+    const uintptr_t ptrs = reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(target) |
+                           reinterpret_cast<uintptr_t>(grad);
+    if ((ptrs & 15u) == 0) {
+        const int64_t n4 = n >> 2;
+        for (int64_t i = first; i < n4; i += stride) {
+            const float4 a = reinterpret_cast<const float4*>(img)[i];
+            const float4 t = reinterpret_cast<const float4*>(target)[i];
+            const float4 d = make_float4(a.x - t.x, a.y - t.y, a.z - t.z, a.w - t.w);
+            reinterpret_cast<float4*>(grad)[i] = make_float4(scale * d.x, scale * d.y, scale * d.z, scale * d.w);
+            acc = fmaf(d.x, d.x, acc);
+            acc = fmaf(d.y, d.y, acc);
+            acc = fmaf(d.z, d.z, acc);
+            acc = fmaf(d.w, d.w, acc);
+        }
+        done = n4 << 2;
+    }
+    for (int64_t i = done + first; i < n; i += stride) {
         const float d = img[i] - target[i];
         grad[i] = scale * d;
         acc = fmaf(d, d, acc);

@@ -264,19 +264,33 @@ __global__ void __launch_bounds__(256) k_mlp_encode_backward(const float* __rest
     pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const __nv_bfloat16* a = dg0 + i * kInPad;
-    const __nv_bfloat16* b = dgs + i * kInPad;
+    // columns 0 .. 63 of both rows (the centre's encoding is columns 0 .. 62), in 16-byte pieces
+    constexpr int kCols = 64;
+    static_assert(3 + 6 * kLx <= kCols && kInPad % 8 == 0, "the centre's encoding fits the loaded columns");
+    float ab[kCols];  // the encoding's gradient: layer 0's part plus the skip input's
+#pragma unroll
+    for (int q = 0; q < kCols / 8; ++q) {
+        const uint4 va = reinterpret_cast<const uint4*>(dg0 + i * kInPad)[q];
+        const uint4 vb = reinterpret_cast<const uint4*>(dgs + i * kInPad)[q];
+        const uint32_t wa[4] = {va.x, va.y, va.z, va.w}, wb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wa[h]));
+            const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wb[h]));
+            ab[8 * q + 2 * h] = fa.x + fb.x, ab[8 * q + 2 * h + 1] = fa.y + fb.y;
+        }
+    }
     float gm[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) gm[j] = __bfloat162float(a[j]) + __bfloat162float(b[j]);
+    for (int j = 0; j < 3; ++j) gm[j] = ab[j];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float x = params3[i * WIPES_P3D + j];
 #pragma unroll
         for (int k = 0; k < kLx; ++k) {
             const float f = (float)(1 << k);
-            const float gs = __bfloat162float(a[3 + 6 * k + j]) + __bfloat162float(b[3 + 6 * k + j]);
-            const float gc = __bfloat162float(a[6 + 6 * k + j]) + __bfloat162float(b[6 + 6 * k + j]);
+            const float gs = ab[3 + 6 * k + j];
+            const float gc = ab[6 + 6 * k + j];
             float sn, cs;
             sincosf(f * x, &sn, &cs);
             gm[j] += f * (gs * cs - gc * sn);
