@@ -298,8 +298,12 @@ class Workload:
         self.target_d = torch.from_numpy(target).to(dev)
         self.img = torch.empty(self.H, self.W, 3, device=dev)
         self.gimg = torch.empty_like(self.img)
-        self.loss = torch.empty((), device=dev)
-        self.grad = torch.empty_like(self.params)
+        # the parameter gradient and the loss share one buffer, so that a step's results come back
+        # to the host in one copy
+        n_out = self.params.numel()
+        self.out = torch.empty(n_out + 4, device=dev)
+        self.grad = self.out[:n_out].view_as(self.params)
+        self.loss = self.out[n_out]
         if kind in ("6d", "6dmlp"):
             self.p3 = torch.empty(p.shape[0], 20, device=dev)
             self.g3 = torch.empty_like(self.p3)
@@ -450,22 +454,24 @@ def our_arm(args, rank: int, world: int, local_rank: int):
 
     # end to end through the public API with host buffers: parameters and target in from pinned
     # host memory, gradient and loss back to pinned host memory, every step
-    p_host = torch.from_numpy(wl.p).pin_memory()
-    t_host = torch.from_numpy(wl.target).pin_memory()
-    g_host = torch.empty_like(p_host).pin_memory()
-    l_host = torch.empty((), dtype=torch.float32).pin_memory()
-    e2e_params = torch.empty_like(wl.params)
-    e2e_target = torch.empty_like(wl.target_d)
+    # a step's inputs (parameters, then target) travel in one pinned buffer and one copy, its
+    # results (gradient, then loss) in another
+    n_p = wl.params.numel()
+    in_host = torch.empty(n_p + wl.target_d.numel(), dtype=torch.float32).pin_memory()
+    in_host[:n_p].copy_(torch.from_numpy(wl.p).reshape(-1))
+    in_host[n_p:].copy_(torch.from_numpy(wl.target).reshape(-1))
+    out_host = torch.empty(wl.out.numel(), dtype=torch.float32).pin_memory()
+    e2e_in = torch.empty(in_host.numel(), device=dev)
+    e2e_params = e2e_in[:n_p].view_as(wl.params)     # offset 0: 16-byte aligned
+    e2e_target = e2e_in[n_p:].view_as(wl.target_d)   # offset n_p * 4 bytes, a multiple of 64
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.zero_()
         e_ev[k][0].record()
-        e2e_params.copy_(p_host, non_blocking=True)
-        e2e_target.copy_(t_host, non_blocking=True)
+        e2e_in.copy_(in_host, non_blocking=True)
         wl.step(e2e_params, e2e_target)
-        g_host.copy_(wl.grad, non_blocking=True)
-        l_host.copy_(wl.loss, non_blocking=True)
+        out_host.copy_(wl.out, non_blocking=True)
         e_ev[k][1].record()
         torch.cuda.current_stream().synchronize()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev), dist, dev)
@@ -558,7 +564,7 @@ def our_arm(args, rank: int, world: int, local_rank: int):
         "fwd_mpix_s": wl.pixels_per_step / (fwd_ms * 1e-3) / 1e6 * world,
         "fwd_ms": fwd_ms,
         "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": n_h2d,
-                "d2h_bytes_per_step": int(wl.p.nbytes + 4)},
+                "d2h_bytes_per_step": int(out_host.numel() * 4)},
         "gpu_launches": int(launches),
         "stages_ms": {k: v["ms_per_launch"] for k, v in stages.items()},
         "pairs": {"visited": visited, "inside": inside, "instances": instances},
