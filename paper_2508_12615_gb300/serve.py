@@ -179,7 +179,7 @@ class Server:
                     key = self._key(req)
                     v = self.views.get(key) if self.cache_views else None
                     if v is None and prepares >= self.max_prepares and reqs:
-                        break  # leave further new views to the next round
+                        break  # leave further new views to the next scheduling pass
                     prepares += v is None
                     out_need = out_bytes + nbytes + H * W * 12
                     while self.resident_bytes + out_need + self._reserved() > self.budget and self._free_one(key):
