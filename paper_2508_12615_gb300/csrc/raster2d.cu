@@ -35,19 +35,36 @@ __device__ __forceinline__ float half_reduce_scatter16(float v[16]) {
     return v[0];
 }
 
+// Reduce-scatter within each group of 8 lanes: 16 values over its 8 lanes; lane q of a group ends
+// with the group's totals of values 2q (first) and 2q + 1 (second).
+__device__ __forceinline__ float2 oct_reduce_scatter16(float v[16]) {
+    const int ql = threadIdx.x & 7;
+#pragma unroll
+    for (int off = 4, half = 8; off >= 1; off >>= 1, half >>= 1) {
+        const bool hi = ql & off;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = hi ? v[i] : v[half + i];
+            const float keep = hi ? v[half + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return make_float2(v[0], v[1]);
+}
+
 // Backward.  The tile's dL/dimage sits in shared memory, stored by pixel pairs in the layout of
 // the forward pass (quadrant k, pair l: pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the 8x8
 // quadrant).  Batches of the tile list are staged with the mask of the quadrants that each pair's
-// cutoff ellipse reaches, and ordered by the number of those quadrants.  Each half-warp takes one
-// (tile, primitive) pair, so a warp works on two pairs that reach equally many quadrants; a lane
-// covers four pixels of a quadrant, column h & 7 and rows r, r + 4 (pixel pair r) and r + 2, r + 6
-// (pixel pair r + 2), r = h >> 3, in packed f32x2 arithmetic.  Per pixel inside the cutoff a lane
+// cutoff ellipse reaches, and ordered by the number of those quadrants.  Each group of 8 lanes
+// takes one (tile, primitive) pair, so a warp works on four pairs that reach equally many
+// quadrants; lane q of a group covers column q of a quadrant, its four pixel pairs (r, r + 4),
+// r = 0..3, in packed f32x2 arithmetic.  Per pixel inside the cutoff a lane
 // accumulates the factored sums
 //   sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy, sum g W
 // (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
-// b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one half-warp
-// reduction, since L, f and the centre are constant over the pair, and one reduction pass serves
-// both halves.  The sums are taken of -ga, -gb and -gt / pi (one multiplication less per pixel) and
+// b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one reduction
+// over the group's 8 lanes, since L, f and the centre are constant over the pair, and one reduction
+// pass serves the warp's four pairs.  The sums are taken of -ga, -gb and -gt / pi (one multiplication less per pixel) and
 // scaled once per pair.
 __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
@@ -66,7 +83,7 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int hl = lane & 15, half = lane >> 4;
+    const int ql = lane & 7, grp = lane >> 3;
     if (threadIdx.x < kTilePixels / 2) {
         const int k = threadIdx.x >> 5;
         const int u = x0 + (k & 1) * 8 + (lane & 7);
@@ -84,10 +101,9 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
         s_g[1][threadIdx.x] = make_ulonglong2(f2_pack(g0[2], g1[2]).r, 0ull);
     }
     if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;
-    // the lane's pixels in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1) rows), and
-    // its two pixel pairs' places in the pair layout
-    const float lane_px = (float)(x0 + (hl & 7)) + 0.5f, lane_py = (float)(y0 + (hl >> 3)) + 0.5f;
-    const int gp0 = (hl & 7) + 8 * (hl >> 3), gp1 = gp0 + 16;
+    // the lane's column in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1) rows); its
+    // pixel pair r sits at ql + 8 r in the pair layout
+    const float lane_px = (float)(x0 + ql) + 0.5f, lane_py = (float)y0 + 0.5f;
     const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
     const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
@@ -121,9 +137,9 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
         }
         __syncthreads();
         if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;  // read by no one until the next batch's counts
-        const int npairs = (n + 1) >> 1;
-        for (int pi = warp; pi < npairs; pi += kTilePixels / 32) {
-            const int idx = 2 * pi + half;
+        const int ngroups = (n + 3) >> 2;
+        for (int pi = warp; pi < ngroups; pi += kTilePixels / 32) {
+            const int idx = 4 * pi + grp;
             const bool has = idx < n;
             const int j = has ? (int)s_order[idx] : 0;
             uint32_t mask = has ? (uint32_t)s_mask[j] : 0u;
@@ -137,8 +153,8 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
                     // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
                     const float px = lane_px + (float)((k & 1) * 8), pyq = lane_py + (float)((k >> 1) * 8);
 #pragma unroll
-                    for (int pp = 0; pp < 2; ++pp) {
-                        const float py = pyq + (float)(2 * pp);
+                    for (int pp = 0; pp < 4; ++pp) {
+                        const float py = pyq + (float)pp;
                         // the pair's record, read again for each pixel pair rather than held in registers
                         const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
                         const f2x2 e2 = ld_f2x2_here(&s_e[2][j]), e3 = ld_f2x2_here(&s_e[3][j]);
@@ -157,7 +173,7 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
                         const f2 cs = f2_pack(cos_approx(alo), cos_approx(ahi));
                         const f2 sn = f2_pack(sin_approx(alo), sin_approx(ahi));
                         const f2 Wv = f2_mul(f2_fma(HALF, cs, HALF), G);
-                        const int gi = k * 32 + (pp ? gp1 : gp0);
+                        const int gi = k * 32 + ql + 8 * pp;
                         const f2x2 g01 = ld_f2x2(&s_g[0][gi]);
                         const f2 gb_ = ld_f2x2(&s_g[1][gi]).x;
                         const f2x2 e4 = ld_f2x2_here(&s_e[4][j]), e5 = ld_f2x2_here(&s_e[5][j]);
@@ -187,24 +203,34 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             for (int i = 11; i < 16; ++i) sums[i] = 0.f;
             sums[0] = -sums[0], sums[1] = -sums[1], sums[3] = -sums[3], sums[4] = -sums[4], sums[5] = -sums[5];
             sums[2] *= -kPi, sums[6] *= -kPi, sums[7] *= -kPi;
-            // lane h of the half holds the half's total of sum h; lane h < 12 writes slot h of the pair
-            const float tot = half_reduce_scatter16(sums);
-            const int base = half * 16;
-            const float sga = __shfl_sync(0xffffffffu, tot, base + 0);
-            const float sgb = __shfl_sync(0xffffffffu, tot, base + 1);
-            const float sgt = __shfl_sync(0xffffffffu, tot, base + 2);
+            // lane q of the group holds the group's totals of sums 2q and 2q + 1; lane q < 6 writes
+            // slots 2q and 2q + 1 of the pair
+            const float2 tot = oct_reduce_scatter16(sums);
+            const int base = grp * 8;
+            const float sga = __shfl_sync(0xffffffffu, tot.x, base + 0);
+            const float sgb = __shfl_sync(0xffffffffu, tot.y, base + 0);
+            const float sgt = __shfl_sync(0xffffffffu, tot.x, base + 1);
             // sum feeding each slot: l11 <- ga dx (3), l21 <- ga dy (4), l22 <- gb dy (5), fx <- gt dx (6),
             // fy <- gt dy (7), phc <- gt (2), colour 8..10
-            const int src = hl == 7 ? 2 : (hl >= 2 && hl <= 6 ? hl + 1 : hl);
-            float val = __shfl_sync(0xffffffffu, tot, base + src);
-            if (has && hl < kSlot) {
+            float val[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int slot = 2 * ql + e;
+                const int m = slot == 7 ? 2 : (slot >= 2 && slot <= 6 ? slot + 1 : slot);
+                const float a0 = __shfl_sync(0xffffffffu, tot.x, base + (m >> 1));
+                const float a1 = __shfl_sync(0xffffffffu, tot.y, base + (m >> 1));
+                val[e] = (m & 1) ? a1 : a0;
+            }
+            if (has && ql < kSlot / 2) {
                 const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
                 const float l11 = f2_lo(e1.x), l21 = f2_lo(e1.y), l22 = f2_lo(e2.x), fx = f2_lo(e2.y);
                 const float fy = f2_lo(ld_f2x2(&s_e[3][j]).x);
-                if (hl == 0) val = -fmaf(l11, sga, fx * sgt);
-                if (hl == 1) val = -fmaf(l21, sga, fmaf(l22, sgb, fy * sgt));
-                if (hl == 11) val = 0.f;
-                partial[(size_t)s_slot[j] * kSlot + hl] = val;
+                if (ql == 0) {
+                    val[0] = -fmaf(l11, sga, fx * sgt);
+                    val[1] = -fmaf(l21, sga, fmaf(l22, sgb, fy * sgt));
+                }
+                if (ql == 5) val[1] = 0.f;  // slot 11 is padding
+                *reinterpret_cast<float2*>(partial + (size_t)s_slot[j] * kSlot + 2 * ql) = make_float2(val[0], val[1]);
             }
         }
     }
