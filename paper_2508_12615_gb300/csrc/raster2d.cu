@@ -35,13 +35,13 @@ __device__ __forceinline__ float half_reduce_scatter16(float v[16]) {
     return v[0];
 }
 
-// Reduce-scatter within each group of 8 lanes: 16 values over its 8 lanes; lane q of a group ends
-// with the group's totals of values 2q (first) and 2q + 1 (second).
-__device__ __forceinline__ float2 oct_reduce_scatter16(float v[16]) {
-    const int ql = threadIdx.x & 7;
+// Reduce-scatter within each group of 4 lanes: 16 values over its 4 lanes; lane q of a group ends
+// with the group's totals of values 4q .. 4q + 3 in v[0 .. 3].
+__device__ __forceinline__ void group4_reduce_scatter16(float v[16]) {
+    const int q = threadIdx.x & 3;
 #pragma unroll
-    for (int off = 4, half = 8; off >= 1; off >>= 1, half >>= 1) {
-        const bool hi = ql & off;
+    for (int off = 2, half = 8; off >= 1; off >>= 1, half >>= 1) {
+        const bool hi = q & off;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
             const float send = hi ? v[i] : v[half + i];
@@ -49,22 +49,21 @@ __device__ __forceinline__ float2 oct_reduce_scatter16(float v[16]) {
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
-    return make_float2(v[0], v[1]);
 }
 
 // Backward.  The tile's dL/dimage sits in shared memory, stored by pixel pairs in the layout of
 // the forward pass (quadrant k, pair l: pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the 8x8
 // quadrant).  Batches of the tile list are staged with the mask of the quadrants that each pair's
-// cutoff ellipse reaches, and ordered by the number of those quadrants.  Each group of 8 lanes
-// takes one (tile, primitive) pair, so a warp works on four pairs that reach equally many
-// quadrants; lane q of a group covers column q of a quadrant, its four pixel pairs (r, r + 4),
-// r = 0..3, in packed f32x2 arithmetic.  Per pixel inside the cutoff a lane
+// cutoff ellipse reaches, and ordered by the number of those quadrants.  Each group of 4 lanes
+// takes one (tile, primitive) pair, so a warp works on eight pairs that reach equally many
+// quadrants; lane q of a group covers columns 2q and 2q + 1 of a quadrant, its eight pixel pairs
+// (r, r + 4), r = 0..3, in packed f32x2 arithmetic.  Per pixel inside the cutoff a lane
 // accumulates the factored sums
 //   sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy, sum g W
 // (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
 // b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one reduction
-// over the group's 8 lanes, since L, f and the centre are constant over the pair, and one reduction
-// pass serves the warp's four pairs.  The sums are taken of -ga, -gb and -gt / pi (one multiplication less per pixel) and
+// over the group's 4 lanes, since L, f and the centre are constant over the pair, and one reduction
+// pass serves the warp's eight pairs.  The sums are taken of -ga, -gb and -gt / pi (one multiplication less per pixel) and
 // scaled once per pair.
 __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
@@ -83,7 +82,8 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ql = lane & 7, grp = lane >> 3;
+    const int ql = lane & 3, grp = lane >> 2;
+    __shared__ __align__(16) float s_red[kTilePixels / 32][8][16];  // per warp and group: the pair's 16 sums
     if (threadIdx.x < kTilePixels / 2) {
         const int k = threadIdx.x >> 5;
         const int u = x0 + (k & 1) * 8 + (lane & 7);
@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
         s_g[1][threadIdx.x] = make_ulonglong2(f2_pack(g0[2], g1[2]).r, 0ull);
     }
     if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;
-    // the lane's column in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1) rows); its
-    // pixel pair r sits at ql + 8 r in the pair layout
-    const float lane_px = (float)(x0 + ql) + 0.5f, lane_py = (float)y0 + 0.5f;
+    // the lane's first column in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1)
+    // rows); its pixel pair (column 2 ql + c, rows r, r + 4) sits at 2 ql + c + 8 r in the pair layout
+    const float lane_px = (float)(x0 + 2 * ql) + 0.5f, lane_py = (float)y0 + 0.5f;
     const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
     const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
@@ -137,9 +137,9 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
         }
         __syncthreads();
         if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;  // read by no one until the next batch's counts
-        const int ngroups = (n + 3) >> 2;
+        const int ngroups = (n + 7) >> 3;
         for (int pi = warp; pi < ngroups; pi += kTilePixels / 32) {
-            const int idx = 4 * pi + grp;
+            const int idx = 8 * pi + grp;
             const bool has = idx < n;
             const int j = has ? (int)s_order[idx] : 0;
             uint32_t mask = has ? (uint32_t)s_mask[j] : 0u;
@@ -151,9 +151,11 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
                     const int k = __ffs(mask) - 1;
                     mask &= mask - 1u;
                     // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
-                    const float px = lane_px + (float)((k & 1) * 8), pyq = lane_py + (float)((k >> 1) * 8);
-#pragma unroll
-                    for (int pp = 0; pp < 4; ++pp) {
+                    const float pxq = lane_px + (float)((k & 1) * 8), pyq = lane_py + (float)((k >> 1) * 8);
+#pragma unroll 4
+                    for (int pq = 0; pq < 8; ++pq) {
+                        const int pp = pq & 3, cc = pq >> 2;
+                        const float px = pxq + (float)cc;
                         const float py = pyq + (float)pp;
                         // the pair's record, read again for each pixel pair rather than held in registers
                         const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
                         const f2 cs = f2_pack(cos_approx(alo), cos_approx(ahi));
                         const f2 sn = f2_pack(sin_approx(alo), sin_approx(ahi));
                         const f2 Wv = f2_mul(f2_fma(HALF, cs, HALF), G);
-                        const int gi = k * 32 + ql + 8 * pp;
+                        const int gi = k * 32 + 2 * ql + cc + 8 * pp;
                         const f2x2 g01 = ld_f2x2(&s_g[0][gi]);
                         const f2 gb_ = ld_f2x2(&s_g[1][gi]).x;
                         const f2x2 e4 = ld_f2x2_here(&s_e[4][j]), e5 = ld_f2x2_here(&s_e[5][j]);
@@ -203,35 +205,36 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             for (int i = 11; i < 16; ++i) sums[i] = 0.f;
             sums[0] = -sums[0], sums[1] = -sums[1], sums[3] = -sums[3], sums[4] = -sums[4], sums[5] = -sums[5];
             sums[2] *= -kPi, sums[6] *= -kPi, sums[7] *= -kPi;
-            // lane q of the group holds the group's totals of sums 2q and 2q + 1; lane q < 6 writes
-            // slots 2q and 2q + 1 of the pair
-            const float2 tot = oct_reduce_scatter16(sums);
-            const int base = grp * 8;
-            const float sga = __shfl_sync(0xffffffffu, tot.x, base + 0);
-            const float sgb = __shfl_sync(0xffffffffu, tot.y, base + 0);
-            const float sgt = __shfl_sync(0xffffffffu, tot.x, base + 1);
-            // sum feeding each slot: l11 <- ga dx (3), l21 <- ga dy (4), l22 <- gb dy (5), fx <- gt dx (6),
-            // fy <- gt dy (7), phc <- gt (2), colour 8..10
-            float val[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int slot = 2 * ql + e;
-                const int m = slot == 7 ? 2 : (slot >= 2 && slot <= 6 ? slot + 1 : slot);
-                const float a0 = __shfl_sync(0xffffffffu, tot.x, base + (m >> 1));
-                const float a1 = __shfl_sync(0xffffffffu, tot.y, base + (m >> 1));
-                val[e] = (m & 1) ? a1 : a0;
-            }
-            if (has && ql < kSlot / 2) {
+            // lane q of the group ends with the totals of sums 4q .. 4q + 3, which the group shares
+            // through shared memory; lanes 0 .. 2 write slots 4q .. 4q + 3 of the pair
+            group4_reduce_scatter16(sums);
+            const int q4 = ql;
+            float* red = s_red[warp][grp];
+            *reinterpret_cast<float4*>(red + 4 * q4) = make_float4(sums[0], sums[1], sums[2], sums[3]);
+            __syncwarp();
+            if (has && q4 < 3) {
+                const float sga = red[0], sgb = red[1], sgt = red[2];
                 const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
                 const float l11 = f2_lo(e1.x), l21 = f2_lo(e1.y), l22 = f2_lo(e2.x), fx = f2_lo(e2.y);
                 const float fy = f2_lo(ld_f2x2(&s_e[3][j]).x);
-                if (ql == 0) {
+                float val[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    // slots 4 q4 + e: l11 <- ga dx (3), l21 <- ga dy (4), l22 <- gb dy (5), fx <- gt dx (6),
+                    // fy <- gt dy (7), phc <- gt (2), colour 8..10
+                    const int slot = 4 * q4 + e;
+                    const int m = slot == 7 ? 2 : (slot >= 2 && slot <= 6 ? slot + 1 : slot);
+                    val[e] = red[m];
+                }
+                if (q4 == 0) {
                     val[0] = -fmaf(l11, sga, fx * sgt);
                     val[1] = -fmaf(l21, sga, fmaf(l22, sgb, fy * sgt));
                 }
-                if (ql == 5) val[1] = 0.f;  // slot 11 is padding
-                *reinterpret_cast<float2*>(partial + (size_t)s_slot[j] * kSlot + 2 * ql) = make_float2(val[0], val[1]);
+                if (q4 == 2) val[3] = 0.f;  // slot 11 is padding
+                *reinterpret_cast<float4*>(partial + (size_t)s_slot[j] * kSlot + 4 * q4) =
+                    make_float4(val[0], val[1], val[2], val[3]);
             }
+            __syncwarp();  // the group's sums are read before the next pass overwrites them
         }
     }
 }
