@@ -43,7 +43,7 @@ OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend":
 # DRAM bytes (read + write) per launch, per (workload, kernel), from the ncu captures summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
 # entry is removed when its kernel changes.
-TRAFFIC_BYTES = {("2d", "k_blend2d"): 9_052_928,
+TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_503_744 + 424_960, ("2d", "k_blend2d"): 9_052_928,
                  ("5d", "k_backward3d"): 27_144_448 + 768, ("5d", "k_blend3d"): 16_071_168 + 70_912}
 
 
