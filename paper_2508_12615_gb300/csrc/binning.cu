@@ -614,11 +614,14 @@ void launch_iota(uint32_t* v, int64_t n, cudaStream_t stream) {
 // ---------------------------------------------------------------------------------------------
 
 constexpr int kChunkBlocksPerSm = 2;
+// Below this many keys reduce-then-scan ranks 4096-key tiles, twice the blocks of a short sort.
+constexpr int64_t kSmallTileMaxKeys = (int64_t)1 << 20;
+int down_tile_keys(int64_t n) { return n < kSmallTileMaxKeys ? kPassTile : kSortTile; }
 constexpr int64_t kOnesweepMaxKeys = (int64_t)1 << 22;  // onesweep only below this many keys (and > 2 passes)
 
 // Chunks and whole tiles per chunk for n keys.
-int sort_chunks(int64_t n, int* tiles_per_chunk) {
-    const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kSortTile);
+int sort_chunks(int64_t n, int tile_keys, int* tiles_per_chunk) {
+    const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), (int64_t)tile_keys);
     const int64_t target = std::min<int64_t>(tiles, (int64_t)152 * kChunkBlocksPerSm);
     const int64_t tpc = ceil_div(tiles, target);
     *tiles_per_chunk = (int)tpc;
@@ -694,30 +697,35 @@ struct SortDownArgs {
 
 // One tile of a chunk (see sort_tile for the element layout and the ranking).  s_base[d]: where
 // the chunk's next digit-d pair goes.
-template <bool FULL>
+// ITEMS keys per thread: kSortItems (8192-key tiles, the peer tables in the key area) or
+// kPassItems (4096-key tiles in the layout of k_sort_pass, the peer tables after the arrays).
+template <int ITEMS, bool FULL>
 __device__ __forceinline__ void down_tile(const SortDownArgs& a, int64_t tile, int cnt, uint32_t* s_keys,
                                           uint32_t* s_vals, uint32_t (*s_wc)[kMaxRadix], uint32_t* s_dstart,
                                           uint32_t* s_base, uint32_t* s_gofs, uint32_t* s_warp) {
+    static_assert(ITEMS == kSortItems || ITEMS == kPassItems, "tile layouts");
+    constexpr int kTileKeys = kSortThreads * ITEMS;
+    uint32_t* peer_base = ITEMS == kSortItems ? s_keys : s_keys + kPassPeerWords;
     const int radix = 1 << a.nbits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const int shift = a.shift;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t blk = tile * kSortTile;
-    const int run = warp * (kSortItems * 32) + lane;
+    const int64_t blk = tile * kTileKeys;
+    const int run = warp * (ITEMS * 32) + lane;
     auto valid = [&](int i) { return FULL || run + 32 * i < cnt; };
-    uint32_t(*s_peer)[kSortWarps][kMaxRadix] = reinterpret_cast<uint32_t(*)[kSortWarps][kMaxRadix]>(s_keys);
+    uint32_t(*s_peer)[kSortWarps][kMaxRadix] = reinterpret_cast<uint32_t(*)[kSortWarps][kMaxRadix]>(peer_base);
     for (int k = threadIdx.x; k < kSortWarps * kMaxRadix; k += kSortThreads) (&s_wc[0][0])[k] = 0u;
-    for (int k = threadIdx.x; k < 2 * kSortWarps * kMaxRadix; k += kSortThreads) s_keys[k] = 0u;
+    for (int k = threadIdx.x; k < 2 * kSortWarps * kMaxRadix; k += kSortThreads) peer_base[k] = 0u;
     {
         const uint32_t* keys_in = a.keys_in + blk;
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) s_vals[run + 32 * i] = valid(i) ? keys_in[run + 32 * i] : 0u;
+        for (int i = 0; i < ITEMS; ++i) s_vals[run + 32 * i] = valid(i) ? keys_in[run + 32 * i] : 0u;
     }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t pos[kSortItems];
+    uint32_t pos[ITEMS];
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         const bool ok = valid(i);
         const uint32_t d = (s_vals[run + 32 * i] >> shift) & mask;
         uint32_t* peer = &s_peer[i & 1][warp][d];
@@ -753,7 +761,7 @@ __device__ __forceinline__ void down_tile(const SortDownArgs& a, int64_t tile, i
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         if (valid(i)) {
             const uint32_t key = s_vals[run + 32 * i];
             const uint32_t d = (key >> shift) & mask;
@@ -763,16 +771,16 @@ __device__ __forceinline__ void down_tile(const SortDownArgs& a, int64_t tile, i
     }
     {
         const uint32_t* vals_in = a.vals_in + blk;
-        uint32_t v[kSortItems];
+        uint32_t v[ITEMS];
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) v[i] = valid(i) ? vals_in[run + 32 * i] : 0u;
+        for (int i = 0; i < ITEMS; ++i) v[i] = valid(i) ? vals_in[run + 32 * i] : 0u;
         __syncthreads();  // every key has left s_vals
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i)
+        for (int i = 0; i < ITEMS; ++i)
             if (valid(i)) s_vals[pos[i]] = v[i];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < (FULL ? kSortTile : cnt); t += kSortThreads) {
+    for (int t = threadIdx.x; t < (FULL ? kTileKeys : cnt); t += kSortThreads) {
         const uint32_t key = s_keys[t];
         const uint32_t g = s_gofs[(key >> shift) & mask] + (uint32_t)t;
         const uint32_t val = s_vals[t];
@@ -783,13 +791,15 @@ __device__ __forceinline__ void down_tile(const SortDownArgs& a, int64_t tile, i
     __syncthreads();  // the tile's buffers are free for the next tile
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads, 2) k_sort_downsweep(const __grid_constant__ SortDownArgs a) {
     pdl_enter();
+    constexpr int kTileKeys = kSortThreads * ITEMS;
     extern __shared__ uint4 s_sort_raw[];
     uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_sort_raw);
-    uint32_t* s_vals = s_keys + kSortTile;
-    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kSortTile);
-    uint32_t* s_dstart = s_vals + kSortTile + kSortWarps * kMaxRadix;
+    uint32_t* s_vals = s_keys + kTileKeys;
+    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kTileKeys);
+    uint32_t* s_dstart = s_vals + kTileKeys + kSortWarps * kMaxRadix;
     uint32_t* s_base = s_dstart + kMaxRadix;
     uint32_t* s_gofs = s_base + kMaxRadix;
     uint32_t* s_warp = s_gofs + kMaxRadix;
@@ -801,14 +811,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_downsweep(const __grid
         if ((int)threadIdx.x < radix) s_base[threadIdx.x] = ex + a.bases[(size_t)threadIdx.x * a.chunks + blockIdx.x];
     }
     __syncthreads();
-    const int64_t tiles = (a.n + kSortTile - 1) / kSortTile;
+    const int64_t tiles = (a.n + kTileKeys - 1) / kTileKeys;
     const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_chunk, t1 = min(tiles, t0 + a.tiles_per_chunk);
     for (int64_t tile = t0; tile < t1; ++tile) {
-        const int64_t left = a.n - tile * kSortTile;
-        if (left >= kSortTile)
-            down_tile<true>(a, tile, kSortTile, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
+        const int64_t left = a.n - tile * kTileKeys;
+        if (left >= kTileKeys)
+            down_tile<ITEMS, true>(a, tile, kTileKeys, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
         else
-            down_tile<false>(a, tile, (int)left, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
+            down_tile<ITEMS, false>(a, tile, (int)left, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
     }
 }
 
@@ -816,7 +826,7 @@ int64_t radix_hist_words(int64_t n) {
     const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kPassTile);
     const int64_t onesweep = sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
     int tpc = 0;
-    const int64_t chunked = 2 * (int64_t)kMaxRadix * sort_chunks(n, &tpc) + kMaxRadix;
+    const int64_t chunked = 2 * (int64_t)kMaxRadix * sort_chunks(n, down_tile_keys(n), &tpc) + kMaxRadix;
     return std::max(onesweep, chunked);
 }
 
@@ -826,7 +836,10 @@ void sort_pass_attributes() {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmemBytes);
-        cudaFuncSetAttribute(k_sort_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmemBytes);
+        cudaFuncSetAttribute(k_sort_downsweep<kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSortSmemBytes);
+        cudaFuncSetAttribute(k_sort_downsweep<kPassItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPassSmemBytes);
     });
 }
 
@@ -849,7 +862,8 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
     // otherwise reduce-then-scan, which never waits on another block, is.
     if (plan.passes <= 2 || n >= kOnesweepMaxKeys) {
         int tpc = 0;
-        const int chunks = sort_chunks(n, &tpc);
+        const int tile_keys = down_tile_keys(n);
+        const int chunks = sort_chunks(n, tile_keys, &tpc);
         uint32_t* counts = hist;
         uint32_t* bases = hist + (size_t)kMaxRadix * chunks;
         uint32_t* totals = bases + (size_t)kMaxRadix * chunks;
@@ -857,12 +871,15 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         for (int p = 0; p < plan.passes; ++p) {
             const bool last_pass = p == plan.passes - 1;
             launch_pdl(k_sort_upsweep, (unsigned)chunks, kThreads, 0, stream, (const uint32_t*)keys[cur], n, plan.shift[p],
-                       plan.nbits[p], (int64_t)tpc * kSortTile, chunks, counts);
+                       plan.nbits[p], (int64_t)tpc * tile_keys, chunks, counts);
             launch_pdl(k_sort_chunk_scan, (unsigned)(1 << plan.nbits[p]), kScanThreads, 0, stream, (const uint32_t*)counts,
                        chunks, bases, totals);
             SortDownArgs da{keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, plan.shift[p], plan.nbits[p], chunks,
                             tpc, bases, totals, last_pass ? table : nullptr, last_pass ? gathered : nullptr};
-            launch_pdl(k_sort_downsweep, (unsigned)chunks, kSortThreads, kSortSmemBytes, stream, da);
+            if (tile_keys == kPassTile)
+                launch_pdl(k_sort_downsweep<kPassItems>, (unsigned)chunks, kSortThreads, kPassSmemBytes, stream, da);
+            else
+                launch_pdl(k_sort_downsweep<kSortItems>, (unsigned)chunks, kSortThreads, kSortSmemBytes, stream, da);
             count_launches(3);
             cur ^= 1;
         }
