@@ -1,0 +1,63 @@
+"""Host logic of bench.py's oracle baseline (no GPU): the bounded sample of one step.
+
+The sample is sized from a tiny calibration run; when that run overstates the per-item cost (a
+fixed cost per call, as thread start-up gives the real oracle), the first sample takes far less
+than the budget, and the sampler sizes it again from the first sample's own rate.  The fake oracle
+below charges a fixed 20 ms per call plus a per-item time, so the calibration overstates the cost
+about 25-fold.
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+CALL_S, PIXEL_S, PRIM_S = 0.02, 2e-6, 1e-4
+
+
+class FakeOracle:
+    def __init__(self):
+        self.calls = []
+
+    def build(self):
+        pass
+
+    def render2d(self, p, H, W, pixels=None):
+        pix = np.asarray(pixels)
+        self.calls.append(("render", len(pix)))
+        time.sleep(CALL_S + PIXEL_S * len(pix))
+        return np.zeros((len(pix), 3))
+
+    def grad2d(self, p, H, W, g):
+        self.calls.append(("grad", len(p)))
+        time.sleep(CALL_S + PRIM_S * len(p))
+        return np.zeros_like(p, dtype=np.float64)
+
+
+def test_sample_is_resized_from_its_own_rate(monkeypatch):
+    fake = FakeOracle()
+    monkeypatch.setitem(sys.modules, "oracle", fake)
+    H, W, n, budget = 64, 64, 4000, 1.0
+    p = np.zeros((n, 16), np.float32)
+    target = np.zeros((H, W, 3), np.float32)
+    t0 = time.perf_counter()
+    per_step, desc = bench.oracle_step_sample(p, target, H, W, budget)
+    wall = time.perf_counter() - t0
+    # calibration (1 row, n / 2000 primitives), the first sample, then the resized one
+    renders = [k for kind, k in fake.calls if kind == "render"]
+    grads = [k for kind, k in fake.calls if kind == "grad"]
+    assert len(renders) == 3 and len(grads) == 3
+    assert renders[2] > renders[1] and grads[2] > grads[1]
+    # the true cost of a full step, and the estimate from the final sample
+    true_step = 2 * CALL_S + PIXEL_S * H * W + PRIM_S * n
+    rows, prims = renders[2] // W, grads[2]
+    est = (CALL_S + PIXEL_S * rows * W) * (H / rows) + (CALL_S + PRIM_S * prims) * (n / prims)
+    assert abs(per_step - est) <= 0.5 * est  # the sleeps only overrun
+    assert per_step >= 0.9 * true_step
+    assert wall <= 3 * budget
+    assert f"of {H} rows" in desc and f"of {n} primitives" in desc
