@@ -166,10 +166,14 @@ wipes_status wipes_l2_loss(wipes_ctx* ctx, const float* img, const float* target
  * current device and needs no context.  Its scratch is a fixed 256 KB array inside the library's
  * device image (one partial sum per 4096 elements), held by every GPU that loads the library until
  * the process exits.  Limits: 1 <= n <= 268,435,456 (65,536 x 4,096); larger n returns
- * WIPES_ERR_INVALID.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls on a device
- * share the array: calls that overlap on the GPU race.  Each call writes every partial sum before
- * reading it, so the array needs no clearing. */
+ * WIPES_ERR_INVALID.  Every call outside stream capture looks up the array's device address in
+ * the current context (cudaGetSymbolAddress); a call on a capturing stream reuses the address of
+ * the last call outside capture on that device, so make a first call on each device before any
+ * stream capture (without one, the call fails with WIPES_ERR_CUDA).  The call does not switch
+ * devices: img, target, loss and dL_dimg must be on the calling thread's current device.  The
+ * array is per process and per device (other processes hold their own).  All calls on a device
+ * in this process share it: calls that overlap on the GPU race.  Each call writes every partial
+ * sum before reading it, so the array needs no clearing. */
 wipes_status wipes_l2_loss_noalloc(const float* img, const float* target, int64_t n, float* loss, float* dL_dimg,
                                    void* stream);
 

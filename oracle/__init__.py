@@ -70,6 +70,8 @@ def _load():
         lib.wo_deform6d_grad.argtypes = [P, i64, f64, P, P]
         lib.wo_cutoff_coverage.argtypes = [i32, P, i64, P, i32, i32, f32, f32, P]
         lib.wo_sh_basis.argtypes = [P, i64, P]
+        lib.wo_alpha_decisions.argtypes = [P, i64, P, i32, i32, P, P, i64, P, P]
+        lib.wo_rule_cos_sin.argtypes = [P, i64, P]
         _lib = lib
     return _lib
 
@@ -151,9 +153,10 @@ AMB_ALPHA_MIN, AMB_T_MIN, AMB_ALPHA_MAX = 1, 2, 4
 
 
 def render3d(params, cam, H, W, opts=None, truncated=True, pixels=None):
-    """Front-to-back blend.  Returns (C, T_final, n_contrib, ambiguous) where ambiguous holds the
-    AMB_* bits of threshold decisions taken within the kernels' error margin: bits 0-1 (alpha_min
-    skip, T_min stop) can change the image, bit 2 (alpha_max clamp) only the gradient."""
+    """Front-to-back blend.  Returns (C, T_final, n_contrib, ambiguous).  The threshold decisions
+    are taken from the kernels' binary32 projected record (see alpha_decisions); ambiguous holds the
+    AMB_* bits of decisions that lie within the kernels' error bound of their threshold: bits 0-1
+    (alpha_min skip, T_min stop) can change the image, bit 2 (alpha_max clamp) only the gradient."""
     params = _f32(params)
     camv = _f32(cam)
     o = _opts3(opts)
@@ -182,6 +185,32 @@ def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True, with_abs=False)
     _load().wo_grad3d(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), int(truncated), _ptr(g), _ptr(out),
                       _ptr(gabs))
     return (out, gabs) if with_abs else out
+
+
+def rule_cos_sin(theta):
+    """The footprint rule's binary32 (cos, sin) of 2D rotation angles (binary64 inputs): a fixed
+    sequence of binary64 additions and multiplications (Cody-Waite reduction, Taylor series),
+    rounded once.  Returns [n,2] float32."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    out = np.zeros((th.size, 2), np.float32)
+    _load().wo_rule_cos_sin(_ptr(th), th.size, _ptr(out))
+    return out
+
+
+def alpha_decisions(params, cam, H, W, pairs, opts=None):
+    """Threshold-decision values (Eq. 3's alpha_min skip, alpha_max clamp and T_min stop are taken
+    from the kernels' binary32 projected record).  pairs[n,3] = (primitive, u, v).  Returns
+    (rec[N,9] = mx, my, l11, l21, l22, f'x, f'y, phase in cycles, opacity as binary32,
+     out[n,3] = record alpha before the clamp (binary64), its kernel error bound, binary64-projection alpha)."""
+    params = _f32(params)
+    camv = _f32(cam)
+    o = _opts3(opts)
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    rec = np.zeros((params.shape[0], 9), np.float32)
+    out = np.zeros((pr.shape[0], 3), np.float64)
+    _load().wo_alpha_decisions(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), _ptr(pr), pr.shape[0],
+                               _ptr(rec), _ptr(out))
+    return rec, out
 
 
 def project3d(params, cam, H, W, opts=None):

@@ -42,6 +42,7 @@
 
 #define TILE 16
 #define EXT_MARGIN 1.0009765625f /* 1 + 2^-10: footprint half-extent safety factor */
+#define INV_TWO_PI_F 0.15915494309189535f /* 1 / (2 pi) rounded to binary32: phase in cycles */
 
 static const double PI = 3.14159265358979323846;
 
@@ -56,6 +57,11 @@ typedef struct {
     float depth;           /* camera z (3D), 0 (2D) */
     int u0, v0, u1, v1;    /* covered pixel range (inclusive); empty if u0 > u1 */
     int valid;
+    /* 3D only: the record's binary32 projected frequency (cycles/px) under either frequency map
+     * (index 0: phase gradient on the fronto-parallel plane, 1: literal J W f), its phase in
+     * cycles and the opacity.  They take part in no integer decision of the rule itself; the
+     * threshold decisions of the blend are evaluated from them (see alpha_decision). */
+    float fp[2][2], phc, op;
 } fp32_footprint;
 
 static int finite4(float a, float b, float c, float d) { return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d); }
@@ -79,11 +85,57 @@ static void footprint_pixrect(fp32_footprint* k, int W, int H) {
     if (u0 > u1 || v0 > v1) { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
 }
 
+/* cos and sin of the 2D rotation angle for the footprint rule, as a fixed sequence of binary64
+ * additions and multiplications (no library transcendental, so that any two IEEE binary64
+ * implementations of the rule return the same bits), rounded once to binary32.
+ * Cody and Waite's reduction: k = nearest integer to th 2/pi, r = th - k pi/2 with pi/2 split into
+ * three parts (the first two of 33 significant bits, so k times them is exact for |k| < 2^20);
+ * then the Taylor series of sin r through r^17 and of cos r through r^18 (|r| <= pi/4: truncation
+ * below 1e-19), in Horner form in r^2; the quadrant k mod 4 picks the signs and the swap.
+ * |th| > 1e15 (or not finite) gives NaN, which makes the primitive invalid. */
+static void rule_cos_sin(double th, float* c, float* s) {
+    if (!(fabs(th) <= 1e15)) { *c = *s = (float)NAN; return; }
+    const double k = nearbyint(th * 0x1.45f306dc9c883p-1);
+    const double r = ((th - k * 0x1.921fb544p+0) - k * 0x1.0b4611a6p-34) - k * 0x1.3198a2e037073p-69;
+    const double z = r * r;
+    double ps = 0x1.952c77030ad4ap-49;           /*  1/17! */
+    ps = ps * z - 0x1.ae7f3e733b81fp-41;         /* -1/15! */
+    ps = ps * z + 0x1.6124613a86d09p-33;         /*  1/13! */
+    ps = ps * z - 0x1.ae64567f544e4p-26;         /* -1/11! */
+    ps = ps * z + 0x1.71de3a556c734p-19;         /*  1/9!  */
+    ps = ps * z - 0x1.a01a01a01a01ap-13;         /* -1/7!  */
+    ps = ps * z + 0x1.1111111111111p-7;          /*  1/5!  */
+    ps = ps * z - 0x1.5555555555555p-3;          /* -1/3!  */
+    const double sr = r + (r * z) * ps;
+    double pc = -0x1.6827863b97d97p-53;          /* -1/18! */
+    pc = pc * z + 0x1.ae7f3e733b81fp-45;         /*  1/16! */
+    pc = pc * z - 0x1.93974a8c07c9dp-37;         /* -1/14! */
+    pc = pc * z + 0x1.1eed8eff8d898p-29;         /*  1/12! */
+    pc = pc * z - 0x1.27e4fb7789f5cp-22;         /* -1/10! */
+    pc = pc * z + 0x1.a01a01a01a01ap-16;         /*  1/8!  */
+    pc = pc * z - 0x1.6c16c16c16c17p-10;         /* -1/6!  */
+    pc = pc * z + 0x1.5555555555555p-5;          /*  1/4!  */
+    pc = pc * z - 0.5;                           /* -1/2!  */
+    const double cr = 1.0 + z * pc;
+    switch ((int)((long long)k & 3)) {
+        case 0: *c = (float)cr; *s = (float)sr; break;
+        case 1: *c = (float)(-sr); *s = (float)cr; break;
+        case 2: *c = (float)(-cr); *s = (float)(-sr); break;
+        default: *c = (float)sr; *s = (float)(-cr); break;
+    }
+}
+
+/* exported for its pin: out[n,2] = the rule's (cos, sin) of th[n] */
+int wo_rule_cos_sin(const double* th, int64_t n, float* out) {
+    for (int64_t i = 0; i < n; ++i) rule_cos_sin(th[i], &out[2 * i], &out[2 * i + 1]);
+    return 0;
+}
+
 /* 2D record: mu(2) s(2) theta f(2) phi c(3) */
 static void footprint2d(const float* p, float cutoff, int W, int H, fp32_footprint* k) {
     float sx = p[2], sy = p[3];
-    float c = (float)cos((double)p[4]);
-    float s = (float)sin((double)p[4]);
+    float c, s;
+    rule_cos_sin((double)p[4], &c, &s);
     float sx2 = sx * sx, sy2 = sy * sy;
     float ix = 1.0f / sx2, iy = 1.0f / sy2;
     float cc = c * c, ss = s * s, cs = c * s;
@@ -198,6 +250,17 @@ static void footprint3d(const float* p, const float* cam, float cutoff, float di
     k->ex = (cutoff * sqrtf(S00)) * EXT_MARGIN;
     k->ey = (cutoff * sqrtf(S11)) * EXT_MARGIN;
     k->depth = tz;
+    {
+        float fcx = (V[0] * p[10] + V[1] * p[11]) + V[2] * p[12];
+        float fcy = (V[4] * p[10] + V[5] * p[11]) + V[6] * p[12];
+        float fcz = (V[8] * p[10] + V[9] * p[11]) + V[10] * p[12];
+        k->fp[0][0] = fcx * tz / fx;
+        k->fp[0][1] = fcy * tz / fy;
+        k->fp[1][0] = j00 * fcx + j02 * fcz;
+        k->fp[1][1] = j11 * fcy + j12 * fcz;
+        k->phc = p[13] * INV_TWO_PI_F;
+        k->op = p[14];
+    }
     k->valid = finite4(k->mx, k->my, l11, l21) && finite4(l22, k->ex, k->ey, D) && D > 0.0f && S11 > 0.0f &&
                l11 > 0.0f && l22 > 0.0f;
     if (k->valid) footprint_pixrect(k, W, H);
@@ -794,22 +857,71 @@ static void scene3_build(const float* params, int64_t N, const float* cam, int H
 
 static void scene3_free(scene3* s) { free(s->k); free(s->w); free(s->order); }
 
-/* Ambiguity margins.  The kernels evaluate alpha in binary32 with approximate exp and cos; over the
- * workloads here its absolute error stays below AMB_ALPHA.  A transmittance that has passed through
- * layers of opacity a_i then carries a relative error of at most sum_i AMB_ALPHA / (1 - a_i) plus
- * one rounding per product. */
-#define AMB_ALPHA 2e-6
+/* Threshold decisions (alpha_min skip, alpha_max clamp, T_min stop: Eq. 3 with the 3DGS constants).
+ * A decision that floating point turns into a branch is taken, on both sides, from the values the
+ * kernels decide with: the primitive's binary32 projected record (centre, Cholesky factor of
+ * Sigma'^-1, frequency, phase in cycles, opacity; bit-exact with the kernels' footprint rule).
+ * The oracle evaluates alpha from that record exactly (binary64), and decides with it.  The
+ * kernels evaluate the same expression in binary32 with approximate exp2 and cos; the bound below
+ * follows their operations one by one, so a decision whose exact value lies farther than the bound
+ * from its threshold is the kernels' decision too.  Pixels with a decision inside its bound are
+ * reported as ambiguous.  The colour values themselves are still accumulated from the binary64
+ * projection (proj), so the image keeps the full precision of the method.
+ *
+ * Error constants of the approximate instructions, taken conservatively from their documented
+ * accuracy: cos.approx.f32 absolute error <= 2^-20 on [-pi, pi]; ex2.approx.f32 relative error
+ * <= 2^-21.  U = 2^-24 is the unit roundoff of binary32. */
+#define U32 5.9604644775390625e-08
+#define EPS_COS 9.5367431640625e-07
+#define EPS_EX2 4.76837158203125e-07
+#define AMB_SAFETY 1.5
 #define AMB_ALPHA_MIN 1 /* bit 0: the alpha_min skip could go either way */
 #define AMB_T_MIN 2     /* bit 1: the T_min stop could go either way */
 #define AMB_ALPHA_MAX 4 /* bit 2: the alpha_max clamp could go either way (a kink, not a jump) */
 
+/* alpha before the clamp, o W'(x), from the binary32 record, in binary64; *bound receives an upper
+ * bound of |kernel value - exact value|.  The kernel computes, in binary32:
+ *   dx = px - mx, dy = py - my;  a = fma(l11, dx, l21 dy);  b = l22 dy;  q = fma(a, a, b b);
+ *   G = ex2(q * (-log2(e) / 2));  t = fma(fx, dx, fma(fy, dy, phc));
+ *   ang = (t - rint(t)) * 2pi;  M = fma(1/2, cos(ang), 1/2);  raw = o (M G). */
+static double alpha_decision(const fp32_footprint* k, int fmode, int u, int v, double* bound) {
+    const double dx = ((double)u + 0.5) - (double)k->mx, dy = ((double)v + 0.5) - (double)k->my;
+    const double l11 = k->l11, l21 = k->l21, l22 = k->l22;
+    const double fx = k->fp[fmode][0], fy = k->fp[fmode][1], phc = k->phc, o = k->op;
+    const double a = l11 * dx + l21 * dy, b = l22 * dy;
+    const double q = a * a + b * b;
+    const double G = exp(-0.5 * q);
+    const double s1 = fy * dy + phc, t = fx * dx + s1;
+    const double ang = 2.0 * PI * (t - nearbyint(t));
+    const double ca = cos(ang), sa = sin(ang);
+    const double M = 0.5 + 0.5 * ca, raw = o * M * G;
+    /* rounding of the kernel's steps, first order, with every term taken in absolute value */
+    const double ddx = U32 * fabs(dx), ddy = U32 * fabs(dy);
+    const double da = fabs(l11) * ddx + fabs(l21) * ddy + U32 * (fabs(l21 * dy) + fabs(a));
+    const double db = fabs(l22) * ddy + U32 * fabs(b);
+    const double dq = 2.0 * fabs(a) * da + 2.0 * fabs(b) * db + da * da + db * db + U32 * (b * b + q);
+    const double e = 0.5 * q * 1.4426950408889634;          /* |q * (-log2(e) / 2)| */
+    const double de = 0.7213475204444817 * dq + 2.0 * U32 * e; /* the constant's and the product's rounding */
+    const double dG = G * (EPS_EX2 + 0.6931471805599453 * de);
+    const double dt = fabs(fx) * ddx + fabs(fy) * ddy + U32 * (fabs(s1) + fabs(t));
+    const double dang = 2.0 * PI * dt + 2.0 * U32 * fabs(ang);
+    const double dcos = fabs(sa) * dang + 0.5 * dang * dang + EPS_COS;
+    const double dM = 0.5 * dcos + U32 * M;
+    const double dW = M * dG + G * dM + dM * dG + U32 * M * G;
+    *bound = AMB_SAFETY * (o * dW + U32 * raw) + 1e-15;
+    return raw;
+}
+
 typedef struct { uint32_t prim; double alpha, T, Wv; int clamped; wval e; } contrib;
 
 /* Blend one pixel front to back.  Writes the contributors (when list != NULL), returns their count.
- * *amb collects the AMB_* bits of the threshold decisions taken within their error margins. */
+ * *amb collects the AMB_* bits of the threshold decisions taken within their error bounds.
+ * The decisions use the record's alpha (alpha_decision) and the transmittance built from it,
+ * T_dec, whose relative error in the kernels is at most Trel: per contributor its alpha's bound
+ * over 1 - alpha plus the rounding of 1 - alpha and of the product. */
 static int64_t blend_pixel(const scene3* s, int u, int v, const blend_opts* o, int truncated, double C[3],
                            double* Tout, int* amb, contrib* list) {
-    double T = 1.0, Trel = 0.0;
+    double T = 1.0, Tdec = 1.0, Trel = 0.0;
     float k2 = o->cutoff * o->cutoff;
     int64_t n = 0;
     C[0] = C[1] = C[2] = 0.0;
@@ -817,25 +929,29 @@ static int64_t blend_pixel(const scene3* s, int u, int v, const blend_opts* o, i
     for (int64_t j = 0; j < s->nvalid; ++j) {
         uint32_t i = s->order[j];
         if (truncated && !(q32(&s->k[i], u, v) <= k2)) continue;
+        double bound;
+        const double rdec = alpha_decision(&s->k[i], o->fmode, u, v, &bound);
+        if (o->amin > 0.0f && fabs(rdec - (double)o->amin) <= bound) *amb |= AMB_ALPHA_MIN;
+        if (fabs(rdec - (double)o->amax) <= bound) *amb |= AMB_ALPHA_MAX;
+        const int clamped = rdec > (double)o->amax;
+        const double adec = clamped ? (double)o->amax : rdec;
+        if (adec < (double)o->amin) continue;
+        const double testTdec = Tdec * (1.0 - adec);
+        const double rel = Trel + (clamped ? 0.0 : bound / (1.0 - adec)) + 2.0 * U32;
+        if (o->Tmin > 0.0f && fabs(testTdec - (double)o->Tmin) <= AMB_SAFETY * rel * testTdec) *amb |= AMB_T_MIN;
+        if (testTdec < (double)o->Tmin) break;
+        /* the value: the binary64 projection */
         wval e;
         eval_wavelet(&s->w[i], u, v, &e);
-        double raw = s->w[i].o * e.W;
-        if (o->amin > 0.0f && fabs(raw - (double)o->amin) < AMB_ALPHA) *amb |= AMB_ALPHA_MIN;
-        if (fabs(raw - (double)o->amax) < AMB_ALPHA) *amb |= AMB_ALPHA_MAX;
-        int clamped = raw > (double)o->amax;
-        double alpha = clamped ? (double)o->amax : raw;
-        if (alpha < (double)o->amin) continue;
-        double testT = T * (1.0 - alpha);
-        double rel = Trel + AMB_ALPHA / (1.0 - alpha) + 1.2e-7;
-        if (o->Tmin > 0.0f && fabs(testT - (double)o->Tmin) <= 2.0 * rel * testT) *amb |= AMB_T_MIN;
-        if (testT < (double)o->Tmin) break;
+        const double alpha = clamped ? (double)o->amax : s->w[i].o * e.W;
         for (int ch = 0; ch < 3; ++ch) C[ch] += s->w[i].c[ch] * alpha * T;
         if (list) {
             list[n].prim = i; list[n].alpha = alpha; list[n].T = T; list[n].Wv = e.W;
             list[n].clamped = clamped; list[n].e = e;
         }
         ++n;
-        T = testT;
+        T *= 1.0 - alpha;
+        Tdec = testTdec;
         Trel = rel;
     }
     for (int ch = 0; ch < 3; ++ch) C[ch] += T * o->bg[ch];
@@ -1105,6 +1221,39 @@ int wo_project3d(const float* params, int64_t N, const float* cam, int H, int W,
         r[7] = w.f[0]; r[8] = w.f[1]; r[9] = w.phi; r[10] = w.o;
         r[11] = w.c[0]; r[12] = w.c[1]; r[13] = w.c[2];
     }
+    return 0;
+}
+
+/* The threshold-decision values of (primitive, pixel) pairs: out[n,4] = the record's binary32
+ * values the decision reads are in rec[N,9] (mx, my, l11, l21, l22, f'x, f'y, phase in cycles,
+ * opacity; zeros for an invalid primitive); per pair (prim, u, v) in pairs[n,3]: out[n,3] = the
+ * record's alpha before the clamp, its kernel error bound, and the alpha of the binary64 projection. */
+int wo_alpha_decisions(const float* params, int64_t N, const float* cam, int H, int W, const float* opts,
+                       const int32_t* pairs, int64_t n, float* rec, double* out) {
+    blend_opts o = read_opts(opts);
+    const int P = rec3_stride(&o);
+    fp32_footprint* k = all_footprints(o.sh ? KIND_3D_SH : KIND_3D, params, N, cam, H, W, o.cutoff, o.dil);
+    if (rec)
+        for (int64_t i = 0; i < N; ++i) {
+            float* r = rec + i * 9;
+            memset(r, 0, sizeof(float) * 9);
+            if (!k[i].valid) continue;
+            r[0] = k[i].mx; r[1] = k[i].my; r[2] = k[i].l11; r[3] = k[i].l21; r[4] = k[i].l22;
+            r[5] = k[i].fp[o.fmode][0]; r[6] = k[i].fp[o.fmode][1]; r[7] = k[i].phc; r[8] = k[i].op;
+        }
+    for (int64_t j = 0; j < n; ++j) {
+        const int32_t i = pairs[j * 3], u = pairs[j * 3 + 1], v = pairs[j * 3 + 2];
+        double* r = out + j * 3;
+        r[0] = r[1] = r[2] = 0.0;
+        if (i < 0 || i >= N || !k[i].valid) continue;
+        r[0] = alpha_decision(&k[i], o.fmode, u, v, &r[1]);
+        proj w;
+        project3d(params + (int64_t)i * P, cam, H, W, o.dil, o.fmode, 1, &w);
+        wval e;
+        eval_wavelet(&w, u, v, &e);
+        r[2] = w.o * e.W;
+    }
+    free(k);
     return 0;
 }
 

@@ -95,6 +95,54 @@ __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rec
     if (depth_keys) depth_keys[i] = 0xFFFFFFFFu;
 }
 
+// cos and sin of a 2D rotation angle for the footprint rule, built from binary64 additions and
+// multiplications only (each written as its correctly rounded intrinsic, so no contraction or
+// reassociation can change a bit), then rounded once to binary32.  Any IEEE binary64 evaluation
+// of this sequence gives the same bits, which keeps the tile lists bit-exact without relying on
+// two math libraries agreeing.  Reduction by Cody and Waite: k = rint(th * 2/pi),
+// r = th - k pi/2 with pi/2 in three pieces (33, 33 and 53 significant bits; k times the first
+// two is exact for |k| < 2^20).  Then the Taylor series of sin r to r^17 and cos r to r^18
+// (|r| <= pi/4, truncation below 1e-19) in Horner form in z = r^2; k mod 4 selects the quadrant.
+// |th| > 1e15 or a non-finite th gives NaN (the primitive becomes invalid).
+__device__ __forceinline__ void rule_cos_sin(double th, float& c, float& s) {
+    if (!(fabs(th) <= 1e15)) {
+        c = s = __int_as_float(0x7fc00000);
+        return;
+    }
+    const double k = rint(__dmul_rn(th, 0x1.45f306dc9c883p-1));
+    double r = __dsub_rn(th, __dmul_rn(k, 0x1.921fb544p+0));
+    r = __dsub_rn(r, __dmul_rn(k, 0x1.0b4611a6p-34));
+    r = __dsub_rn(r, __dmul_rn(k, 0x1.3198a2e037073p-69));
+    const double z = __dmul_rn(r, r);
+    // sin: coefficients 1/17!, -1/15!, ..., -1/3!
+    double ps = 0x1.952c77030ad4ap-49;
+    ps = __dsub_rn(__dmul_rn(ps, z), 0x1.ae7f3e733b81fp-41);
+    ps = __dadd_rn(__dmul_rn(ps, z), 0x1.6124613a86d09p-33);
+    ps = __dsub_rn(__dmul_rn(ps, z), 0x1.ae64567f544e4p-26);
+    ps = __dadd_rn(__dmul_rn(ps, z), 0x1.71de3a556c734p-19);
+    ps = __dsub_rn(__dmul_rn(ps, z), 0x1.a01a01a01a01ap-13);
+    ps = __dadd_rn(__dmul_rn(ps, z), 0x1.1111111111111p-7);
+    ps = __dsub_rn(__dmul_rn(ps, z), 0x1.5555555555555p-3);
+    const double sr = __dadd_rn(r, __dmul_rn(__dmul_rn(r, z), ps));
+    // cos: coefficients -1/18!, 1/16!, ..., -1/2!
+    double pc = -0x1.6827863b97d97p-53;
+    pc = __dadd_rn(__dmul_rn(pc, z), 0x1.ae7f3e733b81fp-45);
+    pc = __dsub_rn(__dmul_rn(pc, z), 0x1.93974a8c07c9dp-37);
+    pc = __dadd_rn(__dmul_rn(pc, z), 0x1.1eed8eff8d898p-29);
+    pc = __dsub_rn(__dmul_rn(pc, z), 0x1.27e4fb7789f5cp-22);
+    pc = __dadd_rn(__dmul_rn(pc, z), 0x1.a01a01a01a01ap-16);
+    pc = __dsub_rn(__dmul_rn(pc, z), 0x1.6c16c16c16c17p-10);
+    pc = __dadd_rn(__dmul_rn(pc, z), 0x1.5555555555555p-5);
+    pc = __dsub_rn(__dmul_rn(pc, z), 0.5);
+    const double cr = __dadd_rn(1.0, __dmul_rn(z, pc));
+    switch ((int)((long long)k & 3)) {
+        case 0: c = __double2float_rn(cr); s = __double2float_rn(sr); break;
+        case 1: c = __double2float_rn(-sr); s = __double2float_rn(cr); break;
+        case 2: c = __double2float_rn(-cr); s = __double2float_rn(-sr); break;
+        default: c = __double2float_rn(sr); s = __double2float_rn(-cr); break;
+    }
+}
+
 // 2D, RS record (cov2d = 0): Sigma = R(theta) diag(sx^2, sy^2) R(theta)^T;
 // Sigma^-1 = R diag(1/sx^2, 1/sy^2) R^T, whose Cholesky factor is l11 = sqrt(A), l21 = B / l11,
 // l22 = sqrt(det)/l11 = 1 / (sx sy l11).
@@ -126,9 +174,8 @@ __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ 
         shape_ok = aac > 0.0f;
     } else {
         const float sx = p0.z, sy = p0.w;
-        // cos and sin in binary64, rounded once to binary32
-        const float c = (float)cos((double)p1.x);
-        const float s = (float)sin((double)p1.x);
+        float c, s;
+        rule_cos_sin((double)p1.x, c, s);
         const float sx2 = sx * sx, sy2 = sy * sy;
         const float ix = 1.0f / sx2, iy = 1.0f / sy2;
         const float cc = c * c, ss = s * s, cs = c * s;

@@ -9,7 +9,8 @@
 //
 // The array is shared by every call on a device and keeps the last call's contents.  Each call
 // writes every partial sum it later reads, so nothing in it has to start at zero; two calls that
-// overlap on the GPU (different streams, no ordering between them) race on it.
+// overlap on the GPU (different streams, no ordering between them) race on it.  The array belongs
+// to this process's copy of the library on each device: other processes have their own.
 #include <mutex>
 
 #include "common.cuh"
@@ -75,18 +76,28 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_l2_loss_total(const float* 
     if (threadIdx.x == 0) *loss = (float)(s[0] / (double)n);
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-cudaError_t scratch_for_current_device(float** out) {
+// Device address of the scratch array for the current device.  Host code cannot use the array's
+// name as a device address; cudaGetSymbolAddress gives the address in the context that is current.
+// Outside stream capture it is looked up on every call, so a reset device (whose library image
+// may load elsewhere) or another current context never leaves a stale address behind; while
+// `stream` is capturing, the address from the last call outside capture on this device is used, and
+// a device with none yet returns cudaErrorStreamCaptureUnsupported.
+cudaError_t scratch_for_current_device(cudaStream_t stream, float** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> guard(g_setup_lock);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         float* p = nullptr;
         e = cudaGetSymbolAddress((void**)&p, g_loss_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -99,13 +110,16 @@ int64_t l2_loss_noalloc_max_elements() { return kNoAllocMaxElems; }
 cudaError_t l2_loss_noalloc(const float* img, const float* target, int64_t n, float* loss, float* grad,
                             cudaStream_t stream) {
     float* scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
+    cudaError_t e = scratch_for_current_device(stream, &scratch);
     if (e != cudaSuccess) return e;
     const int nb = (int)ceil_div(n, kNoAllocBlockElems);
-    launch_pdl(k_l2_loss_blocks, nb, kNoAllocThreads, 0, stream, img, target, n, grad, scratch);
-    launch_pdl(k_l2_loss_total, 1, kNoAllocThreads, 0, stream, scratch, nb, n, loss);
+    // this call's own launch results: an error left behind by unrelated earlier work stays for
+    // its owner to read
+    e = launch_pdl(k_l2_loss_blocks, nb, kNoAllocThreads, 0, stream, img, target, n, grad, scratch);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_l2_loss_total, 1, kNoAllocThreads, 0, stream, scratch, nb, n, loss);
     count_launches(2);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace wipes

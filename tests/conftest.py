@@ -23,3 +23,18 @@ def oracle_lib():
 
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Print the measured ambiguity shares and plain gradient pass rates of the parity tests."""
+    try:
+        from helpers import REPORT
+    except ImportError:
+        return
+    if not REPORT:
+        return
+    tr = terminalreporter
+    tr.section("parity measurements")
+    for kind, test, what, value, limit in REPORT:
+        op = "<" if kind.startswith("ambiguous") else ">="
+        tr.write_line(f"{kind:22s} {value:.6f} ({op} {limit:g})  {test}  {what}")

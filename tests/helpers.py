@@ -1,4 +1,6 @@
 """Shared helpers of the device parity tests (inputs from ``synth``, expectations from ``oracle``)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -10,6 +12,28 @@ GRAD_RTOL = 1e-3  # gradients: |g - g*| <= 1e-3 max(|g*|, 1e-3 max_col |g*|) + S
 # transmittance in front of a layer of opacity a is recovered by dividing by 1 - a, so an alpha
 # error of ~1e-6 becomes ~1e-6 / (1 - a) <= 1e-4 relative.
 SUM_RTOL = {2: 2e-5, 3: 2e-4}
+# Gradient entries must pass the plain check |g - g*| <= 1e-3 max(|g*|, floor), without the
+# summation-scale term, in at least this share of every column; the rest are counted and reported.
+PLAIN_PASS = 0.999
+# Largest share of pixels whose threshold decisions (alpha_min skip, T_min stop) lie within the
+# kernels' error bound of their threshold (the oracle's ambiguity bits); such pixels are excluded
+# from the forward check and carry no upstream gradient in the backward check.
+AMB_SHARE = 1e-3
+
+# (kind, test, detail, value, limit) rows printed in the terminal summary (tests/conftest.py)
+REPORT = []
+
+
+def _label():
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("::", 1)[-1]
+
+
+def check_amb_share(amb, what="image", limit=AMB_SHARE):
+    """Assert and report the share of ambiguous pixels."""
+    share = float(np.mean(amb)) if np.size(amb) else 0.0
+    REPORT.append(("ambiguous share", _label(), what, share, limit))
+    assert share < limit, (what, share, limit)
+    return share
 
 
 def torch_cuda():
@@ -36,10 +60,20 @@ def grad_close(g, ref, gabs=None, dims=2, rtol=GRAD_RTOL, floor_frac=1e-3, cols=
     if cols is not None:
         g, ref, gabs = g[:, cols], ref[:, cols], gabs[:, cols]
     floor = floor_frac * np.abs(ref).max(axis=0, keepdims=True)
-    tol = rtol * np.maximum(np.abs(ref), floor) + SUM_RTOL[dims] * gabs
-    ratio = np.abs(g - ref) / np.maximum(tol, 1e-30)
+    plain = rtol * np.maximum(np.abs(ref), floor)
+    err = np.abs(g - ref)
+    tol = plain + SUM_RTOL[dims] * gabs
+    ratio = err / np.maximum(tol, 1e-30)
     idx = np.unravel_index(np.argmax(ratio), ratio.shape)
-    return bool(np.all(ratio <= 1.0)), float(ratio.max()), idx
+    # entries that pass without the summation-scale term, per column
+    rate = (err <= plain).mean(axis=0) if g.shape[0] else np.ones(g.shape[1])
+    worst_col = int(np.argmin(rate))
+    n_sum_only = int((err > plain).sum())
+    col = cols[worst_col] if cols is not None else worst_col
+    REPORT.append(("plain 1e-3 pass rate", _label(), f"min over columns (col {col}; {n_sum_only} of {err.size} "
+                   f"entries need the summation term)", float(rate.min()), PLAIN_PASS))
+    ok = bool(np.all(ratio <= 1.0)) and bool(rate.min() >= PLAIN_PASS)
+    return ok, float(ratio.max()), (idx, "plain pass rate", float(rate.min()), "column", col)
 
 
 def sample_pixels(H, W, n, seed):

@@ -688,3 +688,105 @@ def test_deform6d_grad_matches_central_differences():
 
     fd = _central_fd(L, p, range(4), range(30), floor=[1.0] * 20 + [0.05] * 10)
     np.testing.assert_allclose(an[:, :30], fd, rtol=1e-6, atol=1e-8)
+
+
+def _f32_fma(a, b, c):
+    """binary32 fused multiply-add: the product of two binary32 values is exact in binary64, so
+    one rounding of the binary64 sum to binary32 emulates it (up to a double rounding that is far
+    below the bounds checked here)."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def _decision_pairs(seed, fmode):
+    """(primitive, pixel) pairs inside the cutoff of a dense 3D view, with the oracle's decision values."""
+    H, W = 96, 96
+    p = synth.scene3d(20000, seed)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    opts = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, float(fmode)], np.float32)
+    if fmode:
+        p[:, 10:13] *= 0.02  # the literal map scales f by about fx / tz
+    rec, _, valid = oracle.footprints(3, p, H, W, cam)
+    rng = np.random.default_rng(seed)
+    prims = np.nonzero(valid)[0]
+    pairs = []
+    for i in rng.choice(prims, 3000):
+        u = int(rng.integers(0, W)); v = int(rng.integers(0, H))
+        # a pixel near the centre, so that most pairs fall inside the cutoff
+        u = int(np.clip(round(rec[i, 0] - 0.5 + rng.normal(0, rec[i, 5] / 3.0)), 0, W - 1))
+        v = int(np.clip(round(rec[i, 1] - 0.5 + rng.normal(0, rec[i, 6] / 3.0)), 0, H - 1))
+        pairs.append((i, u, v))
+    pairs = np.array(pairs, np.int32)
+    r9, out = oracle.alpha_decisions(p, cam, H, W, pairs, opts)
+    k2 = np.float32(9.0)
+    # keep the pairs inside the binary32 cutoff (the decision is only taken there)
+    m = r9[pairs[:, 0]]
+    dx = (pairs[:, 1].astype(np.float32) + np.float32(0.5)) - m[:, 0]
+    dy = (pairs[:, 2].astype(np.float32) + np.float32(0.5)) - m[:, 1]
+    a = _f32_fma(m[:, 2], dx, m[:, 3] * dy)
+    b = m[:, 4] * dy
+    q = _f32_fma(a, a, b * b)
+    inside = q <= k2
+    return pairs[inside], m[inside], out[inside], dx[inside], dy[inside], q[inside]
+
+
+@pytest.mark.parametrize("fmode", [0, 1])
+def test_threshold_decision_alpha_bound_covers_binary32_evaluation(fmode):
+    """Eq. 3's threshold decisions (alpha_min skip, alpha_max clamp, T_min stop) are taken from the
+    binary32 projected record; the oracle's per-pair bound must cover the error of evaluating alpha
+    in binary32 along the kernels' sequence of operations.  Emulated here in float32 with
+    correctly rounded exp2 and cos (their approximate hardware forms are covered by the bound's
+    documented instruction errors on top)."""
+    pairs, m, out, dx, dy, q = _decision_pairs(301, fmode)
+    assert len(pairs) > 1500
+    f32 = np.float32
+    e = q * f32(-0.7213475204444817)
+    G = np.exp2(e.astype(np.float64)).astype(f32)
+    t = _f32_fma(m[:, 5], dx, _f32_fma(m[:, 6], dy, m[:, 7]))
+    r = (t + f32(12582912.0)) - f32(12582912.0)
+    ang = (t - r) * f32(6.283185307179586)
+    c = np.cos(ang.astype(np.float64)).astype(f32)
+    M = _f32_fma(np.full_like(c, 0.5), c, np.full_like(c, 0.5))
+    raw = m[:, 8] * (M * G)
+    err = np.abs(raw.astype(np.float64) - out[:, 0])
+    # the bound carries a safety factor of 1.5 over its first-order terms; the emulation must fit
+    # within the terms themselves
+    assert np.all(err <= out[:, 1] / 1.5), (err.max(), out[np.argmax(err / out[:, 1]), :])
+    # and the bound is a few binary32 roundings of the pair's scale, not a blanket margin
+    assert np.median(out[:, 1]) < 1e-6
+
+
+@pytest.mark.parametrize("fmode", [0, 1])
+def test_threshold_decision_alpha_matches_binary64_projection(fmode):
+    """The record the decisions read (centre, Cholesky factor, frequency under the chosen map,
+    phase in cycles, opacity) is the binary32 rounding of the projection of Sec. 3.1 / Sec. 4.1:
+    its alpha agrees with the binary64 projection's alpha to the rounding of the record.  A record
+    built from a dropped phase, the other frequency map or a wrong opacity fails this."""
+    pairs, m, out, dx, dy, q = _decision_pairs(302, fmode)
+    diff = np.abs(out[:, 0] - out[:, 2])
+    assert np.max(diff) < 2e-4, np.max(diff)
+    assert np.median(diff) < 2e-6
+
+
+def test_footprint_rule_cos_sin_is_the_rounded_cosine_and_sine():
+    """The 2D footprint rule's rotation (Sec. 3.1, Sigma = R S S^T R^T) takes cos and sin from a
+    fixed sequence of binary64 operations (no library transcendental); its binary32 results are
+    the correctly rounded cosine and sine (numpy's binary64 ones, rounded) over many quadrants,
+    and the quadrant identities hold bit for bit."""
+    th = np.concatenate([np.linspace(0.0, math.pi, 100001), np.linspace(-60.0, 60.0, 100001),
+                         np.random.default_rng(5).uniform(-1e5, 1e5, 20000)])
+    r = oracle.rule_cos_sin(th)
+    c32, s32 = np.cos(th).astype(np.float32), np.sin(th).astype(np.float32)
+    small = np.abs(th) <= 60.0
+    # exact agreement away from binary32 rounding ties (none occur on these grids)
+    assert np.array_equal(r[small, 0], c32[small]) and np.array_equal(r[small, 1], s32[small])
+    # far out the reduction keeps ~1e-11 absolute accuracy: within one binary32 ulp
+    ulp = np.spacing(np.float32(1.0))
+    assert np.abs(r[:, 0] - c32).max() <= ulp and np.abs(r[:, 1] - s32).max() <= ulp
+    # special angles
+    sp = oracle.rule_cos_sin(np.array([0.0, math.pi / 2, math.pi, -math.pi / 2]))
+    np.testing.assert_array_equal(sp[0], [1.0, 0.0])
+    assert sp[1, 1] == 1.0 and abs(sp[1, 0]) < 1e-7
+    assert sp[2, 0] == -1.0 and abs(sp[2, 1]) < 1e-7
+    assert sp[3, 1] == -1.0
+    # non-finite or absurd angles make the primitive invalid
+    assert np.isnan(oracle.rule_cos_sin(np.array([np.inf, np.nan, 1e16]))).all()

@@ -76,6 +76,24 @@ def test_backward_matches_oracle(N, H, W, scale, seed):
     assert np.all(grad.cpu().numpy()[:, 11:] == 0)
 
 
+def test_rotation_angles_across_quadrants_bit_exact():
+    """Rotation angles far outside [0, pi) (negative, many turns): the footprint rule's cos and sin
+    come from the same binary64 operation sequence on both sides, so the lists stay bit-exact and
+    the image matches the oracle's binary64 rotation."""
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 96, 128
+    p = synth.scene2d(1500, H, W, 21, (0.5, 24.0))
+    p[:, 4] = np.random.default_rng(22).uniform(-200.0, 200.0, p.shape[0]).astype(np.float32)
+    _, st, img = _gpu_forward(w, torch, p, H, W)
+    tiles, prims, _ = st.lists()
+    ot, op = oracle.tile_lists(2, p, H, W)
+    assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+    assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+    ref = oracle.render2d(p, H, W, truncated=True)
+    assert np.abs(img.cpu().numpy().astype(np.float64) - ref).max() <= FWD_ATOL
+
+
 def test_autograd_function_matches_direct_calls():
     torch = torch_cuda()
     w = lib_ready()

@@ -5,15 +5,12 @@ import pytest
 
 import oracle
 import synth
-from helpers import FWD_ATOL, grad_close, lib_ready, sample_pixels, torch_cuda
+from helpers import FWD_ATOL, check_amb_share, grad_close, lib_ready, sample_pixels, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
 DEFAULT = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0], np.float32)
 STRICT = np.array([3.0, 0.0, 0.99, 0.0, 0.3, 0.1, 0.2, 0.3], np.float32)  # no alpha floor, no T floor
-# Largest share of pixels whose threshold decisions lie within the kernels' error margin (excluded
-# from the comparison and reported); binary32 phase rounding puts alpha errors near 1e-6.
-AMB_SHARE = 1e-2
 
 
 LITERAL = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 1.0], np.float32)  # f' = J W f
@@ -72,7 +69,7 @@ def test_forward_matches_oracle(N, H, W, seed, kw, mode):
     amb = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
     if mode == "strict":
         assert not amb.any()
-    assert amb.mean() < AMB_SHARE
+    check_amb_share(amb, f"{mode}: alpha_min / T_min bits")
     err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
     err[amb] = 0
     assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
@@ -93,7 +90,7 @@ def test_backward_matches_oracle(N, H, W, seed, kw, mode):
     params, st, _ = _gpu(w, torch, p, cam, H, W, o)
     _, _, _, amb_bits = oracle.render3d(p, cam, H, W, o)
     amb = amb_bits != 0
-    assert amb.mean() < AMB_SHARE
+    check_amb_share(amb, f"{mode}: any bit")
     g = synth.upstream_grad(H, W, seed + 5)
     g[amb] = 0.0  # threshold decisions that floating point may take either way carry no gradient
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
@@ -115,7 +112,7 @@ def test_literal_frequency_projection_matches_oracle(N, H, W, seed):
     params, st, img = _gpu(w, torch, p, cam, H, W, LITERAL)
     C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, LITERAL)
     amb_img = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
-    assert amb_img.mean() < AMB_SHARE
+    check_amb_share(amb_img, "alpha_min / T_min bits")
     err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
     err[amb_img] = 0
     assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
@@ -144,7 +141,7 @@ def test_spherical_harmonic_colour_matches_oracle(N, H, W, seed, degree):
     params, st, img = _gpu(w, torch, p, cam, H, W, o)
     C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, o)
     amb_img = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
-    assert amb_img.mean() < AMB_SHARE
+    check_amb_share(amb_img, "alpha_min / T_min bits")
     err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
     err[amb_img] = 0
     assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
@@ -179,7 +176,7 @@ def test_autograd_function_and_culling():
     assert np.all(g[:2] == 0)
     ref, gabs = oracle.grad3d(p, cam, H, W, synth.upstream_grad(H, W, 43), with_abs=True)
     C, T, nc, amb = oracle.render3d(p, cam, H, W)
-    assert (amb != 0).mean() < AMB_SHARE
+    check_amb_share(amb != 0, "any bit")
     if not amb.any():
         ok, worst, idx = grad_close(g, ref, gabs, dims=3, cols=list(range(18)))
         assert ok, (worst, idx)
@@ -254,6 +251,7 @@ def test_full_size_800x800_300k_sampled():
         C, T, nc, amb = oracle.render3d(p, cam, c.H, c.W, DEFAULT, pixels=pix)
         got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
         err = np.abs(got - C).max(axis=1)
+        check_amb_share((amb & 3) != 0, "sampled pixels, alpha_min / T_min bits")
         err[(amb & 3) != 0] = 0
         assert err.max() <= FWD_ATOL
 
@@ -283,6 +281,7 @@ def test_6d_render_and_gradient_chain():
     p3 = oracle.deform6d(p6, t).astype(np.float32)
     C, T, nc, amb = oracle.render3d(p3, cam, H, W)
     err = np.abs(img.detach().cpu().numpy() - C).max(axis=2)
+    check_amb_share(amb != 0, "any bit")
     err[(amb & 3) != 0] = 0
     assert err.max() <= FWD_ATOL
     g = synth.upstream_grad(H, W, 74)
@@ -292,4 +291,109 @@ def test_6d_render_and_gradient_chain():
     ref = oracle.deform6d_grad(p6, t, g3)
     gabs = np.abs(oracle.deform6d_grad(p6, t, gabs3))  # the time model is linear in each term's sign
     ok, worst, idx = grad_close(params6.grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(30)))
+    assert ok, (worst, idx)
+
+
+# The densest 96x96 windows of the two full-density workloads: the centre of the 300k-primitive
+# view holds about 9,000 tile-list entries per tile and its pixels composite about 170 layers; a
+# T_min stop there is decided after that many layers, whose binary32 phase rounding bounds the
+# kernels' transmittance to a few 1e-4 relative, so 0.1-0.3 % of these pixels have a stop decision
+# inside that bound (0.04 % over the whole 800x800 view).
+CROP_AMB_SHARE = 4e-3
+
+
+def _crop(cam, H, W):
+    """The same camera, its image cut to the centre H x W window (principal point moved)."""
+    c = cam.copy()
+    c[14] = W / 2
+    c[15] = H / 2
+    return c
+
+
+def _chunk_report(st, label):
+    from helpers import REPORT
+
+    _, _, ranges = st.lists()
+    r = ranges.cpu().numpy().astype(np.int64)
+    lengths = r[:, 1] - r[:, 0]
+    _, last = st.pixel_state()
+    last = last.cpu().numpy().astype(np.int64)
+    hist = np.histogram(last, bins=[0, 1, 257, 513, 1025, 2049, 1 << 30])[0]
+    REPORT.append(("chunk path", label, f"list lengths {lengths.min()}..{lengths.max()}; last index per pixel "
+                   f"[0,1,257,513,1025,2049,inf) histogram {hist.tolist()}", float(last.max()), 512))
+    return lengths, last
+
+
+def test_chunked_backward_at_full_scene_density():
+    """The 3D backward cuts each tile list into chunks of 256 entries and starts every chunk from a
+    state that the forward recorded.  At the 300,000-primitive scene's density (its cameras and
+    focal length, the image cut to the centre 96x96), the lists run to thousands of entries and
+    pixels composite past the second boundary; forward, last-contributor states and the gradient of
+    every record column are compared with the oracle."""
+    torch = torch_cuda()
+    w = lib_ready()
+    p, cams = synth.cfg2_inputs(n_cams=2)
+    H = W = 96
+    for k, full in enumerate(cams):
+        cam = _crop(full, H, W)
+        params, st, img = _gpu(w, torch, p, cam, H, W, DEFAULT)
+        lengths, last = _chunk_report(st, f"5D crop, camera {k}")
+        assert lengths.max() > 2 * 256 and last.max() > 512
+        C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, DEFAULT)
+        amb = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
+        check_amb_share(amb, f"5D crop camera {k}: alpha_min / T_min bits", CROP_AMB_SHARE)
+        err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
+        err[amb] = 0
+        assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+        Tg, _ = st.pixel_state()
+        terr = np.abs(Tg.cpu().numpy() - T)
+        terr[amb] = 0
+        assert terr.max() <= 1e-5
+        g = synth.upstream_grad(H, W, 81 + k)
+        g[amb_bits != 0] = 0.0
+        grad = w.backward(st, params, torch.from_numpy(g).cuda())
+        torch.cuda.synchronize()
+        ref, gabs = oracle.grad3d(p, cam, H, W, g, DEFAULT, with_abs=True)
+        ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
+        assert ok, (worst, idx)
+
+
+def test_chunked_backward_6d_sample_at_full_scene_density():
+    """One (view, time) sample of the 200,000-primitive dynamic scene (its cameras and focal
+    length, the image cut to the centre 96x96): render, backward through the chunks and chain to
+    the time rates with the library's time-model backward, against the oracle.  Both sides render
+    the oracle's deformed records (the time model's own forward is compared in
+    test_deform6d_matches_oracle), so that the cutoff decisions see the same binary32 records."""
+    torch = torch_cuda()
+    w = lib_ready()
+    import ctypes
+
+    from paper_2508_12615_gb300 import _abi
+
+    p6, cams, ts = synth.cfg3_inputs(n_cams=1)
+    H = W = 96
+    cam = _crop(cams[0], H, W)
+    t = float(ts[150])
+    p3 = oracle.deform6d(p6, t).astype(np.float32)
+    params3, st, img = _gpu(w, torch, p3, cam, H, W, DEFAULT)
+    lengths, last = _chunk_report(st, "6D crop")
+    assert lengths.max() > 2 * 256 and last.max() > 512
+    C, T, nc, amb = oracle.render3d(p3, cam, H, W)
+    check_amb_share((amb & 3) != 0, "6D crop: alpha_min / T_min bits", CROP_AMB_SHARE)
+    err = np.abs(img.cpu().numpy() - C).max(axis=2)
+    err[(amb & 3) != 0] = 0
+    assert err.max() <= FWD_ATOL
+    g = synth.upstream_grad(H, W, 91)
+    g[amb != 0] = 0
+    g3 = w.backward(st, params3, torch.from_numpy(g).cuda())
+    params6 = torch.from_numpy(p6).cuda()
+    g6 = torch.empty_like(params6)
+    _abi.call("wipes_deform6d_backward", ctypes.c_void_p(params6.data_ptr()), p6.shape[0], ctypes.c_float(t),
+              ctypes.c_void_p(g3.data_ptr()), ctypes.c_void_p(g6.data_ptr()), 0,
+              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    r3, gabs3 = oracle.grad3d(p3, cam, H, W, g, with_abs=True)
+    ref = oracle.deform6d_grad(p6, t, r3)
+    gabs = np.abs(oracle.deform6d_grad(p6, t, gabs3))
+    ok, worst, idx = grad_close(g6.cpu().numpy(), ref, gabs, dims=3, cols=list(range(30)))
     assert ok, (worst, idx)

@@ -50,3 +50,30 @@ def test_noalloc_loss_rejects_sizes_beyond_its_scratch():
     st = lib.wipes_l2_loss_noalloc(_p(x), _p(x), 268435456 + 1, _p(x), _p(x), None)
     assert st == 1 and b"268,435,456" not in lib.wipes_last_error() and b"268435456" in lib.wipes_last_error()
     assert lib.wipes_l2_loss_noalloc(_p(x), _p(x), 0, _p(x), _p(x), None) == 1
+
+
+def test_noalloc_loss_leaves_device_memory_untouched():
+    """After a first call (which may load the library's kernels and its scratch array), further
+    calls change neither the device's free memory nor torch's reserved pool."""
+    torch = torch_cuda()
+    lib_ready()
+    from paper_2508_12615_gb300 import _abi
+
+    lib = _abi.lib()
+    n = 1 << 20
+    img = torch.rand(n, device="cuda")
+    tgt = torch.rand(n, device="cuda")
+    loss = torch.empty((), device="cuda")
+    grad = torch.empty_like(img)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _abi.check(lib.wipes_l2_loss_noalloc(_p(img), _p(tgt), n, _p(loss), _p(grad), stream), "warm-up")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        _abi.check(lib.wipes_l2_loss_noalloc(_p(img), _p(tgt), n, _p(loss), _p(grad), stream), "l2_loss_noalloc")
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    ref = float(((img.double() - tgt.double()) ** 2).mean())
+    assert abs(float(loss) - ref) <= 1e-6 * ref
