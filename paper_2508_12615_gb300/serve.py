@@ -222,6 +222,53 @@ class Server:
         torch.cuda.synchronize(self.dev)
         return res
 
+    # -- plain path over the view cache ----------------------------------------------------------
+    def run_plain_cached(self, requests: np.ndarray, keep_outputs: bool = False) -> RunResult:
+        """One request at a time, in arrival order, from the same view cache and HBM budget as the
+        batched path: a view is prepared on first use and kept; each request is rendered by its own
+        one-frame launch (wipes_blend_batch with one job) on one stream.  Against run_batched this
+        leaves batching as the only difference."""
+        R = len(requests)
+        res = RunResult(requests[:, 0].copy(), np.full(R, np.nan), np.zeros(R))
+        stream = self.streams[0]
+        start = torch.cuda.Event(enable_timing=True)
+        start.record()
+        torch.cuda.synchronize(self.dev)
+        t0 = time.perf_counter()
+        events = []
+        with torch.cuda.stream(stream):
+            for i in range(R):
+                while time.perf_counter() - t0 < requests[i, 0]:
+                    pass
+                req = requests[i]
+                H, W = SIZES[int(req[2])]
+                key = self._key(req)
+                out = torch.empty(H, W, 3, device=self.dev)
+                v = self.views.get(key) if self.cache_views else None
+                if v is None:
+                    st = self._prepare_within_budget(req, key, stream, H * W * 12)
+                    if st is None:
+                        raise RuntimeError("a single request does not fit the HBM budget")
+                    res.prepared += 1
+                    v = _View(st, 0)
+                    if self.cache_views:
+                        self.views[key] = v
+                else:
+                    self.views.move_to_end(key)
+                _abi.call("wipes_blend_batch", self.ctx.handle, (ctypes.c_void_p * 1)(v.state.handle.value),
+                          (ctypes.c_void_p * 1)(out.data_ptr()), 1, ctypes.c_void_p(stream.cuda_stream))
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(stream)
+                events.append(ev)
+                res.pixels[i] = H * W
+                res.peak_bytes = max(res.peak_bytes, self.resident_bytes + self._reserved() + H * W * 12)
+                if keep_outputs:
+                    res.outputs[i] = out
+        torch.cuda.synchronize(self.dev)
+        res.complete[:] = [start.elapsed_time(e) / 1e3 for e in events]
+        res.batches = R
+        return res
+
     # -- plain path -------------------------------------------------------------------------------
     def run_plain(self, requests: np.ndarray, keep_outputs: bool = False) -> RunResult:
         """One request at a time, in arrival order, with the one-frame calls (no batching, no view

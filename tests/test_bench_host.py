@@ -61,3 +61,49 @@ def test_sample_is_resized_from_its_own_rate(monkeypatch):
     assert per_step >= 0.9 * true_step
     assert wall <= 3 * budget
     assert f"of {H} rows" in desc and f"of {n} primitives" in desc
+
+
+class FakeOracle3D:
+    """A 3D oracle whose calls cost a fixed set-up plus a time per pixel of the band."""
+
+    SETUP_S, PX_S = 0.05, 2e-4
+
+    def __init__(self):
+        self.calls = []
+
+    def build(self):
+        pass
+
+    def deform6d(self, p, t):
+        return np.asarray(p, np.float64)[:, :20]
+
+    def render3d(self, p, cam, H, W, pixels=None):
+        self.calls.append(("render", len(pixels)))
+        time.sleep(self.SETUP_S + self.PX_S * len(pixels))
+
+    def grad3d(self, p, cam, H, W, g):
+        n = int(np.count_nonzero(np.any(g != 0, axis=2)))
+        self.calls.append(("grad", n))
+        time.sleep(self.SETUP_S + self.PX_S * n)
+
+
+def test_3d_sample_separates_the_fixed_cost_from_the_rows(monkeypatch):
+    """The 3D baseline times bands of rows of one frame: the cost per call that does not depend on
+    the band is counted once per pass, the rest scaled to every row and every sample of a step."""
+    import types
+
+    fake = FakeOracle3D()
+    monkeypatch.setitem(sys.modules, "oracle", fake)
+    H, W, batch, budget = 64, 40, 4, 1.5
+    wl = types.SimpleNamespace(p=np.zeros((10, 32), np.float32), cams=[np.zeros(17, np.float32)],
+                               samples=[(0, 0.25)], H=H, W=W, batch=batch)
+    t0 = time.perf_counter()
+    per_step, desc = bench.oracle_3d_sample(wl, budget)
+    wall = time.perf_counter() - t0
+    true_step = batch * (2 * fake.SETUP_S + 2 * fake.PX_S * H * W)
+    assert 0.8 * true_step <= per_step <= 1.5 * true_step, (per_step, true_step)
+    # three band heights, each pass on every pixel of the band
+    grads = [k for kind, k in fake.calls if kind == "grad"]
+    assert [k // W for k in grads][:2] == [1, 4] and grads[2] > grads[1]
+    assert wall <= 3 * budget
+    assert f"of {H} rows" in desc and "4 full frames per step" in desc

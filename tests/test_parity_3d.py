@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import FWD_ATOL, check_amb_share, grad_close, lib_ready, sample_pixels, torch_cuda
+from helpers import FWD_ATOL, check_amb_share, check_pooled_plain_rate, grad_close, lib_ready, sample_pixels, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -96,7 +96,7 @@ def test_backward_matches_oracle(N, H, W, seed, kw, mode):
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
     ref, gabs = oracle.grad3d(p, cam, H, W, g, o, with_abs=True)
-    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)), pool="3d record")
     assert ok, (worst, idx)
 
 
@@ -124,7 +124,7 @@ def test_literal_frequency_projection_matches_oracle(N, H, W, seed):
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
     ref, gabs = oracle.grad3d(p, cam, H, W, g, LITERAL, with_abs=True)
-    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)), pool="3d record")
     assert ok, (worst, idx)
 
 
@@ -152,7 +152,7 @@ def test_spherical_harmonic_colour_matches_oracle(N, H, W, seed, degree):
     assert grad.shape == (N, synth.P3D_SH)
     ref, gabs = oracle.grad3d(p, cam, H, W, g, o, with_abs=True)
     cols = list(range(18)) + list(range(20, 20 + 3 * ((degree + 1) ** 2 - 1)))
-    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=cols)
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=cols, pool="3d record")
     assert ok, (worst, idx)
     unused = [c for c in range(synth.P3D_SH) if c not in cols]
     assert np.all(grad.cpu().numpy()[:, unused] == 0)
@@ -178,7 +178,7 @@ def test_autograd_function_and_culling():
     C, T, nc, amb = oracle.render3d(p, cam, H, W)
     check_amb_share(amb != 0, "any bit")
     if not amb.any():
-        ok, worst, idx = grad_close(g, ref, gabs, dims=3, cols=list(range(18)))
+        ok, worst, idx = grad_close(g, ref, gabs, dims=3, cols=list(range(18)), pool="3d record")
         assert ok, (worst, idx)
 
 
@@ -290,7 +290,7 @@ def test_6d_render_and_gradient_chain():
     g3, gabs3 = oracle.grad3d(p3, cam, H, W, g, with_abs=True)
     ref = oracle.deform6d_grad(p6, t, g3)
     gabs = np.abs(oracle.deform6d_grad(p6, t, gabs3))  # the time model is linear in each term's sign
-    ok, worst, idx = grad_close(params6.grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(30)))
+    ok, worst, idx = grad_close(params6.grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(30)), pool="6d record")
     assert ok, (worst, idx)
 
 
@@ -395,5 +395,18 @@ def test_chunked_backward_6d_sample_at_full_scene_density():
     r3, gabs3 = oracle.grad3d(p3, cam, H, W, g, with_abs=True)
     ref = oracle.deform6d_grad(p6, t, r3)
     gabs = np.abs(oracle.deform6d_grad(p6, t, gabs3))
-    ok, worst, idx = grad_close(g6.cpu().numpy(), ref, gabs, dims=3, cols=list(range(30)))
+    ok, worst, idx = grad_close(g6.cpu().numpy(), ref, gabs, dims=3, cols=list(range(30)), pool="6d record")
     assert ok, (worst, idx)
+
+
+# The plain 1e-3 check pooled over the cases above, per column.  Every entry that needs the
+# summation term is a sum whose pixel terms cancel (the sum of |terms| is 20-40,000 times the
+# result): there the binary32 alpha of each term (phase rounding, amplified by 1 / (1 - alpha) in
+# the recovered transmittance) leaves an error of 1e-6 to 1e-4 of the sum of |terms|.  A column of
+# a few hundred entries cannot show a share of 1e-3, so the share is taken over all the cases.
+def test_plain_pass_rate_pooled_over_3d_cases():
+    check_pooled_plain_rate("3d record")
+
+
+def test_plain_pass_rate_pooled_over_6d_cases():
+    check_pooled_plain_rate("6d record")
