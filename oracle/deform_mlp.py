@@ -14,8 +14,9 @@ The deformed 3D record: mu + dx, q + dq, s * exp(dlog s), f + df; phase, opacity
 
 Precision.  The device path runs the products in bfloat16 with fp32 accumulation.  ``bf16=True``
 reproduces its roundings: every matrix-product operand (encoding, weights, hidden activations,
-upstream gradients) and the hidden layers' biases are rounded to bfloat16 where the device rounds
-them, and everything else is binary64.  ``bf16=False`` is the exact binary64 network, against which central differences pin
+upstream gradients) is rounded to bfloat16 where the device rounds it; biases, the outputs and the
+encoding's gradient (the skip layer's and layer 0's products summed unrounded) are not rounded,
+and everything else is binary64.  ``bf16=False`` is the exact binary64 network, against which central differences pin
 the gradient.  theta is the packed float32 parameter vector: for each layer W (out x in,
 row-major) then b (out).
 """
@@ -93,10 +94,10 @@ def forward(mu, t, theta, bf16_ops=True):
         W, b = layers[l]
         if l == SKIP:
             x = np.concatenate([g, hs[4]], axis=1)
-        z = x @ R(W).T + R(b)
+        z = x @ R(W).T + b
         # a pre-activation this close to 0 (relative to the magnitude of its terms) can take the
         # ReLU either way under a different summation order
-        amb |= (np.abs(z) <= AMB_REL * (np.abs(x) @ np.abs(R(W)).T + np.abs(R(b)))).any(axis=1)
+        amb |= (np.abs(z) <= AMB_REL * (np.abs(x) @ np.abs(R(W)).T + np.abs(b))).any(axis=1)
         h = R(np.maximum(z, 0.0))
         hs.append(h)
         x = h
@@ -164,14 +165,14 @@ def backward(mu, cache, gd, with_abs=False):
         absg[l] = (np.abs(dz).T @ np.abs(x), np.abs(dz).sum(0))
         if with_abs:
             maxg[l] = (_max_row_term(dh, x), np.abs(dh).max(0))
-        dx = R(dz @ R(W))
+        dx = dz @ R(W)
         if l == SKIP:
             dg += dx[:, :IN_PAD]
-            dh = dx[:, IN_PAD:]
+            dh = R(dx[:, IN_PAD:])
         elif l == 0:
             dg += dx
         else:
-            dh = dx
+            dh = R(dx)
     # gamma(x): d/dx of (x, sin(2^k x), cos(2^k x))
     m = np.asarray(mu, np.float32).astype(np.float64)
     dmu = dg[:, 0:3].copy()

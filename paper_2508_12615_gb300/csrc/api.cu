@@ -144,8 +144,6 @@ struct wipes_ctx {
     unsigned long long* d_counters = nullptr;  // pair counters
     unsigned int* d_batch_counters = nullptr;  // work counters of in-flight batch launches (a ring)
     unsigned int batch_slot = 0;
-    MlpLt* mlp = nullptr;  // cuBLASLt state of the deformation network, created on first use
-    std::mutex mlp_mu;
     // stage timing
     bool timing = false;
     struct Bracket {
@@ -247,10 +245,13 @@ wipes_status check_image(int H, int W) {
 // The device error word as last read back into h_total[1]: a set bit is reported once and cleared.
 wipes_status take_device_error(wipes_ctx* ctx, cudaStream_t s) {
     if (ctx->h_total[1] == 0) return WIPES_OK;
+    const unsigned long long bits = ctx->h_total[1];
     ctx->h_total[1] = 0;
     WIPES_CUDA(cudaMemsetAsync(ctx->d_error, 0, sizeof(unsigned long long), s));
-    return fail(WIPES_ERR_TIMEOUT, "a bounded device wait ran out (radix sort look-back); results of the "
-                                   "calls since the last check are undefined");
+    std::string where = (bits & 1u) ? "radix sort look-back" : "";
+    if (bits & 2u) where += std::string(where.empty() ? "" : ", ") + "deformation network pipeline";
+    return fail(WIPES_ERR_TIMEOUT, "a bounded device wait ran out (" + where + "); results of the calls since the "
+                                   "last check are undefined");
 }
 
 // Scan the per-primitive tile counts (in `perm` order when given), read the instance total back,
@@ -441,7 +442,6 @@ wipes_status wipes_destroy(wipes_ctx* ctx) {
     cudaFree(ctx->d_loss_partials);
     cudaFree(ctx->d_counters);
     cudaFree(ctx->d_error);
-    mlp_lt_destroy(ctx->mlp);
     cudaFree(ctx->d_batch_counters);
     if (ctx->mem.pool) cudaMemPoolDestroy(ctx->mem.pool);
     delete ctx;
@@ -858,22 +858,14 @@ wipes_status wipes_deform_mlp(wipes_ctx* ctx, wipes_state* st, const float* para
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     AllocStream alloc_stream(s);
-    {
-        std::lock_guard<std::mutex> lk(ctx->mlp_mu);
-        if (!ctx->mlp) {
-            std::string err;
-            ctx->mlp = mlp_lt_create(&err);
-            if (!ctx->mlp) return fail(WIPES_ERR_CUDA, err);
-        }
-    }
     const MlpSizes z = mlp_sizes(std::max<int64_t>(N, 1));
     WIPES_TRY(ensure(st->mlp_act, z.act));
     WIPES_TRY(ensure(st->mlp_d, z.out));
     WIPES_TRY(ensure(st->mlp_theta16, z.theta16));
     st->mlp_N = -1;
     StageTimer tm(ctx, WIPES_STAGE_MLP_FWD, s);
-    const std::string e = mlp_forward(*ctx->mlp, params3, N, t, theta, st->mlp_theta16.p, st->mlp_act.p,
-                                      st->mlp_d.as<float>(), params_out, s);
+    const std::string e = mlp_forward(params3, N, t, theta, st->mlp_theta16.p, st->mlp_act.p, st->mlp_d.as<float>(),
+                                      params_out, ctx->d_error, s);
     if (!e.empty()) return fail(WIPES_ERR_CUDA, e);
     WIPES_CUDA(cudaGetLastError());
     st->mlp_N = N;
@@ -896,8 +888,8 @@ wipes_status wipes_deform_mlp_backward(wipes_ctx* ctx, wipes_state* st, const fl
         return WIPES_OK;
     }
     StageTimer tm(ctx, WIPES_STAGE_MLP_BWD, s);
-    const std::string e = mlp_backward(*ctx->mlp, params3, N, st->mlp_theta16.p, st->mlp_act.p, st->mlp_d.as<float>(),
-                                       st->mlp_scratch.p, dL_dout, dL_dtheta, dL_dparams3, accumulate, s);
+    const std::string e = mlp_backward(params3, N, st->mlp_theta16.p, st->mlp_act.p, st->mlp_d.as<float>(),
+                                       st->mlp_scratch.p, dL_dout, dL_dtheta, dL_dparams3, accumulate, ctx->d_error, s);
     if (!e.empty()) return fail(WIPES_ERR_CUDA, e);
     WIPES_CUDA(cudaGetLastError());
     return WIPES_OK;

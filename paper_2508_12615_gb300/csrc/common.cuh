@@ -544,21 +544,19 @@ int64_t l2_loss_noalloc_max_elements();
 cudaError_t l2_loss_noalloc(const float* img, const float* target, int64_t n, float* loss, float* grad,
                             cudaStream_t stream);
 
-// mlp.cu: the 6D deformation network (cuBLASLt products, bfloat16 activations)
-struct MlpLt;  // cuBLASLt handle, workspace and cached algorithms of a context
+// mlp.cu: the 6D deformation network (tcgen05 kernels, bfloat16 operands, fp32 accumulation)
 struct MlpSizes {
     size_t act, scratch, out, theta16;  // bytes of the state buffers for N primitives
 };
-MlpLt* mlp_lt_create(std::string* err);
-void mlp_lt_destroy(MlpLt* lt);
 int64_t mlp_param_count();
 MlpSizes mlp_sizes(int64_t N);
-// Each returns "" on success, else a description of the failure.
-std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, const float* theta, void* theta16,
-                        void* act, float* d, float* params_out, cudaStream_t stream);
-std::string mlp_backward(MlpLt& lt, const float* params3, int64_t N, const void* theta16, const void* act,
-                         const float* d, void* scratch, const float* g_out, float* g_theta, float* g_params3,
-                         int accumulate, cudaStream_t stream);
+// Each returns "" on success, else a description of the failure.  A bounded device wait that runs
+// out sets bit 1 of *err (the context's device error word).
+std::string mlp_forward(const float* params3, int64_t N, float t, const float* theta, void* theta16, void* act,
+                        float* d, float* params_out, unsigned int* err, cudaStream_t stream);
+std::string mlp_backward(const float* params3, int64_t N, const void* theta16, const void* act, const float* d,
+                         void* scratch, const float* g_out, float* g_theta, float* g_params3, int accumulate,
+                         unsigned int* err, cudaStream_t stream);
 
 // loss.cu
 void launch_l2_loss(const float* img, const float* target, int64_t n, float* loss, float* grad, float* partials,

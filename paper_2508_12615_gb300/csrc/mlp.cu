@@ -9,22 +9,34 @@
 //   deformed record: mu + dx, q + dq, s exp(dlog s), f + df (phase, opacity, colour kept).
 // Parameters theta: packed float32, per layer W (out x in, row-major) then b (out).
 //
-// The products are dense contractions over 200k-row activation matrices: they run on the tensor
-// cores through cuBLASLt (bfloat16 operands, fp32 accumulation, bias + ReLU fused in the epilogue
-// for the hidden layers, whose biases are used in bfloat16 like their weights).  Activations are kept in bfloat16 for the backward pass.  Layouts: every
-// activation matrix is row-major [N, width]; in cuBLASLt's column-major terms that is a
-// [width, N] matrix, so Y = X W^T + b is  Y^T (out x N) = W (out x in, i.e. column-major in x out
-// read transposed) * X^T (in x N).  The skip input lives in one [N, 336] buffer: columns 0..79 the
-// encoding (written by the encoder), columns 80..335 the output h_4 of layer 4.
-#include <cublasLt.h>
+// Every product runs on the 5th-generation tensor cores (tcgen05, bfloat16 operands, fp32
+// accumulation in tensor memory), in three hand-written kernels:
+//   k_mlp_fwd   one 128-row tile at a time: the encoding, the nine layers and the record update.
+//               The activations stay in shared memory between layers (each layer's output is the
+//               next layer's A operand); the weights stream in by bulk copies, one 64-column
+//               K-block at a time, through a ring of stages.  For the backward it writes the ReLU
+//               bit masks and each layer's input, transposed (rows along K), in 128-row tiles.
+//   k_mlp_bwd   one tile at a time: the record update's backward, then dh = dz W through the
+//               layers (W transposed, the masks applied on chip), the bias gradients, and the
+//               encoding's backward to the centre.  It writes each layer's dz, transposed.
+//   k_mlp_wgrad the weight gradients dW_l = dz_l^T x_l: a product over all rows, split into row
+//               chunks (one partial per chunk), then k_mlp_wsum adds the partials in a fixed order.
+// Rounding points: the encoding, weights, hidden activations and upstream gradients are rounded
+// to bfloat16 where they become product operands; biases, accumulators, the network outputs and
+// the encoding's gradient (both products summed in one accumulator) stay fp32.
+// Warp roles in the tile kernels: warp 0 streams operands, warp 1 issues the MMAs (one thread),
+// warps 2-5 run the epilogue (thread = row: warp w reads TMEM lanes 32 (w % 4) ..).  Every wait on
+// an mbarrier is bounded; one that runs out sets bit 1 of the context's error word, every role
+// leaves its loop, in-flight copies and MMAs are waited for (bounded again), and the tensor
+// memory is freed before the block exits.
 #include <cuda_bf16.h>
 
-#include <map>
+#include <algorithm>
 #include <mutex>
 #include <string>
-#include <tuple>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace wipes {
 
@@ -40,568 +52,1083 @@ constexpr int kOut = 13;
 constexpr int kOutPad = 16;
 constexpr int kX5 = kInPad + kWidth;  // 336
 
-struct LayerShape {
-    int out, in;
-};
-constexpr LayerShape kShapes[kHidden + 1] = {{kWidth, kInPad}, {kWidth, kWidth}, {kWidth, kWidth}, {kWidth, kWidth},
-                                             {kWidth, kWidth}, {kWidth, kX5},    {kWidth, kWidth}, {kWidth, kWidth},
-                                             {kOut, kWidth}};
+// inputs and outputs of layer l (0 .. 8)
+__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kInPad : l == kSkipLayer ? kX5 : kWidth; }
+__host__ __device__ constexpr int layer_out(int l) { return l == kHidden ? kOut : kWidth; }
 
-int64_t layer_offset(int l) {
+__host__ __device__ constexpr int64_t layer_offset(int l) {
     int64_t k = 0;
-    for (int i = 0; i < l; ++i) k += (int64_t)kShapes[i].out * kShapes[i].in + kShapes[i].out;
+    for (int i = 0; i < l; ++i) k += (int64_t)layer_out(i) * layer_in(i) + layer_out(i);
     return k;
 }
 
-// gamma(mu, t) into columns 0..79 of the [N, 336] bf16 buffer; one thread per (row, column).
-__global__ void __launch_bounds__(256) k_mlp_encode(const float* __restrict__ params3, int64_t N, float t,
-                                                    __nv_bfloat16* __restrict__ x5) {
-    pdl_enter();
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N * kInPad) return;
-    const int64_t row = idx / kInPad;
-    const int c = (int)(idx - row * kInPad);
-    float v = 0.f;
-    if (c < 3) {
-        v = params3[row * WIPES_P3D + c];
-    } else if (c < 3 + 6 * kLx) {
+constexpr int kRows = 128;                      // rows per tile: the MMA's M
+constexpr int kEpiWarps = 8;                    // two per SM sub-partition, each owning half the columns
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTcThreads = 64 + kEpiThreads;    // warp 0 streams weights, warp 1 issues MMAs
+constexpr int kWgThreads = 192;                 // weight gradient: 4 epilogue warps
+constexpr int kStages = 4;                      // weight stages: a whole 256-wide layer in flight
+constexpr uint32_t kABlock = kRows * 128;       // one K-block of a 128-row tile: 16 KB
+constexpr uint32_t kWBlock = kWidth * 128;      // one K-block of a 256-row operand: 32 KB
+constexpr uint64_t kWaitNs = 2000000000ull;     // a wait on an mbarrier gives up after 2 s
+constexpr unsigned kMlpTimeoutBit = 2u;
+constexpr int kBiasFloats = kHidden * kWidth + kOutPad;  // 2064: hidden biases, then the head's (padded)
+constexpr int kEpiBar = 1;                      // named barrier of the epilogue warps
+
+// Per-tile copies in global memory of the tiles' A operands, as they stand in shared memory
+// (K-major along the features, 128-byte swizzle): K-block g holds features 64 g .. 64 g + 63 of
+// the 128 rows.  Read back by the weight gradient, where the rows are the contraction (K) axis,
+// they are MN-major operands.
+constexpr uint32_t kHtLayer = 4 * kABlock;            // a 256-wide layer: 64 KB
+constexpr uint32_t kHtTile = kHidden * kHtLayer;      // 8 layers: 512 KB
+constexpr uint32_t kGtTile = 2 * kABlock;             // gamma: features 0-63 and 64-79 (+ padding)
+constexpr uint32_t kDdTile = kABlock;                 // dL/dd: 16 features (+ padding)
+
+// ---- weight streams ------------------------------------------------------------------------------
+// One entry per K-block an MMA group reads: the image's byte offset and size, the A K-block, the K
+// steps of 16 in it, the B rows (the MMA's N), the accumulator column, whether its first step
+// starts the accumulator (else it adds), and whether the group ends with it.
+struct Blk {
+    uint32_t off, bytes;
+    uint8_t akb, steps, first, last;
+    uint16_t n, dcol;
+};
+constexpr int kMaxBlk = 40;
+struct Sched {
+    int n;
+    Blk b[kMaxBlk];
+};
+
+// Forward, per tile: L0 (A = gamma in A K-blocks 4, 5: K 80), L1-L4 (A = h, K-blocks 0-3), L5 (A =
+// (h4, gamma), K-blocks 0-5: its image's columns are ordered h4 first), L6, L7, L8 (16 rows).
+constexpr Sched make_fwd() {
+    Sched s{};
+    uint32_t off = 0;
+    auto add = [&](int akb, int steps, int n, bool first, bool last) {
+        Blk& b = s.b[s.n++];
+        b.off = off;
+        b.bytes = (uint32_t)n * 128u;
+        b.akb = (uint8_t)akb;
+        b.steps = (uint8_t)steps;
+        b.n = (uint16_t)n;
+        b.dcol = 0;
+        b.first = first;
+        b.last = last;
+        off += b.bytes;
+    };
+    add(4, 4, kWidth, true, false);
+    add(5, 1, kWidth, false, true);
+    for (int l = 1; l <= 7; ++l) {
+        const int nkb = l == kSkipLayer ? 6 : 4;
+        for (int kb = 0; kb < nkb; ++kb) add(kb, (l == kSkipLayer && kb == 5) ? 1 : 4, kWidth, kb == 0, kb == nkb - 1);
+    }
+    for (int kb = 0; kb < 4; ++kb) add(kb, 4, kOutPad, kb == 0, kb == 3);
+    return s;
+}
+// Backward data, per tile: head (A = dd, one K step; B = W8^T), L7, L6, L5 (dh4 into columns
+// 0-255, then dgamma into columns 256-335), L4 .. L1, L0 (dgamma += dz0 W0).
+constexpr Sched make_bwd() {
+    Sched s{};
+    uint32_t off = 0;
+    auto add = [&](int akb, int steps, int n, int dcol, bool first, bool last) {
+        Blk& b = s.b[s.n++];
+        b.off = off;
+        b.bytes = (uint32_t)n * 128u;
+        b.akb = (uint8_t)akb;
+        b.steps = (uint8_t)steps;
+        b.n = (uint16_t)n;
+        b.dcol = (uint16_t)dcol;
+        b.first = first;
+        b.last = last;
+        off += b.bytes;
+    };
+    add(0, 1, kWidth, 0, true, true);
+    for (int l = 7; l >= 0; --l) {
+        if (l == 0) {
+            for (int kb = 0; kb < 4; ++kb) add(kb, 4, kInPad, kWidth, false, kb == 3);
+            continue;
+        }
+        for (int kb = 0; kb < 4; ++kb) add(kb, 4, kWidth, 0, kb == 0, l != kSkipLayer && kb == 3);
+        if (l == kSkipLayer)
+            for (int kb = 0; kb < 4; ++kb) add(kb, 4, kInPad, kWidth, kb == 0, kb == 3);
+    }
+    return s;
+}
+constexpr Sched kFwdSched = make_fwd();
+constexpr Sched kBwdSched = make_bwd();
+constexpr uint32_t kFwdImgBytes = kFwdSched.b[kFwdSched.n - 1].off + kFwdSched.b[kFwdSched.n - 1].bytes;
+constexpr uint32_t kBwdImgBytes = kBwdSched.b[kBwdSched.n - 1].off + kBwdSched.b[kBwdSched.n - 1].bytes;
+__constant__ Sched c_fwd = make_fwd();
+__constant__ Sched c_bwd = make_bwd();
+
+// Images of the weights, described for the packing kernel: element (row n, column k) of image i is
+// theta[src + n sn + col(k) sk] for n < nvalid and k < kvalid (0 elsewhere), with col(k) = k + klo
+// for k < ksplit and k - ksplit + khi beyond (the skip layer's reordered columns).
+struct ImgDesc {
+    uint32_t dst, rows, nkb;  // byte offset, rows (N), K-blocks
+    int64_t src;
+    int32_t sn, sk, nvalid, kvalid, ksplit, klo, khi;
+};
+constexpr int kNumImg = 22;
+struct ImgTable {
+    ImgDesc d[kNumImg];
+    int n;
+};
+ImgTable make_images() {
+    ImgTable t{};
+    uint32_t off = 0;
+    auto add = [&](int rows, int nkb, int64_t src, int sn, int sk, int nvalid, int kvalid, int ksplit, int klo, int khi) {
+        ImgDesc& d = t.d[t.n++];
+        d.dst = off;
+        d.rows = (uint32_t)rows;
+        d.nkb = (uint32_t)nkb;
+        d.src = src;
+        d.sn = sn;
+        d.sk = sk;
+        d.nvalid = nvalid;
+        d.kvalid = kvalid;
+        d.ksplit = ksplit;
+        d.klo = klo;
+        d.khi = khi;
+        off += (uint32_t)rows * 128u * (uint32_t)nkb;
+    };
+    // forward images (B = W_l: rows = outputs, K = inputs), in the order of kFwdSched
+    add(kWidth, 2, layer_offset(0), kInPad, 1, kWidth, kInPad, 1 << 30, 0, 0);
+    for (int l = 1; l <= 7; ++l) {
+        if (l == kSkipLayer)
+            add(kWidth, 6, layer_offset(l), kX5, 1, kWidth, kX5, kWidth, kInPad, 0);
+        else
+            add(kWidth, 4, layer_offset(l), kWidth, 1, kWidth, kWidth, 1 << 30, 0, 0);
+    }
+    add(kOutPad, 4, layer_offset(8), kWidth, 1, kOut, kWidth, 1 << 30, 0, 0);
+    // backward images (B = W_l^T: rows = inputs, K = outputs), in the order of kBwdSched
+    add(kWidth, 1, layer_offset(8), 1, kWidth, kWidth, kOut, 1 << 30, 0, 0);
+    for (int l = 7; l >= 0; --l) {
+        if (l == 0) {
+            add(kInPad, 4, layer_offset(0), 1, kInPad, kInPad, kWidth, 1 << 30, 0, 0);
+        } else if (l == kSkipLayer) {
+            add(kWidth, 4, layer_offset(l) + kInPad, 1, kX5, kWidth, kWidth, 1 << 30, 0, 0);
+            add(kInPad, 4, layer_offset(l), 1, kX5, kInPad, kWidth, 1 << 30, 0, 0);
+        } else {
+            add(kWidth, 4, layer_offset(l), 1, kWidth, kWidth, kWidth, 1 << 30, 0, 0);
+        }
+    }
+    return t;
+}
+
+// ---- small device helpers -------------------------------------------------------------------------
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+    const uint32_t a = tc::smem_u32(p);
+    return p + ((1024u - (a & 1023u)) & 1023u);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&b);
+}
+// max(lo, 0) and max(hi, 0) rounded to bfloat16 and packed (one instruction)
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// Write 8 packed bfloat16 pairs (16 columns starting at a multiple of 16) of row r into a 128-row
+// K-major swizzled tile in shared memory.
+__device__ __forceinline__ void store_a16(uint32_t a_base, int r, int k0, const uint32_t* w) {
+    const uint32_t kb = (uint32_t)k0 / 64u, c = ((uint32_t)k0 % 64u) / 8u;
+    st_shared_v4(a_base + tc::sw128_chunk(kRows, (uint32_t)r, kb, c), w[0], w[1], w[2], w[3]);
+    st_shared_v4(a_base + tc::sw128_chunk(kRows, (uint32_t)r, kb, c + 1), w[4], w[5], w[6], w[7]);
+}
+// Sum 32 per-lane values over the warp by recursive halving: on return lane l holds the warp's
+// total of value l (31 shuffles).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = lane & s;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = up ? v[i] : v[i + s];
+            const float keep = up ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+// Control block of a tile kernel in shared memory.
+struct Ctl {
+    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain;
+    uint32_t tmem;
+    volatile int abort;
+};
+
+__device__ __forceinline__ void raise_abort(Ctl* ctl, unsigned int* err) {
+    ctl->abort = 1;
+    atomicOr(err, kMlpTimeoutBit);
+}
+__device__ __forceinline__ bool wait_or_abort(Ctl* ctl, uint64_t* bar, uint32_t parity, unsigned int* err) {
+    if (ctl->abort) return false;
+    if (tc::mbar_wait(bar, parity, kWaitNs)) return true;
+    raise_abort(ctl, err);
+    return false;
+}
+
+// Producer (warp 0, one thread): stream `per_tile` schedule entries for every tile of this block
+// through the stage ring; at the end wait for the copies still in flight.
+__device__ void produce_weights(Ctl* ctl, uint8_t* sW, const uint8_t* img, const Sched* S, int tiles,
+                                unsigned int* err) {
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < tiles && !ctl->abort; tile += gridDim.x) {
+        for (int j = 0; j < S->n; ++j, ++it) {
+            const uint32_t stage = it % kStages, round = it / kStages;
+            if (round > 0 && !wait_or_abort(ctl, &ctl->empty[stage], (round - 1) & 1u, err)) goto drain;
+            tc::mbar_arrive_expect_tx(&ctl->full[stage], S->b[j].bytes);
+            tc::bulk_g2s(sW + stage * kWBlock, img + S->b[j].off, S->b[j].bytes, &ctl->full[stage]);
+        }
+    }
+drain:
+    for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0u; k < it; ++k)
+        tc::mbar_wait(&ctl->full[k % kStages], (k / kStages) & 1u, kWaitNs);
+}
+
+// MMA issuer (warp 1, one thread): for every tile, the schedule's groups, each after the
+// epilogue has its A operand ready; a stage is released when its MMAs complete, a group's end is
+// signalled on mma_done.  At the end, the MMAs in flight are waited for.
+__device__ void issue_mmas(Ctl* ctl, uint8_t* sA, uint8_t* sW, const Sched* S, int tiles, uint32_t tmem,
+                           unsigned int* err) {
+    uint32_t it = 0, ar = 0;
+    const uint32_t a0 = tc::smem_u32(sA), w0 = tc::smem_u32(sW);
+    for (int tile = blockIdx.x; tile < tiles && !ctl->abort; tile += gridDim.x) {
+        for (int j = 0; j < S->n; ++j, ++it) {
+            const Blk b = S->b[j];
+            if (j == 0 || S->b[j - 1].last) {  // a new group: its A operand comes from the epilogue
+                if (!wait_or_abort(ctl, &ctl->a_ready, ar & 1u, err)) goto drain;
+                ++ar;
+                tc::fence_after_sync();
+            }
+            const uint32_t stage = it % kStages;
+            if (!wait_or_abort(ctl, &ctl->full[stage], (it / kStages) & 1u, err)) goto drain;
+            tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_bf16(kRows, b.n);
+            for (int k = 0; k < b.steps; ++k) {
+                const uint64_t ad = tc::desc_sw128(a0 + b.akb * kABlock + 32u * k);
+                const uint64_t bd = tc::desc_sw128(w0 + stage * kWBlock + 32u * k);
+                tc::mma_bf16(tmem + b.dcol, ad, bd, idesc, (b.first && k == 0) ? 0u : 1u);
+            }
+            tc::mma_commit(&ctl->empty[stage]);
+            if (b.last) tc::mma_commit(&ctl->mma_done);
+        }
+    }
+drain:
+    tc::mma_commit(&ctl->drain);
+    tc::mbar_wait(&ctl->drain, 0, kWaitNs);
+}
+
+// ---- forward ----------------------------------------------------------------------------------
+struct FwdArgs {
+    const float* params3;
+    int64_t N;
+    float t;
+    const uint8_t* wimg;   // forward weight images (kFwdSched order)
+    const float* bias;     // kBiasFloats
+    float* d;              // [N, 16] network outputs including the head's bias
+    float* params_out;     // [N, 20]
+    uint8_t* ht;           // [tiles][8 layers][4 K-blocks of 16 KB] hidden activations
+    uint8_t* gt;           // [tiles][2 K-blocks of 16 KB] encoding
+    unsigned int* err;
+    int tiles;
+    int vec;               // params3 / params_out rows 16-byte aligned
+};
+
+constexpr uint32_t kFwdSmem = 1024 + 6 * kABlock + kStages * kWBlock + sizeof(Ctl);
+
+// gamma of one row (Sec. 4.3): columns 0-2 mu, then per octave k sin(2^k mu) (3), cos(2^k mu) (3);
+// column 63 t, then per octave sin(2^k t), cos(2^k t); 76-79 zero.
+__device__ __forceinline__ float encoding(int c, const float mu[3], float t) {
+    if (c < 3) return mu[c];
+    if (c < 3 + 6 * kLx) {
         const int k = (c - 3) / 6, r = (c - 3) % 6;
-        const float x = params3[row * WIPES_P3D + (r % 3)] * (float)(1 << k);
-        v = r < 3 ? sinf(x) : cosf(x);
-    } else if (c == 3 + 6 * kLx) {
-        v = t;
-    } else if (c < kIn) {
+        const float x = mu[r % 3] * (float)(1 << k);
+        return r < 3 ? sinf(x) : cosf(x);
+    }
+    if (c == 3 + 6 * kLx) return t;
+    if (c < kIn) {
         const int k = (c - 4 - 6 * kLx) / 2, r = (c - 4 - 6 * kLx) % 2;
         const float x = t * (float)(1 << k);
-        v = r == 0 ? sinf(x) : cosf(x);
+        return r == 0 ? sinf(x) : cosf(x);
     }
-    x5[row * kX5 + c] = __float2bfloat16_rn(v);
+    return 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                                                 int64_t n) {
-    pdl_enter();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = __float2bfloat16_rn(src[i]);
+// The epilogue warps' hand-off around an A operand that they rewrite: the copy of its previous
+// contents to global memory (issued by one thread) must have read them first.
+__device__ __forceinline__ void await_a_free(bool lead) {
+    if (lead) tc::bulk_wait_read();
+    tc::named_sync(kEpiBar, kEpiThreads);
 }
-
-// deformed record from the canonical record and the network outputs d [N, 16] (13 used): the
-// output layer's bias b is added here, and d keeps the biased outputs for the backward.  VEC: the
-// caller's record rows are 16-byte aligned and move in 16-byte pieces (d always does).
-template <bool VEC>
-__global__ void __launch_bounds__(256) k_mlp_apply(const float* __restrict__ params3, int64_t N,
-                                                   float* __restrict__ d, const float* __restrict__ b,
-                                                   float* __restrict__ out) {
-    pdl_enter();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    float p[WIPES_P3D], e[kOutPad], o[WIPES_P3D];
-    load_row<VEC, WIPES_P3D>(p, params3 + i * WIPES_P3D);
-    load_row<true, kOutPad>(e, d + i * kOutPad);
-#pragma unroll
-    for (int k = 0; k < kOut; ++k) e[k] += b[k];
-    store_row<true, kOutPad>(d + i * kOutPad, e);
-#pragma unroll
-    for (int k = 0; k < WIPES_P3D; ++k) o[k] = p[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        o[k] = p[k] + e[k];
-        o[3 + k] = p[3 + k] * expf(e[7 + k]);
-        o[10 + k] = p[10 + k] + e[10 + k];
+// After writing A: make it visible to the tensor core, copy `nkb` K-blocks from A K-block `kb0`
+// to global `dst` (one thread), and tell the MMA issuer.
+__device__ __forceinline__ void publish_a(Ctl* ctl, bool lead, uint8_t* sA, int kb0, int nkb, uint8_t* dst) {
+    tc::fence_proxy_async();
+    tc::named_sync(kEpiBar, kEpiThreads);
+    if (lead) {
+        for (int k = 0; k < nkb; ++k) tc::bulk_s2g(dst + (size_t)k * kABlock, sA + (size_t)(kb0 + k) * kABlock, kABlock);
+        tc::bulk_commit();
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[6 + k] = p[6 + k] + e[3 + k];
-    store_row<VEC, WIPES_P3D>(out + i * WIPES_P3D, o);
+    tc::fence_before_sync();
+    tc::mbar_arrive(&ctl->a_ready);
+}
+// Wait for the MMA group; every epilogue thread learns whether any of them (or another role) gave up.
+__device__ __forceinline__ bool await_mma(Ctl* ctl, uint32_t parity, unsigned int* err) {
+    const bool ok = wait_or_abort(ctl, &ctl->mma_done, parity, err);
+    const bool stop = tc::named_sync_or(kEpiBar, kEpiThreads, !ok || ctl->abort);
+    tc::fence_after_sync();
+    return !stop;
 }
 
-// dL/dd (bfloat16, the backward's product operand) and the direct part of dL/dparams3; the output
-// bias gradient is the column sum of the rounded dL/dd (summed over the warp, then the block)
-template <bool VEC>
-__global__ void __launch_bounds__(256) k_mlp_apply_backward(const float* __restrict__ params3, int64_t N,
-                                                            const float* __restrict__ d,
-                                                            const float* __restrict__ g_out,
-                                                            __nv_bfloat16* __restrict__ gd,
-                                                            float* __restrict__ g_params3, int accumulate,
-                                                            float* __restrict__ db_head) {
-    pdl_enter();
-    __shared__ float s_db[kOutPad];
-    if (threadIdx.x < kOutPad) s_db[threadIdx.x] = 0.f;
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant__ FwdArgs P) {
+    pdl_enter();  // inputs written by the previous kernel on the stream
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ Sched s_sched;
+    if (threadIdx.x < kMaxBlk) s_sched.b[threadIdx.x] = c_fwd.b[threadIdx.x];
+    if (threadIdx.x == 0) s_sched.n = c_fwd.n;
+    uint8_t* sA = align1024(smem_raw);        // 6 K-blocks: h (0-3), gamma (4-5)
+    uint8_t* sW = sA + 6 * kABlock;           // stage ring
+    Ctl* ctl = reinterpret_cast<Ctl*>(sW + kStages * kWBlock);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->empty[s], 1);
+        }
+        tc::mbar_init(&ctl->mma_done, 1);
+        tc::mbar_init(&ctl->a_ready, kEpiThreads);
+        tc::mbar_init(&ctl->tmem_free, kEpiThreads);
+        tc::mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem, 256);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float gdr[kOutPad];  // the rounded dL/dd of this row (0 past N)
-#pragma unroll
-    for (int k = 0; k < kOutPad; ++k) gdr[k] = 0.f;
-    if (i < N) {
-        float p[WIPES_P3D], e[kOutPad], g[WIPES_P3D];
-        load_row<VEC, WIPES_P3D>(p, params3 + i * WIPES_P3D);
-        load_row<true, kOutPad>(e, d + i * kOutPad);
-        load_row<VEC, WIPES_P3D>(g, g_out + i * WIPES_P3D);
-        float gdv[kOutPad];
-#pragma unroll
-        for (int k = 0; k < kOutPad; ++k) gdv[k] = 0.f;
-        float gp[WIPES_P3D];
-#pragma unroll
-        for (int k = 0; k < WIPES_P3D; ++k) gp[k] = g[k];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float es = expf(e[7 + k]);
-            gdv[k] = g[k];
-            gdv[7 + k] = g[3 + k] * p[3 + k] * es;
-            gdv[10 + k] = g[10 + k];
-            gp[3 + k] = g[3 + k] * es;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) gdv[3 + k] = g[6 + k];
-        uint32_t packed[kOutPad / 2];
-#pragma unroll
-        for (int k = 0; k < kOutPad; k += 2) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(gdv[k], gdv[k + 1]);
-            packed[k / 2] = *reinterpret_cast<const uint32_t*>(&b2);
-            const float2 f2v = __bfloat1622float2(b2);
-            gdr[k] = f2v.x;
-            gdr[k + 1] = f2v.y;
-        }
-        uint4* gd4 = reinterpret_cast<uint4*>(gd + i * kOutPad);
-        gd4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        gd4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-        float* go = g_params3 + i * WIPES_P3D;
-        if (accumulate) {
-            float prev[WIPES_P3D];
-            load_row<VEC, WIPES_P3D>(prev, go);
-#pragma unroll
-            for (int k = 0; k < WIPES_P3D; ++k) gp[k] = prev[k] + gp[k];
-        }
-        store_row<VEC, WIPES_P3D>(go, gp);
-    }
-#pragma unroll
-    for (int k = 0; k < kOut; ++k) {
-        float v = gdr[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_db[k], v);
-    }
-    __syncthreads();
-    if (threadIdx.x < kOut) atomicAdd(&db_head[threadIdx.x], s_db[threadIdx.x]);
-}
+    tc::fence_after_sync();
+    const uint32_t tmem = ctl->tmem;
 
-// the output layer's weights += rows 0..12 of the padded [16, 256] weight gradient
-__global__ void __launch_bounds__(256) k_mlp_add_head_dw(const float* __restrict__ dw_head16,
-                                                         float* __restrict__ g_theta, int64_t head_off) {
-    pdl_enter();
-    const int c = threadIdx.x;
-    for (int o = 0; o < kOut; ++o) g_theta[head_off + (int64_t)o * kWidth + c] += dw_head16[o * kWidth + c];
-}
-
-// the output layer's weights in bfloat16, zero-padded from 13 to 16 rows (aligned product shapes)
-__global__ void __launch_bounds__(256) k_mlp_head16(const float* __restrict__ w_head, __nv_bfloat16* __restrict__ out) {
-    pdl_enter();
-    const int c = threadIdx.x;
-    for (int o = 0; o < kOutPad; ++o) out[o * kWidth + c] = __float2bfloat16_rn(o < kOut ? w_head[o * kWidth + c] : 0.f);
-}
-
-// dz = dh where the layer's activation was positive (its ReLU bit-mask from the forward product)
-// and the bias gradient (column sums of dz) of a 256-wide layer: a warp takes a row, each lane 8
-// columns with a 16-byte access and one mask byte; the block sums its column totals in shared
-// memory and adds them with one atomic per column
-constexpr int kReluBlocks = 152 * 4;
-constexpr int kReluRows = 4;  // rows a warp has in flight: its loads are issued before any is used
-__global__ void __launch_bounds__(256) k_relu_backward(const __nv_bfloat16* __restrict__ dh, int ld_dh,
-                                                       const uint8_t* __restrict__ mask, int64_t N,
-                                                       __nv_bfloat16* __restrict__ dz, float* __restrict__ db) {
-    pdl_enter();
-    __shared__ float s_db[8][kWidth];
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    float acc[8];
+    if (warp == 0) {
+        if (lane == 0) produce_weights(ctl, sW, P.wimg, &s_sched, P.tiles, P.err);
+    } else if (warp == 1) {
+        if (lane == 0) issue_mmas(ctl, sA, sW, &s_sched, P.tiles, tmem, P.err);
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; warps 2-5 own columns 0-127, 6-9 128-255
+        const int ew = warp - 2, q = warp & 3, half = ew >> 2, r = q * 32 + lane;
+        const bool lead = ew == 0 && lane == 0;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t a0 = tc::smem_u32(sA);
+        uint32_t md = 0;
+        for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+            const int64_t row = (int64_t)tile * kRows + r;
+            const bool valid = row < P.N;
+            // the encoding into A K-blocks 4 and 5 (chunks of 16 features: half 0 the first three)
+            float mu[3] = {0.f, 0.f, 0.f};
+            if (valid)
+                for (int j = 0; j < 3; ++j) mu[j] = P.params3[row * WIPES_P3D + j];
+            await_a_free(lead);
+#pragma unroll 1
+            for (int c0 = half * 48; c0 < (half ? kInPad : 48); c0 += 16) {
+                uint32_t w[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-    const int64_t stride = (int64_t)gridDim.x * 8;
-    for (int64_t r0 = (int64_t)blockIdx.x * 8 + g; r0 < N; r0 += kReluRows * stride) {
-        uint4 vd[kReluRows];
-        uint32_t mb[kReluRows];
-#pragma unroll
-        for (int j = 0; j < kReluRows; ++j) {
-            const int64_t r = r0 + j * stride;
-            vd[j] = make_uint4(0u, 0u, 0u, 0u);
-            mb[j] = 0u;
-            if (r < N) {
-                mb[j] = mask[r * (kWidth / 8) + lane];  // activations 8 lane .. 8 lane + 7 of row r
-                vd[j] = *reinterpret_cast<const uint4*>(dh + r * ld_dh + 8 * lane);
+                for (int j = 0; j < 8; ++j)
+                    w[j] = valid ? pack_bf16(encoding(c0 + 2 * j, mu, P.t), encoding(c0 + 2 * j + 1, mu, P.t)) : 0u;
+                store_a16(a0 + 4 * kABlock, r, c0, w);
             }
-        }
+            publish_a(ctl, lead, sA, 4, 2, P.gt + (size_t)tile * kGtTile);
+            for (int l = 0; l <= kHidden; ++l) {
+                if (!await_mma(ctl, md & 1u, P.err)) goto done;
+                ++md;
+                if (l == kHidden) {
+                    // the head: 16 fp32 outputs (13 used) plus the bias, and the deformed record
+                    if (half == 0) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(tl, v);
+                        tc::tmem_wait_ld();
+                        float e[kOutPad];
 #pragma unroll
-        for (int j = 0; j < kReluRows; ++j) {
-            const int64_t r = r0 + j * stride;
-            const __nv_bfloat162* pd = reinterpret_cast<const __nv_bfloat162*>(&vd[j]);
-            uint4 vo;
-            __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&vo);
+                        for (int j = 0; j < kOutPad; ++j) e[j] = __uint_as_float(v[j]) + __ldg(&P.bias[kHidden * kWidth + j]);
+                        if (valid) {
+                            float4* dr = reinterpret_cast<float4*>(P.d + row * kOutPad);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float2 fd = __bfloat1622float2(pd[k]);
-                fd.x = (mb[j] >> (2 * k)) & 1u ? fd.x : 0.f;
-                fd.y = (mb[j] >> (2 * k + 1)) & 1u ? fd.y : 0.f;
-                po[k] = __floats2bfloat162_rn(fd.x, fd.y);  // exact: fd is a bfloat16 value or 0
-                acc[2 * k] += fd.x;
-                acc[2 * k + 1] += fd.y;
-            }
-            if (r < N) *reinterpret_cast<uint4*>(dz + r * kWidth + 8 * lane) = vo;
-        }
-    }
+                            for (int j = 0; j < 4; ++j)
+                                dr[j] = make_float4(e[4 * j], e[4 * j + 1], e[4 * j + 2], e[4 * j + 3]);
+                            float p[WIPES_P3D], o[WIPES_P3D];
+                            if (P.vec) load_row<true, WIPES_P3D>(p, P.params3 + row * WIPES_P3D);
+                            else load_row<false, WIPES_P3D>(p, P.params3 + row * WIPES_P3D);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s_db[g][8 * lane + k] = acc[k];
-    __syncthreads();
-    float sum = 0.f;
+                            for (int k = 0; k < WIPES_P3D; ++k) o[k] = p[k];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sum += s_db[q][threadIdx.x];
-    atomicAdd(&db[threadIdx.x], sum);
-}
-
-// dL/dmu through gamma: d/dx (x, sin(2^k x), cos(2^k x)) = (1, 2^k cos, -2^k sin); the encoding's
-// gradient is the sum of layer 0's (dg0 [N, 80]) and layer 5's through its skip input (dgs [N, 80])
-__global__ void __launch_bounds__(256) k_mlp_encode_backward(const float* __restrict__ params3, int64_t N,
-                                                             const __nv_bfloat16* __restrict__ dg0,
-                                                             const __nv_bfloat16* __restrict__ dgs,
-                                                             float* __restrict__ g_params3) {
-    pdl_enter();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    // columns 0 .. 63 of both rows (the centre's encoding is columns 0 .. 62), in 16-byte pieces
-    constexpr int kCols = 64;
-    static_assert(3 + 6 * kLx <= kCols && kInPad % 8 == 0, "the centre's encoding fits the loaded columns");
-    float ab[kCols];  // the encoding's gradient: layer 0's part plus the skip input's
+                            for (int k = 0; k < 3; ++k) {
+                                o[k] = p[k] + e[k];
+                                o[3 + k] = p[3 + k] * expf(e[7 + k]);
+                                o[10 + k] = p[10 + k] + e[10 + k];
+                            }
 #pragma unroll
-    for (int q = 0; q < kCols / 8; ++q) {
-        const uint4 va = reinterpret_cast<const uint4*>(dg0 + i * kInPad)[q];
-        const uint4 vb = reinterpret_cast<const uint4*>(dgs + i * kInPad)[q];
-        const uint32_t wa[4] = {va.x, va.y, va.z, va.w}, wb[4] = {vb.x, vb.y, vb.z, vb.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wa[h]));
-            const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wb[h]));
-            ab[8 * q + 2 * h] = fa.x + fb.x, ab[8 * q + 2 * h + 1] = fa.y + fb.y;
-        }
-    }
-    float gm[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gm[j] = ab[j];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float x = params3[i * WIPES_P3D + j];
-#pragma unroll
-        for (int k = 0; k < kLx; ++k) {
-            const float f = (float)(1 << k);
-            const float gs = ab[3 + 6 * k + j];
-            const float gc = ab[6 + 6 * k + j];
-            float sn, cs;
-            sincosf(f * x, &sn, &cs);
-            gm[j] += f * (gs * cs - gc * sn);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) g_params3[i * WIPES_P3D + j] += gm[j];
-}
-
-// ---------------------------------------------------------------------------------------------
-// cuBLASLt products (column-major views, see the header comment)
-// ---------------------------------------------------------------------------------------------
-
-#define LT_TRY(x)                                                                                        \
-    do {                                                                                                 \
-        cublasStatus_t st_ = (x);                                                                        \
-        if (st_ != CUBLAS_STATUS_SUCCESS) return std::string("cuBLASLt: " #x " failed with status ") + \
-                                                 std::to_string((int)st_);                               \
-    } while (0)
-
-struct GemmKey {
-    int ta, tb, m, n, k, lda, ldb, ldc, dtype, epi;
-    bool operator<(const GemmKey& o) const {
-        return std::tie(ta, tb, m, n, k, lda, ldb, ldc, dtype, epi) <
-               std::tie(o.ta, o.tb, o.m, o.n, o.k, o.lda, o.ldb, o.ldc, o.dtype, o.epi);
-    }
-};
-
-}  // namespace
-
-struct MlpLt {
-    cublasLtHandle_t h = nullptr;
-    void* ws = nullptr;
-    size_t ws_size = 32u << 20;
-    std::map<GemmKey, cublasLtMatmulHeuristicResult_t> algos;
-    std::mutex mu;
-};
-
-namespace {
-
-// D (m x n, column-major, type dtype) = alpha op(A) op(B) (+ beta D) [+ bias, ReLU]; A, B bfloat16.
-// The bias (when given) has the type of D: bfloat16 for the hidden layers, fp32 for the output layer.
-std::string gemm(MlpLt& lt, bool ta, bool tb, int m, int n, int k, const void* A, int lda, const void* B, int ldb,
-                 void* D, int ldc, cudaDataType_t dtype, float beta, cublasLtEpilogue_t epi, const void* bias,
-                 cudaStream_t stream, void* aux = nullptr) {
-    cublasLtMatmulDesc_t desc = nullptr;
-    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, lc = nullptr;
-    LT_TRY(cublasLtMatmulDescCreate(&desc, CUBLAS_COMPUTE_32F, CUDA_R_32F));
-    const cublasOperation_t opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N, opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
-    LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_TRANSA, &opa, sizeof(opa)));
-    LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb)));
-    LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE, &epi, sizeof(epi)));
-    if (bias) LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_BIAS_POINTER, &bias, sizeof(bias)));
-    if (aux) {
-        // ReLU bit-mask, one bit per element of D (m rows), leading dimension in bits
-        const int64_t aux_ld = kWidth;
-        LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE_AUX_POINTER, &aux, sizeof(aux)));
-        LT_TRY(cublasLtMatmulDescSetAttribute(desc, CUBLASLT_MATMUL_DESC_EPILOGUE_AUX_LD, &aux_ld, sizeof(aux_ld)));
-    }
-    LT_TRY(cublasLtMatrixLayoutCreate(&la, CUDA_R_16BF, ta ? k : m, ta ? m : k, lda));
-    LT_TRY(cublasLtMatrixLayoutCreate(&lb, CUDA_R_16BF, tb ? n : k, tb ? k : n, ldb));
-    LT_TRY(cublasLtMatrixLayoutCreate(&lc, dtype, m, n, ldc));
-    const GemmKey key{ta, tb, m, n, k, lda, ldb, ldc, (int)dtype, (int)epi};
-    cublasLtMatmulHeuristicResult_t res{};
-    {
-        std::lock_guard<std::mutex> g(lt.mu);
-        auto it = lt.algos.find(key);
-        if (it != lt.algos.end()) {
-            res = it->second;
-        } else {
-            cublasLtMatmulPreference_t pref = nullptr;
-            LT_TRY(cublasLtMatmulPreferenceCreate(&pref));
-            LT_TRY(cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &lt.ws_size,
-                                                        sizeof(lt.ws_size)));
-            // the heuristic's candidates are timed once on this product and the fastest is kept:
-            // its first choice is slow for some epilogues
-            constexpr int kCandidates = 12;
-            cublasLtMatmulHeuristicResult_t cand[kCandidates];
-            int found = 0;
-            const cublasStatus_t hs =
-                cublasLtMatmulAlgoGetHeuristic(lt.h, desc, la, lb, lc, lc, pref, kCandidates, cand, &found);
-            cublasLtMatmulPreferenceDestroy(pref);
-            if (hs != CUBLAS_STATUS_SUCCESS || found == 0)
-                return "cuBLASLt: no algorithm for the product (m=" + std::to_string(m) + ", n=" + std::to_string(n) +
-                       ", k=" + std::to_string(k) + ")";
-            res = cand[0];
-            if (found > 1) {
-                // trials write D (and the epilogue outputs) with beta 0: into a scratch copy when the
-                // call accumulates (beta != 0), else into D itself, which the real call rewrites
-                void* Dt = D;
-                const size_t d_bytes = (size_t)ldc * n * (dtype == CUDA_R_32F ? 4 : 2);
-                if (beta != 0.f && cudaMallocAsync(&Dt, d_bytes, stream) != cudaSuccess) Dt = nullptr;
-                cudaEvent_t e0, e1;
-                cudaEventCreate(&e0);
-                cudaEventCreate(&e1);
-                const float one = 1.f, zero = 0.f;
-                float best = 1e30f;
-                for (int c = 0; Dt && c < found; ++c) {
-                    float ms_sum = 0.f;
-                    bool ok = true;
-                    for (int rep = 0; rep < 3 && ok; ++rep) {
-                        cudaEventRecord(e0, stream);
-                        ok = cublasLtMatmul(lt.h, desc, &one, A, la, B, lb, &zero, Dt, lc, Dt, lc, &cand[c].algo, lt.ws,
-                                            lt.ws_size, stream) == CUBLAS_STATUS_SUCCESS;
-                        cudaEventRecord(e1, stream);
-                        cudaEventSynchronize(e1);
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep > 0) ms_sum += ms;  // the first run warms up
+                            for (int k = 0; k < 4; ++k) o[6 + k] = p[6 + k] + e[3 + k];
+                            if (P.vec) store_row<true, WIPES_P3D>(P.params_out + row * WIPES_P3D, o);
+                            else store_row<false, WIPES_P3D>(P.params_out + row * WIPES_P3D, o);
+                        }
                     }
-                    if (ok && ms_sum < best) {
-                        best = ms_sum;
-                        res = cand[c];
-                    }
+                    tc::fence_before_sync();
+                    break;
                 }
-                cudaGetLastError();
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                if (Dt && Dt != D) cudaFreeAsync(Dt, stream);
+                await_a_free(lead);
+                // bias (packed f32x2 add), ReLU and bfloat16 rounding (one instruction per pair)
+                const float4* b4 = reinterpret_cast<const float4*>(P.bias + l * kWidth + half * 128);
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = half * 4 + cc;
+                    uint32_t v[32];
+                    tc::tmem_ld32(tl + 32u * c, v);
+                    tc::tmem_wait_ld();
+                    uint32_t w[16];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 b = __ldg(b4 + cc * 8 + j);
+                        const f2 z0 = f2_add(f2_pack(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1])),
+                                             f2_pack(b.x, b.y));
+                        const f2 z1 = f2_add(f2_pack(__uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3])),
+                                             f2_pack(b.z, b.w));
+                        w[2 * j] = pack_bf16_relu(f2_lo(z0), f2_hi(z0));
+                        w[2 * j + 1] = pack_bf16_relu(f2_lo(z1), f2_hi(z1));
+                    }
+                    store_a16(a0, r, 32 * c, w);
+                    store_a16(a0, r, 32 * c + 16, w + 8);
+                }
+                publish_a(ctl, lead, sA, 0, 4, P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
             }
-            lt.algos[key] = res;
         }
+    done:
+        if (lead) tc::bulk_wait_all();
     }
-    const float alpha = 1.f;
-    const cublasStatus_t st = cublasLtMatmul(lt.h, desc, &alpha, A, la, B, lb, &beta, D, lc, D, lc, &res.algo, lt.ws,
-                                             lt.ws_size, stream);
-    cublasLtMatrixLayoutDestroy(la);
-    cublasLtMatrixLayoutDestroy(lb);
-    cublasLtMatrixLayoutDestroy(lc);
-    cublasLtMatmulDescDestroy(desc);
-    if (st != CUBLAS_STATUS_SUCCESS) return "cuBLASLt: matmul failed with status " + std::to_string((int)st);
-    count_launches(1);
-    return "";
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 256);
 }
 
-// forward product of layer l: Y [N, out] (row-major, ldy) = X [N, in] (ldx) W^T + b, ReLU for hidden
-// layers (bias b in bfloat16 for them, fp32 for the output layer), whose ReLU bit-mask goes to mask
-std::string layer_forward(MlpLt& lt, int l, const __nv_bfloat16* w, const void* b, const void* x, int ldx, void* y,
-                          int ldy, int64_t N, void* mask, cudaStream_t s) {
-    const LayerShape sh = kShapes[l];
-    if (l == kHidden)  // output layer: the padded [16, 256] weights, bias added by k_mlp_apply
-        return gemm(lt, true, false, kOutPad, (int)N, kWidth, w, kWidth, x, ldx, y, ldy, CUDA_R_32F, 0.f,
-                    CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-    return gemm(lt, true, false, sh.out, (int)N, sh.in, w, sh.in, x, ldx, y, ldy, CUDA_R_16BF, 0.f,
-                CUBLASLT_EPILOGUE_RELU_AUX_BIAS, b, s, mask);
+// ---- backward (data) ---------------------------------------------------------------------------
+struct BwdArgs {
+    const float* params3;
+    int64_t N;
+    const uint8_t* wimg;   // backward weight images (kBwdSched order)
+    const float* d;        // [N, 16]
+    const float* g_out;    // [N, 20]
+    float* g_params3;      // [N, 20]
+    int accumulate;
+    const uint8_t* ht;     // the forward's hidden activations (their sign is the ReLU mask)
+    uint8_t* dzt;          // [tiles][8 layers][4 K-blocks of 16 KB] dz
+    uint8_t* ddt;          // [tiles][1 K-block of 16 KB] dL/dd
+    float* g_theta;        // bias gradients are added here (atomics, one per entry and block)
+    unsigned int* err;
+    int tiles;
+    int vec;
+};
+
+constexpr uint32_t kBwdSmem = 1024 + 4 * kABlock + kStages * kWBlock + kBiasFloats * 4 + sizeof(Ctl);
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant__ BwdArgs P) {
+    pdl_enter();  // inputs written by the previous kernel on the stream
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ Sched s_sched;
+    if (threadIdx.x < kMaxBlk) s_sched.b[threadIdx.x] = c_bwd.b[threadIdx.x];
+    if (threadIdx.x == 0) s_sched.n = c_bwd.n;
+    uint8_t* sA = align1024(smem_raw);        // 4 K-blocks: dd (K-block 0, 16 columns) or dz
+    uint8_t* sW = sA + 4 * kABlock;
+    float* s_db = reinterpret_cast<float*>(sW + kStages * kWBlock);  // bias gradients of this block
+    Ctl* ctl = reinterpret_cast<Ctl*>(s_db + kBiasFloats);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->empty[s], 1);
+        }
+        tc::mbar_init(&ctl->mma_done, 1);
+        tc::mbar_init(&ctl->a_ready, kEpiThreads);
+        tc::mbar_init(&ctl->tmem_free, kEpiThreads);
+        tc::mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        tc::fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < kBiasFloats; i += blockDim.x) s_db[i] = 0.f;
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0) {
+        if (lane == 0) produce_weights(ctl, sW, P.wimg, &s_sched, P.tiles, P.err);
+    } else if (warp == 1) {
+        if (lane == 0) issue_mmas(ctl, sA, sW, &s_sched, P.tiles, tmem, P.err);
+    } else {
+        const int ew = warp - 2, q = warp & 3, half = ew >> 2, r = q * 32 + lane;
+        const bool lead = ew == 0 && lane == 0;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t a0 = tc::smem_u32(sA);
+        uint32_t md = 0;
+        for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+            const int64_t row = (int64_t)tile * kRows + r;
+            const bool valid = row < P.N;
+            float mu[3] = {0.f, 0.f, 0.f};
+            await_a_free(lead);
+            if (half == 0) {
+                // the record update's backward: dL/dd (rounded: the head's product operand) and the
+                // direct part of dL/dparams3
+                float gd[kOutPad];
+#pragma unroll
+                for (int k = 0; k < kOutPad; ++k) gd[k] = 0.f;
+                if (valid) {
+                    float p[WIPES_P3D], e[kOutPad], g[WIPES_P3D], gp[WIPES_P3D];
+                    if (P.vec) {
+                        load_row<true, WIPES_P3D>(p, P.params3 + row * WIPES_P3D);
+                        load_row<true, WIPES_P3D>(g, P.g_out + row * WIPES_P3D);
+                    } else {
+                        load_row<false, WIPES_P3D>(p, P.params3 + row * WIPES_P3D);
+                        load_row<false, WIPES_P3D>(g, P.g_out + row * WIPES_P3D);
+                    }
+                    load_row<true, kOutPad>(e, P.d + row * kOutPad);
+#pragma unroll
+                    for (int k = 0; k < WIPES_P3D; ++k) gp[k] = g[k];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float es = expf(e[7 + k]);
+                        gd[k] = g[k];
+                        gd[7 + k] = g[3 + k] * p[3 + k] * es;
+                        gd[10 + k] = g[10 + k];
+                        gp[3 + k] = g[3 + k] * es;
+                        mu[k] = p[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) gd[3 + k] = g[6 + k];
+                    float* go = P.g_params3 + row * WIPES_P3D;
+                    if (P.accumulate) {
+                        float prev[WIPES_P3D];
+                        if (P.vec) load_row<true, WIPES_P3D>(prev, go);
+                        else load_row<false, WIPES_P3D>(prev, go);
+#pragma unroll
+                        for (int k = 0; k < WIPES_P3D; ++k) gp[k] = prev[k] + gp[k];
+                    }
+                    if (P.vec) store_row<true, WIPES_P3D>(go, gp);
+                    else store_row<false, WIPES_P3D>(go, gp);
+                }
+                uint32_t w[8];
+                float s32[32];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    w[j] = pack_bf16(gd[2 * j], gd[2 * j + 1]);
+                    s32[2 * j] = bf16_lo(w[j]);
+                    s32[2 * j + 1] = bf16_hi(w[j]);
+                }
+#pragma unroll
+                for (int j = 16; j < 32; ++j) s32[j] = 0.f;
+                store_a16(a0, r, 0, w);
+                const float tot = warp_reduce_scatter32(s32);
+                if (lane < kOutPad) atomicAdd(&s_db[kHidden * kWidth + lane], tot);
+            }
+            publish_a(ctl, lead, sA, 0, 1, P.ddt + (size_t)tile * kDdTile);
+            // dz_l = dh_l (rounded) where h_l > 0, for l = 7 .. 0; then dgamma
+            for (int l = kHidden - 1; l >= -1; --l) {
+                if (!await_mma(ctl, md & 1u, P.err)) goto done;
+                ++md;
+                if (l < 0) {
+                    // dgamma (columns 256 .. 335: the skip layer's part plus layer 0's) -> dL/dmu
+                    if (half == 0) {
+                        float dg[kInPad];
+                        uint32_t v[32];
+                        tc::tmem_ld32(tl + 256u, v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dg[j] = __uint_as_float(v[j]);
+                        tc::tmem_ld32(tl + 288u, v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dg[32 + j] = __uint_as_float(v[j]);
+                        uint32_t v16[16];
+                        tc::tmem_ld16(tl + 320u, v16);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) dg[64 + j] = __uint_as_float(v16[j]);
+                        if (valid) {
+                            float gm[3] = {dg[0], dg[1], dg[2]};
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                                for (int k = 0; k < kLx; ++k) {
+                                    const float f = (float)(1 << k);
+                                    float sn, cs;
+                                    sincosf(f * mu[j], &sn, &cs);
+                                    gm[j] += f * (dg[3 + 6 * k + j] * cs - dg[6 + 6 * k + j] * sn);
+                                }
+                            }
+                            float* go = P.g_params3 + row * WIPES_P3D;
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) go[j] += gm[j];
+                        }
+                    }
+                    tc::fence_before_sync();
+                    break;
+                }
+                // h_l of this row (the forward's copy of its A operand): its positive entries are the
+                // ReLU mask; a packed signed compare turns each bfloat16 pair into a keep mask
+                const uint8_t* hrow = P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer;
+                await_a_free(lead);
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = half * 4 + cc;
+                    uint32_t hw[16];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint4 u = __ldg(reinterpret_cast<const uint4*>(
+                            hrow + tc::sw128_chunk(kRows, (uint32_t)r, (uint32_t)c / 2u, (uint32_t)(c % 2) * 4u + k)));
+                        hw[4 * k] = u.x; hw[4 * k + 1] = u.y; hw[4 * k + 2] = u.z; hw[4 * k + 3] = u.w;
+                    }
+                    uint32_t v[32];
+                    tc::tmem_ld32(tl + 32u * c, v);
+                    tc::tmem_wait_ld();
+                    uint32_t w[16];
+                    float s32[32];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        w[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])) & __vcmpgts2(hw[j], 0u);
+                        s32[2 * j] = bf16_lo(w[j]);
+                        s32[2 * j + 1] = bf16_hi(w[j]);
+                    }
+                    store_a16(a0, r, 32 * c, w);
+                    store_a16(a0, r, 32 * c + 16, w + 8);
+                    const float tot = warp_reduce_scatter32(s32);
+                    atomicAdd(&s_db[l * kWidth + 32 * c + lane], tot);
+                }
+                publish_a(ctl, lead, sA, 0, 4, P.dzt + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
+            }
+        }
+    done:
+        if (lead) tc::bulk_wait_all();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+    // the block's bias gradients (hidden layers: [l][256]; head: 13 of 16)
+    for (int i = threadIdx.x; i < kBiasFloats; i += blockDim.x) {
+        const int l = i / kWidth, j = i % kWidth;
+        if (l < kHidden) atomicAdd(&P.g_theta[layer_offset(l) + (int64_t)layer_out(l) * layer_in(l) + j], s_db[i]);
+        else if (j < kOut) atomicAdd(&P.g_theta[layer_offset(kHidden) + (int64_t)kOut * kWidth + j], s_db[i]);
+    }
+}
+
+// ---- weight gradients ----------------------------------------------------------------------------
+// Ten products over the rows: part 0 dW_0 = dz_0^T gamma; 1-4 dW_l = dz_l^T h_{l-1}; 5 the skip
+// layer's h4 columns (dz_5^T h_4), 6 its gamma columns (dz_5^T gamma); 7, 8 dW_6, dW_7; 9 the head,
+// taken transposed (h_7^T dd: M = the 256 inputs, N = the 16 padded outputs).  Each part is split
+// into `chunks` ranges of tiles; an item = (part, chunk) accumulates its range in tensor memory
+// (two 128-row halves of M, at columns 0 and 256) and writes its 256 x N partial.  Both operands
+// are the tile copies written by the tile kernels, read MN-major: a stage holds 64 rows (K) of
+// every 64-feature group (8 KB each; A: 4 groups, B: N / 64 rounded up).
+constexpr int kParts = 10;
+struct WgArgs {
+    const uint8_t* ht;
+    const uint8_t* gt;
+    const uint8_t* dzt;
+    const uint8_t* ddt;
+    float* partial;  // [parts * chunks][256][256]
+    int tiles, chunks;
+    unsigned int* err;
+};
+struct WgPart {
+    const uint8_t* a;  // tile 0 of A's tensor
+    const uint8_t* b;
+    uint32_t a_tile, b_tile, n, nb;  // tile strides, N, B's 64-feature groups
+};
+__device__ __forceinline__ WgPart wg_part(const WgArgs& P, int p) {
+    WgPart w;
+    w.a_tile = kHtTile;
+    if (p == kParts - 1) {
+        w.a = P.ht + 7u * kHtLayer;
+        w.b = P.ddt;
+        w.b_tile = kDdTile;
+        w.n = kOutPad;
+        w.nb = 1;
+        return w;
+    }
+    const int la = p == 0 ? 0 : p <= 4 ? p : p <= 6 ? 5 : p - 1;  // dz layer of parts 0-8
+    w.a = P.dzt + (size_t)la * kHtLayer;
+    if (p == 0 || p == 6) {
+        w.b = P.gt;
+        w.b_tile = kGtTile;
+        w.n = kInPad;
+        w.nb = 2;
+    } else {
+        w.b = P.ht + (size_t)(la - 1) * kHtLayer;  // h_{l-1}; part 5 reads h_4
+        w.b_tile = kHtTile;
+        w.n = kWidth;
+        w.nb = 4;
+    }
+    return w;
+}
+
+constexpr uint32_t kGroupRows = 64;                  // K rows per stage
+constexpr uint32_t kGroupBytes = kGroupRows * 128;   // one 64-feature group of them: 8 KB
+constexpr uint32_t kWgStage = 8 * kGroupBytes;       // A (4 groups) and B (up to 4 groups): 64 KB
+constexpr int kWgStages = 3;
+constexpr uint32_t kWgSmem = 1024 + kWgStages * kWgStage + sizeof(Ctl);
+
+__global__ void __launch_bounds__(kWgThreads, 1) k_mlp_wgrad(const __grid_constant__ WgArgs P) {
+    pdl_enter();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sW = align1024(smem_raw);
+    Ctl* ctl = reinterpret_cast<Ctl*>(sW + kWgStages * kWgStage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int items = kParts * P.chunks;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->empty[s], 1);
+        }
+        tc::mbar_init(&ctl->mma_done, 1);
+        tc::mbar_init(&ctl->a_ready, 1);
+        tc::mbar_init(&ctl->tmem_free, 128);
+        tc::mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&ctl->tmem, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int item = blockIdx.x; item < items && !ctl->abort; item += gridDim.x) {
+                const WgPart w = wg_part(P, item / P.chunks);
+                const int c = item % P.chunks;
+                const int t0 = (int)((int64_t)c * P.tiles / P.chunks), t1 = (int)((int64_t)(c + 1) * P.tiles / P.chunks);
+                for (int t = t0; t < t1; ++t)
+                    for (uint32_t kc = 0; kc < kRows / kGroupRows; ++kc, ++it) {
+                        const uint32_t stage = it % kWgStages, round = it / kWgStages;
+                        if (round > 0 && !wait_or_abort(ctl, &ctl->empty[stage], (round - 1) & 1u, P.err)) goto pdrain;
+                        tc::mbar_arrive_expect_tx(&ctl->full[stage], (4 + w.nb) * kGroupBytes);
+                        uint8_t* dst = sW + stage * kWgStage;
+                        const uint8_t* a = w.a + (size_t)t * w.a_tile + kc * kGroupBytes;
+                        const uint8_t* b = w.b + (size_t)t * w.b_tile + kc * kGroupBytes;
+                        for (int g = 0; g < 4; ++g)
+                            tc::bulk_g2s(dst + g * kGroupBytes, a + (size_t)g * kABlock, kGroupBytes, &ctl->full[stage]);
+                        for (uint32_t g = 0; g < w.nb; ++g)
+                            tc::bulk_g2s(dst + (4 + g) * kGroupBytes, b + (size_t)g * kABlock, kGroupBytes,
+                                         &ctl->full[stage]);
+                    }
+            }
+        pdrain:
+            for (uint32_t k = it > (uint32_t)kWgStages ? it - kWgStages : 0u; k < it; ++k)
+                tc::mbar_wait(&ctl->full[k % kWgStages], (k / kWgStages) & 1u, kWaitNs);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, nitem = 0;
+            const uint32_t w0 = tc::smem_u32(sW);
+            for (int item = blockIdx.x; item < items && !ctl->abort; item += gridDim.x, ++nitem) {
+                const WgPart w = wg_part(P, item / P.chunks);
+                const int c = item % P.chunks;
+                const int t0 = (int)((int64_t)c * P.tiles / P.chunks), t1 = (int)((int64_t)(c + 1) * P.tiles / P.chunks);
+                // the accumulator is free once the epilogue has read the previous item's
+                if (nitem > 0) {
+                    if (!wait_or_abort(ctl, &ctl->tmem_free, (nitem - 1) & 1u, P.err)) goto mdrain;
+                    tc::fence_after_sync();
+                }
+                const uint32_t idesc = tc::idesc_bf16(kRows, (int)w.n, true, true);
+                bool first = true;
+                for (int t = t0; t < t1; ++t)
+                    for (uint32_t kc = 0; kc < kRows / kGroupRows; ++kc, ++it) {
+                        const uint32_t stage = it % kWgStages;
+                        if (!wait_or_abort(ctl, &ctl->full[stage], (it / kWgStages) & 1u, P.err)) goto mdrain;
+                        tc::fence_after_sync();
+                        const uint32_t sa = w0 + stage * kWgStage, sb = sa + 4 * kGroupBytes;
+                        for (int h = 0; h < 2; ++h)
+                            for (int k = 0; k < 4; ++k)  // 16 rows (two 8-row groups) per step
+                                tc::mma_bf16(tmem + (uint32_t)h * 256u,
+                                             tc::desc_sw128_mn(sa + (uint32_t)h * 2 * kGroupBytes + 2048u * k,
+                                                               kGroupBytes, 1024),
+                                             tc::desc_sw128_mn(sb + 2048u * k, kGroupBytes, 1024), idesc,
+                                             (first && k == 0) ? 0u : 1u);
+                        first = false;
+                        tc::mma_commit(&ctl->empty[stage]);
+                    }
+                // an empty range leaves the accumulator unwritten: the epilogue writes zeros then
+                tc::mma_commit(&ctl->mma_done);
+            }
+        mdrain:
+            tc::mma_commit(&ctl->drain);
+            tc::mbar_wait(&ctl->drain, 0, kWaitNs);
+        }
+    } else {
+        const int q = warp & 3, m = q * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        uint32_t nitem = 0;
+        for (int item = blockIdx.x; item < items; item += gridDim.x, ++nitem) {
+            const WgPart w = wg_part(P, item / P.chunks);
+            const int c = item % P.chunks;
+            const bool empty_range = (int64_t)c * P.tiles / P.chunks == (int64_t)(c + 1) * P.tiles / P.chunks;
+            if (!wait_or_abort(ctl, &ctl->mma_done, nitem & 1u, P.err)) break;
+            tc::fence_after_sync();
+            float* out = P.partial + (size_t)item * kWidth * kWidth;
+            for (int h = 0; h < 2; ++h) {
+                float* orow = out + (size_t)(h * kRows + m) * kWidth;
+                for (uint32_t c0 = 0; c0 < w.n; c0 += 16) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tl + (uint32_t)h * 256u + c0, v);
+                    tc::tmem_wait_ld();
+                    float4* o4 = reinterpret_cast<float4*>(orow + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        o4[j] = empty_range ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                            : make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                                          __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&ctl->tmem_free);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// g_theta (weights) += the sum of the chunks' partials, in chunk order; one thread per weight.
+__global__ void __launch_bounds__(256) k_mlp_wsum(const float* __restrict__ partial, int chunks,
+                                                  float* __restrict__ g_theta) {
+    pdl_enter();
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // weights in theta order: layer l, output o, input i
+    int l = 0;
+    int64_t rem = idx;
+    while (l <= kHidden && rem >= (int64_t)layer_out(l) * layer_in(l)) {
+        rem -= (int64_t)layer_out(l) * layer_in(l);
+        ++l;
+    }
+    if (l > kHidden) return;
+    const int o = (int)(rem / layer_in(l)), i = (int)(rem % layer_in(l));
+    int part, row, col;
+    if (l == kHidden) {
+        part = kParts - 1, row = i, col = o;  // the head's product is transposed
+    } else if (l == kSkipLayer) {
+        if (i < kInPad) part = 6, row = o, col = i;
+        else part = 5, row = o, col = i - kInPad;
+    } else {
+        part = l <= 4 ? l : l + 1;
+        row = o, col = i;
+    }
+    float s = 0.f;
+    for (int c = 0; c < chunks; ++c)
+        s += partial[((size_t)(part * chunks + c) * kWidth + row) * kWidth + col];
+    g_theta[layer_offset(l) + (int64_t)o * layer_in(l) + i] += s;
+}
+
+// Pack theta (fp32) into the weight images (bfloat16, K-major, 128-byte swizzle) and the fp32
+// bias vector: one thread per 16-byte chunk of an image.
+__global__ void __launch_bounds__(256) k_mlp_pack(const float* __restrict__ theta, const ImgTable tab,
+                                                  uint8_t* __restrict__ img, float* __restrict__ bias) {
+    pdl_enter();
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < kBiasFloats) {
+        const int l = (int)(idx / kWidth), j = (int)(idx % kWidth);
+        float b = 0.f;
+        if (l < kHidden) b = theta[layer_offset(l) + (int64_t)layer_out(l) * layer_in(l) + j];
+        else if (j < kOut) b = theta[layer_offset(kHidden) + (int64_t)kOut * kWidth + j];
+        bias[idx] = b;
+    }
+    for (int i = 0; i < tab.n; ++i) {
+        const ImgDesc& d = tab.d[i];
+        const int64_t chunks = (int64_t)d.rows * d.nkb * 8;
+        if (idx >= chunks) {
+            idx -= chunks;
+            continue;
+        }
+        const uint32_t kb = (uint32_t)(idx / ((int64_t)d.rows * 8)), rem = (uint32_t)(idx % ((int64_t)d.rows * 8));
+        const uint32_t n = rem / 8, c = rem % 8;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = (int)(kb * 64 + c * 8 + e);
+            v[e] = 0.f;
+            if ((int)n < d.nvalid && k < d.kvalid) {
+                const int col = k < d.ksplit ? k + d.klo : k - d.ksplit + d.khi;
+                v[e] = theta[d.src + (int64_t)n * d.sn + (int64_t)col * d.sk];
+            }
+        }
+        uint4 w;
+        w.x = pack_bf16(v[0], v[1]);
+        w.y = pack_bf16(v[2], v[3]);
+        w.z = pack_bf16(v[4], v[5]);
+        w.w = pack_bf16(v[6], v[7]);
+        *reinterpret_cast<uint4*>(img + d.dst + tc::sw128_chunk(d.rows, n, kb, c)) = w;
+        return;
+    }
+}
+
+int tiles_of(int64_t N) { return (int)((N + kRows - 1) / kRows); }
+int chunks_of(int tiles) { return std::max(1, std::min(tiles, 30)); }
+
+std::once_flag g_attr_once;
+cudaError_t g_attr_err = cudaSuccess;
+void set_smem_attributes() {
+    std::call_once(g_attr_once, [] {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+        g_attr_err = e;
+    });
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// Layout of the state buffers (mlp_sizes): theta16 = forward images, backward images, bias;
+// act = h^T tiles, gamma^T tiles, masks; scratch = dz^T tiles, dd^T tiles, partials.
+struct ActLayout {
+    size_t ht, gt, total;
+};
+ActLayout act_layout(int64_t N) {
+    const size_t tiles = (size_t)tiles_of(std::max<int64_t>(N, 1));
+    ActLayout a;
+    a.ht = 0;
+    a.gt = tiles * kHtTile;
+    a.total = a.gt + tiles * kGtTile;
+    return a;
+}
+struct ScratchLayout {
+    size_t dzt, ddt, partial, total;
+};
+ScratchLayout scratch_layout(int64_t N) {
+    const int tiles = tiles_of(std::max<int64_t>(N, 1));
+    ScratchLayout s;
+    s.dzt = 0;
+    s.ddt = (size_t)tiles * kHtTile;
+    s.partial = s.ddt + (size_t)tiles * kDdTile;
+    s.total = s.partial + (size_t)kParts * chunks_of(tiles) * kWidth * kWidth * sizeof(float);
+    return s;
 }
 
 }  // namespace
-
-MlpLt* mlp_lt_create(std::string* err) {
-    MlpLt* lt = new MlpLt();
-    if (cublasLtCreate(&lt->h) != CUBLAS_STATUS_SUCCESS) {
-        *err = "cublasLtCreate failed";
-        delete lt;
-        return nullptr;
-    }
-    if (cudaMalloc(&lt->ws, lt->ws_size) != cudaSuccess) {
-        *err = "cuBLASLt workspace allocation failed";
-        cublasLtDestroy(lt->h);
-        delete lt;
-        return nullptr;
-    }
-    return lt;
-}
-
-void mlp_lt_destroy(MlpLt* lt) {
-    if (!lt) return;
-    cudaFree(lt->ws);
-    cublasLtDestroy(lt->h);
-    delete lt;
-}
 
 int64_t mlp_param_count() { return layer_offset(kHidden + 1); }
 
-namespace {
-// bytes of one hidden layer's ReLU bit-mask: 256 bits (32 bytes) per row, rows padded to 128
-size_t mask_bytes(int64_t N) { return (size_t)((N + 127) / 128 * 128) * (kWidth / 8); }
-}  // namespace
-
-// element offset of the padded output layer in the bfloat16 parameter buffer (8 elements = 16 bytes)
-int64_t head16_offset() { return (mlp_param_count() + 7) / 8 * 8; }
-
 MlpSizes mlp_sizes(int64_t N) {
     MlpSizes z;
-    // activations: x5 and seven 256-wide layers, then the eight hidden layers' ReLU bit-masks
-    z.act = (size_t)N * (kX5 + 7 * kWidth) * sizeof(__nv_bfloat16) + mask_bytes(N) * kHidden;
-    // dh [N, 256], dz [N, 256], encoding gradients [N, 80] x 2, dL/dd [N, 16]; the padded output
-    // layer's weight gradient [16, 256] (fp32)
-    z.scratch = (size_t)N * (2 * kWidth + 2 * kInPad + kOutPad) * sizeof(__nv_bfloat16) +
-                kOutPad * kWidth * sizeof(float);
-    z.out = (size_t)N * kOutPad * sizeof(float);
-    // the bfloat16 parameters, then (16-byte aligned) the padded [16, 256] output layer
-    z.theta16 = (size_t)(head16_offset() + kOutPad * kWidth) * sizeof(__nv_bfloat16);
+    z.act = act_layout(N).total;
+    z.scratch = scratch_layout(N).total;
+    z.out = (size_t)std::max<int64_t>(N, 1) * kOutPad * sizeof(float);
+    z.theta16 = (size_t)kFwdImgBytes + kBwdImgBytes + kBiasFloats * sizeof(float);
     return z;
 }
 
-namespace {
-// activation buffer: x5 [N, 336] then h0..h3, h5..h7 [N, 256] each
-__nv_bfloat16* act_x5(void* act) { return static_cast<__nv_bfloat16*>(act); }
-__nv_bfloat16* act_h(void* act, int64_t N, int l) {
-    const int slot = l < 4 ? l : l - 1;  // h0..h3 -> 0..3, h5..h7 -> 4..6 (h4 lives in x5)
-    return act_x5(act) + (size_t)N * kX5 + (size_t)slot * N * kWidth;
-}
-// ReLU bit-mask of hidden layer l, written by its forward product: bit m + 256 n is set when
-// activation m of row n is positive (row n's 256 bits are bytes 32 n .. 32 n + 31)
-uint8_t* act_mask(void* act, int64_t N, int l) {
-    return reinterpret_cast<uint8_t*>(act_x5(act) + (size_t)N * (kX5 + 7 * kWidth)) + (size_t)l * mask_bytes(N);
-}
-}  // namespace
-
-std::string mlp_forward(MlpLt& lt, const float* params3, int64_t N, float t, const float* theta, void* theta16_buf,
-                        void* act, float* d, float* params_out, cudaStream_t s) {
+std::string mlp_forward(const float* params3, int64_t N, float t, const float* theta, void* theta16_buf, void* act,
+                        float* d, float* params_out, unsigned int* err, cudaStream_t s) {
     if (N == 0) return "";
-    __nv_bfloat16* w16 = static_cast<__nv_bfloat16*>(theta16_buf);
-    const int64_t P = mlp_param_count();
-    launch_pdl(k_to_bf16, (unsigned)std::min<int64_t>(ceil_div(P, 256), 1024), 256, 0, s, theta, w16, P);
-    launch_pdl(k_mlp_head16, 1u, kWidth, 0, s, theta + layer_offset(kHidden), w16 + head16_offset());
+    set_smem_attributes();
+    if (g_attr_err != cudaSuccess) return std::string("deformation network: ") + cudaGetErrorString(g_attr_err);
+    static const ImgTable tab = make_images();
+    uint8_t* img = static_cast<uint8_t*>(theta16_buf);
+    float* bias = reinterpret_cast<float*>(img + kFwdImgBytes + kBwdImgBytes);
+    int64_t chunks = 0;
+    for (int i = 0; i < tab.n; ++i) chunks += (int64_t)tab.d[i].rows * tab.d[i].nkb * 8;
+    launch_pdl(k_mlp_pack, ceil_div(std::max<int64_t>(chunks, kBiasFloats), 256), 256, 0, s, theta, tab, img, bias);
+    const ActLayout a = act_layout(N);
+    uint8_t* ab = static_cast<uint8_t*>(act);
+    FwdArgs P;
+    P.params3 = params3;
+    P.N = N;
+    P.t = t;
+    P.wimg = img;
+    P.bias = bias;
+    P.d = d;
+    P.params_out = params_out;
+    P.ht = ab + a.ht;
+    P.gt = ab + a.gt;
+    P.err = err;
+    P.tiles = tiles_of(N);
+    P.vec = ((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(params_out)) & 15u) == 0;
+    const int grid = std::min(P.tiles, sm_count());
+    launch_pdl(k_mlp_fwd, grid, kTcThreads, kFwdSmem, s, P);
     count_launches(2);
-    __nv_bfloat16* x5 = act_x5(act);
-    launch_pdl(k_mlp_encode, ceil_div(N * kInPad, 256), 256, 0, s, params3, N, t, x5);
-    count_launches(1);
-    for (int l = 0; l <= kHidden; ++l) {
-        // input: the encoding (layer 0, the first 80 columns of x5), (gamma, h4) (layer 5, all of
-        // x5), else the previous layer's output; layer 4 writes h4 into columns 80.. of x5
-        const void* x = (l == 0 || l == kSkipLayer) ? (const void*)x5 : (const void*)act_h(act, N, l - 1);
-        const int ldx = (l == 0 || l == kSkipLayer) ? kX5 : kWidth;
-        void* y = l == kHidden ? (void*)d : (l == 4 ? (void*)(x5 + kInPad) : (void*)act_h(act, N, l));
-        const int ldy = l == kHidden ? kOutPad : (l == 4 ? kX5 : kWidth);
-        const int64_t boff = layer_offset(l) + (int64_t)kShapes[l].out * kShapes[l].in;
-        const __nv_bfloat16* wl = l == kHidden ? w16 + head16_offset() : w16 + layer_offset(l);
-        const std::string e =
-            layer_forward(lt, l, wl, w16 + boff, x, ldx, y, ldy, N, l == kHidden ? nullptr : act_mask(act, N, l), s);
-        if (!e.empty()) return e;
-    }
-    const float* b_head = theta + layer_offset(kHidden) + (int64_t)kOut * kWidth;
-    if (((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(params_out)) & 15u) == 0)
-        launch_pdl(k_mlp_apply<true>, ceil_div(N, 256), 256, 0, s, params3, N, d, b_head, params_out);
-    else
-        launch_pdl(k_mlp_apply<false>, ceil_div(N, 256), 256, 0, s, params3, N, d, b_head, params_out);
-    count_launches(1);
     return "";
 }
 
-std::string mlp_backward(MlpLt& lt, const float* params3, int64_t N, const void* theta16_buf, const void* act,
-                         const float* d, void* scratch, const float* g_out, float* g_theta, float* g_params3,
-                         int accumulate, cudaStream_t s) {
+std::string mlp_backward(const float* params3, int64_t N, const void* theta16_buf, const void* act, const float* d,
+                         void* scratch, const float* g_out, float* g_theta, float* g_params3, int accumulate,
+                         unsigned int* err, cudaStream_t s) {
     if (N == 0) return "";
-    const __nv_bfloat16* w16 = static_cast<const __nv_bfloat16*>(theta16_buf);
-    const __nv_bfloat16* whead16 = w16 + head16_offset();  // [16, 256], rows 13..15 zero
-    void* actm = const_cast<void*>(act);
-    const __nv_bfloat16* x5 = act_x5(actm);
-    // scratch layout (see mlp_sizes)
-    __nv_bfloat16* dh = static_cast<__nv_bfloat16*>(scratch);  // [N, 256] before the ReLU mask
-    __nv_bfloat16* dz = dh + (size_t)N * kWidth;                // [N, 256] after it
-    __nv_bfloat16* dg0 = dz + (size_t)N * kWidth;               // [N, 80] through layer 0
-    __nv_bfloat16* dgs = dg0 + (size_t)N * kInPad;              // [N, 80] through the skip input of layer 5
-    __nv_bfloat16* gd = dgs + (size_t)N * kInPad;               // [N, 16]
-    float* dw_head16 = reinterpret_cast<float*>(gd + (size_t)N * kOutPad);  // [16, 256]
+    set_smem_attributes();
+    if (g_attr_err != cudaSuccess) return std::string("deformation network: ") + cudaGetErrorString(g_attr_err);
+    const uint8_t* img = static_cast<const uint8_t*>(theta16_buf);
+    const ActLayout a = act_layout(N);
+    const ScratchLayout sl = scratch_layout(N);
+    const uint8_t* ab = static_cast<const uint8_t*>(act);
+    uint8_t* sb = static_cast<uint8_t*>(scratch);
+    const int tiles = tiles_of(N);
     if (!accumulate) cudaMemsetAsync(g_theta, 0, sizeof(float) * (size_t)mlp_param_count(), s);
-    float* db_head = g_theta + layer_offset(kHidden) + (int64_t)kOut * kWidth;
-    const uintptr_t rows = reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(g_out) |
-                           reinterpret_cast<uintptr_t>(g_params3);
-    if ((rows & 15u) == 0)
-        launch_pdl(k_mlp_apply_backward<true>, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3,
-                   accumulate, db_head);
-    else
-        launch_pdl(k_mlp_apply_backward<false>, ceil_div(N, 256), 256, 0, s, params3, N, d, g_out, gd, g_params3,
-                   accumulate, db_head);
-    count_launches(1);
-    std::string e;
-    // output layer (padded to 16 rows): dW_8 = gd^T h7 into [16, 256]; dh7 = gd W_8
-    e = gemm(lt, false, true, kWidth, kOutPad, (int)N, act_h(actm, N, 7), kWidth, gd, kOutPad, dw_head16, kWidth,
-             CUDA_R_32F, 0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-    if (!e.empty()) return e;
-    e = gemm(lt, false, false, kWidth, (int)N, kOutPad, whead16, kWidth, gd, kOutPad, dh, kWidth, CUDA_R_16BF, 0.f,
-             CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-    if (!e.empty()) return e;
-    for (int l = kHidden - 1; l >= 0; --l) {
-        const LayerShape sh = kShapes[l];
-        const __nv_bfloat16* wl = w16 + layer_offset(l);
-        float* gb = g_theta + layer_offset(l) + (int64_t)sh.out * sh.in;
-        launch_pdl(k_relu_backward, (unsigned)std::min<int64_t>(kReluBlocks, ceil_div(N, 8)), 256, 0, s,
-                   (const __nv_bfloat16*)dh, kWidth, (const uint8_t*)act_mask(actm, N, l), N, dz, gb);
-        count_launches(1);
-        // dW_l += dz_l^T x_l  (column-major [in, out] = x^T (in x N) dz (N x out))
-        const void* xin = (l == 0 || l == kSkipLayer) ? (const void*)x5 : (const void*)act_h(actm, N, l - 1);
-        const int ldx = (l == 0 || l == kSkipLayer) ? kX5 : kWidth;
-        e = gemm(lt, false, true, sh.in, sh.out, (int)N, xin, ldx, dz, kWidth, g_theta + layer_offset(l), sh.in,
-                 CUDA_R_32F, 1.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        if (!e.empty()) return e;
-        // input gradient dz_l W_l (W_l row-major [out, in] = column-major [in, out]) into dh for layer
-        // l - 1; layer 5 splits it into the encoding's part and h4's, layer 0 has only the encoding's
-        if (l == 0) {
-            e = gemm(lt, false, false, kInPad, (int)N, kWidth, wl, kInPad, dz, kWidth, dg0, kInPad, CUDA_R_16BF, 0.f,
-                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        } else if (l == kSkipLayer) {
-            e = gemm(lt, false, false, kInPad, (int)N, kWidth, wl, kX5, dz, kWidth, dgs, kInPad, CUDA_R_16BF, 0.f,
-                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-            if (!e.empty()) return e;
-            e = gemm(lt, false, false, kWidth, (int)N, kWidth, wl + kInPad, kX5, dz, kWidth, dh, kWidth, CUDA_R_16BF,
-                     0.f, CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        } else {
-            e = gemm(lt, false, false, kWidth, (int)N, kWidth, wl, kWidth, dz, kWidth, dh, kWidth, CUDA_R_16BF, 0.f,
-                     CUBLASLT_EPILOGUE_DEFAULT, nullptr, s);
-        }
-        if (!e.empty()) return e;
-    }
-    launch_pdl(k_mlp_add_head_dw, 1u, kWidth, 0, s, (const float*)dw_head16, g_theta, layer_offset(kHidden));
-    launch_pdl(k_mlp_encode_backward, ceil_div(N, 256), 256, 0, s, params3, N, (const __nv_bfloat16*)dg0,
-               (const __nv_bfloat16*)dgs, g_params3);
-    count_launches(2);
+    BwdArgs B;
+    B.params3 = params3;
+    B.N = N;
+    B.wimg = img + kFwdImgBytes;
+    B.d = d;
+    B.g_out = g_out;
+    B.g_params3 = g_params3;
+    B.accumulate = accumulate;
+    B.ht = ab + a.ht;
+    B.dzt = sb + sl.dzt;
+    B.ddt = sb + sl.ddt;
+    B.g_theta = g_theta;
+    B.err = err;
+    B.tiles = tiles;
+    B.vec = ((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(g_out) |
+              reinterpret_cast<uintptr_t>(g_params3)) & 15u) == 0;
+    const int n_sm = sm_count();
+    launch_pdl(k_mlp_bwd, std::min(tiles, n_sm), kTcThreads, kBwdSmem, s, B);
+    WgArgs W;
+    W.ht = ab + a.ht;
+    W.gt = ab + a.gt;
+    W.dzt = B.dzt;
+    W.ddt = B.ddt;
+    W.partial = reinterpret_cast<float*>(sb + sl.partial);
+    W.tiles = tiles;
+    W.chunks = chunks_of(tiles);
+    W.err = err;
+    launch_pdl(k_mlp_wgrad, std::min(kParts * W.chunks, n_sm), kWgThreads, kWgSmem, s, W);
+    const int64_t nw = mlp_param_count() - (int64_t)kHidden * kWidth - kOut;  // weights (no biases)
+    launch_pdl(k_mlp_wsum, ceil_div(nw, 256), 256, 0, s, (const float*)W.partial, W.chunks, g_theta);
+    count_launches(3);
     return "";
 }
 
