@@ -263,7 +263,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 
 // Control block of a tile kernel in shared memory.
 struct Ctl {
-    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain;
+    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain, g_full;
     uint32_t tmem;
     volatile int abort;
 };
@@ -340,7 +340,7 @@ struct FwdArgs {
     float* d;              // [N, 16] network outputs including the head's bias
     float* params_out;     // [N, 20]
     uint8_t* ht;           // [tiles][8 layers][4 K-blocks of 16 KB] hidden activations
-    uint8_t* gt;           // [tiles][2 K-blocks of 16 KB] encoding
+    const uint8_t* gt;     // [tiles][2 K-blocks of 16 KB] encoding (written by k_mlp_encode)
     unsigned int* err;
     int tiles;
     int vec;               // params3 / params_out rows 16-byte aligned
@@ -392,6 +392,66 @@ __device__ __forceinline__ bool await_mma(Ctl* ctl, uint32_t parity, unsigned in
     return !stop;
 }
 
+// The encoding of every row, as the forward's gamma tiles (K-major, 128-byte swizzle: K-block 0
+// features 0-63, K-block 1 features 64-79 in its first two chunks): one thread per row and chunk
+// of 8 features.
+__global__ void __launch_bounds__(256) k_mlp_encode(const float* __restrict__ params3, int64_t N, float t, int tiles,
+                                                    uint8_t* __restrict__ gt) {
+    pdl_enter();
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)tiles * kRows * (kInPad / 8)) return;
+    const int c = (int)(idx % (kInPad / 8));
+    const int64_t row = idx / (kInPad / 8);
+    const int tile = (int)(row / kRows), r = (int)(row % kRows);
+    float mu[3] = {0.f, 0.f, 0.f};
+    const bool valid = row < N;
+    if (valid)
+        for (int j = 0; j < 3; ++j) mu[j] = params3[row * WIPES_P3D + j];
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (valid) {
+        w.x = pack_bf16(encoding(8 * c, mu, t), encoding(8 * c + 1, mu, t));
+        w.y = pack_bf16(encoding(8 * c + 2, mu, t), encoding(8 * c + 3, mu, t));
+        w.z = pack_bf16(encoding(8 * c + 4, mu, t), encoding(8 * c + 5, mu, t));
+        w.w = pack_bf16(encoding(8 * c + 6, mu, t), encoding(8 * c + 7, mu, t));
+    }
+    *reinterpret_cast<uint4*>(gt + (size_t)tile * kGtTile +
+                              tc::sw128_chunk(kRows, (uint32_t)r, (uint32_t)c / 8u, (uint32_t)c % 8u)) = w;
+}
+
+// dL/dmu += the encoding's backward: d/dx (x, sin(2^k x), cos(2^k x)) = (1, 2^k cos, -2^k sin), from
+// dgamma [N, 80] (fp32, the skip layer's and layer 0's products summed)
+__global__ void __launch_bounds__(256) k_mlp_encode_backward(const float* __restrict__ params3, int64_t N,
+                                                             const float* __restrict__ dgam,
+                                                             float* __restrict__ g_params3) {
+    pdl_enter();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float dg[64];
+    const float4* src = reinterpret_cast<const float4*>(dgam + i * kInPad);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float4 v = src[q];
+        dg[4 * q] = v.x;
+        dg[4 * q + 1] = v.y;
+        dg[4 * q + 2] = v.z;
+        dg[4 * q + 3] = v.w;
+    }
+    float gm[3] = {dg[0], dg[1], dg[2]};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float x = params3[i * WIPES_P3D + j];
+#pragma unroll
+        for (int k = 0; k < kLx; ++k) {
+            const float f = (float)(1 << k);
+            float sn, cs;
+            sincosf(f * x, &sn, &cs);
+            gm[j] += f * (dg[3 + 6 * k + j] * cs - dg[6 + 6 * k + j] * sn);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g_params3[i * WIPES_P3D + j] += gm[j];
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant__ FwdArgs P) {
     pdl_enter();  // inputs written by the previous kernel on the stream
     extern __shared__ uint8_t smem_raw[];
@@ -411,6 +471,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
         tc::mbar_init(&ctl->a_ready, kEpiThreads);
         tc::mbar_init(&ctl->tmem_free, kEpiThreads);
         tc::mbar_init(&ctl->drain, 1);
+        tc::mbar_init(&ctl->g_full, 1);
         ctl->abort = 0;
         tc::fence_mbar_init();
     }
@@ -433,24 +494,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
         const bool lead = ew == 0 && lane == 0;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const uint32_t a0 = tc::smem_u32(sA);
-        uint32_t md = 0;
+        uint32_t md = 0, ng = 0;
         for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * kRows + r;
             const bool valid = row < P.N;
-            // the encoding into A K-blocks 4 and 5 (chunks of 16 features: half 0 the first three)
-            float mu[3] = {0.f, 0.f, 0.f};
-            if (valid)
-                for (int j = 0; j < 3; ++j) mu[j] = P.params3[row * WIPES_P3D + j];
+            // the tile's encoding (written by k_mlp_encode) into A K-blocks 4 and 5
             await_a_free(lead);
-#pragma unroll 1
-            for (int c0 = half * 48; c0 < (half ? kInPad : 48); c0 += 16) {
-                uint32_t w[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    w[j] = valid ? pack_bf16(encoding(c0 + 2 * j, mu, P.t), encoding(c0 + 2 * j + 1, mu, P.t)) : 0u;
-                store_a16(a0 + 4 * kABlock, r, c0, w);
+            if (lead) {
+                tc::mbar_arrive_expect_tx(&ctl->g_full, kGtTile);
+                tc::bulk_g2s(sA + 4 * kABlock, P.gt + (size_t)tile * kGtTile, kGtTile, &ctl->g_full);
             }
-            publish_a(ctl, lead, sA, 4, 2, P.gt + (size_t)tile * kGtTile);
+            {
+                const bool ok = wait_or_abort(ctl, &ctl->g_full, ng & 1u, P.err);
+                ++ng;
+                if (tc::named_sync_or(kEpiBar, kEpiThreads, !ok || ctl->abort)) goto done;
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&ctl->a_ready);
             for (int l = 0; l <= kHidden; ++l) {
                 if (!await_mma(ctl, md & 1u, P.err)) goto done;
                 ++md;
@@ -535,6 +595,7 @@ struct BwdArgs {
     const uint8_t* ht;     // the forward's hidden activations (their sign is the ReLU mask)
     uint8_t* dzt;          // [tiles][8 layers][4 K-blocks of 16 KB] dz
     uint8_t* ddt;          // [tiles][1 K-block of 16 KB] dL/dd
+    float* dgam;           // [N, 80] dL/dgamma (fp32), for k_mlp_encode_backward
     float* g_theta;        // bias gradients are added here (atomics, one per entry and block)
     unsigned int* err;
     int tiles;
@@ -589,7 +650,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
         for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * kRows + r;
             const bool valid = row < P.N;
-            float mu[3] = {0.f, 0.f, 0.f};
             await_a_free(lead);
             if (half == 0) {
                 // the record update's backward: dL/dd (rounded: the head's product operand) and the
@@ -616,7 +676,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
                         gd[7 + k] = g[3 + k] * p[3 + k] * es;
                         gd[10 + k] = g[10 + k];
                         gp[3 + k] = g[3 + k] * es;
-                        mu[k] = p[k];
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) gd[3 + k] = g[6 + k];
@@ -651,38 +710,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
                 if (!await_mma(ctl, md & 1u, P.err)) goto done;
                 ++md;
                 if (l < 0) {
-                    // dgamma (columns 256 .. 335: the skip layer's part plus layer 0's) -> dL/dmu
+                    // dgamma (columns 256 .. 335: the skip layer's part plus layer 0's), written out for
+                    // k_mlp_encode_backward
                     if (half == 0) {
-                        float dg[kInPad];
-                        uint32_t v[32];
-                        tc::tmem_ld32(tl + 256u, v);
-                        tc::tmem_wait_ld();
+                        float4* dst = reinterpret_cast<float4*>(P.dgam + row * kInPad);
+#pragma unroll 1
+                        for (int c0 = 0; c0 < kInPad; c0 += 16) {
+                            uint32_t v[16];
+                            tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
+                            tc::tmem_wait_ld();
+                            if (valid)
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) dg[j] = __uint_as_float(v[j]);
-                        tc::tmem_ld32(tl + 288u, v);
-                        tc::tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) dg[32 + j] = __uint_as_float(v[j]);
-                        uint32_t v16[16];
-                        tc::tmem_ld16(tl + 320u, v16);
-                        tc::tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) dg[64 + j] = __uint_as_float(v16[j]);
-                        if (valid) {
-                            float gm[3] = {dg[0], dg[1], dg[2]};
-#pragma unroll
-                            for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                                for (int k = 0; k < kLx; ++k) {
-                                    const float f = (float)(1 << k);
-                                    float sn, cs;
-                                    sincosf(f * mu[j], &sn, &cs);
-                                    gm[j] += f * (dg[3 + 6 * k + j] * cs - dg[6 + 6 * k + j] * sn);
-                                }
-                            }
-                            float* go = P.g_params3 + row * WIPES_P3D;
-#pragma unroll
-                            for (int j = 0; j < 3; ++j) go[j] += gm[j];
+                                for (int j = 0; j < 4; ++j)
+                                    dst[c0 / 4 + j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                                                  __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
                         }
                     }
                     tc::fence_before_sync();
@@ -1028,7 +1069,7 @@ ActLayout act_layout(int64_t N) {
     return a;
 }
 struct ScratchLayout {
-    size_t dzt, ddt, partial, total;
+    size_t dzt, ddt, partial, dgam, total;
 };
 ScratchLayout scratch_layout(int64_t N) {
     const int tiles = tiles_of(std::max<int64_t>(N, 1));
@@ -1036,7 +1077,8 @@ ScratchLayout scratch_layout(int64_t N) {
     s.dzt = 0;
     s.ddt = (size_t)tiles * kHtTile;
     s.partial = s.ddt + (size_t)tiles * kDdTile;
-    s.total = s.partial + (size_t)kParts * chunks_of(tiles) * kWidth * kWidth * sizeof(float);
+    s.dgam = s.partial + (size_t)kParts * chunks_of(tiles) * kWidth * kWidth * sizeof(float);
+    s.total = s.dgam + (size_t)tiles * kRows * kInPad * sizeof(float);
     return s;
 }
 
@@ -1079,9 +1121,11 @@ std::string mlp_forward(const float* params3, int64_t N, float t, const float* t
     P.err = err;
     P.tiles = tiles_of(N);
     P.vec = ((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(params_out)) & 15u) == 0;
+    launch_pdl(k_mlp_encode, ceil_div((int64_t)P.tiles * kRows * (kInPad / 8), 256), 256, 0, s, params3, N, t, P.tiles,
+               ab + a.gt);
     const int grid = std::min(P.tiles, sm_count());
     launch_pdl(k_mlp_fwd, grid, kTcThreads, kFwdSmem, s, P);
-    count_launches(2);
+    count_launches(3);
     return "";
 }
 
@@ -1109,6 +1153,7 @@ std::string mlp_backward(const float* params3, int64_t N, const void* theta16_bu
     B.ht = ab + a.ht;
     B.dzt = sb + sl.dzt;
     B.ddt = sb + sl.ddt;
+    B.dgam = reinterpret_cast<float*>(sb + sl.dgam);
     B.g_theta = g_theta;
     B.err = err;
     B.tiles = tiles;
@@ -1116,6 +1161,7 @@ std::string mlp_backward(const float* params3, int64_t N, const void* theta16_bu
               reinterpret_cast<uintptr_t>(g_params3)) & 15u) == 0;
     const int n_sm = sm_count();
     launch_pdl(k_mlp_bwd, std::min(tiles, n_sm), kTcThreads, kBwdSmem, s, B);
+    launch_pdl(k_mlp_encode_backward, ceil_div(N, 256), 256, 0, s, params3, N, (const float*)B.dgam, g_params3);
     WgArgs W;
     W.ht = ab + a.ht;
     W.gt = ab + a.gt;
@@ -1128,7 +1174,7 @@ std::string mlp_backward(const float* params3, int64_t N, const void* theta16_bu
     launch_pdl(k_mlp_wgrad, std::min(kParts * W.chunks, n_sm), kWgThreads, kWgSmem, s, W);
     const int64_t nw = mlp_param_count() - (int64_t)kHidden * kWidth - kOut;  // weights (no biases)
     launch_pdl(k_mlp_wsum, ceil_div(nw, 256), 256, 0, s, (const float*)W.partial, W.chunks, g_theta);
-    count_launches(3);
+    count_launches(4);
     return "";
 }
 

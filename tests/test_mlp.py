@@ -2,20 +2,22 @@
 oracle with the device's bfloat16 operand roundings emulated.
 
 Tolerance.  Both sides round the same operands to bfloat16 at the same points; they differ by the
-accumulation (fp32 on the device, binary64 in the oracle, ~1e-6 relative) and, where an fp32 value
-falls within that distance of a bfloat16 rounding boundary, by one bfloat16 unit (2^-8 relative)
-of that activation, which propagates.  Such flips are rare (~1e-5 of the activations), so an
-output or gradient entry moves by at most a few 2^-8 of the scale of the sum it is made of:
-|d_dev - d*| <= 4 2^-8 A + 1e-6 with A the sum of |terms| of the output layer for the outputs,
-and 2^-6 of the |products| sum for the parameter gradients.
+accumulation (fp32 in the tensor cores, binary64 in the oracle, ~1e-6 relative) and, where an fp32
+value falls within that distance of a bfloat16 rounding boundary, by one bfloat16 unit (2^-8
+relative) of that activation, which propagates.  Measured on the device: output errors stay below
+0.22 2^-8 A (A the sum of |terms| of the output layer, median 1e-4 2^-8 A), so outputs are checked
+at 2^-9 A; parameter-gradient errors exceed 2^-10 of their |products| sum for at most 0.2 % of
+the entries, so every entry is checked at 2^-8 of that sum (plus the single-row term below) and
+99.9 % of them without the single-row term.
 
 A ReLU decision close to 0 can go either way: under the accumulation difference directly, or
 after a bfloat16 flip upstream has moved its pre-activation by a unit of that flip.  It then moves
 a whole row's term of the gradient (|dh| |x| before the mask, not a rounding of it).  The oracle
 flags the rows with a pre-activation within the accumulation error of 0, and the backward checks
 give them a zero upstream gradient; the rare decisions moved by upstream flips are covered by
-adding a few times the largest single-row term to the parameter gradients' tolerance, and by
-requiring the centre gradient of at least 97 % of the rows to agree.
+adding twice the largest single-row term (measured at most 0.7 of it) to the parameter
+gradients' tolerance, and by requiring the centre gradient of at least 99.5 % of the rows to
+agree within 2^-10 of its scale.
 """
 import numpy as np
 import pytest
@@ -66,7 +68,7 @@ def test_deform_mlp_forward_matches_oracle(N, seed, t):
     rec_ulp[:, 3:7] = np.spacing(np.abs(q[:, 6:10]).astype(np.float32))
     rec_ulp[:, 7:10] = 2e-7
     rec_ulp[:, 10:13] = np.spacing(np.abs(q[:, 10:13]).astype(np.float32))
-    tol = 4 * 2.0 ** -8 * A + 1e-6 + 2 * rec_ulp
+    tol = 2.0 ** -9 * A + 1e-6 + 2 * rec_ulp
     err = np.abs(d_dev - d_ref)
     assert np.all(err <= tol), (err / tol).max()
     # the fields the network does not touch are copied
@@ -88,10 +90,10 @@ def test_deform_mlp_backward_matches_oracle(N, seed, t):
     gth_ref, dmu, gabs, gmax = M.backward(p[:, 0:3], cache, gd, with_abs=True)
     gp_ref[:, 0:3] += dmu
     err = np.abs(gth.cpu().numpy() - gth_ref)
-    tol = 2.0 ** -6 * gabs + 4.0 * gmax + 1e-6 * np.abs(gth_ref).max()
+    tol = 2.0 ** -8 * gabs + 2.0 * gmax + 1e-6 * np.abs(gth_ref).max()
     assert np.all(err <= tol), (err / tol).max()
     # the same bound without the single-row term holds for nearly every entry
-    assert np.mean(err > 2.0 ** -6 * gabs + 1e-6 * np.abs(gth_ref).max()) < 1e-3
+    assert np.mean(err > 2.0 ** -8 * gabs + 1e-6 * np.abs(gth_ref).max()) < 1e-3
     gp_dev = gp.cpu().numpy()
     # direct terms: rotation, frequency, phase, opacity and colour pass dL/d(deformed) through
     cols = list(range(6, 20))
@@ -99,12 +101,12 @@ def test_deform_mlp_backward_matches_oracle(N, seed, t):
     # the scale's is dL/ds' exp(dlog s): exp of a network output, within the forward bound
     W8, b8 = cache["layers"][-1]
     A = np.abs(cache["hs"][-1]) @ np.abs(M.bf16(W8)).T + np.abs(b8)
-    tol_s = np.abs(gp_ref[:, 3:6]) * (4 * 2.0 ** -8 * A[:, 7:10] + 1e-6) + 1e-7
+    tol_s = np.abs(gp_ref[:, 3:6]) * (2.0 ** -9 * A[:, 7:10] + 1e-6) + 1e-7
     assert np.all(np.abs(gp_dev[:, 3:6] - gp_ref[:, 3:6]) <= tol_s)
     # the centre: the direct term plus the network's gradient through gamma(x)
     scale = np.abs(gp_ref[:, 0:3]).max(axis=0)
-    rows_ok = np.all(np.abs(gp_dev[:, 0:3] - gp_ref[:, 0:3]) <= 2.0 ** -6 * scale, axis=1)
-    assert rows_ok.mean() >= 0.97
+    rows_ok = np.all(np.abs(gp_dev[:, 0:3] - gp_ref[:, 0:3]) <= 2.0 ** -10 * scale, axis=1)
+    assert rows_ok.mean() >= 0.995
 
 
 def test_deform_mlp_backward_accumulates():
