@@ -9,26 +9,29 @@
 //   deformed record: mu + dx, q + dq, s exp(dlog s), f + df (phase, opacity, colour kept).
 // Parameters theta: packed float32, per layer W (out x in, row-major) then b (out).
 //
-// Every product runs on the 5th-generation tensor cores (tcgen05, bfloat16 operands, fp32
-// accumulation in tensor memory), in three hand-written kernels:
-//   k_mlp_fwd   one 128-row tile at a time: the encoding, the nine layers and the record update.
-//               The activations stay in shared memory between layers (each layer's output is the
-//               next layer's A operand); the weights stream in by bulk copies, one 64-column
-//               K-block at a time, through a ring of stages.  For the backward it writes the ReLU
-//               bit masks and each layer's input, transposed (rows along K), in 128-row tiles.
+// Every product runs on the 5th-generation tensor cores (tcgen05.mma, bfloat16 operands, fp32
+// accumulation in tensor memory), in hand-written kernels:
+//   k_mlp_encode the positional encoding of every row, written as the tiles the forward loads.
+//   k_mlp_fwd   one 128-row tile at a time: the nine layers and the record update.  Each layer's
+//               output stays in shared memory as the next layer's A operand (K-major, 128-byte
+//               swizzle); the weights, packed once per call into the same layout (k_mlp_pack),
+//               stream in by bulk copies, one 64-column K-block at a time, through a ring of
+//               stages.  A copy of every layer's A operand goes to global memory for the backward.
 //   k_mlp_bwd   one tile at a time: the record update's backward, then dh = dz W through the
-//               layers (W transposed, the masks applied on chip), the bias gradients, and the
-//               encoding's backward to the centre.  It writes each layer's dz, transposed.
-//   k_mlp_wgrad the weight gradients dW_l = dz_l^T x_l: a product over all rows, split into row
-//               chunks (one partial per chunk), then k_mlp_wsum adds the partials in a fixed order.
+//               layers (W transposed), the ReLU mask taken from the stored activations (positive
+//               entries), the bias gradients; it writes each layer's dz and dL/dgamma.
+//   k_mlp_encode_backward  the encoding's backward to the centre.
+//   k_mlp_wgrad the weight gradients dW_l = dz_l^T x_l: a product over all rows (the stored tiles
+//               read as MN-major operands), split into row chunks (one partial per chunk), then
+//               k_mlp_wsum adds the partials in a fixed order.
 // Rounding points: the encoding, weights, hidden activations and upstream gradients are rounded
 // to bfloat16 where they become product operands; biases, accumulators, the network outputs and
 // the encoding's gradient (both products summed in one accumulator) stay fp32.
-// Warp roles in the tile kernels: warp 0 streams operands, warp 1 issues the MMAs (one thread),
-// warps 2-5 run the epilogue (thread = row: warp w reads TMEM lanes 32 (w % 4) ..).  Every wait on
-// an mbarrier is bounded; one that runs out sets bit 1 of the context's error word, every role
-// leaves its loop, in-flight copies and MMAs are waited for (bounded again), and the tensor
-// memory is freed before the block exits.
+// Warp roles in the tile kernels: warp 0 streams weights, warp 1 issues the MMAs (one thread),
+// warps 2-9 run the epilogue (thread = row; warp w reads TMEM lanes 32 (w % 4) .., warps 2-5 the
+// output columns 0-127, warps 6-9 128-255).  Every wait on an mbarrier is bounded (2 s); one that
+// runs out sets bit 1 of the context's error word, every role leaves its loop, in-flight copies
+// and MMAs are waited for, and the tensor memory is freed before the block exits.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -43,7 +46,6 @@ namespace wipes {
 namespace {
 
 constexpr int kLx = 10, kLt = 6;
-constexpr int kIn = 3 * (1 + 2 * kLx) + (1 + 2 * kLt);  // 76
 constexpr int kInPad = 80;
 constexpr int kWidth = 256;
 constexpr int kHidden = 8;
@@ -348,24 +350,6 @@ struct FwdArgs {
 
 constexpr uint32_t kFwdSmem = 1024 + 6 * kABlock + kStages * kWBlock + sizeof(Ctl);
 
-// gamma of one row (Sec. 4.3): columns 0-2 mu, then per octave k sin(2^k mu) (3), cos(2^k mu) (3);
-// column 63 t, then per octave sin(2^k t), cos(2^k t); 76-79 zero.
-__device__ __forceinline__ float encoding(int c, const float mu[3], float t) {
-    if (c < 3) return mu[c];
-    if (c < 3 + 6 * kLx) {
-        const int k = (c - 3) / 6, r = (c - 3) % 6;
-        const float x = mu[r % 3] * (float)(1 << k);
-        return r < 3 ? sinf(x) : cosf(x);
-    }
-    if (c == 3 + 6 * kLx) return t;
-    if (c < kIn) {
-        const int k = (c - 4 - 6 * kLx) / 2, r = (c - 4 - 6 * kLx) % 2;
-        const float x = t * (float)(1 << k);
-        return r == 0 ? sinf(x) : cosf(x);
-    }
-    return 0.f;
-}
-
 // The epilogue warps' hand-off around an A operand that they rewrite: the copy of its previous
 // contents to global memory (issued by one thread) must have read them first.
 __device__ __forceinline__ void await_a_free(bool lead) {
@@ -393,29 +377,35 @@ __device__ __forceinline__ bool await_mma(Ctl* ctl, uint32_t parity, unsigned in
 }
 
 // The encoding of every row, as the forward's gamma tiles (K-major, 128-byte swizzle: K-block 0
-// features 0-63, K-block 1 features 64-79 in its first two chunks): one thread per row and chunk
-// of 8 features.
+// features 0-63, K-block 1 features 64-79 in its first two chunks): one thread per row, one
+// sincosf per coordinate and octave (Sec. 4.3: gamma(p) = (p, sin 2^k p, cos 2^k p)).
 __global__ void __launch_bounds__(256) k_mlp_encode(const float* __restrict__ params3, int64_t N, float t, int tiles,
                                                     uint8_t* __restrict__ gt) {
     pdl_enter();
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)tiles * kRows * (kInPad / 8)) return;
-    const int c = (int)(idx % (kInPad / 8));
-    const int64_t row = idx / (kInPad / 8);
-    const int tile = (int)(row / kRows), r = (int)(row % kRows);
-    float mu[3] = {0.f, 0.f, 0.f};
-    const bool valid = row < N;
-    if (valid)
-        for (int j = 0; j < 3; ++j) mu[j] = params3[row * WIPES_P3D + j];
-    uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    if (valid) {
-        w.x = pack_bf16(encoding(8 * c, mu, t), encoding(8 * c + 1, mu, t));
-        w.y = pack_bf16(encoding(8 * c + 2, mu, t), encoding(8 * c + 3, mu, t));
-        w.z = pack_bf16(encoding(8 * c + 4, mu, t), encoding(8 * c + 5, mu, t));
-        w.w = pack_bf16(encoding(8 * c + 6, mu, t), encoding(8 * c + 7, mu, t));
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (int64_t)tiles * kRows) return;
+    float g[kInPad];
+#pragma unroll
+    for (int c = 0; c < kInPad; ++c) g[c] = 0.f;
+    if (row < N) {
+        float mu[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mu[j] = g[j] = params3[row * WIPES_P3D + j];
+#pragma unroll
+        for (int k = 0; k < kLx; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) sincosf(mu[j] * (float)(1 << k), &g[3 + 6 * k + j], &g[6 + 6 * k + j]);
+        g[3 + 6 * kLx] = t;
+#pragma unroll
+        for (int k = 0; k < kLt; ++k) sincosf(t * (float)(1 << k), &g[4 + 6 * kLx + 2 * k], &g[5 + 6 * kLx + 2 * k]);
     }
-    *reinterpret_cast<uint4*>(gt + (size_t)tile * kGtTile +
-                              tc::sw128_chunk(kRows, (uint32_t)r, (uint32_t)c / 8u, (uint32_t)c % 8u)) = w;
+    uint8_t* base = gt + (size_t)(row / kRows) * kGtTile;
+    const uint32_t r = (uint32_t)(row % kRows);
+#pragma unroll
+    for (int c = 0; c < kInPad / 8; ++c)
+        *reinterpret_cast<uint4*>(base + tc::sw128_chunk(kRows, r, (uint32_t)c / 8u, (uint32_t)c % 8u)) =
+            make_uint4(pack_bf16(g[8 * c], g[8 * c + 1]), pack_bf16(g[8 * c + 2], g[8 * c + 3]),
+                       pack_bf16(g[8 * c + 4], g[8 * c + 5]), pack_bf16(g[8 * c + 6], g[8 * c + 7]));
 }
 
 // dL/dmu += the encoding's backward: d/dx (x, sin(2^k x), cos(2^k x)) = (1, 2^k cos, -2^k sin), from
@@ -1121,8 +1111,7 @@ std::string mlp_forward(const float* params3, int64_t N, float t, const float* t
     P.err = err;
     P.tiles = tiles_of(N);
     P.vec = ((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(params_out)) & 15u) == 0;
-    launch_pdl(k_mlp_encode, ceil_div((int64_t)P.tiles * kRows * (kInPad / 8), 256), 256, 0, s, params3, N, t, P.tiles,
-               ab + a.gt);
+    launch_pdl(k_mlp_encode, ceil_div((int64_t)P.tiles * kRows, 256), 256, 0, s, params3, N, t, P.tiles, ab + a.gt);
     const int grid = std::min(P.tiles, sm_count());
     launch_pdl(k_mlp_fwd, grid, kTcThreads, kFwdSmem, s, P);
     count_launches(3);
