@@ -24,7 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 # opts vector layout shared by the 3D calls: cutoff, alpha_min, alpha_max, T_min, dilation, bg(3),
-# frequency projection mode (0: phase gradient on the fronto-parallel plane, 1: literal J W f),
+# frequency projection mode (0: phase gradient on the fronto-parallel plane, 1: literal J W f,
+# 2: the oscillation integrated along the viewing ray, damped by kappa),
 # spherical-harmonic colour degree (0: the record's RGB; 1..3: records of P3D_SH floats)
 DEFAULT_OPTS_3D = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 0.0, 0.0], dtype=np.float32)
 P3D_SH = 68
@@ -200,13 +201,14 @@ def rule_cos_sin(theta):
 def alpha_decisions(params, cam, H, W, pairs, opts=None):
     """Threshold-decision values (Eq. 3's alpha_min skip, alpha_max clamp and T_min stop are taken
     from the kernels' binary32 projected record).  pairs[n,3] = (primitive, u, v).  Returns
-    (rec[N,9] = mx, my, l11, l21, l22, f'x, f'y, phase in cycles, opacity as binary32,
+    (rec[N,10] = mx, my, l11, l21, l22, f'x, f'y, phase in cycles, opacity and, under frequency map 2,
+     the damping exponent kx (kappa = 2^kx; 0 otherwise) as binary32,
      out[n,3] = record alpha before the clamp (binary64), its kernel error bound, binary64-projection alpha)."""
     params = _f32(params)
     camv = _f32(cam)
     o = _opts3(opts)
     pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
-    rec = np.zeros((params.shape[0], 9), np.float32)
+    rec = np.zeros((params.shape[0], 10), np.float32)
     out = np.zeros((pr.shape[0], 3), np.float64)
     _load().wo_alpha_decisions(_ptr(params), params.shape[0], _ptr(camv), H, W, _ptr(o), _ptr(pr), pr.shape[0],
                                _ptr(rec), _ptr(out))
@@ -214,7 +216,8 @@ def alpha_decisions(params, cam, H, W, pairs, opts=None):
 
 
 def project3d(params, cam, H, W, opts=None):
-    """[N,16]: valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), 0, 0."""
+    """[N,16]: valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), kappa, 0
+    (kappa: the damping of the oscillation, 1 except under frequency map 2)."""
     params = _f32(params)
     camv = _f32(cam)
     o = _opts3(opts)

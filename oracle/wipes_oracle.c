@@ -35,6 +35,7 @@
  * bit; pixels where one of them is within a small margin of its threshold are reported as
  * ambiguous.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -43,6 +44,7 @@
 #define TILE 16
 #define EXT_MARGIN 1.0009765625f /* 1 + 2^-10: footprint half-extent safety factor */
 #define INV_TWO_PI_F 0.15915494309189535f /* 1 / (2 pi) rounded to binary32: phase in cycles */
+#define DAMP_EXP2_F 28.47765864997501f   /* 2 pi^2 log2(e) rounded to binary32: kappa = 2^-(this fn^2 / c) */
 
 static const double PI = 3.14159265358979323846;
 
@@ -57,11 +59,12 @@ typedef struct {
     float depth;           /* camera z (3D), 0 (2D) */
     int u0, v0, u1, v1;    /* covered pixel range (inclusive); empty if u0 > u1 */
     int valid;
-    /* 3D only: the record's binary32 projected frequency (cycles/px) under either frequency map
-     * (index 0: phase gradient on the fronto-parallel plane, 1: literal J W f), its phase in
-     * cycles and the opacity.  They take part in no integer decision of the rule itself; the
-     * threshold decisions of the blend are evaluated from them (see alpha_decision). */
-    float fp[2][2], phc, op;
+    /* 3D only: the record's binary32 projected frequency (cycles/px) under each frequency map
+     * (index 0: phase gradient on the fronto-parallel plane, 1: literal J W f, 2: integrated along
+     * the viewing ray), its phase in cycles, the opacity, and for map 2 the exponent kx of the
+     * damping of the oscillation, kappa = 2^kx.  They take part in no integer decision of the rule
+     * itself; the threshold decisions of the blend are evaluated from them (see alpha_decision). */
+    float fp[3][2], phc, op, kx;
 } fp32_footprint;
 
 static int finite4(float a, float b, float c, float d) { return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d); }
@@ -260,6 +263,26 @@ static void footprint3d(const float* p, const float* cam, float cutoff, float di
         k->fp[1][1] = j11 * fcy + j12 * fcz;
         k->phc = p[13] * INV_TWO_PI_F;
         k->op = p[14];
+        /* map 2 (Sec. 4.1, the integral along z): with n = (txz, tyz, 1) the viewing direction of
+         * the affine ray space (J n = 0) and A = V R the camera-frame principal axes,
+         * m = A^T n, w = S^-2 m, c = n^T Sigma_c^-1 n = m . w, b = Sigma_c^-1 n = A w, fn = fc . n;
+         * f' = P0^T (fc - (fn / c) b) with P0^T v = (v_x tz / fx, v_y tz / fy), and
+         * kappa = exp(-2 pi^2 fn^2 / c) = 2^kx.  binary32, in this order of operations. */
+        float A[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                A[i * 3 + j] = (V[i * 4 + 0] * R[0 * 3 + j] + V[i * 4 + 1] * R[1 * 3 + j]) + V[i * 4 + 2] * R[2 * 3 + j];
+        float m[3], w[3];
+        for (int j = 0; j < 3; ++j) m[j] = (A[0 * 3 + j] * txz + A[1 * 3 + j] * tyz) + A[2 * 3 + j];
+        for (int j = 0; j < 3; ++j) w[j] = m[j] / (p[3 + j] * p[3 + j]);
+        float cq = (m[0] * w[0] + m[1] * w[1]) + m[2] * w[2];
+        float bx = (A[0] * w[0] + A[1] * w[1]) + A[2] * w[2];
+        float by = (A[3] * w[0] + A[4] * w[1]) + A[5] * w[2];
+        float fn = (fcx * txz + fcy * tyz) + fcz;
+        float rr = fn / cq;
+        k->fp[2][0] = ((fcx - rr * bx) * tz) / fx;
+        k->fp[2][1] = ((fcy - rr * by) * tz) / fy;
+        k->kx = -((DAMP_EXP2_F * fn) * rr);
     }
     k->valid = finite4(k->mx, k->my, l11, l21) && finite4(l22, k->ex, k->ey, D) && D > 0.0f && S11 > 0.0f &&
                l11 > 0.0f && l22 > 0.0f;
@@ -448,6 +471,7 @@ typedef struct {
     double mu[2];    /* mu' (pixels) */
     double K[4];     /* inverse of Sigma' (row-major 2x2) */
     double f[2];     /* f' (cycles per pixel) */
+    double kap;      /* damping of the oscillation (1 except under frequency map 2) */
     double phi;      /* phase (radians) */
     double o;        /* opacity (3D) */
     double c[3];     /* colour */
@@ -455,6 +479,7 @@ typedef struct {
     double t[3], R[9], M[9], V[9], Sc[9], J[6], fc[3], qn[4], qnorm, s[3];
     int unclamped_x, unclamped_y;
     int fmode;       /* frequency projection mode of project3d */
+    double lim[2];   /* view-angle clamp of the Jacobian (|tx / tz|, |ty / tz|) */
     int sh;          /* SH degree of the colour (0: the record's RGB) */
     double dir[3], dist, raw[3];  /* SH colour: unit direction camera -> centre, its length, unclamped colour */
 } proj;
@@ -480,6 +505,7 @@ static void project2d(const float* p, int cov2d, proj* w) {
     mat2_inv(Sig, w->K);
     w->mu[0] = p[0]; w->mu[1] = p[1];
     w->f[0] = p[5]; w->f[1] = p[6];
+    w->kap = 1.0;
     w->phi = p[7];
     w->o = 1.0;
     w->c[0] = p[8]; w->c[1] = p[9]; w->c[2] = p[10];
@@ -537,6 +563,78 @@ int wo_sh_basis(const double* dirs, int64_t n, double* Y) {
 /* view-dependent colour of an SH record: the coefficient of basis k for channel ch */
 static double sh_coef(const float* p, int k, int ch) { return k == 0 ? (double)p[15 + ch] : (double)p[20 + 3 * (k - 1) + ch]; }
 
+/* Frequency map 2, the oscillation integrated along the viewing ray (Sec. 4.1 integrates the 3D
+ * wavelet over z).  In the affine ray space of the EWA projection a camera-frame offset from the
+ * centre is y - t = P0 a + n z: a is the image-plane offset in pixels, n = (txz, tyz, 1) the viewing
+ * direction (J n = 0, with the Jacobian's clamped view angles) and P0 the right inverse of J with
+ * P0 a = (a_x tz / fx, a_y tz / fy, 0).  With Q = B^T Sigma_c^-1 B, B = [P0 | n], completing the
+ * square in z turns the integral over z of cos(2 pi fc.(y - t) + phi) G into
+ *   kappa cos(2 pi f'.a + phi) G'(a) (times the constant of the Gaussian integral),
+ *   f' = P0^T fc - (fc.n) Q_az / Q_zz,   kappa = exp(-2 pi^2 (fc.n)^2 / Q_zz),
+ * where G' is the marginal the covariance projection gives; the constant is dropped as for G' (the
+ * opacity carries it).  Q_zz = n^T Sigma_c^-1 n and Q_az = P0^T Sigma_c^-1 n, with Sigma_c = V Sigma V^T.
+ * Written over complex numbers so that the complex step gives its exact derivatives (chain3d);
+ * real inputs give the value.  out = (f'_x, f'_y, kappa). */
+static void quat_to_rot_c(const double complex q[4], double complex R[9]) {
+    double complex w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void damped_freq(const double complex t[3], const double complex s[3], const double complex qn[4],
+                        const double complex fc[3], const double V[9], double fx, double fy, const double lim[2],
+                        double complex out[3]) {
+    double complex R[9], M[9], Sig[9], VS[9], Sc[9], adj[9], n[3], b[3];
+    quat_to_rot_c(qn, R);
+    /* Sigma_c = V R S S^T R^T V^T, the camera-frame covariance of the covariance projection */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i * 3 + j] = R[i * 3 + j] * s[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Sig[i * 3 + j] = M[i * 3 + 0] * M[j * 3 + 0] + M[i * 3 + 1] * M[j * 3 + 1] + M[i * 3 + 2] * M[j * 3 + 2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) VS[i * 3 + j] = V[i * 3 + 0] * Sig[0 * 3 + j] + V[i * 3 + 1] * Sig[1 * 3 + j] + V[i * 3 + 2] * Sig[2 * 3 + j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Sc[i * 3 + j] = VS[i * 3 + 0] * V[j * 3 + 0] + VS[i * 3 + 1] * V[j * 3 + 1] + VS[i * 3 + 2] * V[j * 3 + 2];
+    /* b = Sigma_c^-1 n by the adjugate */
+    adj[0] = Sc[4] * Sc[8] - Sc[5] * Sc[7]; adj[1] = Sc[2] * Sc[7] - Sc[1] * Sc[8]; adj[2] = Sc[1] * Sc[5] - Sc[2] * Sc[4];
+    adj[3] = Sc[5] * Sc[6] - Sc[3] * Sc[8]; adj[4] = Sc[0] * Sc[8] - Sc[2] * Sc[6]; adj[5] = Sc[2] * Sc[3] - Sc[0] * Sc[5];
+    adj[6] = Sc[3] * Sc[7] - Sc[4] * Sc[6]; adj[7] = Sc[1] * Sc[6] - Sc[0] * Sc[7]; adj[8] = Sc[0] * Sc[4] - Sc[1] * Sc[3];
+    const double complex det = Sc[0] * adj[0] + Sc[1] * adj[3] + Sc[2] * adj[6];
+    n[0] = t[0] / t[2];
+    n[1] = t[1] / t[2];
+    n[2] = 1.0;
+    for (int a = 0; a < 2; ++a) {
+        if (creal(n[a]) < -lim[a]) n[a] = -lim[a];
+        if (creal(n[a]) > lim[a]) n[a] = lim[a];
+    }
+    for (int i = 0; i < 3; ++i) b[i] = (adj[i * 3 + 0] * n[0] + adj[i * 3 + 1] * n[1] + adj[i * 3 + 2] * n[2]) / det;
+    const double complex c = n[0] * b[0] + n[1] * b[1] + n[2] * b[2];  /* Q_zz */
+    const double complex fn = fc[0] * n[0] + fc[1] * n[1] + fc[2] * n[2];
+    const double complex r = fn / c;
+    for (int a = 0; a < 2; ++a) out[a] = (fc[a] - r * b[a]) * t[2] / (a == 0 ? fx : fy);
+    out[2] = cexp(-2.0 * PI * PI * fn * r);
+}
+
+/* the map's value at the projection's inputs (real) and, when d is not NULL, its derivatives
+ * d[k][0..2] by input k of (t(3), s(3), qn(4), fc(3)), each from one complex step of 1e-30 */
+static void damped_freq_eval(const proj* w, double fx, double fy, double val[3], double d[13][3]) {
+    double complex in[13], out[3];
+    for (int j = 0; j < 3; ++j) { in[j] = w->t[j]; in[3 + j] = w->s[j]; in[10 + j] = w->fc[j]; }
+    for (int m = 0; m < 4; ++m) in[6 + m] = w->qn[m];
+    damped_freq(in, in + 3, in + 6, in + 10, w->V, fx, fy, w->lim, out);
+    for (int a = 0; a < 3; ++a) val[a] = creal(out[a]);
+    if (!d) return;
+    const double h = 1e-30;
+    for (int k = 0; k < 13; ++k) {
+        double complex x[13];
+        memcpy(x, in, sizeof(x));
+        x[k] += h * I;
+        damped_freq(x, x + 3, x + 6, x + 10, w->V, fx, fy, w->lim, out);
+        for (int a = 0; a < 3; ++a) d[k][a] = cimag(out[a]) / h;
+    }
+}
+
 static void project3d(const float* p, const float* cam, int H, int W, double dil, int fmode, int valid32, proj* w) {
     memset(w, 0, sizeof(*w));
     w->valid = valid32;
@@ -562,6 +660,8 @@ static void project3d(const float* p, const float* cam, int H, int W, double dil
     matmul(tmp, Vt, w->Sc, 3, 3, 3);
     /* local affine Jacobian of the perspective map, with the usual clamp of the view angle */
     double limx = 1.3 * (0.5 * W / fx), limy = 1.3 * (0.5 * H / fy);
+    w->lim[0] = limx;
+    w->lim[1] = limy;
     double txz = tx / tz, tyz = ty / tz;
     w->unclamped_x = txz > -limx && txz < limx;
     w->unclamped_y = tyz > -limy && tyz < limy;
@@ -581,7 +681,14 @@ static void project3d(const float* p, const float* cam, int H, int W, double dil
     w->mu[0] = fx * tx / tz + cx;
     w->mu[1] = fy * ty / tz + cy;
     for (int i = 0; i < 3; ++i) w->fc[i] = w->V[i * 3 + 0] * p[10] + w->V[i * 3 + 1] * p[11] + w->V[i * 3 + 2] * p[12];
-    if (fmode) {
+    w->kap = 1.0;
+    if (fmode == 2) {
+        double val[3];
+        damped_freq_eval(w, fx, fy, val, NULL);
+        w->f[0] = val[0];
+        w->f[1] = val[1];
+        w->kap = val[2];
+    } else if (fmode) {
         w->f[0] = J[0] * w->fc[0] + J[1] * w->fc[1] + J[2] * w->fc[2];
         w->f[1] = J[3] * w->fc[0] + J[4] * w->fc[1] + J[5] * w->fc[2];
     } else {
@@ -628,22 +735,25 @@ static void eval_wavelet(const proj* w, int u, int v, wval* e) {
     double arg = 2.0 * PI * (w->f[0] * e->d[0] + w->f[1] * e->d[1]) + w->phi;
     e->ca = cos(arg);
     e->sa = sin(arg);
-    e->M = 0.5 * (1.0 + e->ca);
+    e->M = 0.5 * (1.0 + w->kap * e->ca);
     e->W = e->M * e->G;
 }
 
 /* per-primitive image-plane gradient accumulator: dL/d(mu', K (full 2x2), f', phi, o, c) */
-typedef struct { double mu[2], K[4], f[2], phi, o, c[3]; } pgrad;
+typedef struct { double mu[2], K[4], f[2], phi, o, c[3], kap; } pgrad;
 
 /* add gW * dW'/d(mu', K, f', phi) */
 static void accum_wavelet_grad(const proj* w, const wval* e, double gW, pgrad* g) {
-    /* dW/dmu = W K d + pi G sin(arg) f ;  dW/df = -pi G sin(arg) d ;  dW/dphi = -G sin(arg) / 2 ;
-       dW/dK_ab = -W d_a d_b / 2 */
+    /* W = (1 + kappa cos(arg)) G / 2:  dW/dmu = W K d + pi kappa G sin(arg) f ;
+       dW/df = -pi kappa G sin(arg) d ;  dW/dphi = -kappa G sin(arg) / 2 ;  dW/dK_ab = -W d_a d_b / 2 ;
+       dW/dkappa = cos(arg) G / 2 */
+    const double kGs = w->kap * e->G * e->sa;
     for (int a = 0; a < 2; ++a) {
-        g->mu[a] += gW * (e->W * e->Kd[a] + PI * e->G * e->sa * w->f[a]);
-        g->f[a] += gW * (-PI * e->G * e->sa * e->d[a]);
+        g->mu[a] += gW * (e->W * e->Kd[a] + PI * kGs * w->f[a]);
+        g->f[a] += gW * (-PI * kGs * e->d[a]);
     }
-    g->phi += gW * (-0.5 * e->G * e->sa);
+    g->phi += gW * (-0.5 * kGs);
+    g->kap += gW * 0.5 * e->ca * e->G;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) g->K[a * 2 + b] += gW * (-0.5 * e->W * e->d[a] * e->d[b]);
 }
@@ -810,12 +920,13 @@ int wo_grad2d(const float* params, int64_t N, int H, int W, float cutoff, int tr
 /* ------------------------------------------------------------------------------------------ */
 
 /* opts[10] = cutoff, alpha_min, alpha_max, T_min, dilation, bg_r, bg_g, bg_b, frequency projection
- * mode (0: phase gradient on the fronto-parallel plane; 1: the literal f' = (J W f)_xy), degree of
+ * mode (0: phase gradient on the fronto-parallel plane; 1: the literal f' = (J W f)_xy; 2: the
+ * oscillation integrated along the viewing ray, with its damping kappa), degree of
  * the spherical-harmonic colour (0: the record's RGB colour; 1..3: SH records of P3D_SH floats) */
 typedef struct { float cutoff, amin, amax, Tmin, dil; double bg[3]; int fmode, sh; } blend_opts;
 
 static blend_opts read_opts(const float* o) {
-    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}, o[8] != 0.0f, (int)o[9]};
+    blend_opts b = {o[0], o[1], o[2], o[3], o[4], {o[5], o[6], o[7]}, (int)o[8], (int)o[9]};
     return b;
 }
 
@@ -883,7 +994,9 @@ static void scene3_free(scene3* s) { free(s->k); free(s->w); free(s->order); }
  * bound of |kernel value - exact value|.  The kernel computes, in binary32:
  *   dx = px - mx, dy = py - my;  a = fma(l11, dx, l21 dy);  b = l22 dy;  q = fma(a, a, b b);
  *   G = ex2(q * (-log2(e) / 2));  t = fma(fx, dx, fma(fy, dy, phc));
- *   ang = (t - rint(t)) * 2pi;  M = fma(1/2, cos(ang), 1/2);  raw = o (M G). */
+ *   ang = (t - rint(t)) * 2pi;  M = fma(hk, cos(ang), 1/2);  raw = o (M G),
+ * with hk = 1/2, or under frequency map 2 hk = ex2(kx) / 2 = kappa / 2 from the record's exponent
+ * (ex2's relative error on top; a result below the smallest normal binary32 may be flushed). */
 static double alpha_decision(const fp32_footprint* k, int fmode, int u, int v, double* bound) {
     const double dx = ((double)u + 0.5) - (double)k->mx, dy = ((double)v + 0.5) - (double)k->my;
     const double l11 = k->l11, l21 = k->l21, l22 = k->l22;
@@ -894,7 +1007,9 @@ static double alpha_decision(const fp32_footprint* k, int fmode, int u, int v, d
     const double s1 = fy * dy + phc, t = fx * dx + s1;
     const double ang = 2.0 * PI * (t - nearbyint(t));
     const double ca = cos(ang), sa = sin(ang);
-    const double M = 0.5 + 0.5 * ca, raw = o * M * G;
+    const double hk = fmode == 2 ? 0.5 * exp2((double)k->kx) : 0.5;
+    const double dhk = fmode == 2 ? hk * EPS_EX2 + 0x1p-126 : 0.0;
+    const double M = 0.5 + hk * ca, raw = o * M * G;
     /* rounding of the kernel's steps, first order, with every term taken in absolute value */
     const double ddx = U32 * fabs(dx), ddy = U32 * fabs(dy);
     const double da = fabs(l11) * ddx + fabs(l21) * ddy + U32 * (fabs(l21 * dy) + fabs(a));
@@ -906,7 +1021,7 @@ static double alpha_decision(const fp32_footprint* k, int fmode, int u, int v, d
     const double dt = fabs(fx) * ddx + fabs(fy) * ddy + U32 * (fabs(s1) + fabs(t));
     const double dang = 2.0 * PI * dt + 2.0 * U32 * fabs(ang);
     const double dcos = fabs(sa) * dang + 0.5 * dang * dang + EPS_COS;
-    const double dM = 0.5 * dcos + U32 * M;
+    const double dM = hk * dcos + fabs(ca) * dhk + U32 * M;
     const double dW = M * dG + G * dM + dM * dG + U32 * M * G;
     *bound = AMB_SAFETY * (o * dW + U32 * raw) + 1e-15;
     return raw;
@@ -1003,6 +1118,14 @@ static void chain3d(const proj* w, const float* p, const float* cam, const pgrad
     double fx = cam[12], fy = cam[13];
     double tx = w->t[0], ty = w->t[1], tz = w->t[2];
     memset(out, 0, sizeof(double) * (w->sh ? P3D_SH : 20));
+    /* frequency map 2: (f', kappa) depend on t, s, the unit quaternion and fc; dmap[k] holds their
+       derivatives by input k (t(3), s(3), qn(4), fc(3)) and gmap[k] the gradient they pass on */
+    double gmap[13] = {0};
+    if (w->fmode == 2) {
+        double val[3], dmap[13][3];
+        damped_freq_eval(w, fx, fy, val, dmap);
+        for (int k = 0; k < 13; ++k) gmap[k] = g->f[0] * dmap[k][0] + g->f[1] * dmap[k][1] + g->kap * dmap[k][2];
+    }
     /* K = Sigma'^-1:  dL/dSigma' = -K (dL/dK) K */
     double t1[4], gS2[4];
     matmul(w->K, g->K, t1, 2, 2, 2);
@@ -1038,6 +1161,8 @@ static void chain3d(const proj* w, const float* p, const float* cam, const pgrad
     quat_rot_jac(w->qn, dR);
     for (int e = 0; e < 9; ++e)
         for (int m = 0; m < 4; ++m) gqn[m] += gR[e] * dR[e * 4 + m];
+    for (int m = 0; m < 4; ++m) gqn[m] += gmap[6 + m];
+    for (int j = 0; j < 3; ++j) out[3 + j] += gmap[3 + j];
     double dot = 0.0;
     for (int m = 0; m < 4; ++m) dot += w->qn[m] * gqn[m];
     for (int m = 0; m < 4; ++m) out[6 + m] = (gqn[m] - w->qn[m] * dot) / w->qnorm;
@@ -1048,7 +1173,12 @@ static void chain3d(const proj* w, const float* p, const float* cam, const pgrad
     gt[1] += g->mu[1] * fy / tz;
     gt[2] += -g->mu[1] * fy * ty / (tz * tz);
     double gfc[3];
-    if (w->fmode) {
+    if (w->fmode == 2) {
+        for (int k = 0; k < 3; ++k) {
+            gt[k] += gmap[k];
+            gfc[k] = gmap[10 + k];
+        }
+    } else if (w->fmode) {
         /* f' = J fc: dL/dfc = J^T dL/df', and dL/dJ gains dL/df' fc^T */
         for (int k = 0; k < 3; ++k) {
             gfc[k] = w->J[k] * g->f[0] + w->J[3 + k] * g->f[1];
@@ -1111,6 +1241,7 @@ static void pgrad_add(pgrad* g, const pgrad* a) {
     for (int m = 0; m < 3; ++m) g->c[m] += a->c[m];
     g->phi += a->phi;
     g->o += a->o;
+    g->kap += a->kap;
 }
 
 /* grad[N,20] (or [N,P3D_SH] with SH colour) of L = sum_pixels dldimg . C.  Pixels with a zero upstream
@@ -1184,6 +1315,7 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
             for (int m = 0; m < 3; ++m) g.c[m] += a->c[m];
             g.phi += a->phi;
             g.o += a->o;
+            g.kap += a->kap;
         }
         if (s.w[i].valid) chain3d(&s.w[i], params + i * P, cam, &g, grad + i * P);
         else memset(grad + i * P, 0, sizeof(double) * P);
@@ -1202,7 +1334,7 @@ int wo_grad3d(const float* params, int64_t N, const float* cam, int H, int W, co
 }
 
 /* Binary64 projection of each primitive, out[N,16]:
- * valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), 0, 0 */
+ * valid, tz, mu'x, mu'y, Sigma'00, Sigma'01, Sigma'11, f'x, f'y, phi, opacity, c(3), kappa, 0 */
 int wo_project3d(const float* params, int64_t N, const float* cam, int H, int W, const float* opts, double* out) {
     blend_opts o = read_opts(opts);
     const int P = rec3_stride(&o);
@@ -1220,13 +1352,15 @@ int wo_project3d(const float* params, int64_t N, const float* cam, int H, int W,
         r[4] = S2[0]; r[5] = S2[1]; r[6] = S2[3];
         r[7] = w.f[0]; r[8] = w.f[1]; r[9] = w.phi; r[10] = w.o;
         r[11] = w.c[0]; r[12] = w.c[1]; r[13] = w.c[2];
+        r[14] = w.kap;
     }
     return 0;
 }
 
 /* The threshold-decision values of (primitive, pixel) pairs: out[n,4] = the record's binary32
- * values the decision reads are in rec[N,9] (mx, my, l11, l21, l22, f'x, f'y, phase in cycles,
- * opacity; zeros for an invalid primitive); per pair (prim, u, v) in pairs[n,3]: out[n,3] = the
+ * values the decision reads are in rec[N,10] (mx, my, l11, l21, l22, f'x, f'y, phase in cycles,
+ * opacity, and under frequency map 2 the damping exponent kx, else 0; zeros for an invalid
+ * primitive); per pair (prim, u, v) in pairs[n,3]: out[n,3] = the
  * record's alpha before the clamp, its kernel error bound, and the alpha of the binary64 projection. */
 int wo_alpha_decisions(const float* params, int64_t N, const float* cam, int H, int W, const float* opts,
                        const int32_t* pairs, int64_t n, float* rec, double* out) {
@@ -1235,11 +1369,12 @@ int wo_alpha_decisions(const float* params, int64_t N, const float* cam, int H, 
     fp32_footprint* k = all_footprints(o.sh ? KIND_3D_SH : KIND_3D, params, N, cam, H, W, o.cutoff, o.dil);
     if (rec)
         for (int64_t i = 0; i < N; ++i) {
-            float* r = rec + i * 9;
-            memset(r, 0, sizeof(float) * 9);
+            float* r = rec + i * 10;
+            memset(r, 0, sizeof(float) * 10);
             if (!k[i].valid) continue;
             r[0] = k[i].mx; r[1] = k[i].my; r[2] = k[i].l11; r[3] = k[i].l21; r[4] = k[i].l22;
             r[5] = k[i].fp[o.fmode][0]; r[6] = k[i].fp[o.fmode][1]; r[7] = k[i].phc; r[8] = k[i].op;
+            r[9] = o.fmode == 2 ? k[i].kx : 0.0f;
         }
     for (int64_t j = 0; j < n; ++j) {
         const int32_t i = pairs[j * 3], u = pairs[j * 3 + 1], v = pairs[j * 3 + 2];

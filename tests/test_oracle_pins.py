@@ -477,6 +477,163 @@ def test_literal_frequency_grad_matches_central_differences():
 
 
 # ---------------------------------------------------------------------------------------------
+# frequency map 2 (opt-in reading of Sec. 4.1): the oscillation integrated along the viewing ray,
+# with the damping factor the integral over z brings
+# ---------------------------------------------------------------------------------------------
+
+OPTS_RAY = np.array([3.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 2.0], np.float32)  # exact, no dilation
+
+
+def _camera_frame(p, cam):
+    """Camera-frame centre t, covariance Sigma_c and frequency fc of a 3D record (scipy's rotation,
+    numpy products), and the pixel Jacobian J of the pinhole map at t."""
+    from scipy.spatial.transform import Rotation
+
+    V = cam[:12].reshape(3, 4).astype(np.float64)
+    fx, fy = float(cam[12]), float(cam[13])
+    r = p.astype(np.float64)
+    t = V[:, :3] @ r[0:3] + V[:, 3]
+    q = r[6:10] / np.linalg.norm(r[6:10])
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    Sig = V[:, :3] @ R @ np.diag(r[3:6] ** 2) @ R.T @ V[:, :3].T
+    fc = V[:, :3] @ r[10:13]
+    J = np.array([[fx / t[2], 0.0, -fx * t[0] / t[2] ** 2], [0.0, fy / t[2], -fy * t[1] / t[2] ** 2]])
+    return t, Sig, fc, J
+
+
+def _ray_integral(p, cam, a):
+    """W'(a) of one primitive at image-plane offset a (pixels from the projected centre): the 3D
+    wavelet integrated numerically along the line of camera-frame offsets y with J y = a (the
+    viewing ray of the affine ray space), over the Gaussian integrated along the line through the
+    centre.  The line comes from J's pseudo-inverse and null space (SVD); trapezoid rule over
+    +-16 of the largest scale, far finer than the oscillation."""
+    t, Sig, fc, J = _camera_frame(p, cam)
+    Sinv = np.linalg.inv(Sig)
+    n = np.linalg.svd(J)[2][2]  # unit direction with J n = 0
+    smax = float(np.max(p[3:6]))
+    phi = float(p[13])
+
+    def line(y0, cosine):
+        zc = -float(n @ y0)
+        z = np.linspace(zc - 16 * smax, zc + 16 * smax, 40001)
+        y = y0[None, :] + z[:, None] * n[None, :]
+        G = np.exp(-0.5 * np.einsum("ki,ij,kj->k", y, Sinv, y))
+        f = 0.5 * (np.cos(2 * math.pi * (y @ fc) + phi) + 1.0) * G if cosine else G
+        return np.trapezoid(f, z)
+
+    y0 = np.linalg.pinv(J) @ np.asarray(a, np.float64)
+    return line(y0, True) / line(np.zeros(3), False)
+
+
+def test_ray_integrated_frequency_matches_quadrature_along_the_ray():
+    """Sec. 4.1 integrates the 3D wavelet over z.  In the EWA ray space (the same affine map as the
+    covariance projection) the oracle's closed form (f' and the damping kappa from completing the
+    square, with the marginal Gaussian of Sigma') must equal numerical quadrature of the 3D
+    wavelet along the viewing line, for rotated anisotropic primitives off the optical axis under
+    a rotated camera, at pixels across the footprint.  A dropped damping, a wrong sign of the
+    correction term, the conditional taken along the optical axis instead of the ray, or Sigma in
+    place of its inverse fails here."""
+    H, W = 120, 160
+    cam = synth.camera(synth.look_at((0.6, -2.5, 0.8)), H, W, 50.0)
+    rng = np.random.default_rng(71)
+    checked = 0
+    kaps = []
+    for trial in range(4):
+        mu = rng.uniform(-0.25, 0.25, 3)
+        s = np.exp(rng.uniform(np.log(0.03), np.log(0.08), 3))
+        q = rng.standard_normal(4)
+        p = rec3d(mu, s, q / np.linalg.norm(q), (0, 0, 0), rng.uniform(0, 2 * math.pi), 0.5, (1, 1, 1))
+        # a frequency with a component of 3 cycles/unit along the viewing ray and 2 across it
+        t = _camera_frame(p[0], cam)[0]
+        V = cam[:12].reshape(3, 4).astype(np.float64)[:, :3]
+        fcam = 3.0 * t / np.linalg.norm(t) + 2.0 * rng.standard_normal(3) / math.sqrt(3.0)
+        p[0, 10:13] = V.T @ fcam
+        proj = oracle.project3d(p, cam, H, W, OPTS_RAY)[0]
+        kaps.append(proj[14])
+        mx, my = proj[2], proj[3]
+        Sd = np.array([[proj[4], proj[5]], [proj[5], proj[6]]])
+        pix = []
+        for _ in range(12):
+            d = rng.multivariate_normal([0, 0], Sd)
+            u, v = int(np.floor(mx + d[0])), int(np.floor(my + d[1]))
+            if 0 <= u < W and 0 <= v < H:
+                pix.append((u, v))
+        C = oracle.render3d(p, cam, H, W, OPTS_RAY, truncated=False, pixels=pix)[0]
+        for (u, v), c in zip(pix, C[:, 0]):
+            ref = _ray_integral(p[0], cam, (u + 0.5 - mx, v + 0.5 - my))
+            assert abs(c / float(np.float32(0.5)) - ref) <= 1e-9, (trial, u, v, c, ref)
+            checked += 1
+    assert checked >= 30
+    assert max(kaps) < 0.99 and min(kaps) < 0.7, kaps  # dampings that matter
+
+
+def test_ray_integrated_frequency_across_the_ray_is_the_plane_gradient():
+    """A frequency perpendicular to the viewing ray (fc . n = 0) is not damped by the integral and
+    its projection is the phase gradient on the fronto-parallel plane (frequency map 0)."""
+    H, W = 120, 160
+    cam = synth.camera(synth.look_at((0.6, -2.5, 0.8)), H, W, 50.0)
+    mu = np.array([0.1, -0.05, 0.2])
+    p = rec3d(mu, (0.05, 0.08, 0.03), (0.7, 0.2, -0.4, 0.5), (0, 0, 0), 0.4, 0.5, (1, 1, 1))
+    t, Sig, fc, J = _camera_frame(p[0], cam)
+    n = t / t[2]  # the viewing direction through the centre (unclamped)
+    V = cam[:12].reshape(3, 4).astype(np.float64)[:, :3]
+    fcam = np.cross(n, [0.3, 1.0, -0.2])
+    fcam *= 5.0 / np.linalg.norm(fcam)
+    p[0, 10:13] = V.T @ fcam
+    p32 = p.astype(np.float32)
+    t, Sig, fc, J = _camera_frame(p32[0], cam)
+    assert abs(fc @ (t / t[2])) < 1e-6 * np.linalg.norm(fc)
+    r2 = oracle.project3d(p32, cam, H, W, OPTS_RAY)[0]
+    r0 = oracle.project3d(p32, cam, H, W, OPTS_EXACT)[0]
+    np.testing.assert_allclose(r2[7:9], r0[7:9], rtol=1e-5, atol=1e-12)
+    assert abs(r2[14] - 1.0) < 1e-9
+
+
+def test_ray_integrated_damping_on_axis_isotropic_closed_form():
+    """On the optical axis with an isotropic Gaussian of std sigma the viewing ray is the z axis and
+    the z integral of cos(2 pi f_z z) exp(-z^2 / 2 sigma^2) over that of the Gaussian is the
+    Gaussian's Fourier transform exp(-2 pi^2 f_z^2 sigma^2); the in-plane frequency keeps the map-0
+    value (f_x tz / fx, f_y tz / fy)."""
+    H, W = 64, 80
+    fx, fy = 300.0, 250.0
+    cam = cam_identity(H, W, fx=fx, fy=fy)
+    for sig, f in [(0.05, (1.0, -2.0, 4.0)), (0.1, (0.0, 0.5, 2.5)), (0.02, (3.0, 0.0, -9.0))]:
+        p = rec3d((0, 0, 5.0), (sig,) * 3, (0.6, -0.3, 0.2, 0.7), f, 0.0, 0.5, (1, 1, 1))
+        r = oracle.project3d(p, cam, H, W, OPTS_RAY)[0]
+        sg, fz, f0, f1 = (float(np.float32(v)) for v in (sig, f[2], f[0], f[1]))
+        assert r[14] == pytest.approx(math.exp(-2 * math.pi ** 2 * fz ** 2 * sg ** 2), rel=1e-6)
+        np.testing.assert_allclose(r[7:9], [f0 * 5.0 / fx, f1 * 5.0 / fy], rtol=1e-6, atol=1e-14)
+
+
+def test_ray_integrated_frequency_grad_matches_central_differences():
+    """The gradient under frequency map 2 (f' and kappa through the centre, the scales, the
+    rotation and the frequency) against central differences of the binary64 forward."""
+    H, W = 28, 32
+    p = synth.scene3d(6, 47, scale_range=(0.03, 0.08), max_freq=6.0, extent=0.3)
+    p[:, 14] = np.linspace(0.3, 0.8, 6)
+    cam = synth.camera(synth.look_at((0.4, -2.2, 0.9)), H, W, 50.0)
+    g = synth.upstream_grad(H, W, 48)
+    opts = OPTS_EXACT.copy()
+    opts = np.concatenate([opts, [2.0]]).astype(np.float32)
+    kap = oracle.project3d(p, cam, H, W, opts)[:, 14]
+    assert kap.min() < 0.9  # the damping takes part
+    an = oracle.grad3d(p, cam, H, W, g, opts, truncated=False)
+    cols = list(range(18))
+    floor = [0.3] * 3 + [0.03] * 3 + [0.5] * 4 + [1.0] * 3 + [1.0] + [0.3] + [0.3] * 3
+
+    def L(pp):
+        return float((oracle.render3d(pp, cam, H, W, opts, truncated=False)[0] * g).sum())
+
+    fd = _central_fd(L, p, range(len(p)), cols, floor=floor)
+    err = np.abs(an[:, cols] - fd)
+    tol = 1e-5 * np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max(axis=0, keepdims=True))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-300)).max()
+    # the map matters: map 0 gives a different gradient here
+    an0 = oracle.grad3d(p, cam, H, W, g, OPTS_EXACT, truncated=False)
+    assert np.abs(an0[:, 10:13] - an[:, 10:13]).max() > 1e-2 * np.abs(an[:, 10:13]).max()
+
+
+# ---------------------------------------------------------------------------------------------
 # spherical-harmonic colour (the view-dependent colour of 3DGS, Sec. 3.1)
 # ---------------------------------------------------------------------------------------------
 
@@ -703,7 +860,7 @@ def _decision_pairs(seed, fmode):
     p = synth.scene3d(20000, seed)
     cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
     opts = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, float(fmode)], np.float32)
-    if fmode:
+    if fmode == 1:
         p[:, 10:13] *= 0.02  # the literal map scales f by about fx / tz
     rec, _, valid = oracle.footprints(3, p, H, W, cam)
     rng = np.random.default_rng(seed)
@@ -716,10 +873,10 @@ def _decision_pairs(seed, fmode):
         v = int(np.clip(round(rec[i, 1] - 0.5 + rng.normal(0, rec[i, 6] / 3.0)), 0, H - 1))
         pairs.append((i, u, v))
     pairs = np.array(pairs, np.int32)
-    r9, out = oracle.alpha_decisions(p, cam, H, W, pairs, opts)
+    r10, out = oracle.alpha_decisions(p, cam, H, W, pairs, opts)
     k2 = np.float32(9.0)
     # keep the pairs inside the binary32 cutoff (the decision is only taken there)
-    m = r9[pairs[:, 0]]
+    m = r10[pairs[:, 0]]
     dx = (pairs[:, 1].astype(np.float32) + np.float32(0.5)) - m[:, 0]
     dy = (pairs[:, 2].astype(np.float32) + np.float32(0.5)) - m[:, 1]
     a = _f32_fma(m[:, 2], dx, m[:, 3] * dy)
@@ -729,7 +886,7 @@ def _decision_pairs(seed, fmode):
     return pairs[inside], m[inside], out[inside], dx[inside], dy[inside], q[inside]
 
 
-@pytest.mark.parametrize("fmode", [0, 1])
+@pytest.mark.parametrize("fmode", [0, 1, 2])
 def test_threshold_decision_alpha_bound_covers_binary32_evaluation(fmode):
     """Eq. 3's threshold decisions (alpha_min skip, alpha_max clamp, T_min stop) are taken from the
     binary32 projected record; the oracle's per-pair bound must cover the error of evaluating alpha
@@ -745,7 +902,9 @@ def test_threshold_decision_alpha_bound_covers_binary32_evaluation(fmode):
     r = (t + f32(12582912.0)) - f32(12582912.0)
     ang = (t - r) * f32(6.283185307179586)
     c = np.cos(ang.astype(np.float64)).astype(f32)
-    M = _f32_fma(np.full_like(c, 0.5), c, np.full_like(c, 0.5))
+    # map 2: hk = kappa / 2 = ex2(kx) / 2 (correctly rounded here), else 1/2
+    hk = (np.exp2(m[:, 9].astype(np.float64)).astype(f32) * f32(0.5)) if fmode == 2 else np.full_like(c, 0.5)
+    M = _f32_fma(hk, c, np.full_like(c, 0.5))
     raw = m[:, 8] * (M * G)
     err = np.abs(raw.astype(np.float64) - out[:, 0])
     # the bound carries a safety factor of 1.5 over its first-order terms; the emulation must fit
@@ -755,7 +914,7 @@ def test_threshold_decision_alpha_bound_covers_binary32_evaluation(fmode):
     assert np.median(out[:, 1]) < 1e-6
 
 
-@pytest.mark.parametrize("fmode", [0, 1])
+@pytest.mark.parametrize("fmode", [0, 1, 2])
 def test_threshold_decision_alpha_matches_binary64_projection(fmode):
     """The record the decisions read (centre, Cholesky factor, frequency under the chosen map,
     phase in cycles, opacity) is the binary32 rounding of the projection of Sec. 3.1 / Sec. 4.1:
