@@ -86,7 +86,12 @@ typedef struct {
     float bg[3];            /* 3D: background colour, weighted by the final transmittance */
     int32_t freq_proj_mode; /* 3D: 0 = phase gradient on the fronto-parallel plane through the centre,
                                f' = (fc_x t_z / f_x, fc_y t_z / f_y) with fc = W f; 1 = the literal
-                               f' = J W f (the covariance's ray-space map, Sec. 4.1) */
+                               f' = J W f (the covariance's ray-space map, Sec. 4.1); 2 = the
+                               oscillation integrated along the viewing ray (Sec. 4.1's integral
+                               over z, in the EWA ray space): f' = P0^T fc - (fc.n) Q_az / Q_zz and
+                               W' = (1 + kappa cos(2 pi f'.x' + phi)) G' / 2 with the damping
+                               kappa = exp(-2 pi^2 (fc.n)^2 / Q_zz), n the ray direction, P0 the
+                               right inverse of J, Q = [P0|n]^T Sigma_c^-1 [P0|n] */
     int32_t cov2d;          /* 2D: 0 = RS record (s_x, s_y, theta), 1 = Cholesky record (l1, l2, l3) */
     int32_t sh_degree;      /* 3D: 0 = RGB colour of the [N,20] record; 1..3 = spherical-harmonic colour of
                                that degree from [N,68] records (params and dL/dparams) */

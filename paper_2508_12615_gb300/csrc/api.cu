@@ -358,6 +358,7 @@ BlendOpts3 blend_opts(const wipes_opts& o) {
     b.bg[0] = o.bg[0];
     b.bg[1] = o.bg[1];
     b.bg[2] = o.bg[2];
+    b.damp = o.freq_proj_mode == 2;
     return b;
 }
 
@@ -369,8 +370,10 @@ wipes_status check_opts(const wipes_opts* o) {
         return fail(WIPES_ERR_INVALID, "alpha_max must lie in (0, 1)");
     if (!(o->alpha_min >= 0.f) || !(o->T_min >= 0.f) || !(o->dilation >= 0.f))
         return fail(WIPES_ERR_INVALID, "alpha_min, T_min and dilation must be non-negative");
-    if (o->freq_proj_mode != 0 && o->freq_proj_mode != 1)
-        return fail(WIPES_ERR_INVALID, "freq_proj_mode must be 0 (fronto-parallel phase gradient) or 1 (literal J W f)");
+    if (o->freq_proj_mode < 0 || o->freq_proj_mode > 2)
+        return fail(WIPES_ERR_INVALID,
+                    "freq_proj_mode must be 0 (fronto-parallel phase gradient), 1 (literal J W f) or 2 (integrated "
+                    "along the viewing ray)");
     if (o->cov2d != 0 && o->cov2d != 1) return fail(WIPES_ERR_INVALID, "cov2d must be 0 (RS) or 1 (Cholesky)");
     if (o->sh_degree < 0 || o->sh_degree > 3) return fail(WIPES_ERR_INVALID, "sh_degree must lie in 0..3");
     return WIPES_OK;
@@ -636,10 +639,11 @@ wipes_status wipes_render_backward(wipes_ctx* ctx, wipes_state* st, const float*
         launch_reduce_chain2d(params, N, st->opts.cov2d, st->offsets.as<uint32_t>(), st->counts.as<uint32_t>(),
                               st->partial.as<float>(), dL_dparams, s);
     } else {
-        WIPES_TRY(ensure(st->grad_img, sizeof(float) * 12 * (size_t)std::max<int64_t>(N, 1)));
+        const size_t gstride = (size_t)image_grad_stride3d(st->opts.freq_proj_mode);
+        WIPES_TRY(ensure(st->grad_img, sizeof(float) * gstride * (size_t)std::max<int64_t>(N, 1)));
         {
             StageTimer t(ctx, WIPES_STAGE_BWD_RASTER, s);
-            if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * 12 * (size_t)N, s));
+            if (N > 0) WIPES_CUDA(cudaMemsetAsync(st->grad_img.p, 0, sizeof(float) * gstride * (size_t)N, s));
             const BwdChunks ch{st->bwd_items.as<uint2>(), st->n_items.as<uint32_t>(), st->item_base.as<uint32_t>(),
                                st->bnd.as<float4>(), st->cfin.as<float>(), st->n_items.as<unsigned int>() + 1};
             launch_backward3d(st->rec.as<float4>(), st->rect.as<PixRect>(), st->lists(), st->W, st->H, st->tiles_x,

@@ -134,15 +134,16 @@ struct Px3 {
 
 // One tile-list entry at one pixel (Eq. 3 with W'): nothing outside the cutoff ellipse or below
 // alpha_min; stop before an entry that would take T below T_min; else add c alpha T and update T.
-// `pos` is the entry's 1-based position in the tile list.  Every 3D forward kernel blends through
-// this function, so a pixel gets the same bits whatever the block shape.
+// `pos` is the entry's 1-based position in the tile list; hk the record's oscillation weight
+// (1/2, or kappa / 2 under frequency map 2).  Every 3D forward kernel blends in these operations,
+// so a pixel gets the same bits whatever the block shape.
 __device__ __forceinline__ void blend3d_pair(Px3& s, float px, float py, const float4& A, const float4& B,
-                                             const float4& C, const BlendOpts3& o, uint32_t pos) {
+                                             const float4& C, float hk, const BlendOpts3& o, uint32_t pos) {
     const float q = mahalanobis2(px, py, A.x, A.y, A.z, A.w, B.x);
     if (!(q <= o.cutoff2)) return;
     const float dx = px - A.x, dy = py - A.y;
     const float G = ex2_approx(q * kNegHalfLog2e);
-    const float w = fmaf(0.5f, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
+    const float w = fmaf(hk, cos_approx(reduced_angle(fmaf(B.y, dx, fmaf(B.z, dy, B.w)))), 0.5f) * G;
     const float alpha = fminf(o.alpha_max, C.w * w);
     if (alpha < o.alpha_min) return;
     const float test_T = s.T * (1.f - alpha);
@@ -185,6 +186,7 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
     __shared__ float4 s_c[kTilePixels];
+    __shared__ float s_k[kTilePixels];
     __shared__ uint8_t s_mask[kTilePixels];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -205,6 +207,7 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
             s_a[threadIdx.x] = A;
             s_b[threadIdx.x] = B;
             s_c[threadIdx.x] = rec[(size_t)id * kRecF4 + 2];
+            s_k[threadIdx.x] = o.damp ? rec[(size_t)id * kRecF4 + 3].w : 0.5f;
             s_mask[threadIdx.x] = (uint8_t)subtile_mask_ellipse(A, B.x, rect[id], x0, y0, o.lim);
         }
         __syncthreads();
@@ -216,7 +219,7 @@ __device__ __forceinline__ void blend3d_tile(const BlendJob& job, int tile) {
                 const int j = c + __ffs(bal) - 1;
                 bal &= bal - 1u;
                 if (s.done) continue;
-                blend3d_pair(s, px, py, s_a[j], s_b[j], s_c[j], o, b0 - range.x + (uint32_t)j + 1u);
+                blend3d_pair(s, px, py, s_a[j], s_b[j], s_c[j], s_k[j], o, b0 - range.x + (uint32_t)j + 1u);
             }
         }
     }
@@ -238,6 +241,9 @@ constexpr int kQuadThreads = 32;
 struct Eval3 {
     f2 q, alpha;
 };
+// DAMP: frequency map 2, the entry's oscillation weight hk = kappa / 2 is staged in s_e[6][j].x
+// (else the constant 1/2, the same bits as hk = 1/2).
+template <bool DAMP>
 __device__ __forceinline__ void eval3_entry(Eval3& r, const ulonglong2 (*s_e)[kQuadThreads], int j, f2 PX, f2 PY,
                                             const BlendOpts3& o) {
     const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
@@ -251,7 +257,9 @@ __device__ __forceinline__ void eval3_entry(Eval3& r, const ulonglong2 (*s_e)[kQ
     const f2 G = f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e)));
     const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
     const f2 HALF = f2_dup(0.5f);
-    const f2 w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang))), HALF), G);
+    f2 hk = HALF;
+    if constexpr (DAMP) hk = ld_f2x2(&s_e[6][j]).x;
+    const f2 w = f2_mul(f2_fma(hk, f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang))), HALF), G);
     const f2 raw = f2_mul(e5.y, w);
     r.alpha = f2_pack(fminf(o.alpha_max, f2_lo(raw)), fminf(o.alpha_max, f2_hi(raw)));
 }
@@ -280,13 +288,15 @@ __device__ __forceinline__ void apply3_entry(const Eval3& r, const ulonglong2 (*
 }
 
 
+template <bool DAMP>
 __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int quad) {
     const float4* __restrict__ rec = job.rec;
     const PixRect* __restrict__ rect = job.rect;
     const TileLists& tl = job.tl;
     const BlendOpts3& o = job.o;
-    // staged entry: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, o), each value twice
-    __shared__ ulonglong2 s_e[6][kQuadThreads];
+    // staged entry: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, o), each value twice,
+    // and with DAMP (hk, 0)
+    __shared__ ulonglong2 s_e[DAMP ? 7 : 6][kQuadThreads];
     const int tx = tile % job.tiles_x, ty = tile / job.tiles_x;
     const int lane = threadIdx.x & 31;
     const int x0 = tx * kTile + (quad & 1) * 8, y0 = ty * kTile + (quad >> 1) * 8;
@@ -300,6 +310,7 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
     // registers of the software pipeline: records of the batch to stage next, primitive id of the
     // batch after it
     float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
+    float nK = 0.5f;
     PixRect nR{0, 0, -1, -1};
     uint32_t np = 0u;
     if (range.x + lane < range.y) {
@@ -307,6 +318,7 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
         nA = rec[(size_t)p * kRecF4 + 0];
         nB = rec[(size_t)p * kRecF4 + 1];
         nC = rec[(size_t)p * kRecF4 + 2];
+        if (DAMP) nK = rec[(size_t)p * kRecF4 + 3].w;
         nR = rect[p];
     }
     if (range.x + kQuadThreads + lane < range.y) np = tl.prim[range.x + kQuadThreads + lane];
@@ -334,6 +346,7 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
             s_e[3][lane] = dup2(nB.z, nB.w);
             s_e[4][lane] = dup2(nC.x, nC.y);
             s_e[5][lane] = dup2(nC.z, nC.w);
+            if constexpr (DAMP) s_e[6][lane] = dup2(nK, 0.f);
             float nBA, nBC;
             ellipse_edge_ratios(nA, nB.x, nBA, nBC);
             hit = box_touched_ellipse(nA, nB.x, nBA, nBC, nR, x0, y0, 8, 8, o.lim);
@@ -344,6 +357,7 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
             nA = rec[(size_t)np * kRecF4 + 0];
             nB = rec[(size_t)np * kRecF4 + 1];
             nC = rec[(size_t)np * kRecF4 + 2];
+            if (DAMP) nK = rec[(size_t)np * kRecF4 + 3].w;
             nR = rect[np];
         }
         if (b0 + 2 * kQuadThreads + lane < range.y) np = tl.prim[b0 + 2 * kQuadThreads + lane];
@@ -356,8 +370,8 @@ __device__ __forceinline__ void blend3d_quad(const BlendJob& job, int tile, int 
             const int j2 = bal ? __ffs(bal) - 1 : -1;
             if (bal) bal &= bal - 1u;
             Eval3 ea, eb;
-            eval3_entry(ea, s_e, j1, PX, PY, o);
-            if (j2 >= 0) eval3_entry(eb, s_e, j2, PX, PY, o);
+            eval3_entry<DAMP>(ea, s_e, j1, PX, PY, o);
+            if (j2 >= 0) eval3_entry<DAMP>(eb, s_e, j2, PX, PY, o);
             apply3_entry(ea, s_e, j1, o, T, c0, c1, c2, last0, last1, done0, done1, b0 - range.x + (uint32_t)j1 + 1u);
             if (j2 >= 0)
                 apply3_entry(eb, s_e, j2, o, T, c0, c1, c2, last0, last1, done0, done1, b0 - range.x + (uint32_t)j2 + 1u);

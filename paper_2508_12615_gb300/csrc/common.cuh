@@ -16,12 +16,16 @@ constexpr float kExtMargin = 1.0009765625f;  // 1 + 2^-10: footprint half-extent
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr float kInvTwoPi = 0.15915494309189535f;
 constexpr float kPi = 3.141592653589793f;
+constexpr float kDampExp2 = 28.47765864997501f;  // 2 pi^2 log2(e): kappa = exp(-2 pi^2 x) = ex2(-x kDampExp2)
 
 // Projected record (4 x float4 = 64 bytes per primitive), written by the footprint kernels:
 //   [0] mx, my, l11, l21    centre (px) and lower Cholesky factor L of Sigma'^-1 = L L^T
 //   [1] l22, fx, fy, phc    frequency (cycles/px) and phase (cycles)
 //   [2] c_r, c_g, c_b, o    colour and opacity (2D: o = 1)
-//   [3] ex, ey, depth, 0    half extents of the cutoff ellipse (px) and camera z (3D)
+//   [3] ex, ey, depth, hk   half extents of the cutoff ellipse (px), camera z (3D) and the
+//                           oscillation's weight hk = kappa / 2 (3D; 1/2 but under frequency map 2,
+//                           where kappa is the damping of the oscillation integrated along the ray)
+// The modulation is M = hk cos(2 pi t) + 1/2 (t the phase in cycles).
 // The squared Mahalanobis distance at offset (dx, dy) is  q = (l11 dx + l21 dy)^2 + (l22 dy)^2,
 // evaluated everywhere by mahalanobis2() so that the cutoff decision is the same in every kernel.
 constexpr int kRecF4 = 4;
@@ -490,6 +494,7 @@ struct TileLists {
 struct BlendOpts3 {
     float cutoff2, lim, alpha_min, alpha_max, T_min;
     float bg[3];
+    int damp;  // 3D frequency map 2: the records carry hk = kappa / 2 (else hk = 1/2 everywhere)
 };
 struct BlendJob {
     const float4* rec;
@@ -530,6 +535,9 @@ void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cud
 void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        const BlendOpts3& o, const float* T_final, const uint32_t* last, const float* dl_dout,
                        float* grad_img, const BwdChunks& ch, int64_t max_items, cudaStream_t stream);
+// Floats per primitive of the 3D image-plane gradient (mx my l11 l21 l22 fx fy phc c_r c_g c_b o,
+// and under frequency map 2 kappa, in rows of 16 for 16-byte alignment).
+inline int image_grad_stride3d(int fmode) { return fmode == 2 ? 16 : 12; }
 void launch_chain3d(const float* params, int64_t N, const wipes_camera& cam, int W, int H, float dilation, int fmode,
                     int sh_degree, const float4* rec, const float* grad_img, float* dl_dparams, cudaStream_t stream);
 

@@ -300,8 +300,35 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     // projected frequency (not part of any integer decision)
     const float fcx = (V[0] * p[10] + V[1] * p[11]) + V[2] * p[12];
     const float fcy = (V[4] * p[10] + V[5] * p[11]) + V[6] * p[12];
-    float fpx, fpy;
-    if (fmode) {
+    float fpx, fpy, hk = 0.5f;
+    if (fmode == 2) {
+        // the oscillation integrated along the viewing ray (Sec. 4.1's integral over z) in the EWA
+        // ray space: n = (txz, tyz, 1) the ray direction (J n = 0), A = V R the camera-frame
+        // principal axes; m = A^T n, w = S^-2 m, c = n^T Sigma_c^-1 n = m . w, b = Sigma_c^-1 n = A w,
+        // fn = fc . n;  f' = P0^T (fc - (fn / c) b) with P0^T v = (v_x tz / fx, v_y tz / fy), and the
+        // damping kappa = exp(-2 pi^2 fn^2 / c) = ex2(kx)
+        const float fcz = (V[8] * p[10] + V[9] * p[11]) + V[10] * p[12];
+        float A[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                A[a * 3 + b] = (V[a * 4 + 0] * R[0 * 3 + b] + V[a * 4 + 1] * R[1 * 3 + b]) + V[a * 4 + 2] * R[2 * 3 + b];
+        float m[3], w[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            m[b] = (A[0 * 3 + b] * txz + A[1 * 3 + b] * tyz) + A[2 * 3 + b];
+            w[b] = m[b] / (p[3 + b] * p[3 + b]);
+        }
+        const float cq = (m[0] * w[0] + m[1] * w[1]) + m[2] * w[2];
+        const float bx = (A[0] * w[0] + A[1] * w[1]) + A[2] * w[2];
+        const float by = (A[3] * w[0] + A[4] * w[1]) + A[5] * w[2];
+        const float fn = (fcx * txz + fcy * tyz) + fcz;
+        const float rr = fn / cq;
+        fpx = ((fcx - rr * bx) * tz) / cam.fx;
+        fpy = ((fcy - rr * by) * tz) / cam.fy;
+        hk = 0.5f * ex2_approx(-((kDampExp2 * fn) * rr));
+    } else if (fmode) {
         const float fcz = (V[8] * p[10] + V[9] * p[11]) + V[10] * p[12];
         fpx = j00 * fcx + j02 * fcz;
         fpy = j11 * fcy + j12 * fcz;
@@ -333,7 +360,7 @@ __global__ void __launch_bounds__(256) k_footprint3d(const float* __restrict__ p
     rec[i * kRecF4 + 0] = make_float4(mx, my, l11, l21);
     rec[i * kRecF4 + 1] = make_float4(l22, fpx, fpy, p[13] * kInvTwoPi);
     rec[i * kRecF4 + 2] = make_float4(col[0], col[1], col[2], p[14]);
-    rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, 0.0f);
+    rec[i * kRecF4 + 3] = make_float4(ex, ey, tz, hk);
     rect[i] = rr;
     counts[i] = cnt;
     depth_keys[i] = __float_as_uint(tz);

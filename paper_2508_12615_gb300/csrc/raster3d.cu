@@ -11,34 +11,44 @@
 namespace wipes {
 namespace {
 
-// One block per 8x8 quad, tiles taken in the given order (longest list first).
+// One block per 8x8 quad, tiles taken in the given order (longest list first).  DAMP: frequency
+// map 2 (the records carry the oscillation weight hk = kappa / 2).
+template <bool DAMP>
 __global__ void __launch_bounds__(kQuadThreads) k_blend3d(BlendJob job, const uint32_t* __restrict__ order) {
     pdl_enter();
-    blend3d_quad(job, (int)order[blockIdx.x >> 2], (int)(blockIdx.x & 3u));
+    blend3d_quad<DAMP>(job, (int)order[blockIdx.x >> 2], (int)(blockIdx.x & 3u));
 }
 
-// Image-plane gradient per primitive (12 floats): mx my l11 l21 l22 fx fy phc c_r c_g c_b o
-constexpr int kG = 12;
+// Image-plane gradient per primitive: mx my l11 l21 l22 fx fy phc c_r c_g c_b o (12 floats a row),
+// and with DAMP kappa (13 components in rows of 16).
+template <bool DAMP>
+__host__ __device__ constexpr int grad_components() { return DAMP ? 13 : 12; }
+template <bool DAMP>
+__host__ __device__ constexpr int grad_stride() { return DAMP ? 16 : 12; }
 
 // Record of one staged entry with every value twice, for packed arithmetic over a lane's two
-// pixels: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, o).
+// pixels: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, o), and with DAMP (hk, 0).
+template <bool DAMP>
 __device__ __forceinline__ void stage_dup(ulonglong2 (*s_e)[32], int i, const float4& A, const float4& B,
-                                          const float4& C) {
+                                          const float4& C, float hk) {
     s_e[0][i] = dup2(A.x, A.y);
     s_e[1][i] = dup2(A.z, A.w);
     s_e[2][i] = dup2(B.x, B.y);
     s_e[3][i] = dup2(B.z, B.w);
     s_e[4][i] = dup2(C.x, C.y);
     s_e[5][i] = dup2(C.z, C.w);
+    if constexpr (DAMP) s_e[6][i] = dup2(hk, 0.f);
 }
 
 // One entry at a lane's two pixels, before the transmittance: the offsets, the cutoff form, the
-// envelope, the modulation, alpha and whether the entry contributes to each pixel.
+// envelope, the modulation, alpha and whether the entry contributes to each pixel (with DAMP also
+// the cosine and the entry's hk).
 struct BwdEval {
-    f2 dx, dy, a, b, G, w, raw, sn;
+    f2 dx, dy, a, b, G, w, raw, sn, cs, hk;
     float alpha0, alpha1;
     bool k0, k1;
 };
+template <bool DAMP>
 __device__ __forceinline__ void bwd_eval(BwdEval& r, const ulonglong2 (*s_e)[32], int j, f2 PX, f2 PY,
                                          const BlendOpts3& o, bool live0, bool live1) {
     const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]);
@@ -55,7 +65,13 @@ __device__ __forceinline__ void bwd_eval(BwdEval& r, const ulonglong2 (*s_e)[32]
     const f2 ang = f2_reduced_angle(f2_fma(e2.y, r.dx, f2_fma(e3.x, r.dy, e3.y)));
     const float al = f2_lo(ang), ah = f2_hi(ang);
     const f2 HALF = f2_dup(0.5f);
-    r.w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(al), cos_approx(ah)), HALF), r.G);
+    if constexpr (DAMP) {
+        r.hk = ld_f2x2(&s_e[6][j]).x;
+        r.cs = f2_pack(cos_approx(al), cos_approx(ah));
+        r.w = f2_mul(f2_fma(r.hk, r.cs, HALF), r.G);
+    } else {
+        r.w = f2_mul(f2_fma(HALF, f2_pack(cos_approx(al), cos_approx(ah)), HALF), r.G);
+    }
     r.sn = f2_pack(sin_approx(al), sin_approx(ah));
     r.raw = f2_mul(e5.y, r.w);
     r.alpha0 = fminf(o.alpha_max, f2_lo(r.raw));
@@ -65,8 +81,10 @@ __device__ __forceinline__ void bwd_eval(BwdEval& r, const ulonglong2 (*s_e)[32]
 }
 // The entry's gradient at the lane's pixels, with the transmittance recovered in front of it and
 // the colour behind it advanced; the warp's sum is added to the primitive's image-plane gradient.
+template <bool DAMP>
 __device__ __forceinline__ void bwd_apply(const BwdEval& r, const ulonglong2 (*s_e)[32], int j, const BlendOpts3& o,
                                           f2& T, f2& S0, f2& S1, f2& S2, f2 g0, f2 g1, f2 g2, float* grad) {
+    constexpr int kG = grad_components<DAMP>();
     if (!__any_sync(0xffffffffu, r.k0 || r.k1)) return;
     const int lane = threadIdx.x & 31;
     const f2x2 e1 = ld_f2x2(&s_e[1][j]), e2 = ld_f2x2(&s_e[2][j]), e3 = ld_f2x2(&s_e[3][j]);
@@ -94,8 +112,15 @@ __device__ __forceinline__ void bwd_apply(const BwdEval& r, const ulonglong2 (*s
                            r.k1 && f2_hi(r.raw) < o.alpha_max ? f2_hi(galpha) : 0.f);
     acc[11] = f2_mul(gal, r.w);
     const f2 gW = f2_mul(gal, e5.y);
-    const f2 gq2 = f2_mul(NEG1, f2_mul(gW, r.w));                       // 2 dL/dq  (dW/dq = -W/2)
-    const f2 gt = f2_mul(f2_mul(f2_dup(-kPi), r.G), f2_mul(gW, r.sn));  // dL/dt, t in cycles
+    const f2 gq2 = f2_mul(NEG1, f2_mul(gW, r.w));  // 2 dL/dq  (dW/dq = -W/2)
+    // dL/dt, t in cycles: dW/dt = -2 pi hk sin(2 pi t) G (hk = 1/2 without DAMP)
+    f2 gt;
+    if constexpr (DAMP) {
+        gt = f2_mul(f2_mul(f2_mul(f2_dup(-2.f * kPi), r.hk), r.G), f2_mul(gW, r.sn));
+        acc[12] = f2_mul(f2_mul(gW, f2_dup(0.5f)), f2_mul(r.cs, r.G));  // dW/dkappa = cos G / 2
+    } else {
+        gt = f2_mul(f2_mul(f2_dup(-kPi), r.G), f2_mul(gW, r.sn));
+    }
     const f2 ga = f2_mul(gq2, r.a), gb = f2_mul(gq2, r.b);
     acc[2] = f2_mul(ga, r.dx);
     acc[3] = f2_mul(ga, r.dy);
@@ -123,6 +148,7 @@ __device__ __forceinline__ void bwd_apply(const BwdEval& r, const ulonglong2 (*s
 // with one atomic per component.  Batches of 32 entries are staged in shared memory with the bit
 // "the cutoff ellipse reaches the quad"; the records of the next batch are loaded while the
 // current one is processed.
+template <bool DAMP>
 __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
                                            const TileLists& tl, int W, int H, int tiles_x, const BlendOpts3& o,
                                            const float* __restrict__ T_final, const uint32_t* __restrict__ last,
@@ -188,6 +214,7 @@ __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const
     uint32_t b0 = end - min(end - lo, 32u);
     // software pipeline: records (and id) of the batch to stage next, id of the batch after it
     float4 nA = make_float4(0.f, 0.f, 0.f, 0.f), nB = nA, nC = nA;
+    float nK = 0.5f;
     PixRect nR{0, 0, -1, -1};
     uint32_t nid = 0u, np = 0u;
     if (b0 + lane < b_end) {
@@ -195,6 +222,7 @@ __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const
         nA = rec[(size_t)nid * kRecF4 + 0];
         nB = rec[(size_t)nid * kRecF4 + 1];
         nC = rec[(size_t)nid * kRecF4 + 2];
+        if (DAMP) nK = rec[(size_t)nid * kRecF4 + 3].w;
         nR = rect[nid];
     }
     uint32_t nb0 = b0 - min(b0 - lo, 32u);  // start of the next batch
@@ -205,7 +233,7 @@ __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const
         bool hit = false;
         if (lane < n) {
             s_id[lane] = nid;
-            stage_dup(s_e, lane, nA, nB, nC);
+            stage_dup<DAMP>(s_e, lane, nA, nB, nC, nK);
             float nBA, nBC;
             ellipse_edge_ratios(nA, nB.x, nBA, nBC);
             hit = box_touched_ellipse(nA, nB.x, nBA, nBC, nR, x0, y0, 8, 8, o.lim);
@@ -219,6 +247,7 @@ __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const
             nA = rec[(size_t)nid * kRecF4 + 0];
             nB = rec[(size_t)nid * kRecF4 + 1];
             nC = rec[(size_t)nid * kRecF4 + 2];
+            if (DAMP) nK = rec[(size_t)nid * kRecF4 + 3].w;
             nR = rect[nid];
         }
         if (nnb0 + lane < nb0) np = tl.prim[nnb0 + lane];
@@ -233,10 +262,12 @@ __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const
             const uint32_t pos1 = b0 - range.x + (uint32_t)j1 + 1u;  // 1-based positions in the tile list
             const uint32_t pos2 = b0 - range.x + (uint32_t)j2 + 1u;
             BwdEval ea, eb;
-            bwd_eval(ea, s_e, j1, PX, PY, o, in0 && pos1 <= last0, in1 && pos1 <= last1);
-            if (j2 >= 0) bwd_eval(eb, s_e, j2, PX, PY, o, in0 && pos2 <= last0, in1 && pos2 <= last1);
-            bwd_apply(ea, s_e, j1, o, T, S0, S1, S2, g0, g1, g2, grad_img + (size_t)s_id[j1] * kG);
-            if (j2 >= 0) bwd_apply(eb, s_e, j2, o, T, S0, S1, S2, g0, g1, g2, grad_img + (size_t)s_id[j2] * kG);
+            bwd_eval<DAMP>(ea, s_e, j1, PX, PY, o, in0 && pos1 <= last0, in1 && pos1 <= last1);
+            if (j2 >= 0) bwd_eval<DAMP>(eb, s_e, j2, PX, PY, o, in0 && pos2 <= last0, in1 && pos2 <= last1);
+            constexpr int kGS = grad_stride<DAMP>();
+            bwd_apply<DAMP>(ea, s_e, j1, o, T, S0, S1, S2, g0, g1, g2, grad_img + (size_t)s_id[j1] * kGS);
+            if (j2 >= 0)
+                bwd_apply<DAMP>(eb, s_e, j2, o, T, S0, S1, S2, g0, g1, g2, grad_img + (size_t)s_id[j2] * kGS);
         }
         b_end = b0;
         b0 = nb0;
@@ -246,6 +277,7 @@ __device__ __forceinline__ void bwd3d_unit(const float4* __restrict__ rec, const
 
 // Persistent: each warp takes (item, quad) units in order from a counter until they run out, so no
 // block is spent on an item past the last one.
+template <bool DAMP>
 __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ rec, const PixRect* __restrict__ rect,
                                                    TileLists tl, int W, int H, int tiles_x, BlendOpts3 o,
                                                    const float* __restrict__ T_final,
@@ -253,7 +285,7 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
                                                    const float* __restrict__ dl_dout,
                                                    float* __restrict__ grad_img, BwdChunks ch) {
     pdl_enter();
-    __shared__ ulonglong2 s_e[6][32];
+    __shared__ ulonglong2 s_e[DAMP ? 7 : 6][32];
     __shared__ uint32_t s_id[32];
     const uint32_t n_units = 4u * *ch.n_items;
     for (;;) {
@@ -262,8 +294,8 @@ __global__ void __launch_bounds__(32) k_backward3d(const float4* __restrict__ re
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= n_units) break;
         __syncwarp();
-        bwd3d_unit(rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout, grad_img, ch, s_e, s_id, unit >> 2,
-                   (int)(unit & 3u));
+        bwd3d_unit<DAMP>(rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout, grad_img, ch, s_e, s_id,
+                         unit >> 2, (int)(unit & 3u));
     }
 }
 
@@ -318,8 +350,13 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
     float p[WIPES_P3D];  // the record's geometry, frequency, phase, opacity and base colour
     load_row<VEC, WIPES_P3D>(p, params + i * stride);
     const float* p_sh = params + i * stride;  // the SH coefficients are read where they are used
-    float g[kG];
-    load_row<true, kG>(g, grad_img + (size_t)i * kG);
+    float g[16];
+    if (fmode == 2) {
+        load_row<true, 16>(g, grad_img + (size_t)i * 16);
+    } else {
+        load_row<true, 12>(g, grad_img + (size_t)i * 12);
+        g[12] = 0.f;
+    }
     float out[WIPES_P3D];
     const float g_mx = g[0], g_my = g[1], g11 = g[2], g21 = g[3], g22 = g[4], g_fx = g[5], g_fy = g[6];
     const float* V = cam.V;
@@ -403,14 +440,74 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
             gR[a * 3 + b] = gM * s[b];
             gs[b] += gM * R[a * 3 + b];
         }
-    float gqn[4];
-    quat_rot_grad(qn, gR, gqn);
-    const float dot = gqn[0] * qn[0] + gqn[1] * qn[1] + gqn[2] * qn[2] + gqn[3] * qn[3];
     // camera-frame frequency; with f' = J fc (fmode 1) dL/dJ gains dL/df' fc^T
     const float fcx = V[0] * p[10] + V[1] * p[11] + V[2] * p[12];
     const float fcy = V[4] * p[10] + V[5] * p[11] + V[6] * p[12];
     const float fcz = V[8] * p[10] + V[9] * p[11] + V[10] * p[12];
-    if (fmode) {
+    // frequency map 2 (integrated along the ray, as in the footprint kernel): reverse mode through
+    // m = A^T n, w = S^-2 m, c = m . w, b = A w, fn = fc . n, r = fn / c, f' = P0^T (fc - r b) and
+    // kappa = exp(-2 pi^2 fn r), with A = V R and n = (txz, tyz, 1); the pieces for the centre
+    // (through n and P0) and the frequency are kept for below
+    float gn0 = 0.f, gn1 = 0.f, gtz_map = 0.f, gfc_map[3] = {0.f, 0.f, 0.f};
+    if (fmode == 2) {
+        const float g_kap = g[12];
+        float A[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                A[a * 3 + b] = V[a * 4 + 0] * R[0 * 3 + b] + V[a * 4 + 1] * R[1 * 3 + b] + V[a * 4 + 2] * R[2 * 3 + b];
+        const float nv[3] = {txz, tyz, 1.f};
+        float m[3], wv[3], is2[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            m[b] = A[b] * txz + A[3 + b] * tyz + A[6 + b];
+            is2[b] = 1.f / (s[b] * s[b]);
+            wv[b] = m[b] * is2[b];
+        }
+        const float c = m[0] * wv[0] + m[1] * wv[1] + m[2] * wv[2];
+        const float bx = A[0] * wv[0] + A[1] * wv[1] + A[2] * wv[2];
+        const float by = A[3] * wv[0] + A[4] * wv[1] + A[5] * wv[2];
+        const float fn = fcx * txz + fcy * tyz + fcz;
+        const float ic = 1.f / c, r = fn * ic;
+        const float k2pi2 = 2.f * kPi * kPi;
+        const float kap = __expf(-k2pi2 * fn * r);
+        // f'x = (fcx - r bx) tz / fx, f'y = (fcy - r by) tz / fy, x = 2 pi^2 fn r, kappa = exp(-x)
+        const float gx = g_fx * tz / cam.fx, gy = g_fy * tz / cam.fy;
+        gtz_map = g_fx * (fcx - r * bx) / cam.fx + g_fy * (fcy - r * by) / cam.fy;
+        const float gxx = -kap * g_kap;
+        const float gr = -(gx * bx + gy * by) + k2pi2 * fn * gxx;
+        const float gbx = -r * gx, gby = -r * gy;
+        const float gfn = k2pi2 * r * gxx + gr * ic;
+        const float gc = -gr * r * ic;
+        gfc_map[0] = gx + gfn * txz;
+        gfc_map[1] = gy + gfn * tyz;
+        gfc_map[2] = gfn;
+        gn0 = gfn * fcx;
+        gn1 = gfn * fcy;
+        float gA[9];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float gw = A[b] * gbx + A[3 + b] * gby + gc * m[b];
+            const float gm = gc * wv[b] + gw * is2[b];
+            gs[b] += -2.f * gw * wv[b] / s[b];
+            gA[b] = gbx * wv[b] + nv[0] * gm;
+            gA[3 + b] = gby * wv[b] + nv[1] * gm;
+            gA[6 + b] = nv[2] * gm;
+            gn0 += A[b] * gm;
+            gn1 += A[3 + b] * gm;
+        }
+        // A = V R: dL/dR = V^T dL/dA (V's rows are the first three entries of cam.V's rows)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                gR[k * 3 + b] += V[0 * 4 + k] * gA[b] + V[1 * 4 + k] * gA[3 + b] + V[2 * 4 + k] * gA[6 + b];
+    }
+    float gqn[4];
+    quat_rot_grad(qn, gR, gqn);
+    const float dot = gqn[0] * qn[0] + gqn[1] * qn[1] + gqn[2] * qn[2] + gqn[3] * qn[3];
+    if (fmode == 1) {
         gj00 += g_fx * fcx;
         gj02 += g_fx * fcz;
         gj11 += g_fy * fcy;
@@ -421,19 +518,25 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
     float gtx = g_mx * cam.fx * iz;
     float gty = g_my * cam.fy * iz;
     float gtz = -g_mx * cam.fx * tx * iz2 - g_my * cam.fy * ty * iz2;
-    if (!fmode) gtz += g_fx * fcx / cam.fx + g_fy * fcy / cam.fy;
+    if (fmode == 0) gtz += g_fx * fcx / cam.fx + g_fy * fcy / cam.fy;
+    if (fmode == 2) gtz += gtz_map;
     gtz += -gj00 * cam.fx * iz2 - gj11 * cam.fy * iz2 + gj02 * cam.fx * txz * iz2 + gj12 * cam.fy * tyz * iz2;
     if (free_x) {
         gtx += -gj02 * cam.fx * iz2;
         gtz += gj02 * cam.fx * tx * iz2 * iz;
+        // map 2: txz = tx / tz
+        gtx += gn0 * iz;
+        gtz += -gn0 * tx * iz2;
     }
     if (free_y) {
         gty += -gj12 * cam.fy * iz2;
         gtz += gj12 * cam.fy * ty * iz2 * iz;
+        gty += gn1 * iz;
+        gtz += -gn1 * ty * iz2;
     }
-    const float gfc0 = fmode ? g_fx * j00 : g_fx * tz / cam.fx;
-    const float gfc1 = fmode ? g_fy * j11 : g_fy * tz / cam.fy;
-    const float gfc2 = fmode ? g_fx * j02 + g_fy * j12 : 0.f;
+    const float gfc0 = fmode == 2 ? gfc_map[0] : fmode ? g_fx * j00 : g_fx * tz / cam.fx;
+    const float gfc1 = fmode == 2 ? gfc_map[1] : fmode ? g_fy * j11 : g_fy * tz / cam.fy;
+    const float gfc2 = fmode == 2 ? gfc_map[2] : fmode ? g_fx * j02 + g_fy * j12 : 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         out[a] = V[0 * 4 + a] * gtx + V[1 * 4 + a] * gty + V[2 * 4 + a] * gtz;
@@ -495,7 +598,8 @@ __global__ void __launch_bounds__(128) k_chain3d(const float* __restrict__ param
 }  // namespace
 
 void launch_blend3d(const BlendJob& job, int tiles_y, const uint32_t* order, cudaStream_t stream) {
-    launch_pdl(k_blend3d, 4 * job.tiles_x * tiles_y, kQuadThreads, 0, stream, job, order);
+    if (job.o.damp) launch_pdl(k_blend3d<true>, 4 * job.tiles_x * tiles_y, kQuadThreads, 0, stream, job, order);
+    else launch_pdl(k_blend3d<false>, 4 * job.tiles_x * tiles_y, kQuadThreads, 0, stream, job, order);
     count_launches(1);
 }
 
@@ -505,12 +609,17 @@ void launch_backward3d(const float4* rec, const PixRect* rect, const TileLists& 
     if (max_items <= 0) return;
     cudaMemsetAsync(ch.counter, 0, sizeof(unsigned int), stream);
     int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward3d, 32, 0);
+    if (o.damp) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward3d<true>, 32, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward3d<false>, 32, 0);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = std::min<int64_t>((int64_t)std::max(1, per_sm) * std::max(1, sms), 4 * max_items);
-    launch_pdl(k_backward3d, (unsigned)grid, 32, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final, last, dl_dout,
-               grad_img, ch);
+    if (o.damp)
+        launch_pdl(k_backward3d<true>, (unsigned)grid, 32, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final, last,
+                   dl_dout, grad_img, ch);
+    else
+        launch_pdl(k_backward3d<false>, (unsigned)grid, 32, 0, stream, rec, rect, tl, W, H, tiles_x, o, T_final, last,
+                   dl_dout, grad_img, ch);
     count_launches(1);
 }
 

@@ -1,5 +1,7 @@
 """Device parity of the 3D path (EWA projection, frequency projection, front-to-back blending of the
 projected wavelets) and of the 6D time model against the binary64 oracle."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -17,6 +19,8 @@ LITERAL = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 1.0], np.f
 
 
 SH3 = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 0.0, 3.0], np.float32)  # SH colour, degree 3
+
+RAY = np.array([3.0, 1.0 / 255.0, 0.99, 1e-4, 0.3, 0.0, 0.0, 0.0, 2.0], np.float32)  # f integrated along the ray
 
 
 def _opts(w, o):
@@ -124,6 +128,48 @@ def test_literal_frequency_projection_matches_oracle(N, H, W, seed):
     grad = w.backward(st, params, torch.from_numpy(g).cuda())
     torch.cuda.synchronize()
     ref, gabs = oracle.grad3d(p, cam, H, W, g, LITERAL, with_abs=True)
+    ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)), pool="3d record")
+    assert ok, (worst, idx)
+
+
+@pytest.mark.parametrize("N,H,W,seed", [(600, 72, 88, 41), (1500, 100, 100, 42), (3000, 53, 131, 43)])
+def test_ray_integrated_frequency_matches_oracle(N, H, W, seed):
+    """freq_proj_mode 2 (the oscillation integrated along the viewing ray, with its damping kappa):
+    forward, the batch kernel's bits and gradients against the oracle.  The scene's frequencies
+    (up to 40 cycles/unit) give dampings from about 1 (small primitives) to about 0 (large ones)."""
+    torch = torch_cuda()
+    w = lib_ready()
+    from paper_2508_12615_gb300 import _abi
+
+    p = synth.scene3d(N, seed)
+    cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
+    kap = oracle.project3d(p, cam, H, W, RAY)[:, 14]
+    assert np.mean(kap < 0.5) > 0.1 and np.mean(kap > 0.9) > 0.1  # the damping spans its range
+    params, st, img = _gpu(w, torch, p, cam, H, W, RAY)
+    C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, RAY)
+    amb_img = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
+    check_amb_share(amb_img, "alpha_min / T_min bits")
+    err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
+    err[amb_img] = 0
+    assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    Tg = st.pixel_state()[0].cpu().numpy()
+    assert np.abs(Tg - T)[~amb_img].max() <= 1e-5
+    # the map changes the image
+    C0 = oracle.render3d(p, cam, H, W, DEFAULT)[0]
+    assert np.abs(C0 - C).max() > 10 * FWD_ATOL
+    # the persistent batch kernel renders the prepared frame to the same bits
+    out = torch.empty(H, W, 3, device="cuda")
+    _abi.call("wipes_blend_batch", w.Context.get(0).handle, (ctypes.c_void_p * 1)(st.handle.value),
+              (ctypes.c_void_p * 1)(out.data_ptr()), 1, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert torch.equal(out, img)
+    # gradients (the batch blend left the one-frame forward's records in place)
+    params, st, img = _gpu(w, torch, p, cam, H, W, RAY)
+    g = synth.upstream_grad(H, W, seed + 5)
+    g[amb_bits != 0] = 0.0
+    grad = w.backward(st, params, torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    ref, gabs = oracle.grad3d(p, cam, H, W, g, RAY, with_abs=True)
     ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)), pool="3d record")
     assert ok, (worst, idx)
 
