@@ -27,14 +27,15 @@
 // Rounding points: the encoding, weights, hidden activations and upstream gradients are rounded
 // to bfloat16 where they become product operands; biases, accumulators, the network outputs and
 // the encoding's gradient (both products summed in one accumulator) stay fp32.
-// Warp roles in the tile kernels: warp 0 streams weights, warp 1 issues the MMAs (one thread),
-// warps 2-9 run the epilogue (thread = row; warp w reads TMEM lanes 32 (w % 4) .., warps 2-5 the
+// Warp roles in the tile kernels: warps 0 and 10 stream weights (one thread each, half of every
+// block), warp 1 issues the MMAs (one thread), warps 2-9 run the epilogue (thread = row; warp w reads TMEM lanes 32 (w % 4) .., warps 2-5 the
 // output columns 0-127, warps 6-9 128-255).  Every wait on an mbarrier is bounded (2 s); one that
 // runs out sets bit 1 of the context's error word, every role leaves its loop, in-flight copies
 // and MMAs are waited for, and the tensor memory is freed before the block exits.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <utility>
 #include <mutex>
 #include <string>
 
@@ -67,7 +68,8 @@ __host__ __device__ constexpr int64_t layer_offset(int l) {
 constexpr int kRows = 128;                      // rows per tile: the MMA's M
 constexpr int kEpiWarps = 8;                    // two per SM sub-partition, each owning half the columns
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kTcThreads = 64 + kEpiThreads;    // warp 0 streams weights, warp 1 issues MMAs
+constexpr int kTcThreads = 96 + kEpiThreads;    // warps 0 and 10 stream weights, warp 1 issues MMAs
+constexpr int kProducer2 = 2 + kEpiWarps;       // the second weight-streaming warp
 constexpr int kWgThreads = 192;                 // weight gradient: 4 epilogue warps
 constexpr int kStages = 4;                      // weight stages: a whole 256-wide layer in flight
 constexpr uint32_t kABlock = kRows * 128;       // one K-block of a 128-row tile: 16 KB
@@ -103,7 +105,7 @@ struct Sched {
 
 // Forward, per tile: L0 (A = gamma in A K-blocks 4, 5: K 80), L1-L4 (A = h, K-blocks 0-3), L5 (A =
 // (h4, gamma), K-blocks 0-5: its image's columns are ordered h4 first), L6, L7, L8 (16 rows).
-constexpr Sched make_fwd() {
+__host__ __device__ constexpr Sched make_fwd() {
     Sched s{};
     uint32_t off = 0;
     auto add = [&](int akb, int steps, int n, bool first, bool last) {
@@ -129,7 +131,7 @@ constexpr Sched make_fwd() {
 }
 // Backward data, per tile: head (A = dd, one K step; B = W8^T), L7, L6, L5 (dh4 into columns
 // 0-255, then dgamma into columns 256-335), L4 .. L1, L0 (dgamma += dz0 W0).
-constexpr Sched make_bwd() {
+__host__ __device__ constexpr Sched make_bwd() {
     Sched s{};
     uint32_t off = 0;
     auto add = [&](int akb, int steps, int n, int dcol, bool first, bool last) {
@@ -281,17 +283,21 @@ __device__ __forceinline__ bool wait_or_abort(Ctl* ctl, uint64_t* bar, uint32_t 
     return false;
 }
 
-// Producer (warp 0, one thread): stream `per_tile` schedule entries for every tile of this block
-// through the stage ring; at the end wait for the copies still in flight.
+// Producers (warps 0 and 10, one thread each; `part` 0 or 1): stream the schedule's weight blocks
+// for every tile of this block through the stage ring, each producer one half of every block
+// (the bulk-copy rate per issuing thread is about half of what the SM's shared memory can take
+// in); a stage is full when both halves have landed.  At the end wait for the copies in flight.
 __device__ void produce_weights(Ctl* ctl, uint8_t* sW, const uint8_t* img, const Sched* S, int tiles,
-                                unsigned int* err) {
+                                unsigned int* err, int part) {
     uint32_t it = 0;
     for (int tile = blockIdx.x; tile < tiles && !ctl->abort; tile += gridDim.x) {
         for (int j = 0; j < S->n; ++j, ++it) {
             const uint32_t stage = it % kStages, round = it / kStages;
             if (round > 0 && !wait_or_abort(ctl, &ctl->empty[stage], (round - 1) & 1u, err)) goto drain;
-            tc::mbar_arrive_expect_tx(&ctl->full[stage], S->b[j].bytes);
-            tc::bulk_g2s(sW + stage * kWBlock, img + S->b[j].off, S->b[j].bytes, &ctl->full[stage]);
+            const uint32_t h0 = S->b[j].bytes / 32u * 16u;  // first half, a multiple of 16 bytes
+            const uint32_t off = part ? h0 : 0u, bytes = part ? S->b[j].bytes - h0 : h0;
+            tc::mbar_arrive_expect_tx(&ctl->full[stage], bytes);
+            if (bytes) tc::bulk_g2s(sW + stage * kWBlock + off, img + S->b[j].off + off, bytes, &ctl->full[stage]);
         }
     }
 drain:
@@ -301,33 +307,49 @@ drain:
 
 // MMA issuer (warp 1, one thread): for every tile, the schedule's groups, each after the
 // epilogue has its A operand ready; a stage is released when its MMAs complete, a group's end is
-// signalled on mma_done.  At the end, the MMAs in flight are waited for.
-__device__ void issue_mmas(Ctl* ctl, uint8_t* sA, uint8_t* sW, const Sched* S, int tiles, uint32_t tmem,
-                           unsigned int* err) {
-    uint32_t it = 0, ar = 0;
-    const uint32_t a0 = tc::smem_u32(sA), w0 = tc::smem_u32(sW);
-    for (int tile = blockIdx.x; tile < tiles && !ctl->abort; tile += gridDim.x) {
-        for (int j = 0; j < S->n; ++j, ++it) {
-            const Blk b = S->b[j];
-            if (j == 0 || S->b[j - 1].last) {  // a new group: its A operand comes from the epilogue
-                if (!wait_or_abort(ctl, &ctl->a_ready, ar & 1u, err)) goto drain;
-                ++ar;
-                tc::fence_after_sync();
-            }
-            const uint32_t stage = it % kStages;
-            if (!wait_or_abort(ctl, &ctl->full[stage], (it / kStages) & 1u, err)) goto drain;
-            tc::fence_after_sync();
-            const uint32_t idesc = tc::idesc_bf16(kRows, b.n);
-            for (int k = 0; k < b.steps; ++k) {
-                const uint64_t ad = tc::desc_sw128(a0 + b.akb * kABlock + 32u * k);
-                const uint64_t bd = tc::desc_sw128(w0 + stage * kWBlock + 32u * k);
-                tc::mma_bf16(tmem + b.dcol, ad, bd, idesc, (b.first && k == 0) ? 0u : 1u);
-            }
-            tc::mma_commit(&ctl->empty[stage]);
-            if (b.last) tc::mma_commit(&ctl->mma_done);
-        }
+// signalled on mma_done.  At the end, the MMAs in flight are waited for.  The schedule is expanded
+// at compile time (every block's A K-block, steps, N, accumulator column and flags are constants):
+// a tcgen05.mma takes about as long to issue as to run, so the issuing thread keeps nothing but
+// the MMAs, the commits and one test of each stage's barrier between them.
+template <bool BWD, int J>
+__device__ __forceinline__ bool issue_block(Ctl* ctl, uint32_t& it, uint32_t& ar, uint64_t adesc0, uint64_t wdesc0,
+                                            uint32_t tmem, unsigned int* err) {
+    constexpr Blk b = (BWD ? make_bwd() : make_fwd()).b[J];
+    constexpr bool group_start = J == 0 || (BWD ? make_bwd() : make_fwd()).b[J - 1].last;
+    constexpr uint32_t idesc = tc::idesc_bf16(kRows, b.n);
+    if (group_start) {  // a new group: its A operand comes from the epilogue
+        if (!wait_or_abort(ctl, &ctl->a_ready, ar & 1u, err)) return false;
+        ++ar;
+        tc::fence_after_sync();
     }
-drain:
+    const uint32_t stage = it % kStages;
+    if (!tc::mbar_try_wait(&ctl->full[stage], (it / kStages) & 1u) &&
+        !wait_or_abort(ctl, &ctl->full[stage], (it / kStages) & 1u, err))
+        return false;
+    tc::fence_after_sync();
+    // descriptor start addresses are in 16-byte units
+    const uint64_t ad = adesc0 + (uint64_t)((b.akb * kABlock) >> 4);
+    const uint64_t bd = wdesc0 + (uint64_t)((stage * kWBlock) >> 4);
+#pragma unroll
+    for (int k = 0; k < b.steps; ++k)
+        tc::mma_bf16(tmem + b.dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (b.first && k == 0) ? 0u : 1u);
+    tc::mma_commit(&ctl->empty[stage]);
+    if (b.last) tc::mma_commit(&ctl->mma_done);
+    ++it;
+    return true;
+}
+template <bool BWD, int... J>
+__device__ __forceinline__ bool issue_tile(Ctl* ctl, uint32_t& it, uint32_t& ar, uint64_t adesc0, uint64_t wdesc0,
+                                           uint32_t tmem, unsigned int* err, std::integer_sequence<int, J...>) {
+    return (issue_block<BWD, J>(ctl, it, ar, adesc0, wdesc0, tmem, err) && ...);
+}
+template <bool BWD>
+__device__ void issue_mmas(Ctl* ctl, uint8_t* sA, uint8_t* sW, int tiles, uint32_t tmem, unsigned int* err) {
+    constexpr int nblk = (BWD ? make_bwd() : make_fwd()).n;
+    uint32_t it = 0, ar = 0;
+    const uint64_t adesc0 = tc::desc_sw128(tc::smem_u32(sA)), wdesc0 = tc::desc_sw128(tc::smem_u32(sW));
+    for (int tile = blockIdx.x; tile < tiles && !ctl->abort; tile += gridDim.x)
+        if (!issue_tile<BWD>(ctl, it, ar, adesc0, wdesc0, tmem, err, std::make_integer_sequence<int, nblk>{})) break;
     tc::mma_commit(&ctl->drain);
     tc::mbar_wait(&ctl->drain, 0, kWaitNs);
 }
@@ -454,7 +476,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->full[s], 2);
             tc::mbar_init(&ctl->empty[s], 1);
         }
         tc::mbar_init(&ctl->mma_done, 1);
@@ -474,10 +496,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
     tc::fence_after_sync();
     const uint32_t tmem = ctl->tmem;
 
-    if (warp == 0) {
-        if (lane == 0) produce_weights(ctl, sW, P.wimg, &s_sched, P.tiles, P.err);
+    if (warp == 0 || warp == kProducer2) {
+        if (lane == 0) produce_weights(ctl, sW, P.wimg, &s_sched, P.tiles, P.err, warp == kProducer2);
     } else if (warp == 1) {
-        if (lane == 0) issue_mmas(ctl, sA, sW, &s_sched, P.tiles, tmem, P.err);
+        if (lane == 0) issue_mmas<false>(ctl, sA, sW, P.tiles, tmem, P.err);
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; warps 2-5 own columns 0-127, 6-9 128-255
         const int ew = warp - 2, q = warp & 3, half = ew >> 2, r = q * 32 + lane;
@@ -539,27 +561,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                     break;
                 }
                 await_a_free(lead);
-                // bias (packed f32x2 add), ReLU and bfloat16 rounding (one instruction per pair)
+                // bias (packed f32x2 add), ReLU and bfloat16 rounding (one instruction per pair), 64
+                // columns at a time: both tensor-memory loads and the bias loads are in flight
+                // before the one wait
                 const float4* b4 = reinterpret_cast<const float4*>(P.bias + l * kWidth + half * 128);
 #pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int c = half * 4 + cc;
-                    uint32_t v[32];
-                    tc::tmem_ld32(tl + 32u * c, v);
-                    tc::tmem_wait_ld();
-                    uint32_t w[16];
+                for (int cp = 0; cp < 2; ++cp) {
+                    const int c = half * 4 + 2 * cp;
+                    uint32_t v0[32], v1[32];
+                    tc::tmem_ld32(tl + 32u * c, v0);
+                    tc::tmem_ld32(tl + 32u * (c + 1), v1);
+                    float4 b[16];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 b = __ldg(b4 + cc * 8 + j);
-                        const f2 z0 = f2_add(f2_pack(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1])),
-                                             f2_pack(b.x, b.y));
-                        const f2 z1 = f2_add(f2_pack(__uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3])),
-                                             f2_pack(b.z, b.w));
+                    for (int j = 0; j < 16; ++j) b[j] = __ldg(b4 + cp * 16 + j);
+                    tc::tmem_wait_ld();
+                    uint32_t w[32];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const uint32_t* v = j < 8 ? v0 + 4 * j : v1 + 4 * (j - 8);
+                        const f2 z0 = f2_add(f2_pack(__uint_as_float(v[0]), __uint_as_float(v[1])), f2_pack(b[j].x, b[j].y));
+                        const f2 z1 = f2_add(f2_pack(__uint_as_float(v[2]), __uint_as_float(v[3])), f2_pack(b[j].z, b[j].w));
                         w[2 * j] = pack_bf16_relu(f2_lo(z0), f2_hi(z0));
                         w[2 * j + 1] = pack_bf16_relu(f2_lo(z1), f2_hi(z1));
                     }
                     store_a16(a0, r, 32 * c, w);
                     store_a16(a0, r, 32 * c + 16, w + 8);
+                    store_a16(a0, r, 32 * c + 32, w + 16);
+                    store_a16(a0, r, 32 * c + 48, w + 24);
                 }
                 publish_a(ctl, lead, sA, 0, 4, P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
             }
@@ -607,7 +635,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(&ctl->full[s], 1);
+            tc::mbar_init(&ctl->full[s], 2);
             tc::mbar_init(&ctl->empty[s], 1);
         }
         tc::mbar_init(&ctl->mma_done, 1);
@@ -627,10 +655,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
     tc::fence_after_sync();
     const uint32_t tmem = ctl->tmem;
 
-    if (warp == 0) {
-        if (lane == 0) produce_weights(ctl, sW, P.wimg, &s_sched, P.tiles, P.err);
+    if (warp == 0 || warp == kProducer2) {
+        if (lane == 0) produce_weights(ctl, sW, P.wimg, &s_sched, P.tiles, P.err, warp == kProducer2);
     } else if (warp == 1) {
-        if (lane == 0) issue_mmas(ctl, sA, sW, &s_sched, P.tiles, tmem, P.err);
+        if (lane == 0) issue_mmas<true>(ctl, sA, sW, P.tiles, tmem, P.err);
     } else {
         const int ew = warp - 2, q = warp & 3, half = ew >> 2, r = q * 32 + lane;
         const bool lead = ew == 0 && lane == 0;
