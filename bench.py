@@ -594,31 +594,23 @@ def our_arm(args, rank: int, world: int, local_rank: int):
     pk, pk_kind = peaks()
     roofline, pairs = roofline_of(wl, stages, pk, pk_kind)
 
-    # the deformation network: its layers do 2 x 256 x K flops per row against (K + 256) x 2 bytes
-    # (K <= 336), about 127 flop per byte, below the GPU's balance point (measured bf16 peak over HBM
-    # copy bandwidth, about 250): the chain of products is bound by HBM.  Bytes per row that this
-    # layer-by-layer implementation moves (bfloat16 activations and gradients, fp32 records):
-    #   forward  160 encode + 672 + 4 x 1024 + 1184 + 2 x 1024 hidden + 8 x 32 ReLU bit-masks + 576 head
-    #            + 224 apply = 9216
-    #   backward 336 apply + 1088 head + 24448 for the 8 hidden layers (1056 ReLU pass: gradient in
-    #            and out, mask byte; 1024 + 2 K for the two products each) + 480 encoding = 26352
+    # the deformation network is a dense contraction on the tensor cores: per row and layer
+    # 2 x out x in flops forward and twice that backward (dh = dz W and dW = dz^T x), so
+    # 6 x sum(out x in) flops per row for one forward and backward; bf16 operands, fp32
+    # accumulation, against the measured sustained bf16 rate (the network runs inside a long step)
     roofline_mlp = None
     if wl.kind == "6dmlp" and "mlp_fwd" in stages:
         rows = wl.p.shape[0]
         macs = sum(o * i for o, i in synth.MLP_SHAPES) * rows
         t_f = stages["mlp_fwd"]["ms_per_launch"] * 1e-3
         t_b = stages["mlp_bwd"]["ms_per_launch"] * 1e-3
-        byts = (9216 + 26352) * rows
-        hbm = float(pk.get("hbm_gbs", 6800.0))
-        peak_bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))
-        ach = byts / (t_f + t_b) / 1e9
-        roofline_mlp = {"bound": "hbm", "kernel": "deformation network (encode, 9 layers, apply; forward and backward)",
-                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                        "peak_source": f"{pk_kind} HBM copy bandwidth",
-                        "work": f"{byts / rows:.0f} bytes per row moved by the layer-by-layer products x {rows} rows",
-                        "tensor_tflops": 6.0 * macs / (t_f + t_b) / 1e12,
-                        "tensor_frac": 6.0 * macs / (t_f + t_b) / 1e12 / peak_bf16,
-                        "fwd_gbs": 9216 * rows / t_f / 1e9, "bwd_gbs": 26352 * rows / t_b / 1e9}
+        peak_bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0)))
+        ach = 6.0 * macs / (t_f + t_b) / 1e12
+        roofline_mlp = {"bound": "tensor", "kernel": "deformation network (encode, 9 layers, apply; forward and backward)",
+                        "achieved": ach, "peak": peak_bf16, "unit": "TFLOP/s", "frac": ach / peak_bf16, "traffic": None,
+                        "peak_source": f"{pk_kind} sustained bf16 (cuBLAS)",
+                        "work": f"6 x {macs // rows} multiply-adds per row x {rows} rows",
+                        "fwd_tflops": 2.0 * macs / t_f / 1e12, "bwd_tflops": 4.0 * macs / t_b / 1e12}
 
     configs = {}
     for o, mo in others:
