@@ -264,7 +264,9 @@ __device__ __forceinline__ void chain_rs(const float* p, float g11, float g21, f
     out[4] = g11 * d11_th + g21 * d21_th + g22 * d22_th;
 }
 
-// One warp per primitive: sum its slots, then chain (mx, my, L, f, phc, c) to the record
+constexpr int kChainPrims = 8;  // primitives per warp in k_reduce_chain2d
+
+// One warp per kChainPrims primitives: sum each one's slots, then chain (mx, my, L, f, phc, c) to the record
 // mu, s, theta, f, phi, c.  L depends on (theta, s_x, s_y) through
 // A = c^2/sx^2 + s^2/sy^2, B = c s (1/sx^2 - 1/sy^2), l11 = sqrt(A), l21 = B/l11, l22 = 1/(sx sy l11);
 // for the Cholesky record (cov2d = 1) on (l1, l2, l3) through, with u = l2^2 + l3^2, s = sqrt(u):
@@ -280,14 +282,16 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
                                                         const float* __restrict__ partial,
                                                         float* __restrict__ dl_dparams) {
     pdl_enter();
-    // a warp takes 32 consecutive primitives: its half-warps sum the slots of two of them at a time
-    // (lanes over the slots, coalesced), keeping the 11 totals of primitive k in s_tot[warp][k];
-    // then lane k chains primitive k, all 32 at once
-    __shared__ float s_tot[8][32][12];
+    // a warp takes kChainPrims consecutive primitives: its half-warps sum the slots of two of them
+    // at a time (lanes over the slots, coalesced), keeping the 11 totals of primitive k in
+    // s_tot[warp][k]; then lane k chains primitive k.  The slot loads are the kernel's latency, so
+    // a few primitives per warp and many warps hide it best.
+    __shared__ float s_tot[8][kChainPrims][12];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int hl = lane & 15, half = lane >> 4;
-    const int64_t prim0 = (((int64_t)blockIdx.x * blockDim.x) >> 5 << 5) + (int64_t)warp * 32;
-    for (int k2 = 0; k2 < 32; k2 += 2) {
+    const int64_t prim0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * kChainPrims;
+#pragma unroll
+    for (int k2 = 0; k2 < kChainPrims; k2 += 2) {
         if (prim0 + k2 >= N) break;  // uniform across the warp
         const int64_t pk = prim0 + k2 + half;
         const uint32_t off = pk < N ? offsets[pk] : 0u, cnt = pk < N ? counts[pk] : 0u;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     }
     __syncwarp();
     const int64_t prim = prim0 + lane;
-    if (prim >= N) return;
+    if (lane >= kChainPrims || prim >= N) return;
     const float* t = s_tot[warp][lane];
     const uint32_t cnt = counts[prim];
     const float* p = params + prim * WIPES_P2D;
@@ -410,11 +414,12 @@ void launch_count_pairs(const float4* rec, const TileLists& tl, int W, int H, in
 void launch_reduce_chain2d(const float* params, int64_t N, int cov2d, const uint32_t* offsets, const uint32_t* counts,
                            const float* partial, float* dl_dparams, cudaStream_t stream) {
     if (N == 0) return;
+    const int64_t blocks = ceil_div(N, 8 * kChainPrims);  // 8 warps per block
     if ((reinterpret_cast<uintptr_t>(dl_dparams) & 15u) == 0)
-        launch_pdl(k_reduce_chain2d<true>, ceil_div(N, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial,
+        launch_pdl(k_reduce_chain2d<true>, blocks, 256, 0, stream, params, N, cov2d, offsets, counts, partial,
                    dl_dparams);
     else
-        launch_pdl(k_reduce_chain2d<false>, ceil_div(N, 256), 256, 0, stream, params, N, cov2d, offsets, counts, partial,
+        launch_pdl(k_reduce_chain2d<false>, blocks, 256, 0, stream, params, N, cov2d, offsets, counts, partial,
                    dl_dparams);
     count_launches(1);
 }
