@@ -87,6 +87,12 @@ constexpr uint32_t kHtLayer = 4 * kABlock;            // a 256-wide layer: 64 KB
 constexpr uint32_t kHtTile = kHidden * kHtLayer;      // 8 layers: 512 KB
 constexpr uint32_t kGtTile = 2 * kABlock;             // gamma: features 0-63 and 64-79 (+ padding)
 constexpr uint32_t kDdTile = kABlock;                 // dL/dd: 16 features (+ padding)
+// ReLU masks of a tile's hidden layers, written by the forward for the backward: per layer and row
+// 256 bits, 8 words (word w covers columns 32 w .. 32 w + 31: bit j is column 32 w + 2 j, bit
+// 16 + j column 32 w + 2 j + 1, set where the ReLU output is positive), the order in which packed
+// bfloat16 pairs give up their halves most cheaply
+constexpr uint32_t kMkLayer = kRows * 32;             // 4 KB
+constexpr uint32_t kMkTile = kHidden * kMkLayer;      // 32 KB
 
 // ---- weight streams ------------------------------------------------------------------------------
 // One entry per K-block an MMA group reads: the image's byte offset and size, the A K-block, the K
@@ -267,7 +273,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 
 // Control block of a tile kernel in shared memory.
 struct Ctl {
-    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain, g_full;
+    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain, g_full, mk_full[2];
     uint32_t tmem;
     volatile int abort;
 };
@@ -365,6 +371,7 @@ struct FwdArgs {
     float* params_out;     // [N, 20]
     uint8_t* ht;           // [tiles][8 layers][4 K-blocks of 16 KB] hidden activations
     const uint8_t* gt;     // [tiles][2 K-blocks of 16 KB] encoding (written by k_mlp_encode)
+    uint8_t* mk;           // [tiles][8 layers][128 rows][8 words] ReLU masks
     unsigned int* err;
     int tiles;
     int vec;               // params3 / params_out rows 16-byte aligned
@@ -588,6 +595,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                     store_a16(a0, r, 32 * c + 16, w + 8);
                     store_a16(a0, r, 32 * c + 32, w + 16);
                     store_a16(a0, r, 32 * c + 48, w + 24);
+                    // the ReLU masks of these 64 columns for the backward (the ReLU output is +0 or
+                    // positive, so a nonzero half is a positive one)
+                    uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        m0 |= __vcmpne2(w[j], 0u) & (0x00010001u << j);
+                        m1 |= __vcmpne2(w[16 + j], 0u) & (0x00010001u << j);
+                    }
+                    *reinterpret_cast<uint2*>(P.mk + ((size_t)tile * kHidden + l) * kMkLayer + (size_t)r * 32u +
+                                              (size_t)c * 4u) = make_uint2(m0, m1);
                 }
                 publish_a(ctl, lead, sA, 0, 4, P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
             }
@@ -610,7 +627,7 @@ struct BwdArgs {
     const float* g_out;    // [N, 20]
     float* g_params3;      // [N, 20]
     int accumulate;
-    const uint8_t* ht;     // the forward's hidden activations (their sign is the ReLU mask)
+    const uint8_t* mk;     // the forward's ReLU masks (kMkTile per tile)
     uint8_t* dzt;          // [tiles][8 layers][4 K-blocks of 16 KB] dz
     uint8_t* ddt;          // [tiles][1 K-block of 16 KB] dL/dd
     float* dgam;           // [N, 80] dL/dgamma (fp32), for k_mlp_encode_backward
@@ -620,7 +637,7 @@ struct BwdArgs {
     int vec;
 };
 
-constexpr uint32_t kBwdSmem = 1024 + 4 * kABlock + kStages * kWBlock + kBiasFloats * 4 + sizeof(Ctl);
+constexpr uint32_t kBwdSmem = 1024 + 4 * kABlock + kStages * kWBlock + 2 * kMkLayer + kBiasFloats * 4 + sizeof(Ctl);
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant__ BwdArgs P) {
     pdl_enter();  // inputs written by the previous kernel on the stream
@@ -630,7 +647,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
     if (threadIdx.x == 0) s_sched.n = c_bwd.n;
     uint8_t* sA = align1024(smem_raw);        // 4 K-blocks: dd (K-block 0, 16 columns) or dz
     uint8_t* sW = sA + 4 * kABlock;
-    float* s_db = reinterpret_cast<float*>(sW + kStages * kWBlock);  // bias gradients of this block
+    uint8_t* sMk = sW + kStages * kWBlock;     // two slots of a layer's ReLU masks (layer l in slot l & 1)
+    float* s_db = reinterpret_cast<float*>(sMk + 2 * kMkLayer);  // bias gradients of this block
     Ctl* ctl = reinterpret_cast<Ctl*>(s_db + kBiasFloats);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -642,6 +660,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
         tc::mbar_init(&ctl->a_ready, kEpiThreads);
         tc::mbar_init(&ctl->tmem_free, kEpiThreads);
         tc::mbar_init(&ctl->drain, 1);
+        tc::mbar_init(&ctl->mk_full[0], 1);
+        tc::mbar_init(&ctl->mk_full[1], 1);
         ctl->abort = 0;
         tc::fence_mbar_init();
     }
@@ -665,9 +685,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const uint32_t a0 = tc::smem_u32(sA);
         uint32_t md = 0;
+        // the lead copies each layer's masks into slot l & 1 one layer ahead: fills[s] counts the
+        // copies issued into slot s (by the lead), used[s] those waited for (by every thread)
+        uint32_t fills[2] = {0u, 0u}, used[2] = {0u, 0u};
+        auto fetch_masks = [&](int tile, int l) {
+            const int slot = l & 1;
+            tc::fence_proxy_async();  // the slot's previous masks were read by the generic proxy
+            tc::mbar_arrive_expect_tx(&ctl->mk_full[slot], kMkLayer);
+            tc::bulk_g2s(sMk + (size_t)slot * kMkLayer, P.mk + ((size_t)tile * kHidden + l) * kMkLayer, kMkLayer,
+                         &ctl->mk_full[slot]);
+            ++fills[slot];
+        };
         for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * kRows + r;
             const bool valid = row < P.N;
+            if (lead) fetch_masks(tile, kHidden - 1);
             await_a_free(lead);
             if (half == 0) {
                 // the record update's backward: dL/dd (rounded: the head's product operand) and the
@@ -747,20 +779,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
                     tc::fence_before_sync();
                     break;
                 }
-                // h_l of this row (the forward's copy of its A operand): its positive entries are the
-                // ReLU mask; a packed signed compare turns each bfloat16 pair into a keep mask
-                const uint8_t* hrow = P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer;
+                // the ReLU mask of h_l for this row (the forward wrote it, the lead copied it into
+                // slot l & 1 a layer ago): every thread waits for the copy, the lead then fetches the
+                // next layer's into the other slot (read by every thread before this layer's
+                // await_mma barrier)
+                {
+                    const int slot = l & 1;
+                    const bool ok = wait_or_abort(ctl, &ctl->mk_full[slot], used[slot] & 1u, P.err);
+                    ++used[slot];
+                    if (lead && ok && l > 0) fetch_masks(tile, l - 1);
+                }
                 await_a_free(lead);
+                const uint4 mw4 = *reinterpret_cast<const uint4*>(sMk + (size_t)(l & 1) * kMkLayer + (size_t)r * 32u +
+                                                                 (size_t)half * 16u);
 #pragma unroll 1
                 for (int cc = 0; cc < 4; ++cc) {
                     const int c = half * 4 + cc;
-                    uint32_t hw[16];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint4 u = __ldg(reinterpret_cast<const uint4*>(
-                            hrow + tc::sw128_chunk(kRows, (uint32_t)r, (uint32_t)c / 2u, (uint32_t)(c % 2) * 4u + k)));
-                        hw[4 * k] = u.x; hw[4 * k + 1] = u.y; hw[4 * k + 2] = u.z; hw[4 * k + 3] = u.w;
-                    }
+                    const uint32_t mword = cc == 0 ? mw4.x : cc == 1 ? mw4.y : cc == 2 ? mw4.z : mw4.w;
                     uint32_t v[32];
                     tc::tmem_ld32(tl + 32u * c, v);
                     tc::tmem_wait_ld();
@@ -768,7 +803,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
                     float s32[32];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        w[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])) & __vcmpgts2(hw[j], 0u);
+                        const uint32_t keep = ((mword >> j) & 0x00010001u) * 0xFFFFu;
+                        w[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])) & keep;
                         s32[2 * j] = bf16_lo(w[j]);
                         s32[2 * j + 1] = bf16_hi(w[j]);
                     }
@@ -781,7 +817,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
             }
         }
     done:
-        if (lead) tc::bulk_wait_all();
+        if (lead) {
+            // masks copied into a slot but not waited for (a role gave up): let the copies land
+            for (int sl = 0; sl < 2; ++sl)
+                for (; used[sl] < fills[sl]; ++used[sl]) tc::mbar_wait(&ctl->mk_full[sl], used[sl] & 1u, kWaitNs);
+            tc::bulk_wait_all();
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1074,16 +1115,17 @@ int sm_count() {
 }
 
 // Layout of the state buffers (mlp_sizes): theta16 = forward images, backward images, bias;
-// act = h^T tiles, gamma^T tiles, masks; scratch = dz^T tiles, dd^T tiles, partials.
+// act = h^T tiles, gamma^T tiles, ReLU mask tiles; scratch = dz^T tiles, dd^T tiles, partials.
 struct ActLayout {
-    size_t ht, gt, total;
+    size_t ht, gt, mk, total;
 };
 ActLayout act_layout(int64_t N) {
     const size_t tiles = (size_t)tiles_of(std::max<int64_t>(N, 1));
     ActLayout a;
     a.ht = 0;
     a.gt = tiles * kHtTile;
-    a.total = a.gt + tiles * kGtTile;
+    a.mk = a.gt + tiles * kGtTile;
+    a.total = a.mk + tiles * kMkTile;
     return a;
 }
 struct ScratchLayout {
@@ -1136,6 +1178,7 @@ std::string mlp_forward(const float* params3, int64_t N, float t, const float* t
     P.params_out = params_out;
     P.ht = ab + a.ht;
     P.gt = ab + a.gt;
+    P.mk = ab + a.mk;
     P.err = err;
     P.tiles = tiles_of(N);
     P.vec = ((reinterpret_cast<uintptr_t>(params3) | reinterpret_cast<uintptr_t>(params_out)) & 15u) == 0;
@@ -1167,7 +1210,7 @@ std::string mlp_backward(const float* params3, int64_t N, const void* theta16_bu
     B.g_out = g_out;
     B.g_params3 = g_params3;
     B.accumulate = accumulate;
-    B.ht = ab + a.ht;
+    B.mk = ab + a.mk;
     B.dzt = sb + sl.dzt;
     B.ddt = sb + sl.ddt;
     B.dgam = reinterpret_cast<float*>(sb + sl.dgam);
