@@ -273,7 +273,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 
 // Control block of a tile kernel in shared memory.
 struct Ctl {
-    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain, g_full, mk_full[2];
+    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain, g_full, mk_full[2], b_full;
     uint32_t tmem;
     volatile int abort;
 };
@@ -377,7 +377,7 @@ struct FwdArgs {
     int vec;               // params3 / params_out rows 16-byte aligned
 };
 
-constexpr uint32_t kFwdSmem = 1024 + 6 * kABlock + kStages * kWBlock + sizeof(Ctl);
+constexpr uint32_t kFwdSmem = 1024 + 6 * kABlock + kStages * kWBlock + kWidth * 4 + sizeof(Ctl);
 
 // The epilogue warps' hand-off around an A operand that they rewrite: the copy of its previous
 // contents to global memory (issued by one thread) must have read them first.
@@ -479,7 +479,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
     if (threadIdx.x == 0) s_sched.n = c_fwd.n;
     uint8_t* sA = align1024(smem_raw);        // 6 K-blocks: h (0-3), gamma (4-5)
     uint8_t* sW = sA + 6 * kABlock;           // stage ring
-    Ctl* ctl = reinterpret_cast<Ctl*>(sW + kStages * kWBlock);
+    float* s_bias = reinterpret_cast<float*>(sW + kStages * kWBlock);  // the current hidden layer's bias
+    Ctl* ctl = reinterpret_cast<Ctl*>(s_bias + kWidth);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -491,6 +492,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
         tc::mbar_init(&ctl->tmem_free, kEpiThreads);
         tc::mbar_init(&ctl->drain, 1);
         tc::mbar_init(&ctl->g_full, 1);
+        tc::mbar_init(&ctl->b_full, 1);
         ctl->abort = 0;
         tc::fence_mbar_init();
     }
@@ -514,14 +516,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const uint32_t a0 = tc::smem_u32(sA);
         uint32_t md = 0, ng = 0;
+        uint32_t bfills = 0, bused = 0;  // bias copies issued (lead) and waited for (every thread)
+        auto fetch_bias = [&](int l) {
+            tc::fence_proxy_async();  // the previous layer's bias was read by the generic proxy
+            tc::mbar_arrive_expect_tx(&ctl->b_full, kWidth * 4);
+            tc::bulk_g2s(s_bias, P.bias + (size_t)l * kWidth, kWidth * 4, &ctl->b_full);
+            ++bfills;
+        };
         for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * kRows + r;
             const bool valid = row < P.N;
-            // the tile's encoding (written by k_mlp_encode) into A K-blocks 4 and 5
+            // the tile's encoding (written by k_mlp_encode) into A K-blocks 4 and 5, and layer 0's
+            // bias into s_bias (each hidden layer's bias is copied there once the previous layer's
+            // epilogue has read its own, so it lands while the layer's MMAs run)
             await_a_free(lead);
             if (lead) {
                 tc::mbar_arrive_expect_tx(&ctl->g_full, kGtTile);
                 tc::bulk_g2s(sA + 4 * kABlock, P.gt + (size_t)tile * kGtTile, kGtTile, &ctl->g_full);
+                fetch_bias(0);
             }
             {
                 const bool ok = wait_or_abort(ctl, &ctl->g_full, ng & 1u, P.err);
@@ -567,11 +579,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                     tc::fence_before_sync();
                     break;
                 }
+                // this layer's bias in s_bias (a wait that runs out raises the abort flag, and the
+                // next await_mma takes every epilogue thread out together)
+                (void)wait_or_abort(ctl, &ctl->b_full, bused & 1u, P.err);
+                ++bused;
                 await_a_free(lead);
                 // bias (packed f32x2 add), ReLU and bfloat16 rounding (one instruction per pair), 64
-                // columns at a time: both tensor-memory loads and the bias loads are in flight
-                // before the one wait
-                const float4* b4 = reinterpret_cast<const float4*>(P.bias + l * kWidth + half * 128);
+                // columns at a time: both tensor-memory loads are in flight before the one wait
+                const float4* b4 = reinterpret_cast<const float4*>(s_bias + half * 128);
 #pragma unroll 1
                 for (int cp = 0; cp < 2; ++cp) {
                     const int c = half * 4 + 2 * cp;
@@ -580,7 +595,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                     tc::tmem_ld32(tl + 32u * (c + 1), v1);
                     float4 b[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) b[j] = __ldg(b4 + cp * 16 + j);
+                    for (int j = 0; j < 16; ++j) b[j] = b4[cp * 16 + j];
                     tc::tmem_wait_ld();
                     uint32_t w[32];
 #pragma unroll
@@ -607,10 +622,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                                               (size_t)c * 4u) = make_uint2(m0, m1);
                 }
                 publish_a(ctl, lead, sA, 0, 4, P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
+                // every thread has read s_bias (publish_a's barrier): the next hidden layer's bias
+                if (lead && l + 1 < kHidden) fetch_bias(l + 1);
             }
         }
     done:
-        if (lead) tc::bulk_wait_all();
+        if (lead) {
+            for (; bused < bfills; ++bused) tc::mbar_wait(&ctl->b_full, bused & 1u, kWaitNs);  // copies still in flight
+            tc::bulk_wait_all();
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
