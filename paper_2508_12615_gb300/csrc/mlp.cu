@@ -820,20 +820,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
                     tc::tmem_ld32(tl + 32u * c, v);
                     tc::tmem_wait_ld();
                     uint32_t w[16];
-                    float s32[32];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const uint32_t keep = ((mword >> j) & 0x00010001u) * 0xFFFFu;
                         w[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])) & keep;
-                        s32[2 * j] = bf16_lo(w[j]);
-                        s32[2 * j + 1] = bf16_hi(w[j]);
                     }
                     store_a16(a0, r, 32 * c, w);
                     store_a16(a0, r, 32 * c + 16, w + 8);
-                    const float tot = warp_reduce_scatter32(s32);
-                    atomicAdd(&s_db[l * kWidth + 32 * c + lane], tot);
                 }
                 publish_a(ctl, lead, sA, 0, 4, P.dzt + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
+                // the bias gradient of layer l: the column sums of dz over the tile's rows, read back
+                // from the A operand just published while the next product runs (thread t sums
+                // columns 2 (t % 128), + 1 over rows 64 (t / 128) .. + 63; the A operand is next
+                // rewritten only after the await_mma barrier that every thread reaches)
+                {
+                    const uint32_t t = (uint32_t)(ew * 32 + lane), col = 2u * (t & 127u), rh = t >> 7;
+                    const uint32_t kb = col / 64u, cch = (col % 64u) / 8u, e = col % 8u;
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+                    for (uint32_t i = 0; i < 64u; ++i) {
+                        const uint32_t v2 = *reinterpret_cast<const uint32_t*>(
+                            sA + tc::sw128_chunk(kRows, rh * 64u + i, kb, cch) + e * 2u);
+                        s0 += bf16_lo(v2);
+                        s1 += bf16_hi(v2);
+                    }
+                    atomicAdd(&s_db[l * kWidth + (int)col], s0);
+                    atomicAdd(&s_db[l * kWidth + (int)col + 1], s1);
+                }
             }
         }
     done:
