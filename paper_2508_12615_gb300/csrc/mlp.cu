@@ -516,7 +516,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const uint32_t a0 = tc::smem_u32(sA);
         uint32_t md = 0, ng = 0;
-        uint32_t bfills = 0, bused = 0;  // bias copies issued (lead) and waited for (every thread)
+        // the bias copies are issued by another thread than the lead, whose bulk copies queue behind
+        // the activation stores it issues
+        const bool blead = ew == 1 && lane == 0;
+        uint32_t bfills = 0, bused = 0;  // bias copies issued (blead) and waited for (every thread)
         auto fetch_bias = [&](int l) {
             tc::fence_proxy_async();  // the previous layer's bias was read by the generic proxy
             tc::mbar_arrive_expect_tx(&ctl->b_full, kWidth * 4);
@@ -533,8 +536,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
             if (lead) {
                 tc::mbar_arrive_expect_tx(&ctl->g_full, kGtTile);
                 tc::bulk_g2s(sA + 4 * kABlock, P.gt + (size_t)tile * kGtTile, kGtTile, &ctl->g_full);
-                fetch_bias(0);
             }
+            if (blead) fetch_bias(0);
             {
                 const bool ok = wait_or_abort(ctl, &ctl->g_full, ng & 1u, P.err);
                 ++ng;
@@ -623,14 +626,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                 }
                 publish_a(ctl, lead, sA, 0, 4, P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
                 // every thread has read s_bias (publish_a's barrier): the next hidden layer's bias
-                if (lead && l + 1 < kHidden) fetch_bias(l + 1);
+                if (blead && l + 1 < kHidden) fetch_bias(l + 1);
             }
         }
     done:
-        if (lead) {
+        if (blead)
             for (; bused < bfills; ++bused) tc::mbar_wait(&ctl->b_full, bused & 1u, kWaitNs);  // copies still in flight
-            tc::bulk_wait_all();
-        }
+        if (lead) tc::bulk_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -705,8 +707,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const uint32_t a0 = tc::smem_u32(sA);
         uint32_t md = 0;
-        // the lead copies each layer's masks into slot l & 1 one layer ahead: fills[s] counts the
-        // copies issued into slot s (by the lead), used[s] those waited for (by every thread)
+        // one thread (not the lead, whose bulk copies queue behind the dz stores it issues) copies
+        // each layer's masks into slot l & 1 one layer ahead: fills[s] counts the copies issued into
+        // slot s (by mlead), used[s] those waited for (by every thread)
+        const bool mlead = ew == 1 && lane == 0;
         uint32_t fills[2] = {0u, 0u}, used[2] = {0u, 0u};
         auto fetch_masks = [&](int tile, int l) {
             const int slot = l & 1;
@@ -719,7 +723,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
         for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * kRows + r;
             const bool valid = row < P.N;
-            if (lead) fetch_masks(tile, kHidden - 1);
+            if (mlead) fetch_masks(tile, kHidden - 1);
             await_a_free(lead);
             if (half == 0) {
                 // the record update's backward: dL/dd (rounded: the head's product operand) and the
@@ -807,7 +811,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
                     const int slot = l & 1;
                     const bool ok = wait_or_abort(ctl, &ctl->mk_full[slot], used[slot] & 1u, P.err);
                     ++used[slot];
-                    if (lead && ok && l > 0) fetch_masks(tile, l - 1);
+                    if (mlead && ok && l > 0) fetch_masks(tile, l - 1);
                 }
                 await_a_free(lead);
                 const uint4 mw4 = *reinterpret_cast<const uint4*>(sMk + (size_t)(l & 1) * kMkLayer + (size_t)r * 32u +
@@ -850,12 +854,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
             }
         }
     done:
-        if (lead) {
-            // masks copied into a slot but not waited for (a role gave up): let the copies land
+        if (mlead)  // masks copied into a slot but not waited for (a role gave up): let the copies land
             for (int sl = 0; sl < 2; ++sl)
                 for (; used[sl] < fills[sl]; ++used[sl]) tc::mbar_wait(&ctl->mk_full[sl], used[sl] & 1u, kWaitNs);
-            tc::bulk_wait_all();
-        }
+        if (lead) tc::bulk_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
