@@ -97,10 +97,14 @@ constexpr uint32_t kMkTile = kHidden * kMkLayer;      // 32 KB
 // ---- weight streams ------------------------------------------------------------------------------
 // One entry per K-block an MMA group reads: the image's byte offset and size, the A K-block, the K
 // steps of 16 in it, the B rows (the MMA's N), the accumulator column, whether its first step
-// starts the accumulator (else it adds), and whether the group ends with it.
+// starts the accumulator (else it adds), whether the group ends with it, and what the issuer waits
+// for before it: nothing (its A operand is already in place), the tile's encoding (the bulk copy's
+// barrier), or one half of the previous layer's output (the epilogue publishes A K-blocks 0 and 2,
+// then 1 and 3, each on its own barrier).
+enum : uint8_t { kWaitNone = 0, kWaitGamma = 1, kWaitHalf0 = 2, kWaitHalf1 = 3 };
 struct Blk {
     uint32_t off, bytes;
-    uint8_t akb, steps, first, last;
+    uint8_t akb, steps, first, last, wait;
     uint16_t n, dcol;
 };
 constexpr int kMaxBlk = 40;
@@ -111,35 +115,56 @@ struct Sched {
 
 // Forward, per tile: L0 (A = gamma in A K-blocks 4, 5: K 80), L1-L4 (A = h, K-blocks 0-3), L5 (A =
 // (h4, gamma), K-blocks 0-5: its image's columns are ordered h4 first), L6, L7, L8 (16 rows).
+// Layer l accumulates in tensor-memory columns 256 (l & 1) .., so that layer l + 1's products can
+// start while the epilogue still reads layer l's; the h K-blocks go in the order 0, 2, 1, 3, the
+// order in which the epilogue publishes them, and the skip layer's encoding part goes first (its A
+// operand is in place since the tile started).
+__host__ __device__ constexpr uint32_t fwd_image_base(int l) {
+    uint32_t base = 2u * kWBlock;  // layer 0: two K-blocks of 256 rows
+    for (int i = 1; i < l; ++i) base += (uint32_t)(i == kSkipLayer ? 6 : 4) * kWBlock;
+    return l == 0 ? 0u : base;
+}
 __host__ __device__ constexpr Sched make_fwd() {
     Sched s{};
-    uint32_t off = 0;
-    auto add = [&](int akb, int steps, int n, bool first, bool last) {
+    auto add = [&](uint32_t off, int akb, int steps, int n, int dcol, bool first, bool last, uint8_t wait) {
         Blk& b = s.b[s.n++];
         b.off = off;
         b.bytes = (uint32_t)n * 128u;
         b.akb = (uint8_t)akb;
         b.steps = (uint8_t)steps;
         b.n = (uint16_t)n;
-        b.dcol = 0;
+        b.dcol = (uint16_t)dcol;
         b.first = first;
         b.last = last;
-        off += b.bytes;
+        b.wait = wait;
     };
-    add(4, 4, kWidth, true, false);
-    add(5, 1, kWidth, false, true);
-    for (int l = 1; l <= 7; ++l) {
-        const int nkb = l == kSkipLayer ? 6 : 4;
-        for (int kb = 0; kb < nkb; ++kb) add(kb, (l == kSkipLayer && kb == 5) ? 1 : 4, kWidth, kb == 0, kb == nkb - 1);
+    add(0u, 4, 4, kWidth, 0, true, false, kWaitGamma);
+    add(kWBlock, 5, 1, kWidth, 0, false, true, kWaitNone);
+    for (int l = 1; l <= kHidden; ++l) {
+        const int n = l == kHidden ? kOutPad : kWidth;
+        const uint32_t kbytes = (uint32_t)n * 128u, base = fwd_image_base(l);
+        const int dcol = (l & 1) * kWidth;
+        bool first = true;
+        if (l == kSkipLayer) {
+            add(base + 4u * kbytes, 4, 4, n, dcol, true, false, kWaitNone);
+            add(base + 5u * kbytes, 5, 1, n, dcol, false, false, kWaitNone);
+            first = false;
+        }
+        const int order[4] = {0, 2, 1, 3};
+        for (int i = 0; i < 4; ++i)
+            add(base + (uint32_t)order[i] * kbytes, order[i], 4, n, dcol, first && i == 0, i == 3,
+                i == 0 ? kWaitHalf0 : i == 2 ? kWaitHalf1 : kWaitNone);
     }
-    for (int kb = 0; kb < 4; ++kb) add(kb, 4, kOutPad, kb == 0, kb == 3);
     return s;
 }
+constexpr uint32_t kFwdImgBytesTotal = fwd_image_base(kHidden) + 4u * kOutPad * 128u;
 // Backward data, per tile: head (A = dd, one K step; B = W8^T), L7, L6, L5 (dh4 into columns
-// 0-255, then dgamma into columns 256-335), L4 .. L1, L0 (dgamma += dz0 W0).
+// 0-255, then dgamma into columns 256-335), L4 .. L1, L0 (dgamma += dz0 W0).  A group starts once
+// the epilogue has published its A operand.
 __host__ __device__ constexpr Sched make_bwd() {
     Sched s{};
     uint32_t off = 0;
+    bool group_start = true;
     auto add = [&](int akb, int steps, int n, int dcol, bool first, bool last) {
         Blk& b = s.b[s.n++];
         b.off = off;
@@ -150,6 +175,8 @@ __host__ __device__ constexpr Sched make_bwd() {
         b.dcol = (uint16_t)dcol;
         b.first = first;
         b.last = last;
+        b.wait = group_start ? kWaitHalf0 : kWaitNone;
+        group_start = last;
         off += b.bytes;
     };
     add(0, 1, kWidth, 0, true, true);
@@ -166,7 +193,7 @@ __host__ __device__ constexpr Sched make_bwd() {
 }
 constexpr Sched kFwdSched = make_fwd();
 constexpr Sched kBwdSched = make_bwd();
-constexpr uint32_t kFwdImgBytes = kFwdSched.b[kFwdSched.n - 1].off + kFwdSched.b[kFwdSched.n - 1].bytes;
+constexpr uint32_t kFwdImgBytes = kFwdImgBytesTotal;
 constexpr uint32_t kBwdImgBytes = kBwdSched.b[kBwdSched.n - 1].off + kBwdSched.b[kBwdSched.n - 1].bytes;
 __constant__ Sched c_fwd = make_fwd();
 __constant__ Sched c_bwd = make_bwd();
@@ -273,7 +300,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 
 // Control block of a tile kernel in shared memory.
 struct Ctl {
-    uint64_t full[kStages], empty[kStages], mma_done, a_ready, tmem_free, drain, g_full, mk_full[2], b_full;
+    uint64_t full[kStages], empty[kStages], mma_done, a_ready[2], tmem_free, drain, g_full, mk_full[2], b_full;
     uint32_t tmem;
     volatile int abort;
 };
@@ -317,20 +344,25 @@ drain:
 // at compile time (every block's A K-block, steps, N, accumulator column and flags are constants):
 // a tcgen05.mma takes about as long to issue as to run, so the issuing thread keeps nothing but
 // the MMAs, the commits and one test of each stage's barrier between them.
+// The issuer's barrier counters: stage ring position, a_ready[0], a_ready[1] and g_full phases.
+struct IssueCount {
+    uint32_t it, ar0, ar1, gr;
+};
 template <bool BWD, int J>
-__device__ __forceinline__ bool issue_block(Ctl* ctl, uint32_t& it, uint32_t& ar, uint64_t adesc0, uint64_t wdesc0,
-                                            uint32_t tmem, unsigned int* err) {
+__device__ __forceinline__ bool issue_block(Ctl* ctl, IssueCount& n, uint64_t adesc0, uint64_t wdesc0, uint32_t tmem,
+                                            unsigned int* err) {
     constexpr Blk b = (BWD ? make_bwd() : make_fwd()).b[J];
-    constexpr bool group_start = J == 0 || (BWD ? make_bwd() : make_fwd()).b[J - 1].last;
     constexpr uint32_t idesc = tc::idesc_bf16(kRows, b.n);
-    if (group_start) {  // a new group: its A operand comes from the epilogue
-        if (!wait_or_abort(ctl, &ctl->a_ready, ar & 1u, err)) return false;
-        ++ar;
+    if constexpr (b.wait != kWaitNone) {  // the A operand comes from the epilogue or the encoding's copy
+        uint64_t* bar = b.wait == kWaitGamma ? &ctl->g_full : b.wait == kWaitHalf0 ? &ctl->a_ready[0] : &ctl->a_ready[1];
+        uint32_t& ph = b.wait == kWaitGamma ? n.gr : b.wait == kWaitHalf0 ? n.ar0 : n.ar1;
+        if (!wait_or_abort(ctl, bar, ph & 1u, err)) return false;
+        ++ph;
         tc::fence_after_sync();
     }
-    const uint32_t stage = it % kStages;
-    if (!tc::mbar_try_wait(&ctl->full[stage], (it / kStages) & 1u) &&
-        !wait_or_abort(ctl, &ctl->full[stage], (it / kStages) & 1u, err))
+    const uint32_t stage = n.it % kStages;
+    if (!tc::mbar_try_wait(&ctl->full[stage], (n.it / kStages) & 1u) &&
+        !wait_or_abort(ctl, &ctl->full[stage], (n.it / kStages) & 1u, err))
         return false;
     tc::fence_after_sync();
     // descriptor start addresses are in 16-byte units
@@ -341,21 +373,21 @@ __device__ __forceinline__ bool issue_block(Ctl* ctl, uint32_t& it, uint32_t& ar
         tc::mma_bf16(tmem + b.dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (b.first && k == 0) ? 0u : 1u);
     tc::mma_commit(&ctl->empty[stage]);
     if (b.last) tc::mma_commit(&ctl->mma_done);
-    ++it;
+    ++n.it;
     return true;
 }
 template <bool BWD, int... J>
-__device__ __forceinline__ bool issue_tile(Ctl* ctl, uint32_t& it, uint32_t& ar, uint64_t adesc0, uint64_t wdesc0,
-                                           uint32_t tmem, unsigned int* err, std::integer_sequence<int, J...>) {
-    return (issue_block<BWD, J>(ctl, it, ar, adesc0, wdesc0, tmem, err) && ...);
+__device__ __forceinline__ bool issue_tile(Ctl* ctl, IssueCount& n, uint64_t adesc0, uint64_t wdesc0, uint32_t tmem,
+                                           unsigned int* err, std::integer_sequence<int, J...>) {
+    return (issue_block<BWD, J>(ctl, n, adesc0, wdesc0, tmem, err) && ...);
 }
 template <bool BWD>
 __device__ void issue_mmas(Ctl* ctl, uint8_t* sA, uint8_t* sW, int tiles, uint32_t tmem, unsigned int* err) {
     constexpr int nblk = (BWD ? make_bwd() : make_fwd()).n;
-    uint32_t it = 0, ar = 0;
+    IssueCount n{0u, 0u, 0u, 0u};
     const uint64_t adesc0 = tc::desc_sw128(tc::smem_u32(sA)), wdesc0 = tc::desc_sw128(tc::smem_u32(sW));
     for (int tile = blockIdx.x; tile < tiles && !ctl->abort; tile += gridDim.x)
-        if (!issue_tile<BWD>(ctl, it, ar, adesc0, wdesc0, tmem, err, std::make_integer_sequence<int, nblk>{})) break;
+        if (!issue_tile<BWD>(ctl, n, adesc0, wdesc0, tmem, err, std::make_integer_sequence<int, nblk>{})) break;
     tc::mma_commit(&ctl->drain);
     tc::mbar_wait(&ctl->drain, 0, kWaitNs);
 }
@@ -395,7 +427,7 @@ __device__ __forceinline__ void publish_a(Ctl* ctl, bool lead, uint8_t* sA, int 
         tc::bulk_commit();
     }
     tc::fence_before_sync();
-    tc::mbar_arrive(&ctl->a_ready);
+    tc::mbar_arrive(&ctl->a_ready[0]);
 }
 // Wait for the MMA group; every epilogue thread learns whether any of them (or another role) gave up.
 __device__ __forceinline__ bool await_mma(Ctl* ctl, uint32_t parity, unsigned int* err) {
@@ -488,8 +520,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
             tc::mbar_init(&ctl->empty[s], 1);
         }
         tc::mbar_init(&ctl->mma_done, 1);
-        tc::mbar_init(&ctl->a_ready, kEpiThreads);
-        tc::mbar_init(&ctl->tmem_free, kEpiThreads);
+        tc::mbar_init(&ctl->a_ready[0], 1);
+        tc::mbar_init(&ctl->a_ready[1], 1);
+        tc::mbar_init(&ctl->tmem_free, 1);
         tc::mbar_init(&ctl->drain, 1);
         tc::mbar_init(&ctl->g_full, 1);
         tc::mbar_init(&ctl->b_full, 1);
@@ -497,7 +530,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
         tc::fence_mbar_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(&ctl->tmem, 256);
+        tc::tmem_alloc(&ctl->tmem, 512);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -532,19 +565,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
             // the tile's encoding (written by k_mlp_encode) into A K-blocks 4 and 5, and layer 0's
             // bias into s_bias (each hidden layer's bias is copied there once the previous layer's
             // epilogue has read its own, so it lands while the layer's MMAs run)
+            // (the MMA issuer waits for the encoding's copy itself; every tensor-memory load of the
+            // previous tile precedes await_a_free's barrier, after which the copy is issued)
+            tc::fence_before_sync();
             await_a_free(lead);
             if (lead) {
                 tc::mbar_arrive_expect_tx(&ctl->g_full, kGtTile);
                 tc::bulk_g2s(sA + 4 * kABlock, P.gt + (size_t)tile * kGtTile, kGtTile, &ctl->g_full);
+                ++ng;
             }
             if (blead) fetch_bias(0);
-            {
-                const bool ok = wait_or_abort(ctl, &ctl->g_full, ng & 1u, P.err);
-                ++ng;
-                if (tc::named_sync_or(kEpiBar, kEpiThreads, !ok || ctl->abort)) goto done;
-            }
-            tc::fence_before_sync();
-            tc::mbar_arrive(&ctl->a_ready);
             for (int l = 0; l <= kHidden; ++l) {
                 if (!await_mma(ctl, md & 1u, P.err)) goto done;
                 ++md;
@@ -590,12 +620,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                 // bias (packed f32x2 add), ReLU and bfloat16 rounding (one instruction per pair), 64
                 // columns at a time: both tensor-memory loads are in flight before the one wait
                 const float4* b4 = reinterpret_cast<const float4*>(s_bias + half * 128);
+                const uint32_t tacc = tl + (uint32_t)(l & 1) * (uint32_t)kWidth;  // layer l's accumulator
+                uint8_t* hdst = P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer;
 #pragma unroll 1
                 for (int cp = 0; cp < 2; ++cp) {
+                    // pass cp writes A K-block cp (warps 2-5) and K-block cp + 2 (warps 6-9)
                     const int c = half * 4 + 2 * cp;
                     uint32_t v0[32], v1[32];
-                    tc::tmem_ld32(tl + 32u * c, v0);
-                    tc::tmem_ld32(tl + 32u * (c + 1), v1);
+                    tc::tmem_ld32(tacc + 32u * c, v0);
+                    tc::tmem_ld32(tacc + 32u * (c + 1), v1);
                     float4 b[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) b[j] = b4[cp * 16 + j];
@@ -623,21 +656,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd(const __grid_constant
                     }
                     *reinterpret_cast<uint2*>(P.mk + ((size_t)tile * kHidden + l) * kMkLayer + (size_t)r * 32u +
                                               (size_t)c * 4u) = make_uint2(m0, m1);
+                    // publish this half of the next layer's A operand: the next layer's products on
+                    // it start while the other half is computed
+                    tc::fence_proxy_async();
+                    tc::fence_before_sync();
+                    tc::named_sync(kEpiBar, kEpiThreads);
+                    if (lead) {
+                        tc::bulk_s2g(hdst + (size_t)cp * kABlock, sA + (size_t)cp * kABlock, kABlock);
+                        tc::bulk_s2g(hdst + (size_t)(cp + 2) * kABlock, sA + (size_t)(cp + 2) * kABlock, kABlock);
+                        tc::bulk_commit();
+                        tc::mbar_arrive(&ctl->a_ready[cp]);
+                    }
                 }
-                publish_a(ctl, lead, sA, 0, 4, P.ht + (size_t)tile * kHtTile + (size_t)l * kHtLayer);
-                // every thread has read s_bias (publish_a's barrier): the next hidden layer's bias
+                // every thread has read s_bias (the second publish's barrier): the next layer's bias
                 if (blead && l + 1 < kHidden) fetch_bias(l + 1);
             }
         }
     done:
         if (blead)
             for (; bused < bfills; ++bused) tc::mbar_wait(&ctl->b_full, bused & 1u, kWaitNs);  // copies still in flight
-        if (lead) tc::bulk_wait_all();
+        if (lead) {
+            if (ng > 0) tc::mbar_wait(&ctl->g_full, (ng - 1u) & 1u, kWaitNs);  // the last encoding copy
+            tc::bulk_wait_all();
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 1) tc::tmem_dealloc(tmem, 256);
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
 // ---- backward (data) ---------------------------------------------------------------------------
@@ -679,7 +725,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd(const __grid_constant
             tc::mbar_init(&ctl->empty[s], 1);
         }
         tc::mbar_init(&ctl->mma_done, 1);
-        tc::mbar_init(&ctl->a_ready, kEpiThreads);
+        tc::mbar_init(&ctl->a_ready[0], kEpiThreads);
+        tc::mbar_init(&ctl->a_ready[1], 1);
         tc::mbar_init(&ctl->tmem_free, kEpiThreads);
         tc::mbar_init(&ctl->drain, 1);
         tc::mbar_init(&ctl->mk_full[0], 1);
@@ -940,7 +987,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_mlp_wgrad(const __grid_consta
             tc::mbar_init(&ctl->empty[s], 1);
         }
         tc::mbar_init(&ctl->mma_done, 1);
-        tc::mbar_init(&ctl->a_ready, 1);
+        tc::mbar_init(&ctl->a_ready[0], 1);
+        tc::mbar_init(&ctl->a_ready[1], 1);
         tc::mbar_init(&ctl->tmem_free, 128);
         tc::mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
