@@ -174,14 +174,18 @@ def test_ray_integrated_frequency_matches_oracle(N, H, W, seed):
     assert ok, (worst, idx)
 
 
+@pytest.mark.parametrize("fmode", [0, 2])
 @pytest.mark.parametrize("N,H,W,seed,degree", [(600, 72, 88, 37, 3), (1500, 100, 100, 38, 3), (800, 64, 96, 39, 1)])
-def test_spherical_harmonic_colour_matches_oracle(N, H, W, seed, degree):
+def test_spherical_harmonic_colour_matches_oracle(N, H, W, seed, degree, fmode):
     """sh_degree > 0 ([N,68] records): the view-dependent colour, forward and gradients of every
-    coefficient (zero above the degree) and of the centre through the view direction."""
+    coefficient (zero above the degree) and of the centre through the view direction; with the
+    default frequency map and with the ray-integrated one (map 2: both add to the centre's
+    gradient through the same record)."""
     torch = torch_cuda()
     w = lib_ready()
     o = SH3.copy()
     o[9] = degree
+    o[8] = fmode
     p = synth.scene3d_sh(N, seed, degree=3)
     cam = synth.sphere_cameras(1, H, W, seed + 1)[0]
     params, st, img = _gpu(w, torch, p, cam, H, W, o)
@@ -370,22 +374,24 @@ def _chunk_report(st, label):
     return lengths, last
 
 
-def test_chunked_backward_at_full_scene_density():
+@pytest.mark.parametrize("opts", [DEFAULT, RAY], ids=["map0", "map2"])
+def test_chunked_backward_at_full_scene_density(opts):
     """The 3D backward cuts each tile list into chunks of 256 entries and starts every chunk from a
     state that the forward recorded.  At the 300,000-primitive scene's density (its cameras and
     focal length, the image cut to the centre 96x96), the lists run to thousands of entries and
     pixels composite past the second boundary; forward, last-contributor states and the gradient of
-    every record column are compared with the oracle."""
+    every record column are compared with the oracle, with the default frequency map and with the
+    ray-integrated one (map 2: the damping's weight staged with every chunk's entries)."""
     torch = torch_cuda()
     w = lib_ready()
     p, cams = synth.cfg2_inputs(n_cams=2)
     H = W = 96
     for k, full in enumerate(cams):
         cam = _crop(full, H, W)
-        params, st, img = _gpu(w, torch, p, cam, H, W, DEFAULT)
-        lengths, last = _chunk_report(st, f"5D crop, camera {k}")
+        params, st, img = _gpu(w, torch, p, cam, H, W, opts)
+        lengths, last = _chunk_report(st, f"5D crop, camera {k}, map {int(opts[8]) if len(opts) > 8 else 0}")
         assert lengths.max() > 2 * 256 and last.max() > 512
-        C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, DEFAULT)
+        C, T, nc, amb_bits = oracle.render3d(p, cam, H, W, opts)
         amb = (amb_bits & (oracle.AMB_ALPHA_MIN | oracle.AMB_T_MIN)) != 0
         check_amb_share(amb, f"5D crop camera {k}: alpha_min / T_min bits", CROP_AMB_SHARE)
         err = np.abs(img.cpu().numpy().astype(np.float64) - C).max(axis=2)
@@ -399,7 +405,7 @@ def test_chunked_backward_at_full_scene_density():
         g[amb_bits != 0] = 0.0
         grad = w.backward(st, params, torch.from_numpy(g).cuda())
         torch.cuda.synchronize()
-        ref, gabs = oracle.grad3d(p, cam, H, W, g, DEFAULT, with_abs=True)
+        ref, gabs = oracle.grad3d(p, cam, H, W, g, opts, with_abs=True)
         ok, worst, idx = grad_close(grad.cpu().numpy(), ref, gabs, dims=3, cols=list(range(18)))
         assert ok, (worst, idx)
 
