@@ -78,7 +78,8 @@ typedef struct {
  * alpha_max 0.99, T_min 1e-4, dilation 0.3 px^2 (3D) / 0 (2D), bg 0, freq_proj_mode 0, cov2d 0,
  * sh_degree 0. */
 typedef struct {
-    float cutoff_sigma;     /* a primitive counts at a pixel iff its squared Mahalanobis distance <= cutoff^2 */
+    float cutoff_sigma;     /* a primitive counts at a pixel iff its squared Mahalanobis distance <= cutoff^2;
+                             * 2^-10 <= cutoff_sigma <= 2^10, else WIPES_ERR_INVALID */
     float alpha_min;        /* 3D: alpha below this is skipped */
     float alpha_max;        /* 3D: alpha is clamped to this */
     float T_min;            /* 3D: blending stops before a primitive that takes T below this */

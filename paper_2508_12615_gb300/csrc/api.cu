@@ -359,13 +359,14 @@ BlendOpts3 blend_opts(const wipes_opts& o) {
     b.bg[1] = o.bg[1];
     b.bg[2] = o.bg[2];
     b.damp = o.freq_proj_mode == 2;
+    b.cut_scale = cutoff_scale(b.cutoff2);
     return b;
 }
 
 wipes_status check_opts(const wipes_opts* o) {
     if (!o) return fail(WIPES_ERR_INVALID, "opts is NULL");
-    if (!(o->cutoff_sigma > 0.f) || !std::isfinite(o->cutoff_sigma))
-        return fail(WIPES_ERR_INVALID, "cutoff_sigma must be positive and finite");
+    if (!(o->cutoff_sigma >= 0x1p-10f && o->cutoff_sigma <= 0x1p10f))
+        return fail(WIPES_ERR_INVALID, "cutoff_sigma must lie in [2^-10, 2^10]");
     if (!(o->alpha_max > 0.f && o->alpha_max < 1.f))
         return fail(WIPES_ERR_INVALID, "alpha_max must lie in (0, 1)");
     if (!(o->alpha_min >= 0.f) || !(o->T_min >= 0.f) || !(o->dilation >= 0.f))

@@ -19,23 +19,28 @@ __device__ __forceinline__ uint32_t stage_entry(const float4* __restrict__ rec, 
 }
 
 // Forward.  The 16x16 tile is four 8x8 quadrants.  Warp w serves quadrant w & 3 and, of each
-// staged batch, the 32-entry chunks of parity w >> 2; lane l owns the two pixels (l & 7, l >> 3)
-// and (l & 7, (l >> 3) + 4) of its quadrant and evaluates both at once in packed f32x2
-// arithmetic.  When a batch is staged, each thread marks which quadrants its primitive's cutoff
-// ellipse reaches (exact in binary32, conservative) and stores the record with every value
-// duplicated, so that a warp reads ready-made pairs by broadcast.  A warp visits only the entries
-// marked for its quadrant.  Per pixel, the sum runs over the batch (a batch-local partial, added
-// once per batch), and at the end the two warps of a quadrant add their totals in a fixed order.
+// staged batch, every second entry (from w >> 2) of the entries whose cutoff ellipse reaches that
+// quadrant; lane l owns the two pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of its quadrant
+// and evaluates both at once in packed f32x2 arithmetic.  When a batch is staged, each thread
+// stores its record with every value duplicated (so that a warp reads ready-made pairs by
+// broadcast) and the colour halved (the modulation is then taken as G (1 + cos)), and marks which
+// quadrants its primitive's cutoff ellipse reaches (exact in binary32, conservative); the marks
+// become one list of staged entries per quadrant, in tile-list order.  The cutoff enters the
+// exponent: outside it the argument is S (cutoff^2 - q) <= -512 and ex2 returns 0 (S the
+// power-of-two scale of cutoff_scale()), inside it is -q log2(e) / 2.  Per pixel, the sum runs
+// over the batch (a batch-local partial, added once per batch), and at the end the two warps of a
+// quadrant add their totals in a fixed order.
 __device__ __forceinline__ void blend2d_tile(const BlendJob& job, int tile) {
     const float4* __restrict__ rec = job.rec;
     const PixRect* __restrict__ rect = job.rect;
     const TileLists& tl = job.tl;
     const int W = job.W, H = job.H, tiles_x = job.tiles_x;
-    const float cutoff2 = job.o.cutoff2, lim = job.o.lim;
+    const float lim = job.o.lim;
     float* __restrict__ out = job.out;
-    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, 0), each value twice
+    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) / 2 (c_b / 2, 0), each value twice
     __shared__ ulonglong2 s_e[6][kTilePixels];
-    __shared__ uint8_t s_mask[kTilePixels];
+    __shared__ uint8_t s_list[4][kTilePixels];        // per quadrant: the staged entries that reach it
+    __shared__ uint32_t s_cnt[kTilePixels / 32][4];   // per warp and quadrant: its staged entries that reach it
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = warp & 3, half = warp >> 2;
@@ -44,52 +49,65 @@ __device__ __forceinline__ void blend2d_tile(const BlendJob& job, int tile) {
     const int v = y0 + (quad >> 1) * 8 + (lane >> 3);  // and v + 4
     const f2 PX = f2_dup((float)u + 0.5f);
     const f2 PY = f2_pack((float)v + 0.5f, (float)(v + 4) + 0.5f);
-    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
+    const f2 K = f2_dup(kNegHalfLog2e);
+    const f2 NEG_S = f2_dup(-job.o.cut_scale), CUT_S = f2_dup(job.o.cutoff2 * job.o.cut_scale);
     const uint2 range = tl.ranges[tile];
     f2 c0 = f2_dup(0.f), c1 = c0, c2 = c0;
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         __syncthreads();
+        uint32_t m = 0u;
         if ((int)threadIdx.x < n) {
             const uint32_t prim = tl.prim[b0 + threadIdx.x];
             const float4 A = rec[(size_t)prim * kRecF4 + 0];
             const float4 B = rec[(size_t)prim * kRecF4 + 1];
             const float4 C = rec[(size_t)prim * kRecF4 + 2];
-            s_mask[threadIdx.x] = (uint8_t)quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
+            m = quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
             s_e[0][threadIdx.x] = dup2(A.x, A.y);
             s_e[1][threadIdx.x] = dup2(A.z, A.w);
             s_e[2][threadIdx.x] = dup2(B.x, B.y);
             s_e[3][threadIdx.x] = dup2(B.z, B.w);
-            s_e[4][threadIdx.x] = dup2(C.x, C.y);
-            s_e[5][threadIdx.x] = dup2(C.z, 0.f);
+            s_e[4][threadIdx.x] = dup2(0.5f * C.x, 0.5f * C.y);
+            s_e[5][threadIdx.x] = dup2(0.5f * C.z, 0.f);
         }
+        uint32_t bal[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bal[k] = __ballot_sync(0xffffffffu, (m >> k) & 1u);
+        if (lane < 4) s_cnt[warp][lane] = __popc(lane == 0 ? bal[0] : lane == 1 ? bal[1] : lane == 2 ? bal[2] : bal[3]);
+        __syncthreads();
+        // each entry's place in the list of every quadrant it reaches: the entries of earlier
+        // warps, then those of earlier lanes
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((m >> k) & 1u) {
+                uint32_t pos = __popc(bal[k] & ((1u << lane) - 1u));
+                for (int w = 0; w < warp; ++w) pos += s_cnt[w][k];
+                s_list[k][pos] = (uint8_t)threadIdx.x;
+            }
+        }
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kTilePixels / 32; ++w) cnt += s_cnt[w][quad];
         __syncthreads();
         f2 a0 = f2_dup(0.f), a1 = a0, a2 = a0;
-        for (int c = half * 32; c < n; c += 64) {
-            const uint32_t m = c + lane < n ? s_mask[c + lane] : 0u;
-            uint32_t bal = __ballot_sync(0xffffffffu, (m >> quad) & 1u);
-            while (bal) {
-                const int j = c + __ffs(bal) - 1;
-                bal &= bal - 1u;
-                const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]);
-                const f2x2 e2 = ld_f2x2(&s_e[2][j]), e3 = ld_f2x2(&s_e[3][j]);
-                // the cutoff test in the operation order of mahalanobis2()
-                const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
-                const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
-                const f2 b = f2_mul(e2.x, dy);
-                const f2 q = f2_fma(a, a, f2_mul(b, b));
-                // outside the cutoff the envelope is taken as ex2(-inf) = 0, so the entry adds 0
-                const f2 e = f2_mul(q, K);
-                const float glo = ex2_approx(f2_lo(q) <= cutoff2 ? f2_lo(e) : -INFINITY);
-                const float ghi = ex2_approx(f2_hi(q) <= cutoff2 ? f2_hi(e) : -INFINITY);
-                const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
-                const f2 cs = f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang)));
-                const f2 wv = f2_mul(f2_fma(HALF, cs, HALF), f2_pack(glo, ghi));
-                const f2x2 e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
-                a0 = f2_fma(e4.x, wv, a0);
-                a1 = f2_fma(e4.y, wv, a1);
-                a2 = f2_fma(e5.x, wv, a2);
-            }
+        for (uint32_t i = half; i < cnt; i += 2) {
+            const int j = s_list[quad][i];
+            const f2x2 e0 = ld_f2x2(&s_e[0][j]), e1 = ld_f2x2(&s_e[1][j]);
+            const f2x2 e2 = ld_f2x2(&s_e[2][j]), e3 = ld_f2x2(&s_e[3][j]);
+            // the cutoff test in the operation order of mahalanobis2()
+            const f2 dx = f2_sub(PX, e0.x), dy = f2_sub(PY, e0.y);
+            const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
+            const f2 b = f2_mul(e2.x, dy);
+            const f2 q = f2_fma(a, a, f2_mul(b, b));
+            const f2 ex = f2_mul(q, K), cut = f2_fma(q, NEG_S, CUT_S);
+            const f2 G = f2_pack(ex2_approx(fminf(f2_lo(ex), f2_lo(cut))), ex2_approx(fminf(f2_hi(ex), f2_hi(cut))));
+            const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+            const f2 cs = f2_pack(cos_approx(f2_lo(ang)), cos_approx(f2_hi(ang)));
+            const f2 wv = f2_fma(cs, G, G);  // 2 W
+            const f2x2 e4 = ld_f2x2(&s_e[4][j]), e5 = ld_f2x2(&s_e[5][j]);
+            a0 = f2_fma(e4.x, wv, a0);
+            a1 = f2_fma(e4.y, wv, a1);
+            a2 = f2_fma(e5.x, wv, a2);
         }
         c0 = f2_add(c0, a0);
         c1 = f2_add(c1, a1);

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include <string>
 
 #include "../../include/wipes.h"
@@ -417,6 +420,14 @@ inline float touch_limit(float cutoff) {
     return k2 * 1.01f;
 }
 
+// Power-of-two scale S with S cutoff^2 in [2^32, 2^33): any binary32 q > cutoff^2 then has
+// S (cutoff^2 - q) <= -512, so ex2 of it is 0 (host side; cutoff^2 is a normal binary32 number).
+inline float cutoff_scale(float cutoff2) {
+    int e = 0;
+    std::frexp(cutoff2, &e);
+    return std::ldexp(1.0f, std::min(33 - e, 126));
+}
+
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // Camera centre in world coordinates, -R^T t for the view matrix [R | t].
@@ -495,6 +506,7 @@ struct BlendOpts3 {
     float cutoff2, lim, alpha_min, alpha_max, T_min;
     float bg[3];
     int damp;  // 3D frequency map 2: the records carry hk = kappa / 2 (else hk = 1/2 everywhere)
+    float cut_scale;  // 2D: cutoff_scale(cutoff2), the power-of-two scale of the cutoff in the exponent
 };
 struct BlendJob {
     const float4* rec;

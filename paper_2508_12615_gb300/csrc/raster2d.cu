@@ -51,28 +51,40 @@ __device__ __forceinline__ void group4_reduce_scatter16(float v[16]) {
     }
 }
 
-// Backward.  The tile's dL/dimage sits in shared memory, stored by pixel pairs in the layout of
-// the forward pass (quadrant k, pair l: pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of the 8x8
-// quadrant).  Batches of the tile list are staged with the mask of the quadrants that each pair's
-// cutoff ellipse reaches, and ordered by the number of those quadrants.  Each group of 4 lanes
-// takes one (tile, primitive) pair, so a warp works on eight pairs that reach equally many
-// quadrants; lane q of a group covers columns 2q and 2q + 1 of a quadrant, its eight pixel pairs
-// (r, r + 4), r = 0..3, in packed f32x2 arithmetic.  Per pixel inside the cutoff a lane
-// accumulates the factored sums
+// Backward.  The tile's dL/dimage sits in shared memory by pixel pairs: pair (k, r, c) holds the
+// pixels (c, r) and (c, r + 4) of the 8x8 quadrant k.  Batches of the tile list
+// are staged with the mask of the quadrants that each pair's cutoff ellipse reaches, and ordered
+// by the number of those quadrants.  Each group of 4 lanes takes one (tile, primitive) pair, so a
+// warp works on eight pairs that reach equally many quadrants.  In a quadrant, lane r of a group
+// walks the row pair (r, r + 4) across the eight columns (from column 0 or from column 7, by the
+// parity of the pair's staged position) in packed f32x2 arithmetic:
+//  - dy and b = l22 dy are constant along the walk, so the Mahalanobis distance costs two FMAs
+//    per pixel pair (the same operations as mahalanobis2(), so the cutoff decision is the same);
+//  - the oscillation's phasor (cos, sin)(2 pi t) is evaluated once at the first column and
+//    advanced column by column by the rotation through +-2 pi fx (sincospif of 2 fx: accurate to
+//    an ulp or so, so that seven steps stay within the MUFU cos/sin error);
+//  - the cutoff enters the exponent: outside, the argument is S (cutoff^2 - q) <= -256 and ex2
+//    returns 0, inside it is -q log2(e) / 2 (S a power of two that makes the scaled gap of any
+//    binary32 q > cutoff^2 at least 256).
+// Per pixel inside the cutoff a lane accumulates the factored sums
 //   sum ga, sum gb, sum gt, sum ga dx, sum ga dy, sum gb dy, sum gt dx, sum gt dy, sum g W
 // (ga = 2 dL/dq a, gb = 2 dL/dq b, gt = dL/dt, with q = a^2 + b^2, a = l11 dx + l21 dy,
-// b = l22 dy, t the phase in cycles); the pair's gradient follows from them after one reduction
-// over the group's 4 lanes, since L, f and the centre are constant over the pair, and one reduction
-// pass serves the warp's eight pairs.  The sums are taken of -ga, -gb and -gt / pi (one multiplication less per pixel) and
-// scaled once per pair.
-__global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __restrict__ rec,
+// b = l22 dy, t the phase in cycles), those with a factor constant along a walk (b, dy) once per
+// walk.  The pair's gradient follows from them after one reduction over the group's 4 lanes, since
+// L, f and the centre are constant over the pair.  The colours are staged halved and the
+// modulation taken as G (1 + cos), which saves the 1/2 of W per pixel; the sums are taken of
+// -ga, -gb and -gt / (2 pi) and scaled once per pair.
+__global__ void __launch_bounds__(kTilePixels, 2) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
                                                             int H, int tiles_x, float cutoff2, float lim,
-                                                            const float* __restrict__ dl_dout,
+                                                            float cut_scale, const float* __restrict__ dl_dout,
                                                             float* __restrict__ partial) {
     pdl_enter();
-    __shared__ ulonglong2 s_g[2][kTilePixels / 2];  // (g_r, g_g) and (g_b, 0) pairs by pixel pair
-    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) (c_b, 0), each value twice
+    // (g_r, g_g) and g_b pairs by pixel pair, column-swizzled: pair (k, r, c) at slot
+    // 32 k + 8 r + ((c + 2 r) & 7), so that the four rows of a walk read four different bank groups
+    __shared__ ulonglong2 s_g[kTilePixels / 2];
+    __shared__ unsigned long long s_gb[kTilePixels / 2];
+    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) / 2 (c_b / 2, 0), each value twice
     __shared__ ulonglong2 s_e[6][kTilePixels];
     __shared__ uint32_t s_slot[kTilePixels];
     __shared__ uint8_t s_mask[kTilePixels];
@@ -85,6 +97,7 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
     const int ql = lane & 3, grp = lane >> 2;
     __shared__ __align__(16) float s_red[kTilePixels / 32][8][16];  // per warp and group: the pair's 16 sums
     if (threadIdx.x < kTilePixels / 2) {
+        // pixel pair p = threadIdx.x: quadrant k = p >> 5, column p & 7, rows (p >> 3) & 3 and + 4
         const int k = threadIdx.x >> 5;
         const int u = x0 + (k & 1) * 8 + (lane & 7);
         const int v = y0 + (k >> 1) * 8 + (lane >> 3);
@@ -97,14 +110,13 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             const float* g = dl_dout + ((size_t)(v + 4) * W + u) * 3;
             g1[0] = g[0], g1[1] = g[1], g1[2] = g[2];
         }
-        s_g[0][threadIdx.x] = make_ulonglong2(f2_pack(g0[0], g1[0]).r, f2_pack(g0[1], g1[1]).r);
-        s_g[1][threadIdx.x] = make_ulonglong2(f2_pack(g0[2], g1[2]).r, 0ull);
+        const int r = (threadIdx.x >> 3) & 3, slot = (threadIdx.x & ~7) | (((threadIdx.x & 7) + 2 * r) & 7);
+        s_g[slot] = make_ulonglong2(f2_pack(g0[0], g1[0]).r, f2_pack(g0[1], g1[1]).r);
+        s_gb[slot] = f2_pack(g0[2], g1[2]).r;
     }
     if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;
-    // the lane's first column in quadrant 0 (quadrant k adds 8 (k & 1) columns and 8 (k >> 1)
-    // rows); its pixel pair (column 2 ql + c, rows r, r + 4) sits at 2 ql + c + 8 r in the pair layout
-    const float lane_px = (float)(x0 + 2 * ql) + 0.5f, lane_py = (float)y0 + 0.5f;
-    const f2 K = f2_dup(kNegHalfLog2e), HALF = f2_dup(0.5f);
+    const f2 K = f2_dup(kNegHalfLog2e);
+    const f2 NEG_S = f2_dup(-cut_scale), CUT_S = f2_dup(cutoff2 * cut_scale);  // exact: a power-of-two scale
     const uint2 range = tl.ranges[tile];
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
@@ -121,8 +133,8 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             s_e[1][threadIdx.x] = dup2(A.z, A.w);
             s_e[2][threadIdx.x] = dup2(B.x, B.y);
             s_e[3][threadIdx.x] = dup2(B.z, B.w);
-            s_e[4][threadIdx.x] = dup2(C.x, C.y);
-            s_e[5][threadIdx.x] = dup2(C.z, 0.f);
+            s_e[4][threadIdx.x] = dup2(0.5f * C.x, 0.5f * C.y);
+            s_e[5][threadIdx.x] = dup2(0.5f * C.z, 0.f);
             const uint32_t m = quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
             s_mask[threadIdx.x] = (uint8_t)m;
             s_slot[threadIdx.x] = e;
@@ -143,68 +155,100 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
             const bool has = idx < n;
             const int j = has ? (int)s_order[idx] : 0;
             uint32_t mask = has ? (uint32_t)s_mask[j] : 0u;
-            f2 acc[11];
-#pragma unroll
-            for (int i = 0; i < 11; ++i) acc[i] = f2_dup(0.f);
+            // pairs at even staged positions walk the columns 0 -> 7, odd ones 7 -> 0: the walk (and
+            // so the summation order) is a property of the pair, and the groups of a warp, about
+            // half each way, spread their dL/dimage reads over all eight bank groups
+            const int c0 = (j & 1) ? 7 : 0, cstep = (j & 1) ? -1 : 1;
+            const float dir = (float)cstep;
+            const f2 STEP = f2_dup(dir);
+            // per pixel pair (packed): 3 -ga dx, 6 -gt' dx, 8..10 2 g W; per walk (scalar, both
+            // pixels summed): 0 -ga, 1 -gb, 2 -gt', 4 -ga dy, 5 -gb dy, 7 -gt' dy
+            f2 acc3 = f2_dup(0.f), acc6 = acc3, acc8 = acc3, acc9 = acc3, acc10 = acc3;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s4 = 0.f, s5 = 0.f, s7 = 0.f;
+            // the rotation of the phasor from one column to the next: 2 pi fx
+            f2 CX, SX, NSX;
+            {
+                float sx, cx;
+                sincospif(2.0f * f2_lo(ld_f2x2(&s_e[2][j]).y), &sx, &cx);
+                CX = f2_dup(cx), SX = f2_dup(dir * sx), NSX = f2_dup(-dir * sx);
+            }
             while (__any_sync(0xffffffffu, mask != 0u)) {
                 if (mask) {
                     const int k = __ffs(mask) - 1;
                     mask &= mask - 1u;
+                    const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
+                    const f2x2 e2 = ld_f2x2_here(&s_e[2][j]), e3 = ld_f2x2_here(&s_e[3][j]);
                     // integers below 2^24 are exact in binary32, so these equal (float)u + 0.5f
-                    const float pxq = lane_px + (float)((k & 1) * 8), pyq = lane_py + (float)((k >> 1) * 8);
-#pragma unroll 4
-                    for (int pq = 0; pq < 8; ++pq) {
-                        const int pp = pq & 3, cc = pq >> 2;
-                        const float px = pxq + (float)cc;
-                        const float py = pyq + (float)pp;
-                        // the pair's record, read again for each pixel pair rather than held in registers
-                        const f2x2 e0 = ld_f2x2_here(&s_e[0][j]), e1 = ld_f2x2_here(&s_e[1][j]);
-                        const f2x2 e2 = ld_f2x2_here(&s_e[2][j]), e3 = ld_f2x2_here(&s_e[3][j]);
-                        // the cutoff test in the operation order of mahalanobis2()
-                        const f2 dx = f2_sub(f2_dup(px), e0.x), dy = f2_sub(f2_pack(py, py + 4.0f), e0.y);
-                        const f2 a = f2_fma(e1.x, dx, f2_mul(e1.y, dy));
-                        const f2 b = f2_mul(e2.x, dy);
-                        const f2 q = f2_fma(a, a, f2_mul(b, b));
-                        // outside the cutoff the envelope is taken as ex2(-inf) = 0: every term below is 0
-                        const f2 e = f2_mul(q, K);
-                        const float glo = ex2_approx(f2_lo(q) <= cutoff2 ? f2_lo(e) : -INFINITY);
-                        const float ghi = ex2_approx(f2_hi(q) <= cutoff2 ? f2_hi(e) : -INFINITY);
-                        const f2 G = f2_pack(glo, ghi);
-                        const f2 ang = f2_reduced_angle(f2_fma(e2.y, dx, f2_fma(e3.x, dy, e3.y)));
+                    const float px0 = (float)(x0 + (k & 1) * 8 + c0) + 0.5f;
+                    const float py = (float)(y0 + (k >> 1) * 8 + ql) + 0.5f;
+                    const f2 DY = f2_sub(f2_pack(py, py + 4.0f), e0.y);
+                    const f2 L21DY = f2_mul(e1.y, DY);
+                    const f2 B = f2_mul(e2.x, DY);
+                    const f2 BB = f2_mul(B, B);
+                    f2 PX = f2_dup(px0);
+                    f2 cs, sn;
+                    {
+                        const f2 ang = f2_reduced_angle(f2_fma(e2.y, f2_sub(PX, e0.x), f2_fma(e3.x, DY, e3.y)));
                         const float alo = f2_lo(ang), ahi = f2_hi(ang);
-                        const f2 cs = f2_pack(cos_approx(alo), cos_approx(ahi));
-                        const f2 sn = f2_pack(sin_approx(alo), sin_approx(ahi));
-                        const f2 Wv = f2_mul(f2_fma(HALF, cs, HALF), G);
-                        const int gi = k * 32 + 2 * ql + cc + 8 * pp;
-                        const f2x2 g01 = ld_f2x2(&s_g[0][gi]);
-                        const f2 gb_ = ld_f2x2(&s_g[1][gi]).x;
-                        const f2x2 e4 = ld_f2x2_here(&s_e[4][j]), e5 = ld_f2x2_here(&s_e[5][j]);
-                        const f2 gW = f2_fma(g01.x, e4.x, f2_fma(g01.y, e4.y, f2_mul(gb_, e5.x)));
-                        const f2 hq = f2_mul(gW, Wv);              // -2 dL/dq  (dW/dq = -W/2)
-                        const f2 ht = f2_mul(G, f2_mul(gW, sn));  // -dL/dt / pi, t in cycles
-                        const f2 ha = f2_mul(hq, a), hb = f2_mul(hq, b);
-                        acc[0] = f2_add(acc[0], ha);
-                        acc[1] = f2_add(acc[1], hb);
-                        acc[2] = f2_add(acc[2], ht);
-                        acc[3] = f2_fma(ha, dx, acc[3]);
-                        acc[4] = f2_fma(ha, dy, acc[4]);
-                        acc[5] = f2_fma(hb, dy, acc[5]);
-                        acc[6] = f2_fma(ht, dx, acc[6]);
-                        acc[7] = f2_fma(ht, dy, acc[7]);
-                        acc[8] = f2_fma(g01.x, Wv, acc[8]);
-                        acc[9] = f2_fma(g01.y, Wv, acc[9]);
-                        acc[10] = f2_fma(gb_, Wv, acc[10]);
+                        cs = f2_pack(cos_approx(alo), cos_approx(ahi));
+                        sn = f2_pack(sin_approx(alo), sin_approx(ahi));
                     }
+                    const f2x2 e4 = ld_f2x2_here(&s_e[4][j]);
+                    const f2 CB = ld_f2x2_here(&s_e[5][j]).x;
+                    f2 sa = f2_dup(0.f), sq = sa, st = sa;  // this walk's sums of ha, hq, ht
+                    const int gbase = 32 * k + 8 * ql;
+                    int gofs = c0 + 2 * ql;  // the column's slot in the swizzled row, before & 7
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        // the cutoff test in the operation order of mahalanobis2()
+                        const f2 dx = f2_sub(PX, e0.x);
+                        const f2 a = f2_fma(e1.x, dx, L21DY);
+                        const f2 q = f2_fma(a, a, BB);
+                        const f2 ex = f2_mul(q, K), cut = f2_fma(q, NEG_S, CUT_S);
+                        const f2 G = f2_pack(ex2_approx(fminf(f2_lo(ex), f2_lo(cut))),
+                                             ex2_approx(fminf(f2_hi(ex), f2_hi(cut))));
+                        const f2 Wv = f2_fma(cs, G, G);  // 2 W
+                        const f2x2 g01 = ld_f2x2(&s_g[gbase + (gofs & 7)]);
+                        const f2 gb_{s_gb[gbase + (gofs & 7)]};
+                        const f2 gW = f2_fma(g01.x, e4.x, f2_fma(g01.y, e4.y, f2_mul(gb_, CB)));  // g.c / 2
+                        const f2 hq = f2_mul(gW, Wv);                  // -2 dL/dq
+                        const f2 ht = f2_mul(G, f2_mul(gW, sn));      // -dL/dt / (2 pi), t in cycles
+                        const f2 ha = f2_mul(hq, a);
+                        sa = f2_add(sa, ha);
+                        sq = f2_add(sq, hq);
+                        st = f2_add(st, ht);
+                        acc3 = f2_fma(ha, dx, acc3);
+                        acc6 = f2_fma(ht, dx, acc6);
+                        acc8 = f2_fma(g01.x, Wv, acc8);
+                        acc9 = f2_fma(g01.y, Wv, acc9);
+                        acc10 = f2_fma(gb_, Wv, acc10);
+                        if (c < 7) {
+                            PX = f2_add(PX, STEP);
+                            gofs += cstep;
+                            const f2 cs_next = f2_fma(sn, NSX, f2_mul(cs, CX));
+                            sn = f2_fma(cs, SX, f2_mul(sn, CX));
+                            cs = cs_next;
+                        }
+                    }
+                    // b and dy are constant along the walk (recomputed: cheaper than holding them)
+                    const f2 DY2 = f2_sub(f2_pack(py, py + 4.0f), ld_f2x2_here(&s_e[0][j]).y);
+                    const f2 B2 = f2_mul(ld_f2x2_here(&s_e[2][j]).x, DY2);
+                    const f2 hb = f2_mul(sq, B2), ady = f2_mul(sa, DY2), bdy = f2_mul(hb, DY2), tdy = f2_mul(st, DY2);
+                    s0 += f2_lo(sa) + f2_hi(sa);
+                    s1 += f2_lo(hb) + f2_hi(hb);
+                    s2 += f2_lo(st) + f2_hi(st);
+                    s4 += f2_lo(ady) + f2_hi(ady);
+                    s5 += f2_lo(bdy) + f2_hi(bdy);
+                    s7 += f2_lo(tdy) + f2_hi(tdy);
                 }
             }
             // the lane's pixels, then the sums of ga, gb, gt from the scaled ones
-            float sums[16];
-#pragma unroll
-            for (int i = 0; i < 11; ++i) sums[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
-#pragma unroll
-            for (int i = 11; i < 16; ++i) sums[i] = 0.f;
+            float sums[16] = {s0, s1, s2, f2_lo(acc3) + f2_hi(acc3), s4, s5, f2_lo(acc6) + f2_hi(acc6), s7,
+                              f2_lo(acc8) + f2_hi(acc8), f2_lo(acc9) + f2_hi(acc9), f2_lo(acc10) + f2_hi(acc10),
+                              0.f, 0.f, 0.f, 0.f, 0.f};
             sums[0] = -sums[0], sums[1] = -sums[1], sums[3] = -sums[3], sums[4] = -sums[4], sums[5] = -sums[5];
-            sums[2] *= -kPi, sums[6] *= -kPi, sums[7] *= -kPi;
+            sums[2] *= -kTwoPi, sums[6] *= -kTwoPi, sums[7] *= -kTwoPi;
+            sums[8] *= 0.5f, sums[9] *= 0.5f, sums[10] *= 0.5f;
             // lane q of the group ends with the totals of sums 4q .. 4q + 3, which the group shares
             // through shared memory; lanes 0 .. 2 write slots 4q .. 4q + 3 of the pair
             group4_reduce_scatter16(sums);
@@ -400,8 +444,9 @@ void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream) {
 
 void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream) {
-    launch_pdl(k_backward2d, tiles_x * tiles_y, kTilePixels, 0, stream, rec, rect, tl, W, H, tiles_x, cutoff * cutoff,
-                                                                 touch_limit(cutoff), dl_dout, partial);
+    const float cutoff2 = cutoff * cutoff;
+    launch_pdl(k_backward2d, tiles_x * tiles_y, kTilePixels, 0, stream, rec, rect, tl, W, H, tiles_x, cutoff2,
+               touch_limit(cutoff), cutoff_scale(cutoff2), dl_dout, partial);
     count_launches(1);
 }
 

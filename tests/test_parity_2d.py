@@ -94,6 +94,62 @@ def test_rotation_angles_across_quadrants_bit_exact():
     assert np.abs(img.cpu().numpy().astype(np.float64) - ref).max() <= FWD_ATOL
 
 
+def test_cutoff_boundary_pixels():
+    """Axis-aligned primitives (theta = 0, s = (1, 2), so L = diag(1, 1/2) exactly) centred on pixel
+    centres put pixel centres exactly on the cutoff ellipse (q = 9, inside by reading 6); centres
+    moved by one binary32 step put the same pixels one step inside or outside.  The kernels fold
+    the cutoff into the exponent, so these pixels check that the fold agrees with the q <= 9
+    decision of the oracle's binary32 rule exactly."""
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 32, 48
+    rng = np.random.default_rng(31)
+    rows = []
+    for k, (cx, cy) in enumerate([(8.5, 8.5), (24.5, 10.5), (40.5, 8.5), (10.5, 24.5), (26.5, 22.5), (38.5, 24.5)]):
+        mx, my = np.float32(cx), np.float32(cy)
+        if k % 3 == 1:  # one step towards -inf: pixels at dx = +3 fall outside, dx = -3 inside
+            mx, my = np.nextafter(mx, np.float32(-np.inf)), np.nextafter(my, np.float32(-np.inf))
+        elif k % 3 == 2:  # one step towards +inf: the reverse
+            mx, my = np.nextafter(mx, np.float32(np.inf)), np.nextafter(my, np.float32(np.inf))
+        f = rng.uniform(-0.3, 0.3, 2)
+        rows.append([mx, my, 1.0, 2.0, 0.0, f[0], f[1], rng.uniform(0, 6.28), *rng.uniform(0.2, 1.0, 3)] + [0.0] * 5)
+    p = np.array(rows, dtype=np.float32)
+    rec, _, _ = oracle.footprints(2, p, H, W)
+    assert np.all(rec[:, 2] == 1.0) and np.all(rec[:, 3] == 0.0) and np.all(rec[:, 4] == 0.5)
+    # the boundary pixels of the centred primitive 0: q = 9 exactly at dx = +-3 and dy = +-6
+    assert (np.float32(8.5 + 3.0) - p[0, 0]) ** 2 == np.float32(9.0)
+    params, st, img = _gpu_forward(w, torch, p, H, W)
+    tiles, prims, _ = st.lists()
+    ot, op = oracle.tile_lists(2, p, H, W)
+    assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+    assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+    ref = oracle.render2d(p, H, W, truncated=True)
+    err = np.abs(img.cpu().numpy().astype(np.float64) - ref)
+    assert err.max() <= FWD_ATOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    g = synth.upstream_grad(H, W, 32)
+    grad = w.backward(st, params, torch.from_numpy(g).cuda()).cpu().numpy()
+    ref_g, gabs = oracle.grad2d(p, H, W, g, truncated=True, with_abs=True)
+    ok, worst, idx = grad_close(grad, ref_g, gabs, cols=list(range(11)))
+    assert ok, (worst, idx)
+
+
+def test_cutoff_outside_supported_range_is_refused():
+    """The cutoff's power-of-two scale in the exponent is exact for cutoffs in [2^-10, 2^10]; other
+    values are refused on the host with WIPES_ERR_INVALID before any device work."""
+    torch = torch_cuda()
+    w = lib_ready()
+    from paper_2508_12615_gb300 import _abi
+
+    params = torch.from_numpy(synth.scene2d(10, 16, 16, 3)).cuda()
+    for bad in (2.0 ** -11, 2.0 ** 11, 0.0, float("inf"), float("nan")):
+        with pytest.raises(_abi.WipesError) as e:
+            w.forward2d(params, 16, 16, opts=w.make_opts(2, cutoff_sigma=bad))
+        assert e.value.status == 1
+    for ok in (2.0 ** -10, 2.0 ** 10):
+        w.forward2d(params, 16, 16, opts=w.make_opts(2, cutoff_sigma=ok))
+    torch.cuda.synchronize()
+
+
 def test_autograd_function_matches_direct_calls():
     torch = torch_cuda()
     w = lib_ready()
