@@ -628,9 +628,10 @@ int sort_chunks(int64_t n, int tile_keys, int* tiles_per_chunk) {
     return (int)ceil_div(tiles, tpc);
 }
 
+// counts: [radix][chunks], or with chunk_major [chunks][kMaxRadix] (read by k_sort_downsweep_fused)
 __global__ void __launch_bounds__(kThreads) k_sort_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                           int nbits, int64_t chunk_keys, int chunks,
-                                                           uint32_t* __restrict__ counts /* [radix][chunks] */) {
+                                                           int nbits, int64_t chunk_keys, int chunks, int chunk_major,
+                                                           uint32_t* __restrict__ counts) {
     pdl_enter();
     __shared__ uint32_t s_cnt[kWarps][kMaxRadix];
     for (int k = threadIdx.x; k < kWarps * kMaxRadix; k += kThreads) (&s_cnt[0][0])[k] = 0u;
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_upsweep(const uint32_t* __res
         uint32_t sum = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) sum += s_cnt[w][d];
-        counts[(size_t)d * chunks + blockIdx.x] = sum;
+        counts[chunk_major ? (size_t)blockIdx.x * kMaxRadix + d : (size_t)d * chunks + blockIdx.x] = sum;
     }
 }
 
@@ -689,7 +690,8 @@ struct SortDownArgs {
     int64_t n;
     int shift, nbits;
     int chunks, tiles_per_chunk;
-    const uint32_t* bases;   // [radix][chunks]: the digit's count in earlier chunks
+    const uint32_t* bases;   // [radix][chunks]: the digit's count in earlier chunks (k_sort_downsweep_fused:
+                             // the chunk-major counts of k_sort_upsweep)
     const uint32_t* totals;  // [radix]
     const uint32_t* table;   // optional: gathered[g] = table[value] for each placed pair
     uint32_t* gathered;
@@ -822,6 +824,59 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_downsweep(const __grid
     }
 }
 
+// k_sort_downsweep without the scan kernel before it, for sorts with few chunks: each block finds
+// its chunk's digit offsets from the chunk-major counts itself.  Digit d of chunk c starts after all
+// keys of smaller digits and after digit d's keys in the chunks before c; the kSortThreads / radix
+// threads of a digit sum its counts over interleaved chunks.
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort_downsweep_fused(const __grid_constant__ SortDownArgs a) {
+    pdl_enter();
+    constexpr int kTileKeys = kSortThreads * ITEMS;
+    extern __shared__ uint4 s_sort_raw[];
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_sort_raw);
+    uint32_t* s_vals = s_keys + kTileKeys;
+    uint32_t(*s_wc)[kMaxRadix] = reinterpret_cast<uint32_t(*)[kMaxRadix]>(s_vals + kTileKeys);
+    uint32_t* s_dstart = s_vals + kTileKeys + kSortWarps * kMaxRadix;
+    uint32_t* s_base = s_dstart + kMaxRadix;
+    uint32_t* s_gofs = s_base + kMaxRadix;
+    uint32_t* s_warp = s_gofs + kMaxRadix;
+    const int radix = 1 << a.nbits;  // 2 .. 256
+    {
+        const int parts = kSortThreads / radix;
+        const int d = (int)threadIdx.x & (radix - 1), part = (int)threadIdx.x / radix;
+        uint32_t all = 0, before = 0;
+        for (int c = part; c < a.chunks; c += parts) {
+            const uint32_t x = a.bases[(size_t)c * kMaxRadix + d];  // chunk-major counts
+            all += x;
+            before += c < (int)blockIdx.x ? x : 0u;
+        }
+        s_keys[threadIdx.x] = all;
+        s_vals[threadIdx.x] = before;
+        __syncthreads();
+        uint32_t tot = 0, bef = 0;
+        if ((int)threadIdx.x < radix) {
+            for (int q = 0; q < parts; ++q) {
+                tot += s_keys[q * radix + threadIdx.x];
+                bef += s_vals[q * radix + threadIdx.x];
+            }
+        }
+        const uint32_t ex = block_exclusive_scan<uint32_t, kSortWarps>(tot, nullptr, s_warp);
+        if ((int)threadIdx.x < radix) s_base[threadIdx.x] = ex + bef;
+    }
+    __syncthreads();
+    const int64_t tiles = (a.n + kTileKeys - 1) / kTileKeys;
+    const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_chunk, t1 = min(tiles, t0 + a.tiles_per_chunk);
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t left = a.n - tile * kTileKeys;
+        if (left >= kTileKeys)
+            down_tile<ITEMS, true>(a, tile, kTileKeys, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
+        else
+            down_tile<ITEMS, false>(a, tile, (int)left, s_keys, s_vals, s_wc, s_dstart, s_base, s_gofs, s_warp);
+    }
+}
+// Sorts whose chunk-major counts hold at most this many words skip the scan kernel.
+constexpr int64_t kFusedScanMaxWords = (int64_t)1 << 16;
+
 int64_t radix_hist_words(int64_t n) {
     const int64_t tiles = ceil_div(std::max<int64_t>(n, 1), kPassTile);
     const int64_t onesweep = sort_status_offset_words() + 2 * (int64_t)kMaxPasses * tiles * kMaxRadix;
@@ -839,6 +894,10 @@ void sort_pass_attributes() {
         cudaFuncSetAttribute(k_sort_downsweep<kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSortSmemBytes);
         cudaFuncSetAttribute(k_sort_downsweep<kPassItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPassSmemBytes);
+        cudaFuncSetAttribute(k_sort_downsweep_fused<kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSortSmemBytes);
+        cudaFuncSetAttribute(k_sort_downsweep_fused<kPassItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kPassSmemBytes);
     });
 }
@@ -867,20 +926,32 @@ int radix_sort_pairs(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits, 
         uint32_t* counts = hist;
         uint32_t* bases = hist + (size_t)kMaxRadix * chunks;
         uint32_t* totals = bases + (size_t)kMaxRadix * chunks;
+        // few chunks: the downsweep finds its offsets from the counts itself (two launches a pass)
+        const bool fused = (int64_t)chunks * kMaxRadix <= kFusedScanMaxWords;
         int cur = 0;
         for (int p = 0; p < plan.passes; ++p) {
             const bool last_pass = p == plan.passes - 1;
             launch_pdl(k_sort_upsweep, (unsigned)chunks, kThreads, 0, stream, (const uint32_t*)keys[cur], n, plan.shift[p],
-                       plan.nbits[p], (int64_t)tpc * tile_keys, chunks, counts);
-            launch_pdl(k_sort_chunk_scan, (unsigned)(1 << plan.nbits[p]), kScanThreads, 0, stream, (const uint32_t*)counts,
-                       chunks, bases, totals);
+                       plan.nbits[p], (int64_t)tpc * tile_keys, chunks, (int)fused, counts);
+            if (!fused)
+                launch_pdl(k_sort_chunk_scan, (unsigned)(1 << plan.nbits[p]), kScanThreads, 0, stream,
+                           (const uint32_t*)counts, chunks, bases, totals);
             SortDownArgs da{keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, plan.shift[p], plan.nbits[p], chunks,
-                            tpc, bases, totals, last_pass ? table : nullptr, last_pass ? gathered : nullptr};
-            if (tile_keys == kPassTile)
+                            tpc, fused ? counts : bases, totals, last_pass ? table : nullptr,
+                            last_pass ? gathered : nullptr};
+            if (fused) {
+                if (tile_keys == kPassTile)
+                    launch_pdl(k_sort_downsweep_fused<kPassItems>, (unsigned)chunks, kSortThreads, kPassSmemBytes, stream,
+                               da);
+                else
+                    launch_pdl(k_sort_downsweep_fused<kSortItems>, (unsigned)chunks, kSortThreads, kSortSmemBytes, stream,
+                               da);
+            } else if (tile_keys == kPassTile) {
                 launch_pdl(k_sort_downsweep<kPassItems>, (unsigned)chunks, kSortThreads, kPassSmemBytes, stream, da);
-            else
+            } else {
                 launch_pdl(k_sort_downsweep<kSortItems>, (unsigned)chunks, kSortThreads, kSortSmemBytes, stream, da);
-            count_launches(3);
+            }
+            count_launches(fused ? 2 : 3);
             cur ^= 1;
         }
         return cur;
