@@ -37,13 +37,16 @@ METRIC = "fwd Mpix/s and fwd+bwd iter/s (768×512, 70k prims); serving p50/p99 m
 WORKLOAD = "2d_image_fitting_768x512_n70000"
 FP32_LANES_PER_SM = 128
 SMS = 152
-# FP32-pipe operations (an FMA counts as one) and MUFU operations per (pixel, primitive) pair inside
-# the cutoff ellipse, as the oracle's definition requires them (counted in the design notes).
-OPS_PER_PAIR = {"2d": {"blend": (19, 2), "bwd_raster": (42, 3)}, "3d": {"blend": (25, 2), "bwd_raster": (55, 3)}}
+# Algorithmic FP32-pipe operations (an FMA counts as one) and MUFU operations per (pixel, primitive)
+# pair inside the cutoff ellipse, counted from the method's arithmetic rather than from the kernels:
+# the 2D forward 15 + 2 (offsets, quadratic form, phase reduction, exp2, cos, modulation, 3-channel
+# accumulate), the 3D forward 6 more (alpha, clamp, transmittance update and tests), each backward
+# 2.5 times its forward with one more MUFU (sin).
+OPS_PER_PAIR = {"2d": {"blend": (15, 2), "bwd_raster": (37.5, 3)}, "3d": {"blend": (21, 2), "bwd_raster": (52.5, 3)}}
 # DRAM bytes (read + write) per launch, per (workload, kernel), from the ncu captures summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
 # entry is removed when its kernel changes.
-TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_503_744 + 424_960, ("2d", "k_blend2d"): 9_052_928,
+TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_434_368 + 329_728, ("2d", "k_blend2d"): 9_069_824,
                  ("5d", "k_backward3d"): 27_144_448 + 768, ("5d", "k_blend3d"): 16_071_168 + 70_912}
 
 
@@ -507,7 +510,7 @@ def roofline_of(wl, stages: dict, pk: dict, pk_kind: str):
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz ({pk_kind} max SM clock)",
-                "work": f"{pairs_per_launch:.0f} pairs inside the cutoff per launch x {fp32_ops} FP32 + "
+                "work": f"{pairs_per_launch:.0f} pairs inside the cutoff per launch x {fp32_ops:g} FP32 + "
                         f"{mufu_ops} MUFU ops",
                 "mufu_frac": pairs_per_launch * mufu_ops / launch_s / (SMS * 16 * clock_mhz * 1e6)}
     return roofline, {"visited": visited, "inside": inside, "instances": instances}
