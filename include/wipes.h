@@ -167,8 +167,8 @@ wipes_status wipes_l2_loss(wipes_ctx* ctx, const float* img, const float* target
                            float* dL_dimg, void* stream);
 
 /* The same loss without allocating device memory (the paper has no counterpart; this serves
- * callers that cannot call cudaMalloc: work recorded into a CUDA graph, code whose allocator owns
- * all device memory, hosts that forbid allocation after start-up).  Runs on the calling thread's
+ * callers that cannot call cudaMalloc: code whose allocator owns all device memory, hosts that
+ * forbid device allocation after start-up).  Runs on the calling thread's
  * current device and needs no context.  Its scratch is a fixed 256 KB array inside the library's
  * device image (one partial sum per 4096 elements), held by every GPU that loads the library until
  * the process exits.  Limits: 1 <= n <= 268,435,456 (65,536 x 4,096); larger n returns

@@ -1,9 +1,8 @@
 // Mean squared error and its gradient without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that records its work into a CUDA graph (allocation
-// is not a capturable operation), code running under an allocator that owns all device memory
-// (a framework's caching allocator or a fixed arena), and embedded hosts that forbid allocation
-// after start-up.  This entry point serves them: its only scratch is the file-scope array below,
+// Some callers cannot call cudaMalloc: code running under an allocator that owns all device
+// memory (a framework's caching allocator or a fixed arena), and embedded hosts that forbid
+// device allocation after start-up.  This entry point serves them: its only scratch is the file-scope array below,
 // part of the library's device image, so every GPU that loads the library holds it (256 KB) until
 // the process exits.
 //

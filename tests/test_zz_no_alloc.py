@@ -1,6 +1,6 @@
-"""The allocation-free loss entry point (for callers that cannot call cudaMalloc, e.g. work
-recorded into a CUDA graph or code whose allocator owns all device memory) matches the regular
-loss entry point.  This file is collected last on purpose."""
+"""The allocation-free loss entry point (for callers that cannot call cudaMalloc, e.g. code whose
+allocator owns all device memory, or hosts that forbid device allocation after start-up) matches
+the regular loss entry point.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
