@@ -406,7 +406,9 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     cudaError_t e = cudaMallocHost(&c->h_total, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_error, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_error, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_loss_partials, sizeof(float) * kLossBlocks);
+    // the loss's block partials and, after them, its block counter (zero between calls)
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_loss_partials, sizeof(float) * (kLossBlocks + 1));
+    if (e == cudaSuccess) e = cudaMemset(c->d_loss_partials + kLossBlocks, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_batch_counters, sizeof(unsigned int) * kBatchCounterSlots);
     if (e == cudaSuccess) {

@@ -497,6 +497,20 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(const __grid_cons
     __syncthreads();
     const uint32_t tile = *s_tile_p;
     const int64_t left = a.n - (int64_t)tile * kPassTile;
+    // a pass whose digit is the same for every key (one digit holds all n) is the identity: every
+    // block of the pass sees the same totals, so all of them copy their tile and none waits on
+    // another's look-back word
+    if (__syncthreads_or((int)threadIdx.x < radix && a.totals[threadIdx.x] == (uint32_t)a.n)) {
+        const int64_t base = (int64_t)tile * kPassTile;
+        const int cnt = left < (int64_t)kPassTile ? (int)left : kPassTile;
+        for (int t = threadIdx.x; t < cnt; t += kSortThreads) {
+            const uint32_t key = a.keys_in[base + t], val = a.vals_in[base + t];
+            a.keys_out[base + t] = key;
+            a.vals_out[base + t] = val;
+            if (a.table) a.gathered[base + t] = a.table[val];
+        }
+        return;
+    }
     if (left >= kPassTile)
         sort_tile<true>(a, tile, kPassTile, s_keys, s_vals, s_wc, s_cnt, s_dstart, s_gbase, s_warp);
     else

@@ -579,6 +579,8 @@ std::string mlp_backward(const float* params3, int64_t N, const void* theta16, c
                          unsigned int* err, cudaStream_t stream);
 
 // loss.cu
+// partials: kLossBlocks floats, then one unsigned counter that is zero between calls (the last
+// block to finish sums the partials and puts it back to zero)
 void launch_l2_loss(const float* img, const float* target, int64_t n, float* loss, float* grad, float* partials,
                     cudaStream_t stream);
 constexpr int kLossBlocks = 304;  // 2 x 152 SMs

@@ -4,10 +4,16 @@
 namespace wipes {
 namespace {
 
+// One launch: every block adds the squared differences of its grid-stride share and writes the
+// gradient; the last block to finish (a counter after the partials) sums the block partials in a
+// fixed order in binary64, writes the loss and puts the counter back to zero.
 __global__ void __launch_bounds__(256) k_l2_loss(const float* __restrict__ img, const float* __restrict__ target,
-                                                 int64_t n, float* __restrict__ grad, float* __restrict__ partials) {
+                                                 int64_t n, float* __restrict__ grad, float* __restrict__ partials,
+                                                 float* __restrict__ loss) {
     pdl_enter();
     __shared__ float s_warp[8];
+    __shared__ double s_sum[256];
+    __shared__ bool s_last;
     const float scale = 2.0f / (float)n;
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x, first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -37,24 +43,29 @@ __global__ void __launch_bounds__(256) k_l2_loss(const float* __restrict__ img, 
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = acc;
     __syncthreads();
+    unsigned int* counter = reinterpret_cast<unsigned int*>(partials + kLossBlocks);
     if (threadIdx.x == 0) {
         float s = 0.f;
         for (int w = 0; w < 8; ++w) s += s_warp[w];
         partials[blockIdx.x] = s;
+        __threadfence();  // the partial is visible before the count says so
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
-}
-
-__global__ void k_l2_finish(const float* __restrict__ partials, int nb, int64_t n, float* __restrict__ loss) {
-    pdl_enter();
-    __shared__ double s[32];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += 32) acc += partials[i];
-    s[threadIdx.x] = acc;
-    __syncwarp();
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nb = (int)gridDim.x;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) t += (double)__ldcg(partials + i);
+    s_sum[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < 32; ++i) t += s[i];
-        *loss = (float)(t / (double)n);
+        *loss = (float)(s_sum[0] / (double)n);
+        *counter = 0u;
     }
 }
 
@@ -63,8 +74,8 @@ __global__ void k_l2_finish(const float* __restrict__ partials, int nb, int64_t 
 void launch_l2_loss(const float* img, const float* target, int64_t n, float* loss, float* grad, float* partials,
                     cudaStream_t stream) {
     const int nb = (int)std::min<int64_t>(kLossBlocks, std::max<int64_t>(1, ceil_div(n, 256)));
-    launch_pdl(k_l2_loss, nb, 256, 0, stream, img, target, n, grad, partials); count_launches(1);
-    launch_pdl(k_l2_finish, 1, 32, 0, stream, partials, nb, n, loss); count_launches(1);
+    launch_pdl(k_l2_loss, nb, 256, 0, stream, img, target, n, grad, partials, loss);
+    count_launches(1);
 }
 
 }  // namespace wipes

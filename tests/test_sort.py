@@ -35,6 +35,29 @@ def test_sort_matches_oracle(n, key_bits, seed):
     assert np.array_equal(dv, ov)
 
 
+@pytest.mark.parametrize("n,key_bits,shape,seed", [
+    (300_001, 32, "top byte 0", 13),      # the last of four one-sweep passes has one digit
+    (300_003, 24, "low byte 0", 14),      # the first pass has one digit
+    (4097, 32, "top two bytes 0", 15),     # two passes with one digit, a ragged last tile
+])
+def test_sort_passes_with_a_single_digit(n, key_bits, shape, seed):
+    """Passes whose digit is the same for every key keep the order as it is (the kernels copy the
+    tile instead of ranking it); the result still equals the oracle's stable sort."""
+    rng = np.random.default_rng(seed)
+    keys = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    if shape == "top byte 0":
+        keys &= np.uint32(0x00FFFFFF)
+    elif shape == "low byte 0":
+        keys &= np.uint32(0x00FFFF00)
+    else:
+        keys &= np.uint32(0x0000FFFF)
+    vals = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    dk, dv = _run(keys, vals, key_bits)
+    ok, ov = oracle.sort_pairs(keys, vals, key_bits)
+    assert np.array_equal(dk, ok)
+    assert np.array_equal(dv, ov)
+
+
 def test_sort_with_heavy_ties_keeps_input_order():
     rng = np.random.default_rng(11)
     n = 600_001
