@@ -19,6 +19,10 @@ __global__ void __launch_bounds__(kQuadThreads) k_blend3d(BlendJob job, const ui
     blend3d_quad<DAMP>(job, (int)order[blockIdx.x >> 2], (int)(blockIdx.x & 3u));
 }
 
+// Entries whose terms come from at most this many lanes of a warp are added by those lanes
+// directly instead of through the warp's reduce-scatter.
+constexpr int kBwdDirectLanes = 4;
+
 // Image-plane gradient per primitive: mx my l11 l21 l22 fx fy phc c_r c_g c_b o (12 floats a row),
 // and with DAMP kappa (13 components in rows of 16).
 template <bool DAMP>
@@ -133,6 +137,17 @@ __device__ __forceinline__ void bwd_apply(const BwdEval& r, const ulonglong2 (*s
     float tot16[16];
 #pragma unroll
     for (int i = 0; i < kG; ++i) tot16[i] = f2_lo(acc[i]) + f2_hi(acc[i]);
+    // an entry that reaches the pixels of only a few lanes (a small footprint, or the edge of a
+    // larger one): those lanes add their terms directly, which costs fewer instructions than the
+    // warp's reduction (a lane whose pixels the entry does not reach holds only zero terms)
+    const bool mine = r.k0 || r.k1;
+    if (__popc(__ballot_sync(0xffffffffu, mine)) <= kBwdDirectLanes) {
+        if (mine) {
+#pragma unroll
+            for (int i = 0; i < kG; ++i) atomicAdd(grad + i, tot16[i]);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = kG; i < 16; ++i) tot16[i] = 0.f;
     const float tot = warp_reduce_scatter16(tot16);
