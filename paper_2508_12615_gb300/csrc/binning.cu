@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
     PixRect r{1, 1, 0, 0};
     int tx0 = 0, ty0 = 0, nx = 1, nt = 0;
     bool big = false;
+    Ellipse eb{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (j < n) {
         p = perm ? perm[j] : (uint32_t)j;
         cnt = counts[p];
@@ -132,28 +133,33 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
             ty0 = r.v0 / kTile;
             nx = r.u1 / kTile - tx0 + 1;
             nt = nx * (r.v1 / kTile - ty0 + 1);
+            const int ty1 = ty0 + nt / nx;  // one past the last tile row
             if ((int)cnt == nt) {
-                for (int t = 0; t < nt; ++t) {
-                    const uint32_t w = o + (uint32_t)t;
-                    keys[w] = (uint32_t)((ty0 + t / nx) * tiles_x + tx0 + t % nx);
-                    vals[w] = w;
-                    inst_prim[w] = p;
-                }
+                uint32_t w = o;
+                for (int ty = ty0; ty < ty1; ++ty)
+                    for (int tx = tx0; tx < tx0 + nx; ++tx, ++w) {
+                        keys[w] = (uint32_t)(ty * tiles_x + tx);
+                        vals[w] = w;
+                        inst_prim[w] = p;
+                    }
             } else if (nt <= kEmitSmall) {
                 const float4 A = rec[(size_t)p * kRecF4 + 0];
                 const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
                 uint32_t w = o;
-                for (int t = 0; t < nt; ++t) {
-                    const int ty = ty0 + t / nx, tx = tx0 + t % nx;
-                    if (tile_touched(e, r, tx, ty, lim)) {
-                        keys[w] = (uint32_t)(ty * tiles_x + tx);
-                        vals[w] = w;
-                        inst_prim[w] = p;
-                        ++w;
-                    }
-                }
+                for (int ty = ty0; ty < ty1; ++ty)
+                    for (int tx = tx0; tx < tx0 + nx; ++tx)
+                        if (tile_touched(e, r, tx, ty, lim)) {
+                            keys[w] = (uint32_t)(ty * tiles_x + tx);
+                            vals[w] = w;
+                            inst_prim[w] = p;
+                            ++w;
+                        }
             } else {
+                // a large range: the warp emits it below; its ellipse is made here, by every such
+                // lane at once, so that the warp's walk over them waits on no load
                 big = true;
+                const float4 A = rec[(size_t)p * kRecF4 + 0];
+                eb = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
             }
         }
     }
@@ -168,14 +174,29 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
         rk.v0 = __shfl_sync(0xffffffffu, r.v0, k);
         rk.v1 = __shfl_sync(0xffffffffu, r.v1, k);
         uint32_t ok = __shfl_sync(0xffffffffu, o, k);
-        const float4 A = rec[(size_t)pk * kRecF4 + 0];
-        const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)pk * kRecF4 + 1].x);
+        Ellipse e;
+        e.mx = __shfl_sync(0xffffffffu, eb.mx, k);
+        e.my = __shfl_sync(0xffffffffu, eb.my, k);
+        e.l11 = __shfl_sync(0xffffffffu, eb.l11, k);
+        e.l21 = __shfl_sync(0xffffffffu, eb.l21, k);
+        e.l22 = __shfl_sync(0xffffffffu, eb.l22, k);
+        e.rBA = __shfl_sync(0xffffffffu, eb.rBA, k);
+        e.rBC = __shfl_sync(0xffffffffu, eb.rBC, k);
         const int kx0 = rk.u0 / kTile, ky0 = rk.v0 / kTile;
         const int knx = rk.u1 / kTile - kx0 + 1, knt = knx * (rk.v1 / kTile - ky0 + 1);
+        // tile t = t0 + lane of the range as (row, column) = divmod(t, knx), advanced by 32 a step
+        const int s_row = 32 / knx, s_col = 32 % knx;
+        int row = lane / knx, col = lane % knx;
         for (int t0 = 0; t0 < knt; t0 += 32) {
             const int t = t0 + lane;
-            const int ty = ky0 + t / knx, tx = kx0 + t % knx;
+            const int ty = ky0 + row, tx = kx0 + col;
             const bool hit = t < knt && tile_touched(e, rk, tx, ty, lim);
+            row += s_row;
+            col += s_col;
+            if (col >= knx) {
+                col -= knx;
+                ++row;
+            }
             const uint32_t bal = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 const uint32_t w = ok + __popc(bal & ((1u << lane) - 1u));

@@ -50,7 +50,9 @@ __device__ __forceinline__ uint32_t warp_tile_counts(float mx, float my, float l
         const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
         const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
         if (nt <= kSmallRangeTiles) {
-            for (int t = 0; t < nt; ++t) result += tile_touched(mine, r, tx0 + t % nx, ty0 + t / nx, lim) ? 1u : 0u;
+            const int ty1 = ty0 + nt / nx;
+            for (int ty = ty0; ty < ty1; ++ty)
+                for (int tx = tx0; tx < tx0 + nx; ++tx) result += tile_touched(mine, r, tx, ty, lim) ? 1u : 0u;
         } else {
             big = true;
         }
@@ -75,10 +77,19 @@ __device__ __forceinline__ uint32_t warp_tile_counts(float mx, float my, float l
         const int tx0 = rk.u0 / kTile, ty0 = rk.v0 / kTile;
         const int nx = rk.u1 / kTile - tx0 + 1, nt = nx * (rk.v1 / kTile - ty0 + 1);
         uint32_t c = 0;
+        // tile t = t0 + lane of the range as (row, column) = divmod(t, nx), advanced by 32 a step
+        const int s_row = 32 / nx, s_col = 32 % nx;
+        int row = lane / nx, col = lane % nx;
         for (int t0 = 0; t0 < nt; t0 += 32) {
             const int t = t0 + lane;
-            const bool hit = t < nt && tile_touched(e, rk, tx0 + t % nx, ty0 + t / nx, lim);
+            const bool hit = t < nt && tile_touched(e, rk, tx0 + col, ty0 + row, lim);
             c += __popc(__ballot_sync(0xffffffffu, hit));
+            row += s_row;
+            col += s_col;
+            if (col >= nx) {
+                col -= nx;
+                ++row;
+            }
         }
         if (lane == k) result = c;
     }
