@@ -293,7 +293,7 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
         launch_emit(st->counts.as<uint32_t>(), perm, N, st->rec.as<float4>(), st->rect.as<PixRect>(),
                     st->block_sums.as<unsigned long long>(), st->tiles_x, touch_limit(st->opts.cutoff_sigma),
                     st->keys[0].as<uint32_t>(), st->vals[0].as<uint32_t>(), st->inst_prim.as<uint32_t>(),
-                    st->offsets.as<uint32_t>(), s);
+                    st->offsets.as<uint32_t>(), st->ranges.as<uint2>(), n_tiles, s);
     }
     uint32_t* kb[2] = {st->keys[0].as<uint32_t>(), st->keys[1].as<uint32_t>()};
     uint32_t* vb[2] = {st->vals[0].as<uint32_t>(), st->vals[1].as<uint32_t>()};
@@ -304,7 +304,7 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
     }
     {
         StageTimer t(st->ctx, WIPES_STAGE_RANGES, s);
-        launch_tile_ranges(kb[st->sorted], I, st->ranges.as<uint2>(), n_tiles, s);
+        launch_tile_ranges(kb[st->sorted], I, st->ranges.as<uint2>(), n_tiles, /*zeroed=*/N > 0, s);
     }
     return WIPES_OK;
 }

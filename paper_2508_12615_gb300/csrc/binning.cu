@@ -82,9 +82,12 @@ __global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long
 __global__ void __launch_bounds__(kThreads) k_scan_offsets(const uint32_t* __restrict__ counts,
                                                            const uint32_t* __restrict__ perm, int64_t n,
                                                            const unsigned long long* __restrict__ block_offsets,
-                                                           uint32_t* __restrict__ offsets) {
+                                                           uint32_t* __restrict__ offsets, uint2* __restrict__ ranges,
+                                                           int n_tiles) {
     pdl_enter();
     __shared__ unsigned long long s_warp[kWarps];
+    // the tile ranges start empty: k_tile_ranges writes those of the tiles that get pairs
+    for (int t = blockIdx.x * kThreads + threadIdx.x; t < n_tiles; t += gridDim.x * kThreads) ranges[t] = make_uint2(0u, 0u);
     const int64_t base = (int64_t)blockIdx.x * kScanBlockElems + threadIdx.x * kScanItems;
     uint32_t prim[kScanItems], cnt[kScanItems];
     unsigned long long s = 0;
@@ -603,9 +606,10 @@ void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned lon
 
 void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,
                  const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
-                 uint32_t* inst_prim, uint32_t* offsets, cudaStream_t stream) {
+                 uint32_t* inst_prim, uint32_t* offsets, uint2* ranges, int n_tiles, cudaStream_t stream) {
     if (n == 0) return;
-    launch_pdl(k_scan_offsets, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_offsets, offsets);
+    launch_pdl(k_scan_offsets, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_offsets, offsets,
+               ranges, n_tiles);
     launch_pdl(k_emit, ceil_div(n, kThreads), kThreads, 0, stream, counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
                vals, inst_prim);
     count_launches(2);
@@ -618,8 +622,9 @@ void launch_gather_u32(uint32_t* out, const uint32_t* table, const uint32_t* idx
     count_launches(1);
 }
 
-void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, int n_tiles, cudaStream_t stream) {
-    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, stream);
+void launch_tile_ranges(const uint32_t* sorted_keys, int64_t n, uint2* ranges, int n_tiles, bool zeroed,
+                        cudaStream_t stream) {
+    if (!zeroed) cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, stream);
     if (n == 0) return;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
     launch_pdl(k_tile_ranges, grid, 256, 0, stream, sorted_keys, n, ranges); count_launches(1);

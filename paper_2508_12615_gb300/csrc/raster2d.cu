@@ -74,7 +74,7 @@ __device__ __forceinline__ void group4_reduce_scatter16(float v[16]) {
 // L, f and the centre are constant over the pair.  The colours are staged halved and the
 // modulation taken as G (1 + cos), which saves the 1/2 of W per pixel; the sums are taken of
 // -ga, -gb and -gt / (2 pi) and scaled once per pair.
-__global__ void __launch_bounds__(kTilePixels, 2) k_backward2d(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __restrict__ rec,
                                                             const PixRect* __restrict__ rect, TileLists tl, int W,
                                                             int H, int tiles_x, float cutoff2, float lim,
                                                             float cut_scale, const float* __restrict__ dl_dout,
@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kTilePixels, 2) k_backward2d(const float4* __r
     // 32 k + 8 r + ((c + 2 r) & 7), so that the four rows of a walk read four different bank groups
     __shared__ ulonglong2 s_g[kTilePixels / 2];
     __shared__ unsigned long long s_gb[kTilePixels / 2];
-    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) / 2 (c_b / 2, 0), each value twice
+    // staged entry k: (mx, my) (l11, l21) (l22, fx) (fy, phc) (c_r, c_g) / 2, each value twice, then
+    // (c_b / 2, c_b / 2) and the column rotation (cos 2 pi fx, sin 2 pi fx)
     __shared__ ulonglong2 s_e[6][kTilePixels];
     __shared__ uint32_t s_slot[kTilePixels];
     __shared__ uint8_t s_mask[kTilePixels];
@@ -134,7 +135,9 @@ __global__ void __launch_bounds__(kTilePixels, 2) k_backward2d(const float4* __r
             s_e[2][threadIdx.x] = dup2(B.x, B.y);
             s_e[3][threadIdx.x] = dup2(B.z, B.w);
             s_e[4][threadIdx.x] = dup2(0.5f * C.x, 0.5f * C.y);
-            s_e[5][threadIdx.x] = dup2(0.5f * C.z, 0.f);
+            float srot, crot;
+            sincospif(2.0f * B.y, &srot, &crot);  // once per staged entry, for every lane that walks it
+            s_e[5][threadIdx.x] = make_ulonglong2(f2_dup(0.5f * C.z).r, f2_pack(crot, srot).r);
             const uint32_t m = quadrant_mask_ellipse(A, B.x, rect[prim], x0, y0, lim);
             s_mask[threadIdx.x] = (uint8_t)m;
             s_slot[threadIdx.x] = e;
@@ -168,8 +171,8 @@ __global__ void __launch_bounds__(kTilePixels, 2) k_backward2d(const float4* __r
             // the rotation of the phasor from one column to the next: 2 pi fx
             f2 CX, SX, NSX;
             {
-                float sx, cx;
-                sincospif(2.0f * f2_lo(ld_f2x2(&s_e[2][j]).y), &sx, &cx);
+                const f2 rot = ld_f2x2(&s_e[5][j]).y;  // (cos, sin)(2 pi fx), staged
+                const float cx = f2_lo(rot), sx = f2_hi(rot);
                 CX = f2_dup(cx), SX = f2_dup(dir * sx), NSX = f2_dup(-dir * sx);
             }
             while (__any_sync(0xffffffffu, mask != 0u)) {
