@@ -216,6 +216,32 @@ def test_edge_cases():
     assert ok, (worst, idx)
 
 
+def test_state_reused_for_a_frame_with_no_pairs():
+    """A state that held tile lists is reused for primitives that all lie off-screen (primitives,
+    but no (tile, primitive) pairs): every tile range comes back empty, the image and the gradient
+    are zero."""
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 48, 64
+    st = w.Context.get(0).acquire_state()
+    p = synth.scene2d(300, H, W, 41)
+    params = torch.from_numpy(p).cuda()
+    w.forward2d(params, H, W, state=st)
+    torch.cuda.synchronize()
+    assert st.info()["n_instances"] > 0
+    q = p.copy()
+    q[:, 0] += 10_000.0  # every centre far to the right of the image
+    params2 = torch.from_numpy(q).cuda()
+    img = w.forward2d(params2, H, W, state=st)
+    grad = w.backward(st, params2, torch.ones(H, W, 3, device="cuda"))
+    torch.cuda.synchronize()
+    assert st.info()["n_instances"] == 0
+    _, _, ranges = st.lists()
+    r = ranges.cpu().numpy()
+    assert np.all(r[:, 0] == r[:, 1])
+    assert img.abs().max().item() == 0 and grad.abs().max().item() == 0
+
+
 def test_full_size_768x512_70k_sampled():
     """The 768x512, 70,000-primitive image-fitting workload, in the launch configuration the
     benchmark times: lists bit-exact, sampled pixels and sampled primitive gradients vs the oracle."""
