@@ -19,6 +19,7 @@ import json
 import math
 import os
 import statistics
+import types
 import subprocess
 import sys
 import tempfile
@@ -326,6 +327,24 @@ class Workload:
             self.p3 = torch.empty(p.shape[0], 20, device=dev)
             self.g3 = torch.empty_like(self.p3)
         self.batch = 4 if kind in ("6d", "6dmlp") else 1
+        # 6D: the step's samples run concurrently, one stream each, every one with its own library
+        # context (a context's loss buffer serves one call at a time), state and buffers; only
+        # their accumulation into the shared parameter gradient follows the sample order
+        self.lanes = []
+        self.concurrent = True
+        if kind in ("6d", "6dmlp"):
+            for b in range(self.batch):
+                first = b == 0
+                lctx = ctx if first else w.Context(dev.index)
+                lane = types.SimpleNamespace(
+                    ctx=lctx, st=self.st if first else w.State(lctx), stream=torch.cuda.Stream(device=dev),
+                    done=torch.cuda.Event(), img=self.img if first else torch.empty_like(self.img),
+                    gimg=self.gimg if first else torch.empty_like(self.gimg),
+                    p3=self.p3 if first else torch.empty_like(self.p3), g3=self.g3 if first else torch.empty_like(self.g3),
+                    loss=self.out[n_out + b])
+                if kind == "6dmlp":
+                    lane.st_mlp = self.st_mlp if first else w.State(lctx)
+                self.lanes.append(lane)
         self.k = 0
         self.pixels_per_step = self.H * self.W * self.batch
 
@@ -352,36 +371,70 @@ class Workload:
             w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
             w.backward(self.st, params, self.gimg, out=self.grad)
             return
+        raise AssertionError("6D samples run through _one_6d")
+
+    def _one_6d(self, lane, b, params, target, fwd_only, prev_done):
+        """Sample b of a 6D step on its lane's stream (the current stream): the time model or the
+        network, the render, the loss, the render backward, and, after sample b - 1's (prev_done),
+        the accumulation into the parameter gradient."""
+        import torch
+
         from paper_2508_12615_gb300 import _abi
         from paper_2508_12615_gb300.render import _ptr, _stream
 
+        w = self.w
+        cam_i, t = self._sample()
+        cam = self.cams[cam_i]
         n = params.shape[0]
         if self.kind == "6dmlp":
-            w.deform_mlp(params, t, self.theta, state=self.st_mlp, out=self.p3)
-            w.forward3d(self.p3, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
-            if fwd_only:
-                return
-            w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
-            w.backward(self.st, self.p3, self.gimg, out=self.g3)
-            w.deform_mlp_backward(self.st_mlp, params, self.g3, grad_theta=self.gtheta, grad_params3=self.grad,
-                                  accumulate=accumulate)
-            return
-        _abi.call("wipes_deform6d", _ptr(params), n, t, _ptr(self.p3), _stream(self.dev))
-        w.forward3d(self.p3, cam, self.H, self.W, self.opts, state=self.st, out=self.img)
+            w.deform_mlp(params, t, self.theta, state=lane.st_mlp, out=lane.p3)
+        else:
+            _abi.call("wipes_deform6d", _ptr(params), n, t, _ptr(lane.p3), _stream(self.dev))
+        w.forward3d(lane.p3, cam, self.H, self.W, self.opts, state=lane.st, out=lane.img)
         if fwd_only:
             return
-        w.l2_loss(self.img, target, loss=self.loss, grad=self.gimg)
-        w.backward(self.st, self.p3, self.gimg, out=self.g3)
-        _abi.call("wipes_deform6d_backward", _ptr(params), n, t, _ptr(self.g3), _ptr(self.grad), int(accumulate),
-                  _stream(self.dev))
+        w.l2_loss(lane.img, target, loss=lane.loss, grad=lane.gimg, ctx=lane.ctx)
+        w.backward(lane.st, lane.p3, lane.gimg, out=lane.g3)
+        if prev_done is not None:
+            torch.cuda.current_stream().wait_event(prev_done)
+        if self.kind == "6dmlp":
+            w.deform_mlp_backward(lane.st_mlp, params, lane.g3, grad_theta=self.gtheta, grad_params3=self.grad,
+                                  accumulate=b > 0)
+        else:
+            _abi.call("wipes_deform6d_backward", _ptr(params), n, t, _ptr(lane.g3), _ptr(self.grad), int(b > 0),
+                      _stream(self.dev))
+        lane.done.record()
+
+    def _lanes_run(self, params, target, fwd_only):
+        import torch
+
+        main = torch.cuda.current_stream()
+        if not self.concurrent:  # one sample after another on the current stream
+            for b, lane in enumerate(self.lanes):
+                self._one_6d(lane, b, params, target, fwd_only, None)
+            return
+        prev = None
+        for b, lane in enumerate(self.lanes):
+            lane.stream.wait_stream(main)
+            with torch.cuda.stream(lane.stream):
+                self._one_6d(lane, b, params, target, fwd_only, prev)
+            prev = lane.done
+        for lane in self.lanes:
+            main.wait_stream(lane.stream)
 
     def step(self, params=None, target=None):
         params = self.params if params is None else params
         target = self.target_d if target is None else target
+        if self.lanes:
+            self._lanes_run(params, target, fwd_only=False)
+            return
         for b in range(self.batch):
             self._one(params, target, accumulate=b > 0)
 
     def forward(self):
+        if self.lanes:
+            self._lanes_run(self.params, self.target_d, fwd_only=True)
+            return
         for b in range(self.batch):
             self._one(self.params, self.target_d, fwd_only=True)
 
@@ -391,7 +444,10 @@ class Workload:
         from paper_2508_12615_gb300 import _abi
 
         self.k = 0
-        self._one(self.params, self.target_d, fwd_only=True)
+        if self.lanes:
+            self._one_6d(self.lanes[0], 0, self.params, self.target_d, True, None)
+        else:
+            self._one(self.params, self.target_d, fwd_only=True)
         visited, inside = ctypes.c_int64(), ctypes.c_int64()
         _abi.call("wipes_state_count_pairs", self.ctx.handle, self.st.handle, ctypes.byref(visited),
                   ctypes.byref(inside), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -437,13 +493,16 @@ def measure(wl, steps: int, warmup: int, flush, dist, world: int, dev, sample_cl
     clocks = sampler.stop() if sampler else None
     launches = lib.wipes_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    # per-stage times: more steps with the library's CUDA-event brackets around each stage
+    # per-stage times: more steps with the library's CUDA-event brackets around each stage (the
+    # samples of a 6D step one after another, so that each kernel is timed alone)
     lib.wipes_set_timing(ctx.handle, 1)
     lib.wipes_get_timing(ctx.handle, None, None, 1)
+    wl.concurrent = False
     for _ in range(max(3, min(steps, 20))):
         flush.zero_()
         wl.step()
     torch.cuda.synchronize()
+    wl.concurrent = True
     stage_ms = (ctypes.c_double * len(_abi.STAGES))()
     stage_n = (ctypes.c_int64 * len(_abi.STAGES))()
     lib.wipes_get_timing(ctx.handle, stage_ms, stage_n, 1)

@@ -135,7 +135,7 @@ def forward2d(params: torch.Tensor, H: int, W: int, opts: _abi.Opts | None = Non
               out: torch.Tensor | None = None) -> torch.Tensor:
     """Summed wavelet field [H,W,3] (no autograd)."""
     params = _check(params, P2D, "params")
-    ctx = Context.get(params.device)
+    ctx = state.ctx if state is not None else Context.get(params.device)
     state = state or ctx.acquire_state()
     opts = opts or make_opts(2)
     if out is None:
@@ -151,7 +151,7 @@ def forward3d(params: torch.Tensor, camera, H: int, W: int, opts: _abi.Opts | No
     [N,68] with spherical-harmonic colour (opts.sh_degree > 0)."""
     opts = opts or make_opts(3)
     params = _check(params, P3D_SH if opts.sh_degree else P3D, "params")
-    ctx = Context.get(params.device)
+    ctx = state.ctx if state is not None else Context.get(params.device)
     state = state or ctx.acquire_state()
     cam = _abi.camera_struct(camera.tolist() if hasattr(camera, "tolist") else camera)
     if out is None:
@@ -173,11 +173,13 @@ def backward(state: State, params: torch.Tensor, grad_out: torch.Tensor,
 
 
 def l2_loss(img: torch.Tensor, target: torch.Tensor, loss: torch.Tensor | None = None,
-            grad: torch.Tensor | None = None):
-    """(mean squared error as a device scalar, its gradient with respect to img)."""
+            grad: torch.Tensor | None = None, ctx: Context | None = None):
+    """(mean squared error as a device scalar, its gradient with respect to img).  The call uses
+    a small reduction buffer of its context (the device's default one unless ``ctx`` is given):
+    calls on one context must not overlap on the GPU."""
     img = img.contiguous()
     target = target.contiguous()
-    ctx = Context.get(img.device)
+    ctx = ctx or Context.get(img.device)
     if loss is None:
         loss = torch.empty((), dtype=torch.float32, device=img.device)
     if grad is None:
@@ -279,7 +281,7 @@ def deform_mlp(params3: torch.Tensor, t: float, theta: torch.Tensor, state: Stat
     theta = theta.contiguous()
     if theta.dtype != torch.float32 or theta.numel() != deform_mlp_param_count():
         raise ValueError("theta must be float32 with deform_mlp_param_count() entries")
-    ctx = Context.get(params3.device)
+    ctx = state.ctx if state is not None else Context.get(params3.device)
     state = state or ctx.acquire_state()
     if out is None:
         out = torch.empty_like(params3)
