@@ -51,6 +51,10 @@ __device__ __forceinline__ void group4_reduce_scatter16(float v[16]) {
     }
 }
 
+// The 2D backward's pairs are independent of one another, so a tile's staged batches of 256 list
+// entries are shared out over kBwdSplit blocks: more, smaller blocks leave a shorter tail.
+constexpr int kBwdSplit = 2;
+
 // Backward.  The tile's dL/dimage sits in shared memory by pixel pairs: pair (k, r, c) holds the
 // pixels (c, r) and (c, r + 4) of the 8x8 quadrant k.  Batches of the tile list
 // are staged with the mask of the quadrants that each pair's cutoff ellipse reaches, and ordered
@@ -91,7 +95,12 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
     __shared__ uint8_t s_mask[kTilePixels];
     __shared__ uint16_t s_order[kTilePixels];  // staged entries, most quadrants first
     __shared__ uint32_t s_nq[5];               // staged entries that reach 0 .. 4 quadrants
-    const int tile = blockIdx.x;
+    // block (part, tile): the tile's staged batches part, part + kBwdSplit, ...; the first parts of
+    // all tiles come first
+    const int n_tiles = (int)(gridDim.x / kBwdSplit);
+    const int tile = (int)blockIdx.x % n_tiles, part = (int)blockIdx.x / n_tiles;
+    const uint2 range = tl.ranges[tile];
+    if (range.x + (uint32_t)part * kTilePixels >= range.y) return;  // the whole block: no batch of its own
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -118,8 +127,7 @@ __global__ void __launch_bounds__(kTilePixels, 3) k_backward2d(const float4* __r
     if (threadIdx.x < 5) s_nq[threadIdx.x] = 0u;
     const f2 K = f2_dup(kNegHalfLog2e);
     const f2 NEG_S = f2_dup(-cut_scale), CUT_S = f2_dup(cutoff2 * cut_scale);  // exact: a power-of-two scale
-    const uint2 range = tl.ranges[tile];
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
+    for (uint32_t b0 = range.x + (uint32_t)part * kTilePixels; b0 < range.y; b0 += kBwdSplit * kTilePixels) {
         const int n = (int)min((uint32_t)kTilePixels, range.y - b0);
         __syncthreads();
         int my_q = 0;
@@ -448,7 +456,7 @@ void launch_blend2d(const BlendJob& job, int tiles_y, cudaStream_t stream) {
 void launch_backward2d(const float4* rec, const PixRect* rect, const TileLists& tl, int W, int H, int tiles_x,
                        int tiles_y, float cutoff, const float* dl_dout, float* partial, cudaStream_t stream) {
     const float cutoff2 = cutoff * cutoff;
-    launch_pdl(k_backward2d, tiles_x * tiles_y, kTilePixels, 0, stream, rec, rect, tl, W, H, tiles_x, cutoff2,
+    launch_pdl(k_backward2d, kBwdSplit * tiles_x * tiles_y, kTilePixels, 0, stream, rec, rect, tl, W, H, tiles_x, cutoff2,
                touch_limit(cutoff), cutoff_scale(cutoff2), dl_dout, partial);
     count_launches(1);
 }
