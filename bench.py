@@ -47,7 +47,7 @@ OPS_PER_PAIR = {"2d": {"blend": (15, 2), "bwd_raster": (37.5, 3)}, "3d": {"blend
 # DRAM bytes (read + write) per launch, per (workload, kernel), from the ncu captures summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), for the kernel build measured there; an
 # entry is removed when its kernel changes.
-TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_516_032 + 723_712, ("2d", "k_blend2d"): 9_069_824,
+TRAFFIC_BYTES = {("2d", "k_backward2d"): 17_499_648 + 737_536, ("2d", "k_blend2d"): 9_069_824,
                  ("5d", "k_backward3d"): 23_489_536 + 3_840, ("5d", "k_blend3d"): 14_042_880 + 19_712}
 
 
