@@ -189,10 +189,10 @@ def grad3d(params, cam, H, W, dldimg, opts=None, truncated=True, with_abs=False)
 
 
 def rule_cos_sin(theta):
-    """The footprint rule's binary32 (cos, sin) of 2D rotation angles (binary64 inputs): a fixed
-    sequence of binary64 additions and multiplications (Cody-Waite reduction, Taylor series),
-    rounded once.  Returns [n,2] float32."""
-    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    """The footprint rule's binary32 (cos, sin) of 2D rotation angles, taken as binary32 (the
+    record's type): a fixed sequence of IEEE operations (Cody-Waite reduction, Taylor series; in
+    binary32 up to |theta| = 2^16, in binary64 rounded once beyond).  Returns [n,2] float32."""
+    th = np.ascontiguousarray(theta, dtype=np.float32).ravel()
     out = np.zeros((th.size, 2), np.float32)
     _load().wo_rule_cos_sin(_ptr(th), th.size, _ptr(out))
     return out

@@ -88,16 +88,21 @@ static void footprint_pixrect(fp32_footprint* k, int W, int H) {
     if (u0 > u1 || v0 > v1) { k->u0 = 1; k->u1 = 0; k->v0 = 1; k->v1 = 0; }
 }
 
-/* cos and sin of the 2D rotation angle for the footprint rule, as a fixed sequence of binary64
- * additions and multiplications (no library transcendental, so that any two IEEE binary64
- * implementations of the rule return the same bits), rounded once to binary32.
- * Cody and Waite's reduction: k = nearest integer to th 2/pi, r = th - k pi/2 with pi/2 split into
- * three parts (the first two of 33 significant bits, so k times them is exact for |k| < 2^20);
- * then the Taylor series of sin r through r^17 and of cos r through r^18 (|r| <= pi/4: truncation
- * below 1e-19), in Horner form in r^2; the quadrant k mod 4 picks the signs and the swap.
+/* cos and sin of the 2D rotation angle for the footprint rule, as a fixed sequence of IEEE
+ * operations (no library transcendental, so that any two IEEE implementations of the rule return
+ * the same bits).  The angle is the record's binary32 value.
+ * |th| <= 2^16: binary32 arithmetic with fused multiply-adds written as fmaf.  Cody and Waite's
+ * reduction: k = nearest integer to th * (2/pi rounded), r = th - k pi/2 with pi/2 split into three
+ * binary32 parts P1 + P2 + P3 (within 1e-23 of pi/2).  th - k P1 is exact in one fmaf: both are
+ * multiples of 2^-23 (of 2^-24 when |th| < 1, where |k| <= 1) and their difference is below 1.
+ * Then the Taylor series of sin r through r^11 and of cos r through r^10 (|r| <= pi/4 + 0.01:
+ * truncation below 2e-10), in Horner form in z = r^2; the quadrant k mod 4 picks the signs and the
+ * swap.  Each result is within one binary32 ulp of the correctly rounded cosine or sine.
+ * 2^16 < |th| <= 1e15: the same steps in binary64 (pi/2 in parts of 33, 33 and 53 significant
+ * bits, so k times the first two is exact for |k| < 2^20; Taylor series through r^17 and r^18),
+ * rounded once to binary32: the correctly rounded cosine and sine up to |th| = 2^20 pi/2.
  * |th| > 1e15 (or not finite) gives NaN, which makes the primitive invalid. */
-static void rule_cos_sin(double th, float* c, float* s) {
-    if (!(fabs(th) <= 1e15)) { *c = *s = (float)NAN; return; }
+static void rule_cos_sin_wide(double th, float* c, float* s) {
     const double k = nearbyint(th * 0x1.45f306dc9c883p-1);
     const double r = ((th - k * 0x1.921fb544p+0) - k * 0x1.0b4611a6p-34) - k * 0x1.3198a2e037073p-69;
     const double z = r * r;
@@ -128,8 +133,39 @@ static void rule_cos_sin(double th, float* c, float* s) {
     }
 }
 
+static void rule_cos_sin(float th, float* c, float* s) {
+    if (!(fabsf(th) <= 0x1p16f)) {
+        if (!(fabs((double)th) <= 1e15)) { *c = *s = (float)NAN; return; }
+        rule_cos_sin_wide((double)th, c, s);
+        return;
+    }
+    const float k = rintf(th * 0x1.45f306p-1f);  /* th 2/pi */
+    float r = fmaf(-k, 0x1.921fb6p+0f, th);      /* - k P1, exact */
+    r = fmaf(-k, -0x1.777a5cp-25f, r);           /* - k P2 */
+    r = fmaf(-k, -0x1.ee59dap-50f, r);           /* - k P3 */
+    const float z = r * r;
+    float ps = -0x1.ae6456p-26f;                 /* -1/11! */
+    ps = fmaf(ps, z, 0x1.71de3ap-19f);           /*  1/9!  */
+    ps = fmaf(ps, z, -0x1.a01a02p-13f);          /* -1/7!  */
+    ps = fmaf(ps, z, 0x1.111112p-7f);            /*  1/5!  */
+    ps = fmaf(ps, z, -0x1.555556p-3f);           /* -1/3!  */
+    const float sr = fmaf(r * z, ps, r);
+    float pc = -0x1.27e4fcp-22f;                 /* -1/10! */
+    pc = fmaf(pc, z, 0x1.a01a02p-16f);           /*  1/8!  */
+    pc = fmaf(pc, z, -0x1.6c16c2p-10f);          /* -1/6!  */
+    pc = fmaf(pc, z, 0x1.555556p-5f);            /*  1/4!  */
+    pc = fmaf(pc, z, -0.5f);                     /* -1/2!  */
+    const float cr = fmaf(z, pc, 1.0f);
+    switch ((int)k & 3) {
+        case 0: *c = cr; *s = sr; break;
+        case 1: *c = -sr; *s = cr; break;
+        case 2: *c = -cr; *s = -sr; break;
+        default: *c = sr; *s = -cr; break;
+    }
+}
+
 /* exported for its pin: out[n,2] = the rule's (cos, sin) of th[n] */
-int wo_rule_cos_sin(const double* th, int64_t n, float* out) {
+int wo_rule_cos_sin(const float* th, int64_t n, float* out) {
     for (int64_t i = 0; i < n; ++i) rule_cos_sin(th[i], &out[2 * i], &out[2 * i + 1]);
     return 0;
 }
@@ -138,7 +174,7 @@ int wo_rule_cos_sin(const double* th, int64_t n, float* out) {
 static void footprint2d(const float* p, float cutoff, int W, int H, fp32_footprint* k) {
     float sx = p[2], sy = p[3];
     float c, s;
-    rule_cos_sin((double)p[4], &c, &s);
+    rule_cos_sin(p[4], &c, &s);
     float sx2 = sx * sx, sy2 = sy * sy;
     float ix = 1.0f / sx2, iy = 1.0f / sy2;
     float cc = c * c, ss = s * s, cs = c * s;

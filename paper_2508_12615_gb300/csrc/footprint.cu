@@ -34,33 +34,37 @@ __device__ __forceinline__ PixRect covered_pixels(float mx, float my, float ex, 
 }
 
 // Number of tiles of each lane's covered pixel range that its cutoff ellipse reaches
-// (tile_touched()).  A lane whose range spans at most kSmallRangeTiles tiles tests them itself (the
-// common case: most footprints cover a few tiles); the ranges above that are counted by the whole
-// warp, one after another, 32 tiles at a time.  Every lane of the warp must call it; an empty range
-// counts 0.
-constexpr int kSmallRangeTiles = 16;
+// (tile_touched()).  The warp's ranges are laid end to end (an exclusive prefix of their tile
+// counts over the lanes) and tested 32 tiles a round: the tile in slot s belongs to the lane whose
+// prefix range holds s (a binary search over the lanes' inclusive prefixes), and each lane counts
+// the hits in its own slots of the round's ballot.  Every lane of the warp must call it; an empty
+// range counts 0.
 __device__ __forceinline__ uint32_t warp_tile_counts(float mx, float my, float l11, float l21, float l22,
                                                      const PixRect& r, float lim) {
     const int lane = threadIdx.x & 31;
-    uint32_t result = 0;
-    bool big = false;
     Ellipse mine = make_ellipse(0.f, 0.f, 1.f, 0.f, 1.f);
+    int tx0 = 0, ty0 = 0, nx = 1, nt = 0;
     if (r.u0 <= r.u1) {
         mine = make_ellipse(mx, my, l11, l21, l22);
-        const int tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
-        const int nx = r.u1 / kTile - tx0 + 1, nt = nx * (r.v1 / kTile - ty0 + 1);
-        if (nt <= kSmallRangeTiles) {
-            const int ty1 = ty0 + nt / nx;
-            for (int ty = ty0; ty < ty1; ++ty)
-                for (int tx = tx0; tx < tx0 + nx; ++tx) result += tile_touched(mine, r, tx, ty, lim) ? 1u : 0u;
-        } else {
-            big = true;
-        }
+        tx0 = r.u0 / kTile, ty0 = r.v0 / kTile;
+        nx = r.u1 / kTile - tx0 + 1;
+        nt = nx * (r.v1 / kTile - ty0 + 1);
     }
-    uint32_t bigs = __ballot_sync(0xffffffffu, big);
-    while (bigs) {
-        const int k = __ffs(bigs) - 1;
-        bigs &= bigs - 1u;
+    int incl = nt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - nt;
+    uint32_t result = 0;
+    for (int s0 = 0; s0 < total; s0 += 32) {
+        const int s = s0 + lane;
+        int k = 0;  // the number of lanes whose inclusive prefix is at most s: the slot's owner
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, k + step - 1) <= s) k += step;
         PixRect rk;
         rk.u0 = __shfl_sync(0xffffffffu, r.u0, k);
         rk.u1 = __shfl_sync(0xffffffffu, r.u1, k);
@@ -74,24 +78,15 @@ __device__ __forceinline__ uint32_t warp_tile_counts(float mx, float my, float l
         e.l22 = __shfl_sync(0xffffffffu, mine.l22, k);
         e.rBA = __shfl_sync(0xffffffffu, mine.rBA, k);
         e.rBC = __shfl_sync(0xffffffffu, mine.rBC, k);
-        const int tx0 = rk.u0 / kTile, ty0 = rk.v0 / kTile;
-        const int nx = rk.u1 / kTile - tx0 + 1, nt = nx * (rk.v1 / kTile - ty0 + 1);
-        uint32_t c = 0;
-        // tile t = t0 + lane of the range as (row, column) = divmod(t, nx), advanced by 32 a step
-        const int s_row = 32 / nx, s_col = 32 % nx;
-        int row = lane / nx, col = lane % nx;
-        for (int t0 = 0; t0 < nt; t0 += 32) {
-            const int t = t0 + lane;
-            const bool hit = t < nt && tile_touched(e, rk, tx0 + col, ty0 + row, lim);
-            c += __popc(__ballot_sync(0xffffffffu, hit));
-            row += s_row;
-            col += s_col;
-            if (col >= nx) {
-                col -= nx;
-                ++row;
-            }
-        }
-        if (lane == k) result = c;
+        const int t = s - __shfl_sync(0xffffffffu, excl, k);
+        const int nxk = __shfl_sync(0xffffffffu, nx, k);
+        const int txk = __shfl_sync(0xffffffffu, tx0, k), tyk = __shfl_sync(0xffffffffu, ty0, k);
+        const int row = t / nxk, col = t - row * nxk;
+        const bool hit = s < total && tile_touched(e, rk, txk + col, tyk + row, lim);
+        const uint32_t hits = __ballot_sync(0xffffffffu, hit);
+        // this lane's slots of the round: [excl, incl) within [s0, s0 + 32)
+        const int lo = max(excl - s0, 0), hi = min(incl - s0, 32);
+        if (lo < hi) result += (uint32_t)__popc((hits >> lo) & (0xffffffffu >> (32 - (hi - lo))));
     }
     return result;
 }
@@ -106,16 +101,21 @@ __device__ __forceinline__ void write_empty(int64_t i, float4* rec, PixRect* rec
     if (depth_keys) depth_keys[i] = 0xFFFFFFFFu;
 }
 
-// cos and sin of a 2D rotation angle for the footprint rule, built from binary64 additions and
-// multiplications only (each written as its correctly rounded intrinsic, so no contraction or
-// reassociation can change a bit), then rounded once to binary32.  Any IEEE binary64 evaluation
-// of this sequence gives the same bits, which keeps the tile lists bit-exact without relying on
-// two math libraries agreeing.  Reduction by Cody and Waite: k = rint(th * 2/pi),
-// r = th - k pi/2 with pi/2 in three pieces (33, 33 and 53 significant bits; k times the first
-// two is exact for |k| < 2^20).  Then the Taylor series of sin r to r^17 and cos r to r^18
-// (|r| <= pi/4, truncation below 1e-19) in Horner form in z = r^2; k mod 4 selects the quadrant.
-// |th| > 1e15 or a non-finite th gives NaN (the primitive becomes invalid).
-__device__ __forceinline__ void rule_cos_sin(double th, float& c, float& s) {
+// cos and sin of a 2D rotation angle for the footprint rule: a fixed sequence of IEEE operations
+// (each written as its correctly rounded intrinsic, so no contraction or reassociation can change
+// a bit), with no library transcendental.  Any IEEE evaluation of the sequence gives the same
+// bits, which keeps the tile lists bit-exact without relying on two math libraries agreeing.
+// |th| <= 2^16 (the common case, rule_cos_sin): binary32 arithmetic with fused multiply-adds.
+// Reduction by Cody and Waite: k = rint(th * 2/pi), r = th - k pi/2 with pi/2 in three binary32
+// pieces; the first product is exact (th and k P1 are multiples of 2^-23, or of 2^-24 when
+// |th| < 1, and differ by less than 1).  Then the Taylor series of sin r to r^11 and cos r to r^10
+// (|r| <= pi/4 + 0.01, truncation below 2e-10) in Horner form in z = r^2; k mod 4 selects the
+// quadrant.  Each result is within one binary32 ulp of the correctly rounded value.
+// 2^16 < |th| <= 1e15 (rule_cos_sin_wide): the same steps in binary64 (pi/2 in three pieces of 33,
+// 33 and 53 significant bits, k times the first two exact for |k| < 2^20; Taylor series to r^17
+// and r^18), rounded once to binary32.  A larger or non-finite th gives NaN (the primitive becomes
+// invalid).
+__device__ __noinline__ void rule_cos_sin_wide(double th, float& c, float& s) {
     if (!(fabs(th) <= 1e15)) {
         c = s = __int_as_float(0x7fc00000);
         return;
@@ -154,6 +154,38 @@ __device__ __forceinline__ void rule_cos_sin(double th, float& c, float& s) {
     }
 }
 
+__device__ __forceinline__ void rule_cos_sin(float th, float& c, float& s) {
+    if (!(fabsf(th) <= 0x1p16f)) {
+        rule_cos_sin_wide((double)th, c, s);
+        return;
+    }
+    const float k = rintf(__fmul_rn(th, 0x1.45f306p-1f));  // th 2/pi
+    float r = __fmaf_rn(-k, 0x1.921fb6p+0f, th);           // - k P1, exact
+    r = __fmaf_rn(-k, -0x1.777a5cp-25f, r);                // - k P2
+    r = __fmaf_rn(-k, -0x1.ee59dap-50f, r);                // - k P3
+    const float z = __fmul_rn(r, r);
+    // sin: coefficients -1/11!, 1/9!, ..., -1/3! (binary32)
+    float ps = -0x1.ae6456p-26f;
+    ps = __fmaf_rn(ps, z, 0x1.71de3ap-19f);
+    ps = __fmaf_rn(ps, z, -0x1.a01a02p-13f);
+    ps = __fmaf_rn(ps, z, 0x1.111112p-7f);
+    ps = __fmaf_rn(ps, z, -0x1.555556p-3f);
+    const float sr = __fmaf_rn(__fmul_rn(r, z), ps, r);
+    // cos: coefficients -1/10!, 1/8!, ..., -1/2!
+    float pc = -0x1.27e4fcp-22f;
+    pc = __fmaf_rn(pc, z, 0x1.a01a02p-16f);
+    pc = __fmaf_rn(pc, z, -0x1.6c16c2p-10f);
+    pc = __fmaf_rn(pc, z, 0x1.555556p-5f);
+    pc = __fmaf_rn(pc, z, -0.5f);
+    const float cr = __fmaf_rn(z, pc, 1.0f);
+    switch ((int)k & 3) {
+        case 0: c = cr; s = sr; break;
+        case 1: c = -sr; s = cr; break;
+        case 2: c = -cr; s = -sr; break;
+        default: c = sr; s = -cr; break;
+    }
+}
+
 // 2D, RS record (cov2d = 0): Sigma = R(theta) diag(sx^2, sy^2) R(theta)^T;
 // Sigma^-1 = R diag(1/sx^2, 1/sy^2) R^T, whose Cholesky factor is l11 = sqrt(A), l21 = B / l11,
 // l22 = sqrt(det)/l11 = 1 / (sx sy l11).
@@ -186,7 +218,7 @@ __global__ void __launch_bounds__(256) k_footprint2d(const float4* __restrict__ 
     } else {
         const float sx = p0.z, sy = p0.w;
         float c, s;
-        rule_cos_sin((double)p1.x, c, s);
+        rule_cos_sin(p1.x, c, s);
         const float sx2 = sx * sx, sy2 = sy * sy;
         const float ix = 1.0f / sx2, iy = 1.0f / sy2;
         const float cc = c * c, ss = s * s, cs = c * s;

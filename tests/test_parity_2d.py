@@ -77,14 +77,19 @@ def test_backward_matches_oracle(N, H, W, scale, seed):
 
 
 def test_rotation_angles_across_quadrants_bit_exact():
-    """Rotation angles far outside [0, pi) (negative, many turns): the footprint rule's cos and sin
-    come from the same binary64 operation sequence on both sides, so the lists stay bit-exact and
-    the image matches the oracle's binary64 rotation."""
+    """Rotation angles far outside [0, pi) (negative, many turns, and a third beyond 2^16, where
+    the rule takes its binary64 branch): the footprint rule's cos and sin come from the same IEEE
+    operation sequence on both sides, so the lists stay bit-exact and the image matches the
+    oracle's binary64 rotation."""
     torch = torch_cuda()
     w = lib_ready()
     H, W = 96, 128
     p = synth.scene2d(1500, H, W, 21, (0.5, 24.0))
-    p[:, 4] = np.random.default_rng(22).uniform(-200.0, 200.0, p.shape[0]).astype(np.float32)
+    rng = np.random.default_rng(22)
+    th = rng.uniform(-200.0, 200.0, p.shape[0])
+    wide = rng.random(p.shape[0]) < 1.0 / 3.0
+    th[wide] = rng.choice([-1.0, 1.0], int(wide.sum())) * rng.uniform(7.0e4, 1.5e6, int(wide.sum()))
+    p[:, 4] = th.astype(np.float32)
     _, st, img = _gpu_forward(w, torch, p, H, W)
     tiles, prims, _ = st.lists()
     ot, op = oracle.tile_lists(2, p, H, W)
