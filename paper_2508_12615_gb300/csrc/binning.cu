@@ -107,11 +107,12 @@ __global__ void __launch_bounds__(kThreads) k_scan_offsets(const uint32_t* __res
 }
 
 // Emission, one thread per scan position: a primitive writes the tiles of its covered range that
-// its cutoff ellipse reaches, in row-major tile order, from its offset on.  When its count equals
-// the number of tiles of the range (the common case for small footprints) every tile is reached and
-// none needs the test; a range of at most kEmitSmall tiles is tested by the thread; larger ones are
-// emitted by the whole warp, one after another, 32 tiles at a time (ballot + population count).
-constexpr int kEmitSmall = 16;
+// its cutoff ellipse reaches, in row-major tile order, from its offset on.  The warp's 32 ranges
+// are laid end to end (a prefix of their tile counts over the lanes) and visited 32 tiles a round:
+// the tile in slot s belongs to the lane whose prefix range holds s (a binary search over the
+// lanes' inclusive prefixes); a primitive whose count equals its range's tile count reaches every
+// tile and needs no test.  A hit goes to its primitive's next index at the round's start plus the
+// primitive's hits in earlier slots of the round's ballot.
 __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ counts,
                                                    const uint32_t* __restrict__ perm, int64_t n,
                                                    const float4* __restrict__ rec, const PixRect* __restrict__ rect,
@@ -121,94 +122,75 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
     pdl_enter();
     const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    uint32_t p = 0u, cnt = 0u, o = 0u;
+    uint32_t p = 0u, run = 0u;  // run: this lane's primitive's next instance index
     PixRect r{1, 1, 0, 0};
     int tx0 = 0, ty0 = 0, nx = 1, nt = 0;
-    bool big = false;
-    Ellipse eb{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool full = true;
+    Ellipse e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (j < n) {
         p = perm ? perm[j] : (uint32_t)j;
-        cnt = counts[p];
+        const uint32_t cnt = counts[p];
         if (cnt) {
             r = rect[p];
-            o = offsets[p];
+            run = offsets[p];
             tx0 = r.u0 / kTile;
             ty0 = r.v0 / kTile;
             nx = r.u1 / kTile - tx0 + 1;
             nt = nx * (r.v1 / kTile - ty0 + 1);
-            const int ty1 = ty0 + nt / nx;  // one past the last tile row
-            if ((int)cnt == nt) {
-                uint32_t w = o;
-                for (int ty = ty0; ty < ty1; ++ty)
-                    for (int tx = tx0; tx < tx0 + nx; ++tx, ++w) {
-                        keys[w] = (uint32_t)(ty * tiles_x + tx);
-                        vals[w] = w;
-                        inst_prim[w] = p;
-                    }
-            } else if (nt <= kEmitSmall) {
+            full = (int)cnt == nt;
+            if (!full) {
                 const float4 A = rec[(size_t)p * kRecF4 + 0];
-                const Ellipse e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
-                uint32_t w = o;
-                for (int ty = ty0; ty < ty1; ++ty)
-                    for (int tx = tx0; tx < tx0 + nx; ++tx)
-                        if (tile_touched(e, r, tx, ty, lim)) {
-                            keys[w] = (uint32_t)(ty * tiles_x + tx);
-                            vals[w] = w;
-                            inst_prim[w] = p;
-                            ++w;
-                        }
-            } else {
-                // a large range: the warp emits it below; its ellipse is made here, by every such
-                // lane at once, so that the warp's walk over them waits on no load
-                big = true;
-                const float4 A = rec[(size_t)p * kRecF4 + 0];
-                eb = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
+                e = make_ellipse(A.x, A.y, A.z, A.w, rec[(size_t)p * kRecF4 + 1].x);
             }
         }
     }
-    uint32_t bigs = __ballot_sync(0xffffffffu, big);
-    while (bigs) {
-        const int k = __ffs(bigs) - 1;
-        bigs &= bigs - 1u;
-        const uint32_t pk = __shfl_sync(0xffffffffu, p, k);
+    int incl = nt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - nt;
+    for (int s0 = 0; s0 < total; s0 += 32) {
+        const int s = s0 + lane;
+        int k = 0;  // the slot's owner: the number of lanes whose inclusive prefix is at most s
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, k + step - 1) <= s) k += step;
+        const int ek = __shfl_sync(0xffffffffu, excl, k);
+        const int nxk = __shfl_sync(0xffffffffu, nx, k);
+        const int txk = __shfl_sync(0xffffffffu, tx0, k), tyk = __shfl_sync(0xffffffffu, ty0, k);
+        const bool fullk = __shfl_sync(0xffffffffu, full, k);
+        const uint32_t pk = __shfl_sync(0xffffffffu, p, k), basek = __shfl_sync(0xffffffffu, run, k);
         PixRect rk;
         rk.u0 = __shfl_sync(0xffffffffu, r.u0, k);
         rk.u1 = __shfl_sync(0xffffffffu, r.u1, k);
         rk.v0 = __shfl_sync(0xffffffffu, r.v0, k);
         rk.v1 = __shfl_sync(0xffffffffu, r.v1, k);
-        uint32_t ok = __shfl_sync(0xffffffffu, o, k);
-        Ellipse e;
-        e.mx = __shfl_sync(0xffffffffu, eb.mx, k);
-        e.my = __shfl_sync(0xffffffffu, eb.my, k);
-        e.l11 = __shfl_sync(0xffffffffu, eb.l11, k);
-        e.l21 = __shfl_sync(0xffffffffu, eb.l21, k);
-        e.l22 = __shfl_sync(0xffffffffu, eb.l22, k);
-        e.rBA = __shfl_sync(0xffffffffu, eb.rBA, k);
-        e.rBC = __shfl_sync(0xffffffffu, eb.rBC, k);
-        const int kx0 = rk.u0 / kTile, ky0 = rk.v0 / kTile;
-        const int knx = rk.u1 / kTile - kx0 + 1, knt = knx * (rk.v1 / kTile - ky0 + 1);
-        // tile t = t0 + lane of the range as (row, column) = divmod(t, knx), advanced by 32 a step
-        const int s_row = 32 / knx, s_col = 32 % knx;
-        int row = lane / knx, col = lane % knx;
-        for (int t0 = 0; t0 < knt; t0 += 32) {
-            const int t = t0 + lane;
-            const int ty = ky0 + row, tx = kx0 + col;
-            const bool hit = t < knt && tile_touched(e, rk, tx, ty, lim);
-            row += s_row;
-            col += s_col;
-            if (col >= knx) {
-                col -= knx;
-                ++row;
-            }
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const uint32_t w = ok + __popc(bal & ((1u << lane) - 1u));
-                keys[w] = (uint32_t)(ty * tiles_x + tx);
-                vals[w] = w;
-                inst_prim[w] = pk;
-            }
-            ok += __popc(bal);
+        Ellipse ekk;
+        ekk.mx = __shfl_sync(0xffffffffu, e.mx, k);
+        ekk.my = __shfl_sync(0xffffffffu, e.my, k);
+        ekk.l11 = __shfl_sync(0xffffffffu, e.l11, k);
+        ekk.l21 = __shfl_sync(0xffffffffu, e.l21, k);
+        ekk.l22 = __shfl_sync(0xffffffffu, e.l22, k);
+        ekk.rBA = __shfl_sync(0xffffffffu, e.rBA, k);
+        ekk.rBC = __shfl_sync(0xffffffffu, e.rBC, k);
+        const int t = s - ek;
+        const int row = t / nxk, col = t - row * nxk;
+        const int tx = txk + col, ty = tyk + row;
+        const bool hit = s < total && (fullk || tile_touched(ekk, rk, tx, ty, lim));
+        const uint32_t hits = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int lo = max(ek - s0, 0);  // the owner's first slot of the round
+            const uint32_t w = basek + (uint32_t)__popc(hits & ((1u << lane) - 1u) & ~((1u << lo) - 1u));
+            keys[w] = (uint32_t)(ty * tiles_x + tx);
+            vals[w] = w;
+            inst_prim[w] = pk;
         }
+        // each primitive's index moves past its hits of the round
+        const int lo = max(excl - s0, 0), hi = min(incl - s0, 32);
+        if (lo < hi) run += (uint32_t)__popc((hits >> lo) & (0xffffffffu >> (32 - (hi - lo))));
     }
 }
 
