@@ -345,11 +345,17 @@ __global__ void __launch_bounds__(256) k_reduce_chain2d(const float* __restrict_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int hl = lane & 15, half = lane >> 4;
     const int64_t prim0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * kChainPrims;
+    // the offsets and counts of the warp's primitives, loaded once (lane k: primitive k)
+    uint32_t my_off = 0u, my_cnt = 0u;
+    if (lane < kChainPrims && prim0 + lane < N) {
+        my_off = offsets[prim0 + lane];
+        my_cnt = counts[prim0 + lane];
+    }
 #pragma unroll
     for (int k2 = 0; k2 < kChainPrims; k2 += 2) {
         if (prim0 + k2 >= N) break;  // uniform across the warp
         const int64_t pk = prim0 + k2 + half;
-        const uint32_t off = pk < N ? offsets[pk] : 0u, cnt = pk < N ? counts[pk] : 0u;
+        const uint32_t off = __shfl_sync(0xffffffffu, my_off, k2 + half), cnt = __shfl_sync(0xffffffffu, my_cnt, k2 + half);
         float acc[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) acc[m] = 0.f;
