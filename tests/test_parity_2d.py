@@ -76,6 +76,35 @@ def test_backward_matches_oracle(N, H, W, scale, seed):
     assert np.all(grad.cpu().numpy()[:, 11:] == 0)
 
 
+def test_tile_lists_with_huge_and_offscreen_footprints():
+    """Warps whose covered ranges differ by two orders of magnitude: huge footprints (hundreds of
+    tiles each, so one primitive's range spans many of the 32-tile counting and emission rounds),
+    primitives whose centre lies far outside the image (empty or partial ranges) and small ones,
+    interleaved in index order.  Lists and ranges bit-exact; the image within the forward bound."""
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 200, 300
+    rng = np.random.default_rng(41)
+    p = synth.scene2d(1200, H, W, 41, (0.5, 6.0))
+    huge = rng.random(p.shape[0]) < 0.04
+    p[huge, 2:4] = rng.uniform(60.0, 200.0, (int(huge.sum()), 2)).astype(np.float32)
+    off = rng.random(p.shape[0]) < 0.10
+    p[off, 0] = rng.choice([-1.0, 1.0], int(off.sum())).astype(np.float32) * rng.uniform(310.0, 700.0, int(off.sum())).astype(np.float32)
+    _, st, img = _gpu_forward(w, torch, p, H, W)
+    tiles, prims, ranges = st.lists()
+    ot, op = oracle.tile_lists(2, p, H, W)
+    assert np.array_equal(tiles.cpu().numpy().view(np.uint32), ot)
+    assert np.array_equal(prims.cpu().numpy().view(np.uint32), op)
+    per_prim = np.bincount(op.astype(np.int64), minlength=p.shape[0])
+    assert per_prim[huge].max() > 96  # some range spans more than three rounds
+    r = ranges.cpu().numpy()
+    for t in range(r.shape[0]):
+        sel = np.nonzero(ot == t)[0]
+        assert (r[t, 0], r[t, 1]) == ((sel[0], sel[-1] + 1) if len(sel) else (r[t, 0], r[t, 0]))
+    ref = oracle.render2d(p, H, W, truncated=True)
+    assert np.abs(img.cpu().numpy().astype(np.float64) - ref).max() <= FWD_ATOL
+
+
 def test_rotation_angles_across_quadrants_bit_exact():
     """Rotation angles far outside [0, pi) (negative, many turns, and a third beyond 2^16, where
     the rule takes its binary64 branch): the footprint rule's cos and sin come from the same IEEE
