@@ -139,6 +139,7 @@ struct wipes_ctx {
     MemAccount mem;
     std::atomic<int64_t> live_states{0};  // a context is not destroyed while states refer to it
     unsigned long long* h_total = nullptr;  // pinned readback: [0] instance count, [1] device error word
+    unsigned long long* d_readback = nullptr;  // h_total's device address (mapped pinned memory)
     unsigned int* d_error = nullptr;        // device error word: bit 0 = a bounded device wait ran out
     float* d_loss_partials = nullptr;
     unsigned long long* d_counters = nullptr;  // pair counters
@@ -267,10 +268,8 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
     if (N > 0) {
         StageTimer t(st->ctx, WIPES_STAGE_SCAN, s);
         launch_block_sums(st->counts.as<uint32_t>(), perm, N, st->block_sums.as<unsigned long long>(), s);
-        launch_scan_block_sums(st->block_sums.as<unsigned long long>(), nb, total, s);
-        WIPES_CUDA(cudaMemcpyAsync(st->ctx->h_total, total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        WIPES_CUDA(cudaMemcpyAsync(st->ctx->h_total + 1, st->ctx->d_error, sizeof(unsigned long long),
-                                   cudaMemcpyDeviceToHost, s));
+        launch_scan_block_sums(st->block_sums.as<unsigned long long>(), nb, total,
+                               reinterpret_cast<const unsigned long long*>(st->ctx->d_error), st->ctx->d_readback, s);
         t.stop();
         WIPES_CUDA(cudaStreamSynchronize(s));
         st->n_inst = (int64_t)st->ctx->h_total[0];
@@ -404,6 +403,7 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     wipes_ctx* c = new wipes_ctx();
     c->device = device;
     cudaError_t e = cudaMallocHost(&c->h_total, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->d_readback, c->h_total, 0);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_error, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_error, 0, sizeof(unsigned long long));
     // the loss's block partials and, after them, its block counter (zero between calls)

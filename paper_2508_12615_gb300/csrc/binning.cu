@@ -62,7 +62,9 @@ __global__ void __launch_bounds__(kThreads) k_block_sums(const uint32_t* __restr
 }
 
 __global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long* __restrict__ v, int nb,
-                                                              unsigned long long* __restrict__ total_out) {
+                                                              unsigned long long* __restrict__ total_out,
+                                                              const unsigned long long* __restrict__ error,
+                                                              unsigned long long* __restrict__ readback) {
     pdl_enter();
     __shared__ unsigned long long s_warp[kWarps];
     unsigned long long carry = 0;
@@ -74,7 +76,15 @@ __global__ void __launch_bounds__(kThreads) k_scan_block_sums(unsigned long long
         if (j < nb) v[j] = carry + ex;
         carry += chunk;
     }
-    if (threadIdx.x == 0) *total_out = carry;
+    if (threadIdx.x == 0) {
+        *total_out = carry;
+        // the host's pinned readback (device address of mapped host memory): the total and the
+        // device error word, read after the stream is synchronised, with no copy
+        if (readback) {
+            readback[0] = carry;
+            readback[1] = *error;
+        }
+    }
 }
 
 // First instance index of every primitive: the block-local exclusive scan of the tile counts of
@@ -582,8 +592,9 @@ void launch_block_sums(const uint32_t* counts, const uint32_t* perm, int64_t n, 
     launch_pdl(k_block_sums, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_sums); count_launches(1);
 }
 
-void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total, cudaStream_t stream) {
-    launch_pdl(k_scan_block_sums, 1, kThreads, 0, stream, block_sums, nb, total); count_launches(1);
+void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total,
+                            const unsigned long long* error, unsigned long long* readback, cudaStream_t stream) {
+    launch_pdl(k_scan_block_sums, 1, kThreads, 0, stream, block_sums, nb, total, error, readback); count_launches(1);
 }
 
 void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,

@@ -457,8 +457,10 @@ void launch_deform6d_backward(const float* params6, int64_t N, float t, const fl
 constexpr int kScanBlockElems = 1024;
 void launch_block_sums(const uint32_t* counts, const uint32_t* perm, int64_t n, unsigned long long* block_sums,
                        cudaStream_t stream);
-// Exclusive scan of nb block sums in place; total written to *total.
-void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total, cudaStream_t stream);
+// Exclusive scan of nb block sums in place; total written to *total.  With a readback pointer (the
+// device address of mapped pinned host memory) the total and *error also go to readback[0..1].
+void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned long long* total,
+                            const unsigned long long* error, unsigned long long* readback, cudaStream_t stream);
 // Emit one instance per tile the cutoff ellipse reaches, in scan order: keys[e] = tile id,
 // vals[e] = e (the emission index), inst_prim[e] = primitive; offsets[prim] = its first index.
 // Also sets the n_tiles tile ranges to empty (for launch_tile_ranges with zeroed = true).
