@@ -267,6 +267,40 @@ def test_backward_needs_a_recording_forward():
     assert (grad - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
 
 
+@pytest.mark.parametrize("o", [DEFAULT, RAY], ids=["map0", "map2"])
+def test_backward_repeated_on_one_forward(o):
+    """Backward passes leave the per-primitive image-plane gradient at zero and the persistent
+    kernel's work counter at zero for the next one: three backward passes on one forward, with the
+    upstream gradient g, 2 g and g, give gradients g1, 2 g1 (to rounding) and g1 again (equal up to
+    the order of the atomic additions), and a forward of another view in between changes nothing
+    of that."""
+    torch = torch_cuda()
+    w = lib_ready()
+    H, W = 64, 80
+    p = synth.scene3d(1500, 51)
+    cams = synth.sphere_cameras(2, H, W, 52)
+    params = torch.from_numpy(p).cuda()
+    g = torch.from_numpy(synth.upstream_grad(H, W, 53)).cuda()
+    ctx = w.Context.get(0)
+    st = ctx.acquire_state()
+    opts = _opts(w, o)
+    w.forward3d(params, cams[0], H, W, opts, state=st)
+    g1 = w.backward(st, params, g)
+    g2 = w.backward(st, params, 2.0 * g)
+    g3 = w.backward(st, params, g)
+    torch.cuda.synchronize()
+    scale = g1.abs().max().item()
+    assert scale > 0.0
+    assert (g2 - 2.0 * g1).abs().max().item() <= 2e-4 * scale
+    assert (g3 - g1).abs().max().item() <= 1e-4 * scale
+    w.forward3d(params, cams[1], H, W, opts, state=st)
+    w.backward(st, params, g)
+    w.forward3d(params, cams[0], H, W, opts, state=st)
+    g4 = w.backward(st, params, g)
+    torch.cuda.synchronize()
+    assert (g4 - g1).abs().max().item() <= 1e-4 * scale
+
+
 def test_empty_and_all_culled():
     torch = torch_cuda()
     w = lib_ready()
