@@ -140,6 +140,7 @@ struct wipes_ctx {
     std::atomic<int64_t> live_states{0};  // a context is not destroyed while states refer to it
     unsigned long long* h_total = nullptr;  // pinned readback: [0] instance count, [1] device error word
     unsigned long long* d_readback = nullptr;  // h_total's device address (mapped pinned memory)
+    cudaEvent_t scan_done = nullptr;           // recorded after the scan writes h_total; the host waits on it
     unsigned int* d_error = nullptr;        // device error word: bit 0 = a bounded device wait ran out
     float* d_loss_partials = nullptr;
     unsigned long long* d_counters = nullptr;  // pair counters
@@ -265,13 +266,32 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
     const int n_tiles = st->tiles_x * st->tiles_y;
     WIPES_TRY(ensure(st->ranges, sizeof(uint2) * (size_t)n_tiles));
     unsigned long long* total = st->total.as<unsigned long long>();
+    // Emission is enqueued before the host waits for the instance total, into the list buffers as
+    // they are, so that the GPU runs it while the host wakes up.  It writes nothing when the total
+    // exceeds their capacity (a state's first call, or lists that grew) and is launched again below,
+    // once they have grown.
+    auto capacity = [&]() {
+        return (int64_t)(std::min({st->keys[0].cap, st->vals[0].cap, st->inst_prim.cap}) / sizeof(uint32_t));
+    };
+    auto emit = [&]() {
+        StageTimer t(st->ctx, WIPES_STAGE_EMIT, s);
+        launch_emit(st->counts.as<uint32_t>(), perm, N, st->rec.as<float4>(), st->rect.as<PixRect>(),
+                    st->block_sums.as<unsigned long long>(), total, capacity(), st->tiles_x,
+                    touch_limit(st->opts.cutoff_sigma), st->keys[0].as<uint32_t>(), st->vals[0].as<uint32_t>(),
+                    st->inst_prim.as<uint32_t>(), st->offsets.as<uint32_t>(), st->ranges.as<uint2>(), n_tiles, s);
+    };
+    const int64_t emitted_capacity = capacity();
     if (N > 0) {
-        StageTimer t(st->ctx, WIPES_STAGE_SCAN, s);
-        launch_block_sums(st->counts.as<uint32_t>(), perm, N, st->block_sums.as<unsigned long long>(), s);
-        launch_scan_block_sums(st->block_sums.as<unsigned long long>(), nb, total,
-                               reinterpret_cast<const unsigned long long*>(st->ctx->d_error), st->ctx->d_readback, s);
-        t.stop();
-        WIPES_CUDA(cudaStreamSynchronize(s));
+        {
+            StageTimer t(st->ctx, WIPES_STAGE_SCAN, s);
+            launch_block_sums(st->counts.as<uint32_t>(), perm, N, st->block_sums.as<unsigned long long>(), s);
+            launch_scan_block_sums(st->block_sums.as<unsigned long long>(), nb, total,
+                                   reinterpret_cast<const unsigned long long*>(st->ctx->d_error), st->ctx->d_readback,
+                                   s);
+            WIPES_CUDA(cudaEventRecord(st->ctx->scan_done, s));
+        }
+        emit();
+        WIPES_CUDA(cudaEventSynchronize(st->ctx->scan_done));
         st->n_inst = (int64_t)st->ctx->h_total[0];
         WIPES_TRY(take_device_error(st->ctx, s));
     } else {
@@ -287,13 +307,7 @@ wipes_status bin_and_sort(wipes_state* st, const uint32_t* perm, cudaStream_t s)
     WIPES_TRY(ensure(st->inst_prim, sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
     WIPES_TRY(ensure(st->sprim, sizeof(uint32_t) * (size_t)std::max<int64_t>(I, 1)));
     WIPES_TRY(ensure(st->hist, sizeof(uint32_t) * (size_t)radix_hist_words(I)));
-    if (N > 0) {
-        StageTimer t(st->ctx, WIPES_STAGE_EMIT, s);
-        launch_emit(st->counts.as<uint32_t>(), perm, N, st->rec.as<float4>(), st->rect.as<PixRect>(),
-                    st->block_sums.as<unsigned long long>(), st->tiles_x, touch_limit(st->opts.cutoff_sigma),
-                    st->keys[0].as<uint32_t>(), st->vals[0].as<uint32_t>(), st->inst_prim.as<uint32_t>(),
-                    st->offsets.as<uint32_t>(), st->ranges.as<uint2>(), n_tiles, s);
-    }
+    if (N > 0 && I > emitted_capacity) emit();  // the first launch wrote nothing
     uint32_t* kb[2] = {st->keys[0].as<uint32_t>(), st->keys[1].as<uint32_t>()};
     uint32_t* vb[2] = {st->vals[0].as<uint32_t>(), st->vals[1].as<uint32_t>()};
     {
@@ -404,6 +418,7 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     c->device = device;
     cudaError_t e = cudaMallocHost(&c->h_total, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->d_readback, c->h_total, 0);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->scan_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_error, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_error, 0, sizeof(unsigned long long));
     // the loss's block partials and, after them, its block counter (zero between calls)
@@ -424,6 +439,7 @@ wipes_status wipes_create(int device, wipes_ctx** out) {
     }
     if (e != cudaSuccess) {
         if (c->h_total) cudaFreeHost(c->h_total);
+        if (c->scan_done) cudaEventDestroy(c->scan_done);
         if (c->mem.pool) cudaMemPoolDestroy(c->mem.pool);
         delete c;
         return fail(WIPES_ERR_CUDA, std::string("context allocation failed: ") + cudaGetErrorString(e));
@@ -444,6 +460,7 @@ wipes_status wipes_destroy(wipes_ctx* ctx) {
         cudaEventDestroy(b.b);
     }
     for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
+    cudaEventDestroy(ctx->scan_done);
     cudaFreeHost(ctx->h_total);
     cudaFree(ctx->d_loss_partials);
     cudaFree(ctx->d_counters);

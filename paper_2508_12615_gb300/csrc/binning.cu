@@ -127,9 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ perm, int64_t n,
                                                    const float4* __restrict__ rec, const PixRect* __restrict__ rect,
                                                    const uint32_t* __restrict__ offsets, int tiles_x, float lim,
+                                                   const unsigned long long* __restrict__ n_inst, int64_t capacity,
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    uint32_t* __restrict__ inst_prim) {
     pdl_enter();
+    if (*n_inst > (unsigned long long)capacity) return;  // the host launches it again into larger buffers
     const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
     uint32_t p = 0u, run = 0u;  // run: this lane's primitive's next instance index
@@ -598,13 +600,14 @@ void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned lon
 }
 
 void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,
-                 const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
-                 uint32_t* inst_prim, uint32_t* offsets, uint2* ranges, int n_tiles, cudaStream_t stream) {
+                 const unsigned long long* block_offsets, const unsigned long long* total, int64_t capacity,
+                 int tiles_x, float lim, uint32_t* keys, uint32_t* vals, uint32_t* inst_prim, uint32_t* offsets,
+                 uint2* ranges, int n_tiles, cudaStream_t stream) {
     if (n == 0) return;
     launch_pdl(k_scan_offsets, ceil_div(n, kScanBlockElems), kThreads, 0, stream, counts, perm, n, block_offsets, offsets,
                ranges, n_tiles);
-    launch_pdl(k_emit, ceil_div(n, kThreads), kThreads, 0, stream, counts, perm, n, rec, rect, offsets, tiles_x, lim, keys,
-               vals, inst_prim);
+    launch_pdl(k_emit, ceil_div(n, kThreads), kThreads, 0, stream, counts, perm, n, rec, rect, offsets, tiles_x, lim,
+               total, capacity, keys, vals, inst_prim);
     count_launches(2);
 }
 

@@ -463,10 +463,13 @@ void launch_scan_block_sums(unsigned long long* block_sums, int nb, unsigned lon
                             const unsigned long long* error, unsigned long long* readback, cudaStream_t stream);
 // Emit one instance per tile the cutoff ellipse reaches, in scan order: keys[e] = tile id,
 // vals[e] = e (the emission index), inst_prim[e] = primitive; offsets[prim] = its first index.
-// Also sets the n_tiles tile ranges to empty (for launch_tile_ranges with zeroed = true).
+// Also sets the n_tiles tile ranges to empty (for launch_tile_ranges with zeroed = true).  The
+// emission writes nothing when the instance total (*total, on the device) exceeds `capacity`, the
+// element count of keys, vals and inst_prim.
 void launch_emit(const uint32_t* counts, const uint32_t* perm, int64_t n, const float4* rec, const PixRect* rect,
-                 const unsigned long long* block_offsets, int tiles_x, float lim, uint32_t* keys, uint32_t* vals,
-                 uint32_t* inst_prim, uint32_t* offsets, uint2* ranges, int n_tiles, cudaStream_t stream);
+                 const unsigned long long* block_offsets, const unsigned long long* total, int64_t capacity,
+                 int tiles_x, float lim, uint32_t* keys, uint32_t* vals, uint32_t* inst_prim, uint32_t* offsets,
+                 uint2* ranges, int n_tiles, cudaStream_t stream);
 // out[i] = table[idx[i]]
 void launch_gather_u32(uint32_t* out, const uint32_t* table, const uint32_t* idx, int64_t n, cudaStream_t stream);
 // ranges[t] = [start, end) of tile t in the sorted keys; zeroed: the ranges were set to empty before
