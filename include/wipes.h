@@ -17,8 +17,10 @@
  *     frees caller memory and keeps no pointer to it after the call returns (except as stated for
  *     wipes_state).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls enqueue
- *     work on it and return; WIPES_OK means "enqueued".  wipes_render2d/3d read one 8-byte value
- *     back to the host (the number of tile instances) and therefore synchronise `stream` once.
+ *     work on it and return; WIPES_OK means "enqueued".  wipes_render2d/3d (and the prepare calls)
+ *     read one value back to the host (the number of tile instances): each waits once for the work
+ *     on `stream` up to the scan that produces it (the emission that follows is already enqueued
+ *     and keeps running), then enqueues the rest.
  *   - Pixel (u, v) (column u, row v) is sampled at (u + 0.5, v + 0.5).  Images are [H, W, 3].
  *   - Frequencies are in cycles per pixel (2D) or cycles per world unit (3D); phases in radians.
  *   - On failure a call returns a non-zero wipes_status and wipes_last_error() describes it.
