@@ -103,7 +103,10 @@ typedef struct {
 /* Fill `out` with the defaults for dims = 2 or 3. */
 void wipes_default_opts(int dims, wipes_opts* out);
 
-/* Create a context on CUDA device `device`.  Errors: INVALID (bad device), CUDA. */
+/* Create a context on CUDA device `device`.  Errors: INVALID (bad device), CUDA.  A context holds
+ * one host readback word pair, one event and the loss's reduction buffer: calls that use one
+ * context are made from one host thread at a time (separate contexts serve concurrent threads or
+ * concurrently running streams, as the bench's 6D samples do). */
 wipes_status wipes_create(int device, wipes_ctx** out);
 /* Destroy a context; fails with WIPES_ERR_INVALID (and destroys nothing) while states created on
  * it are alive. */
